@@ -1,0 +1,100 @@
+"""Lattice sampling and Fourier-coefficient recovery (oracle; test
+infrastructure only).
+
+Section 2 (Definition of Fourier coefficients): g_hat_k = integral of
+g(x) exp(-2 pi i k.x) over the torus.  On a rank-1 lattice, x_j = (j z / M) mod 1
+and k.x_j = j (k.z) / M (mod 1), so the univariate samples t -> g(t z) hold
+the coefficient of k in DFT bin (k.z mod M):
+
+    g_hat_k = (1/M) sum_{j<M} g(x_j) exp(-2 pi i j (k.z mod M) / M)
+
+exactly, whenever g's support is a subset of a set I on which the lattice is
+reconstructing (Section "Previous results on SFTs", the reconstructing
+property).  This module evaluates that sum directly (no FFT).
+
+Known-support recovery (the premise of Theorem SFTRecovery that a
+reconstructing lattice for I is known): read the bins of the candidates k in
+I, symmetrise g_hat_k := (g_hat_k + conj(g_hat_{-k}))/2 (a real g has
+Hermitian coefficients), and keep |g_hat_k| > tau * max |g_hat| (the paper
+gives no threshold: tau is a parameter, 1e-9 in FP64 by default).  More than
+``s_max`` survivors is an error (the paper's SFT returns at most 2s terms).
+
+Pins: closed forms of cosine, sine and constant terms; equality with a full
+length-M FFT from numpy when I is a bijective box; direct evaluation of g at
+floating-point lattice points (tests/test_oracle_sft.py).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .lattice import residues, is_reconstructing
+
+
+def sample(freq, coef, z, M, js=None):
+    """g(x_j) for g(x) = sum_t Re(coef_t exp(2 pi i freq_t.x)), at lattice
+    indices ``js`` (all j < M by default).  The phase of term t at x_j is
+    2 pi (j q_t mod M)/M with q_t = freq_t.z mod M, in exact integers."""
+    M = int(M)
+    js = np.arange(M, dtype=np.int64) if js is None else np.asarray(js, dtype=np.int64)
+    q = residues(freq, z, M)
+    g = np.zeros(len(js), dtype=np.float64)
+    for qt, ct in zip(q, np.asarray(coef, np.complex128)):
+        r = (js * int(qt)) % M
+        g += (ct * np.exp(2j * np.pi * (r / M))).real
+    return g
+
+
+def dft_bins(samples, bins, M, chunk=1 << 14):
+    """(1/M) sum_j samples[j] exp(-2 pi i j b / M) for each bin b (plain DFT)."""
+    M = int(M)
+    samples = np.asarray(samples)
+    bins = np.asarray(bins, dtype=np.int64)
+    out = np.zeros(len(bins), dtype=np.complex128)
+    for j0 in range(0, M, chunk):
+        j = np.arange(j0, min(M, j0 + chunk), dtype=np.int64)
+        r = (j[:, None] * bins[None, :]) % M
+        out += samples[j0:j0 + len(j)] @ np.exp(-2j * np.pi * (r / M))
+    return out / M
+
+
+def recover_known(samples, cand, z, M, tau=1e-9, s_max=None):
+    """Known-support recovery from lattice samples.
+
+    Returns (freq, val) of the kept candidates, in candidate order.  Raises if
+    the lattice is not reconstructing for ``cand``, if ``cand`` is not closed
+    under negation, or if more than ``s_max`` candidates survive."""
+    cand = np.asarray(cand, np.int64)
+    M = int(M)
+    keys = {tuple(int(x) for x in row) for row in cand}
+    if len(keys) != len(cand):
+        raise ValueError("duplicate candidates")
+    if any(tuple(-x for x in k) not in keys for k in keys):
+        raise ValueError("candidate set is not symmetric")
+    if not is_reconstructing(cand, z, M):
+        raise ValueError("lattice is not reconstructing for the candidates")
+    b = residues(cand, z, M)
+    bneg = (M - b) % M
+    ghat = dft_bins(samples, np.concatenate([b, bneg]), M)
+    n = len(cand)
+    val = 0.5 * (ghat[:n] + np.conj(ghat[n:]))
+    mag = np.abs(val)
+    keep = mag > tau * mag.max() if n else np.zeros(0, bool)
+    if s_max is not None and keep.sum() > s_max:
+        raise ValueError("more terms above threshold than s_max")
+    return cand[keep].astype(np.int32), val[keep]
+
+
+def true_coefficients(freq, coef):
+    """Fourier coefficients of sum_t Re(c_t e_{p_t}) from the definition:
+    Re(c e_p) = (c e_p + conj(c) e_{-p})/2, so p gets c/2 and -p gets conj(c)/2
+    (p = 0 gets Re(c)).  Returns a dict {k: value}."""
+    out = {}
+    for p, c in zip(np.asarray(freq, np.int64), np.asarray(coef, np.complex128)):
+        k = tuple(int(x) for x in p)
+        mk = tuple(-x for x in k)
+        if not any(k):
+            out[k] = out.get(k, 0) + c.real
+        else:
+            out[k] = out.get(k, 0) + c / 2
+            out[mk] = out.get(mk, 0) + np.conj(c) / 2
+    return out

@@ -1,0 +1,86 @@
+"""Pins for oracle.sft (lattice sampling; recovery of Fourier coefficients by the
+DFT of lattice samples, Section 2 coefficient definition and the
+reconstructing-lattice premise of Theorem SFTRecovery)."""
+import numpy as np
+import pytest
+
+from oracle import lattice as lat
+from oracle import sft
+
+
+def eval_at_float_points(freq, coef, z, M, js):
+    """g at x_j = (j z / M) mod 1 computed in floating point (no residues)."""
+    x = np.mod(np.outer(js, np.asarray(z, np.float64)) / M, 1.0)
+    ph = 2 * np.pi * x @ np.asarray(freq, np.float64).T
+    return (np.exp(1j * ph) * np.asarray(coef)[None, :]).real.sum(axis=1)
+
+
+def test_sample_equals_pointwise_evaluation():
+    rng = np.random.default_rng(0)
+    d, M = 3, 1009
+    z = rng.integers(1, M, size=d)
+    freq = rng.integers(-7, 8, size=(6, d))
+    coef = rng.standard_normal(6) + 1j * rng.standard_normal(6)
+    js = np.arange(M)
+    np.testing.assert_allclose(sft.sample(freq, coef, z, M), eval_at_float_points(freq, coef, z, M, js),
+                               atol=1e-11)
+
+
+def test_recover_closed_form_cos_sin_mean():
+    # g = 0.7 + 0.3 cos(2pi p.x) - 0.2 sin(2pi q.x):
+    # g_hat_0 = 0.7, g_hat_{+-p} = 0.15, g_hat_{+q} = -0.2/(2i) = 0.1i, g_hat_{-q} = -0.1i
+    d = 3
+    p = np.array([2, -1, 3])
+    q = np.array([-4, 0, 1])
+    freq = np.array([[0, 0, 0], p, q])
+    coef = np.array([0.7, 0.3, -0.2 * -1j])       # sine term c sin = Re(-i c e)
+    # box lattice z = (1, 9, 81), M = 9^3: a bijection of [-4,4]^3 onto Z_M
+    g = np.arange(-4, 5)
+    cand = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    z, M = np.array([1, 9, 81]), 729
+    assert lat.is_reconstructing(cand, z, M)
+    samples = sft.sample(freq, coef, z, M)
+    kf, kv = sft.recover_known(samples, cand, z, M, tau=1e-9)
+    got = {tuple(k): v for k, v in zip(kf.tolist(), kv)}
+    want = {(0, 0, 0): 0.7, tuple(p): 0.15, tuple(-p): 0.15, tuple(q): 0.1j, tuple(-q): -0.1j}
+    assert set(got) == set(want)
+    for k, v in want.items():
+        assert abs(got[k] - v) < 1e-12 * 1.2
+
+
+def test_dft_equals_library_fft_on_box_lattice():
+    rng = np.random.default_rng(2)
+    M = 1089
+    samples = rng.standard_normal(M)
+    bins = np.arange(M)
+    np.testing.assert_allclose(sft.dft_bins(samples, bins, M), np.fft.fft(samples) / M, atol=1e-13)
+
+
+def test_true_coefficients_definition():
+    c = sft.true_coefficients([[0, 0], [1, 2], [1, 2]], [2.0, 1.0 + 1j, 0.5])
+    assert c[(0, 0)] == 2.0
+    assert c[(1, 2)] == pytest.approx((1.5 + 1j) / 2)
+    assert c[(-1, -2)] == pytest.approx((1.5 - 1j) / 2)
+
+
+def test_recover_rejects_bad_inputs():
+    cand = np.array([[1, 0], [-1, 0], [0, 1], [0, -1]])
+    s = np.zeros(7)
+    with pytest.raises(ValueError):
+        sft.recover_known(s, cand[:3], [1, 2], 7)            # not symmetric
+    with pytest.raises(ValueError):
+        sft.recover_known(s, cand, [1, 1], 7)                # (1,0) ~ (0,1)
+
+
+def test_threshold_and_cap():
+    d, M = 1, 101
+    freq = np.array([[3], [5]])
+    coef = np.array([1.0, 1e-12])
+    cand = np.arange(-10, 11).reshape(-1, 1)
+    s = sft.sample(freq, coef, [1], M)
+    kf, _ = sft.recover_known(s, cand, [1], M, tau=1e-9)
+    assert sorted(kf.ravel().tolist()) == [-3, 3]
+    kf, _ = sft.recover_known(s, cand, [1], M, tau=1e-14)
+    assert sorted(kf.ravel().tolist()) == [-5, -3, 3, 5]
+    with pytest.raises(ValueError):
+        sft.recover_known(s, cand, [1], M, tau=1e-14, s_max=3)
