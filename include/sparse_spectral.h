@@ -1,0 +1,243 @@
+/*
+ * sparse_spectral.h - C ABI of a single-GPU (sm_103a) implementation of the
+ * sparse spectral method of Gross & Iwen (arXiv 2302.00752) for the periodic
+ * elliptic problem  -div(a grad u) = f  on the d-dimensional torus.
+ *
+ * The method (Algorithm 1 of the paper) is:
+ *   1. recover the Fourier coefficients a_hat, f_hat of the data by sampling
+ *      on a rank-1 lattice and taking a length-M one-dimensional FFT
+ *      (sft_recover; Section "Previous results on SFTs", Theorem SFTRecovery);
+ *   2. build the stamping set S^N[a_hat](supp f_hat) (stamp_build; eq. StampSet);
+ *   3. apply the finite Galerkin operator (galerkin_apply; eq. GF,
+ *      eq. FiniteGalerkinOperator);
+ *   4. solve L_{N,s} u_hat = f_hat on S^N (solve, batch_solve;
+ *      eq. SparseSpectralSFTEquation).
+ *
+ * Conventions shared by every call
+ *   - Plain C types only.  "device" pointers are CUDA device memory owned by
+ *     the caller; the library never frees them.  "host" pointers are read
+ *     during the call only.
+ *   - Complex values are interleaved (re, im): 2*n doubles for FP64, 2*n
+ *     floats for FP32.  Frequencies are int32, row-major [n][d].
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued on it.  Calls that must return a size or a status computed on
+ *     the GPU synchronise that stream once before returning (stated per call).
+ *   - Every call returns SS_OK or an error status; ss_last_error() then holds
+ *     a message for the calling thread.  On error, outputs are unspecified and
+ *     handles stay valid to destroy.
+ *   - Fourier convention (Section 2): g_hat_k = integral g(x) exp(-2 pi i k.x) dx.
+ *   - A "trigonometric sum" is g(x) = sum_t Re(c_t exp(2 pi i p_t . x)): a
+ *     cosine c cos(2 pi p.x) is (p, c), a sine c sin(2 pi p.x) is (p, -i c).
+ */
+#ifndef SPARSE_SPECTRAL_H
+#define SPARSE_SPECTRAL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SS_OK = 0,
+    SS_ERR_INVALID = 1,            /* bad argument (sizes, duplicates, f_hat_0 != 0, ...) */
+    SS_ERR_OOM = 2,                /* device allocation failed */
+    SS_ERR_CUDA = 3,               /* CUDA runtime or cuFFT error */
+    SS_ERR_NOT_RECONSTRUCTING = 4, /* two candidates share a lattice residue */
+    SS_ERR_HASH_FULL = 5,          /* frequency hash table exhausted */
+    SS_ERR_NOT_ELLIPTIC = 6,       /* ||a_hat - a_hat_0||_1 >= |a_hat_0| */
+    SS_ERR_NOT_CONVERGED = 7,      /* iteration cap reached before the tolerance */
+    SS_ERR_TIMEOUT = 8,            /* a bounded device-side wait gave up */
+    SS_ERR_KEY_RANGE = 9           /* frequencies too large for the packed key / index */
+} ss_status;
+
+typedef enum {
+    SS_FP64 = 0,   /* FP64 samples and FFT; FP64 operator; plain FP64 CG */
+    SS_FP32 = 1    /* FP32 samples and FFT; FP32 operator; FP32 CG inside FP64 iterative refinement */
+} ss_precision;
+
+/* Rank-1 lattice Lambda(z, M) = { (j z / M) mod 1 : j < M } (Section "Previous
+ * results on SFTs", Definition of the rank-1 lattice).  z: host, d entries in
+ * [1, M-1]; 2 <= M < 2^31. */
+typedef struct { int32_t d; int64_t M; const int64_t* z; } ss_lattice;
+
+/* Trigonometric sum: freq device int32 [n_terms][d], coef device FP64 complex
+ * [n_terms]. */
+typedef struct { int32_t d; int64_t n_terms; const int32_t* freq; const double* coef; } ss_trig;
+
+/* Sparse coefficient list: freq device int32 [n][d], val device FP64 complex [n]. */
+typedef struct { int32_t d; int64_t n; const int32_t* freq; const double* val; } ss_sparse;
+
+/* Opaque stamping set: owns its hash table, packed keys, levels, neighbour
+ * table and operator scratch until stamp_destroy. */
+typedef struct ss_stamp_s* ss_stamp;
+
+/* Opaque batch of stamping sets prepared for one persistent solve. */
+typedef struct ss_batch_s* ss_batch;
+
+typedef struct {
+    int32_t status;        /* ss_status of this solve */
+    int32_t outer_iters;   /* refinement steps (FP32 mode), 1 in FP64 mode */
+    int32_t inner_iters;   /* CG iterations in total */
+    int32_t applies;       /* operator applications (FP64 + FP32) */
+    double rel_residual;   /* ||f - L u||_2 / ||f||_2 in FP64 at exit */
+} ss_solve_stats;
+
+const char* ss_last_error(void);
+const char* ss_version(void);
+
+/* ---------------------------------------------------------------- lattice */
+
+/* Lemma RandomRank1Lattice: smallest prime > max(K, n_I^2 / sigma) and
+ * >= M_min.  Host arithmetic only.  K = expansion of the frequency set (side of
+ * the smallest cube holding it). */
+ss_status lattice_size(int64_t K, int64_t n_I, double sigma, int64_t M_min, int64_t* M_out);
+
+/* Reconstructing property (Definition after the rank-1 lattice): checks
+ * k.z != l.z (mod M) for all distinct rows of `freq` (device [n][d]).
+ * Returns SS_ERR_NOT_RECONSTRUCTING on a collision and SS_ERR_INVALID on a
+ * duplicate row.  Synchronises `stream`. */
+ss_status lattice_check(const ss_lattice* lat, const int32_t* freq, int64_t n, void* stream);
+
+/* Random lattice of Lemma RandomRank1Lattice for the frequency set `freq`
+ * (device [n][d], distinct rows): M = lattice_size(K, n, sigma, M_min) and, for
+ * attempt a = 0.., z_j = 1 + raw[a][j] mod (M-1) (raw: host [attempts][d],
+ * non-negative); the first reconstructing attempt is returned in z_out (host,
+ * d entries), M_out, attempt_out.  SS_ERR_NOT_RECONSTRUCTING if none is.
+ * Synchronises `stream`. */
+ss_status lattice_random(const int32_t* freq, int64_t n, int32_t d, double sigma, int64_t M_min,
+                         const int64_t* raw, int32_t attempts, int64_t* z_out, int64_t* M_out,
+                         int32_t* attempt_out, void* stream);
+
+/* Component-by-component lattice (named in Section "Improvements with
+ * randomized lattices"; criterion not given by the paper): M = smallest prime
+ * >= max(M_min, K + 1), z_1 = 1, and for j >= 2 the first candidate
+ * 1 + raw[j][c] mod (M-1) (raw: host [d][n_cand]) under which the distinct
+ * projections of `freq` onto coordinates 1..j have distinct residues.
+ * Synchronises `stream`. */
+ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int64_t M_min, const int64_t* raw,
+                      int32_t n_cand, int64_t* z_out, int64_t* M_out, void* stream);
+
+/* -------------------------------------------------------------------- SFT */
+
+/* Lattice sampling: samples[j] = g(x_j), x_j = (j z / M) mod 1, j < M, with the
+ * phase of each term taken from the exact residue (j (p.z mod M)) mod M.
+ * samples: device, M doubles (SS_FP64) or M floats (SS_FP32). */
+ss_status lattice_sample(const ss_lattice* lat, const ss_trig* g, ss_precision prec, void* samples,
+                         void* stream);
+
+/* Known-support recovery from lattice samples (Theorem SFTRecovery with a
+ * reconstructing lattice for the candidate set I given): one real-to-complex
+ * FFT of length M (cuFFT), then for every candidate k in I (device [n_cand][d],
+ * closed under negation, lattice reconstructing for I):
+ *   g_hat_k = (X[k.z mod M] + conj(X[-k.z mod M])) / (2M),
+ * kept when |g_hat_k| > tau * max_I |g_hat|.  Kept frequencies and values are
+ * written in candidate order to freq_out (device [n_cand][d]) and val_out
+ * (device FP64 complex [n_cand]); their number to *n_out.  More than s_max
+ * survivors is SS_ERR_INVALID.  samples: device, M reals in `prec`.
+ * Synchronises `stream`. */
+ss_status sft_recover_samples(const ss_lattice* lat, const void* samples, ss_precision prec,
+                              const int32_t* cand, int64_t n_cand, int64_t s_max, double tau,
+                              int32_t* freq_out, double* val_out, int64_t* n_out, void* stream);
+
+/* lattice_sample followed by sft_recover_samples (library-owned sample and
+ * FFT buffers).  Synchronises `stream`. */
+ss_status sft_recover(const ss_lattice* lat, const ss_trig* g, ss_precision prec, const int32_t* cand,
+                      int64_t n_cand, int64_t s_max, double tau, int32_t* freq_out, double* val_out,
+                      int64_t* n_out, void* stream);
+
+/* ------------------------------------------------------------------ stamp */
+
+/* S^N[a_hat](F) of eq. StampSet with F = f_freq (device [n_f][d], distinct,
+ * nonzero) and supp a_hat from a_hat (closed under negation, containing 0,
+ * Hermitian values).  Canonical order: level 0 is F in signed lexicographic
+ * order; level n lists new frequencies in order of first discovery over the
+ * parents of level n-1 (index order) and the nonzero p of supp a_hat in
+ * signed lexicographic order.  Also builds the neighbour table of the
+ * operator.  Rejects a_hat that fails the positivity check
+ * ||a_hat - a_hat_0||_1 < |a_hat_0| (Remark after Corollary
+ * SpectralConvergenceNoSFT) with SS_ERR_NOT_ELLIPTIC.  Synchronises `stream`
+ * once per level. */
+ss_status stamp_build(const ss_sparse* a_hat, const int32_t* f_freq, int64_t n_f, int32_t N,
+                      ss_stamp* out, void* stream);
+
+/* |S|, operator nonzeros #{(k,p): k in S\{0}, k-p in S\{0}}, the canonical
+ * index of k = 0 (-1 if absent), and the number of levels (N + 1).  Host. */
+ss_status stamp_info(ss_stamp s, int64_t* size, int64_t* nnz, int64_t* zero_index, int32_t* n_levels);
+
+/* Frequencies (device int32 [|S|][d]) and levels (device int8 [|S|]) in
+ * canonical order; either output may be NULL. */
+ss_status stamp_export(ss_stamp s, int32_t* freq_out, int8_t* level_out, void* stream);
+
+/* Canonical index of each query frequency (device [n][d]) into idx_out
+ * (device int64 [n]), -1 when absent. */
+ss_status stamp_lookup(ss_stamp s, const int32_t* freq, int64_t n, int64_t* idx_out, void* stream);
+
+/* Scatter a sparse list onto S: out (device FP64 complex [|S|]) is zeroed,
+ * then out[index(k)] = val for every entry whose k lies in S; *n_outside
+ * (host, may be NULL) receives the number of entries that do not (the call then
+ * synchronises `stream`). */
+ss_status stamp_scatter(ss_stamp s, const ss_sparse* g, double* out, int64_t* n_outside, void* stream);
+
+void stamp_destroy(ss_stamp s);
+
+/* -------------------------------------------------------------- operator */
+
+/* y = L_{N,s} u on S (eq. FiniteGalerkinOperator):
+ *   y_k = sum_{p in supp a_hat, k-p in S} 4 pi^2 (k.(k-p)) a_hat_p u_{k-p},
+ * the integer k.(k-p) formed exactly as (|k|^2 + |k-p|^2 - |p|^2)/2; the row of
+ * k = 0 is the identity (pins u_hat_0).  u, y: device complex [|S|], FP64 or
+ * FP32 per `prec` (FP32: FP32 values, FP32 accumulation).  Uses the stamp's
+ * scratch: concurrent calls on one stamp must be on one stream. */
+ss_status galerkin_apply(ss_stamp s, const void* u, void* y, ss_precision prec, void* stream);
+
+/* ----------------------------------------------------------------- solve */
+
+/* Solve L_{N,s} u = f on S (eq. SparseSpectralSFTEquation) by Jacobi-
+ * preconditioned CG (D_k = 4 pi^2 Re(a_hat_0) |k|^2, the denominator of the
+ * diagonal rearrangement in the proof of Proposition SolutionSupport):
+ *   SS_FP64  plain FP64 CG until ||f - L u||_2 <= tol ||f||_2;
+ *   SS_FP32  FP32-operator CG (FP64 vectors and scalars) inside FP64 iterative
+ *            refinement whose residual f - L u is formed with the FP64 operator.
+ * f_on_S, u_on_S: device FP64 complex [|S|].  One persistent cooperative
+ * launch.  Writes stats (host, may be NULL) and synchronises `stream`.
+ * f_hat_0 must be 0 (SS_ERR_INVALID otherwise). */
+ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, double tol, int32_t max_iter,
+                ss_precision prec, ss_solve_stats* stats, void* stream);
+
+/* Many instances in one persistent launch: the rows of all instances are
+ * concatenated, every CG phase runs over all of them with per-instance scalars,
+ * and converged instances drop out.  batch_create copies the instances'
+ * operators into one layout (the stamps may be destroyed afterwards);
+ * tile shapes come from the autotuner (batch_autotune) when it has run. */
+ss_status batch_create(int32_t n_inst, const ss_stamp* stamps, ss_batch* out, void* stream);
+
+/* f[i], u[i]: device FP64 complex [|S_i|].  use_graph != 0 captures the
+ * launch sequence in a CUDA graph on first use and replays it while the
+ * pointers are unchanged.  stats: host array [n_inst] (may be NULL).
+ * Synchronises `stream`. */
+ss_status batch_solve(ss_batch b, const double* const* f, double* const* u, double tol,
+                      int32_t max_iter, ss_precision prec, int32_t use_graph,
+                      ss_solve_stats* stats, void* stream);
+
+/* Times the persistent solve over candidate tile shapes (warps per block,
+ * blocks per SM) for this batch and keeps the fastest.  best_ms (host, may be
+ * NULL) receives its time.  Synchronises `stream`. */
+ss_status batch_autotune(ss_batch b, const double* const* f, double* const* u, double tol,
+                         int32_t max_iter, ss_precision prec, double* best_ms, void* stream);
+
+/* Current tile shape and work split of the batch (any output may be NULL). */
+ss_status batch_config(ss_batch b, int32_t* block, int32_t* blocks_per_sm, int32_t* chunks_per_block,
+                       int32_t* grid, int32_t* n_chunks);
+
+/* Set the tile shape: block in {128, 256, 512} threads, blocks_per_sm (0 = as
+ * many as fit), chunks_per_block >= 1 (static work units per block). */
+ss_status batch_set_config(ss_batch b, int32_t block, int32_t blocks_per_sm, int32_t chunks_per_block);
+
+void batch_destroy(ss_batch b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPARSE_SPECTRAL_H */

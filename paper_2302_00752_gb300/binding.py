@@ -1,0 +1,371 @@
+"""Python binding of the C ABI in include/sparse_spectral.h (ctypes).
+
+Argument marshalling only: tensors are passed as device pointers on the
+current torch CUDA stream, every computation runs in the library's kernels.
+The library must have been built (``paper_2302_00752_gb300.build``); importing
+this module without it raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsparse_spectral.so")
+
+SS_FP64, SS_FP32 = 0, 1
+STATUS = {0: "SS_OK", 1: "SS_ERR_INVALID", 2: "SS_ERR_OOM", 3: "SS_ERR_CUDA", 4: "SS_ERR_NOT_RECONSTRUCTING",
+          5: "SS_ERR_HASH_FULL", 6: "SS_ERR_NOT_ELLIPTIC", 7: "SS_ERR_NOT_CONVERGED", 8: "SS_ERR_TIMEOUT",
+          9: "SS_ERR_KEY_RANGE"}
+
+
+class SSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class Lattice(C.Structure):
+    _fields_ = [("d", C.c_int32), ("M", C.c_int64), ("z", C.POINTER(C.c_int64))]
+
+
+class Trig(C.Structure):
+    _fields_ = [("d", C.c_int32), ("n_terms", C.c_int64), ("freq", C.c_void_p), ("coef", C.c_void_p)]
+
+
+class Sparse(C.Structure):
+    _fields_ = [("d", C.c_int32), ("n", C.c_int64), ("freq", C.c_void_p), ("val", C.c_void_p)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("outer_iters", C.c_int32), ("inner_iters", C.c_int32),
+                ("applies", C.c_int32), ("rel_residual", C.c_double)]
+
+    def as_dict(self):
+        return {"status": STATUS.get(self.status, self.status), "outer_iters": self.outer_iters,
+                "inner_iters": self.inner_iters, "applies": self.applies, "rel_residual": self.rel_residual}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                           "(run python -m paper_2302_00752_gb300.build)")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    P = C.POINTER
+    sigs = {
+        "ss_last_error": (C.c_char_p, []),
+        "ss_version": (C.c_char_p, []),
+        "lattice_size": (i32, [i64, i64, dbl, i64, P(i64)]),
+        "lattice_check": (i32, [P(Lattice), vp, i64, vp]),
+        "lattice_random": (i32, [vp, i64, i32, dbl, i64, P(i64), i32, P(i64), P(i64), P(i32), vp]),
+        "lattice_cbc": (i32, [vp, i64, i32, i64, P(i64), i32, P(i64), P(i64), vp]),
+        "lattice_sample": (i32, [P(Lattice), P(Trig), i32, vp, vp]),
+        "sft_recover_samples": (i32, [P(Lattice), vp, i32, vp, i64, i64, dbl, vp, vp, P(i64), vp]),
+        "sft_recover": (i32, [P(Lattice), P(Trig), i32, vp, i64, i64, dbl, vp, vp, P(i64), vp]),
+        "stamp_build": (i32, [P(Sparse), vp, i64, i32, P(vp), vp]),
+        "stamp_info": (i32, [vp, P(i64), P(i64), P(i64), P(i32)]),
+        "stamp_export": (i32, [vp, vp, vp, vp]),
+        "stamp_lookup": (i32, [vp, vp, i64, vp, vp]),
+        "stamp_scatter": (i32, [vp, P(Sparse), vp, P(i64), vp]),
+        "stamp_destroy": (None, [vp]),
+        "galerkin_apply": (i32, [vp, vp, vp, i32, vp]),
+        "solve": (i32, [vp, vp, vp, dbl, i32, i32, P(SolveStats), vp]),
+        "batch_create": (i32, [i32, P(vp), P(vp), vp]),
+        "batch_solve": (i32, [vp, P(vp), P(vp), dbl, i32, i32, i32, P(SolveStats), vp]),
+        "batch_autotune": (i32, [vp, P(vp), P(vp), dbl, i32, i32, P(dbl), vp]),
+        "batch_config": (i32, [vp, P(i32), P(i32), P(i32), P(i32), P(i32)]),
+        "batch_set_config": (i32, [vp, i32, i32, i32]),
+        "batch_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(status):
+    if status != 0:
+        raise SSError(status, lib.ss_last_error().decode(errors="replace"))
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else C.c_void_p(0)
+
+
+def _dev_i32(x, d=None):
+    t = torch.as_tensor(np.asarray(x) if not torch.is_tensor(x) else x)
+    t = t.to(device="cuda", dtype=torch.int32).contiguous()
+    if d is not None:
+        t = t.reshape(-1, d)
+    return t
+
+
+def _dev_c128(x):
+    t = x if torch.is_tensor(x) else torch.as_tensor(np.asarray(x, dtype=np.complex128))
+    return t.to(device="cuda", dtype=torch.complex128).contiguous()
+
+
+def _lattice(z, M):
+    z = np.ascontiguousarray(np.asarray(z, dtype=np.int64))
+    arr = (C.c_int64 * len(z))(*z.tolist())
+    lat = Lattice(len(z), int(M), arr)
+    lat._keep = arr
+    return lat
+
+
+def _prec(p):
+    if p in (SS_FP64, "fp64", "float64"):
+        return SS_FP64
+    if p in (SS_FP32, "fp32", "float32", "fp32_refined"):
+        return SS_FP32
+    raise ValueError(f"unknown precision {p!r}")
+
+
+def version():
+    return lib.ss_version().decode()
+
+
+# ------------------------------------------------------------------ lattice
+
+def lattice_size(K, n_I, sigma=0.05, M_min=0):
+    M = C.c_int64()
+    _check(lib.lattice_size(int(K), int(n_I), float(sigma), int(M_min), C.byref(M)))
+    return M.value
+
+
+def lattice_check(z, M, freq):
+    f = _dev_i32(freq, len(z))
+    lat = _lattice(z, M)
+    _check(lib.lattice_check(C.byref(lat), _ptr(f), f.shape[0], _stream()))
+
+
+def lattice_random(freq, raw, sigma=0.05, M_min=0):
+    raw = np.ascontiguousarray(np.asarray(raw, dtype=np.int64))
+    attempts, d = raw.shape
+    f = _dev_i32(freq, d)
+    z = (C.c_int64 * d)()
+    M = C.c_int64()
+    att = C.c_int32()
+    _check(lib.lattice_random(_ptr(f), f.shape[0], d, float(sigma), int(M_min),
+                              raw.ctypes.data_as(C.POINTER(C.c_int64)), attempts, z, C.byref(M), C.byref(att),
+                              _stream()))
+    return np.array(z[:], dtype=np.int64), M.value, att.value
+
+
+def lattice_cbc(freq, raw, M_min):
+    raw = np.ascontiguousarray(np.asarray(raw, dtype=np.int64))
+    d, n_cand = raw.shape
+    f = _dev_i32(freq, d)
+    z = (C.c_int64 * d)()
+    M = C.c_int64()
+    _check(lib.lattice_cbc(_ptr(f), f.shape[0], d, int(M_min), raw.ctypes.data_as(C.POINTER(C.c_int64)), n_cand,
+                           z, C.byref(M), _stream()))
+    return np.array(z[:], dtype=np.int64), M.value
+
+
+# ---------------------------------------------------------------------- SFT
+
+def _trig(freq, coef, d):
+    f = _dev_i32(freq, d)
+    c = _dev_c128(coef)
+    t = Trig(d, f.shape[0], _ptr(f), _ptr(c))
+    t._keep = (f, c)
+    return t
+
+
+def lattice_sample(z, M, freq, coef, precision="fp64"):
+    p = _prec(precision)
+    lat = _lattice(z, M)
+    g = _trig(freq, coef, len(z))
+    out = torch.empty(int(M), dtype=torch.float64 if p == SS_FP64 else torch.float32, device="cuda")
+    _check(lib.lattice_sample(C.byref(lat), C.byref(g), p, _ptr(out), _stream()))
+    return out
+
+
+def _recover_out(cand, d):
+    fo = torch.empty((cand.shape[0], d), dtype=torch.int32, device="cuda")
+    vo = torch.empty(cand.shape[0], dtype=torch.complex128, device="cuda")
+    return fo, vo
+
+
+def sft_recover_samples(z, M, samples, cand, s_max=0, tau=1e-9, precision="fp64"):
+    p = _prec(precision)
+    lat = _lattice(z, M)
+    cd = _dev_i32(cand, len(z))
+    fo, vo = _recover_out(cd, len(z))
+    n = C.c_int64()
+    _check(lib.sft_recover_samples(C.byref(lat), _ptr(samples), p, _ptr(cd), cd.shape[0], int(s_max), float(tau),
+                                   _ptr(fo), _ptr(vo), C.byref(n), _stream()))
+    return fo[: n.value], vo[: n.value]
+
+
+def sft_recover(z, M, freq, coef, cand, s_max=0, tau=1e-9, precision="fp64"):
+    p = _prec(precision)
+    lat = _lattice(z, M)
+    g = _trig(freq, coef, len(z))
+    cd = _dev_i32(cand, len(z))
+    fo, vo = _recover_out(cd, len(z))
+    n = C.c_int64()
+    _check(lib.sft_recover(C.byref(lat), C.byref(g), p, _ptr(cd), cd.shape[0], int(s_max), float(tau), _ptr(fo),
+                           _ptr(vo), C.byref(n), _stream()))
+    return fo[: n.value], vo[: n.value]
+
+
+# -------------------------------------------------------------------- stamp
+
+class Stamp:
+    """S^N[a_hat](F) on the device (owns the library handle)."""
+
+    def __init__(self, handle, d):
+        self._h = C.c_void_p(handle)
+        self.d = d
+        size, nnz, zero = C.c_int64(), C.c_int64(), C.c_int64()
+        lv = C.c_int32()
+        _check(lib.stamp_info(self._h, C.byref(size), C.byref(nnz), C.byref(zero), C.byref(lv)))
+        self.size, self.nnz, self.zero_index, self.n_levels = size.value, nnz.value, zero.value, lv.value
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("stamp destroyed")
+        return self._h
+
+    def export(self):
+        freq = torch.empty((self.size, self.d), dtype=torch.int32, device="cuda")
+        level = torch.empty(self.size, dtype=torch.int8, device="cuda")
+        _check(lib.stamp_export(self.handle, _ptr(freq), _ptr(level), _stream()))
+        return freq, level
+
+    def lookup(self, freq):
+        f = _dev_i32(freq, self.d)
+        idx = torch.empty(f.shape[0], dtype=torch.int64, device="cuda")
+        _check(lib.stamp_lookup(self.handle, _ptr(f), f.shape[0], _ptr(idx), _stream()))
+        return idx
+
+    def scatter(self, freq, val):
+        f = _dev_i32(freq, self.d)
+        v = _dev_c128(val)
+        sp = Sparse(self.d, f.shape[0], _ptr(f), _ptr(v))
+        out = torch.empty(self.size, dtype=torch.complex128, device="cuda")
+        outside = C.c_int64()
+        _check(lib.stamp_scatter(self.handle, C.byref(sp), _ptr(out), C.byref(outside), _stream()))
+        return out, outside.value
+
+    def destroy(self):
+        if self._h:
+            lib.stamp_destroy(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.destroy()
+
+
+def stamp_build(a_freq, a_val, f_freq, N):
+    af = torch.as_tensor(a_freq) if torch.is_tensor(a_freq) else torch.as_tensor(np.asarray(a_freq))
+    d = int(af.shape[1])
+    af = _dev_i32(af, d)
+    av = _dev_c128(a_val)
+    ff = _dev_i32(f_freq, d)
+    sp = Sparse(d, af.shape[0], _ptr(af), _ptr(av))
+    h = C.c_void_p()
+    _check(lib.stamp_build(C.byref(sp), _ptr(ff), ff.shape[0], int(N), C.byref(h), _stream()))
+    return Stamp(h.value, d)
+
+
+def galerkin_apply(stamp, u, precision=None):
+    if precision is None:
+        precision = "fp32" if u.dtype == torch.complex64 else "fp64"
+    p = _prec(precision)
+    dt = torch.complex128 if p == SS_FP64 else torch.complex64
+    u = u.to(device="cuda", dtype=dt).contiguous()
+    y = torch.empty_like(u)
+    _check(lib.galerkin_apply(stamp.handle, _ptr(u), _ptr(y), p, _stream()))
+    return y
+
+
+def solve(stamp, f_on_S, tol=1e-12, max_iter=1000, precision="fp64", out=None, raise_on_error=True):
+    f = _dev_c128(f_on_S)
+    u = torch.empty_like(f) if out is None else out
+    st = SolveStats()
+    status = lib.solve(stamp.handle, _ptr(f), _ptr(u), float(tol), int(max_iter), _prec(precision), C.byref(st),
+                       _stream())
+    if raise_on_error:
+        _check(status)
+    return u, st.as_dict()
+
+
+# -------------------------------------------------------------------- batch
+
+class Batch:
+    """Many stamps solved by one persistent launch."""
+
+    def __init__(self, stamps):
+        self.stamps = list(stamps)
+        arr = (C.c_void_p * len(self.stamps))(*[s.handle.value for s in self.stamps])
+        h = C.c_void_p()
+        _check(lib.batch_create(len(self.stamps), arr, C.byref(h), _stream()))
+        self._h = h
+
+    def _ptr_arrays(self, fs, us):
+        fa = (C.c_void_p * len(fs))(*[f.data_ptr() for f in fs])
+        ua = (C.c_void_p * len(us))(*[u.data_ptr() for u in us])
+        return fa, ua
+
+    def solve(self, fs, us=None, tol=1e-12, max_iter=1000, precision="fp32", use_graph=True):
+        fs = [_dev_c128(f) for f in fs]
+        us = [torch.empty_like(f) for f in fs] if us is None else us
+        fa, ua = self._ptr_arrays(fs, us)
+        st = (SolveStats * len(fs))()
+        _check(lib.batch_solve(self._h, fa, ua, float(tol), int(max_iter), _prec(precision), int(bool(use_graph)),
+                               st, _stream()))
+        return us, [s.as_dict() for s in st]
+
+    def autotune(self, fs, us=None, tol=1e-12, max_iter=1000, precision="fp32"):
+        fs = [_dev_c128(f) for f in fs]
+        us = [torch.empty_like(f) for f in fs] if us is None else us
+        fa, ua = self._ptr_arrays(fs, us)
+        best = C.c_double()
+        _check(lib.batch_autotune(self._h, fa, ua, float(tol), int(max_iter), _prec(precision), C.byref(best),
+                                  _stream()))
+        return best.value, self.config()
+
+    def config(self):
+        v = [C.c_int32() for _ in range(5)]
+        _check(lib.batch_config(self._h, *[C.byref(x) for x in v]))
+        return dict(zip(["block", "blocks_per_sm", "chunks_per_block", "grid", "n_chunks"], [x.value for x in v]))
+
+    def set_config(self, block, blocks_per_sm, chunks_per_block):
+        _check(lib.batch_set_config(self._h, int(block), int(blocks_per_sm), int(chunks_per_block)))
+
+    def destroy(self):
+        if self._h:
+            lib.batch_destroy(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -1,0 +1,127 @@
+// galerkin_apply: y = L_{N,s} u on the stamping set (eq. FiniteGalerkinOperator).
+// One thread per row, one warp per 32-row slice of the sliced-ELL table: the
+// index stream is read coalesced (column-major inside a slice) and the values
+// of u are gathered from a record array that carries |l|^2 beside u_l.
+#include "apply.cuh"
+
+namespace ss {
+namespace {
+
+__global__ void k_pack64(const double2* __restrict__ u, int64_t size, double2* rec) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < size) rec[2 * i] = u[i];
+}
+
+__global__ void k_pack32(const float2* __restrict__ u, int64_t size, float4* rec) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < size) {
+    const float2 v = u[i];
+    reinterpret_cast<float2*>(rec + i)[0] = v;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_coef(T* s_ca, int32_t* s_pn, const T* ca, const int32_t* pn, int s_a) {
+  for (int j = threadIdx.x; j < s_a; j += blockDim.x) {
+    s_ca[j] = ca[j];
+    s_pn[j] = pn[j];
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_apply64(OpView op, int64_t size, int64_t rows_pad, const int32_t* __restrict__ norm,
+                                                 const double2* __restrict__ rec, const double2* __restrict__ ca,
+                                                 const int32_t* __restrict__ pn, int s_a, int64_t zero_idx,
+                                                 double2* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double2* s_ca = reinterpret_cast<double2*>(smem);
+  int32_t* s_pn = reinterpret_cast<int32_t*>(s_ca + s_a);
+  load_coef(s_ca, s_pn, ca, pn, s_a);
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= rows_pad) return;
+  const int64_t s = row / kSlice;
+  const int lane = (int)(row % kSlice);
+  double2 acc = row_apply64(op, s, lane, __ldg(norm + row), rec, s_ca, s_pn);
+  if (row == zero_idx) acc = rec[2 * row];
+  if (row < size) y[row] = acc;
+}
+
+__global__ void __launch_bounds__(256) k_apply32(OpView op, int64_t size, int64_t rows_pad, const int32_t* __restrict__ norm,
+                                                 const float4* __restrict__ rec, const float2* __restrict__ ca,
+                                                 const int32_t* __restrict__ pn, int s_a, int64_t zero_idx,
+                                                 float2* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* s_ca = reinterpret_cast<float2*>(smem);
+  int32_t* s_pn = reinterpret_cast<int32_t*>(s_ca + s_a);
+  load_coef(s_ca, s_pn, ca, pn, s_a);
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= rows_pad) return;
+  const int64_t s = row / kSlice;
+  const int lane = (int)(row % kSlice);
+  float2 acc = row_apply32(op, s, lane, __ldg(norm + row), rec, s_ca, s_pn);
+  if (row == zero_idx) {
+    const float4 r = rec[row];
+    acc = make_float2(r.x, r.y);
+  }
+  if (row < size) y[row] = acc;
+}
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+OpView op_view(const ss_stamp_s* s) {
+  OpView op;
+  op.woff = s->slice_off.get();
+  op.ent = s->ent.get();
+  op.colbits = colbits_of(s->jbits);
+  op.colmask = colmask_of(s->jbits);
+  return op;
+}
+
+ss_status launch_pack64(const ss_stamp_s* s, const double2* u, cudaStream_t st) {
+  k_pack64<<<nblk(s->size), 256, 0, st>>>(u, s->size, s->rec64.get());
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
+ss_status launch_pack32(const ss_stamp_s* s, const float2* u, cudaStream_t st) {
+  k_pack32<<<nblk(s->size), 256, 0, st>>>(u, s->size, s->rec32.get());
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
+ss_status launch_apply64(const ss_stamp_s* s, double2* y, cudaStream_t st) {
+  const size_t sm = s->s_a * (sizeof(double2) + sizeof(int32_t)) + 16;
+  k_apply64<<<nblk(s->rows_pad), 256, sm, st>>>(op_view(s), s->size, s->rows_pad, s->norm.get(), s->rec64.get(),
+                                                s->ca64.get(), s->pnorm.get(), s->s_a, s->zero_idx, y);
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
+ss_status launch_apply32(const ss_stamp_s* s, float2* y, cudaStream_t st) {
+  const size_t sm = s->s_a * (sizeof(float2) + sizeof(int32_t)) + 16;
+  k_apply32<<<nblk(s->rows_pad), 256, sm, st>>>(op_view(s), s->size, s->rows_pad, s->norm.get(), s->rec32.get(),
+                                                s->ca32.get(), s->pnorm.get(), s->s_a, s->zero_idx, y);
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
+}  // namespace ss
+
+using namespace ss;
+
+extern "C" ss_status galerkin_apply(ss_stamp s, const void* u, void* y, ss_precision prec, void* stream) {
+  if (!s || !u || !y) SS_FAIL(SS_ERR_INVALID, "galerkin_apply: null argument");
+  cudaStream_t st = as_stream(stream);
+  if (s->size == 0) return SS_OK;
+  if (prec == SS_FP64) {
+    SS_TRY(launch_pack64(s, reinterpret_cast<const double2*>(u), st));
+    return launch_apply64(s, reinterpret_cast<double2*>(y), st);
+  }
+  if (prec == SS_FP32) {
+    SS_TRY(launch_pack32(s, reinterpret_cast<const float2*>(u), st));
+    return launch_apply32(s, reinterpret_cast<float2*>(y), st);
+  }
+  SS_FAIL(SS_ERR_INVALID, "galerkin_apply: unknown precision %d", (int)prec);
+}

@@ -1,0 +1,321 @@
+// Rank-1 lattices: residues k.z mod M, the reconstructing check, the random
+// lattice of Lemma RandomRank1Lattice and a component-by-component search.
+#include <algorithm>
+#include <cmath>
+
+#include "lattice.cuh"
+
+namespace ss {
+
+// -------------------------------------------------------------- host math
+
+static bool is_prime_host(int64_t n) {
+  if (n < 2) return false;
+  if (n % 2 == 0) return n == 2;
+  for (int64_t i = 3; i * i <= n; i += 2)
+    if (n % i == 0) return false;
+  return true;
+}
+
+int64_t next_prime_host(int64_t n) {
+  if (n < 2) n = 2;
+  while (!is_prime_host(n)) ++n;
+  return n;
+}
+
+// ---------------------------------------------------------------- kernels
+
+__global__ void k_residues(const int32_t* __restrict__ f, int64_t n, int d, LatticeDev L, int64_t* res) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  res[i] = residue_of(f + i * d, d, L);
+}
+
+namespace {
+
+__device__ bool rows_equal(const int32_t* a, const int32_t* b, int d) {
+  for (int c = 0; c < d; ++c)
+    if (a[c] != b[c]) return false;
+  return true;
+}
+
+__device__ bool rows_negated(const int32_t* a, const int32_t* b, int d) {
+  for (int c = 0; c < d; ++c)
+    if (a[c] != -b[c]) return false;
+  return true;
+}
+
+__device__ __forceinline__ uint64_t rhash(uint64_t r) {
+  r ^= r >> 33;
+  r *= 0xff51afd7ed558ccdull;
+  r ^= r >> 33;
+  return r;
+}
+
+// Residue table: slot = index + 1 of the row owning a residue (0 = empty).
+__global__ void k_check_insert(const int32_t* __restrict__ f, const int64_t* __restrict__ res, int64_t n, int d,
+                               unsigned long long* table, uint64_t capmask, int32_t* flags) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t r = (uint64_t)res[i];
+  uint64_t h = rhash(r) & capmask;
+  for (uint64_t probe = 0; probe <= capmask; ++probe) {
+    const unsigned long long old = atomicCAS(table + h, 0ull, (unsigned long long)(i + 1));
+    if (old == 0ull) return;
+    const int64_t o = (int64_t)old - 1;
+    if ((uint64_t)res[o] == r) {
+      if (rows_equal(f + o * d, f + i * d, d)) atomicOr(flags + 0, 1);   // duplicate row
+      else atomicOr(flags + 1, 1);                                       // collision
+      return;
+    }
+    h = (h + 1) & capmask;
+  }
+  atomicOr(flags + 2, 1);
+}
+
+// For every row k, is -k present?  (residue of -k is (M - r) mod M)
+__global__ void k_check_symmetric(const int32_t* __restrict__ f, const int64_t* __restrict__ res, int64_t n, int d,
+                                  int64_t M, const unsigned long long* __restrict__ table, uint64_t capmask,
+                                  int32_t* flags) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t r = (uint64_t)((M - res[i]) % M);
+  uint64_t h = rhash(r) & capmask;
+  for (uint64_t probe = 0; probe <= capmask; ++probe) {
+    const unsigned long long v = table[h];
+    if (v == 0ull) break;
+    const int64_t o = (int64_t)v - 1;
+    if ((uint64_t)res[o] == r) {
+      if (rows_negated(f + o * d, f + i * d, d)) return;
+      break;
+    }
+    h = (h + 1) & capmask;
+  }
+  atomicOr(flags + 3, 1);
+}
+
+__global__ void k_minmax(const int32_t* __restrict__ f, int64_t n, int d, int32_t* mn, int32_t* mx) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * d) return;
+  const int c = (int)(t % d);
+  atomicMin(mn + c, f[t]);
+  atomicMax(mx + c, f[t]);
+}
+
+// CBC: partial residues of coordinates [0, j) are in rho; block b tries
+// candidate cand[b] for coordinate j: rho'_i = rho_i + k_ij cand (mod M), and
+// fails if two rows with distinct projections onto [0, j] share rho'.
+__global__ void k_cbc_try(const int32_t* __restrict__ f, int64_t n, int d, int j, int64_t M,
+                          const int64_t* __restrict__ rho, const int64_t* __restrict__ cand, int64_t* scratch,
+                          int32_t* fail) {
+  const int b = blockIdx.x;
+  const uint64_t z = (uint64_t)cand[b];
+  int64_t* rp = scratch + (int64_t)b * n;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    int64_t k = f[i * d + j] % M;
+    if (k < 0) k += M;
+    rp[i] = (int64_t)(((uint64_t)rho[i] + ((uint64_t)k * z) % (uint64_t)M) % (uint64_t)M);
+  }
+  __syncthreads();
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n && !bad; i += blockDim.x) {
+    const int64_t ri = rp[i];
+    for (int64_t q = i + 1; q < n; ++q) {
+      if (rp[q] != ri) continue;
+      bool same = true;
+      for (int c = 0; c <= j; ++c) same &= (f[i * d + c] == f[q * d + c]);
+      if (!same) { bad = 1; break; }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) fail[b] = bad;
+}
+
+__global__ void k_cbc_accept(const int32_t* __restrict__ f, int64_t n, int d, int j, int64_t M, int64_t z,
+                             int64_t* rho) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t k = f[i * d + j] % M;
+  if (k < 0) k += M;
+  rho[i] = (int64_t)(((uint64_t)rho[i] + ((uint64_t)k * (uint64_t)z) % (uint64_t)M) % (uint64_t)M);
+}
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+ss_status make_lattice_dev(const ss_lattice* lat, LatticeDev* L) {
+  if (!lat || !lat->z) SS_FAIL(SS_ERR_INVALID, "lattice: null argument");
+  if (lat->d < 1 || lat->d > kMaxLatticeDim) SS_FAIL(SS_ERR_INVALID, "lattice: d = %d outside 1..%d", lat->d, kMaxLatticeDim);
+  if (lat->M < 2 || lat->M >= (1ll << 31)) SS_FAIL(SS_ERR_INVALID, "lattice: M = %lld outside [2, 2^31)", (long long)lat->M);
+  L->d = lat->d;
+  L->M = lat->M;
+  for (int c = 0; c < lat->d; ++c) {
+    if (lat->z[c] < 1 || lat->z[c] >= lat->M) SS_FAIL(SS_ERR_INVALID, "lattice: z[%d] = %lld outside [1, M)", c, (long long)lat->z[c]);
+    L->z[c] = lat->z[c];
+  }
+  return SS_OK;
+}
+
+ss_status residues(const int32_t* freq, int64_t n, const LatticeDev& L, int64_t* res, cudaStream_t st) {
+  if (n == 0) return SS_OK;
+  k_residues<<<nblk(n), 256, 0, st>>>(freq, n, L.d, L, res);
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
+ss_status check_reconstructing(const int32_t* freq, int64_t n, const LatticeDev& L, const int64_t* res,
+                               bool need_symmetric, cudaStream_t st) {
+  if (n == 0) return SS_OK;
+  uint64_t cap = 1;
+  while (cap < (uint64_t)(2 * n)) cap <<= 1;
+  DevBuf<unsigned long long> table;
+  DevBuf<int32_t> flags;
+  SS_TRY(table.alloc(cap));
+  SS_TRY(flags.alloc(4));
+  SS_CUDA(cudaMemsetAsync(table.get(), 0, cap * sizeof(unsigned long long), st));
+  SS_CUDA(cudaMemsetAsync(flags.get(), 0, 4 * sizeof(int32_t), st));
+  k_check_insert<<<nblk(n), 256, 0, st>>>(freq, res, n, L.d, table.get(), cap - 1, flags.get());
+  if (need_symmetric) k_check_symmetric<<<nblk(n), 256, 0, st>>>(freq, res, n, L.d, L.M, table.get(), cap - 1, flags.get());
+  SS_LAUNCH_CHECK();
+  int32_t h[4];
+  SS_CUDA(cudaMemcpyAsync(h, flags.get(), sizeof(h), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  if (h[0]) SS_FAIL(SS_ERR_INVALID, "lattice: duplicate frequencies in the candidate set");
+  if (h[2]) SS_FAIL(SS_ERR_HASH_FULL, "lattice: residue table exhausted");
+  if (h[1]) SS_FAIL(SS_ERR_NOT_RECONSTRUCTING, "lattice (M = %lld) is not reconstructing for the candidate set",
+                    (long long)L.M);
+  if (h[3]) SS_FAIL(SS_ERR_INVALID, "candidate set is not closed under negation");
+  return SS_OK;
+}
+
+static ss_status expansion_of(const int32_t* freq, int64_t n, int d, int64_t* K, cudaStream_t st) {
+  DevBuf<int32_t> mm;
+  SS_TRY(mm.alloc(2 * d));
+  std::vector<int32_t> init(2 * d);
+  for (int c = 0; c < d; ++c) { init[c] = INT32_MAX; init[d + c] = INT32_MIN; }
+  SS_CUDA(cudaMemcpyAsync(mm.get(), init.data(), 2 * d * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  if (n > 0) k_minmax<<<nblk(n * d), 256, 0, st>>>(freq, n, d, mm.get(), mm.get() + d);
+  SS_LAUNCH_CHECK();
+  SS_CUDA(cudaMemcpyAsync(init.data(), mm.get(), 2 * d * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  int64_t k = 0;
+  for (int c = 0; c < d && n > 0; ++c) k = std::max<int64_t>(k, (int64_t)init[d + c] - init[c]);
+  *K = k;
+  return SS_OK;
+}
+
+}  // namespace ss
+
+using namespace ss;
+
+extern "C" ss_status lattice_size(int64_t K, int64_t n_I, double sigma, int64_t M_min, int64_t* M_out) {
+  if (!M_out || !(sigma > 0.0) || sigma > 1.0 || K < 0 || n_I < 0)
+    SS_FAIL(SS_ERR_INVALID, "lattice_size: need K >= 0, n_I >= 0, 0 < sigma <= 1");
+  const double bound = std::max((double)K, (double)n_I * (double)n_I / sigma);
+  if (bound >= 2147483000.0 || M_min >= 2147483000ll) SS_FAIL(SS_ERR_INVALID, "lattice_size: M would exceed 2^31");
+  const int64_t lo = (int64_t)std::floor(bound) + 1;
+  *M_out = next_prime_host(std::max<int64_t>(lo, M_min));
+  return SS_OK;
+}
+
+extern "C" ss_status lattice_check(const ss_lattice* lat, const int32_t* freq, int64_t n, void* stream) {
+  LatticeDev L;
+  SS_TRY(make_lattice_dev(lat, &L));
+  if (n > 0 && !freq) SS_FAIL(SS_ERR_INVALID, "lattice_check: null frequencies");
+  cudaStream_t st = as_stream(stream);
+  DevBuf<int64_t> res;
+  SS_TRY(res.alloc(n));
+  SS_TRY(residues(freq, n, L, res.get(), st));
+  return check_reconstructing(freq, n, L, res.get(), false, st);
+}
+
+extern "C" ss_status lattice_random(const int32_t* freq, int64_t n, int32_t d, double sigma, int64_t M_min,
+                                    const int64_t* raw, int32_t attempts, int64_t* z_out, int64_t* M_out,
+                                    int32_t* attempt_out, void* stream) {
+  if (!freq || !raw || !z_out || !M_out || d < 1 || d > kMaxLatticeDim || attempts < 1)
+    SS_FAIL(SS_ERR_INVALID, "lattice_random: bad argument");
+  cudaStream_t st = as_stream(stream);
+  int64_t K = 0, M = 0;
+  SS_TRY(expansion_of(freq, n, d, &K, st));
+  SS_TRY(lattice_size(K, n, sigma, M_min, &M));
+  DevBuf<int64_t> res;
+  SS_TRY(res.alloc(n));
+  std::vector<int64_t> z(d);
+  for (int a = 0; a < attempts; ++a) {
+    for (int c = 0; c < d; ++c) {
+      const int64_t r = raw[(int64_t)a * d + c];
+      if (r < 0) SS_FAIL(SS_ERR_INVALID, "lattice_random: raw draws must be non-negative");
+      z[c] = 1 + r % (M - 1);
+    }
+    ss_lattice lat{d, M, z.data()};
+    LatticeDev L;
+    SS_TRY(make_lattice_dev(&lat, &L));
+    SS_TRY(residues(freq, n, L, res.get(), st));
+    ss_status s = check_reconstructing(freq, n, L, res.get(), false, st);
+    if (s == SS_OK) {
+      for (int c = 0; c < d; ++c) z_out[c] = z[c];
+      *M_out = M;
+      if (attempt_out) *attempt_out = a;
+      return SS_OK;
+    }
+    if (s != SS_ERR_NOT_RECONSTRUCTING) return s;
+  }
+  SS_FAIL(SS_ERR_NOT_RECONSTRUCTING, "lattice_random: no reconstructing draw among %d attempts (M = %lld)", attempts,
+          (long long)M);
+}
+
+extern "C" ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int64_t M_min, const int64_t* raw,
+                                 int32_t n_cand, int64_t* z_out, int64_t* M_out, void* stream) {
+  if (!freq || !raw || !z_out || !M_out || d < 1 || d > kMaxLatticeDim || n_cand < 1 || n < 1)
+    SS_FAIL(SS_ERR_INVALID, "lattice_cbc: bad argument");
+  cudaStream_t st = as_stream(stream);
+  int64_t K = 0;
+  SS_TRY(expansion_of(freq, n, d, &K, st));
+  if (std::max<int64_t>(M_min, K + 1) >= 2147483000ll) SS_FAIL(SS_ERR_INVALID, "lattice_cbc: M would exceed 2^31");
+  const int64_t M = next_prime_host(std::max<int64_t>(M_min, K + 1));
+  // the candidate set must be free of duplicates (checked on the full vectors)
+  {
+    std::vector<int64_t> one(d, 1);
+    ss_lattice lat{d, M, one.data()};
+    LatticeDev L;
+    SS_TRY(make_lattice_dev(&lat, &L));
+  }
+  DevBuf<int64_t> rho, cand, scratch;
+  DevBuf<int32_t> fail;
+  SS_TRY(rho.alloc(n));
+  SS_TRY(cand.alloc(n_cand));
+  SS_TRY(scratch.alloc((size_t)n_cand * n));
+  SS_TRY(fail.alloc(n_cand));
+  SS_CUDA(cudaMemsetAsync(rho.get(), 0, n * sizeof(int64_t), st));
+  std::vector<int64_t> z(d, 1), hc(n_cand);
+  std::vector<int32_t> hf(n_cand);
+  // coordinate 0: z_1 = 1 (distinct first coordinates have distinct residues since M > K)
+  k_cbc_accept<<<nblk(n), 256, 0, st>>>(freq, n, d, 0, M, 1, rho.get());
+  SS_LAUNCH_CHECK();
+  for (int j = 1; j < d; ++j) {
+    for (int c = 0; c < n_cand; ++c) {
+      const int64_t r = raw[(int64_t)j * n_cand + c];
+      if (r < 0) SS_FAIL(SS_ERR_INVALID, "lattice_cbc: raw draws must be non-negative");
+      hc[c] = 1 + r % (M - 1);
+    }
+    SS_CUDA(cudaMemcpyAsync(cand.get(), hc.data(), n_cand * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    k_cbc_try<<<n_cand, 256, 0, st>>>(freq, n, d, j, M, rho.get(), cand.get(), scratch.get(), fail.get());
+    SS_LAUNCH_CHECK();
+    SS_CUDA(cudaMemcpyAsync(hf.data(), fail.get(), n_cand * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SS_CUDA(cudaStreamSynchronize(st));
+    int pick = -1;
+    for (int c = 0; c < n_cand; ++c)
+      if (!hf[c]) { pick = c; break; }
+    if (pick < 0) SS_FAIL(SS_ERR_NOT_RECONSTRUCTING, "lattice_cbc: no candidate for coordinate %d", j + 1);
+    z[j] = hc[pick];
+    k_cbc_accept<<<nblk(n), 256, 0, st>>>(freq, n, d, j, M, z[j], rho.get());
+    SS_LAUNCH_CHECK();
+  }
+  SS_CUDA(cudaStreamSynchronize(st));
+  for (int c = 0; c < d; ++c) z_out[c] = z[c];
+  *M_out = M;
+  return SS_OK;
+}

@@ -1,0 +1,34 @@
+// Rank-1 lattice parameters on the device and exact residues k.z mod M.
+#pragma once
+
+#include "ss_internal.cuh"
+
+namespace ss {
+
+constexpr int kMaxLatticeDim = 1024;
+
+struct LatticeDev {
+  int d;
+  int64_t M;
+  int64_t z[kMaxLatticeDim];
+};
+
+// (k.z) mod M in [0, M), exact: every product (k_c mod M) z_c < 2^62.
+__device__ __forceinline__ int64_t residue_of(const int32_t* k, int d, const LatticeDev& L) {
+  const uint64_t M = (uint64_t)L.M;
+  uint64_t r = 0;
+  for (int c = 0; c < d; ++c) {
+    int64_t kc = (int64_t)k[c] % L.M;
+    if (kc < 0) kc += L.M;
+    r = (r + ((uint64_t)kc * (uint64_t)L.z[c]) % M) % M;
+  }
+  return (int64_t)r;
+}
+
+ss_status make_lattice_dev(const ss_lattice* lat, LatticeDev* L);
+ss_status residues(const int32_t* freq, int64_t n, const LatticeDev& L, int64_t* res, cudaStream_t st);
+ss_status check_reconstructing(const int32_t* freq, int64_t n, const LatticeDev& L, const int64_t* res,
+                               bool need_symmetric, cudaStream_t st);
+int64_t next_prime_host(int64_t n);
+
+}  // namespace ss

@@ -1,0 +1,374 @@
+// Coefficient recovery by rank-1 lattice sampling and one length-M FFT
+// (Section "Previous results on SFTs": samples of t -> g(t z) on j/M carry the
+// coefficient of k in DFT bin k.z mod M when the lattice is reconstructing).
+//
+// lattice_sample evaluates g(x_j) = sum_t Re(c_t exp(2 pi i (j q_t mod M)/M)),
+// q_t = p_t.z mod M, with the integer phase kept exact: each thread owns the
+// samples j0 + 256 m (m < kSampPerThread), starts from (j0 q_t) mod M and steps
+// by (256 q_t) mod M.  exp(2 pi i r/M) is the product of two table entries,
+// exp(2 pi i (r >> bl) 2^bl / M) exp(2 pi i (r & (2^bl - 1)) / M), tabulated
+// with sincospi and staged in shared memory when they fit.  The samples are
+// real, so the FFT is real-to-complex (bins b > M/2 are conj(X[M-b])).
+#include <cufft.h>
+
+#include <list>
+#include <memory>
+#include <mutex>
+
+#include "lattice.cuh"
+
+namespace ss {
+namespace {
+
+constexpr int kSampThreads = 256;
+constexpr int kSampPerThread = 8;
+constexpr int kTermChunk = 256;
+
+template <typename R> struct C2;
+template <> struct C2<double> { using T = double2; };
+template <> struct C2<float> { using T = float2; };
+
+template <typename R>
+__global__ void k_twiddles(int64_t M, int bl, int64_t H, typename C2<R>::T* lo, typename C2<R>::T* hi) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t L = 1ll << bl;
+  if (i < L) {
+    double s, c;
+    sincospi(2.0 * (double)i / (double)M, &s, &c);
+    lo[i].x = (R)c;
+    lo[i].y = (R)s;
+  }
+  if (i < H) {
+    const int64_t r = (i << bl) % M;
+    double s, c;
+    sincospi(2.0 * (double)r / (double)M, &s, &c);
+    hi[i].x = (R)c;
+    hi[i].y = (R)s;
+  }
+}
+
+__global__ void k_term_residues(const int32_t* __restrict__ freq, int64_t n, LatticeDev L, int64_t* q,
+                                int64_t* step) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int64_t r = residue_of(freq + t * L.d, L.d, L);
+  q[t] = r;
+  step[t] = (int64_t)(((uint64_t)r * (uint64_t)kSampThreads) % (uint64_t)L.M);
+}
+
+template <typename R, bool SMEM_TAB>
+__global__ void __launch_bounds__(kSampThreads) k_sample(int64_t M, int bl, int64_t H,
+                                                         const typename C2<R>::T* __restrict__ lo_g,
+                                                         const typename C2<R>::T* __restrict__ hi_g,
+                                                         const int64_t* __restrict__ q, const int64_t* __restrict__ step,
+                                                         const double2* __restrict__ coef, int64_t n_terms, R* out) {
+  using T2 = typename C2<R>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int64_t L = 1ll << bl;
+  T2* s_lo = reinterpret_cast<T2*>(smem);
+  T2* s_hi = s_lo + (SMEM_TAB ? L : 0);
+  int64_t* s_q = reinterpret_cast<int64_t*>(s_hi + (SMEM_TAB ? H : 0));
+  int64_t* s_step = s_q + kTermChunk;
+  T2* s_c = reinterpret_cast<T2*>(s_step + kTermChunk);
+  if (SMEM_TAB) {
+    for (int64_t i = threadIdx.x; i < L; i += blockDim.x) s_lo[i] = lo_g[i];
+    for (int64_t i = threadIdx.x; i < H; i += blockDim.x) s_hi[i] = hi_g[i];
+  }
+  const T2* lo = SMEM_TAB ? s_lo : lo_g;
+  const T2* hi = SMEM_TAB ? s_hi : hi_g;
+  const uint32_t lmask = (uint32_t)(L - 1);
+  const int64_t j0 = (int64_t)blockIdx.x * (kSampThreads * kSampPerThread) + threadIdx.x;
+  R acc[kSampPerThread];
+#pragma unroll
+  for (int m = 0; m < kSampPerThread; ++m) acc[m] = (R)0;
+  for (int64_t t0 = 0; t0 < n_terms; t0 += kTermChunk) {
+    const int tc = (n_terms - t0 < kTermChunk) ? (int)(n_terms - t0) : kTermChunk;
+    __syncthreads();
+    for (int i = threadIdx.x; i < tc; i += blockDim.x) {
+      s_q[i] = q[t0 + i];
+      s_step[i] = step[t0 + i];
+      const double2 c = coef[t0 + i];
+      s_c[i].x = (R)c.x;
+      s_c[i].y = (R)c.y;
+    }
+    __syncthreads();
+    for (int t = 0; t < tc; ++t) {
+      const uint32_t st = (uint32_t)s_step[t];
+      uint32_t r = (uint32_t)(((uint64_t)j0 * (uint64_t)s_q[t]) % (uint64_t)M);
+      const T2 c = s_c[t];
+#pragma unroll
+      for (int m = 0; m < kSampPerThread; ++m) {
+        const T2 h = hi[r >> bl], l = lo[r & lmask];
+        const R er = h.x * l.x - h.y * l.y;   // cos(2 pi r / M)
+        const R ei = h.x * l.y + h.y * l.x;   // sin(2 pi r / M)
+        acc[m] += c.x * er - c.y * ei;
+        r += st;
+        if (r >= (uint32_t)M) r -= (uint32_t)M;
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < kSampPerThread; ++m) {
+    const int64_t j = j0 + (int64_t)m * kSampThreads;
+    if (j < M) out[j] = acc[m];
+  }
+}
+
+template <typename T2>
+__device__ __forceinline__ double2 bin(const T2* spec, int64_t M, int64_t b) {
+  if (2 * b <= M) return make_double2((double)spec[b].x, (double)spec[b].y);
+  const T2 v = spec[M - b];
+  return make_double2((double)v.x, -(double)v.y);
+}
+
+template <typename T2>
+__global__ void k_extract(const int32_t* __restrict__ cand, int64_t n, LatticeDev L, const T2* __restrict__ spec,
+                          double2* val, double* mag, unsigned long long* maxbits) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t b = residue_of(cand + i * L.d, L.d, L);
+  const int64_t nb = (L.M - b) % L.M;
+  const double2 x = bin(spec, L.M, b), y = bin(spec, L.M, nb);
+  const double sc = 0.5 / (double)L.M;
+  const double2 v = make_double2((x.x + y.x) * sc, (x.y - y.y) * sc);
+  val[i] = v;
+  const double m = hypot(v.x, v.y);
+  mag[i] = m;
+  atomicMax(maxbits, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void k_keep(const double* __restrict__ mag, int64_t n, const unsigned long long* __restrict__ maxbits,
+                       double tau, int32_t* flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double mx = __longlong_as_double((long long)*maxbits);
+  flag[i] = mag[i] > tau * mx ? 1 : 0;
+}
+
+__global__ void k_compact(const int32_t* __restrict__ cand, const double2* __restrict__ val, int64_t n, int d,
+                          const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int32_t* fo, double2* vo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !flag[i]) return;
+  const int64_t p = pos[i];
+  for (int c = 0; c < d; ++c) fo[p * d + c] = cand[i * d + c];
+  vo[p] = val[i];
+}
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// Per-(M, precision) FFT plan, sample and spectrum buffers and twiddle tables.
+struct SftPlan {
+  int64_t M = 0;
+  ss_precision prec = SS_FP64;
+  int bl = 0;
+  int64_t H = 0;
+  cufftHandle fft = 0;
+  bool has_fft = false;
+  DevBuf<unsigned char> samples, spectrum, lo, hi;
+  ~SftPlan() {
+    if (has_fft) cufftDestroy(fft);
+  }
+};
+
+std::mutex g_plan_mu;
+std::list<std::shared_ptr<SftPlan>> g_plans;   // most recent first
+constexpr size_t kMaxPlans = 4;
+
+ss_status get_plan(int64_t M, ss_precision prec, cudaStream_t st, std::shared_ptr<SftPlan>* out) {
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  for (auto it = g_plans.begin(); it != g_plans.end(); ++it) {
+    if ((*it)->M == M && (*it)->prec == prec) {
+      auto p = *it;
+      g_plans.erase(it);
+      g_plans.push_front(p);
+      *out = p;
+      return SS_OK;
+    }
+  }
+  auto p = std::make_shared<SftPlan>();
+  p->M = M;
+  p->prec = prec;
+  int bits = 0;
+  while ((1ll << bits) < M) ++bits;
+  p->bl = (bits + 1) / 2;
+  p->H = (M + (1ll << p->bl) - 1) >> p->bl;
+  const size_t real_sz = prec == SS_FP64 ? sizeof(double) : sizeof(float);
+  const size_t cplx_sz = 2 * real_sz;
+  SS_TRY(p->samples.alloc(M * real_sz));
+  SS_TRY(p->spectrum.alloc((M / 2 + 1) * cplx_sz));
+  SS_TRY(p->lo.alloc((1ll << p->bl) * cplx_sz));
+  SS_TRY(p->hi.alloc(p->H * cplx_sz));
+  const int64_t nt = std::max<int64_t>(1ll << p->bl, p->H);
+  if (prec == SS_FP64)
+    k_twiddles<double><<<nblk(nt), 256, 0, st>>>(M, p->bl, p->H, reinterpret_cast<double2*>(p->lo.get()),
+                                                 reinterpret_cast<double2*>(p->hi.get()));
+  else
+    k_twiddles<float><<<nblk(nt), 256, 0, st>>>(M, p->bl, p->H, reinterpret_cast<float2*>(p->lo.get()),
+                                                reinterpret_cast<float2*>(p->hi.get()));
+  SS_LAUNCH_CHECK();
+  const cufftResult r = cufftPlan1d(&p->fft, (int)M, prec == SS_FP64 ? CUFFT_D2Z : CUFFT_R2C, 1);
+  if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cufftPlan1d(%lld) failed: %d", (long long)M, (int)r);
+  p->has_fft = true;
+  g_plans.push_front(p);
+  while (g_plans.size() > kMaxPlans) g_plans.pop_back();
+  *out = p;
+  return SS_OK;
+}
+
+ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, void* out, cudaStream_t st) {
+  const int64_t n = g->n_terms;
+  DevBuf<int64_t> q, step;
+  SS_TRY(q.alloc(n));
+  SS_TRY(step.alloc(n));
+  if (n > 0) {
+    k_term_residues<<<nblk(n), 256, 0, st>>>(g->freq, n, L, q.get(), step.get());
+    SS_LAUNCH_CHECK();
+  }
+  const int64_t Lsz = 1ll << P.bl;
+  const unsigned grid = (unsigned)((P.M + kSampThreads * kSampPerThread - 1) / (kSampThreads * kSampPerThread));
+  const double2* coef = reinterpret_cast<const double2*>(g->coef);
+  if (P.prec == SS_FP64) {
+    const size_t terms_sm = kTermChunk * (2 * sizeof(int64_t) + sizeof(double2));
+    const size_t tab_sm = (Lsz + P.H) * sizeof(double2);
+    const bool smem = tab_sm + terms_sm <= 200 * 1024;
+    const size_t sm = (smem ? tab_sm : 0) + terms_sm;
+    auto lo = reinterpret_cast<const double2*>(P.lo.get());
+    auto hi = reinterpret_cast<const double2*>(P.hi.get());
+    if (smem) {
+      SS_CUDA(cudaFuncSetAttribute(k_sample<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      k_sample<double, true><<<grid, kSampThreads, sm, st>>>(P.M, P.bl, P.H, lo, hi, q.get(), step.get(), coef, n,
+                                                             reinterpret_cast<double*>(out));
+    } else {
+      SS_CUDA(cudaFuncSetAttribute(k_sample<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      k_sample<double, false><<<grid, kSampThreads, sm, st>>>(P.M, P.bl, P.H, lo, hi, q.get(), step.get(), coef, n,
+                                                              reinterpret_cast<double*>(out));
+    }
+  } else {
+    const size_t terms_sm = kTermChunk * (2 * sizeof(int64_t) + sizeof(float2));
+    const size_t tab_sm = (Lsz + P.H) * sizeof(float2);
+    const bool smem = tab_sm + terms_sm <= 200 * 1024;
+    const size_t sm = (smem ? tab_sm : 0) + terms_sm;
+    auto lo = reinterpret_cast<const float2*>(P.lo.get());
+    auto hi = reinterpret_cast<const float2*>(P.hi.get());
+    if (smem) {
+      SS_CUDA(cudaFuncSetAttribute(k_sample<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      k_sample<float, true><<<grid, kSampThreads, sm, st>>>(P.M, P.bl, P.H, lo, hi, q.get(), step.get(), coef, n,
+                                                            reinterpret_cast<float*>(out));
+    } else {
+      SS_CUDA(cudaFuncSetAttribute(k_sample<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      k_sample<float, false><<<grid, kSampThreads, sm, st>>>(P.M, P.bl, P.H, lo, hi, q.get(), step.get(), coef, n,
+                                                             reinterpret_cast<float*>(out));
+    }
+  }
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
+ss_status recover_from(const SftPlan& P, const LatticeDev& L, const void* samples, const int32_t* cand, int64_t n_cand,
+                       int64_t s_max, double tau, int32_t* freq_out, double* val_out, int64_t* n_out, cudaStream_t st) {
+  // reconstructing + symmetric candidate set
+  DevBuf<int64_t> res;
+  SS_TRY(res.alloc(n_cand));
+  SS_TRY(residues(cand, n_cand, L, res.get(), st));
+  SS_TRY(check_reconstructing(cand, n_cand, L, res.get(), true, st));
+  // FFT
+  cufftResult r = cufftSetStream(P.fft, st);
+  if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cufftSetStream failed: %d", (int)r);
+  if (P.prec == SS_FP64)
+    r = cufftExecD2Z(P.fft, reinterpret_cast<cufftDoubleReal*>(const_cast<void*>(samples)),
+                     reinterpret_cast<cufftDoubleComplex*>(P.spectrum.get()));
+  else
+    r = cufftExecR2C(P.fft, reinterpret_cast<cufftReal*>(const_cast<void*>(samples)),
+                     reinterpret_cast<cufftComplex*>(P.spectrum.get()));
+  if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cuFFT exec failed: %d", (int)r);
+  // bins, threshold, compaction in candidate order
+  DevBuf<double2> val;
+  DevBuf<double> mag;
+  DevBuf<unsigned long long> maxbits;
+  DevBuf<int32_t> flag, pos;
+  DevBuf<int64_t> total;
+  SS_TRY(val.alloc(n_cand));
+  SS_TRY(mag.alloc(n_cand));
+  SS_TRY(maxbits.alloc(1));
+  SS_TRY(flag.alloc(n_cand));
+  SS_TRY(pos.alloc(n_cand));
+  SS_TRY(total.alloc(1));
+  SS_CUDA(cudaMemsetAsync(maxbits.get(), 0, sizeof(unsigned long long), st));
+  if (P.prec == SS_FP64)
+    k_extract<double2><<<nblk(n_cand), 256, 0, st>>>(cand, n_cand, L, reinterpret_cast<const double2*>(P.spectrum.get()),
+                                                     val.get(), mag.get(), maxbits.get());
+  else
+    k_extract<float2><<<nblk(n_cand), 256, 0, st>>>(cand, n_cand, L, reinterpret_cast<const float2*>(P.spectrum.get()),
+                                                    val.get(), mag.get(), maxbits.get());
+  k_keep<<<nblk(n_cand), 256, 0, st>>>(mag.get(), n_cand, maxbits.get(), tau, flag.get());
+  SS_LAUNCH_CHECK();
+  SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), n_cand, total.get(), st));
+  int64_t kept = 0;
+  SS_CUDA(cudaMemcpyAsync(&kept, total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  if (s_max > 0 && kept > s_max)
+    SS_FAIL(SS_ERR_INVALID, "sft_recover: %lld terms above threshold exceed s_max = %lld", (long long)kept,
+            (long long)s_max);
+  k_compact<<<nblk(n_cand), 256, 0, st>>>(cand, val.get(), n_cand, L.d, flag.get(), pos.get(), freq_out,
+                                          reinterpret_cast<double2*>(val_out));
+  SS_LAUNCH_CHECK();
+  SS_CUDA(cudaStreamSynchronize(st));
+  *n_out = kept;
+  return SS_OK;
+}
+
+ss_status check_trig(const ss_trig* g, int d) {
+  if (!g) SS_FAIL(SS_ERR_INVALID, "null trigonometric sum");
+  if (g->d != d) SS_FAIL(SS_ERR_INVALID, "trigonometric sum has d = %d, lattice d = %d", g->d, d);
+  if (g->n_terms < 0 || (g->n_terms > 0 && (!g->freq || !g->coef))) SS_FAIL(SS_ERR_INVALID, "bad trigonometric sum");
+  return SS_OK;
+}
+
+}  // namespace
+}  // namespace ss
+
+using namespace ss;
+
+extern "C" ss_status lattice_sample(const ss_lattice* lat, const ss_trig* g, ss_precision prec, void* samples,
+                                    void* stream) {
+  LatticeDev L;
+  SS_TRY(make_lattice_dev(lat, &L));
+  SS_TRY(check_trig(g, L.d));
+  if (!samples) SS_FAIL(SS_ERR_INVALID, "lattice_sample: null output");
+  if (prec != SS_FP64 && prec != SS_FP32) SS_FAIL(SS_ERR_INVALID, "lattice_sample: bad precision");
+  cudaStream_t st = as_stream(stream);
+  std::shared_ptr<SftPlan> P;
+  SS_TRY(get_plan(L.M, prec, st, &P));
+  return sample_into(*P, L, g, samples, st);
+}
+
+extern "C" ss_status sft_recover_samples(const ss_lattice* lat, const void* samples, ss_precision prec,
+                                         const int32_t* cand, int64_t n_cand, int64_t s_max, double tau,
+                                         int32_t* freq_out, double* val_out, int64_t* n_out, void* stream) {
+  LatticeDev L;
+  SS_TRY(make_lattice_dev(lat, &L));
+  if (!samples || !cand || !freq_out || !val_out || !n_out || n_cand < 1)
+    SS_FAIL(SS_ERR_INVALID, "sft_recover_samples: bad argument");
+  if (!(tau >= 0.0)) SS_FAIL(SS_ERR_INVALID, "sft_recover_samples: tau must be >= 0");
+  if (prec != SS_FP64 && prec != SS_FP32) SS_FAIL(SS_ERR_INVALID, "sft_recover_samples: bad precision");
+  cudaStream_t st = as_stream(stream);
+  std::shared_ptr<SftPlan> P;
+  SS_TRY(get_plan(L.M, prec, st, &P));
+  return recover_from(*P, L, samples, cand, n_cand, s_max, tau, freq_out, val_out, n_out, st);
+}
+
+extern "C" ss_status sft_recover(const ss_lattice* lat, const ss_trig* g, ss_precision prec, const int32_t* cand,
+                                 int64_t n_cand, int64_t s_max, double tau, int32_t* freq_out, double* val_out,
+                                 int64_t* n_out, void* stream) {
+  LatticeDev L;
+  SS_TRY(make_lattice_dev(lat, &L));
+  SS_TRY(check_trig(g, L.d));
+  if (!cand || !freq_out || !val_out || !n_out || n_cand < 1) SS_FAIL(SS_ERR_INVALID, "sft_recover: bad argument");
+  if (!(tau >= 0.0)) SS_FAIL(SS_ERR_INVALID, "sft_recover: tau must be >= 0");
+  if (prec != SS_FP64 && prec != SS_FP32) SS_FAIL(SS_ERR_INVALID, "sft_recover: bad precision");
+  cudaStream_t st = as_stream(stream);
+  std::shared_ptr<SftPlan> P;
+  SS_TRY(get_plan(L.M, prec, st, &P));
+  SS_TRY(sample_into(*P, L, g, P->samples.get(), st));
+  return recover_from(*P, L, P->samples.get(), cand, n_cand, s_max, tau, freq_out, val_out, n_out, st);
+}

@@ -1,0 +1,778 @@
+// Persistent Jacobi-preconditioned CG for L_{N,s} u = f (eq.
+// SparseSpectralSFTEquation), one cooperative launch per solve.
+//
+// The rows of one or many instances form one row space cut into 32-row slices
+// (one warp each).  The slices are split once into contiguous chunks (static
+// work units); every CG phase walks the block's chunks, and a grid-wide barrier
+// separates phases.  Inner products are reduced deterministically: per chunk
+// and instance, warps add their slices in order, the block adds its warps in
+// order into one partial slot, and every block that needs a scalar sums that
+// instance's slots with the same fixed warp reduction.  Per-instance state that
+// crosses phases (rho, active flags) is double-buffered by iteration parity and
+// written only by the instance's owner block (the one holding its first
+// chunk), so no phase reads a value that is written in the same phase.
+//
+// Modes
+//   FP64  plain CG on the FP64 operator.
+//   FP32  iterative refinement: r = f - L x with the FP64 operator, then CG on
+//         the FP32 operator (FP32 values and accumulation; FP64 vectors and
+//         scalars) to a relative reduction inner_tol, then x += delta.
+// The Jacobi preconditioner is D_k = 4 pi^2 Re(a_hat_0) |k|^2 (the diagonal of L),
+// 1 on the zero row and on padding rows.
+#include <algorithm>
+#include <cmath>
+
+#include "solve.cuh"
+
+namespace ss {
+namespace {
+
+struct Smem {
+  double acc[kMaxWarps][kMaxInstPerChunk][kNQ];
+  double ca[kMaxInstPerChunk];
+  double cb[kMaxInstPerChunk];
+  int32_t flag[kMaxInstPerChunk];
+};
+
+__device__ __forceinline__ long long gtimer() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier (all blocks are co-resident: cooperative launch).  A wait
+// longer than spin_limit ns sets SS_ERR_TIMEOUT and returns false; so does any
+// error already posted by another block.
+__device__ bool grid_sync(const SolveParams& P) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = P.bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(P.bar, 1u) + 1u;
+    int ok = 1;
+    if (arrived == gridDim.x) {
+      atomicExch(P.bar, 0u);
+      __threadfence();
+      atomicAdd(P.bar + 1, 1u);
+    } else {
+      const long long t0 = gtimer();
+      while (*gen == g) {
+        if (*(volatile int*)P.err) { ok = 0; break; }
+        if (gtimer() - t0 > P.spin_limit) {
+          atomicCAS(P.err, 0, (int)SS_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)P.err) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ int read_counter(const int* p) { return atomicAdd(const_cast<int*>(p), 0); }
+
+// Sum of quantity q over the partial slots of instance i (all lanes of the
+// warp call; the result of lane 0 is broadcast, so every block gets the same bits).
+__device__ double inst_sum(const SolveParams& P, int i, int q) {
+  const int lane = threadIdx.x & 31;
+  const SolveInst& in = P.inst[i];
+  const int len = in.c_last - in.c_first + 1;
+  double s = 0.0;
+  for (int c = lane; c < len; c += 32) s += __ldcg(P.part + (int64_t)(in.part_base + c) * kNQ + q);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return __shfl_sync(0xffffffffu, s, 0);
+}
+
+__device__ __forceinline__ double warp_reduce(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Run one phase over the block's chunks.
+//   scal(c, ch, k, i, owner): per instance of the chunk (one warp each), fills
+//                             sm.ca/cb/flag[k] and does the owner's bookkeeping;
+//   row(g, s, lane, i, k, vals): per row, adds to vals[q] for q in qmask.
+template <class Scal, class Row>
+__device__ void run_phase(const SolveParams& P, Smem& sm, unsigned qmask, Scal scal, Row row) {
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = blockIdx.x; c < P.n_chunks; c += gridDim.x) {
+    const Chunk ch = P.chunk[c];
+    const int ni = ch.inst1 - ch.inst0 + 1;
+    if (qmask)
+      for (int t = threadIdx.x; t < nw * kMaxInstPerChunk * kNQ; t += blockDim.x)
+        (&sm.acc[0][0][0])[t] = 0.0;
+    for (int k = warp; k < ni; k += nw) {
+      const int i = ch.inst0 + k;
+      scal(c, ch, k, i, c == P.inst[i].c_first, lane);
+    }
+    __syncthreads();
+    int cur_k = -1;
+    double run[kNQ] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t s = ch.s0 + warp; s < ch.s1; s += nw) {
+      const int i = P.slice_inst ? __ldg(P.slice_inst + s) : 0;
+      const int k = i - ch.inst0;
+      const int64_t g = s * kSlice + lane;
+      double vals[kNQ] = {0.0, 0.0, 0.0, 0.0};
+      row(g, s, lane, i, k, vals);
+      if (qmask) {
+        if (k != cur_k) {
+          if (cur_k >= 0 && lane == 0)
+            for (int q = 0; q < kNQ; ++q) sm.acc[warp][cur_k][q] += run[q];
+          for (int q = 0; q < kNQ; ++q) run[q] = 0.0;
+          cur_k = k;
+        }
+#pragma unroll
+        for (int q = 0; q < kNQ; ++q)
+          if (qmask & (1u << q)) run[q] += warp_reduce(vals[q]);
+      }
+    }
+    if (qmask && cur_k >= 0 && lane == 0)
+      for (int q = 0; q < kNQ; ++q) sm.acc[warp][cur_k][q] += run[q];
+    __syncthreads();
+    if (qmask) {
+      for (int t = threadIdx.x; t < ni * kNQ; t += blockDim.x) {
+        const int k = t / kNQ, q = t % kNQ;
+        if (!(qmask & (1u << q))) continue;
+        double v = 0.0;
+        for (int w = 0; w < nw; ++w) v += sm.acc[w][k][q];
+        const SolveInst& in = P.inst[ch.inst0 + k];
+        P.part[(int64_t)(in.part_base + (c - in.c_first)) * kNQ + q] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ double jacobi(const SolveParams& P, const SolveInst& in, int64_t g) {
+  const int32_t nk = __ldg(P.norm + g);
+  return nk > 0 ? in.dscale * (double)nk : 1.0;
+}
+
+__device__ __forceinline__ double2 f_at(const SolveInst& in, int64_t g) {
+  const int64_t l = g - in.row0;
+  return l < in.rows ? in.f[l] : make_double2(0.0, 0.0);
+}
+
+__device__ __forceinline__ double2 apply64_row(const SolveParams& P, const SolveInst& in, int64_t s, int lane,
+                                               int64_t g, const double2* rec) {
+  if (g == in.zero_row) return __ldcg(rec + 2 * g);
+  return row_apply64<true>(P.op, s, lane, __ldg(P.norm + g), rec, P.ca64 + in.coef_off, P.pn + in.coef_off);
+}
+
+__device__ __forceinline__ float2 apply32_row(const SolveParams& P, const SolveInst& in, int64_t s, int lane,
+                                              int64_t g) {
+  if (g == in.zero_row) {
+    const float4 v = __ldcg(P.prec32 + g);
+    return make_float2(v.x, v.y);
+  }
+  return row_apply32<true>(P.op, s, lane, __ldg(P.norm + g), P.prec32, P.ca32 + in.coef_off, P.pn + in.coef_off);
+}
+
+__device__ __forceinline__ void owner_done(const SolveParams& P, InstState& st, int status) {
+  st.status = status;
+  atomicAdd(P.counters + 0, 1);
+}
+
+// --------------------------------------------------------------- FP64 CG
+
+__device__ void solve_fp64(const SolveParams& P, Smem& sm) {
+  const double tol2 = P.tol * P.tol;
+  // r = f, x = 0, z = D^-1 r, p = z; partials <r,z>, |f|^2
+  run_phase(P, sm, 0b1010u, [](int, const Chunk&, int, int, bool, int) {}, [&](int64_t g, int64_t, int, int i, int, double* v) {
+    const SolveInst& in = P.inst[i];
+    const double2 f = f_at(in, g);
+    const double D = jacobi(P, in, g);
+    const double2 z = make_double2(f.x / D, f.y / D);
+    P.r[g] = f;
+    P.z[g] = z;
+    P.xrec[2 * g] = make_double2(0.0, 0.0);
+    P.prec64[2 * g] = z;
+    v[1] = f.x * z.x + f.y * z.y;
+    v[3] = f.x * f.x + f.y * f.y;
+  });
+  if (!grid_sync(P)) return;
+  run_phase(P, sm, 0u, [&](int, const Chunk&, int, int i, bool owner, int lane) {
+    const double rz = inst_sum(P, i, 1), bb = inst_sum(P, i, 3);
+    if (owner && lane == 0) {
+      InstState& st = P.state[i];
+      st.bb = bb;
+      st.rr = bb;
+      st.rho[0] = rz;
+      st.iters = 0;
+      st.applies = 0;
+      st.outer_iters = 1;
+      st.act[0] = bb > 0.0;
+      if (!(bb > 0.0)) owner_done(P, st, SS_OK);
+    }
+  }, [](int64_t, int64_t, int, int, int, double*) {});
+  if (!grid_sync(P)) return;
+  for (int it = 0;; ++it) {
+    if (read_counter(P.counters + 0) >= P.n_inst) break;
+    const int cur = it & 1, nxt = cur ^ 1;
+    // q = L p, <p, q>
+    run_phase(P, sm, 0b0001u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
+      if (lane == 0) {
+        sm.flag[k] = __ldcg(&P.state[i].act[cur]);
+        if (owner && sm.flag[k]) P.state[i].applies += 1;
+      }
+    }, [&](int64_t g, int64_t s, int lane, int i, int k, double* v) {
+      if (!sm.flag[k]) return;
+      const SolveInst& in = P.inst[i];
+      const double2 q = apply64_row(P, in, s, lane, g, P.prec64);
+      const double2 p = P.prec64[2 * g];
+      P.q64[g] = q;
+      v[0] = p.x * q.x + p.y * q.y;
+    });
+    if (!grid_sync(P)) return;
+    // alpha = rho / <p,q>; x += alpha p; r -= alpha q; z = D^-1 r; <r,z>, |r|^2
+    run_phase(P, sm, 0b0110u, [&](int, const Chunk&, int k, int i, bool, int lane) {
+      const double pq = inst_sum(P, i, 0);
+      if (lane == 0) {
+        sm.flag[k] = __ldcg(&P.state[i].act[cur]);
+        sm.ca[k] = __ldcg(&P.state[i].rho[cur]) / pq;
+      }
+    }, [&](int64_t g, int64_t, int, int i, int k, double* v) {
+      if (!sm.flag[k]) return;
+      const SolveInst& in = P.inst[i];
+      const double a = sm.ca[k];
+      const double2 p = P.prec64[2 * g], q = P.q64[g];
+      double2 x = P.xrec[2 * g], r = P.r[g];
+      x.x += a * p.x; x.y += a * p.y;
+      r.x -= a * q.x; r.y -= a * q.y;
+      const double D = jacobi(P, in, g);
+      const double2 z = make_double2(r.x / D, r.y / D);
+      P.xrec[2 * g] = x;
+      P.r[g] = r;
+      P.z[g] = z;
+      v[1] = r.x * z.x + r.y * z.y;
+      v[2] = r.x * r.x + r.y * r.y;
+    });
+    if (!grid_sync(P)) return;
+    // convergence, beta = rho_new / rho, p = z + beta p
+    run_phase(P, sm, 0u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
+      const double rz = inst_sum(P, i, 1), rr = inst_sum(P, i, 2);
+      if (lane == 0) {
+        InstState& st = P.state[i];
+        const int act = __ldcg(&st.act[cur]);
+        const double bb = __ldcg(&st.bb);
+        const bool conv = rr <= tol2 * bb;
+        const bool cap = it + 1 >= P.max_iter;
+        sm.flag[k] = act && !conv && !cap;
+        sm.cb[k] = rz / __ldcg(&st.rho[cur]);
+        if (owner) {
+          st.act[nxt] = act && !conv && !cap;
+          st.rho[nxt] = rz;
+          if (act) {
+            st.iters = it + 1;
+            st.rr = rr;
+            if (conv) owner_done(P, st, SS_OK);
+            else if (cap) owner_done(P, st, SS_ERR_NOT_CONVERGED);
+          }
+        }
+      }
+    }, [&](int64_t g, int64_t, int, int, int k, double*) {
+      if (!sm.flag[k]) return;
+      const double b = sm.cb[k];
+      const double2 z = P.z[g], p = P.prec64[2 * g];
+      P.prec64[2 * g] = make_double2(z.x + b * p.x, z.y + b * p.y);
+    });
+    if (!grid_sync(P)) return;
+  }
+  // true residual f - L x in FP64, and the output
+  run_phase(P, sm, 0b0100u, [](int, const Chunk&, int, int, bool, int) {},
+            [&](int64_t g, int64_t s, int lane, int i, int, double* v) {
+    const SolveInst& in = P.inst[i];
+    const double2 y = apply64_row(P, in, s, lane, g, P.xrec);
+    const double2 f = f_at(in, g);
+    const double2 r = make_double2(f.x - y.x, f.y - y.y);
+    v[2] = r.x * r.x + r.y * r.y;
+    const int64_t l = g - in.row0;
+    if (l < in.rows) in.u[l] = P.xrec[2 * g];
+  });
+  if (!grid_sync(P)) return;
+  run_phase(P, sm, 0u, [&](int, const Chunk&, int, int i, bool owner, int lane) {
+    const double rr = inst_sum(P, i, 2);
+    if (owner && lane == 0) {
+      P.state[i].rr = rr;
+      P.state[i].applies += 1;
+    }
+  }, [](int64_t, int64_t, int, int, int, double*) {});
+}
+
+// ------------------------------------------------- FP32 CG in FP64 refinement
+
+__device__ void solve_refined(const SolveParams& P, Smem& sm) {
+  const double tol2 = P.tol * P.tol, itol2 = P.inner_tol * P.inner_tol;
+  // x = 0; |f|^2
+  run_phase(P, sm, 0b1000u, [](int, const Chunk&, int, int, bool, int) {},
+            [&](int64_t g, int64_t, int, int i, int, double* v) {
+    const double2 f = f_at(P.inst[i], g);
+    P.xrec[2 * g] = make_double2(0.0, 0.0);
+    v[3] = f.x * f.x + f.y * f.y;
+  });
+  if (!grid_sync(P)) return;
+  run_phase(P, sm, 0u, [&](int, const Chunk&, int, int i, bool owner, int lane) {
+    const double bb = inst_sum(P, i, 3);
+    if (owner && lane == 0) {
+      InstState& st = P.state[i];
+      st.bb = bb;
+      st.rr = bb;
+      st.iters = st.inner_iters = st.outer_iters = st.applies = 0;
+      st.act[0] = bb > 0.0;
+      if (!(bb > 0.0)) owner_done(P, st, SS_OK);
+    }
+  }, [](int64_t, int64_t, int, int, int, double*) {});
+  if (!grid_sync(P)) return;
+  for (int ot = 0;; ++ot) {
+    const int ocur = ot & 1, onxt = ocur ^ 1;
+    // rhat = f - L64 x, |rhat|^2
+    run_phase(P, sm, 0b0100u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
+      if (lane == 0) {
+        sm.flag[k] = __ldcg(&P.state[i].act[ocur]);
+        if (owner && sm.flag[k]) P.state[i].applies += 1;
+      }
+    }, [&](int64_t g, int64_t s, int lane, int i, int k, double* v) {
+      if (!sm.flag[k]) return;
+      const SolveInst& in = P.inst[i];
+      const double2 y = apply64_row(P, in, s, lane, g, P.xrec);
+      const double2 f = f_at(in, g);
+      const double2 r = make_double2(f.x - y.x, f.y - y.y);
+      P.rhat[g] = r;
+      v[2] = r.x * r.x + r.y * r.y;
+    });
+    if (!grid_sync(P)) return;
+    // outer test; inner start: r = rhat, delta = 0, z = D^-1 r, p = z; <r,z>
+    run_phase(P, sm, 0b0010u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
+      const double rr = inst_sum(P, i, 2);
+      if (lane == 0) {
+        InstState& st = P.state[i];
+        const int act = __ldcg(&st.act[ocur]);
+        const bool conv = rr <= tol2 * __ldcg(&st.bb);
+        const bool cap = ot >= P.max_outer;
+        const bool go = act && !conv && !cap;
+        sm.flag[k] = go;
+        if (owner) {
+          st.act[onxt] = go;
+          st.inn[0] = go;
+          if (act) {
+            st.rr = rr;
+            if (conv) owner_done(P, st, SS_OK);
+            else if (cap) owner_done(P, st, SS_ERR_NOT_CONVERGED);
+            else {
+              st.outer_iters = ot + 1;
+              atomicAdd(P.counters + 1, 1);
+            }
+          }
+        }
+      }
+    }, [&](int64_t g, int64_t, int, int i, int k, double* v) {
+      if (!sm.flag[k]) return;
+      const SolveInst& in = P.inst[i];
+      const double2 r = P.rhat[g];
+      const double D = jacobi(P, in, g);
+      const double2 z = make_double2(r.x / D, r.y / D);
+      P.r[g] = r;
+      P.z[g] = z;
+      P.dlt[g] = make_double2(0.0, 0.0);
+      reinterpret_cast<float2*>(P.prec32 + g)[0] = make_float2((float)z.x, (float)z.y);
+      v[1] = r.x * z.x + r.y * z.y;
+    });
+    if (!grid_sync(P)) return;
+    if (read_counter(P.counters + 0) >= P.n_inst) break;
+    for (int it = 0;; ++it) {
+      const int cur = it & 1, nxt = cur ^ 1;
+      // q = L32 p, <p, q>
+      run_phase(P, sm, 0b0001u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
+        const double rz0 = (it == 0) ? inst_sum(P, i, 1) : 0.0;
+        if (lane == 0) {
+          InstState& st = P.state[i];
+          sm.flag[k] = __ldcg(&st.inn[cur]);
+          if (owner && sm.flag[k]) {
+            st.applies += 1;
+            if (it == 0) st.rho[0] = rz0;
+          }
+        }
+      }, [&](int64_t g, int64_t s, int lane, int i, int k, double* v) {
+        if (!sm.flag[k]) return;
+        const SolveInst& in = P.inst[i];
+        const float2 q = apply32_row(P, in, s, lane, g);
+        const float4 p = P.prec32[g];
+        P.q32[g] = q;
+        v[0] = (double)p.x * (double)q.x + (double)p.y * (double)q.y;
+      });
+      if (!grid_sync(P)) return;
+      // alpha; delta += alpha p; r -= alpha q; z = D^-1 r; <r,z>, |r|^2
+      run_phase(P, sm, 0b0110u, [&](int, const Chunk&, int k, int i, bool, int lane) {
+        const double pq = inst_sum(P, i, 0);
+        if (lane == 0) {
+          sm.flag[k] = __ldcg(&P.state[i].inn[cur]);
+          sm.ca[k] = __ldcg(&P.state[i].rho[cur]) / pq;
+        }
+      }, [&](int64_t g, int64_t, int, int i, int k, double* v) {
+        if (!sm.flag[k]) return;
+        const SolveInst& in = P.inst[i];
+        const double a = sm.ca[k];
+        const float4 p = P.prec32[g];
+        const float2 q = P.q32[g];
+        double2 dl = P.dlt[g], r = P.r[g];
+        dl.x += a * (double)p.x; dl.y += a * (double)p.y;
+        r.x -= a * (double)q.x; r.y -= a * (double)q.y;
+        const double D = jacobi(P, in, g);
+        const double2 z = make_double2(r.x / D, r.y / D);
+        P.dlt[g] = dl;
+        P.r[g] = r;
+        P.z[g] = z;
+        v[1] = r.x * z.x + r.y * z.y;
+        v[2] = r.x * r.x + r.y * r.y;
+      });
+      if (!grid_sync(P)) return;
+      // inner test, beta, p = z + beta p (FP32 records)
+      run_phase(P, sm, 0u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
+        const double rz = inst_sum(P, i, 1), rr = inst_sum(P, i, 2);
+        if (lane == 0) {
+          InstState& st = P.state[i];
+          const int act = __ldcg(&st.inn[cur]);
+          const bool conv = rr <= itol2 * __ldcg(&st.rr);
+          const bool cap = it + 1 >= P.max_inner;
+          sm.flag[k] = act && !conv && !cap;
+          sm.cb[k] = rz / __ldcg(&st.rho[cur]);
+          if (owner) {
+            st.inn[nxt] = act && !conv && !cap;
+            st.rho[nxt] = rz;
+            if (act) {
+              st.inner_iters += 1;
+              if (conv || cap) atomicAdd(P.counters + 2, 1);
+            }
+          }
+        }
+      }, [&](int64_t g, int64_t, int, int, int k, double*) {
+        if (!sm.flag[k]) return;
+        const double b = sm.cb[k];
+        const double2 z = P.z[g];
+        const float4 p = P.prec32[g];
+        reinterpret_cast<float2*>(P.prec32 + g)[0] =
+            make_float2((float)(z.x + b * (double)p.x), (float)(z.y + b * (double)p.y));
+      });
+      if (!grid_sync(P)) return;
+      if (read_counter(P.counters + 2) >= read_counter(P.counters + 1)) break;
+    }
+    // x += delta
+    run_phase(P, sm, 0u, [&](int, const Chunk&, int k, int i, bool, int lane) {
+      if (lane == 0) sm.flag[k] = __ldcg(&P.state[i].act[onxt]);
+    }, [&](int64_t g, int64_t, int, int, int k, double*) {
+      if (!sm.flag[k]) return;
+      double2 x = P.xrec[2 * g];
+      const double2 dl = P.dlt[g];
+      x.x += dl.x;
+      x.y += dl.y;
+      P.xrec[2 * g] = x;
+    });
+    if (!grid_sync(P)) return;
+  }
+  run_phase(P, sm, 0u, [](int, const Chunk&, int, int, bool, int) {},
+            [&](int64_t g, int64_t, int, int i, int, double*) {
+    const SolveInst& in = P.inst[i];
+    const int64_t l = g - in.row0;
+    if (l < in.rows) in.u[l] = P.xrec[2 * g];
+  });
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(512) k_solve(SolveParams P) {
+  __shared__ Smem sm;
+  if (MODE == 0) solve_fp64(P, sm);
+  else solve_refined(P, sm);
+}
+
+__global__ void k_init_solve_records(const int32_t* __restrict__ norm, int64_t n, double2* xrec, double2* prec64,
+                                     float4* prec32) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const int32_t nr = norm[g];
+  const double2 nb = make_double2(__longlong_as_double((long long)nr), 0.0);
+  xrec[2 * g] = make_double2(0.0, 0.0);
+  xrec[2 * g + 1] = nb;
+  prec64[2 * g] = make_double2(0.0, 0.0);
+  prec64[2 * g + 1] = nb;
+  prec32[g] = make_float4(0.f, 0.f, __int_as_float(nr), 0.f);
+}
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+
+ss_status plan_chunks(SolvePlan& plan, const std::vector<int32_t>& woff, const std::vector<int32_t>& slice_inst,
+                      int target_chunks) {
+  const int64_t n_slices = (int64_t)woff.size() - 1;
+  const int n_inst = (int)plan.inst.size();
+  plan.chunk.clear();
+  if (n_slices <= 0) SS_FAIL(SS_ERR_INVALID, "solve: empty operator");
+  // weight of a slice: its entries (gathers) plus the vector work of 32 rows
+  auto weight = [&](int64_t s) { return (double)(woff[s + 1] - woff[s]) + 6.0; };
+  double total = 0;
+  for (int64_t s = 0; s < n_slices; ++s) total += weight(s);
+  const double target = total / std::max(1, target_chunks);
+  auto inst_of = [&](int64_t s) { return slice_inst.empty() ? 0 : slice_inst[s]; };
+  int64_t s0 = 0;
+  double acc = 0;
+  for (int64_t s = 0; s < n_slices; ++s) {
+    acc += weight(s);
+    const bool last = s + 1 == n_slices;
+    bool cut = last || acc >= target;
+    if (!last && inst_of(s + 1) - inst_of(s0) + 1 > kMaxInstPerChunk) cut = true;
+    if (cut) {
+      plan.chunk.push_back(Chunk{s0, s + 1, inst_of(s0), inst_of(s)});
+      s0 = s + 1;
+      acc = 0;
+    }
+  }
+  for (auto& in : plan.inst) { in.c_first = INT32_MAX; in.c_last = -1; }
+  for (int c = 0; c < (int)plan.chunk.size(); ++c)
+    for (int i = plan.chunk[c].inst0; i <= plan.chunk[c].inst1; ++i) {
+      plan.inst[i].c_first = std::min(plan.inst[i].c_first, c);
+      plan.inst[i].c_last = std::max(plan.inst[i].c_last, c);
+    }
+  int32_t base = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    if (plan.inst[i].c_last < 0) SS_FAIL(SS_ERR_INVALID, "solve: instance %d has no rows", i);
+    plan.inst[i].part_base = base;
+    base += plan.inst[i].c_last - plan.inst[i].c_first + 1;
+  }
+  plan.n_parts = base;
+  return SS_OK;
+}
+
+ss_status work_alloc(SolveWork& W, int64_t rows_total, const int32_t* norm, cudaStream_t st) {
+  if (W.rows_total == rows_total) return SS_OK;
+  W.rows_total = rows_total;
+  SS_TRY(W.xrec.alloc(2 * rows_total));
+  SS_TRY(W.prec64.alloc(2 * rows_total));
+  SS_TRY(W.prec32.alloc(rows_total));
+  SS_TRY(W.r.alloc(rows_total));
+  SS_TRY(W.z.alloc(rows_total));
+  SS_TRY(W.q64.alloc(rows_total));
+  SS_TRY(W.q32.alloc(rows_total));
+  SS_TRY(W.rhat.alloc(rows_total));
+  SS_TRY(W.dlt.alloc(rows_total));
+  SS_TRY(W.bar.alloc(2));
+  SS_TRY(W.counters.alloc(4));
+  SS_TRY(W.err.alloc(1));
+  k_init_solve_records<<<nblk(rows_total), 256, 0, st>>>(norm, rows_total, W.xrec.get(), W.prec64.get(),
+                                                        W.prec32.get());
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
+ss_status work_upload(SolveWork& W, const SolvePlan& plan, cudaStream_t st) {
+  const int n_inst = (int)plan.inst.size(), n_chunk = (int)plan.chunk.size();
+  if (n_inst > W.cap_inst) { SS_TRY(W.inst.alloc(n_inst)); SS_TRY(W.state.alloc(n_inst)); W.cap_inst = n_inst; }
+  if (n_chunk > W.cap_chunk) { SS_TRY(W.chunk.alloc(n_chunk)); W.cap_chunk = n_chunk; }
+  if (plan.n_parts > W.cap_parts) { SS_TRY(W.part.alloc(plan.n_parts * kNQ)); W.cap_parts = plan.n_parts; }
+  SS_CUDA(cudaMemcpyAsync(W.inst.get(), plan.inst.data(), n_inst * sizeof(SolveInst), cudaMemcpyHostToDevice, st));
+  SS_CUDA(cudaMemcpyAsync(W.chunk.get(), plan.chunk.data(), n_chunk * sizeof(Chunk), cudaMemcpyHostToDevice, st));
+  return SS_OK;
+}
+
+ss_status max_grid(int mode, int block, int* grid) {
+  int nb = 0;
+  if (mode == 0) SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<0>, block, 0));
+  else SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<1>, block, 0));
+  if (nb < 1) SS_FAIL(SS_ERR_CUDA, "solve: kernel does not fit on an SM with %d threads", block);
+  *grid = nb * sm_count();
+  return SS_OK;
+}
+
+// Fill params and launch (capturable: no host synchronisation).
+ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, const int32_t* slice_inst,
+                              const int32_t* norm, const double2* ca64, const float2* ca32, const int32_t* pn,
+                              double tol, int max_iter, ss_precision prec, cudaStream_t st) {
+  SolveParams P{};
+  P.n_inst = (int)plan.inst.size();
+  P.n_chunks = (int)plan.chunk.size();
+  P.inst = W.inst.get();
+  P.chunk = W.chunk.get();
+  P.state = W.state.get();
+  P.op = op;
+  P.slice_inst = slice_inst;
+  P.norm = norm;
+  P.ca64 = ca64;
+  P.ca32 = ca32;
+  P.pn = pn;
+  P.xrec = W.xrec.get();
+  P.prec64 = W.prec64.get();
+  P.prec32 = W.prec32.get();
+  P.r = W.r.get();
+  P.z = W.z.get();
+  P.q64 = W.q64.get();
+  P.q32 = W.q32.get();
+  P.rhat = W.rhat.get();
+  P.dlt = W.dlt.get();
+  P.part = W.part.get();
+  P.bar = W.bar.get();
+  P.counters = W.counters.get();
+  P.err = W.err.get();
+  P.tol = tol;
+  P.inner_tol = 1e-5;
+  P.max_iter = max_iter;
+  P.max_inner = std::max(1, std::min(max_iter, 200));
+  P.max_outer = std::max(1, max_iter);
+  P.spin_limit = 2000000000ll;   // 2 s
+  SS_CUDA(cudaMemsetAsync(W.bar.get(), 0, 2 * sizeof(unsigned), st));
+  SS_CUDA(cudaMemsetAsync(W.counters.get(), 0, 4 * sizeof(int), st));
+  SS_CUDA(cudaMemsetAsync(W.err.get(), 0, sizeof(int), st));
+  SS_CUDA(cudaMemsetAsync(W.state.get(), 0, plan.inst.size() * sizeof(InstState), st));
+  // cooperative launch: all blocks co-resident (required by the grid barrier);
+  // expressed as a launch attribute so that it can be captured in a graph
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(plan.grid);
+  cfg.blockDim = dim3(plan.block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (prec == SS_FP64) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<0>, P));
+  else SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<1>, P));
+  return SS_OK;
+}
+
+ss_status read_stats(SolveWork& W, int n_inst, ss_solve_stats* stats, ss_status* worst, cudaStream_t st) {
+  std::vector<InstState> hs(n_inst);
+  int herr = 0;
+  SS_CUDA(cudaMemcpyAsync(hs.data(), W.state.get(), n_inst * sizeof(InstState), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaMemcpyAsync(&herr, W.err.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  *worst = SS_OK;
+  if (herr) {
+    *worst = (ss_status)herr;
+    set_error("solve: a device-side wait gave up (status %d)", herr);
+  }
+  for (int i = 0; i < n_inst; ++i) {
+    const InstState& s = hs[i];
+    if (stats) {
+      stats[i].status = herr ? herr : s.status;
+      stats[i].outer_iters = s.outer_iters;
+      stats[i].inner_iters = s.inner_iters ? s.inner_iters : s.iters;
+      stats[i].applies = s.applies;
+      stats[i].rel_residual = s.bb > 0 ? std::sqrt(s.rr / s.bb) : 0.0;
+    }
+    if (*worst == SS_OK && s.status != SS_OK) {
+      *worst = (ss_status)s.status;
+      set_error("solve: instance %d did not converge (relative residual %.3e)", i,
+                s.bb > 0 ? std::sqrt(s.rr / s.bb) : 0.0);
+    }
+  }
+  return SS_OK;
+}
+
+}  // namespace ss
+
+// ------------------------------------------------------- per-stamp solve state
+
+struct ss_solve_ctx {
+  ss::SolveWork work;
+  ss::SolvePlan plan;
+  int planned_mode = -1;
+};
+
+namespace ss {
+
+static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream_t st) {
+  if (C.planned_mode == mode) return SS_OK;
+  std::vector<int32_t> woff(s->n_slices + 1);
+  SS_CUDA(cudaMemcpyAsync(woff.data(), s->slice_off.get(), woff.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  C.plan.inst.assign(1, SolveInst{});
+  SolveInst& in = C.plan.inst[0];
+  in.row0 = 0;
+  in.rows = s->size;
+  in.rows_pad = s->rows_pad;
+  in.zero_row = s->zero_idx;
+  in.coef_off = 0;
+  in.dscale = 2.0 * kTwoPiSq * s->a0;   // 4 pi^2 Re(a_hat_0)
+  int grid = 0;
+  C.plan.block = 256;
+  SS_TRY(max_grid(mode, C.plan.block, &grid));
+  const int by_size = (int)std::max<int64_t>(1, s->n_slices / 8);   // at least 8 slices per chunk
+  const int target = std::min(grid, by_size);
+  SS_TRY(plan_chunks(C.plan, woff, {}, target));
+  C.plan.grid = std::min<int>(grid, (int)C.plan.chunk.size());
+  SS_TRY(work_alloc(C.work, s->rows_pad + 1, s->norm.get(), st));
+  SS_TRY(work_upload(C.work, C.plan, st));
+  C.planned_mode = mode;
+  return SS_OK;
+}
+
+}  // namespace ss
+
+using namespace ss;
+
+// The per-stamp context lives in a side table keyed by the stamp pointer so
+// that the stamp layout stays independent of the solver.
+#include <mutex>
+#include <unordered_map>
+static std::mutex g_ctx_mu;
+static std::unordered_map<const ss_stamp_s*, ss_solve_ctx*> g_ctx;
+
+namespace ss {
+void drop_solve_ctx(const ss_stamp_s* s) {
+  std::lock_guard<std::mutex> lk(g_ctx_mu);
+  auto it = g_ctx.find(s);
+  if (it != g_ctx.end()) {
+    delete it->second;
+    g_ctx.erase(it);
+  }
+}
+}  // namespace ss
+
+extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, double tol, int32_t max_iter,
+                           ss_precision prec, ss_solve_stats* stats, void* stream) {
+  if (!s || !f_on_S || !u_on_S) SS_FAIL(SS_ERR_INVALID, "solve: null argument");
+  if (!(tol > 0.0) || max_iter < 1) SS_FAIL(SS_ERR_INVALID, "solve: need tol > 0 and max_iter >= 1");
+  if (prec != SS_FP64 && prec != SS_FP32) SS_FAIL(SS_ERR_INVALID, "solve: bad precision");
+  cudaStream_t st = as_stream(stream);
+  if (s->zero_idx >= 0) {
+    double2 f0;
+    SS_CUDA(cudaMemcpyAsync(&f0, reinterpret_cast<const double2*>(f_on_S) + s->zero_idx, sizeof(f0),
+                            cudaMemcpyDeviceToHost, st));
+    SS_CUDA(cudaStreamSynchronize(st));
+    if (f0.x != 0.0 || f0.y != 0.0) SS_FAIL(SS_ERR_INVALID, "solve: f_hat_0 must be 0 (mean-zero forcing)");
+  }
+  ss_solve_ctx* C;
+  {
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    auto& slot = g_ctx[s];
+    if (!slot) slot = new ss_solve_ctx();
+    C = slot;
+  }
+  const int mode = prec == SS_FP64 ? 0 : 1;
+  SS_TRY(stamp_plan(s, *C, mode, st));
+  C->plan.inst[0].f = reinterpret_cast<const double2*>(f_on_S);
+  C->plan.inst[0].u = reinterpret_cast<double2*>(u_on_S);
+  SS_TRY(work_upload(C->work, C->plan, st));
+  OpView op;
+  op.woff = s->slice_off.get();
+  op.ent = s->ent.get();
+  op.colbits = colbits_of(s->jbits);
+  op.colmask = colmask_of(s->jbits);
+  SS_TRY(launch_solve(C->work, C->plan, op, nullptr, s->norm.get(), s->ca64.get(), s->ca32.get(), s->pnorm.get(), tol,
+                      max_iter, prec, st));
+  ss_status worst;
+  ss_solve_stats one{};
+  SS_TRY(read_stats(C->work, 1, &one, &worst, st));
+  if (stats) *stats = one;
+  return worst;
+}

@@ -1,0 +1,98 @@
+// Persistent CG / iterative-refinement solver shared by solve and batch_solve.
+#pragma once
+
+#include "apply.cuh"
+
+namespace ss {
+
+constexpr int kNQ = 4;        // partial-sum quantities per slot
+constexpr int kMaxInstPerChunk = 32;
+constexpr int kMaxWarps = 16;
+
+struct SolveInst {
+  int64_t row0, rows, rows_pad, zero_row;
+  int32_t coef_off, c_first, c_last, part_base;
+  double dscale;            // 4 pi^2 Re(a_hat_0)
+  const double2* f;         // caller input, rows entries
+  double2* u;               // caller output, rows entries
+};
+
+struct Chunk {
+  int64_t s0, s1;           // global slice range [s0, s1)
+  int32_t inst0, inst1;     // instances touched, inclusive
+};
+
+struct InstState {
+  double rho[2];
+  double bb;                // ||f||^2
+  double rr;                // last residual^2 (FP64 at exit)
+  int32_t act[2];           // by iteration parity: CG (FP64) / refinement (FP32) running
+  int32_t inn[2];           // by inner-iteration parity: inner CG running (FP32 mode)
+  int32_t iters, inner_iters, outer_iters, applies, status, pad_;
+};
+
+struct SolveParams {
+  int n_inst, n_chunks;
+  const SolveInst* inst;
+  const Chunk* chunk;
+  InstState* state;
+  OpView op;
+  const int32_t* slice_inst;   // null for a single instance
+  const int32_t* norm;
+  const double2* ca64;
+  const float2* ca32;
+  const int32_t* pn;
+  double2* xrec;               // FP64 records (value, norm) of x
+  double2* prec64;             // FP64 records of p
+  float4* prec32;              // FP32 records of p
+  double2* r;
+  double2* z;
+  double2* q64;
+  float2* q32;
+  double2* rhat;
+  double2* dlt;
+  double* part;                // [slots][kNQ]
+  unsigned* bar;               // barrier count, generation
+  int* counters;               // done, inner started, inner finished
+  int* err;
+  double tol, inner_tol;
+  int max_iter, max_inner, max_outer;
+  long long spin_limit;
+};
+
+// Host-side plan of the static work split.
+struct SolvePlan {
+  std::vector<SolveInst> inst;
+  std::vector<Chunk> chunk;
+  int64_t n_parts = 0;
+  int grid = 0, block = 256;
+};
+
+// Device workspace of one solve context (single stamp or batch).
+struct SolveWork {
+  int64_t rows_total = 0;   // padded rows, plus one dummy record
+  DevBuf<double2> xrec, prec64, r, z, q64, rhat, dlt;
+  DevBuf<float4> prec32;
+  DevBuf<float2> q32;
+  DevBuf<double> part;
+  DevBuf<unsigned> bar;
+  DevBuf<int> counters, err;
+  DevBuf<InstState> state;
+  DevBuf<SolveInst> inst;
+  DevBuf<Chunk> chunk;
+  int64_t cap_parts = 0;
+  int cap_inst = 0, cap_chunk = 0;
+};
+
+ss_status work_alloc(SolveWork& W, int64_t rows_total, const int32_t* norm, cudaStream_t st);
+ss_status work_upload(SolveWork& W, const SolvePlan& plan, cudaStream_t st);
+ss_status max_grid(int mode, int block, int* grid);
+ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, const int32_t* slice_inst,
+                       const int32_t* norm, const double2* ca64, const float2* ca32, const int32_t* pn,
+                       double tol, int max_iter, ss_precision prec, cudaStream_t st);
+ss_status read_stats(SolveWork& W, int n_inst, ss_solve_stats* stats, ss_status* worst, cudaStream_t st);
+
+ss_status plan_chunks(SolvePlan& plan, const std::vector<int32_t>& woff_host, const std::vector<int32_t>& slice_inst_host,
+                      int target_chunks);
+
+}  // namespace ss

@@ -1,0 +1,182 @@
+// Internal declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/sparse_spectral.h"
+
+namespace ss {
+
+// ----------------------------------------------------------------- errors
+
+void set_error(const char* fmt, ...);
+
+#define SS_CUDA(call)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      ss::set_error("%s:%d: %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+      return e_ == cudaErrorMemoryAllocation ? SS_ERR_OOM : SS_ERR_CUDA;                 \
+    }                                                                                    \
+  } while (0)
+
+#define SS_TRY(call)                  \
+  do {                                \
+    ss_status s_ = (call);            \
+    if (s_ != SS_OK) return s_;       \
+  } while (0)
+
+#define SS_FAIL(code, ...)            \
+  do {                                \
+    ss::set_error(__VA_ARGS__);       \
+    return code;                      \
+  } while (0)
+
+#define SS_LAUNCH_CHECK() SS_CUDA(cudaGetLastError())
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ----------------------------------------------------------- device memory
+
+// Owning device buffer (cudaMalloc / cudaFree).
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  ss_status alloc(size_t count) {
+    release();
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+      return SS_ERR_OOM;
+    }
+    n = count;
+    return SS_OK;
+  }
+  ss_status ensure(size_t count) { return count <= n ? SS_OK : alloc(count); }
+  T* get() const { return p; }
+};
+
+// ------------------------------------------------------------ constants
+
+constexpr double kTwoPiSq = 19.739208802178716;   // 2 pi^2 (half of the 4 pi^2 in eq. GF)
+constexpr uint64_t kEmpty = ~0ull;                // unused hash slot
+constexpr uint64_t kPending = 1ull << 62;         // slot claimed during the current level
+constexpr int kMaxWords = 16;                     // packed key words supported
+constexpr int kSlice = 32;                        // rows per neighbour-table slice (one warp)
+
+// Packed frequency keys.  Coordinate c sits in word c / fpw at bit offset
+// 64 - fb*(c % fpw + 1) (first coordinate most significant) as k_c + 2^(b-1)
+// in b bits below one zero guard bit (fb = b + 1).  Unsigned comparison of the
+// words in order is signed lexicographic order of the frequencies, and adding
+// two packed keys and subtracting the packed bias adds the frequencies field
+// by field without carries as long as every result lies in range.
+struct KeyLayout {
+  int d = 0, W = 0, WT = 1, b = 0, fb = 0, fpw = 0;
+};
+
+// ---------------------------------------------------------- stamp handle
+
+}  // namespace ss
+
+struct ss_stamp_s {
+  // layout
+  int d = 0, N = 0, s_a = 0, j0 = 0, jbits = 0;
+  ss::KeyLayout key;
+  int64_t size = 0, rows_pad = 0, nnz = 0, zero_idx = -1, n_slices = 0, n_ent = 0;
+  std::vector<int64_t> level_start;   // N + 2 entries
+  double a0 = 0.0;                    // Re(a_hat_0)
+  int max_norm = 0;                   // max |k|^2 over S (and |p|^2)
+  // set
+  ss::DevBuf<uint64_t> keys;          // [size][WT]
+  ss::DevBuf<int8_t> level;           // [size]
+  ss::DevBuf<int32_t> norm;           // [rows_pad + 1] |k|^2 (0 on padding and the dummy row)
+  ss::DevBuf<uint64_t> table;         // open-addressing slots
+  int64_t cap = 0;
+  // coefficient data in canonical step order (supp a_hat sorted lexicographically)
+  ss::DevBuf<int32_t> afreq;          // [s_a][d]
+  ss::DevBuf<uint64_t> stepkey;       // [s_a][WT] packed p_j
+  ss::DevBuf<int32_t> pnorm;          // [s_a] |p_j|^2
+  ss::DevBuf<double2> aval;           // [s_a] a_hat_j
+  ss::DevBuf<double2> ca64;           // [s_a] 2 pi^2 a_hat_j
+  ss::DevBuf<float2> ca32;            // [s_a] same in FP32
+  // neighbour table, sliced ELL with 32-row slices, column-major in a slice
+  ss::DevBuf<int32_t> slice_off;      // [n_slices + 1], in entries (multiple of 32)
+  ss::DevBuf<uint32_t> ent;           // [n_ent] col | (j << colbits)
+  // scratch for galerkin_apply
+  ss::DevBuf<float4> rec32;           // [rows_pad + 1]
+  ss::DevBuf<double2> rec64;          // [2 * (rows_pad + 1)] (value, norm|pad) pairs
+};
+
+namespace ss {
+
+// ------------------------------------------------------------- shared API
+
+// Exclusive prefix sum of n int32 values into out (may alias in), total into
+// *d_total (device); scratch is library-managed per call.
+ss_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int64_t* d_total,
+                             cudaStream_t st);
+
+// Neighbour-entry encoding.
+__host__ __device__ inline uint32_t colmask_of(int jbits) { return (jbits >= 32) ? 0u : (0xffffffffu >> jbits); }
+__host__ __device__ inline int colbits_of(int jbits) { return 32 - jbits; }
+
+// Apply launchers used by galerkin_apply and the solver (apply.cu).
+ss_status launch_pack64(const ss_stamp_s* s, const double2* u, cudaStream_t st);
+ss_status launch_pack32(const ss_stamp_s* s, const float2* u, cudaStream_t st);
+ss_status launch_apply64(const ss_stamp_s* s, double2* y, cudaStream_t st);
+ss_status launch_apply32(const ss_stamp_s* s, float2* y, cudaStream_t st);
+
+int sm_count();
+
+// Releases the solver workspace cached for a stamp (solve.cu).
+void drop_solve_ctx(const ss_stamp_s* s);
+
+}  // namespace ss
+
+// -------------------------------------------------------- device helpers
+
+namespace ss {
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  // finaliser of MurmurHash3 (public domain)
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return x;
+}
+
+template <int WT>
+__device__ __forceinline__ uint64_t hash_key(const uint64_t* k) {
+  uint64_t h = 0x9e3779b97f4a7c15ull;
+#pragma unroll
+  for (int w = 0; w < WT; ++w) h = mix64(h ^ (k[w] + 0x632be59bd9b4e019ull * (w + 1)));
+  return h;
+}
+
+template <int WT>
+__device__ __forceinline__ bool key_eq(const uint64_t* a, const uint64_t* b) {
+  bool eq = true;
+#pragma unroll
+  for (int w = 0; w < WT; ++w) eq &= (a[w] == b[w]);
+  return eq;
+}
+
+}  // namespace ss

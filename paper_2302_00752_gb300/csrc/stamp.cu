@@ -1,0 +1,647 @@
+// Stamping set S^N[a_hat](F) (eq. StampSet) built level by level on the GPU,
+// and the sliced-ELL neighbour table of the Galerkin operator.
+//
+// Level n is S^{n-1} + supp(a_hat) minus S^{n-1}.  Candidate c = (parent,
+// step j) of level n gets the discovery key c = (parent - start) * s_a + j.
+// Every candidate probes the open-addressing table: a slot holding a
+// canonical index from an earlier level with the same key drops the
+// candidate; an empty slot is claimed with kPending | c; a pending slot with
+// the same key takes atomicMin(kPending | c).  After the pass, the winner of
+// every new frequency is the candidate with the smallest discovery key, and a
+// prefix sum over the winners in discovery order gives the canonical order
+// (first discovery over parents in index order and steps in lexicographic
+// order).  Keys of pending slots are never stored: they are re-derived from
+// the parent key and the step, so a claim is one 64-bit CAS.
+#include <algorithm>
+#include <cmath>
+
+#include "keys.cuh"
+
+namespace ss {
+namespace {
+
+struct PrepOut {
+  int32_t maxabs_f, maxabs_a;
+  int32_t dup_f, dup_a;
+  int32_t bad_sym, zero_in_f, bad_herm, j0;
+  double a0_re, a0_abs, off_l1, amax;
+};
+
+__device__ int lexcmp(const int32_t* a, const int32_t* b, int d) {
+  for (int c = 0; c < d; ++c) {
+    if (a[c] != b[c]) return a[c] < b[c] ? -1 : 1;
+  }
+  return 0;
+}
+
+// Stable lexicographic rank of every row; flags duplicates.
+__global__ void k_lex_rank(const int32_t* __restrict__ f, int64_t n, int d, int32_t* rank, int32_t* dup) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t r = 0;
+  bool du = false;
+  for (int64_t j = 0; j < n; ++j) {
+    const int c = lexcmp(f + j * d, f + i * d, d);
+    if (c < 0 || (c == 0 && j < i)) ++r;
+    if (c == 0 && j != i) du = true;
+  }
+  rank[i] = r;
+  if (du) atomicExch(dup, 1);
+}
+
+__global__ void k_scatter_rows(const int32_t* __restrict__ f, const double2* __restrict__ v, int64_t n, int d,
+                               const int32_t* __restrict__ rank, int32_t* fo, double2* vo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t r = rank[i];
+  for (int c = 0; c < d; ++c) fo[r * d + c] = f[i * d + c];
+  if (v) vo[r] = v[i];
+}
+
+// One block: ranges, symmetry of supp a_hat (a sorted symmetric set satisfies
+// A[j] = -A[s-1-j]), the zero step, Hermitian values, positivity check.
+__global__ void k_prep(const int32_t* __restrict__ F, int64_t n_f, const int32_t* __restrict__ A,
+                       const double2* __restrict__ av, int s_a, int d, PrepOut* out) {
+  __shared__ int32_t s_maxf, s_maxa, s_zf;
+  if (threadIdx.x == 0) { s_maxf = 0; s_maxa = 0; s_zf = 0; }
+  __syncthreads();
+  int32_t mf = 0;
+  for (int64_t i = threadIdx.x; i < n_f; i += blockDim.x) {
+    bool zero = true;
+    for (int c = 0; c < d; ++c) {
+      const int32_t x = F[i * d + c];
+      mf = max(mf, abs(x));
+      zero &= (x == 0);
+    }
+    if (zero) atomicExch(&s_zf, 1);
+  }
+  atomicMax(&s_maxf, mf);
+  int32_t ma = 0;
+  for (int64_t i = threadIdx.x; i < (int64_t)s_a * d; i += blockDim.x) ma = max(ma, abs(A[i]));
+  atomicMax(&s_maxa, ma);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    out->maxabs_f = s_maxf;
+    out->maxabs_a = s_maxa;
+    out->zero_in_f = s_zf;
+    int bad_sym = (s_a % 2 == 0);
+    int bad_herm = 0;
+    const int j0 = (s_a - 1) / 2;
+    double amax = 0, off = 0;
+    for (int j = 0; j < s_a; ++j) amax = fmax(amax, hypot(av[j].x, av[j].y));
+    for (int j = 0; j < s_a && !bad_sym; ++j) {
+      const int m = s_a - 1 - j;
+      for (int c = 0; c < d; ++c)
+        if (A[j * d + c] != -A[m * d + c]) bad_sym = 1;
+      if (fabs(av[j].x - av[m].x) > 1e-12 * amax || fabs(av[j].y + av[m].y) > 1e-12 * amax) bad_herm = 1;
+      if (j != j0) off += hypot(av[j].x, av[j].y);
+    }
+    if (!bad_sym)
+      for (int c = 0; c < d; ++c)
+        if (A[j0 * d + c] != 0) bad_sym = 1;
+    out->bad_sym = bad_sym;
+    out->bad_herm = bad_herm;
+    out->j0 = j0;
+    out->a0_re = bad_sym ? 0.0 : av[j0].x;
+    out->a0_abs = bad_sym ? 0.0 : hypot(av[j0].x, av[j0].y);
+    out->off_l1 = off;
+    out->amax = amax;
+  }
+}
+
+template <int WT>
+__global__ void k_steps(KeyParams P, const int32_t* __restrict__ A, const double2* __restrict__ av, int s_a,
+                        uint64_t* stepkey, int32_t* pnorm, double2* ca64, float2* ca32) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= s_a) return;
+  uint64_t k[WT];
+  pack_key<WT>(A + (int64_t)j * P.d, P, k);
+#pragma unroll
+  for (int w = 0; w < WT; ++w) stepkey[(int64_t)j * WT + w] = k[w];
+  int32_t s = 0;
+  for (int c = 0; c < P.d; ++c) s += A[(int64_t)j * P.d + c] * A[(int64_t)j * P.d + c];
+  pnorm[j] = s;
+  const double2 a = av[j];
+  ca64[j] = make_double2(kTwoPiSq * a.x, kTwoPiSq * a.y);
+  ca32[j] = make_float2((float)(kTwoPiSq * a.x), (float)(kTwoPiSq * a.y));
+}
+
+// Insert a finalised key with value idx (no duplicates present).
+template <int WT>
+__device__ bool table_insert_final(uint64_t* table, uint64_t capmask, const uint64_t* k, uint64_t idx) {
+  uint64_t h = hash_key<WT>(k) & capmask;
+  for (uint64_t probe = 0; probe <= capmask; ++probe) {
+    const uint64_t old = atomicCAS((unsigned long long*)(table + h), (unsigned long long)kEmpty,
+                                   (unsigned long long)idx);
+    if (old == kEmpty) return true;
+    h = (h + 1) & capmask;
+  }
+  return false;
+}
+
+template <int WT>
+__global__ void k_level0(KeyParams P, const int32_t* __restrict__ F, int64_t n_f, uint64_t* keys, int8_t* level,
+                         int32_t* norm, uint64_t* table, uint64_t capmask, int32_t* err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_f) return;
+  uint64_t k[WT];
+  pack_key<WT>(F + i * P.d, P, k);
+#pragma unroll
+  for (int w = 0; w < WT; ++w) keys[i * WT + w] = k[w];
+  level[i] = 0;
+  norm[i] = key_norm<WT>(k, P);
+  if (!table_insert_final<WT>(table, capmask, k, (uint64_t)i)) atomicExch(err, SS_ERR_HASH_FULL);
+}
+
+template <int WT>
+__global__ void k_rehash(const uint64_t* __restrict__ keys, int64_t size, uint64_t* table, uint64_t capmask,
+                         int32_t* err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= size) return;
+  uint64_t k[WT];
+  load_key<WT>(keys, i, k);
+  if (!table_insert_final<WT>(table, capmask, k, (uint64_t)i)) atomicExch(err, SS_ERR_HASH_FULL);
+}
+
+// Candidate pass of one level (see the file comment).
+template <int WT>
+__global__ void k_insert(KeyParams P, const uint64_t* __restrict__ keys, int64_t par0, int64_t n_par, int s_a,
+                         int j0, const uint64_t* __restrict__ stepkey, uint64_t* table, uint64_t capmask,
+                         int64_t* slot_of, int32_t* err) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_par * s_a) return;
+  const int64_t par = c / s_a;
+  const int j = (int)(c - par * s_a);
+  if (j == j0) { slot_of[c] = -1; return; }
+  uint64_t pk[WT], sk[WT], ck[WT];
+  load_key<WT>(keys, par0 + par, pk);
+  load_key<WT>(stepkey, j, sk);
+  add_keys<WT>(pk, sk, P, ck);
+  const uint64_t mine = kPending | (uint64_t)c;
+  uint64_t h = hash_key<WT>(ck) & capmask;
+  for (uint64_t probe = 0; probe <= capmask; ++probe) {
+    uint64_t v = __ldcg((const unsigned long long*)(table + h));
+    if (v == kEmpty) {
+      const uint64_t old = atomicCAS((unsigned long long*)(table + h), (unsigned long long)kEmpty,
+                                     (unsigned long long)mine);
+      if (old == kEmpty) { slot_of[c] = (int64_t)h; return; }
+      v = old;
+    }
+    uint64_t ok[WT];
+    if (v & kPending) {
+      const int64_t oc = (int64_t)(v & ~kPending);
+      const int64_t opar = oc / s_a;
+      const int oj = (int)(oc - opar * s_a);
+      uint64_t opk[WT], osk[WT];
+      load_key<WT>(keys, par0 + opar, opk);
+      load_key<WT>(stepkey, oj, osk);
+      add_keys<WT>(opk, osk, P, ok);
+      if (key_eq<WT>(ok, ck)) {
+        atomicMin((unsigned long long*)(table + h), (unsigned long long)mine);
+        slot_of[c] = (int64_t)h;
+        return;
+      }
+    } else {
+      load_key<WT>(keys, (int64_t)v, ok);
+      if (key_eq<WT>(ok, ck)) { slot_of[c] = -1; return; }
+    }
+    h = (h + 1) & capmask;
+  }
+  atomicExch(err, SS_ERR_HASH_FULL);
+  slot_of[c] = -1;
+}
+
+__global__ void k_winner_flags(const int64_t* __restrict__ slot_of, const uint64_t* __restrict__ table,
+                               int64_t n, int32_t* flag) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int64_t s = slot_of[c];
+  flag[c] = (s >= 0 && __ldg(table + s) == (kPending | (uint64_t)c)) ? 1 : 0;
+}
+
+template <int WT>
+__global__ void k_finalize(KeyParams P, uint64_t* keys, int64_t par0, int s_a, const uint64_t* __restrict__ stepkey,
+                           const int64_t* __restrict__ slot_of, const int32_t* __restrict__ flag,
+                           const int32_t* __restrict__ pos, int64_t n, int64_t base, int lvl, int8_t* level,
+                           int32_t* norm, uint64_t* table, int64_t* zero_idx) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n || !flag[c]) return;
+  const int64_t par = c / s_a;
+  const int j = (int)(c - par * s_a);
+  uint64_t pk[WT], sk[WT], ck[WT];
+  load_key<WT>(keys, par0 + par, pk);
+  load_key<WT>(stepkey, j, sk);
+  add_keys<WT>(pk, sk, P, ck);
+  const int64_t idx = base + pos[c];
+#pragma unroll
+  for (int w = 0; w < WT; ++w) keys[idx * WT + w] = ck[w];
+  level[idx] = (int8_t)lvl;
+  const int32_t nr = key_norm<WT>(ck, P);
+  norm[idx] = nr;
+  if (nr == 0) *zero_idx = idx;
+  table[slot_of[c]] = (uint64_t)idx;
+}
+
+// Neighbour lookups: nbr[i*s_a + j] = index of k_i - p_j (= k_i + p_{s_a-1-j})
+// when it lies in S, is not 0, and k_i is not 0; else -1.
+template <int WT>
+__global__ void k_neighbors(KeyParams P, const uint64_t* __restrict__ keys, int64_t size, int s_a,
+                            const uint64_t* __restrict__ stepkey, const uint64_t* __restrict__ table,
+                            uint64_t capmask, int64_t zero_idx, int32_t* nbr) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= size * s_a) return;
+  const int64_t i = c / s_a;
+  const int j = (int)(c - i * s_a);
+  int32_t out = -1;
+  if (i != zero_idx) {
+    uint64_t k[WT], sk[WT], l[WT];
+    load_key<WT>(keys, i, k);
+    load_key<WT>(stepkey, s_a - 1 - j, sk);
+    add_keys<WT>(k, sk, P, l);
+    const int64_t v = table_find<WT>(table, capmask, keys, l);
+    if (v >= 0 && v != zero_idx) out = (int32_t)v;
+  }
+  nbr[c] = out;
+}
+
+// Per-row counts, per-slice widths (max over the slice's 32 rows), nnz.
+__global__ void k_row_counts(const int32_t* __restrict__ nbr, int64_t size, int64_t rows_pad, int s_a,
+                             int32_t* slice_w, unsigned long long* nnz) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows_pad) return;
+  int32_t cnt = 0;
+  if (i < size)
+    for (int j = 0; j < s_a; ++j) cnt += (nbr[i * s_a + j] >= 0);
+  const int32_t w = __reduce_max_sync(0xffffffffu, cnt);
+  const unsigned long long tot = __reduce_add_sync(0xffffffffu, (unsigned)cnt);
+  if ((threadIdx.x & 31) == 0) {
+    slice_w[i / kSlice] = w;
+    atomicAdd(nnz, tot);
+  }
+}
+
+__global__ void k_fill_slices(const int32_t* __restrict__ nbr, int64_t size, int64_t rows_pad, int s_a, int j0,
+                              const int32_t* __restrict__ woff, int colbits, uint32_t* ent) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows_pad) return;
+  const int64_t s = i / kSlice;
+  const int lane = (int)(i % kSlice);
+  const int64_t base = (int64_t)woff[s] * kSlice + lane;
+  const int w = woff[s + 1] - woff[s];
+  int t = 0;
+  if (i < size)
+    for (int j = 0; j < s_a; ++j) {
+      const int32_t v = nbr[i * s_a + j];
+      if (v >= 0) ent[base + (int64_t)t++ * kSlice] = (uint32_t)v | ((uint32_t)j << colbits);
+    }
+  const uint32_t pad = (uint32_t)rows_pad | ((uint32_t)j0 << colbits);
+  for (; t < w; ++t) ent[base + (int64_t)t * kSlice] = pad;
+}
+
+__global__ void k_init_records(const int32_t* __restrict__ norm, int64_t n, float4* rec32, double2* rec64) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t nr = norm[i];
+  rec32[i] = make_float4(0.f, 0.f, __int_as_float(nr), 0.f);
+  rec64[2 * i] = make_double2(0.0, 0.0);
+  rec64[2 * i + 1] = make_double2(__longlong_as_double((long long)nr), 0.0);
+}
+
+template <int WT>
+__global__ void k_export(KeyParams P, const uint64_t* __restrict__ keys, int64_t size, int32_t* freq) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= size) return;
+  for (int c = 0; c < P.d; ++c) freq[i * P.d + c] = unpack_coord(keys + i * WT, P, c);
+}
+
+template <int WT>
+__global__ void k_lookup(KeyParams P, const uint64_t* __restrict__ keys, const uint64_t* __restrict__ table,
+                         uint64_t capmask, const int32_t* __restrict__ q, int64_t n, int64_t* idx) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t k[WT];
+  int64_t r = -1;
+  if (pack_key<WT>(q + i * P.d, P, k)) r = table_find<WT>(table, capmask, keys, k);
+  idx[i] = r;
+}
+
+__global__ void k_scatter_vals(const int64_t* __restrict__ idx, const double2* __restrict__ v, int64_t n,
+                               double2* out, unsigned long long* outside) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t r = idx[i];
+  if (r >= 0) out[r] = v[i];
+  else atomicAdd(outside, 1ull);
+}
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+uint64_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ build
+
+static ss_status grow_table(ss_stamp_s* S, int64_t need, const KeyParams& P, cudaStream_t st, int32_t* d_err) {
+  const int64_t want = (int64_t)next_pow2((uint64_t)std::max<int64_t>(2 * need, 1024));
+  if (want <= S->cap) return SS_OK;
+  SS_TRY(S->table.alloc(want));
+  S->cap = want;
+  SS_CUDA(cudaMemsetAsync(S->table.get(), 0xff, want * sizeof(uint64_t), st));
+  if (S->size > 0) {
+    SS_DISPATCH_WT(P.WT, (k_rehash<WT><<<nblk(S->size), 256, 0, st>>>(S->keys.get(), S->size, S->table.get(),
+                                                                        (uint64_t)want - 1, d_err)));
+    SS_LAUNCH_CHECK();
+  }
+  return SS_OK;
+}
+
+static ss_status grow_keys(ss_stamp_s* S, int64_t need, cudaStream_t st) {
+  const int WT = S->key.WT;
+  if ((int64_t)S->keys.n >= need * WT) return SS_OK;
+  const int64_t cap = std::max<int64_t>(need, (int64_t)(S->keys.n / WT) * 2);
+  DevBuf<uint64_t> k2;
+  DevBuf<int8_t> l2;
+  DevBuf<int32_t> n2;
+  SS_TRY(k2.alloc(cap * WT));
+  SS_TRY(l2.alloc(cap));
+  SS_TRY(n2.alloc(cap + kSlice + 1));
+  if (S->size > 0) {
+    SS_CUDA(cudaMemcpyAsync(k2.get(), S->keys.get(), S->size * WT * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+    SS_CUDA(cudaMemcpyAsync(l2.get(), S->level.get(), S->size, cudaMemcpyDeviceToDevice, st));
+    SS_CUDA(cudaMemcpyAsync(n2.get(), S->norm.get(), S->size * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  }
+  SS_CUDA(cudaStreamSynchronize(st));
+  std::swap(S->keys.p, k2.p); std::swap(S->keys.n, k2.n);
+  std::swap(S->level.p, l2.p); std::swap(S->level.n, l2.n);
+  std::swap(S->norm.p, n2.p); std::swap(S->norm.n, n2.n);
+  return SS_OK;
+}
+
+static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t* f_freq, int64_t n_f, int N,
+                            cudaStream_t st) {
+  const int d = a_hat->d;
+  const int s_a = (int)a_hat->n;
+  S->d = d;
+  S->N = N;
+  S->s_a = s_a;
+
+  DevBuf<int32_t> Fs, As, rank, scratch_i;
+  DevBuf<double2> avs;
+  DevBuf<PrepOut> prep;
+  DevBuf<int32_t> err;
+  SS_TRY(Fs.alloc(n_f * d));
+  SS_TRY(As.alloc((size_t)s_a * d));
+  SS_TRY(avs.alloc(s_a));
+  SS_TRY(rank.alloc(std::max<int64_t>(n_f, s_a)));
+  SS_TRY(prep.alloc(1));
+  SS_TRY(err.alloc(4));
+  SS_CUDA(cudaMemsetAsync(err.get(), 0, 4 * sizeof(int32_t), st));
+
+  // signed lexicographic order of F and supp a_hat
+  k_lex_rank<<<nblk(n_f), 256, 0, st>>>(f_freq, n_f, d, rank.get(), err.get() + 1);
+  k_scatter_rows<<<nblk(n_f), 256, 0, st>>>(f_freq, nullptr, n_f, d, rank.get(), Fs.get(), nullptr);
+  k_lex_rank<<<nblk(s_a), 256, 0, st>>>(a_hat->freq, s_a, d, rank.get(), err.get() + 2);
+  k_scatter_rows<<<nblk(s_a), 256, 0, st>>>(a_hat->freq, reinterpret_cast<const double2*>(a_hat->val), s_a, d,
+                                            rank.get(), As.get(), avs.get());
+  k_prep<<<1, 256, 0, st>>>(Fs.get(), n_f, As.get(), avs.get(), s_a, d, prep.get());
+  SS_LAUNCH_CHECK();
+  PrepOut h{};
+  int32_t herr[4];
+  SS_CUDA(cudaMemcpyAsync(&h, prep.get(), sizeof(h), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaMemcpyAsync(herr, err.get(), sizeof(herr), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  if (herr[1]) SS_FAIL(SS_ERR_INVALID, "stamp_build: duplicate frequencies in F");
+  if (herr[2]) SS_FAIL(SS_ERR_INVALID, "stamp_build: duplicate frequencies in supp a_hat");
+  if (h.zero_in_f) SS_FAIL(SS_ERR_INVALID, "stamp_build: F contains k = 0 (f_hat_0 must vanish)");
+  if (h.bad_sym) SS_FAIL(SS_ERR_INVALID, "stamp_build: supp a_hat must contain 0 and be closed under negation");
+  if (h.bad_herm) SS_FAIL(SS_ERR_INVALID, "stamp_build: a_hat is not Hermitian (a must be real)");
+  if (!(h.off_l1 < h.a0_abs)) SS_FAIL(SS_ERR_NOT_ELLIPTIC, "stamp_build: ||a_hat - a_hat_0||_1 = %g >= |a_hat_0| = %g",
+                                       h.off_l1, h.a0_abs);
+  if (!(h.a0_re > 0)) SS_FAIL(SS_ERR_NOT_ELLIPTIC, "stamp_build: Re(a_hat_0) must be positive");
+  S->a0 = h.a0_re;
+  S->j0 = h.j0;
+
+  // key layout: every frequency of S^{N+1} must fit (neighbour lookups reach one level further)
+  const int64_t maxabs = (int64_t)h.maxabs_f + (int64_t)(N + 1) * h.maxabs_a;
+  if ((double)d * (double)maxabs * (double)maxabs >= (double)(1 << 29))
+    SS_FAIL(SS_ERR_KEY_RANGE, "stamp_build: |k|^2 may reach %g; integer dot products need < 2^29",
+            (double)d * maxabs * maxabs);
+  int b = 1;
+  while (((int64_t)1 << (b - 1)) - 1 < maxabs) ++b;
+  KeyLayout L;
+  L.d = d;
+  L.b = b;
+  L.fb = b + 1;
+  L.fpw = 64 / L.fb;
+  L.W = (d + L.fpw - 1) / L.fpw;
+  L.WT = 1;
+  while (L.WT < L.W) L.WT <<= 1;
+  if (L.WT > kMaxWords) SS_FAIL(SS_ERR_KEY_RANGE, "stamp_build: key needs %d words (max %d)", L.W, kMaxWords);
+  S->key = L;
+  const KeyParams P = make_key_params(L);
+  int jb = 0;
+  while ((1 << jb) < s_a) ++jb;
+  S->jbits = std::max(jb, 1);
+
+  // steps and coefficients in canonical order
+  SS_TRY(S->afreq.alloc((size_t)s_a * d));
+  SS_CUDA(cudaMemcpyAsync(S->afreq.get(), As.get(), (size_t)s_a * d * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  SS_TRY(S->aval.alloc(s_a));
+  SS_CUDA(cudaMemcpyAsync(S->aval.get(), avs.get(), s_a * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  SS_TRY(S->stepkey.alloc((size_t)s_a * L.WT));
+  SS_TRY(S->pnorm.alloc(s_a));
+  SS_TRY(S->ca64.alloc(s_a));
+  SS_TRY(S->ca32.alloc(s_a));
+  SS_DISPATCH_WT(L.WT, (k_steps<WT><<<nblk(s_a), 256, 0, st>>>(P, As.get(), avs.get(), s_a, S->stepkey.get(),
+                                                               S->pnorm.get(), S->ca64.get(), S->ca32.get())));
+  SS_LAUNCH_CHECK();
+
+  // level 0
+  S->level_start.assign(1, 0);
+  SS_TRY(grow_keys(S, n_f, st));
+  SS_TRY(grow_table(S, n_f, P, st, err.get()));
+  DevBuf<int64_t> zidx;
+  SS_TRY(zidx.alloc(1));
+  SS_CUDA(cudaMemsetAsync(zidx.get(), 0xff, sizeof(int64_t), st));
+  SS_DISPATCH_WT(L.WT, (k_level0<WT><<<nblk(n_f), 256, 0, st>>>(P, Fs.get(), n_f, S->keys.get(), S->level.get(),
+                                                                S->norm.get(), S->table.get(),
+                                                                (uint64_t)S->cap - 1, err.get())));
+  SS_LAUNCH_CHECK();
+  S->size = n_f;
+  S->level_start.push_back(n_f);
+
+  // levels 1..N
+  DevBuf<int64_t> slot_of, d_total;
+  DevBuf<int32_t> flag;
+  SS_TRY(d_total.alloc(1));
+  for (int n = 1; n <= N; ++n) {
+    const int64_t par0 = S->level_start[n - 1], n_par = S->level_start[n] - par0;
+    const int64_t ncand = n_par * s_a;
+    if (ncand > ((int64_t)1 << 40)) SS_FAIL(SS_ERR_KEY_RANGE, "stamp_build: too many candidates at level %d", n);
+    if (ncand == 0) { S->level_start.push_back(S->size); continue; }
+    SS_TRY(grow_table(S, S->size + n_par * (s_a - 1), P, st, err.get()));
+    SS_TRY(grow_keys(S, S->size + n_par * (s_a - 1), st));
+    SS_TRY(slot_of.ensure(ncand));
+    SS_TRY(flag.ensure(ncand));
+    SS_DISPATCH_WT(L.WT, (k_insert<WT><<<nblk(ncand), 256, 0, st>>>(P, S->keys.get(), par0, n_par, s_a, S->j0,
+                                                                    S->stepkey.get(), S->table.get(),
+                                                                    (uint64_t)S->cap - 1, slot_of.get(), err.get())));
+    k_winner_flags<<<nblk(ncand), 256, 0, st>>>(slot_of.get(), S->table.get(), ncand, flag.get());
+    SS_LAUNCH_CHECK();
+    DevBuf<int32_t> pos;
+    SS_TRY(pos.alloc(ncand));
+    SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), ncand, d_total.get(), st));
+    int64_t added = 0;
+    int32_t e = 0;
+    SS_CUDA(cudaMemcpyAsync(&added, d_total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SS_CUDA(cudaMemcpyAsync(&e, err.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SS_CUDA(cudaStreamSynchronize(st));
+    if (e) SS_FAIL((ss_status)e, "stamp_build: hash table exhausted at level %d", n);
+    SS_DISPATCH_WT(L.WT, (k_finalize<WT><<<nblk(ncand), 256, 0, st>>>(P, S->keys.get(), par0, s_a, S->stepkey.get(),
+                                                                      slot_of.get(), flag.get(), pos.get(), ncand,
+                                                                      S->size, n, S->level.get(), S->norm.get(),
+                                                                      S->table.get(), zidx.get())));
+    SS_LAUNCH_CHECK();
+    SS_CUDA(cudaStreamSynchronize(st));
+    S->size += added;
+    S->level_start.push_back(S->size);
+  }
+  SS_CUDA(cudaMemcpyAsync(&S->zero_idx, zidx.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+
+  // neighbour table
+  S->rows_pad = (S->size + kSlice - 1) / kSlice * kSlice;
+  S->n_slices = S->rows_pad / kSlice;
+  if (S->rows_pad + 1 > ((int64_t)1 << colbits_of(S->jbits)))
+    SS_FAIL(SS_ERR_KEY_RANGE, "stamp_build: |S| = %lld too large for %d-bit columns", (long long)S->size,
+            colbits_of(S->jbits));
+  SS_TRY(grow_keys(S, S->rows_pad + 1, st));   // norm padded to rows_pad + 1
+  SS_CUDA(cudaMemsetAsync(S->norm.get() + S->size, 0, (S->rows_pad + 1 - S->size) * sizeof(int32_t), st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  DevBuf<int32_t> nbr, slice_w;
+  DevBuf<unsigned long long> d_nnz;
+  SS_TRY(nbr.alloc((size_t)S->size * s_a));
+  SS_TRY(slice_w.alloc(S->n_slices + 1));
+  SS_TRY(d_nnz.alloc(1));
+  SS_CUDA(cudaMemsetAsync(d_nnz.get(), 0, sizeof(unsigned long long), st));
+  SS_CUDA(cudaMemsetAsync(slice_w.get(), 0, (S->n_slices + 1) * sizeof(int32_t), st));
+  SS_DISPATCH_WT(L.WT, (k_neighbors<WT><<<nblk(S->size * s_a), 256, 0, st>>>(
+                           P, S->keys.get(), S->size, s_a, S->stepkey.get(), S->table.get(), (uint64_t)S->cap - 1,
+                           S->zero_idx, nbr.get())));
+  k_row_counts<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, slice_w.get(), d_nnz.get());
+  SS_LAUNCH_CHECK();
+  SS_TRY(S->slice_off.alloc(S->n_slices + 1));
+  SS_TRY(exclusive_scan_i32(slice_w.get(), S->slice_off.get(), S->n_slices + 1, d_total.get(), st));
+  int64_t total_w = 0;
+  unsigned long long hnnz = 0;
+  SS_CUDA(cudaMemcpyAsync(&total_w, d_total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaMemcpyAsync(&hnnz, d_nnz.get(), sizeof(hnnz), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  S->nnz = (int64_t)hnnz;
+  S->n_ent = total_w * kSlice;
+  SS_TRY(S->ent.alloc(S->n_ent + 1));
+  k_fill_slices<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, S->j0, S->slice_off.get(),
+                                                   colbits_of(S->jbits), S->ent.get());
+  SS_LAUNCH_CHECK();
+  SS_TRY(S->rec32.alloc(S->rows_pad + 1));
+  SS_TRY(S->rec64.alloc(2 * (S->rows_pad + 1)));
+  k_init_records<<<nblk(S->rows_pad + 1), 256, 0, st>>>(S->norm.get(), S->rows_pad + 1, S->rec32.get(),
+                                                        S->rec64.get());
+  SS_LAUNCH_CHECK();
+  int32_t e = 0;
+  SS_CUDA(cudaMemcpyAsync(&e, err.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  if (e) SS_FAIL((ss_status)e, "stamp_build: hash table exhausted");
+  return SS_OK;
+}
+
+}  // namespace ss
+
+using namespace ss;
+
+extern "C" ss_status stamp_build(const ss_sparse* a_hat, const int32_t* f_freq, int64_t n_f, int32_t N, ss_stamp* out,
+                                 void* stream) {
+  if (!a_hat || !out || !f_freq || !a_hat->freq || !a_hat->val)
+    SS_FAIL(SS_ERR_INVALID, "stamp_build: null argument");
+  if (a_hat->d < 1 || a_hat->n < 1 || n_f < 1 || N < 0 || N > 120)
+    SS_FAIL(SS_ERR_INVALID, "stamp_build: need d >= 1, |supp a_hat| >= 1, |F| >= 1, 0 <= N <= 120");
+  if (a_hat->n > 4096) SS_FAIL(SS_ERR_INVALID, "stamp_build: |supp a_hat| > 4096");
+  *out = nullptr;
+  ss_stamp_s* S = new ss_stamp_s();
+  ss_status s = build_impl(S, a_hat, f_freq, n_f, N, as_stream(stream));
+  if (s != SS_OK) {
+    cudaStreamSynchronize(as_stream(stream));
+    delete S;
+    return s;
+  }
+  *out = S;
+  return SS_OK;
+}
+
+extern "C" void stamp_destroy(ss_stamp s) {
+  if (!s) return;
+  cudaDeviceSynchronize();
+  drop_solve_ctx(s);
+  delete s;
+}
+
+extern "C" ss_status stamp_info(ss_stamp s, int64_t* size, int64_t* nnz, int64_t* zero_index, int32_t* n_levels) {
+  if (!s) SS_FAIL(SS_ERR_INVALID, "stamp_info: null stamp");
+  if (size) *size = s->size;
+  if (nnz) *nnz = s->nnz;
+  if (zero_index) *zero_index = s->zero_idx;
+  if (n_levels) *n_levels = s->N + 1;
+  return SS_OK;
+}
+
+extern "C" ss_status stamp_export(ss_stamp s, int32_t* freq_out, int8_t* level_out, void* stream) {
+  if (!s) SS_FAIL(SS_ERR_INVALID, "stamp_export: null stamp");
+  cudaStream_t st = as_stream(stream);
+  if (freq_out) {
+    const KeyParams P = make_key_params(s->key);
+    SS_DISPATCH_WT(s->key.WT, (k_export<WT><<<nblk(s->size), 256, 0, st>>>(P, s->keys.get(), s->size, freq_out)));
+    SS_LAUNCH_CHECK();
+  }
+  if (level_out) SS_CUDA(cudaMemcpyAsync(level_out, s->level.get(), s->size, cudaMemcpyDeviceToDevice, st));
+  return SS_OK;
+}
+
+extern "C" ss_status stamp_lookup(ss_stamp s, const int32_t* freq, int64_t n, int64_t* idx_out, void* stream) {
+  if (!s || (n > 0 && (!freq || !idx_out))) SS_FAIL(SS_ERR_INVALID, "stamp_lookup: null argument");
+  if (n == 0) return SS_OK;
+  const KeyParams P = make_key_params(s->key);
+  cudaStream_t st = as_stream(stream);
+  SS_DISPATCH_WT(s->key.WT, (k_lookup<WT><<<nblk(n), 256, 0, st>>>(P, s->keys.get(), s->table.get(),
+                                                                  (uint64_t)s->cap - 1, freq, n, idx_out)));
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
+extern "C" ss_status stamp_scatter(ss_stamp s, const ss_sparse* g, double* out, int64_t* n_outside, void* stream) {
+  if (!s || !g || !out) SS_FAIL(SS_ERR_INVALID, "stamp_scatter: null argument");
+  if (g->d != s->d) SS_FAIL(SS_ERR_INVALID, "stamp_scatter: dimension %d != %d", g->d, s->d);
+  cudaStream_t st = as_stream(stream);
+  SS_CUDA(cudaMemsetAsync(out, 0, s->size * sizeof(double2), st));
+  if (g->n == 0) {
+    if (n_outside) *n_outside = 0;
+    return SS_OK;
+  }
+  DevBuf<int64_t> idx;
+  DevBuf<unsigned long long> outside;
+  SS_TRY(idx.alloc(g->n));
+  SS_TRY(outside.alloc(1));
+  SS_CUDA(cudaMemsetAsync(outside.get(), 0, sizeof(unsigned long long), st));
+  SS_TRY(stamp_lookup(s, g->freq, g->n, idx.get(), stream));
+  k_scatter_vals<<<nblk(g->n), 256, 0, st>>>(idx.get(), reinterpret_cast<const double2*>(g->val), g->n,
+                                             reinterpret_cast<double2*>(out), outside.get());
+  SS_LAUNCH_CHECK();
+  unsigned long long h = 0;
+  SS_CUDA(cudaMemcpyAsync(&h, outside.get(), sizeof(h), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  if (n_outside) *n_outside = (int64_t)h;
+  return SS_OK;
+}

@@ -1,0 +1,140 @@
+"""Lattice choice, lattice sampling and coefficient recovery against the oracle.
+Integer results (M, z, attempt, residues, kept support) match exactly; FP64
+values within 1e-12 sum|c| (FFT rounding, O(log M) eps), FP32 within 1e-5 sum|c|."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import lattice as olat
+from oracle import pipeline as opipe
+from oracle import sft as osft
+from tests.helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2302_00752_gb300 import binding
+    return binding
+
+
+def test_lattice_check(B):
+    from paper_2302_00752_gb300.binding import SSError
+    g = np.arange(-16, 17)
+    box = np.stack(np.meshgrid(g, g, indexing="ij"), -1).reshape(-1, 2)
+    B.lattice_check([1, 33], 1089, box)
+    with pytest.raises(SSError) as e:
+        B.lattice_check([1, 33], 1089, np.vstack([box, [[17, 0]]]))
+    assert e.value.name == "SS_ERR_NOT_RECONSTRUCTING"
+    with pytest.raises(SSError) as e:
+        B.lattice_check([1, 33], 1089, np.vstack([box, [[3, 3]]]))
+    assert e.value.name == "SS_ERR_INVALID"
+
+
+def test_random_lattice_matches_oracle(B):
+    inst = W.make_cfg3()
+    cand = opipe.candidates(inst, inst.f.freq)
+    z, M, att = olat.random_lattice(cand, inst.lattice)
+    gz, gM, gatt = B.lattice_random(cand, inst.lattice["raw"], inst.lattice["sigma"], inst.lattice["M_min"])
+    assert (gM, gatt) == (M, att) and np.array_equal(gz, z)
+
+
+def test_random_lattice_retries(B):
+    # a deliberately tiny M forces failed attempts; both sides agree on which succeeds
+    rng = np.random.default_rng(4)
+    cand = np.unique(rng.integers(-3, 4, size=(20, 3)), axis=0)
+    draws = {"kind": "random", "raw": rng.integers(0, 2**62, size=(40, 3)), "M_min": 0, "sigma": 1.0}
+    z, M, att = olat.random_lattice(cand, draws)
+    gz, gM, gatt = B.lattice_random(cand, draws["raw"], 1.0, 0)
+    assert (gM, gatt) == (M, att) and np.array_equal(gz, z)
+
+
+def test_cbc_lattice_matches_oracle(B):
+    rng = np.random.default_rng(5)
+    I = np.unique(rng.integers(-8, 9, size=(300, 6)), axis=0)
+    I = np.unique(np.vstack([I, -I]), axis=0)
+    draws = {"raw": rng.integers(0, 2**62, size=(6, 32)), "M_min": 200003}
+    z, M = olat.cbc_lattice(I, draws)
+    gz, gM = B.lattice_cbc(I, draws["raw"], draws["M_min"])
+    assert gM == M and np.array_equal(gz, z)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+def test_sampling_matches_oracle(B, prec, tol):
+    rng = np.random.default_rng(1)
+    d, M = 4, 100003
+    z = rng.integers(1, M, size=d)
+    freq = rng.integers(-30, 31, size=(37, d))
+    coef = rng.standard_normal(37) + 1j * rng.standard_normal(37)
+    g = B.lattice_sample(z, M, freq, coef, prec).double().cpu().numpy()
+    js = np.concatenate([np.arange(0, M, 7), [M - 1]])
+    ref = osft.sample(freq, coef, z, M, js)
+    scale = np.abs(coef).sum()
+    assert np.abs(g[js] - ref).max() <= tol * scale
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_recover_cfg1_matches_oracle(B, prec, tol):
+    inst = W.make_cfg1()
+    z, M = inst.lattice["z"], inst.lattice["M"]
+    samples = osft.sample(inst.a.freq, inst.a.coef, z, M)
+    kf, kv = osft.recover_known(samples, inst.cand, z, M, tau=1e-9 if prec == "fp64" else 1e-4)
+    gf, gv = B.sft_recover(z, M, inst.a.freq, inst.a.coef, inst.cand, tau=1e-9 if prec == "fp64" else 1e-4,
+                           precision=prec)
+    assert np.array_equal(gf.cpu().numpy(), kf)
+    scale = np.abs(inst.a.coef).sum()
+    assert np.abs(gv.cpu().numpy() - kv).max() <= tol * scale
+
+
+def test_recover_closed_form_and_forcing(B):
+    # cfg3: a (cosines) and f (cosines and sines) recovered on the random lattice;
+    # closed form: c/2 at +-p, -i c/2 / +i c/2 for sines, the mean at 0
+    inst = W.make_cfg3()
+    cand = opipe.candidates(inst, inst.f.freq)
+    z, M, _ = olat.random_lattice(cand, inst.lattice)
+    for trig in (inst.a, inst.f):
+        want = osft.true_coefficients(trig.freq, trig.coef)
+        gf, gv = B.sft_recover(z, M, trig.freq, trig.coef, cand, tau=1e-9)
+        got = {tuple(k): v for k, v in zip(gf.cpu().numpy().tolist(), gv.cpu().numpy())}
+        assert set(got) == {k for k, v in want.items() if abs(v) > 0}
+        scale = np.abs(trig.coef).sum()
+        for k, v in got.items():
+            assert abs(v - want[k]) <= 1e-12 * scale
+
+
+def test_recover_from_samples_and_cap(B):
+    from paper_2302_00752_gb300.binding import SSError
+    inst = W.make_cfg1()
+    z, M = inst.lattice["z"], inst.lattice["M"]
+    s = B.lattice_sample(z, M, inst.a.freq, inst.a.coef, "fp64")
+    gf, gv = B.sft_recover_samples(z, M, s, inst.cand, tau=1e-9)
+    assert len(gf) == 9
+    with pytest.raises(SSError):
+        B.sft_recover_samples(z, M, s, inst.cand, s_max=5, tau=1e-9)
+    with pytest.raises(SSError) as e:
+        B.sft_recover_samples(z, M, s, inst.cand[:-1], tau=1e-9)     # not closed under negation
+    assert e.value.name == "SS_ERR_INVALID"
+
+
+def test_recover_cfg5_fp32_sampled(B):
+    # M = smallest prime >= 2^26, FP32 samples and FP32 FFT, d = 100
+    inst = W.make_cfg5()
+    cand = opipe.candidates(inst, inst.f.freq)
+    z, M, att = olat.random_lattice(cand, inst.lattice)
+    gz, gM, gatt = B.lattice_random(cand, inst.lattice["raw"], inst.lattice["sigma"], inst.lattice["M_min"])
+    assert gM == M == 2**26 + 15 and np.array_equal(gz, z)
+    for trig in (inst.a, inst.f):
+        want = osft.true_coefficients(trig.freq, trig.coef)
+        gf, gv = B.sft_recover(z, M, trig.freq, trig.coef, cand, tau=1e-4, precision="fp32")
+        got = {tuple(k): v for k, v in zip(gf.cpu().numpy().tolist(), gv.cpu().numpy())}
+        assert set(got) == {k for k, v in want.items() if abs(v) > 0}
+        scale = np.abs(trig.coef).sum()
+        err = max(abs(v - want[k]) for k, v in got.items())
+        assert err <= 1e-5 * scale, err
+    # a few FP32 samples against the oracle's direct evaluation
+    js = np.array([0, 1, 12345, M // 2, M - 1])
+    g = B.lattice_sample(z, M, inst.a.freq, inst.a.coef, "fp32").double().cpu().numpy()
+    ref = osft.sample(inst.a.freq, inst.a.coef, z, M, js)
+    assert np.abs(g[js] - ref).max() <= 2e-6 * np.abs(inst.a.coef).sum()
