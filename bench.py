@@ -1,0 +1,351 @@
+"""Benchmark of the sparse spectral method's hot path on one GB300 (or N replicas).
+
+Workload (default): the d = 10 plain-FP64 configuration - a with 10 cosines in
+[-8,8]^10 (s_a = 21), manufactured u with 20 +-pairs, f_hat = L[a_hat] u_hat
+(|supp f_hat| = 840), N = 3 (|S| = 334,440, 2.51e6 operator nonzeros), CBC
+lattice with M = 1,000,003.  Synthetic, seeded (workloads.make_cfg2).
+
+One step = the whole path: CBC lattice choice, sft_recover(a), sft_recover(f)
+(lattice sampling + length-M FFT + bin extraction), stamp_build (S^3 and the
+neighbour table), right-hand side on S, FP64 CG solve to 1e-12.
+
+Metric: stamped Galerkin nonzeros per second = nnz(L) x operator applications in
+the step / step time.  Also reported: time to solution of the FP64 and the
+FP32-refined solves (solve only) with their errors against the exact
+(manufactured) solution, per-stage times, the roofline of the dominant kernel,
+and the CPU oracle timed on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+L2_BYTES = 129 * 2**20
+FLUSH_BYTES = 512 * 2**20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in self.rows for n, v in zip(names, r[5:9]) if v.strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------- oracle legs
+
+def oracle_sample(inst):
+    """The CPU oracle on a bounded sample of the workload: its solve path
+    (stamping set by BFS, explicit sparse operator, Jacobi PCG to 1e-12) from
+    the exact coefficients.  The oracle's O(M |I|) DFT recovery is left out."""
+    from oracle import pipeline as op
+    from oracle import solve as osol
+    from oracle import stamp as ostamp
+    from oracle import galerkin as ogal
+    from oracle.sft import true_coefficients
+
+    a = true_coefficients(inst.a.freq, inst.a.coef)
+    af = np.array(list(a.keys()), np.int64)
+    av = np.array(list(a.values()), np.complex128)
+    ff, fv = op.forcing(inst)
+    keep = np.abs(fv) > 0
+    ff, fv = ff[keep], fv[keep]
+    t0 = time.perf_counter()
+    S, _ = ostamp.stamp_bfs(af, ff, inst.N)
+    L, nnz = ogal.galerkin_matrix(S, af, av)
+    b = op.rhs_on(S, ff, fv)
+    u, it, _ = osol.pcg(L, b, osol.jacobi_diag(S, av[~af.any(axis=1)][0]), 1e-12)
+    dt = time.perf_counter() - t0
+    return {"seconds": dt, "nnz": nnz, "applies": it + 1, "value": nnz * (it + 1) / dt}
+
+
+def run_reference(args, inst):
+    world, rank, _ = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            return
+    for _ in range(args.warmup):
+        oracle_sample(inst)
+    tot, work = 0.0, 0.0
+    for _ in range(args.steps):
+        r = oracle_sample(inst)
+        tot += r["seconds"]
+        work += r["nnz"] * r["applies"]
+    value = work / tot
+    line = {
+        "impl": "reference", "metric": "stamped Galerkin nnz/s", "value": value, "unit": "nnz/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "cfg2: d=10 plain FP64, s_a=21, |supp f|=840, N=3, |S|=334440"},
+        "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": 1, "kind": "oracle",
+                         "sample": "oracle solve path (BFS stamping, explicit sparse operator, Jacobi PCG to 1e-12) "
+                                   "on the full workload from exact coefficients; DFT recovery left out"},
+        "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- our path
+
+def main():
+    args = parse()
+    inst = W.make_cfg2()
+    if args.impl == "reference":
+        run_reference(args, inst)
+        return
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2302_00752_gb300 import binding as B
+    from paper_2302_00752_gb300 import pipeline as gp
+
+    dev = torch.device("cuda", local)
+    prep = gp.prepare(inst)                         # manufactured f_hat built by the library (untimed)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(p, keep=False):
+        t = {}
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        ev[0].record()
+        p.z, p.M = gp.choose_lattice(p.extra["lattice"], p.cand)
+        ev[1].record()
+        af, av = B.sft_recover(p.z, p.M, p.a_freq, p.a_coef, p.cand, tau=1e-9, precision="fp64")
+        ff, fv = B.sft_recover(p.z, p.M, p.f_freq, p.f_coef, p.cand, tau=1e-9, precision="fp64")
+        ev[2].record()
+        stamp = B.stamp_build(af, av, ff, inst.N)
+        f_on, _ = stamp.scatter(ff, fv)
+        ev[3].record()
+        u, st = B.solve(stamp, f_on, 1e-12, 1000, "fp64")
+        ev[4].record()
+        ev[4].synchronize()
+        t["lattice"] = ev[0].elapsed_time(ev[1])
+        t["sft"] = ev[1].elapsed_time(ev[2])
+        t["stamp"] = ev[2].elapsed_time(ev[3])
+        t["solve"] = ev[3].elapsed_time(ev[4])
+        t["solve_kernel"] = st["kernel_ms"]
+        out = {"nnz": stamp.nnz, "size": stamp.size, "applies": st["applies"], "iters": st["inner_iters"],
+               "times": t, "u": u, "stats": st}
+        if keep:
+            out["stamp"], out["f_on"] = stamp, f_on
+        else:
+            stamp.destroy()
+        return out
+
+    for _ in range(max(3, args.warmup)):
+        step(prep)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.5)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    step_ms, work, stage = [], 0, {}
+    for _ in range(args.steps):
+        flush.zero_()                               # L2 flushed between steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = step(prep)
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        work += r["nnz"] * r["applies"]
+        for k, v in r["times"].items():
+            stage.setdefault(k, []).append(v)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = world * work / (total_ms / 1e3)
+
+    # solve-only time to solution, FP64 vs FP32-refined, errors against the exact solution
+    keep = step(prep, keep=True)
+    stamp, f_on = keep["stamp"], keep["f_on"]
+    S = stamp.export()[0].cpu().numpy()
+    idx = {tuple(k): i for i, k in enumerate(S.tolist())}
+    exact = np.zeros(len(S), complex)
+    for k, v in zip(inst.u_freq.tolist(), inst.u_val):
+        exact[idx[tuple(k)]] = v
+    tts = {}
+    for prec in ("fp64", "fp32"):
+        times, kern = [], []
+        for _ in range(5):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            u, st = B.solve(stamp, f_on, 1e-12, 1000, prec)
+            b.record()
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+            kern.append(st["kernel_ms"])
+        uu = u.cpu().numpy()
+        err = float(np.linalg.norm(uu - exact) / np.linalg.norm(exact))
+        tts[prec] = {"time_to_solution_ms": statistics.median(times), "kernel_ms": statistics.median(kern),
+                     "rel_l2_err_vs_exact": err, "rel_residual": st["rel_residual"], "applies": st["applies"],
+                     "outer_iters": st["outer_iters"], "inner_iters": st["inner_iters"],
+                     "nnz_per_s": stamp.nnz * st["applies"] / (statistics.median(kern) / 1e3)}
+
+    # end to end through the C ABI with host buffers: H2D of the data, D2H of u
+    host = {k: getattr(prep, k).cpu().pin_memory() for k in ("a_freq", "a_coef", "f_freq", "f_coef", "cand")}
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    u_host = torch.empty(stamp.size, dtype=torch.complex128).pin_memory()
+    d2h = u_host.numel() * u_host.element_size()
+    stamp.destroy()
+    e2e_ms, e2e_work = [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        p2 = gp.Prepared(prep.d, prep.N, *[host[k].to(dev, non_blocking=True) for k in
+                                           ("a_freq", "a_coef", "f_freq", "f_coef", "cand")],
+                         sft_precision="fp64", solve_precision="fp64", extra=prep.extra)
+        r = step(p2)
+        u_host.copy_(r["u"], non_blocking=True)
+        b.record()
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+        e2e_work += r["nnz"] * r["applies"]
+    e2e_value = world * e2e_work / (sum(e2e_ms) / 1e3)
+
+    # roofline of the dominant kernel (see the design doc for the byte/flop model)
+    med = {k: statistics.median(v) for k, v in stage.items()}
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    nnz, size, iters = r["nnz"], r["size"], r["iters"]
+    solve_bytes = iters * (4 * nnz + 212 * size)
+    kms = med["solve_kernel"]
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    achieved = solve_bytes / (kms / 1e3) / 1e9
+    roofline = {"kernel": "k_solve<FP64> (persistent CG)", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        o = oracle_sample(inst)
+        cpu = {"value": o["value"], "unit": "nnz/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle solve path on the full workload from exact coefficients (BFS stamping, explicit "
+                         f"operator, Jacobi PCG to 1e-12: {o['applies']} applies, {o['seconds']:.1f} s); "
+                         f"DFT recovery left out"}
+
+    if rank == 0:
+        line = {
+            "metric": "stamped Galerkin nnz/s", "value": value, "unit": "nnz/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "cfg2: d=10 plain FP64, s_a=21, manufactured u (20 pairs), |supp f|=840, N=3",
+                       "stamp_size": size, "nnz": nnz, "M": int(prep.M), "l2_flush": True,
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "e2e": {"value": e2e_value, "unit": "nnz/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": sum(e2e_ms) / len(e2e_ms)},
+            "breakdown_ms": med,
+            "solve_only": tts,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -81,6 +81,7 @@ typedef struct {
     int32_t inner_iters;   /* CG iterations in total */
     int32_t applies;       /* operator applications (FP64 + FP32) */
     double rel_residual;   /* ||f - L u||_2 / ||f||_2 in FP64 at exit */
+    double kernel_ms;      /* duration of the persistent solver launch (CUDA events on the stream) */
 } ss_solve_stats;
 
 const char* ss_last_error(void);

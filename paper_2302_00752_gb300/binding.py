@@ -43,11 +43,12 @@ class Sparse(C.Structure):
 
 class SolveStats(C.Structure):
     _fields_ = [("status", C.c_int32), ("outer_iters", C.c_int32), ("inner_iters", C.c_int32),
-                ("applies", C.c_int32), ("rel_residual", C.c_double)]
+                ("applies", C.c_int32), ("rel_residual", C.c_double), ("kernel_ms", C.c_double)]
 
     def as_dict(self):
         return {"status": STATUS.get(self.status, self.status), "outer_iters": self.outer_iters,
-                "inner_iters": self.inner_iters, "applies": self.applies, "rel_residual": self.rel_residual}
+                "inner_iters": self.inner_iters, "applies": self.applies, "rel_residual": self.rel_residual,
+                "kernel_ms": self.kernel_ms}
 
 
 def _load():

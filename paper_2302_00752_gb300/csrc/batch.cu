@@ -31,10 +31,12 @@ struct ss_batch_s {
   int planned_mode = -1;
   // graph
   cudaGraphExec_t graph = nullptr;
+  cudaStream_t cap_stream = nullptr;   // capture needs a stream other than the legacy default
   int graph_mode = -1, graph_max_iter = -1;
   double graph_tol = -1;
   ~ss_batch_s() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
   }
 };
 
@@ -96,19 +98,25 @@ ss_status run_once(ss_batch_s* b, double tol, int max_iter, ss_precision prec, b
   const int mode = prec == SS_FP64 ? 0 : 1;
   if (!b->planned || b->planned_mode != mode) SS_TRY(replan(b, mode, st));
   SS_TRY(work_upload(b->work, b->plan, st));   // f/u pointers may have changed
+  if (!b->work.ev[0]) {
+    SS_CUDA(cudaEventCreate(&b->work.ev[0]));
+    SS_CUDA(cudaEventCreate(&b->work.ev[1]));
+  }
   if (!use_graph)
     return launch_solve(b->work, b->plan, batch_op(b), b->slice_inst.get(), b->norm.get(), b->ca64.get(),
-                        b->ca32.get(), b->pn.get(), tol, max_iter, prec, st);
+                        b->ca32.get(), b->pn.get(), tol, max_iter, prec, st, b->work.ev[0], b->work.ev[1]);
   if (!b->graph || b->graph_mode != mode || b->graph_tol != tol || b->graph_max_iter != max_iter) {
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
     }
     cudaGraph_t g = nullptr;
-    SS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    if (!b->cap_stream) SS_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    // the upload above must land before the graph runs: the graph is launched on st after it
+    SS_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     ss_status s = launch_solve(b->work, b->plan, batch_op(b), b->slice_inst.get(), b->norm.get(), b->ca64.get(),
-                               b->ca32.get(), b->pn.get(), tol, max_iter, prec, st);
-    cudaError_t e = cudaStreamEndCapture(st, &g);
+                               b->ca32.get(), b->pn.get(), tol, max_iter, prec, b->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
     if (s != SS_OK) {
       if (g) cudaGraphDestroy(g);
       return s;
@@ -124,7 +132,9 @@ ss_status run_once(ss_batch_s* b, double tol, int max_iter, ss_precision prec, b
     b->graph_tol = tol;
     b->graph_max_iter = max_iter;
   }
+  SS_CUDA(cudaEventRecord(b->work.ev[0], st));
   SS_CUDA(cudaGraphLaunch(b->graph, st));
+  SS_CUDA(cudaEventRecord(b->work.ev[1], st));
   return SS_OK;
 }
 
@@ -240,7 +250,7 @@ extern "C" ss_status batch_solve(ss_batch b, const double* const* f, double* con
   SS_TRY(set_pointers(b, f, u));
   SS_TRY(run_once(b, tol, max_iter, prec, use_graph != 0, st));
   ss_status worst;
-  SS_TRY(read_stats(b->work, b->n_inst, stats, &worst, st));
+  SS_TRY(read_stats(b->work, b->n_inst, stats, &worst, st, b->work.ev[0], b->work.ev[1]));
   return worst;
 }
 

@@ -596,7 +596,8 @@ ss_status max_grid(int mode, int block, int* grid) {
 // Fill params and launch (capturable: no host synchronisation).
 ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, const int32_t* slice_inst,
                               const int32_t* norm, const double2* ca64, const float2* ca32, const int32_t* pn,
-                              double tol, int max_iter, ss_precision prec, cudaStream_t st) {
+                              double tol, int max_iter, ss_precision prec, cudaStream_t st, cudaEvent_t ev_begin,
+                       cudaEvent_t ev_end) {
   SolveParams P{};
   P.n_inst = (int)plan.inst.size();
   P.n_chunks = (int)plan.chunk.size();
@@ -644,17 +645,22 @@ ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, co
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (ev_begin) SS_CUDA(cudaEventRecord(ev_begin, st));
   if (prec == SS_FP64) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<0>, P));
   else SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<1>, P));
+  if (ev_end) SS_CUDA(cudaEventRecord(ev_end, st));
   return SS_OK;
 }
 
-ss_status read_stats(SolveWork& W, int n_inst, ss_solve_stats* stats, ss_status* worst, cudaStream_t st) {
+ss_status read_stats(SolveWork& W, int n_inst, ss_solve_stats* stats, ss_status* worst, cudaStream_t st,
+                     cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   std::vector<InstState> hs(n_inst);
   int herr = 0;
   SS_CUDA(cudaMemcpyAsync(hs.data(), W.state.get(), n_inst * sizeof(InstState), cudaMemcpyDeviceToHost, st));
   SS_CUDA(cudaMemcpyAsync(&herr, W.err.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
   SS_CUDA(cudaStreamSynchronize(st));
+  float kms = 0.f;
+  if (ev_begin && ev_end) cudaEventElapsedTime(&kms, ev_begin, ev_end);
   *worst = SS_OK;
   if (herr) {
     *worst = (ss_status)herr;
@@ -668,6 +674,7 @@ ss_status read_stats(SolveWork& W, int n_inst, ss_solve_stats* stats, ss_status*
       stats[i].inner_iters = s.inner_iters ? s.inner_iters : s.iters;
       stats[i].applies = s.applies;
       stats[i].rel_residual = s.bb > 0 ? std::sqrt(s.rr / s.bb) : 0.0;
+      stats[i].kernel_ms = kms;
     }
     if (*worst == SS_OK && s.status != SS_OK) {
       *worst = (ss_status)s.status;
@@ -768,11 +775,15 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
   op.ent = s->ent.get();
   op.colbits = colbits_of(s->jbits);
   op.colmask = colmask_of(s->jbits);
+  if (!C->work.ev[0]) {
+    SS_CUDA(cudaEventCreate(&C->work.ev[0]));
+    SS_CUDA(cudaEventCreate(&C->work.ev[1]));
+  }
   SS_TRY(launch_solve(C->work, C->plan, op, nullptr, s->norm.get(), s->ca64.get(), s->ca32.get(), s->pnorm.get(), tol,
-                      max_iter, prec, st));
+                      max_iter, prec, st, C->work.ev[0], C->work.ev[1]));
   ss_status worst;
   ss_solve_stats one{};
-  SS_TRY(read_stats(C->work, 1, &one, &worst, st));
+  SS_TRY(read_stats(C->work, 1, &one, &worst, st, C->work.ev[0], C->work.ev[1]));
   if (stats) *stats = one;
   return worst;
 }

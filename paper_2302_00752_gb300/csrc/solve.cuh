@@ -71,6 +71,11 @@ struct SolvePlan {
 // Device workspace of one solve context (single stamp or batch).
 struct SolveWork {
   int64_t rows_total = 0;   // padded rows, plus one dummy record
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  ~SolveWork() {
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    if (ev[1]) cudaEventDestroy(ev[1]);
+  }
   DevBuf<double2> xrec, prec64, r, z, q64, rhat, dlt;
   DevBuf<float4> prec32;
   DevBuf<float2> q32;
@@ -89,8 +94,10 @@ ss_status work_upload(SolveWork& W, const SolvePlan& plan, cudaStream_t st);
 ss_status max_grid(int mode, int block, int* grid);
 ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, const int32_t* slice_inst,
                        const int32_t* norm, const double2* ca64, const float2* ca32, const int32_t* pn,
-                       double tol, int max_iter, ss_precision prec, cudaStream_t st);
-ss_status read_stats(SolveWork& W, int n_inst, ss_solve_stats* stats, ss_status* worst, cudaStream_t st);
+                       double tol, int max_iter, ss_precision prec, cudaStream_t st,
+                       cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
+ss_status read_stats(SolveWork& W, int n_inst, ss_solve_stats* stats, ss_status* worst, cudaStream_t st,
+                     cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 
 ss_status plan_chunks(SolvePlan& plan, const std::vector<int32_t>& woff_host, const std::vector<int32_t>& slice_inst_host,
                       int target_chunks);
