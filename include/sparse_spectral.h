@@ -111,7 +111,8 @@ ss_status lattice_random(const int32_t* freq, int64_t n, int32_t d, double sigma
                          int32_t* attempt_out, void* stream);
 
 /* Component-by-component lattice (named in Section "Improvements with
- * randomized lattices"; criterion not given by the paper): M = smallest prime
+ * randomized lattices"; criterion not given by the paper): M = smallest
+ * 7-smooth integer (prime factors 2, 3, 5, 7: a mixed-radix FFT length)
  * >= max(M_min, K + 1), z_1 = 1, and for j >= 2 the first candidate
  * 1 + raw[j][c] mod (M-1) (raw: host [d][n_cand]) under which the distinct
  * projections of `freq` onto coordinates 1..j have distinct residues.

@@ -12,7 +12,10 @@ least 1 - sigma (the paper's statement of the probability is read as 1 - sigma).
 Component-by-component (CBC) construction is only named by the paper; the
 reading used here: z_1 = 1 and, for j = 2..d, the first candidate from a
 seeded stream such that the projections of I onto coordinates 1..j that are
-distinct points have distinct residues mod M.
+distinct points have distinct residues mod M.  The CBC check is exact and
+needs no primality (only the random-lattice lemma does), so M is the smallest
+7-smooth integer (prime factors 2, 3, 5, 7) not below max(M_min, K + 1): a
+length that a mixed-radix FFT handles directly.
 
 Pins: exact integer arithmetic throughout; checked against a closed-form
 bijective box lattice, a brute-force pairwise collision check, forced
@@ -78,6 +81,25 @@ def random_lattice_size(K, n_I, sigma, M_min=0):
     return next_prime(max(lo, int(M_min)))
 
 
+def is_smooth(n, primes=(2, 3, 5, 7)):
+    """True when every prime factor of n is in ``primes``."""
+    n = int(n)
+    if n < 1:
+        return False
+    for p in primes:
+        while n % p == 0:
+            n //= p
+    return n == 1
+
+
+def next_smooth(n):
+    """Smallest 7-smooth integer >= n."""
+    n = max(int(n), 1)
+    while not is_smooth(n):
+        n += 1
+    return n
+
+
 def z_from_raw(raw, M):
     """Map raw non-negative integers onto {1..M-1}."""
     return np.array([1 + int(r) % (int(M) - 1) for r in np.asarray(raw).ravel()], dtype=np.int64)
@@ -98,10 +120,10 @@ def random_lattice(freq, draws):
 
 def cbc_lattice(freq, draws):
     """Component-by-component search (reading stated in the module header).
-    M is the smallest prime >= max(M_min, K + 1)."""
+    M is the smallest 7-smooth integer >= max(M_min, K + 1)."""
     uniq = np.unique(np.asarray(freq, np.int64), axis=0)
     d = uniq.shape[1]
-    M = next_prime(max(int(draws["M_min"]), expansion(uniq) + 1))
+    M = next_smooth(max(int(draws["M_min"]), expansion(uniq) + 1))
     raw = np.asarray(draws["raw"])
     z = [1]
     for j in range(1, d):

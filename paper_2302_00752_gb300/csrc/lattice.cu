@@ -23,6 +23,17 @@ int64_t next_prime_host(int64_t n) {
   return n;
 }
 
+// Smallest integer >= n whose prime factors are 2, 3, 5, 7 (FFT-friendly).
+int64_t next_smooth_host(int64_t n) {
+  if (n < 1) n = 1;
+  for (;; ++n) {
+    int64_t m = n;
+    for (int64_t p : {2, 3, 5, 7})
+      while (m % p == 0) m /= p;
+    if (m == 1) return n;
+  }
+}
+
 // ---------------------------------------------------------------- kernels
 
 __global__ void k_residues(const int32_t* __restrict__ f, int64_t n, int d, LatticeDev L, int64_t* res) {
@@ -275,7 +286,8 @@ extern "C" ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int6
   int64_t K = 0;
   SS_TRY(expansion_of(freq, n, d, &K, st));
   if (std::max<int64_t>(M_min, K + 1) >= 2147483000ll) SS_FAIL(SS_ERR_INVALID, "lattice_cbc: M would exceed 2^31");
-  const int64_t M = next_prime_host(std::max<int64_t>(M_min, K + 1));
+  // the CBC check is exact and needs no prime: take an FFT-friendly length
+  const int64_t M = next_smooth_host(std::max<int64_t>(M_min, K + 1));
   // the candidate set must be free of duplicates (checked on the full vectors)
   {
     std::vector<int64_t> one(d, 1);

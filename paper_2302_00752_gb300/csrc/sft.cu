@@ -47,16 +47,65 @@ __global__ void k_twiddles(int64_t M, int bl, int64_t H, typename C2<R>::T* lo, 
   }
 }
 
-__global__ void k_term_residues(const int32_t* __restrict__ freq, int64_t n, LatticeDev L, int64_t* q,
-                                int64_t* step) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const int64_t r = residue_of(freq + t * L.d, L.d, L);
-  q[t] = r;
-  step[t] = (int64_t)(((uint64_t)r * (uint64_t)kSampThreads) % (uint64_t)L.M);
+// Terms p and -p of a real sum are one term: Re(c e_{-p}) = Re(conj(c) e_p).
+// Each term is mapped to the sign representative of its frequency (first
+// nonzero coordinate positive) with c or conj(c); equal representatives are
+// merged by their first occurrence ("leader"), which sums its group in index
+// order (deterministic).  The zero frequency keeps Re(c).
+__device__ __forceinline__ int rep_sign(const int32_t* p, int d) {
+  for (int c = 0; c < d; ++c)
+    if (p[c] != 0) return p[c] > 0 ? 1 : -1;
+  return 0;
 }
 
-template <typename R, bool SMEM_TAB>
+__device__ __forceinline__ bool same_rep(const int32_t* a, int sa, const int32_t* b, int sb, int d) {
+  const int xa = sa < 0 ? -1 : 1, xb = sb < 0 ? -1 : 1;
+  for (int c = 0; c < d; ++c)
+    if (xa * a[c] != xb * b[c]) return false;
+  return true;
+}
+
+__global__ void k_merge_terms(const int32_t* __restrict__ freq, const double2* __restrict__ coef, int64_t n, int d,
+                              int32_t* leader_flag, double2* merged, int32_t* imag_nonzero) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int32_t* pt = freq + t * d;
+  const int st = rep_sign(pt, d);
+  bool leader = true;
+  for (int64_t u = 0; u < t && leader; ++u)
+    if (same_rep(freq + u * d, rep_sign(freq + u * d, d), pt, st, d)) leader = false;
+  leader_flag[t] = leader ? 1 : 0;
+  if (!leader) return;
+  double re = 0.0, im = 0.0;
+  for (int64_t u = t; u < n; ++u) {
+    const int32_t* pu = freq + u * d;
+    const int su = rep_sign(pu, d);
+    if (!same_rep(pu, su, pt, st, d)) continue;
+    const double2 c = coef[u];
+    re += c.x;
+    im += (su == 0) ? 0.0 : (su == st ? c.y : -c.y);
+  }
+  if (st == 0) im = 0.0;
+  merged[t] = make_double2(re, im);
+  if (im != 0.0) atomicExch(imag_nonzero, 1);
+}
+
+// Compact the leaders: residue of the leader's frequency, step and coefficient.
+__global__ void k_compact_terms(const int32_t* __restrict__ freq, int64_t n, LatticeDev L,
+                                const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
+                                const double2* __restrict__ merged, int64_t* q, int64_t* step, double2* coef_out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n || !flag[t]) return;
+  const int64_t k = pos[t];
+  // the merged coefficient is expressed in the leader's own orientation p_t
+  const int64_t r = residue_of(freq + t * L.d, L.d, L);
+  q[k] = r;
+  step[k] = (int64_t)(((uint64_t)r * (uint64_t)kSampThreads) % (uint64_t)L.M);
+  coef_out[k] = merged[t];
+}
+
+
+template <typename R, bool SMEM_TAB, bool REAL>
 __global__ void __launch_bounds__(kSampThreads) k_sample(int64_t M, int bl, int64_t H,
                                                          const typename C2<R>::T* __restrict__ lo_g,
                                                          const typename C2<R>::T* __restrict__ hi_g,
@@ -100,8 +149,12 @@ __global__ void __launch_bounds__(kSampThreads) k_sample(int64_t M, int bl, int6
       for (int m = 0; m < kSampPerThread; ++m) {
         const T2 h = hi[r >> bl], l = lo[r & lmask];
         const R er = h.x * l.x - h.y * l.y;   // cos(2 pi r / M)
-        const R ei = h.x * l.y + h.y * l.x;   // sin(2 pi r / M)
-        acc[m] += c.x * er - c.y * ei;
+        if (REAL) {
+          acc[m] += c.x * er;
+        } else {
+          const R ei = h.x * l.y + h.y * l.x;   // sin(2 pi r / M)
+          acc[m] += c.x * er - c.y * ei;
+        }
         r += st;
         if (r >= (uint32_t)M) r -= (uint32_t)M;
       }
@@ -215,53 +268,73 @@ ss_status get_plan(int64_t M, ss_precision prec, cudaStream_t st, std::shared_pt
   return SS_OK;
 }
 
+template <typename R, bool SMEM>
+ss_status launch_sample(const SftPlan& P, bool real, unsigned grid, size_t sm, const int64_t* q, const int64_t* step,
+                        const double2* coef, int64_t n, void* out, cudaStream_t st) {
+  using T2 = typename C2<R>::T;
+  auto lo = reinterpret_cast<const T2*>(P.lo.get());
+  auto hi = reinterpret_cast<const T2*>(P.hi.get());
+  if (real) {
+    SS_CUDA(cudaFuncSetAttribute(k_sample<R, SMEM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_sample<R, SMEM, true><<<grid, kSampThreads, sm, st>>>(P.M, P.bl, P.H, lo, hi, q, step, coef, n,
+                                                            reinterpret_cast<R*>(out));
+  } else {
+    SS_CUDA(cudaFuncSetAttribute(k_sample<R, SMEM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_sample<R, SMEM, false><<<grid, kSampThreads, sm, st>>>(P.M, P.bl, P.H, lo, hi, q, step, coef, n,
+                                                             reinterpret_cast<R*>(out));
+  }
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
 ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, void* out, cudaStream_t st) {
   const int64_t n = g->n_terms;
-  DevBuf<int64_t> q, step;
-  SS_TRY(q.alloc(n));
-  SS_TRY(step.alloc(n));
-  if (n > 0) {
-    k_term_residues<<<nblk(n), 256, 0, st>>>(g->freq, n, L, q.get(), step.get());
-    SS_LAUNCH_CHECK();
-  }
   const int64_t Lsz = 1ll << P.bl;
   const unsigned grid = (unsigned)((P.M + kSampThreads * kSampPerThread - 1) / (kSampThreads * kSampPerThread));
-  const double2* coef = reinterpret_cast<const double2*>(g->coef);
+  if (n == 0) {
+    SS_CUDA(cudaMemsetAsync(out, 0, P.M * (P.prec == SS_FP64 ? sizeof(double) : sizeof(float)), st));
+    return SS_OK;
+  }
+  // merge +-p terms (exact rewrite of the real sum), then evaluate
+  DevBuf<int64_t> q, step, total;
+  DevBuf<int32_t> flag, pos, imag;
+  DevBuf<double2> merged, coef;
+  SS_TRY(q.alloc(n));
+  SS_TRY(step.alloc(n));
+  SS_TRY(total.alloc(1));
+  SS_TRY(flag.alloc(n));
+  SS_TRY(pos.alloc(n));
+  SS_TRY(imag.alloc(1));
+  SS_TRY(merged.alloc(n));
+  SS_TRY(coef.alloc(n));
+  SS_CUDA(cudaMemsetAsync(imag.get(), 0, sizeof(int32_t), st));
+  k_merge_terms<<<nblk(n), 256, 0, st>>>(g->freq, reinterpret_cast<const double2*>(g->coef), n, L.d, flag.get(),
+                                         merged.get(), imag.get());
+  SS_LAUNCH_CHECK();
+  SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), n, total.get(), st));
+  k_compact_terms<<<nblk(n), 256, 0, st>>>(g->freq, n, L, flag.get(), pos.get(), merged.get(), q.get(), step.get(),
+                                           coef.get());
+  SS_LAUNCH_CHECK();
+  int64_t nm = 0;
+  int32_t has_imag = 0;
+  SS_CUDA(cudaMemcpyAsync(&nm, total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaMemcpyAsync(&has_imag, imag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  const bool real = has_imag == 0;
   if (P.prec == SS_FP64) {
     const size_t terms_sm = kTermChunk * (2 * sizeof(int64_t) + sizeof(double2));
     const size_t tab_sm = (Lsz + P.H) * sizeof(double2);
     const bool smem = tab_sm + terms_sm <= 200 * 1024;
     const size_t sm = (smem ? tab_sm : 0) + terms_sm;
-    auto lo = reinterpret_cast<const double2*>(P.lo.get());
-    auto hi = reinterpret_cast<const double2*>(P.hi.get());
-    if (smem) {
-      SS_CUDA(cudaFuncSetAttribute(k_sample<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      k_sample<double, true><<<grid, kSampThreads, sm, st>>>(P.M, P.bl, P.H, lo, hi, q.get(), step.get(), coef, n,
-                                                             reinterpret_cast<double*>(out));
-    } else {
-      SS_CUDA(cudaFuncSetAttribute(k_sample<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      k_sample<double, false><<<grid, kSampThreads, sm, st>>>(P.M, P.bl, P.H, lo, hi, q.get(), step.get(), coef, n,
-                                                              reinterpret_cast<double*>(out));
-    }
-  } else {
-    const size_t terms_sm = kTermChunk * (2 * sizeof(int64_t) + sizeof(float2));
-    const size_t tab_sm = (Lsz + P.H) * sizeof(float2);
-    const bool smem = tab_sm + terms_sm <= 200 * 1024;
-    const size_t sm = (smem ? tab_sm : 0) + terms_sm;
-    auto lo = reinterpret_cast<const float2*>(P.lo.get());
-    auto hi = reinterpret_cast<const float2*>(P.hi.get());
-    if (smem) {
-      SS_CUDA(cudaFuncSetAttribute(k_sample<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      k_sample<float, true><<<grid, kSampThreads, sm, st>>>(P.M, P.bl, P.H, lo, hi, q.get(), step.get(), coef, n,
-                                                            reinterpret_cast<float*>(out));
-    } else {
-      SS_CUDA(cudaFuncSetAttribute(k_sample<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      k_sample<float, false><<<grid, kSampThreads, sm, st>>>(P.M, P.bl, P.H, lo, hi, q.get(), step.get(), coef, n,
-                                                             reinterpret_cast<float*>(out));
-    }
+    if (smem) return launch_sample<double, true>(P, real, grid, sm, q.get(), step.get(), coef.get(), nm, out, st);
+    return launch_sample<double, false>(P, real, grid, sm, q.get(), step.get(), coef.get(), nm, out, st);
   }
-  SS_LAUNCH_CHECK();
-  return SS_OK;
+  const size_t terms_sm = kTermChunk * (2 * sizeof(int64_t) + sizeof(float2));
+  const size_t tab_sm = (Lsz + P.H) * sizeof(float2);
+  const bool smem = tab_sm + terms_sm <= 200 * 1024;
+  const size_t sm = (smem ? tab_sm : 0) + terms_sm;
+  if (smem) return launch_sample<float, true>(P, real, grid, sm, q.get(), step.get(), coef.get(), nm, out, st);
+  return launch_sample<float, false>(P, real, grid, sm, q.get(), step.get(), coef.get(), nm, out, st);
 }
 
 ss_status recover_from(const SftPlan& P, const LatticeDev& L, const void* samples, const int32_t* cand, int64_t n_cand,

@@ -76,19 +76,59 @@ __device__ bool grid_sync(const SolveParams& P) {
   return s_ok != 0;
 }
 
-__device__ __forceinline__ int read_counter(const int* p) { return atomicAdd(const_cast<int*>(p), 0); }
+// Counter read by one thread and broadcast to the block (uniform control flow).
+__device__ int block_counter(const SolveParams& P, int idx) {
+  __shared__ int s_cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) s_cnt = atomicAdd(P.counters + idx, 0);
+  __syncthreads();
+  return s_cnt;
+}
 
-// Sum of quantity q over the partial slots of instance i (all lanes of the
-// warp call; the result of lane 0 is broadcast, so every block gets the same bits).
-__device__ double inst_sum(const SolveParams& P, int i, int q) {
+// Sums of the kNQ quantities over the partial slots of instance i, by one warp
+// in a fixed order (lane-strided, then a fixed butterfly; lane 0's result is
+// broadcast), so every block that needs them gets the same bits.  Loads of four
+// slots per lane are issued before they are added.
+__device__ void inst_sums(const SolveParams& P, int i, double out[kNQ]) {
   const int lane = threadIdx.x & 31;
   const SolveInst& in = P.inst[i];
   const int len = in.c_last - in.c_first + 1;
-  double s = 0.0;
-  for (int c = lane; c < len; c += 32) s += __ldcg(P.part + (int64_t)(in.part_base + c) * kNQ + q);
+  const double2* base = reinterpret_cast<const double2*>(P.part + (int64_t)in.part_base * kNQ);
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int c = lane;
+  for (; c + 96 < len; c += 128) {
+    double2 x[8];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return __shfl_sync(0xffffffffu, s, 0);
+    for (int u = 0; u < 4; ++u) {
+      x[2 * u] = __ldcg(base + 2 * (c + 32 * u));
+      x[2 * u + 1] = __ldcg(base + 2 * (c + 32 * u) + 1);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a0 += x[2 * u].x;
+      a1 += x[2 * u].y;
+      a2 += x[2 * u + 1].x;
+      a3 += x[2 * u + 1].y;
+    }
+  }
+  for (; c < len; c += 32) {
+    const double2 x0 = __ldcg(base + 2 * c), x1 = __ldcg(base + 2 * c + 1);
+    a0 += x0.x;
+    a1 += x0.y;
+    a2 += x1.x;
+    a3 += x1.y;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+  }
+  out[0] = __shfl_sync(0xffffffffu, a0, 0);
+  out[1] = __shfl_sync(0xffffffffu, a1, 0);
+  out[2] = __shfl_sync(0xffffffffu, a2, 0);
+  out[3] = __shfl_sync(0xffffffffu, a3, 0);
 }
 
 __device__ __forceinline__ double warp_reduce(double v) {
@@ -171,10 +211,10 @@ __device__ __forceinline__ double2 apply64_row(const SolveParams& P, const Solve
 __device__ __forceinline__ float2 apply32_row(const SolveParams& P, const SolveInst& in, int64_t s, int lane,
                                               int64_t g) {
   if (g == in.zero_row) {
-    const float4 v = __ldcg(P.prec32 + g);
+    const float4 v = __ldcg(P.urec32 + g);
     return make_float2(v.x, v.y);
   }
-  return row_apply32<true>(P.op, s, lane, __ldg(P.norm + g), P.prec32, P.ca32 + in.coef_off, P.pn + in.coef_off);
+  return row_apply32<true>(P.op, s, lane, __ldg(P.norm + g), P.urec32, P.ca32 + in.coef_off, P.pn + in.coef_off);
 }
 
 __device__ __forceinline__ void owner_done(const SolveParams& P, InstState& st, int status) {
@@ -182,114 +222,128 @@ __device__ __forceinline__ void owner_done(const SolveParams& P, InstState& st, 
   atomicAdd(P.counters + 0, 1);
 }
 
+// ------------------------------------------------------------ CG recurrences
+//
+// Both modes use the Chronopoulos-Gear form of preconditioned CG, which needs
+// one reduction per iteration (two grid barriers instead of three):
+//   p_i = u_i + beta_i p_{i-1},  s_i = w_i + beta_i s_{i-1}   (s_i = L p_i)
+//   x_{i+1} = x_i + alpha_i p_i, r_{i+1} = r_i - alpha_i s_i, u_{i+1} = D^-1 r_{i+1}
+//   w_{i+1} = L u_{i+1};  gamma = <r,u>, delta = <w,u>
+//   beta_{i+1} = gamma_{i+1}/gamma_i,
+//   alpha_{i+1} = gamma_{i+1} / (delta_{i+1} - beta_{i+1} gamma_{i+1} / alpha_i),
+// with beta_0 = 0, alpha_0 = gamma_0 / delta_0.  Phase X does the scalars and
+// the vector updates, phase Y the operator and the three inner products
+// (gamma, delta, |r|^2).  Partial slot q3 holds |f|^2.
+
+struct Coeffs {
+  double alpha, beta;
+};
+
+__device__ __forceinline__ Coeffs cg_coeffs(int it, double gam, double del, double gam_prev, double alpha_prev) {
+  Coeffs c;
+  if (it == 0) {
+    c.beta = 0.0;
+    c.alpha = gam / del;
+  } else {
+    c.beta = gam / gam_prev;
+    c.alpha = gam / (del - c.beta * gam / alpha_prev);
+  }
+  return c;
+}
+
 // --------------------------------------------------------------- FP64 CG
 
 __device__ void solve_fp64(const SolveParams& P, Smem& sm) {
   const double tol2 = P.tol * P.tol;
-  // r = f, x = 0, z = D^-1 r, p = z; partials <r,z>, |f|^2
-  run_phase(P, sm, 0b1010u, [](int, const Chunk&, int, int, bool, int) {}, [&](int64_t g, int64_t, int, int i, int, double* v) {
+  auto noscal = [](int, const Chunk&, int, int, bool, int) {};
+  // r = f, x = 0, u = D^-1 r, p = s = 0; |f|^2
+  run_phase(P, sm, 0b1000u, noscal, [&](int64_t g, int64_t, int, int i, int, double* v) {
     const SolveInst& in = P.inst[i];
     const double2 f = f_at(in, g);
     const double D = jacobi(P, in, g);
-    const double2 z = make_double2(f.x / D, f.y / D);
     P.r[g] = f;
-    P.z[g] = z;
     P.xrec[2 * g] = make_double2(0.0, 0.0);
-    P.prec64[2 * g] = z;
-    v[1] = f.x * z.x + f.y * z.y;
+    P.urec64[2 * g] = make_double2(f.x / D, f.y / D);
+    P.pd[g] = make_double2(0.0, 0.0);
+    P.sd[g] = make_double2(0.0, 0.0);
     v[3] = f.x * f.x + f.y * f.y;
   });
   if (!grid_sync(P)) return;
-  run_phase(P, sm, 0u, [&](int, const Chunk&, int, int i, bool owner, int lane) {
-    const double rz = inst_sum(P, i, 1), bb = inst_sum(P, i, 3);
-    if (owner && lane == 0) {
-      InstState& st = P.state[i];
-      st.bb = bb;
-      st.rr = bb;
-      st.rho[0] = rz;
-      st.iters = 0;
-      st.applies = 0;
-      st.outer_iters = 1;
-      st.act[0] = bb > 0.0;
-      if (!(bb > 0.0)) owner_done(P, st, SS_OK);
-    }
-  }, [](int64_t, int64_t, int, int, int, double*) {});
-  if (!grid_sync(P)) return;
-  for (int it = 0;; ++it) {
-    if (read_counter(P.counters + 0) >= P.n_inst) break;
-    const int cur = it & 1, nxt = cur ^ 1;
-    // q = L p, <p, q>
-    run_phase(P, sm, 0b0001u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
-      if (lane == 0) {
-        sm.flag[k] = __ldcg(&P.state[i].act[cur]);
-        if (owner && sm.flag[k]) P.state[i].applies += 1;
-      }
+  auto phase_y = [&](unsigned par) {
+    run_phase(P, sm, 0b0111u, [&](int, const Chunk&, int k, int i, bool, int lane) {
+      if (lane == 0) sm.flag[k] = par > 1 ? 1 : __ldcg(&P.state[i].act[par]);
     }, [&](int64_t g, int64_t s, int lane, int i, int k, double* v) {
       if (!sm.flag[k]) return;
       const SolveInst& in = P.inst[i];
-      const double2 q = apply64_row(P, in, s, lane, g, P.prec64);
-      const double2 p = P.prec64[2 * g];
-      P.q64[g] = q;
-      v[0] = p.x * q.x + p.y * q.y;
-    });
-    if (!grid_sync(P)) return;
-    // alpha = rho / <p,q>; x += alpha p; r -= alpha q; z = D^-1 r; <r,z>, |r|^2
-    run_phase(P, sm, 0b0110u, [&](int, const Chunk&, int k, int i, bool, int lane) {
-      const double pq = inst_sum(P, i, 0);
-      if (lane == 0) {
-        sm.flag[k] = __ldcg(&P.state[i].act[cur]);
-        sm.ca[k] = __ldcg(&P.state[i].rho[cur]) / pq;
-      }
-    }, [&](int64_t g, int64_t, int, int i, int k, double* v) {
-      if (!sm.flag[k]) return;
-      const SolveInst& in = P.inst[i];
-      const double a = sm.ca[k];
-      const double2 p = P.prec64[2 * g], q = P.q64[g];
-      double2 x = P.xrec[2 * g], r = P.r[g];
-      x.x += a * p.x; x.y += a * p.y;
-      r.x -= a * q.x; r.y -= a * q.y;
-      const double D = jacobi(P, in, g);
-      const double2 z = make_double2(r.x / D, r.y / D);
-      P.xrec[2 * g] = x;
-      P.r[g] = r;
-      P.z[g] = z;
-      v[1] = r.x * z.x + r.y * z.y;
+      const double2 w = apply64_row(P, in, s, lane, g, P.urec64);
+      const double2 u = P.urec64[2 * g], r = P.r[g];
+      P.w64[g] = w;
+      v[0] = r.x * u.x + r.y * u.y;
+      v[1] = w.x * u.x + w.y * u.y;
       v[2] = r.x * r.x + r.y * r.y;
     });
-    if (!grid_sync(P)) return;
-    // convergence, beta = rho_new / rho, p = z + beta p
+  };
+  phase_y(2);   // every instance
+  if (!grid_sync(P)) return;
+  for (int it = 0;; ++it) {
+    const int cur = it & 1, nxt = cur ^ 1;
     run_phase(P, sm, 0u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
-      const double rz = inst_sum(P, i, 1), rr = inst_sum(P, i, 2);
+      double t[kNQ];
+      inst_sums(P, i, t);
       if (lane == 0) {
         InstState& st = P.state[i];
-        const int act = __ldcg(&st.act[cur]);
-        const double bb = __ldcg(&st.bb);
-        const bool conv = rr <= tol2 * bb;
-        const bool cap = it + 1 >= P.max_iter;
-        sm.flag[k] = act && !conv && !cap;
-        sm.cb[k] = rz / __ldcg(&st.rho[cur]);
+        const int act = it == 0 ? 1 : __ldcg(&st.act[cur]);
+        const double bb = it == 0 ? t[3] : __ldcg(&st.bb);
+        const bool conv = t[2] <= tol2 * bb;
+        const bool cap = it >= P.max_iter;
+        const Coeffs cf = cg_coeffs(it, t[0], t[1], it ? __ldcg(&st.rho[cur]) : 0.0,
+                                    it ? __ldcg(&st.alpha[cur]) : 0.0);
+        const bool go = act && !conv && !cap;
+        sm.flag[k] = go;
+        sm.ca[k] = cf.alpha;
+        sm.cb[k] = cf.beta;
         if (owner) {
-          st.act[nxt] = act && !conv && !cap;
-          st.rho[nxt] = rz;
+          if (it == 0) {
+            st.bb = bb;
+            st.applies = 1;
+            st.outer_iters = 1;
+          }
+          st.act[nxt] = go;
+          st.rho[nxt] = t[0];
+          st.alpha[nxt] = cf.alpha;
           if (act) {
-            st.iters = it + 1;
-            st.rr = rr;
+            st.rr = t[2];
+            st.iters = it;
             if (conv) owner_done(P, st, SS_OK);
             else if (cap) owner_done(P, st, SS_ERR_NOT_CONVERGED);
+            else st.applies += 1;
           }
         }
       }
-    }, [&](int64_t g, int64_t, int, int, int k, double*) {
+    }, [&](int64_t g, int64_t, int, int i, int k, double*) {
       if (!sm.flag[k]) return;
-      const double b = sm.cb[k];
-      const double2 z = P.z[g], p = P.prec64[2 * g];
-      P.prec64[2 * g] = make_double2(z.x + b * p.x, z.y + b * p.y);
+      const SolveInst& in = P.inst[i];
+      const double a = sm.ca[k], b = sm.cb[k];
+      const double2 u = P.urec64[2 * g], w = P.w64[g];
+      double2 p = P.pd[g], sv = P.sd[g], x = P.xrec[2 * g], r = P.r[g];
+      p.x = u.x + b * p.x; p.y = u.y + b * p.y;
+      sv.x = w.x + b * sv.x; sv.y = w.y + b * sv.y;
+      x.x += a * p.x; x.y += a * p.y;
+      r.x -= a * sv.x; r.y -= a * sv.y;
+      const double D = jacobi(P, in, g);
+      P.pd[g] = p;
+      P.sd[g] = sv;
+      P.xrec[2 * g] = x;
+      P.r[g] = r;
+      P.urec64[2 * g] = make_double2(r.x / D, r.y / D);
     });
+    if (!grid_sync(P)) return;
+    if (block_counter(P, 0) >= P.n_inst) break;
+    phase_y(nxt);
     if (!grid_sync(P)) return;
   }
   // true residual f - L x in FP64, and the output
-  run_phase(P, sm, 0b0100u, [](int, const Chunk&, int, int, bool, int) {},
-            [&](int64_t g, int64_t s, int lane, int i, int, double* v) {
+  run_phase(P, sm, 0b0100u, noscal, [&](int64_t g, int64_t s, int lane, int i, int, double* v) {
     const SolveInst& in = P.inst[i];
     const double2 y = apply64_row(P, in, s, lane, g, P.xrec);
     const double2 f = f_at(in, g);
@@ -300,9 +354,10 @@ __device__ void solve_fp64(const SolveParams& P, Smem& sm) {
   });
   if (!grid_sync(P)) return;
   run_phase(P, sm, 0u, [&](int, const Chunk&, int, int i, bool owner, int lane) {
-    const double rr = inst_sum(P, i, 2);
+    double t[kNQ];
+    inst_sums(P, i, t);
     if (owner && lane == 0) {
-      P.state[i].rr = rr;
+      P.state[i].rr = t[2];
       P.state[i].applies += 1;
     }
   }, [](int64_t, int64_t, int, int, int, double*) {});
@@ -312,23 +367,23 @@ __device__ void solve_fp64(const SolveParams& P, Smem& sm) {
 
 __device__ void solve_refined(const SolveParams& P, Smem& sm) {
   const double tol2 = P.tol * P.tol, itol2 = P.inner_tol * P.inner_tol;
+  auto noscal = [](int, const Chunk&, int, int, bool, int) {};
   // x = 0; |f|^2
-  run_phase(P, sm, 0b1000u, [](int, const Chunk&, int, int, bool, int) {},
-            [&](int64_t g, int64_t, int, int i, int, double* v) {
+  run_phase(P, sm, 0b1000u, noscal, [&](int64_t g, int64_t, int, int i, int, double* v) {
     const double2 f = f_at(P.inst[i], g);
     P.xrec[2 * g] = make_double2(0.0, 0.0);
     v[3] = f.x * f.x + f.y * f.y;
   });
   if (!grid_sync(P)) return;
   run_phase(P, sm, 0u, [&](int, const Chunk&, int, int i, bool owner, int lane) {
-    const double bb = inst_sum(P, i, 3);
+    double t[kNQ];
+    inst_sums(P, i, t);
     if (owner && lane == 0) {
       InstState& st = P.state[i];
-      st.bb = bb;
-      st.rr = bb;
-      st.iters = st.inner_iters = st.outer_iters = st.applies = 0;
-      st.act[0] = bb > 0.0;
-      if (!(bb > 0.0)) owner_done(P, st, SS_OK);
+      st.bb = t[3];
+      st.rr = t[3];
+      st.act[0] = t[3] > 0.0;
+      if (!(t[3] > 0.0)) owner_done(P, st, SS_OK);
     }
   }, [](int64_t, int64_t, int, int, int, double*) {});
   if (!grid_sync(P)) return;
@@ -350,13 +405,14 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
       v[2] = r.x * r.x + r.y * r.y;
     });
     if (!grid_sync(P)) return;
-    // outer test; inner start: r = rhat, delta = 0, z = D^-1 r, p = z; <r,z>
-    run_phase(P, sm, 0b0010u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
-      const double rr = inst_sum(P, i, 2);
+    // outer test; inner start: r = rhat, delta = 0, u = D^-1 r (FP32 records), p = s = 0
+    run_phase(P, sm, 0u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
+      double t[kNQ];
+      inst_sums(P, i, t);
       if (lane == 0) {
         InstState& st = P.state[i];
         const int act = __ldcg(&st.act[ocur]);
-        const bool conv = rr <= tol2 * __ldcg(&st.bb);
+        const bool conv = t[2] <= tol2 * __ldcg(&st.bb);
         const bool cap = ot >= P.max_outer;
         const bool go = act && !conv && !cap;
         sm.flag[k] = go;
@@ -364,106 +420,100 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
           st.act[onxt] = go;
           st.inn[0] = go;
           if (act) {
-            st.rr = rr;
+            st.rr = t[2];
             if (conv) owner_done(P, st, SS_OK);
             else if (cap) owner_done(P, st, SS_ERR_NOT_CONVERGED);
             else {
               st.outer_iters = ot + 1;
+              st.applies += 1;
               atomicAdd(P.counters + 1, 1);
             }
           }
         }
       }
-    }, [&](int64_t g, int64_t, int, int i, int k, double* v) {
+    }, [&](int64_t g, int64_t, int, int i, int k, double*) {
       if (!sm.flag[k]) return;
       const SolveInst& in = P.inst[i];
       const double2 r = P.rhat[g];
       const double D = jacobi(P, in, g);
-      const double2 z = make_double2(r.x / D, r.y / D);
       P.r[g] = r;
-      P.z[g] = z;
       P.dlt[g] = make_double2(0.0, 0.0);
-      reinterpret_cast<float2*>(P.prec32 + g)[0] = make_float2((float)z.x, (float)z.y);
-      v[1] = r.x * z.x + r.y * z.y;
+      P.pd[g] = make_double2(0.0, 0.0);
+      P.sd[g] = make_double2(0.0, 0.0);
+      reinterpret_cast<float2*>(P.urec32 + g)[0] = make_float2((float)(r.x / D), (float)(r.y / D));
     });
     if (!grid_sync(P)) return;
-    if (read_counter(P.counters + 0) >= P.n_inst) break;
-    for (int it = 0;; ++it) {
-      const int cur = it & 1, nxt = cur ^ 1;
-      // q = L32 p, <p, q>
-      run_phase(P, sm, 0b0001u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
-        const double rz0 = (it == 0) ? inst_sum(P, i, 1) : 0.0;
-        if (lane == 0) {
-          InstState& st = P.state[i];
-          sm.flag[k] = __ldcg(&st.inn[cur]);
-          if (owner && sm.flag[k]) {
-            st.applies += 1;
-            if (it == 0) st.rho[0] = rz0;
-          }
-        }
+    if (block_counter(P, 0) >= P.n_inst) break;
+    // inner CG on the FP32 operator
+    auto phase_y = [&](int par) {
+      run_phase(P, sm, 0b0111u, [&](int, const Chunk&, int k, int i, bool, int lane) {
+        if (lane == 0) sm.flag[k] = __ldcg(&P.state[i].inn[par]);
       }, [&](int64_t g, int64_t s, int lane, int i, int k, double* v) {
         if (!sm.flag[k]) return;
         const SolveInst& in = P.inst[i];
-        const float2 q = apply32_row(P, in, s, lane, g);
-        const float4 p = P.prec32[g];
-        P.q32[g] = q;
-        v[0] = (double)p.x * (double)q.x + (double)p.y * (double)q.y;
-      });
-      if (!grid_sync(P)) return;
-      // alpha; delta += alpha p; r -= alpha q; z = D^-1 r; <r,z>, |r|^2
-      run_phase(P, sm, 0b0110u, [&](int, const Chunk&, int k, int i, bool, int lane) {
-        const double pq = inst_sum(P, i, 0);
-        if (lane == 0) {
-          sm.flag[k] = __ldcg(&P.state[i].inn[cur]);
-          sm.ca[k] = __ldcg(&P.state[i].rho[cur]) / pq;
-        }
-      }, [&](int64_t g, int64_t, int, int i, int k, double* v) {
-        if (!sm.flag[k]) return;
-        const SolveInst& in = P.inst[i];
-        const double a = sm.ca[k];
-        const float4 p = P.prec32[g];
-        const float2 q = P.q32[g];
-        double2 dl = P.dlt[g], r = P.r[g];
-        dl.x += a * (double)p.x; dl.y += a * (double)p.y;
-        r.x -= a * (double)q.x; r.y -= a * (double)q.y;
-        const double D = jacobi(P, in, g);
-        const double2 z = make_double2(r.x / D, r.y / D);
-        P.dlt[g] = dl;
-        P.r[g] = r;
-        P.z[g] = z;
-        v[1] = r.x * z.x + r.y * z.y;
+        const float2 w = apply32_row(P, in, s, lane, g);
+        const float4 u = P.urec32[g];
+        const double2 r = P.r[g];
+        P.w32[g] = w;
+        v[0] = r.x * (double)u.x + r.y * (double)u.y;
+        v[1] = (double)w.x * (double)u.x + (double)w.y * (double)u.y;
         v[2] = r.x * r.x + r.y * r.y;
       });
-      if (!grid_sync(P)) return;
-      // inner test, beta, p = z + beta p (FP32 records)
+    };
+    phase_y(0);
+    if (!grid_sync(P)) return;
+    for (int it = 0;; ++it) {
+      const int cur = it & 1, nxt = cur ^ 1;
       run_phase(P, sm, 0u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
-        const double rz = inst_sum(P, i, 1), rr = inst_sum(P, i, 2);
+        double t[kNQ];
+        inst_sums(P, i, t);
         if (lane == 0) {
           InstState& st = P.state[i];
           const int act = __ldcg(&st.inn[cur]);
-          const bool conv = rr <= itol2 * __ldcg(&st.rr);
-          const bool cap = it + 1 >= P.max_inner;
-          sm.flag[k] = act && !conv && !cap;
-          sm.cb[k] = rz / __ldcg(&st.rho[cur]);
+          const bool conv = t[2] <= itol2 * __ldcg(&st.rr);
+          const bool cap = it >= P.max_inner;
+          const Coeffs cf = cg_coeffs(it, t[0], t[1], it ? __ldcg(&st.rho[cur]) : 0.0,
+                                      it ? __ldcg(&st.alpha[cur]) : 0.0);
+          const bool go = act && !conv && !cap;
+          sm.flag[k] = go;
+          sm.ca[k] = cf.alpha;
+          sm.cb[k] = cf.beta;
           if (owner) {
-            st.inn[nxt] = act && !conv && !cap;
-            st.rho[nxt] = rz;
+            st.inn[nxt] = go;
+            st.rho[nxt] = t[0];
+            st.alpha[nxt] = cf.alpha;
             if (act) {
-              st.inner_iters += 1;
-              if (conv || cap) atomicAdd(P.counters + 2, 1);
+              if (go) {
+                st.inner_iters += 1;
+                st.applies += 1;
+              } else {
+                atomicAdd(P.counters + 2, 1);
+              }
             }
           }
         }
-      }, [&](int64_t g, int64_t, int, int, int k, double*) {
+      }, [&](int64_t g, int64_t, int, int i, int k, double*) {
         if (!sm.flag[k]) return;
-        const double b = sm.cb[k];
-        const double2 z = P.z[g];
-        const float4 p = P.prec32[g];
-        reinterpret_cast<float2*>(P.prec32 + g)[0] =
-            make_float2((float)(z.x + b * (double)p.x), (float)(z.y + b * (double)p.y));
+        const SolveInst& in = P.inst[i];
+        const double a = sm.ca[k], b = sm.cb[k];
+        const float4 u = P.urec32[g];
+        const float2 w = P.w32[g];
+        double2 p = P.pd[g], sv = P.sd[g], dl = P.dlt[g], r = P.r[g];
+        p.x = (double)u.x + b * p.x; p.y = (double)u.y + b * p.y;
+        sv.x = (double)w.x + b * sv.x; sv.y = (double)w.y + b * sv.y;
+        dl.x += a * p.x; dl.y += a * p.y;
+        r.x -= a * sv.x; r.y -= a * sv.y;
+        const double D = jacobi(P, in, g);
+        P.pd[g] = p;
+        P.sd[g] = sv;
+        P.dlt[g] = dl;
+        P.r[g] = r;
+        reinterpret_cast<float2*>(P.urec32 + g)[0] = make_float2((float)(r.x / D), (float)(r.y / D));
       });
       if (!grid_sync(P)) return;
-      if (read_counter(P.counters + 2) >= read_counter(P.counters + 1)) break;
+      if (block_counter(P, 2) >= block_counter(P, 1)) break;
+      phase_y(nxt);
+      if (!grid_sync(P)) return;
     }
     // x += delta
     run_phase(P, sm, 0u, [&](int, const Chunk&, int k, int i, bool, int lane) {
@@ -478,8 +528,7 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
     });
     if (!grid_sync(P)) return;
   }
-  run_phase(P, sm, 0u, [](int, const Chunk&, int, int, bool, int) {},
-            [&](int64_t g, int64_t, int, int i, int, double*) {
+  run_phase(P, sm, 0u, noscal, [&](int64_t g, int64_t, int, int i, int, double*) {
     const SolveInst& in = P.inst[i];
     const int64_t l = g - in.row0;
     if (l < in.rows) in.u[l] = P.xrec[2 * g];
@@ -557,19 +606,20 @@ ss_status work_alloc(SolveWork& W, int64_t rows_total, const int32_t* norm, cuda
   if (W.rows_total == rows_total) return SS_OK;
   W.rows_total = rows_total;
   SS_TRY(W.xrec.alloc(2 * rows_total));
-  SS_TRY(W.prec64.alloc(2 * rows_total));
-  SS_TRY(W.prec32.alloc(rows_total));
+  SS_TRY(W.urec64.alloc(2 * rows_total));
+  SS_TRY(W.urec32.alloc(rows_total));
   SS_TRY(W.r.alloc(rows_total));
-  SS_TRY(W.z.alloc(rows_total));
-  SS_TRY(W.q64.alloc(rows_total));
-  SS_TRY(W.q32.alloc(rows_total));
+  SS_TRY(W.w64.alloc(rows_total));
+  SS_TRY(W.w32.alloc(rows_total));
+  SS_TRY(W.pd.alloc(rows_total));
+  SS_TRY(W.sd.alloc(rows_total));
   SS_TRY(W.rhat.alloc(rows_total));
   SS_TRY(W.dlt.alloc(rows_total));
   SS_TRY(W.bar.alloc(2));
   SS_TRY(W.counters.alloc(4));
   SS_TRY(W.err.alloc(1));
-  k_init_solve_records<<<nblk(rows_total), 256, 0, st>>>(norm, rows_total, W.xrec.get(), W.prec64.get(),
-                                                        W.prec32.get());
+  k_init_solve_records<<<nblk(rows_total), 256, 0, st>>>(norm, rows_total, W.xrec.get(), W.urec64.get(),
+                                                        W.urec32.get());
   SS_LAUNCH_CHECK();
   return SS_OK;
 }
@@ -611,12 +661,13 @@ ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, co
   P.ca32 = ca32;
   P.pn = pn;
   P.xrec = W.xrec.get();
-  P.prec64 = W.prec64.get();
-  P.prec32 = W.prec32.get();
+  P.urec64 = W.urec64.get();
+  P.urec32 = W.urec32.get();
   P.r = W.r.get();
-  P.z = W.z.get();
-  P.q64 = W.q64.get();
-  P.q32 = W.q32.get();
+  P.w64 = W.w64.get();
+  P.w32 = W.w32.get();
+  P.pd = W.pd.get();
+  P.sd = W.sd.get();
   P.rhat = W.rhat.get();
   P.dlt = W.dlt.get();
   P.part = W.part.get();

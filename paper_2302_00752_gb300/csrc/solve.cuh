@@ -23,7 +23,8 @@ struct Chunk {
 };
 
 struct InstState {
-  double rho[2];
+  double rho[2];            // gamma = <r, u> by iteration parity
+  double alpha[2];          // CG step by iteration parity
   double bb;                // ||f||^2
   double rr;                // last residual^2 (FP64 at exit)
   int32_t act[2];           // by iteration parity: CG (FP64) / refinement (FP32) running
@@ -42,15 +43,16 @@ struct SolveParams {
   const double2* ca64;
   const float2* ca32;
   const int32_t* pn;
-  double2* xrec;               // FP64 records (value, norm) of x
-  double2* prec64;             // FP64 records of p
-  float4* prec32;              // FP32 records of p
+  double2* xrec;               // FP64 records (value, norm) of x: gathered for f - L x
+  double2* urec64;             // FP64 records of u = D^-1 r: gathered by the FP64 operator
+  float4* urec32;              // FP32 records of u: gathered by the FP32 operator
   double2* r;
-  double2* z;
-  double2* q64;
-  float2* q32;
-  double2* rhat;
-  double2* dlt;
+  double2* w64;                // L u (FP64 mode)
+  float2* w32;                 // L u (FP32 operator)
+  double2* pd;                 // search direction p
+  double2* sd;                 // s = L p
+  double2* rhat;               // f - L x (refinement)
+  double2* dlt;                // refinement correction
   double* part;                // [slots][kNQ]
   unsigned* bar;               // barrier count, generation
   int* counters;               // done, inner started, inner finished
@@ -76,9 +78,9 @@ struct SolveWork {
     if (ev[0]) cudaEventDestroy(ev[0]);
     if (ev[1]) cudaEventDestroy(ev[1]);
   }
-  DevBuf<double2> xrec, prec64, r, z, q64, rhat, dlt;
-  DevBuf<float4> prec32;
-  DevBuf<float2> q32;
+  DevBuf<double2> xrec, urec64, r, w64, pd, sd, rhat, dlt;
+  DevBuf<float4> urec32;
+  DevBuf<float2> w32;
   DevBuf<double> part;
   DevBuf<unsigned> bar;
   DevBuf<int> counters, err;

@@ -63,6 +63,13 @@ def test_next_prime_against_sieve():
     assert lat.is_prime(2**26 + 15) and all(not lat.is_prime(2**26 + i) for i in range(15))
 
 
+def test_smooth_sizes():
+    assert lat.next_smooth(10**6) == 10**6               # 2^6 5^6
+    assert lat.next_smooth(1000003) == 1000188           # 2^2 3^2 7^3 ... checked by factoring
+    assert lat.is_smooth(1000188) and not lat.is_smooth(1000003)
+    assert [m for m in range(1, 21) if lat.is_smooth(m)] == [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16, 18, 20]
+
+
 def test_random_lattice_size_rule():
     # smallest prime strictly greater than max(K, |I|^2 / sigma)
     assert lat.random_lattice_size(2048, 35, 0.05) == lat.next_prime(24501)
@@ -88,7 +95,8 @@ def test_cbc_lattice_reconstructs():
     I = np.unique(np.vstack([I, -I]), axis=0)
     draws = {"raw": rng.integers(0, 2**62, size=(6, 16)), "M_min": 100000}
     z, M = lat.cbc_lattice(I, draws)
-    assert z[0] == 1 and lat.is_prime(M) and M >= 100000
+    assert z[0] == 1 and lat.is_smooth(M) and M >= 100000
+    assert not any(lat.is_smooth(m) for m in range(100000, M))
     assert pairwise_reconstructing(I, z, M)
     for j in range(1, 6):
         assert pairwise_reconstructing(np.unique(I[:, : j + 1], axis=0), z[: j + 1], M)

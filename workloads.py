@@ -22,7 +22,7 @@ terms with frequencies uniform in a box) scaled to the five configurations the
 benchmarks use:
 
   cfg1  d=2,   s_a=9,  manufactured u (5 pairs in [-6,6]^2), N=2, box lattice
-  cfg2  d=10,  s_a=21, manufactured u (20 pairs in [-8,8]^10), N=3, CBC lattice
+  cfg2  d=10,  s_a=21, manufactured u (20 pairs in [-8,8]^10), N=3, CBC lattice (M >= 1e6)
   cfg3  d=3,   multiscale a (scales 1, 2^6, 2^10), 8 f pairs, N=4
   cfg4  512 instances, d in 6..30, s_a odd in 5..41, 5..30 f pairs, N in {2,3}
   cfg5  d=100, s_a=41, 50 f pairs, 3 nonzero coordinates per frequency, N=3
@@ -185,7 +185,7 @@ def make_cfg1(seed=0):
 
 def make_cfg2(seed=0):
     """d=10, 10 cosines in [-8,8]^10 (sum|c| = 0.5), u with 20 +-pairs in
-    [-8,8]^10, N=3, CBC lattice with M the smallest prime >= 1e6."""
+    [-8,8]^10, N=3, CBC lattice with M >= 1e6."""
     rng = np.random.default_rng(seed)
     d = 10
     p, _ = draw_freqs(rng, 10, d, -8, 8)
