@@ -172,13 +172,13 @@ static ss_status batch_create_impl(ss_batch_s* b, int32_t n, const ss_stamp* sta
   if (b->rows_total > ((int64_t)1 << colbits_of(jb)) || ent / kSlice >= INT32_MAX)
     SS_FAIL(SS_ERR_KEY_RANGE, "batch_create: %lld rows do not fit %d-bit columns", (long long)b->rows_total,
             colbits_of(jb));
-  SS_TRY(b->norm.alloc(b->rows_total));
-  SS_TRY(b->woff.alloc(slices + 1));
-  SS_TRY(b->slice_inst.alloc(slices));
-  SS_TRY(b->ent.alloc(ent + 1));
-  SS_TRY(b->ca64.alloc(coefs));
-  SS_TRY(b->ca32.alloc(coefs));
-  SS_TRY(b->pn.alloc(coefs));
+  SS_TRY(b->norm.alloc(b->rows_total, st));
+  SS_TRY(b->woff.alloc(slices + 1, st));
+  SS_TRY(b->slice_inst.alloc(slices, st));
+  SS_TRY(b->ent.alloc(ent + 1, st));
+  SS_TRY(b->ca64.alloc(coefs, st));
+  SS_TRY(b->ca32.alloc(coefs, st));
+  SS_TRY(b->pn.alloc(coefs, st));
   b->woff_h.assign(slices + 1, 0);
   b->slice_inst_h.assign(slices, 0);
   b->plan.inst.assign(n, SolveInst{});
@@ -218,6 +218,8 @@ static ss_status batch_create_impl(ss_batch_s* b, int32_t n, const ss_stamp* sta
   SS_CUDA(cudaMemsetAsync(b->norm.get() + (b->rows_total - 1), 0, sizeof(int32_t), st));
   SS_TRY(work_alloc(b->work, b->rows_total, b->norm.get(), st));
   SS_CUDA(cudaStreamSynchronize(st));
+  b->norm.settle(); b->woff.settle(); b->slice_inst.settle(); b->ent.settle();
+  b->ca64.settle(); b->ca32.settle(); b->pn.settle();
   return SS_OK;
 }
 

@@ -144,6 +144,45 @@ __global__ void k_cbc_try(const int32_t* __restrict__ f, int64_t n, int d, int j
   if (threadIdx.x == 0) fail[b] = bad;
 }
 
+// Same test with the residues and an open-addressing residue -> row table in
+// shared memory: a row meeting an earlier row with its residue compares their
+// projections (O(n) per candidate instead of all pairs).
+__global__ void k_cbc_try_hash(const int32_t* __restrict__ f, int64_t n, int d, int j, int64_t M,
+                               const int64_t* __restrict__ rho, const int64_t* __restrict__ cand, int cap,
+                               int32_t* fail) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int64_t* rp = reinterpret_cast<int64_t*>(smem);
+  int32_t* tab = reinterpret_cast<int32_t*>(rp + n);
+  __shared__ int bad;
+  const uint64_t z = (uint64_t)cand[blockIdx.x];
+  if (threadIdx.x == 0) bad = 0;
+  for (int i = threadIdx.x; i < cap; i += blockDim.x) tab[i] = -1;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    int64_t k = f[i * d + j] % M;
+    if (k < 0) k += M;
+    rp[i] = (int64_t)(((uint64_t)rho[i] + ((uint64_t)k * z) % (uint64_t)M) % (uint64_t)M);
+  }
+  __syncthreads();
+  const uint32_t mask = (uint32_t)cap - 1;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const int64_t r = rp[i];
+    uint32_t h = (uint32_t)(rhash((uint64_t)r) & mask);
+    for (int probe = 0; probe < cap; ++probe) {
+      const int32_t old = atomicCAS(tab + h, -1, (int32_t)i);
+      if (old == -1) break;
+      if (rp[old] == r) {
+        bool same = true;
+        for (int c = 0; c <= j; ++c) same &= (f[i * d + c] == f[(int64_t)old * d + c]);
+        if (!same) atomicExch(&bad, 1);
+        break;
+      }
+      h = (h + 1) & mask;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) fail[blockIdx.x] = bad;
+}
+
 __global__ void k_cbc_accept(const int32_t* __restrict__ f, int64_t n, int d, int j, int64_t M, int64_t z,
                              int64_t* rho) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -184,8 +223,8 @@ ss_status check_reconstructing(const int32_t* freq, int64_t n, const LatticeDev&
   while (cap < (uint64_t)(2 * n)) cap <<= 1;
   DevBuf<unsigned long long> table;
   DevBuf<int32_t> flags;
-  SS_TRY(table.alloc(cap));
-  SS_TRY(flags.alloc(4));
+  SS_TRY(table.alloc(cap, st));
+  SS_TRY(flags.alloc(4, st));
   SS_CUDA(cudaMemsetAsync(table.get(), 0, cap * sizeof(unsigned long long), st));
   SS_CUDA(cudaMemsetAsync(flags.get(), 0, 4 * sizeof(int32_t), st));
   k_check_insert<<<nblk(n), 256, 0, st>>>(freq, res, n, L.d, table.get(), cap - 1, flags.get());
@@ -204,7 +243,7 @@ ss_status check_reconstructing(const int32_t* freq, int64_t n, const LatticeDev&
 
 static ss_status expansion_of(const int32_t* freq, int64_t n, int d, int64_t* K, cudaStream_t st) {
   DevBuf<int32_t> mm;
-  SS_TRY(mm.alloc(2 * d));
+  SS_TRY(mm.alloc(2 * d, st));
   std::vector<int32_t> init(2 * d);
   for (int c = 0; c < d; ++c) { init[c] = INT32_MAX; init[d + c] = INT32_MIN; }
   SS_CUDA(cudaMemcpyAsync(mm.get(), init.data(), 2 * d * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -238,7 +277,7 @@ extern "C" ss_status lattice_check(const ss_lattice* lat, const int32_t* freq, i
   if (n > 0 && !freq) SS_FAIL(SS_ERR_INVALID, "lattice_check: null frequencies");
   cudaStream_t st = as_stream(stream);
   DevBuf<int64_t> res;
-  SS_TRY(res.alloc(n));
+  SS_TRY(res.alloc(n, st));
   SS_TRY(residues(freq, n, L, res.get(), st));
   return check_reconstructing(freq, n, L, res.get(), false, st);
 }
@@ -253,7 +292,7 @@ extern "C" ss_status lattice_random(const int32_t* freq, int64_t n, int32_t d, d
   SS_TRY(expansion_of(freq, n, d, &K, st));
   SS_TRY(lattice_size(K, n, sigma, M_min, &M));
   DevBuf<int64_t> res;
-  SS_TRY(res.alloc(n));
+  SS_TRY(res.alloc(n, st));
   std::vector<int64_t> z(d);
   for (int a = 0; a < attempts; ++a) {
     for (int c = 0; c < d; ++c) {
@@ -297,10 +336,19 @@ extern "C" ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int6
   }
   DevBuf<int64_t> rho, cand, scratch;
   DevBuf<int32_t> fail;
-  SS_TRY(rho.alloc(n));
-  SS_TRY(cand.alloc(n_cand));
-  SS_TRY(scratch.alloc((size_t)n_cand * n));
-  SS_TRY(fail.alloc(n_cand));
+  SS_TRY(rho.alloc(n, st));
+  SS_TRY(cand.alloc(n_cand, st));
+  int hash_cap = 1;
+  while (hash_cap < 2 * n) hash_cap <<= 1;
+  const size_t hash_smem = (size_t)n * sizeof(int64_t) + (size_t)hash_cap * sizeof(int32_t);
+  if (hash_smem <= 200 * 1024) {
+    if (hash_smem > 48 * 1024)
+      SS_CUDA(cudaFuncSetAttribute(k_cbc_try_hash, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hash_smem));
+    SS_TRY(scratch.alloc(1, st));
+  } else {
+    SS_TRY(scratch.alloc((size_t)n_cand * n, st));
+  }
+  SS_TRY(fail.alloc(n_cand, st));
   SS_CUDA(cudaMemsetAsync(rho.get(), 0, n * sizeof(int64_t), st));
   std::vector<int64_t> z(d, 1), hc(n_cand);
   std::vector<int32_t> hf(n_cand);
@@ -314,7 +362,11 @@ extern "C" ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int6
       hc[c] = 1 + r % (M - 1);
     }
     SS_CUDA(cudaMemcpyAsync(cand.get(), hc.data(), n_cand * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    k_cbc_try<<<n_cand, 256, 0, st>>>(freq, n, d, j, M, rho.get(), cand.get(), scratch.get(), fail.get());
+    if (hash_smem <= 200 * 1024) {
+      k_cbc_try_hash<<<n_cand, 256, hash_smem, st>>>(freq, n, d, j, M, rho.get(), cand.get(), hash_cap, fail.get());
+    } else {
+      k_cbc_try<<<n_cand, 256, 0, st>>>(freq, n, d, j, M, rho.get(), cand.get(), scratch.get(), fail.get());
+    }
     SS_LAUNCH_CHECK();
     SS_CUDA(cudaMemcpyAsync(hf.data(), fail.get(), n_cand * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     SS_CUDA(cudaStreamSynchronize(st));

@@ -7,7 +7,9 @@
 // samples j0 + 256 m (m < kSampPerThread), starts from (j0 q_t) mod M and steps
 // by (256 q_t) mod M.  exp(2 pi i r/M) is the product of two table entries,
 // exp(2 pi i (r >> bl) 2^bl / M) exp(2 pi i (r & (2^bl - 1)) / M), tabulated
-// with sincospi and staged in shared memory when they fit.  The samples are
+// with sincospi and staged in shared memory when they fit; in FP64, for M up
+// to 2^22, one full table exp(2 pi i r / M) (64 MB, L2-resident) replaces the
+// product, so a term costs one gather and two FP64 FMAs.  The samples are
 // real, so the FFT is real-to-complex (bins b > M/2 are conj(X[M-b])).
 #include <cufft.h>
 
@@ -23,6 +25,7 @@ namespace {
 constexpr int kSampThreads = 256;
 constexpr int kSampPerThread = 8;
 constexpr int kTermChunk = 256;
+constexpr int64_t kFullTableMax = 1ll << 22;   // FP64 full table up to 64 MB (stays in the 126 MB L2)
 
 template <typename R> struct C2;
 template <> struct C2<double> { using T = double2; };
@@ -45,6 +48,15 @@ __global__ void k_twiddles(int64_t M, int bl, int64_t H, typename C2<R>::T* lo, 
     hi[i].x = (R)c;
     hi[i].y = (R)s;
   }
+}
+
+// Full table exp(2 pi i r / M), r < M (FP64 path, L2-resident for M <= 4M).
+__global__ void k_twiddles_full(int64_t M, double2* tab) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= M) return;
+  double s, c;
+  sincospi(2.0 * (double)r / (double)M, &s, &c);
+  tab[r] = make_double2(c, s);
 }
 
 // Terms p and -p of a real sum are one term: Re(c e_{-p}) = Re(conj(c) e_p).
@@ -105,7 +117,9 @@ __global__ void k_compact_terms(const int32_t* __restrict__ freq, int64_t n, Lat
 }
 
 
-template <typename R, bool SMEM_TAB, bool REAL>
+// TAB: 0 split tables in shared memory, 1 split tables in global memory,
+//      2 one full table exp(2 pi i r / M) in global memory (L2-resident).
+template <typename R, int TAB, bool REAL>
 __global__ void __launch_bounds__(kSampThreads) k_sample(int64_t M, int bl, int64_t H,
                                                          const typename C2<R>::T* __restrict__ lo_g,
                                                          const typename C2<R>::T* __restrict__ hi_g,
@@ -115,16 +129,16 @@ __global__ void __launch_bounds__(kSampThreads) k_sample(int64_t M, int bl, int6
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t L = 1ll << bl;
   T2* s_lo = reinterpret_cast<T2*>(smem);
-  T2* s_hi = s_lo + (SMEM_TAB ? L : 0);
-  int64_t* s_q = reinterpret_cast<int64_t*>(s_hi + (SMEM_TAB ? H : 0));
+  T2* s_hi = s_lo + (TAB == 0 ? L : 0);
+  int64_t* s_q = reinterpret_cast<int64_t*>(s_hi + (TAB == 0 ? H : 0));
   int64_t* s_step = s_q + kTermChunk;
   T2* s_c = reinterpret_cast<T2*>(s_step + kTermChunk);
-  if (SMEM_TAB) {
+  if (TAB == 0) {
     for (int64_t i = threadIdx.x; i < L; i += blockDim.x) s_lo[i] = lo_g[i];
     for (int64_t i = threadIdx.x; i < H; i += blockDim.x) s_hi[i] = hi_g[i];
   }
-  const T2* lo = SMEM_TAB ? s_lo : lo_g;
-  const T2* hi = SMEM_TAB ? s_hi : hi_g;
+  const T2* lo = TAB == 0 ? s_lo : lo_g;
+  const T2* hi = TAB == 0 ? s_hi : hi_g;
   const uint32_t lmask = (uint32_t)(L - 1);
   const int64_t j0 = (int64_t)blockIdx.x * (kSampThreads * kSampPerThread) + threadIdx.x;
   R acc[kSampPerThread];
@@ -145,18 +159,36 @@ __global__ void __launch_bounds__(kSampThreads) k_sample(int64_t M, int bl, int6
       const uint32_t st = (uint32_t)s_step[t];
       uint32_t r = (uint32_t)(((uint64_t)j0 * (uint64_t)s_q[t]) % (uint64_t)M);
       const T2 c = s_c[t];
+      if (TAB == 2) {
+        uint32_t rr[kSampPerThread];
 #pragma unroll
-      for (int m = 0; m < kSampPerThread; ++m) {
-        const T2 h = hi[r >> bl], l = lo[r & lmask];
-        const R er = h.x * l.x - h.y * l.y;   // cos(2 pi r / M)
-        if (REAL) {
-          acc[m] += c.x * er;
-        } else {
-          const R ei = h.x * l.y + h.y * l.x;   // sin(2 pi r / M)
-          acc[m] += c.x * er - c.y * ei;
+        for (int m = 0; m < kSampPerThread; ++m) {
+          rr[m] = r;
+          r += st;
+          if (r >= (uint32_t)M) r -= (uint32_t)M;
         }
-        r += st;
-        if (r >= (uint32_t)M) r -= (uint32_t)M;
+        T2 e[kSampPerThread];
+#pragma unroll
+        for (int m = 0; m < kSampPerThread; ++m) e[m] = __ldg(lo + rr[m]);
+#pragma unroll
+        for (int m = 0; m < kSampPerThread; ++m) {
+          if (REAL) acc[m] += c.x * e[m].x;
+          else acc[m] += c.x * e[m].x - c.y * e[m].y;
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < kSampPerThread; ++m) {
+          const T2 h = hi[r >> bl], l = lo[r & lmask];
+          const R er = h.x * l.x - h.y * l.y;   // cos(2 pi r / M)
+          if (REAL) {
+            acc[m] += c.x * er;
+          } else {
+            const R ei = h.x * l.y + h.y * l.x;   // sin(2 pi r / M)
+            acc[m] += c.x * er - c.y * ei;
+          }
+          r += st;
+          if (r >= (uint32_t)M) r -= (uint32_t)M;
+        }
       }
     }
   }
@@ -217,7 +249,7 @@ struct SftPlan {
   int64_t H = 0;
   cufftHandle fft = 0;
   bool has_fft = false;
-  DevBuf<unsigned char> samples, spectrum, lo, hi;
+  DevBuf<unsigned char> samples, spectrum, lo, hi, full;   // full: FP64 exp(2 pi i r/M), r < M
   ~SftPlan() {
     if (has_fft) cufftDestroy(fft);
   }
@@ -247,10 +279,10 @@ ss_status get_plan(int64_t M, ss_precision prec, cudaStream_t st, std::shared_pt
   p->H = (M + (1ll << p->bl) - 1) >> p->bl;
   const size_t real_sz = prec == SS_FP64 ? sizeof(double) : sizeof(float);
   const size_t cplx_sz = 2 * real_sz;
-  SS_TRY(p->samples.alloc(M * real_sz));
-  SS_TRY(p->spectrum.alloc((M / 2 + 1) * cplx_sz));
-  SS_TRY(p->lo.alloc((1ll << p->bl) * cplx_sz));
-  SS_TRY(p->hi.alloc(p->H * cplx_sz));
+  SS_TRY(p->samples.alloc(M * real_sz, st));
+  SS_TRY(p->spectrum.alloc((M / 2 + 1) * cplx_sz, st));
+  SS_TRY(p->lo.alloc((1ll << p->bl) * cplx_sz, st));
+  SS_TRY(p->hi.alloc(p->H * cplx_sz, st));
   const int64_t nt = std::max<int64_t>(1ll << p->bl, p->H);
   if (prec == SS_FP64)
     k_twiddles<double><<<nblk(nt), 256, 0, st>>>(M, p->bl, p->H, reinterpret_cast<double2*>(p->lo.get()),
@@ -259,29 +291,37 @@ ss_status get_plan(int64_t M, ss_precision prec, cudaStream_t st, std::shared_pt
     k_twiddles<float><<<nblk(nt), 256, 0, st>>>(M, p->bl, p->H, reinterpret_cast<float2*>(p->lo.get()),
                                                 reinterpret_cast<float2*>(p->hi.get()));
   SS_LAUNCH_CHECK();
+  if (prec == SS_FP64 && M <= kFullTableMax) {
+    SS_TRY(p->full.alloc(M * sizeof(double2), st));
+    k_twiddles_full<<<nblk(M), 256, 0, st>>>(M, reinterpret_cast<double2*>(p->full.get()));
+    SS_LAUNCH_CHECK();
+  }
   const cufftResult r = cufftPlan1d(&p->fft, (int)M, prec == SS_FP64 ? CUFFT_D2Z : CUFFT_R2C, 1);
   if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cufftPlan1d(%lld) failed: %d", (long long)M, (int)r);
   p->has_fft = true;
+  // the plan is cached across calls and streams
+  SS_CUDA(cudaStreamSynchronize(st));
+  p->samples.settle(); p->spectrum.settle(); p->lo.settle(); p->hi.settle(); p->full.settle();
   g_plans.push_front(p);
   while (g_plans.size() > kMaxPlans) g_plans.pop_back();
   *out = p;
   return SS_OK;
 }
 
-template <typename R, bool SMEM>
+template <typename R, int TAB>
 ss_status launch_sample(const SftPlan& P, bool real, unsigned grid, size_t sm, const int64_t* q, const int64_t* step,
                         const double2* coef, int64_t n, void* out, cudaStream_t st) {
   using T2 = typename C2<R>::T;
-  auto lo = reinterpret_cast<const T2*>(P.lo.get());
+  auto lo = reinterpret_cast<const T2*>(TAB == 2 ? P.full.get() : P.lo.get());
   auto hi = reinterpret_cast<const T2*>(P.hi.get());
   if (real) {
-    SS_CUDA(cudaFuncSetAttribute(k_sample<R, SMEM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_sample<R, SMEM, true><<<grid, kSampThreads, sm, st>>>(P.M, P.bl, P.H, lo, hi, q, step, coef, n,
-                                                            reinterpret_cast<R*>(out));
+    SS_CUDA(cudaFuncSetAttribute(k_sample<R, TAB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_sample<R, TAB, true><<<grid, kSampThreads, sm, st>>>(P.M, P.bl, P.H, lo, hi, q, step, coef, n,
+                                                           reinterpret_cast<R*>(out));
   } else {
-    SS_CUDA(cudaFuncSetAttribute(k_sample<R, SMEM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_sample<R, SMEM, false><<<grid, kSampThreads, sm, st>>>(P.M, P.bl, P.H, lo, hi, q, step, coef, n,
-                                                             reinterpret_cast<R*>(out));
+    SS_CUDA(cudaFuncSetAttribute(k_sample<R, TAB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_sample<R, TAB, false><<<grid, kSampThreads, sm, st>>>(P.M, P.bl, P.H, lo, hi, q, step, coef, n,
+                                                            reinterpret_cast<R*>(out));
   }
   SS_LAUNCH_CHECK();
   return SS_OK;
@@ -299,14 +339,14 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
   DevBuf<int64_t> q, step, total;
   DevBuf<int32_t> flag, pos, imag;
   DevBuf<double2> merged, coef;
-  SS_TRY(q.alloc(n));
-  SS_TRY(step.alloc(n));
-  SS_TRY(total.alloc(1));
-  SS_TRY(flag.alloc(n));
-  SS_TRY(pos.alloc(n));
-  SS_TRY(imag.alloc(1));
-  SS_TRY(merged.alloc(n));
-  SS_TRY(coef.alloc(n));
+  SS_TRY(q.alloc(n, st));
+  SS_TRY(step.alloc(n, st));
+  SS_TRY(total.alloc(1, st));
+  SS_TRY(flag.alloc(n, st));
+  SS_TRY(pos.alloc(n, st));
+  SS_TRY(imag.alloc(1, st));
+  SS_TRY(merged.alloc(n, st));
+  SS_TRY(coef.alloc(n, st));
   SS_CUDA(cudaMemsetAsync(imag.get(), 0, sizeof(int32_t), st));
   k_merge_terms<<<nblk(n), 256, 0, st>>>(g->freq, reinterpret_cast<const double2*>(g->coef), n, L.d, flag.get(),
                                          merged.get(), imag.get());
@@ -323,25 +363,27 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
   const bool real = has_imag == 0;
   if (P.prec == SS_FP64) {
     const size_t terms_sm = kTermChunk * (2 * sizeof(int64_t) + sizeof(double2));
+    if (P.full.get())
+      return launch_sample<double, 2>(P, real, grid, terms_sm, q.get(), step.get(), coef.get(), nm, out, st);
     const size_t tab_sm = (Lsz + P.H) * sizeof(double2);
     const bool smem = tab_sm + terms_sm <= 200 * 1024;
     const size_t sm = (smem ? tab_sm : 0) + terms_sm;
-    if (smem) return launch_sample<double, true>(P, real, grid, sm, q.get(), step.get(), coef.get(), nm, out, st);
-    return launch_sample<double, false>(P, real, grid, sm, q.get(), step.get(), coef.get(), nm, out, st);
+    if (smem) return launch_sample<double, 0>(P, real, grid, sm, q.get(), step.get(), coef.get(), nm, out, st);
+    return launch_sample<double, 1>(P, real, grid, sm, q.get(), step.get(), coef.get(), nm, out, st);
   }
   const size_t terms_sm = kTermChunk * (2 * sizeof(int64_t) + sizeof(float2));
   const size_t tab_sm = (Lsz + P.H) * sizeof(float2);
   const bool smem = tab_sm + terms_sm <= 200 * 1024;
   const size_t sm = (smem ? tab_sm : 0) + terms_sm;
-  if (smem) return launch_sample<float, true>(P, real, grid, sm, q.get(), step.get(), coef.get(), nm, out, st);
-  return launch_sample<float, false>(P, real, grid, sm, q.get(), step.get(), coef.get(), nm, out, st);
+  if (smem) return launch_sample<float, 0>(P, real, grid, sm, q.get(), step.get(), coef.get(), nm, out, st);
+  return launch_sample<float, 1>(P, real, grid, sm, q.get(), step.get(), coef.get(), nm, out, st);
 }
 
 ss_status recover_from(const SftPlan& P, const LatticeDev& L, const void* samples, const int32_t* cand, int64_t n_cand,
                        int64_t s_max, double tau, int32_t* freq_out, double* val_out, int64_t* n_out, cudaStream_t st) {
   // reconstructing + symmetric candidate set
   DevBuf<int64_t> res;
-  SS_TRY(res.alloc(n_cand));
+  SS_TRY(res.alloc(n_cand, st));
   SS_TRY(residues(cand, n_cand, L, res.get(), st));
   SS_TRY(check_reconstructing(cand, n_cand, L, res.get(), true, st));
   // FFT
@@ -360,12 +402,12 @@ ss_status recover_from(const SftPlan& P, const LatticeDev& L, const void* sample
   DevBuf<unsigned long long> maxbits;
   DevBuf<int32_t> flag, pos;
   DevBuf<int64_t> total;
-  SS_TRY(val.alloc(n_cand));
-  SS_TRY(mag.alloc(n_cand));
-  SS_TRY(maxbits.alloc(1));
-  SS_TRY(flag.alloc(n_cand));
-  SS_TRY(pos.alloc(n_cand));
-  SS_TRY(total.alloc(1));
+  SS_TRY(val.alloc(n_cand, st));
+  SS_TRY(mag.alloc(n_cand, st));
+  SS_TRY(maxbits.alloc(1, st));
+  SS_TRY(flag.alloc(n_cand, st));
+  SS_TRY(pos.alloc(n_cand, st));
+  SS_TRY(total.alloc(1, st));
   SS_CUDA(cudaMemsetAsync(maxbits.get(), 0, sizeof(unsigned long long), st));
   if (P.prec == SS_FP64)
     k_extract<double2><<<nblk(n_cand), 256, 0, st>>>(cand, n_cand, L, reinterpret_cast<const double2*>(P.spectrum.get()),

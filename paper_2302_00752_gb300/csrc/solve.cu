@@ -605,30 +605,36 @@ ss_status plan_chunks(SolvePlan& plan, const std::vector<int32_t>& woff, const s
 ss_status work_alloc(SolveWork& W, int64_t rows_total, const int32_t* norm, cudaStream_t st) {
   if (W.rows_total == rows_total) return SS_OK;
   W.rows_total = rows_total;
-  SS_TRY(W.xrec.alloc(2 * rows_total));
-  SS_TRY(W.urec64.alloc(2 * rows_total));
-  SS_TRY(W.urec32.alloc(rows_total));
-  SS_TRY(W.r.alloc(rows_total));
-  SS_TRY(W.w64.alloc(rows_total));
-  SS_TRY(W.w32.alloc(rows_total));
-  SS_TRY(W.pd.alloc(rows_total));
-  SS_TRY(W.sd.alloc(rows_total));
-  SS_TRY(W.rhat.alloc(rows_total));
-  SS_TRY(W.dlt.alloc(rows_total));
-  SS_TRY(W.bar.alloc(2));
-  SS_TRY(W.counters.alloc(4));
-  SS_TRY(W.err.alloc(1));
+  SS_TRY(W.xrec.alloc(2 * rows_total, st));
+  SS_TRY(W.urec64.alloc(2 * rows_total, st));
+  SS_TRY(W.urec32.alloc(rows_total, st));
+  SS_TRY(W.r.alloc(rows_total, st));
+  SS_TRY(W.w64.alloc(rows_total, st));
+  SS_TRY(W.w32.alloc(rows_total, st));
+  SS_TRY(W.pd.alloc(rows_total, st));
+  SS_TRY(W.sd.alloc(rows_total, st));
+  SS_TRY(W.rhat.alloc(rows_total, st));
+  SS_TRY(W.dlt.alloc(rows_total, st));
+  SS_TRY(W.bar.alloc(2, st));
+  SS_TRY(W.counters.alloc(4, st));
+  SS_TRY(W.err.alloc(1, st));
   k_init_solve_records<<<nblk(rows_total), 256, 0, st>>>(norm, rows_total, W.xrec.get(), W.urec64.get(),
                                                         W.urec32.get());
   SS_LAUNCH_CHECK();
+  // the workspace is reused by later calls, possibly on other streams
+  SS_CUDA(cudaStreamSynchronize(st));
+  W.xrec.settle(); W.urec64.settle(); W.urec32.settle(); W.r.settle(); W.w64.settle(); W.w32.settle();
+  W.pd.settle(); W.sd.settle(); W.rhat.settle(); W.dlt.settle(); W.bar.settle(); W.counters.settle();
+  W.err.settle();
   return SS_OK;
 }
 
 ss_status work_upload(SolveWork& W, const SolvePlan& plan, cudaStream_t st) {
   const int n_inst = (int)plan.inst.size(), n_chunk = (int)plan.chunk.size();
-  if (n_inst > W.cap_inst) { SS_TRY(W.inst.alloc(n_inst)); SS_TRY(W.state.alloc(n_inst)); W.cap_inst = n_inst; }
-  if (n_chunk > W.cap_chunk) { SS_TRY(W.chunk.alloc(n_chunk)); W.cap_chunk = n_chunk; }
-  if (plan.n_parts > W.cap_parts) { SS_TRY(W.part.alloc(plan.n_parts * kNQ)); W.cap_parts = plan.n_parts; }
+  if (n_inst > W.cap_inst) { SS_TRY(W.inst.alloc(n_inst, st)); SS_TRY(W.state.alloc(n_inst, st)); W.cap_inst = n_inst; }
+  if (n_chunk > W.cap_chunk) { SS_TRY(W.chunk.alloc(n_chunk, st)); W.cap_chunk = n_chunk; }
+  if (plan.n_parts > W.cap_parts) { SS_TRY(W.part.alloc(plan.n_parts * kNQ, st)); W.cap_parts = plan.n_parts; }
+  W.inst.settle(); W.state.settle(); W.chunk.settle(); W.part.settle();   // reused across calls (see read_stats)
   SS_CUDA(cudaMemcpyAsync(W.inst.get(), plan.inst.data(), n_inst * sizeof(SolveInst), cudaMemcpyHostToDevice, st));
   SS_CUDA(cudaMemcpyAsync(W.chunk.get(), plan.chunk.data(), n_chunk * sizeof(Chunk), cudaMemcpyHostToDevice, st));
   return SS_OK;

@@ -42,33 +42,44 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 
 // ----------------------------------------------------------- device memory
 
-// Owning device buffer (cudaMalloc / cudaFree).
+// Keeps freed device memory in the default stream-ordered pool (set once per
+// device) so that repeated builds do not go back to the driver.
+void retain_pool();
+
+// Owning device buffer from the stream-ordered pool: allocated on a stream
+// and freed on the same stream (work queued there before the free still sees
+// the memory).  settle() moves the free to the legacy stream for buffers that
+// outlive the call that made them (the caller synchronised that call's stream).
 template <typename T>
 struct DevBuf {
   T* p = nullptr;
   size_t n = 0;
+  cudaStream_t s = nullptr;
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
     p = nullptr;
     n = 0;
   }
-  ss_status alloc(size_t count) {
+  void settle() { s = nullptr; }
+  ss_status alloc(size_t count, cudaStream_t stream = nullptr) {
     release();
+    retain_pool();
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), stream);
     if (e != cudaSuccess) {
       p = nullptr;
-      set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+      set_error("device allocation of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
       return SS_ERR_OOM;
     }
     n = count;
+    s = stream;
     return SS_OK;
   }
-  ss_status ensure(size_t count) { return count <= n ? SS_OK : alloc(count); }
+  ss_status ensure(size_t count, cudaStream_t stream = nullptr) { return count <= n ? SS_OK : alloc(count, stream); }
   T* get() const { return p; }
 };
 

@@ -349,7 +349,7 @@ uint64_t next_pow2(uint64_t x) {
 static ss_status grow_table(ss_stamp_s* S, int64_t need, const KeyParams& P, cudaStream_t st, int32_t* d_err) {
   const int64_t want = (int64_t)next_pow2((uint64_t)std::max<int64_t>(2 * need, 1024));
   if (want <= S->cap) return SS_OK;
-  SS_TRY(S->table.alloc(want));
+  SS_TRY(S->table.alloc(want, st));
   S->cap = want;
   SS_CUDA(cudaMemsetAsync(S->table.get(), 0xff, want * sizeof(uint64_t), st));
   if (S->size > 0) {
@@ -367,18 +367,18 @@ static ss_status grow_keys(ss_stamp_s* S, int64_t need, cudaStream_t st) {
   DevBuf<uint64_t> k2;
   DevBuf<int8_t> l2;
   DevBuf<int32_t> n2;
-  SS_TRY(k2.alloc(cap * WT));
-  SS_TRY(l2.alloc(cap));
-  SS_TRY(n2.alloc(cap + kSlice + 1));
+  SS_TRY(k2.alloc(cap * WT, st));
+  SS_TRY(l2.alloc(cap, st));
+  SS_TRY(n2.alloc(cap + kSlice + 1, st));
   if (S->size > 0) {
     SS_CUDA(cudaMemcpyAsync(k2.get(), S->keys.get(), S->size * WT * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
     SS_CUDA(cudaMemcpyAsync(l2.get(), S->level.get(), S->size, cudaMemcpyDeviceToDevice, st));
     SS_CUDA(cudaMemcpyAsync(n2.get(), S->norm.get(), S->size * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   }
   SS_CUDA(cudaStreamSynchronize(st));
-  std::swap(S->keys.p, k2.p); std::swap(S->keys.n, k2.n);
-  std::swap(S->level.p, l2.p); std::swap(S->level.n, l2.n);
-  std::swap(S->norm.p, n2.p); std::swap(S->norm.n, n2.n);
+  std::swap(S->keys.p, k2.p); std::swap(S->keys.n, k2.n); std::swap(S->keys.s, k2.s);
+  std::swap(S->level.p, l2.p); std::swap(S->level.n, l2.n); std::swap(S->level.s, l2.s);
+  std::swap(S->norm.p, n2.p); std::swap(S->norm.n, n2.n); std::swap(S->norm.s, n2.s);
   return SS_OK;
 }
 
@@ -394,12 +394,12 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   DevBuf<double2> avs;
   DevBuf<PrepOut> prep;
   DevBuf<int32_t> err;
-  SS_TRY(Fs.alloc(n_f * d));
-  SS_TRY(As.alloc((size_t)s_a * d));
-  SS_TRY(avs.alloc(s_a));
-  SS_TRY(rank.alloc(std::max<int64_t>(n_f, s_a)));
-  SS_TRY(prep.alloc(1));
-  SS_TRY(err.alloc(4));
+  SS_TRY(Fs.alloc(n_f * d, st));
+  SS_TRY(As.alloc((size_t)s_a * d, st));
+  SS_TRY(avs.alloc(s_a, st));
+  SS_TRY(rank.alloc(std::max<int64_t>(n_f, s_a), st));
+  SS_TRY(prep.alloc(1, st));
+  SS_TRY(err.alloc(4, st));
   SS_CUDA(cudaMemsetAsync(err.get(), 0, 4 * sizeof(int32_t), st));
 
   // signed lexicographic order of F and supp a_hat
@@ -449,14 +449,14 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   S->jbits = std::max(jb, 1);
 
   // steps and coefficients in canonical order
-  SS_TRY(S->afreq.alloc((size_t)s_a * d));
+  SS_TRY(S->afreq.alloc((size_t)s_a * d, st));
   SS_CUDA(cudaMemcpyAsync(S->afreq.get(), As.get(), (size_t)s_a * d * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-  SS_TRY(S->aval.alloc(s_a));
+  SS_TRY(S->aval.alloc(s_a, st));
   SS_CUDA(cudaMemcpyAsync(S->aval.get(), avs.get(), s_a * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-  SS_TRY(S->stepkey.alloc((size_t)s_a * L.WT));
-  SS_TRY(S->pnorm.alloc(s_a));
-  SS_TRY(S->ca64.alloc(s_a));
-  SS_TRY(S->ca32.alloc(s_a));
+  SS_TRY(S->stepkey.alloc((size_t)s_a * L.WT, st));
+  SS_TRY(S->pnorm.alloc(s_a, st));
+  SS_TRY(S->ca64.alloc(s_a, st));
+  SS_TRY(S->ca32.alloc(s_a, st));
   SS_DISPATCH_WT(L.WT, (k_steps<WT><<<nblk(s_a), 256, 0, st>>>(P, As.get(), avs.get(), s_a, S->stepkey.get(),
                                                                S->pnorm.get(), S->ca64.get(), S->ca32.get())));
   SS_LAUNCH_CHECK();
@@ -466,7 +466,7 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   SS_TRY(grow_keys(S, n_f, st));
   SS_TRY(grow_table(S, n_f, P, st, err.get()));
   DevBuf<int64_t> zidx;
-  SS_TRY(zidx.alloc(1));
+  SS_TRY(zidx.alloc(1, st));
   SS_CUDA(cudaMemsetAsync(zidx.get(), 0xff, sizeof(int64_t), st));
   SS_DISPATCH_WT(L.WT, (k_level0<WT><<<nblk(n_f), 256, 0, st>>>(P, Fs.get(), n_f, S->keys.get(), S->level.get(),
                                                                 S->norm.get(), S->table.get(),
@@ -478,7 +478,7 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   // levels 1..N
   DevBuf<int64_t> slot_of, d_total;
   DevBuf<int32_t> flag;
-  SS_TRY(d_total.alloc(1));
+  SS_TRY(d_total.alloc(1, st));
   for (int n = 1; n <= N; ++n) {
     const int64_t par0 = S->level_start[n - 1], n_par = S->level_start[n] - par0;
     const int64_t ncand = n_par * s_a;
@@ -486,15 +486,15 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
     if (ncand == 0) { S->level_start.push_back(S->size); continue; }
     SS_TRY(grow_table(S, S->size + n_par * (s_a - 1), P, st, err.get()));
     SS_TRY(grow_keys(S, S->size + n_par * (s_a - 1), st));
-    SS_TRY(slot_of.ensure(ncand));
-    SS_TRY(flag.ensure(ncand));
+    SS_TRY(slot_of.ensure(ncand, st));
+    SS_TRY(flag.ensure(ncand, st));
     SS_DISPATCH_WT(L.WT, (k_insert<WT><<<nblk(ncand), 256, 0, st>>>(P, S->keys.get(), par0, n_par, s_a, S->j0,
                                                                     S->stepkey.get(), S->table.get(),
                                                                     (uint64_t)S->cap - 1, slot_of.get(), err.get())));
     k_winner_flags<<<nblk(ncand), 256, 0, st>>>(slot_of.get(), S->table.get(), ncand, flag.get());
     SS_LAUNCH_CHECK();
     DevBuf<int32_t> pos;
-    SS_TRY(pos.alloc(ncand));
+    SS_TRY(pos.alloc(ncand, st));
     SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), ncand, d_total.get(), st));
     int64_t added = 0;
     int32_t e = 0;
@@ -524,9 +524,9 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   SS_CUDA(cudaStreamSynchronize(st));
   DevBuf<int32_t> nbr, slice_w;
   DevBuf<unsigned long long> d_nnz;
-  SS_TRY(nbr.alloc((size_t)S->size * s_a));
-  SS_TRY(slice_w.alloc(S->n_slices + 1));
-  SS_TRY(d_nnz.alloc(1));
+  SS_TRY(nbr.alloc((size_t)S->size * s_a, st));
+  SS_TRY(slice_w.alloc(S->n_slices + 1, st));
+  SS_TRY(d_nnz.alloc(1, st));
   SS_CUDA(cudaMemsetAsync(d_nnz.get(), 0, sizeof(unsigned long long), st));
   SS_CUDA(cudaMemsetAsync(slice_w.get(), 0, (S->n_slices + 1) * sizeof(int32_t), st));
   SS_DISPATCH_WT(L.WT, (k_neighbors<WT><<<nblk(S->size * s_a), 256, 0, st>>>(
@@ -534,7 +534,7 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
                            S->zero_idx, nbr.get())));
   k_row_counts<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, slice_w.get(), d_nnz.get());
   SS_LAUNCH_CHECK();
-  SS_TRY(S->slice_off.alloc(S->n_slices + 1));
+  SS_TRY(S->slice_off.alloc(S->n_slices + 1, st));
   SS_TRY(exclusive_scan_i32(slice_w.get(), S->slice_off.get(), S->n_slices + 1, d_total.get(), st));
   int64_t total_w = 0;
   unsigned long long hnnz = 0;
@@ -543,12 +543,12 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   SS_CUDA(cudaStreamSynchronize(st));
   S->nnz = (int64_t)hnnz;
   S->n_ent = total_w * kSlice;
-  SS_TRY(S->ent.alloc(S->n_ent + 1));
+  SS_TRY(S->ent.alloc(S->n_ent + 1, st));
   k_fill_slices<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, S->j0, S->slice_off.get(),
                                                    colbits_of(S->jbits), S->ent.get());
   SS_LAUNCH_CHECK();
-  SS_TRY(S->rec32.alloc(S->rows_pad + 1));
-  SS_TRY(S->rec64.alloc(2 * (S->rows_pad + 1)));
+  SS_TRY(S->rec32.alloc(S->rows_pad + 1, st));
+  SS_TRY(S->rec64.alloc(2 * (S->rows_pad + 1), st));
   k_init_records<<<nblk(S->rows_pad + 1), 256, 0, st>>>(S->norm.get(), S->rows_pad + 1, S->rec32.get(),
                                                         S->rec64.get());
   SS_LAUNCH_CHECK();
@@ -556,6 +556,11 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   SS_CUDA(cudaMemcpyAsync(&e, err.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   SS_CUDA(cudaStreamSynchronize(st));
   if (e) SS_FAIL((ss_status)e, "stamp_build: hash table exhausted");
+  // the stamp's buffers outlive this call's stream (synchronised above)
+  S->keys.settle(); S->level.settle(); S->norm.settle(); S->table.settle();
+  S->afreq.settle(); S->stepkey.settle(); S->pnorm.settle(); S->aval.settle();
+  S->ca64.settle(); S->ca32.settle(); S->slice_off.settle(); S->ent.settle();
+  S->rec32.settle(); S->rec64.settle();
   return SS_OK;
 }
 
@@ -632,8 +637,8 @@ extern "C" ss_status stamp_scatter(ss_stamp s, const ss_sparse* g, double* out, 
   }
   DevBuf<int64_t> idx;
   DevBuf<unsigned long long> outside;
-  SS_TRY(idx.alloc(g->n));
-  SS_TRY(outside.alloc(1));
+  SS_TRY(idx.alloc(g->n, st));
+  SS_TRY(outside.alloc(1, st));
   SS_CUDA(cudaMemsetAsync(outside.get(), 0, sizeof(unsigned long long), st));
   SS_TRY(stamp_lookup(s, g->freq, g->n, idx.get(), stream));
   k_scatter_vals<<<nblk(g->n), 256, 0, st>>>(idx.get(), reinterpret_cast<const double2*>(g->val), g->n,
