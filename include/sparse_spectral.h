@@ -207,6 +207,11 @@ ss_status galerkin_apply(ss_stamp s, const void* u, void* y, ss_precision prec, 
 ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, double tol, int32_t max_iter,
                 ss_precision prec, ss_solve_stats* stats, void* stream);
 
+/* Tile shape of this stamp's persistent solve: threads per block (128, 256,
+ * 512 or 1024), resident blocks per SM (0 = as many as fit) and static work
+ * chunks per block.  Takes effect at the next solve.  Default 1024, 1, 1. */
+ss_status solve_set_config(ss_stamp s, int32_t block, int32_t blocks_per_sm, int32_t chunks_per_block);
+
 /* Many instances in one persistent launch: the rows of all instances are
  * concatenated, every CG phase runs over all of them with per-instance scalars,
  * and converged instances drop out.  batch_create copies the instances'
@@ -232,8 +237,8 @@ ss_status batch_autotune(ss_batch b, const double* const* f, double* const* u, d
 ss_status batch_config(ss_batch b, int32_t* block, int32_t* blocks_per_sm, int32_t* chunks_per_block,
                        int32_t* grid, int32_t* n_chunks);
 
-/* Set the tile shape: block in {128, 256, 512} threads, blocks_per_sm (0 = as
- * many as fit), chunks_per_block >= 1 (static work units per block). */
+/* Set the tile shape: block in {128, 256, 512, 1024} threads, blocks_per_sm
+ * (0 = as many as fit), chunks_per_block >= 1 (static work units per block). */
 ss_status batch_set_config(ss_batch b, int32_t block, int32_t blocks_per_sm, int32_t chunks_per_block);
 
 void batch_destroy(ss_batch b);

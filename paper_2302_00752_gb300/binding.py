@@ -76,6 +76,7 @@ def _load():
         "stamp_destroy": (None, [vp]),
         "galerkin_apply": (i32, [vp, vp, vp, i32, vp]),
         "solve": (i32, [vp, vp, vp, dbl, i32, i32, P(SolveStats), vp]),
+        "solve_set_config": (i32, [vp, i32, i32, i32]),
         "batch_create": (i32, [i32, P(vp), P(vp), vp]),
         "batch_solve": (i32, [vp, P(vp), P(vp), dbl, i32, i32, i32, P(SolveStats), vp]),
         "batch_autotune": (i32, [vp, P(vp), P(vp), dbl, i32, i32, P(dbl), vp]),
@@ -264,6 +265,10 @@ class Stamp:
         outside = C.c_int64()
         _check(lib.stamp_scatter(self.handle, C.byref(sp), _ptr(out), C.byref(outside), _stream()))
         return out, outside.value
+
+    def set_solve_config(self, block, blocks_per_sm, chunks_per_block):
+        """Tile shape of the persistent solve (see solve_set_config)."""
+        _check(lib.solve_set_config(self.handle, int(block), int(blocks_per_sm), int(chunks_per_block)))
 
     def destroy(self):
         if self._h:

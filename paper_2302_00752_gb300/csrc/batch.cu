@@ -26,7 +26,7 @@ struct ss_batch_s {
   ss::SolvePlan plan;
   ss::SolveWork work;
   // tile shape
-  int block = 256, blocks_per_sm = 0, chunks_per_block = 1;
+  int block = 1024, blocks_per_sm = 1, chunks_per_block = 1;
   bool planned = false;
   int planned_mode = -1;
   // graph
@@ -262,7 +262,7 @@ extern "C" ss_status batch_autotune(ss_batch b, const double* const* f, double* 
   cudaStream_t st = as_stream(stream);
   SS_TRY(set_pointers(b, f, u));
   struct Cfg { int block, bps, cpb; };
-  const Cfg cands[] = {{256, 0, 1}, {256, 1, 1}, {128, 0, 1}, {512, 0, 1}, {256, 0, 2}, {128, 0, 2}, {512, 1, 1}};
+  const Cfg cands[] = {{1024, 1, 1}, {1024, 1, 2}, {512, 2, 1}, {512, 1, 1}, {256, 0, 1}, {256, 4, 2}, {128, 0, 2}};
   cudaEvent_t e0, e1;
   SS_CUDA(cudaEventCreate(&e0));
   SS_CUDA(cudaEventCreate(&e1));
@@ -316,8 +316,9 @@ extern "C" ss_status batch_config(ss_batch b, int32_t* block, int32_t* blocks_pe
 }
 
 extern "C" ss_status batch_set_config(ss_batch b, int32_t block, int32_t blocks_per_sm, int32_t chunks_per_block) {
-  if (!b || (block != 128 && block != 256 && block != 512) || blocks_per_sm < 0 || chunks_per_block < 1)
-    SS_FAIL(SS_ERR_INVALID, "batch_set_config: block must be 128, 256 or 512; blocks_per_sm >= 0; chunks >= 1");
+  if (!b || (block != 128 && block != 256 && block != 512 && block != 1024) || blocks_per_sm < 0 ||
+      chunks_per_block < 1)
+    SS_FAIL(SS_ERR_INVALID, "batch_set_config: block in {128,256,512,1024}, blocks_per_sm >= 0, chunks >= 1");
   b->block = block;
   b->blocks_per_sm = blocks_per_sm;
   b->chunks_per_block = chunks_per_block;

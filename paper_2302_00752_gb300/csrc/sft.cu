@@ -7,11 +7,16 @@
 // samples j0 + 256 m (m < kSampPerThread), starts from (j0 q_t) mod M and steps
 // by (256 q_t) mod M.  exp(2 pi i r/M) is the product of two table entries,
 // exp(2 pi i (r >> bl) 2^bl / M) exp(2 pi i (r & (2^bl - 1)) / M), tabulated
-// with sincospi and staged in shared memory when they fit; in FP64, for M up
-// to 2^22, one full table exp(2 pi i r / M) (64 MB, L2-resident) replaces the
-// product, so a term costs one gather and two FP64 FMAs.  The samples are
+// with sincospi and staged in shared memory when they fit.  In FP64 mode, for M
+// up to 2^22, one full table exp(2 pi i r / M) (64 MB, L2-resident) replaces the
+// product and the sum runs in double-float arithmetic (pairs of floats with
+// error-free transformations, ~2^-48 relative) on the FP32 pipes: a term costs
+// one 16-byte gather and ~15 (real) or ~30 (complex) FP32 operations instead of
+// FP64 instructions, which GB300 issues at one per SM clock.  The samples are
 // real, so the FFT is real-to-complex (bins b > M/2 are conj(X[M-b])).
 #include <cufft.h>
+
+#include <cstdlib>
 
 #include <list>
 #include <memory>
@@ -47,6 +52,98 @@ __global__ void k_twiddles(int64_t M, int bl, int64_t H, typename C2<R>::T* lo, 
     sincospi(2.0 * (double)r / (double)M, &s, &c);
     hi[i].x = (R)c;
     hi[i].y = (R)s;
+  }
+}
+
+// Double-float arithmetic (an unevaluated sum hi + lo of two floats, ~48-bit
+// significand) from the error-free transformations TwoSum (Knuth) and the
+// FMA-based TwoProd (Ogita, Rump and Oishi, "Accurate sum and dot product",
+// 2005).  The _rn intrinsics keep the compiler from contracting or reordering.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_split(double x) {
+  const float h = (float)x;
+  return DF{h, (float)(x - (double)h)};
+}
+
+// acc += a * b with a, b double-float; the product error and the sum error are
+// kept exactly (up to the dropped lo*lo term), then acc is renormalised.
+__device__ __forceinline__ void df_fma(DF& acc, const DF a, const DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float s = __fadd_rn(acc.hi, p);
+  const float bb = __fsub_rn(s, acc.hi);
+  const float t = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  const float lo = __fadd_rn(__fadd_rn(acc.lo, t), e);
+  const float hi = __fadd_rn(s, lo);
+  acc.lo = __fsub_rn(lo, __fsub_rn(hi, s));
+  acc.hi = hi;
+}
+
+// Full double-float table (cos_hi, cos_lo, sin_hi, sin_lo)(2 pi r / M), r < M.
+__global__ void k_twiddles_df(int64_t M, float4* tab) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= M) return;
+  double s, c;
+  sincospi(2.0 * (double)r / (double)M, &s, &c);
+  const DF cc = df_split(c), ss = df_split(s);
+  tab[r] = make_float4(cc.hi, cc.lo, ss.hi, ss.lo);
+}
+
+// Lattice evaluation in double-float for the FP64 path (see the file comment).
+template <bool REAL>
+__global__ void __launch_bounds__(kSampThreads) k_sample_df(int64_t M, const float4* __restrict__ tab,
+                                                            const int64_t* __restrict__ q,
+                                                            const int64_t* __restrict__ step,
+                                                            const double2* __restrict__ coef, int64_t n_terms,
+                                                            double* out) {
+  __shared__ int64_t s_q[kTermChunk], s_step[kTermChunk];
+  __shared__ float4 s_c[kTermChunk];
+  const int64_t j0 = (int64_t)blockIdx.x * (kSampThreads * kSampPerThread) + threadIdx.x;
+  DF acc[kSampPerThread];
+#pragma unroll
+  for (int m = 0; m < kSampPerThread; ++m) acc[m] = DF{0.f, 0.f};
+  for (int64_t t0 = 0; t0 < n_terms; t0 += kTermChunk) {
+    const int tc = (n_terms - t0 < kTermChunk) ? (int)(n_terms - t0) : kTermChunk;
+    __syncthreads();
+    for (int i = threadIdx.x; i < tc; i += blockDim.x) {
+      s_q[i] = q[t0 + i];
+      s_step[i] = step[t0 + i];
+      const double2 c = coef[t0 + i];
+      const DF cx = df_split(c.x), cy = df_split(-c.y);
+      s_c[i] = make_float4(cx.hi, cx.lo, cy.hi, cy.lo);
+    }
+    __syncthreads();
+    for (int t = 0; t < tc; ++t) {
+      const uint32_t st = (uint32_t)s_step[t];
+      uint32_t r = (uint32_t)(((uint64_t)j0 * (uint64_t)s_q[t]) % (uint64_t)M);
+      const float4 c = s_c[t];
+      uint32_t rr[kSampPerThread];
+#pragma unroll
+      for (int m = 0; m < kSampPerThread; ++m) {
+        rr[m] = r;
+        r += st;
+        if (r >= (uint32_t)M) r -= (uint32_t)M;
+      }
+      float4 e[kSampPerThread];
+#pragma unroll
+      for (int m = 0; m < kSampPerThread; ++m) e[m] = __ldg(tab + rr[m]);
+#pragma unroll
+      for (int m = 0; m < kSampPerThread; ++m) {
+        // Re(c e^{i theta}) = c.re cos(theta) - c.im sin(theta)
+        df_fma(acc[m], DF{c.x, c.y}, DF{e[m].x, e[m].y});
+        if (!REAL) df_fma(acc[m], DF{c.z, c.w}, DF{e[m].z, e[m].w});
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < kSampPerThread; ++m) {
+    const int64_t j = j0 + (int64_t)m * kSampThreads;
+    if (j < M) out[j] = (double)acc[m].hi + (double)acc[m].lo;
   }
 }
 
@@ -249,11 +346,23 @@ struct SftPlan {
   int64_t H = 0;
   cufftHandle fft = 0;
   bool has_fft = false;
-  DevBuf<unsigned char> samples, spectrum, lo, hi, full;   // full: FP64 exp(2 pi i r/M), r < M
+  DevBuf<unsigned char> samples, spectrum, lo, hi, full;   // full: exp(2 pi i r/M), r < M
+  bool df = false;                                         // full table in double-float form
   ~SftPlan() {
     if (has_fft) cufftDestroy(fft);
   }
 };
+
+// The FP64 path evaluates samples in double-float on the FP32 pipes (GB300
+// issues one FP64 FMA per SM clock, 1/128 of its FP32 rate).  Setting
+// SS_NATIVE_FP64_SAMPLING=1 selects native FP64 arithmetic instead.
+bool native_fp64_sampling() {
+  static const bool v = [] {
+    const char* e = getenv("SS_NATIVE_FP64_SAMPLING");
+    return e && e[0] == '1';
+  }();
+  return v;
+}
 
 std::mutex g_plan_mu;
 std::list<std::shared_ptr<SftPlan>> g_plans;   // most recent first
@@ -292,9 +401,13 @@ ss_status get_plan(int64_t M, ss_precision prec, cudaStream_t st, std::shared_pt
                                                 reinterpret_cast<float2*>(p->hi.get()));
   SS_LAUNCH_CHECK();
   if (prec == SS_FP64 && M <= kFullTableMax) {
-    SS_TRY(p->full.alloc(M * sizeof(double2), st));
-    k_twiddles_full<<<nblk(M), 256, 0, st>>>(M, reinterpret_cast<double2*>(p->full.get()));
+    SS_TRY(p->full.alloc(M * sizeof(double2), st));   // 16 bytes per entry in either form
+    if (native_fp64_sampling())
+      k_twiddles_full<<<nblk(M), 256, 0, st>>>(M, reinterpret_cast<double2*>(p->full.get()));
+    else
+      k_twiddles_df<<<nblk(M), 256, 0, st>>>(M, reinterpret_cast<float4*>(p->full.get()));
     SS_LAUNCH_CHECK();
+    p->df = !native_fp64_sampling();
   }
   const cufftResult r = cufftPlan1d(&p->fft, (int)M, prec == SS_FP64 ? CUFFT_D2Z : CUFFT_R2C, 1);
   if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cufftPlan1d(%lld) failed: %d", (long long)M, (int)r);
@@ -363,6 +476,17 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
   const bool real = has_imag == 0;
   if (P.prec == SS_FP64) {
     const size_t terms_sm = kTermChunk * (2 * sizeof(int64_t) + sizeof(double2));
+    if (P.full.get() && P.df) {
+      auto tab = reinterpret_cast<const float4*>(P.full.get());
+      if (real)
+        k_sample_df<true><<<grid, kSampThreads, 0, st>>>(P.M, tab, q.get(), step.get(), coef.get(), nm,
+                                                         reinterpret_cast<double*>(out));
+      else
+        k_sample_df<false><<<grid, kSampThreads, 0, st>>>(P.M, tab, q.get(), step.get(), coef.get(), nm,
+                                                          reinterpret_cast<double*>(out));
+      SS_LAUNCH_CHECK();
+      return SS_OK;
+    }
     if (P.full.get())
       return launch_sample<double, 2>(P, real, grid, terms_sm, q.get(), step.get(), coef.get(), nm, out, st);
     const size_t tab_sm = (Lsz + P.H) * sizeof(double2);

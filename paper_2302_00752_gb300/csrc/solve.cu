@@ -15,8 +15,9 @@
 // Modes
 //   FP64  plain CG on the FP64 operator.
 //   FP32  iterative refinement: r = f - L x with the FP64 operator, then CG on
-//         the FP32 operator (FP32 values and accumulation; FP64 vectors and
-//         scalars) to a relative reduction inner_tol, then x += delta.
+//         the FP32 operator with FP32 vectors (inner products reduced in FP64,
+//         FP64 scalars) to a relative reduction inner_tol, then x += delta in
+//         FP64.
 // The Jacobi preconditioner is D_k = 4 pi^2 Re(a_hat_0) |k|^2 (the diagonal of L),
 // 1 on the zero row and on padding rows.
 #include <algorithm>
@@ -195,6 +196,11 @@ __device__ void run_phase(const SolveParams& P, Smem& sm, unsigned qmask, Scal s
 __device__ __forceinline__ double jacobi(const SolveParams& P, const SolveInst& in, int64_t g) {
   const int32_t nk = __ldg(P.norm + g);
   return nk > 0 ? in.dscale * (double)nk : 1.0;
+}
+
+__device__ __forceinline__ float jacobi32(const SolveParams& P, const SolveInst& in, int64_t g) {
+  const int32_t nk = __ldg(P.norm + g);
+  return nk > 0 ? (float)in.dscale * (float)nk : 1.0f;
 }
 
 __device__ __forceinline__ double2 f_at(const SolveInst& in, int64_t g) {
@@ -405,7 +411,7 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
       v[2] = r.x * r.x + r.y * r.y;
     });
     if (!grid_sync(P)) return;
-    // outer test; inner start: r = rhat, delta = 0, u = D^-1 r (FP32 records), p = s = 0
+    // outer test; inner start (all FP32): r = rhat, delta = 0, u = D^-1 r, p = s = 0
     run_phase(P, sm, 0u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
       double t[kNQ];
       inst_sums(P, i, t);
@@ -434,17 +440,19 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
     }, [&](int64_t g, int64_t, int, int i, int k, double*) {
       if (!sm.flag[k]) return;
       const SolveInst& in = P.inst[i];
-      const double2 r = P.rhat[g];
-      const double D = jacobi(P, in, g);
-      P.r[g] = r;
-      P.dlt[g] = make_double2(0.0, 0.0);
-      P.pd[g] = make_double2(0.0, 0.0);
-      P.sd[g] = make_double2(0.0, 0.0);
-      reinterpret_cast<float2*>(P.urec32 + g)[0] = make_float2((float)(r.x / D), (float)(r.y / D));
+      const double2 rh = P.rhat[g];
+      const float2 r = make_float2((float)rh.x, (float)rh.y);
+      const float rD = 1.0f / jacobi32(P, in, g);
+      P.r32[g] = r;
+      P.d32[g] = make_float2(0.f, 0.f);
+      P.p32[g] = make_float2(0.f, 0.f);
+      P.s32[g] = make_float2(0.f, 0.f);
+      reinterpret_cast<float2*>(P.urec32 + g)[0] = make_float2(r.x * rD, r.y * rD);
     });
     if (!grid_sync(P)) return;
     if (block_counter(P, 0) >= P.n_inst) break;
-    // inner CG on the FP32 operator
+    // inner CG on the FP32 operator with FP32 vectors; inner products are
+    // formed per row in FP32 and reduced in FP64, scalars stay FP64
     auto phase_y = [&](int par) {
       run_phase(P, sm, 0b0111u, [&](int, const Chunk&, int k, int i, bool, int lane) {
         if (lane == 0) sm.flag[k] = __ldcg(&P.state[i].inn[par]);
@@ -453,11 +461,11 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
         const SolveInst& in = P.inst[i];
         const float2 w = apply32_row(P, in, s, lane, g);
         const float4 u = P.urec32[g];
-        const double2 r = P.r[g];
+        const float2 r = P.r32[g];
         P.w32[g] = w;
-        v[0] = r.x * (double)u.x + r.y * (double)u.y;
-        v[1] = (double)w.x * (double)u.x + (double)w.y * (double)u.y;
-        v[2] = r.x * r.x + r.y * r.y;
+        v[0] = (double)(r.x * u.x + r.y * u.y);
+        v[1] = (double)(w.x * u.x + w.y * u.y);
+        v[2] = (double)(r.x * r.x + r.y * r.y);
       });
     };
     phase_y(0);
@@ -495,20 +503,20 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
       }, [&](int64_t g, int64_t, int, int i, int k, double*) {
         if (!sm.flag[k]) return;
         const SolveInst& in = P.inst[i];
-        const double a = sm.ca[k], b = sm.cb[k];
+        const float a = (float)sm.ca[k], b = (float)sm.cb[k];
         const float4 u = P.urec32[g];
         const float2 w = P.w32[g];
-        double2 p = P.pd[g], sv = P.sd[g], dl = P.dlt[g], r = P.r[g];
-        p.x = (double)u.x + b * p.x; p.y = (double)u.y + b * p.y;
-        sv.x = (double)w.x + b * sv.x; sv.y = (double)w.y + b * sv.y;
-        dl.x += a * p.x; dl.y += a * p.y;
-        r.x -= a * sv.x; r.y -= a * sv.y;
-        const double D = jacobi(P, in, g);
-        P.pd[g] = p;
-        P.sd[g] = sv;
-        P.dlt[g] = dl;
-        P.r[g] = r;
-        reinterpret_cast<float2*>(P.urec32 + g)[0] = make_float2((float)(r.x / D), (float)(r.y / D));
+        float2 p = P.p32[g], sv = P.s32[g], dl = P.d32[g], r = P.r32[g];
+        p.x = fmaf(b, p.x, u.x); p.y = fmaf(b, p.y, u.y);
+        sv.x = fmaf(b, sv.x, w.x); sv.y = fmaf(b, sv.y, w.y);
+        dl.x = fmaf(a, p.x, dl.x); dl.y = fmaf(a, p.y, dl.y);
+        r.x = fmaf(-a, sv.x, r.x); r.y = fmaf(-a, sv.y, r.y);
+        const float rD = 1.0f / jacobi32(P, in, g);
+        P.p32[g] = p;
+        P.s32[g] = sv;
+        P.d32[g] = dl;
+        P.r32[g] = r;
+        reinterpret_cast<float2*>(P.urec32 + g)[0] = make_float2(r.x * rD, r.y * rD);
       });
       if (!grid_sync(P)) return;
       if (block_counter(P, 2) >= block_counter(P, 1)) break;
@@ -521,9 +529,9 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
     }, [&](int64_t g, int64_t, int, int, int k, double*) {
       if (!sm.flag[k]) return;
       double2 x = P.xrec[2 * g];
-      const double2 dl = P.dlt[g];
-      x.x += dl.x;
-      x.y += dl.y;
+      const float2 dl = P.d32[g];
+      x.x += (double)dl.x;
+      x.y += (double)dl.y;
       P.xrec[2 * g] = x;
     });
     if (!grid_sync(P)) return;
@@ -536,7 +544,7 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(512) k_solve(SolveParams P) {
+__global__ void __launch_bounds__(1024) k_solve(SolveParams P) {
   __shared__ Smem sm;
   if (MODE == 0) solve_fp64(P, sm);
   else solve_refined(P, sm);
@@ -615,6 +623,10 @@ ss_status work_alloc(SolveWork& W, int64_t rows_total, const int32_t* norm, cuda
   SS_TRY(W.sd.alloc(rows_total, st));
   SS_TRY(W.rhat.alloc(rows_total, st));
   SS_TRY(W.dlt.alloc(rows_total, st));
+  SS_TRY(W.r32.alloc(rows_total, st));
+  SS_TRY(W.p32.alloc(rows_total, st));
+  SS_TRY(W.s32.alloc(rows_total, st));
+  SS_TRY(W.d32.alloc(rows_total, st));
   SS_TRY(W.bar.alloc(2, st));
   SS_TRY(W.counters.alloc(4, st));
   SS_TRY(W.err.alloc(1, st));
@@ -625,7 +637,7 @@ ss_status work_alloc(SolveWork& W, int64_t rows_total, const int32_t* norm, cuda
   SS_CUDA(cudaStreamSynchronize(st));
   W.xrec.settle(); W.urec64.settle(); W.urec32.settle(); W.r.settle(); W.w64.settle(); W.w32.settle();
   W.pd.settle(); W.sd.settle(); W.rhat.settle(); W.dlt.settle(); W.bar.settle(); W.counters.settle();
-  W.err.settle();
+  W.err.settle(); W.r32.settle(); W.p32.settle(); W.s32.settle(); W.d32.settle();
   return SS_OK;
 }
 
@@ -676,6 +688,10 @@ ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, co
   P.sd = W.sd.get();
   P.rhat = W.rhat.get();
   P.dlt = W.dlt.get();
+  P.r32 = W.r32.get();
+  P.p32 = W.p32.get();
+  P.s32 = W.s32.get();
+  P.d32 = W.d32.get();
   P.part = W.part.get();
   P.bar = W.bar.get();
   P.counters = W.counters.get();
@@ -750,6 +766,7 @@ struct ss_solve_ctx {
   ss::SolveWork work;
   ss::SolvePlan plan;
   int planned_mode = -1;
+  int block = 1024, blocks_per_sm = 1, chunks_per_block = 1;   // tile shape (solve_set_config)
 };
 
 namespace ss {
@@ -768,10 +785,11 @@ static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream
   in.coef_off = 0;
   in.dscale = 2.0 * kTwoPiSq * s->a0;   // 4 pi^2 Re(a_hat_0)
   int grid = 0;
-  C.plan.block = 256;
+  C.plan.block = C.block;
   SS_TRY(max_grid(mode, C.plan.block, &grid));
+  if (C.blocks_per_sm > 0) grid = std::min(grid, C.blocks_per_sm * sm_count());
   const int by_size = (int)std::max<int64_t>(1, s->n_slices / 8);   // at least 8 slices per chunk
-  const int target = std::min(grid, by_size);
+  const int target = std::min<int64_t>((int64_t)grid * C.chunks_per_block, by_size);
   SS_TRY(plan_chunks(C.plan, woff, {}, target));
   C.plan.grid = std::min<int>(grid, (int)C.plan.chunk.size());
   SS_TRY(work_alloc(C.work, s->rows_pad + 1, s->norm.get(), st));
@@ -802,6 +820,25 @@ void drop_solve_ctx(const ss_stamp_s* s) {
 }
 }  // namespace ss
 
+static ss_solve_ctx* solve_ctx(const ss_stamp_s* s) {
+  std::lock_guard<std::mutex> lk(g_ctx_mu);
+  auto& slot = g_ctx[s];
+  if (!slot) slot = new ss_solve_ctx();
+  return slot;
+}
+
+extern "C" ss_status solve_set_config(ss_stamp s, int32_t block, int32_t blocks_per_sm, int32_t chunks_per_block) {
+  if (!s || (block != 128 && block != 256 && block != 512 && block != 1024) || blocks_per_sm < 0 ||
+      chunks_per_block < 1)
+    SS_FAIL(SS_ERR_INVALID, "solve_set_config: block in {128,256,512,1024}, blocks_per_sm >= 0, chunks >= 1");
+  ss_solve_ctx* C = solve_ctx(s);
+  C->block = block;
+  C->blocks_per_sm = blocks_per_sm;
+  C->chunks_per_block = chunks_per_block;
+  C->planned_mode = -1;
+  return SS_OK;
+}
+
 extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, double tol, int32_t max_iter,
                            ss_precision prec, ss_solve_stats* stats, void* stream) {
   if (!s || !f_on_S || !u_on_S) SS_FAIL(SS_ERR_INVALID, "solve: null argument");
@@ -815,13 +852,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
     SS_CUDA(cudaStreamSynchronize(st));
     if (f0.x != 0.0 || f0.y != 0.0) SS_FAIL(SS_ERR_INVALID, "solve: f_hat_0 must be 0 (mean-zero forcing)");
   }
-  ss_solve_ctx* C;
-  {
-    std::lock_guard<std::mutex> lk(g_ctx_mu);
-    auto& slot = g_ctx[s];
-    if (!slot) slot = new ss_solve_ctx();
-    C = slot;
-  }
+  ss_solve_ctx* C = solve_ctx(s);
   const int mode = prec == SS_FP64 ? 0 : 1;
   SS_TRY(stamp_plan(s, *C, mode, st));
   C->plan.inst[0].f = reinterpret_cast<const double2*>(f_on_S);

@@ -7,7 +7,7 @@ namespace ss {
 
 constexpr int kNQ = 4;        // partial-sum quantities per slot
 constexpr int kMaxInstPerChunk = 32;
-constexpr int kMaxWarps = 16;
+constexpr int kMaxWarps = 32;
 
 struct SolveInst {
   int64_t row0, rows, rows_pad, zero_row;
@@ -52,7 +52,11 @@ struct SolveParams {
   double2* pd;                 // search direction p
   double2* sd;                 // s = L p
   double2* rhat;               // f - L x (refinement)
-  double2* dlt;                // refinement correction
+  double2* dlt;                // refinement correction (unused by the FP32 inner solve)
+  float2* r32;                 // inner CG (FP32): residual, direction, L p, correction
+  float2* p32;
+  float2* s32;
+  float2* d32;
   double* part;                // [slots][kNQ]
   unsigned* bar;               // barrier count, generation
   int* counters;               // done, inner started, inner finished
@@ -80,7 +84,7 @@ struct SolveWork {
   }
   DevBuf<double2> xrec, urec64, r, w64, pd, sd, rhat, dlt;
   DevBuf<float4> urec32;
-  DevBuf<float2> w32;
+  DevBuf<float2> w32, r32, p32, s32, d32;
   DevBuf<double> part;
   DevBuf<unsigned> bar;
   DevBuf<int> counters, err;
