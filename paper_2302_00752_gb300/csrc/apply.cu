@@ -29,19 +29,14 @@ __device__ __forceinline__ void load_coef(T* s_ca, int32_t* s_pn, const T* ca, c
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) k_apply64(OpView op, int64_t size, int64_t rows_pad, const int32_t* __restrict__ norm,
-                                                 const double2* __restrict__ rec, const double2* __restrict__ ca,
-                                                 const int32_t* __restrict__ pn, int s_a, int64_t zero_idx,
+__global__ void __launch_bounds__(256) k_apply64(OpView op, int64_t size, int64_t rows_pad,
+                                                 const double2* __restrict__ rec, int64_t zero_idx,
                                                  double2* __restrict__ y) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  double2* s_ca = reinterpret_cast<double2*>(smem);
-  int32_t* s_pn = reinterpret_cast<int32_t*>(s_ca + s_a);
-  load_coef(s_ca, s_pn, ca, pn, s_a);
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= rows_pad) return;
   const int64_t s = row / kSlice;
   const int lane = (int)(row % kSlice);
-  double2 acc = row_apply64(op, s, lane, __ldg(norm + row), rec, s_ca, s_pn);
+  double2 acc = row_apply64(op, s, lane, rec);
   if (row == zero_idx) acc = rec[2 * row];
   if (row < size) y[row] = acc;
 }
@@ -74,6 +69,7 @@ OpView op_view(const ss_stamp_s* s) {
   OpView op;
   op.woff = s->slice_off.get();
   op.ent = s->ent.get();
+  op.ecoef = s->ecoef64.get();
   op.colbits = colbits_of(s->jbits);
   op.colmask = colmask_of(s->jbits);
   return op;
@@ -92,9 +88,7 @@ ss_status launch_pack32(const ss_stamp_s* s, const float2* u, cudaStream_t st) {
 }
 
 ss_status launch_apply64(const ss_stamp_s* s, double2* y, cudaStream_t st) {
-  const size_t sm = s->s_a * (sizeof(double2) + sizeof(int32_t)) + 16;
-  k_apply64<<<nblk(s->rows_pad), 256, sm, st>>>(op_view(s), s->size, s->rows_pad, s->norm.get(), s->rec64.get(),
-                                                s->ca64.get(), s->pnorm.get(), s->s_a, s->zero_idx, y);
+  k_apply64<<<nblk(s->rows_pad), 256, 0, st>>>(op_view(s), s->size, s->rows_pad, s->rec64.get(), s->zero_idx, y);
   SS_LAUNCH_CHECK();
   return SS_OK;
 }

@@ -20,7 +20,7 @@ struct ss_batch_s {
   int jbits = 1;
   ss::DevBuf<int32_t> norm, woff, slice_inst, pn;
   ss::DevBuf<uint32_t> ent;
-  ss::DevBuf<double2> ca64;
+  ss::DevBuf<double2> ca64, ecoef64;
   ss::DevBuf<float2> ca32;
   std::vector<int32_t> woff_h, slice_inst_h;
   ss::SolvePlan plan;
@@ -89,6 +89,7 @@ OpView batch_op(const ss_batch_s* b) {
   OpView op;
   op.woff = b->woff.get();
   op.ent = b->ent.get();
+  op.ecoef = b->ecoef64.get();
   op.colbits = colbits_of(b->jbits);
   op.colmask = colmask_of(b->jbits);
   return op;
@@ -176,6 +177,7 @@ static ss_status batch_create_impl(ss_batch_s* b, int32_t n, const ss_stamp* sta
   SS_TRY(b->woff.alloc(slices + 1, st));
   SS_TRY(b->slice_inst.alloc(slices, st));
   SS_TRY(b->ent.alloc(ent + 1, st));
+  SS_TRY(b->ecoef64.alloc(ent + 1, st));
   SS_TRY(b->ca64.alloc(coefs, st));
   SS_TRY(b->ca32.alloc(coefs, st));
   SS_TRY(b->pn.alloc(coefs, st));
@@ -194,6 +196,8 @@ static ss_status batch_create_impl(ss_batch_s* b, int32_t n, const ss_stamp* sta
                                             (uint32_t)s->rows_pad, (uint32_t)row0, global_dummy, colbits_of(jb),
                                             b->ent.get() + e0);
     k_fill_i32<<<nblk(s->n_slices), 256, 0, st>>>(b->slice_inst.get() + s0, s->n_slices, i);
+    SS_CUDA(cudaMemcpyAsync(b->ecoef64.get() + e0, s->ecoef64.get(), s->n_ent * sizeof(double2),
+                            cudaMemcpyDeviceToDevice, st));
     SS_LAUNCH_CHECK();
     SS_CUDA(cudaMemcpyAsync(b->ca64.get() + c0, s->ca64.get(), s->s_a * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     SS_CUDA(cudaMemcpyAsync(b->ca32.get() + c0, s->ca32.get(), s->s_a * sizeof(float2), cudaMemcpyDeviceToDevice, st));
@@ -219,7 +223,7 @@ static ss_status batch_create_impl(ss_batch_s* b, int32_t n, const ss_stamp* sta
   SS_TRY(work_alloc(b->work, b->rows_total, b->norm.get(), st));
   SS_CUDA(cudaStreamSynchronize(st));
   b->norm.settle(); b->woff.settle(); b->slice_inst.settle(); b->ent.settle();
-  b->ca64.settle(); b->ca32.settle(); b->pn.settle();
+  b->ca64.settle(); b->ca32.settle(); b->pn.settle(); b->ecoef64.settle();
   return SS_OK;
 }
 

@@ -174,25 +174,40 @@ __device__ __forceinline__ bool same_rep(const int32_t* a, int sa, const int32_t
   return true;
 }
 
-__global__ void k_merge_terms(const int32_t* __restrict__ freq, const double2* __restrict__ coef, int64_t n, int d,
-                              int32_t* leader_flag, double2* merged, int32_t* imag_nonzero) {
+__global__ void k_fill_first(int32_t* first, int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) first[t] = (int32_t)n;
+}
+
+// first[t] = smallest u < t with the same representative (n if none), one
+// thread per pair (t, u).
+__global__ void k_merge_first(const int32_t* __restrict__ freq, int64_t n, int d, int32_t* first) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n * n) return;
+  const int64_t t = p / n, u = p - t * n;
+  if (u >= t) return;
+  const int32_t* pt = freq + t * d;
+  const int32_t* pu = freq + u * d;
+  if (same_rep(pu, rep_sign(pu, d), pt, rep_sign(pt, d), d)) atomicMin(first + t, (int32_t)u);
+}
+
+// Leaders sum their group in index order (deterministic).
+__global__ void k_merge_sum(const int32_t* __restrict__ freq, const double2* __restrict__ coef, int64_t n, int d,
+                            const int32_t* __restrict__ first, int32_t* leader_flag, double2* merged,
+                            int32_t* imag_nonzero) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  const int32_t* pt = freq + t * d;
-  const int st = rep_sign(pt, d);
-  bool leader = true;
-  for (int64_t u = 0; u < t && leader; ++u)
-    if (same_rep(freq + u * d, rep_sign(freq + u * d, d), pt, st, d)) leader = false;
+  const bool leader = first[t] == (int32_t)n;
   leader_flag[t] = leader ? 1 : 0;
   if (!leader) return;
+  const int st = rep_sign(freq + t * d, d);
   double re = 0.0, im = 0.0;
   for (int64_t u = t; u < n; ++u) {
-    const int32_t* pu = freq + u * d;
-    const int su = rep_sign(pu, d);
-    if (!same_rep(pu, su, pt, st, d)) continue;
+    if (u != t && first[u] != (int32_t)t) continue;
+    const int su = rep_sign(freq + u * d, d);
     const double2 c = coef[u];
     re += c.x;
-    im += (su == 0) ? 0.0 : (su == st ? c.y : -c.y);
+    im += (su == st) ? c.y : -c.y;
   }
   if (st == 0) im = 0.0;
   merged[t] = make_double2(re, im);
@@ -461,8 +476,13 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
   SS_TRY(merged.alloc(n, st));
   SS_TRY(coef.alloc(n, st));
   SS_CUDA(cudaMemsetAsync(imag.get(), 0, sizeof(int32_t), st));
-  k_merge_terms<<<nblk(n), 256, 0, st>>>(g->freq, reinterpret_cast<const double2*>(g->coef), n, L.d, flag.get(),
-                                         merged.get(), imag.get());
+  if (n > 46340) SS_FAIL(SS_ERR_INVALID, "lattice_sample: more than 46340 terms");
+  DevBuf<int32_t> first;
+  SS_TRY(first.alloc(n, st));
+  k_fill_first<<<nblk(n), 256, 0, st>>>(first.get(), n);
+  k_merge_first<<<nblk(n * n), 256, 0, st>>>(g->freq, n, L.d, first.get());
+  k_merge_sum<<<nblk(n), 256, 0, st>>>(g->freq, reinterpret_cast<const double2*>(g->coef), n, L.d, first.get(),
+                                       flag.get(), merged.get(), imag.get());
   SS_LAUNCH_CHECK();
   SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), n, total.get(), st));
   k_compact_terms<<<nblk(n), 256, 0, st>>>(g->freq, n, L, flag.get(), pos.get(), merged.get(), q.get(), step.get(),

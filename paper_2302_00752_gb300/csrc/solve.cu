@@ -211,7 +211,7 @@ __device__ __forceinline__ double2 f_at(const SolveInst& in, int64_t g) {
 __device__ __forceinline__ double2 apply64_row(const SolveParams& P, const SolveInst& in, int64_t s, int lane,
                                                int64_t g, const double2* rec) {
   if (g == in.zero_row) return __ldcg(rec + 2 * g);
-  return row_apply64<true>(P.op, s, lane, __ldg(P.norm + g), rec, P.ca64 + in.coef_off, P.pn + in.coef_off);
+  return row_apply64<true>(P.op, s, lane, rec);
 }
 
 __device__ __forceinline__ float2 apply32_row(const SolveParams& P, const SolveInst& in, int64_t s, int lane,
@@ -266,10 +266,11 @@ __device__ void solve_fp64(const SolveParams& P, Smem& sm) {
   run_phase(P, sm, 0b1000u, noscal, [&](int64_t g, int64_t, int, int i, int, double* v) {
     const SolveInst& in = P.inst[i];
     const double2 f = f_at(in, g);
-    const double D = jacobi(P, in, g);
+    const double rD = 1.0 / jacobi(P, in, g);
+    P.rdiag[g] = rD;
     P.r[g] = f;
     P.xrec[2 * g] = make_double2(0.0, 0.0);
-    P.urec64[2 * g] = make_double2(f.x / D, f.y / D);
+    P.urec64[2 * g] = make_double2(f.x * rD, f.y * rD);
     P.pd[g] = make_double2(0.0, 0.0);
     P.sd[g] = make_double2(0.0, 0.0);
     v[3] = f.x * f.x + f.y * f.y;
@@ -336,12 +337,12 @@ __device__ void solve_fp64(const SolveParams& P, Smem& sm) {
       sv.x = w.x + b * sv.x; sv.y = w.y + b * sv.y;
       x.x += a * p.x; x.y += a * p.y;
       r.x -= a * sv.x; r.y -= a * sv.y;
-      const double D = jacobi(P, in, g);
+      const double rD = P.rdiag[g];
       P.pd[g] = p;
       P.sd[g] = sv;
       P.xrec[2 * g] = x;
       P.r[g] = r;
-      P.urec64[2 * g] = make_double2(r.x / D, r.y / D);
+      P.urec64[2 * g] = make_double2(r.x * rD, r.y * rD);
     });
     if (!grid_sync(P)) return;
     if (block_counter(P, 0) >= P.n_inst) break;
@@ -627,6 +628,7 @@ ss_status work_alloc(SolveWork& W, int64_t rows_total, const int32_t* norm, cuda
   SS_TRY(W.p32.alloc(rows_total, st));
   SS_TRY(W.s32.alloc(rows_total, st));
   SS_TRY(W.d32.alloc(rows_total, st));
+  SS_TRY(W.rdiag.alloc(rows_total, st));
   SS_TRY(W.bar.alloc(2, st));
   SS_TRY(W.counters.alloc(4, st));
   SS_TRY(W.err.alloc(1, st));
@@ -637,7 +639,7 @@ ss_status work_alloc(SolveWork& W, int64_t rows_total, const int32_t* norm, cuda
   SS_CUDA(cudaStreamSynchronize(st));
   W.xrec.settle(); W.urec64.settle(); W.urec32.settle(); W.r.settle(); W.w64.settle(); W.w32.settle();
   W.pd.settle(); W.sd.settle(); W.rhat.settle(); W.dlt.settle(); W.bar.settle(); W.counters.settle();
-  W.err.settle(); W.r32.settle(); W.p32.settle(); W.s32.settle(); W.d32.settle();
+  W.err.settle(); W.r32.settle(); W.p32.settle(); W.s32.settle(); W.d32.settle(); W.rdiag.settle();
   return SS_OK;
 }
 
@@ -692,6 +694,7 @@ ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, co
   P.p32 = W.p32.get();
   P.s32 = W.s32.get();
   P.d32 = W.d32.get();
+  P.rdiag = W.rdiag.get();
   P.part = W.part.get();
   P.bar = W.bar.get();
   P.counters = W.counters.get();
@@ -861,6 +864,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
   OpView op;
   op.woff = s->slice_off.get();
   op.ent = s->ent.get();
+  op.ecoef = s->ecoef64.get();
   op.colbits = colbits_of(s->jbits);
   op.colmask = colmask_of(s->jbits);
   if (!C->work.ev[0]) {

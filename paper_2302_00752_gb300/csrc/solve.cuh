@@ -57,6 +57,7 @@ struct SolveParams {
   float2* p32;
   float2* s32;
   float2* d32;
+  double* rdiag;               // 1 / D (FP64 mode)
   double* part;                // [slots][kNQ]
   unsigned* bar;               // barrier count, generation
   int* counters;               // done, inner started, inner finished
@@ -85,6 +86,7 @@ struct SolveWork {
   DevBuf<double2> xrec, urec64, r, w64, pd, sd, rhat, dlt;
   DevBuf<float4> urec32;
   DevBuf<float2> w32, r32, p32, s32, d32;
+  DevBuf<double> rdiag;
   DevBuf<double> part;
   DevBuf<unsigned> bar;
   DevBuf<int> counters, err;

@@ -129,6 +129,7 @@ struct ss_stamp_s {
   // neighbour table, sliced ELL with 32-row slices, column-major in a slice
   ss::DevBuf<int32_t> slice_off;      // [n_slices + 1], in entries (multiple of 32)
   ss::DevBuf<uint32_t> ent;           // [n_ent] col | (j << colbits)
+  ss::DevBuf<double2> ecoef64;        // [n_ent] 2 pi^2 (|k|^2 + |l|^2 - |p_j|^2) a_hat_j per entry (FP64 operator)
   // scratch for galerkin_apply
   ss::DevBuf<float4> rec32;           // [rows_pad + 1]
   ss::DevBuf<double2> rec64;          // [2 * (rows_pad + 1)] (value, norm|pad) pairs

@@ -280,8 +280,14 @@ __global__ void k_row_counts(const int32_t* __restrict__ nbr, int64_t size, int6
   }
 }
 
+// Entries of a row in step order, then padding (dummy column rows_pad, zero
+// coefficient).  Also stores the FP64 coefficient of every entry,
+// (|k|^2 + |l|^2 - |p_j|^2) * 2 pi^2 a_hat_j = 4 pi^2 (k.l) a_hat_j (eq. GF), so
+// that the FP64 operator spends four FP64 FMAs per nonzero.
 __global__ void k_fill_slices(const int32_t* __restrict__ nbr, int64_t size, int64_t rows_pad, int s_a, int j0,
-                              const int32_t* __restrict__ woff, int colbits, uint32_t* ent) {
+                              const int32_t* __restrict__ woff, int colbits, const int32_t* __restrict__ norm,
+                              const int32_t* __restrict__ pnorm, const double2* __restrict__ ca64, uint32_t* ent,
+                              double2* ecoef) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows_pad) return;
   const int64_t s = i / kSlice;
@@ -289,13 +295,23 @@ __global__ void k_fill_slices(const int32_t* __restrict__ nbr, int64_t size, int
   const int64_t base = (int64_t)woff[s] * kSlice + lane;
   const int w = woff[s + 1] - woff[s];
   int t = 0;
-  if (i < size)
+  if (i < size) {
+    const int32_t nk = norm[i];
     for (int j = 0; j < s_a; ++j) {
       const int32_t v = nbr[i * s_a + j];
-      if (v >= 0) ent[base + (int64_t)t++ * kSlice] = (uint32_t)v | ((uint32_t)j << colbits);
+      if (v >= 0) {
+        const int64_t e = base + (int64_t)t++ * kSlice;
+        ent[e] = (uint32_t)v | ((uint32_t)j << colbits);
+        const double sc = (double)(nk + norm[v] - pnorm[j]);
+        ecoef[e] = make_double2(sc * ca64[j].x, sc * ca64[j].y);
+      }
     }
+  }
   const uint32_t pad = (uint32_t)rows_pad | ((uint32_t)j0 << colbits);
-  for (; t < w; ++t) ent[base + (int64_t)t * kSlice] = pad;
+  for (; t < w; ++t) {
+    ent[base + (int64_t)t * kSlice] = pad;
+    ecoef[base + (int64_t)t * kSlice] = make_double2(0.0, 0.0);
+  }
 }
 
 __global__ void k_init_records(const int32_t* __restrict__ norm, int64_t n, float4* rec32, double2* rec64) {
@@ -544,8 +560,10 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   S->nnz = (int64_t)hnnz;
   S->n_ent = total_w * kSlice;
   SS_TRY(S->ent.alloc(S->n_ent + 1, st));
+  SS_TRY(S->ecoef64.alloc(S->n_ent + 1, st));
   k_fill_slices<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, S->j0, S->slice_off.get(),
-                                                   colbits_of(S->jbits), S->ent.get());
+                                                   colbits_of(S->jbits), S->norm.get(), S->pnorm.get(), S->ca64.get(),
+                                                   S->ent.get(), S->ecoef64.get());
   SS_LAUNCH_CHECK();
   SS_TRY(S->rec32.alloc(S->rows_pad + 1, st));
   SS_TRY(S->rec64.alloc(2 * (S->rows_pad + 1), st));
@@ -559,7 +577,7 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   // the stamp's buffers outlive this call's stream (synchronised above)
   S->keys.settle(); S->level.settle(); S->norm.settle(); S->table.settle();
   S->afreq.settle(); S->stepkey.settle(); S->pnorm.settle(); S->aval.settle();
-  S->ca64.settle(); S->ca32.settle(); S->slice_off.settle(); S->ent.settle();
+  S->ca64.settle(); S->ca32.settle(); S->slice_off.settle(); S->ent.settle(); S->ecoef64.settle();
   S->rec32.settle(); S->rec64.settle();
   return SS_OK;
 }
