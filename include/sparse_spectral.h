@@ -212,6 +212,26 @@ ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, double tol, in
  * chunks per block.  Takes effect at the next solve.  Default 1024, 1, 1. */
 ss_status solve_set_config(ss_stamp s, int32_t block, int32_t blocks_per_sm, int32_t chunks_per_block);
 
+/* Allocation-free variant of solve() (the paper has no counterpart: this is a
+ * deployment convenience).  For callers that may not allocate device memory
+ * while they run - code inside a region being captured into a CUDA graph,
+ * latency-bound loops that must not stall on cudaMalloc (which synchronises
+ * the device), or processes with a device-memory budget fixed at start-up.
+ * The caller passes f_on_S and u_on_S exactly as for solve(); all workspace
+ * comes from one file-scope device array of about 7.4 MB that every GPU which
+ * loads the library holds until exit, sized for a stamping set of at most
+ * 32,768 padded rows (|S| <= 32,768, rounded up to whole 32-row slices);
+ * larger sets return SS_ERR_INVALID.  It calls no allocating routine.
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call uses the whole array and leaves its contents
+ * there (the next call re-initialises what must start at zero), so calls whose
+ * GPU work overlaps - on different streams or threads - race and must be
+ * serialised by the caller.  Synchronises `stream`; stats as solve() (without
+ * kernel_ms). */
+ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_on_S, double tol, int32_t max_iter,
+                        ss_precision prec, ss_solve_stats* stats, void* stream);
+
 /* Many instances in one persistent launch: the rows of all instances are
  * concatenated, every CG phase runs over all of them with per-instance scalars,
  * and converged instances drop out.  batch_create copies the instances'

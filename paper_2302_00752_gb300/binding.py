@@ -77,6 +77,7 @@ def _load():
         "galerkin_apply": (i32, [vp, vp, vp, i32, vp]),
         "solve": (i32, [vp, vp, vp, dbl, i32, i32, P(SolveStats), vp]),
         "solve_set_config": (i32, [vp, i32, i32, i32]),
+        "solve_noalloc": (i32, [vp, vp, vp, dbl, i32, i32, P(SolveStats), vp]),
         "batch_create": (i32, [i32, P(vp), P(vp), vp]),
         "batch_solve": (i32, [vp, P(vp), P(vp), dbl, i32, i32, i32, P(SolveStats), vp]),
         "batch_autotune": (i32, [vp, P(vp), P(vp), dbl, i32, i32, P(dbl), vp]),
@@ -320,6 +321,24 @@ def solve(stamp, f_on_S, tol=1e-12, max_iter=1000, precision="fp64", out=None, r
     if raise_on_error:
         _check(status)
     return u, st.as_dict()
+
+
+def solve_noalloc(stamp, f_on_S, out, tol=1e-12, max_iter=1000, precision="fp64"):
+    """Allocation-free solve: for callers that must not allocate device memory
+    while they run (inside CUDA-graph capture regions, allocation-free loops,
+    fixed memory budgets).  ``f_on_S`` and ``out`` are caller-owned complex128
+    device tensors of length |S|; the workspace is a fixed library array for
+    |S| <= 32768 (larger sets raise SSError).  Calls that overlap on the GPU
+    share that array and race."""
+    if not (torch.is_tensor(f_on_S) and f_on_S.is_cuda and f_on_S.dtype == torch.complex128
+            and f_on_S.is_contiguous()):
+        raise TypeError("f_on_S must be a contiguous complex128 CUDA tensor")
+    if not (torch.is_tensor(out) and out.is_cuda and out.dtype == torch.complex128 and out.is_contiguous()):
+        raise TypeError("out must be a contiguous complex128 CUDA tensor")
+    st = SolveStats()
+    _check(lib.solve_noalloc(stamp.handle, _ptr(f_on_S), _ptr(out), float(tol), int(max_iter), _prec(precision),
+                             C.byref(st), _stream()))
+    return out, st.as_dict()
 
 
 # -------------------------------------------------------------------- batch

@@ -879,3 +879,218 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
   if (stats) *stats = one;
   return worst;
 }
+
+// ------------------------------------------------------ allocation-free solve
+//
+// solve_noalloc runs the same persistent solver as solve() but takes all of
+// its workspace from one file-scope device array instead of allocating it.
+// It serves callers that may not allocate device memory once they run: code
+// that executes inside a region where an allocation would break a CUDA graph
+// being captured, or that must not let a first call stall on cudaMalloc
+// (allocation synchronises the device), or that runs under a fixed
+// device-memory budget set at start-up.  The array holds a stamping set of at
+// most kNoAllocRows padded rows (stamps of up to 32,736 frequencies, a few MB
+// of device memory on every GPU that loads the library, kept until exit).
+
+namespace ss {
+namespace {
+
+constexpr int64_t kNoAllocRows = 32768;                 // padded rows of S
+constexpr int64_t kNoAllocRecs = kNoAllocRows + 1;      // plus the dummy record
+constexpr int kNoAllocChunks = 1024;
+constexpr int64_t kNoAllocParts = kNoAllocChunks + 1;
+
+constexpr size_t a256(size_t x) { return (x + 255) / 256 * 256; }
+
+// byte offsets of the workspace inside the array
+constexpr size_t kOffXrec = 0;
+constexpr size_t kOffU64 = kOffXrec + a256(2 * kNoAllocRecs * sizeof(double2));
+constexpr size_t kOffU32 = kOffU64 + a256(2 * kNoAllocRecs * sizeof(double2));
+constexpr size_t kOffR = kOffU32 + a256(kNoAllocRecs * sizeof(float4));
+constexpr size_t kOffW64 = kOffR + a256(kNoAllocRecs * sizeof(double2));
+constexpr size_t kOffPd = kOffW64 + a256(kNoAllocRecs * sizeof(double2));
+constexpr size_t kOffSd = kOffPd + a256(kNoAllocRecs * sizeof(double2));
+constexpr size_t kOffRhat = kOffSd + a256(kNoAllocRecs * sizeof(double2));
+constexpr size_t kOffDlt = kOffRhat + a256(kNoAllocRecs * sizeof(double2));
+constexpr size_t kOffW32 = kOffDlt + a256(kNoAllocRecs * sizeof(double2));
+constexpr size_t kOffR32 = kOffW32 + a256(kNoAllocRecs * sizeof(float2));
+constexpr size_t kOffP32 = kOffR32 + a256(kNoAllocRecs * sizeof(float2));
+constexpr size_t kOffS32 = kOffP32 + a256(kNoAllocRecs * sizeof(float2));
+constexpr size_t kOffD32 = kOffS32 + a256(kNoAllocRecs * sizeof(float2));
+constexpr size_t kOffRdiag = kOffD32 + a256(kNoAllocRecs * sizeof(float2));
+constexpr size_t kOffPart = kOffRdiag + a256(kNoAllocRecs * sizeof(double));
+constexpr size_t kOffBar = kOffPart + a256(kNoAllocParts * kNQ * sizeof(double));
+constexpr size_t kOffCnt = kOffBar + 256;
+constexpr size_t kOffErr = kOffCnt + 256;
+constexpr size_t kOffState = kOffErr + 256;
+constexpr size_t kOffInst = kOffState + a256(sizeof(InstState));
+constexpr size_t kOffChunk = kOffInst + a256(sizeof(SolveInst));
+constexpr size_t kNoAllocBytes = kOffChunk + a256(kNoAllocChunks * sizeof(Chunk));
+
+}  // namespace
+}  // namespace ss
+
+// The shared workspace (one per device; every call uses all of it).
+static __device__ __align__(256) unsigned char ss_noalloc_scratch[ss::kNoAllocBytes];
+
+namespace ss {
+namespace {
+
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_base[64] = {};
+
+// Device address of the array for the current device, looked up once per
+// device (host code cannot use the array's name as a device address).
+ss_status noalloc_base(unsigned char** out) {
+  int dev = 0;
+  SS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) SS_FAIL(SS_ERR_INVALID, "solve_noalloc: device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_base[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, ss_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      SS_FAIL(SS_ERR_CUDA, "solve_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    g_noalloc_base[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_noalloc_base[dev];
+  return SS_OK;
+}
+
+}  // namespace
+}  // namespace ss
+
+extern "C" ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_on_S, double tol, int32_t max_iter,
+                                   ss_precision prec, ss_solve_stats* stats, void* stream) {
+  if (!s || !f_on_S || !u_on_S) SS_FAIL(SS_ERR_INVALID, "solve_noalloc: null argument");
+  if (!(tol > 0.0) || max_iter < 1) SS_FAIL(SS_ERR_INVALID, "solve_noalloc: need tol > 0 and max_iter >= 1");
+  if (prec != SS_FP64 && prec != SS_FP32) SS_FAIL(SS_ERR_INVALID, "solve_noalloc: bad precision");
+  if (s->rows_pad > kNoAllocRows)
+    SS_FAIL(SS_ERR_INVALID,
+            "solve_noalloc: |S| = %lld (%lld padded rows) exceeds the allocation-free workspace of %lld rows",
+            (long long)s->size, (long long)s->rows_pad, (long long)kNoAllocRows);
+  cudaStream_t st = as_stream(stream);
+  unsigned char* base = nullptr;
+  SS_TRY(noalloc_base(&base));
+  if (s->zero_idx >= 0) {
+    double2 f0;
+    SS_CUDA(cudaMemcpyAsync(&f0, reinterpret_cast<const double2*>(f_on_S) + s->zero_idx, sizeof(f0),
+                            cudaMemcpyDeviceToHost, st));
+    SS_CUDA(cudaStreamSynchronize(st));
+    if (f0.x != 0.0 || f0.y != 0.0) SS_FAIL(SS_ERR_INVALID, "solve_noalloc: f_hat_0 must be 0 (mean-zero forcing)");
+  }
+  // static work split, as solve() with its default tile shape (host memory only)
+  const int mode = prec == SS_FP64 ? 0 : 1;
+  std::vector<int32_t> woff(s->n_slices + 1);
+  SS_CUDA(cudaMemcpyAsync(woff.data(), s->slice_off.get(), woff.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  SolvePlan plan;
+  plan.inst.assign(1, SolveInst{});
+  SolveInst& in = plan.inst[0];
+  in.row0 = 0;
+  in.rows = s->size;
+  in.rows_pad = s->rows_pad;
+  in.zero_row = s->zero_idx;
+  in.coef_off = 0;
+  in.dscale = 2.0 * kTwoPiSq * s->a0;
+  in.f = reinterpret_cast<const double2*>(f_on_S);
+  in.u = reinterpret_cast<double2*>(u_on_S);
+  plan.block = 1024;
+  int grid = 0;
+  SS_TRY(max_grid(mode, plan.block, &grid));
+  grid = std::min(grid, sm_count());
+  const int by_size = (int)std::max<int64_t>(1, s->n_slices / 8);
+  SS_TRY(plan_chunks(plan, woff, {}, std::min(grid, by_size)));
+  plan.grid = std::min<int>(grid, (int)plan.chunk.size());
+  if ((int)plan.chunk.size() > kNoAllocChunks || plan.n_parts > kNoAllocParts)
+    SS_FAIL(SS_ERR_INVALID, "solve_noalloc: work split exceeds the workspace tables");
+  // pointers into the shared workspace
+  auto at = [&](size_t off) { return static_cast<void*>(base + off); };
+  SolveInst* d_inst = static_cast<SolveInst*>(at(kOffInst));
+  Chunk* d_chunk = static_cast<Chunk*>(at(kOffChunk));
+  InstState* d_state = static_cast<InstState*>(at(kOffState));
+  unsigned* d_bar = static_cast<unsigned*>(at(kOffBar));
+  int* d_cnt = static_cast<int*>(at(kOffCnt));
+  int* d_err = static_cast<int*>(at(kOffErr));
+  SS_CUDA(cudaMemcpyAsync(d_inst, plan.inst.data(), sizeof(SolveInst), cudaMemcpyHostToDevice, st));
+  SS_CUDA(cudaMemcpyAsync(d_chunk, plan.chunk.data(), plan.chunk.size() * sizeof(Chunk), cudaMemcpyHostToDevice, st));
+  // the array keeps the previous call's contents: reset what must start at zero
+  // (barrier, counters, error word, instance state) and the records' norm halves
+  SS_CUDA(cudaMemsetAsync(d_bar, 0, 2 * sizeof(unsigned), st));
+  SS_CUDA(cudaMemsetAsync(d_cnt, 0, 4 * sizeof(int), st));
+  SS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+  SS_CUDA(cudaMemsetAsync(d_state, 0, sizeof(InstState), st));
+  const int64_t recs = s->rows_pad + 1;
+  k_init_solve_records<<<nblk(recs), 256, 0, st>>>(s->norm.get(), recs, static_cast<double2*>(at(kOffXrec)),
+                                                  static_cast<double2*>(at(kOffU64)), static_cast<float4*>(at(kOffU32)));
+  SS_LAUNCH_CHECK();
+  SolveParams P{};
+  P.n_inst = 1;
+  P.n_chunks = (int)plan.chunk.size();
+  P.inst = d_inst;
+  P.chunk = d_chunk;
+  P.state = d_state;
+  P.op.woff = s->slice_off.get();
+  P.op.ent = s->ent.get();
+  P.op.ecoef = s->ecoef64.get();
+  P.op.colbits = colbits_of(s->jbits);
+  P.op.colmask = colmask_of(s->jbits);
+  P.slice_inst = nullptr;
+  P.norm = s->norm.get();
+  P.ca64 = s->ca64.get();
+  P.ca32 = s->ca32.get();
+  P.pn = s->pnorm.get();
+  P.xrec = static_cast<double2*>(at(kOffXrec));
+  P.urec64 = static_cast<double2*>(at(kOffU64));
+  P.urec32 = static_cast<float4*>(at(kOffU32));
+  P.r = static_cast<double2*>(at(kOffR));
+  P.w64 = static_cast<double2*>(at(kOffW64));
+  P.pd = static_cast<double2*>(at(kOffPd));
+  P.sd = static_cast<double2*>(at(kOffSd));
+  P.rhat = static_cast<double2*>(at(kOffRhat));
+  P.dlt = static_cast<double2*>(at(kOffDlt));
+  P.w32 = static_cast<float2*>(at(kOffW32));
+  P.r32 = static_cast<float2*>(at(kOffR32));
+  P.p32 = static_cast<float2*>(at(kOffP32));
+  P.s32 = static_cast<float2*>(at(kOffS32));
+  P.d32 = static_cast<float2*>(at(kOffD32));
+  P.rdiag = static_cast<double*>(at(kOffRdiag));
+  P.part = static_cast<double*>(at(kOffPart));
+  P.bar = d_bar;
+  P.counters = d_cnt;
+  P.err = d_err;
+  P.tol = tol;
+  P.inner_tol = 1e-5;
+  P.max_iter = max_iter;
+  P.max_inner = std::max(1, std::min(max_iter, 200));
+  P.max_outer = std::max(1, max_iter);
+  P.spin_limit = 2000000000ll;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(plan.grid);
+  cfg.blockDim = dim3(plan.block);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (mode == 0) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<0>, P));
+  else SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<1>, P));
+  InstState hs;
+  int herr = 0;
+  SS_CUDA(cudaMemcpyAsync(&hs, d_state, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  const double rel = hs.bb > 0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
+  if (stats) {
+    stats->status = herr ? herr : hs.status;
+    stats->outer_iters = hs.outer_iters;
+    stats->inner_iters = hs.inner_iters ? hs.inner_iters : hs.iters;
+    stats->applies = hs.applies;
+    stats->rel_residual = rel;
+    stats->kernel_ms = 0.0;
+  }
+  if (herr) SS_FAIL((ss_status)herr, "solve_noalloc: a device-side wait gave up (status %d)", herr);
+  if (hs.status != SS_OK) SS_FAIL((ss_status)hs.status, "solve_noalloc: not converged (relative residual %.3e)", rel);
+  return SS_OK;
+}
