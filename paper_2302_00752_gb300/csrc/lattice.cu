@@ -183,13 +183,28 @@ __global__ void k_cbc_try_hash(const int32_t* __restrict__ f, int64_t n, int d, 
   if (threadIdx.x == 0) fail[blockIdx.x] = bad;
 }
 
-__global__ void k_cbc_accept(const int32_t* __restrict__ f, int64_t n, int d, int j, int64_t M, int64_t z,
-                             int64_t* rho) {
+__global__ void k_cbc_accept(const int32_t* __restrict__ f, int64_t n, int d, int j, int64_t M,
+                             const int64_t* __restrict__ zdev, int64_t* rho) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const uint64_t z = (uint64_t)zdev[j];
   int64_t k = f[i * d + j] % M;
   if (k < 0) k += M;
-  rho[i] = (int64_t)(((uint64_t)rho[i] + ((uint64_t)k * (uint64_t)z) % (uint64_t)M) % (uint64_t)M);
+  rho[i] = (int64_t)(((uint64_t)rho[i] + ((uint64_t)k * z) % (uint64_t)M) % (uint64_t)M);
+}
+
+// First candidate of coordinate j that passed (in stream order); on failure
+// records the coordinate and keeps z_j = 1 so the remaining steps stay defined.
+__global__ void k_cbc_pick(const int32_t* __restrict__ fail, const int64_t* __restrict__ cand, int n_cand, int j,
+                           int64_t* zdev, int32_t* err) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int64_t z = 1;
+  int pick = -1;
+  for (int c = 0; c < n_cand; ++c)
+    if (!fail[c]) { pick = c; break; }
+  if (pick >= 0) z = cand[pick];
+  else if (*err == 0) *err = j + 1;
+  zdev[j] = z;
 }
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -213,6 +228,27 @@ ss_status residues(const int32_t* freq, int64_t n, const LatticeDev& L, int64_t*
   if (n == 0) return SS_OK;
   k_residues<<<nblk(n), 256, 0, st>>>(freq, n, L.d, L, res);
   SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
+ss_status check_reconstructing_async(const int32_t* freq, int64_t n, const LatticeDev& L, const int64_t* res,
+                                     bool need_symmetric, unsigned long long* table, uint64_t cap, int32_t* flags,
+                                     cudaStream_t st) {
+  SS_CUDA(cudaMemsetAsync(table, 0, cap * sizeof(unsigned long long), st));
+  SS_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int32_t), st));
+  if (n == 0) return SS_OK;
+  k_check_insert<<<nblk(n), 256, 0, st>>>(freq, res, n, L.d, table, cap - 1, flags);
+  if (need_symmetric) k_check_symmetric<<<nblk(n), 256, 0, st>>>(freq, res, n, L.d, L.M, table, cap - 1, flags);
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
+ss_status reconstructing_status(const int32_t* h, int64_t M) {
+  if (h[0]) SS_FAIL(SS_ERR_INVALID, "lattice: duplicate frequencies in the candidate set");
+  if (h[2]) SS_FAIL(SS_ERR_HASH_FULL, "lattice: residue table exhausted");
+  if (h[1]) SS_FAIL(SS_ERR_NOT_RECONSTRUCTING, "lattice (M = %lld) is not reconstructing for the candidate set",
+                    (long long)M);
+  if (h[3]) SS_FAIL(SS_ERR_INVALID, "candidate set is not closed under negation");
   return SS_OK;
 }
 
@@ -334,10 +370,13 @@ extern "C" ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int6
     LatticeDev L;
     SS_TRY(make_lattice_dev(&lat, &L));
   }
-  DevBuf<int64_t> rho, cand, scratch;
-  DevBuf<int32_t> fail;
+  DevBuf<int64_t> rho, cand, scratch, zdev;
+  DevBuf<int32_t> fail, err;
   SS_TRY(rho.alloc(n, st));
-  SS_TRY(cand.alloc(n_cand, st));
+  SS_TRY(cand.alloc((size_t)d * n_cand, st));
+  SS_TRY(fail.alloc(n_cand, st));
+  SS_TRY(zdev.alloc(d, st));
+  SS_TRY(err.alloc(1, st));
   int hash_cap = 1;
   while (hash_cap < 2 * n) hash_cap <<= 1;
   const size_t hash_smem = (size_t)n * sizeof(int64_t) + (size_t)hash_cap * sizeof(int32_t);
@@ -348,37 +387,37 @@ extern "C" ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int6
   } else {
     SS_TRY(scratch.alloc((size_t)n_cand * n, st));
   }
-  SS_TRY(fail.alloc(n_cand, st));
-  SS_CUDA(cudaMemsetAsync(rho.get(), 0, n * sizeof(int64_t), st));
-  std::vector<int64_t> z(d, 1), hc(n_cand);
-  std::vector<int32_t> hf(n_cand);
-  // coordinate 0: z_1 = 1 (distinct first coordinates have distinct residues since M > K)
-  k_cbc_accept<<<nblk(n), 256, 0, st>>>(freq, n, d, 0, M, 1, rho.get());
-  SS_LAUNCH_CHECK();
-  for (int j = 1; j < d; ++j) {
+  // all candidates up front; each coordinate's pick stays on the device
+  std::vector<int64_t> hc((size_t)d * n_cand, 1), z(d, 1);
+  for (int j = 1; j < d; ++j)
     for (int c = 0; c < n_cand; ++c) {
       const int64_t r = raw[(int64_t)j * n_cand + c];
       if (r < 0) SS_FAIL(SS_ERR_INVALID, "lattice_cbc: raw draws must be non-negative");
-      hc[c] = 1 + r % (M - 1);
+      hc[(size_t)j * n_cand + c] = 1 + r % (M - 1);
     }
-    SS_CUDA(cudaMemcpyAsync(cand.get(), hc.data(), n_cand * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  SS_CUDA(cudaMemcpyAsync(cand.get(), hc.data(), hc.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  SS_CUDA(cudaMemsetAsync(rho.get(), 0, n * sizeof(int64_t), st));
+  SS_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), st));
+  // coordinate 0: z_1 = 1 (distinct first coordinates have distinct residues since M > K)
+  SS_CUDA(cudaMemcpyAsync(zdev.get(), z.data(), sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  k_cbc_accept<<<nblk(n), 256, 0, st>>>(freq, n, d, 0, M, zdev.get(), rho.get());
+  SS_LAUNCH_CHECK();
+  for (int j = 1; j < d; ++j) {
+    const int64_t* cj = cand.get() + (size_t)j * n_cand;
     if (hash_smem <= 200 * 1024) {
-      k_cbc_try_hash<<<n_cand, 256, hash_smem, st>>>(freq, n, d, j, M, rho.get(), cand.get(), hash_cap, fail.get());
+      k_cbc_try_hash<<<n_cand, 256, hash_smem, st>>>(freq, n, d, j, M, rho.get(), cj, hash_cap, fail.get());
     } else {
-      k_cbc_try<<<n_cand, 256, 0, st>>>(freq, n, d, j, M, rho.get(), cand.get(), scratch.get(), fail.get());
+      k_cbc_try<<<n_cand, 256, 0, st>>>(freq, n, d, j, M, rho.get(), cj, scratch.get(), fail.get());
     }
-    SS_LAUNCH_CHECK();
-    SS_CUDA(cudaMemcpyAsync(hf.data(), fail.get(), n_cand * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    SS_CUDA(cudaStreamSynchronize(st));
-    int pick = -1;
-    for (int c = 0; c < n_cand; ++c)
-      if (!hf[c]) { pick = c; break; }
-    if (pick < 0) SS_FAIL(SS_ERR_NOT_RECONSTRUCTING, "lattice_cbc: no candidate for coordinate %d", j + 1);
-    z[j] = hc[pick];
-    k_cbc_accept<<<nblk(n), 256, 0, st>>>(freq, n, d, j, M, z[j], rho.get());
+    k_cbc_pick<<<1, 32, 0, st>>>(fail.get(), cj, n_cand, j, zdev.get(), err.get());
+    k_cbc_accept<<<nblk(n), 256, 0, st>>>(freq, n, d, j, M, zdev.get(), rho.get());
     SS_LAUNCH_CHECK();
   }
+  int32_t herr = 0;
+  SS_CUDA(cudaMemcpyAsync(z.data(), zdev.get(), d * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaMemcpyAsync(&herr, err.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   SS_CUDA(cudaStreamSynchronize(st));
+  if (herr) SS_FAIL(SS_ERR_NOT_RECONSTRUCTING, "lattice_cbc: no candidate for coordinate %d", herr);
   for (int c = 0; c < d; ++c) z_out[c] = z[c];
   *M_out = M;
   return SS_OK;

@@ -29,6 +29,12 @@ ss_status make_lattice_dev(const ss_lattice* lat, LatticeDev* L);
 ss_status residues(const int32_t* freq, int64_t n, const LatticeDev& L, int64_t* res, cudaStream_t st);
 ss_status check_reconstructing(const int32_t* freq, int64_t n, const LatticeDev& L, const int64_t* res,
                                bool need_symmetric, cudaStream_t st);
+// Same check left on the device: flags[0] duplicate, [1] collision, [2] table
+// full, [3] not closed under negation; reconstructing_status decodes them.
+ss_status check_reconstructing_async(const int32_t* freq, int64_t n, const LatticeDev& L, const int64_t* res,
+                                     bool need_symmetric, unsigned long long* table, uint64_t cap, int32_t* flags,
+                                     cudaStream_t st);
+ss_status reconstructing_status(const int32_t* h, int64_t M);
 int64_t next_prime_host(int64_t n);
 
 }  // namespace ss

@@ -94,15 +94,30 @@ __global__ void k_twiddles_df(int64_t M, float4* tab) {
   tab[r] = make_float4(cc.hi, cc.lo, ss.hi, ss.lo);
 }
 
-// Lattice evaluation in double-float for the FP64 path (see the file comment).
-template <bool REAL>
+// Per merged term: W_m = exp(2 pi i (m * step mod M) / M), m < kSampPerThread,
+// from the double-float table (the phase steps of one thread's samples).
+__global__ void k_term_powers(const int64_t* __restrict__ step, const int64_t* __restrict__ n_terms, int64_t M,
+                              const float4* __restrict__ tab, float4* W) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= *n_terms) return;
+  const uint64_t st = (uint64_t)step[t];
+#pragma unroll
+  for (int m = 0; m < kSampPerThread; ++m) W[t * kSampPerThread + m] = tab[((uint64_t)m * st) % (uint64_t)M];
+}
+
+// Lattice evaluation in double-float for the FP64 path.  Thread samples are
+// j0 + 256 m; with r0 = j0 q mod M and B = c exp(2 pi i r0 / M) (one table
+// gather and one double-float complex product per term and thread), sample m
+// adds Re(B W_m): two double-float FMAs per term-sample, no further gathers.
 __global__ void __launch_bounds__(kSampThreads) k_sample_df(int64_t M, const float4* __restrict__ tab,
                                                             const int64_t* __restrict__ q,
-                                                            const int64_t* __restrict__ step,
-                                                            const double2* __restrict__ coef, int64_t n_terms,
-                                                            double* out) {
-  __shared__ int64_t s_q[kTermChunk], s_step[kTermChunk];
+                                                            const float4* __restrict__ W,
+                                                            const double2* __restrict__ coef,
+                                                            const int64_t* __restrict__ n_terms_dev, double* out) {
+  __shared__ uint32_t s_q[kTermChunk];
   __shared__ float4 s_c[kTermChunk];
+  __shared__ float4 s_w[kTermChunk * kSampPerThread];
+  const int64_t n_terms = *n_terms_dev;
   const int64_t j0 = (int64_t)blockIdx.x * (kSampThreads * kSampPerThread) + threadIdx.x;
   DF acc[kSampPerThread];
 #pragma unroll
@@ -111,32 +126,30 @@ __global__ void __launch_bounds__(kSampThreads) k_sample_df(int64_t M, const flo
     const int tc = (n_terms - t0 < kTermChunk) ? (int)(n_terms - t0) : kTermChunk;
     __syncthreads();
     for (int i = threadIdx.x; i < tc; i += blockDim.x) {
-      s_q[i] = q[t0 + i];
-      s_step[i] = step[t0 + i];
+      s_q[i] = (uint32_t)q[t0 + i];
       const double2 c = coef[t0 + i];
-      const DF cx = df_split(c.x), cy = df_split(-c.y);
+      const DF cx = df_split(c.x), cy = df_split(c.y);
       s_c[i] = make_float4(cx.hi, cx.lo, cy.hi, cy.lo);
     }
+    for (int i = threadIdx.x; i < tc * kSampPerThread; i += blockDim.x) s_w[i] = W[t0 * kSampPerThread + i];
     __syncthreads();
     for (int t = 0; t < tc; ++t) {
-      const uint32_t st = (uint32_t)s_step[t];
-      uint32_t r = (uint32_t)(((uint64_t)j0 * (uint64_t)s_q[t]) % (uint64_t)M);
+      const uint32_t r0 = (uint32_t)(((uint64_t)j0 * (uint64_t)s_q[t]) % (uint64_t)M);
+      const float4 e = __ldg(tab + r0);
       const float4 c = s_c[t];
-      uint32_t rr[kSampPerThread];
+      // B = c e (double-float complex product)
+      DF br{0.f, 0.f}, bi{0.f, 0.f};
+      df_fma(br, DF{c.x, c.y}, DF{e.x, e.y});
+      df_fma(br, DF{-c.z, -c.w}, DF{e.z, e.w});
+      df_fma(bi, DF{c.x, c.y}, DF{e.z, e.w});
+      df_fma(bi, DF{c.z, c.w}, DF{e.x, e.y});
+      const DF nbi{-bi.hi, -bi.lo};
+      const float4* w = s_w + t * kSampPerThread;
 #pragma unroll
       for (int m = 0; m < kSampPerThread; ++m) {
-        rr[m] = r;
-        r += st;
-        if (r >= (uint32_t)M) r -= (uint32_t)M;
-      }
-      float4 e[kSampPerThread];
-#pragma unroll
-      for (int m = 0; m < kSampPerThread; ++m) e[m] = __ldg(tab + rr[m]);
-#pragma unroll
-      for (int m = 0; m < kSampPerThread; ++m) {
-        // Re(c e^{i theta}) = c.re cos(theta) - c.im sin(theta)
-        df_fma(acc[m], DF{c.x, c.y}, DF{e[m].x, e[m].y});
-        if (!REAL) df_fma(acc[m], DF{c.z, c.w}, DF{e[m].z, e[m].w});
+        const float4 wm = w[m];
+        df_fma(acc[m], br, DF{wm.x, wm.y});    // Re(B W_m) = B.re W.re - B.im W.im
+        df_fma(acc[m], nbi, DF{wm.z, wm.w});
       }
     }
   }
@@ -231,12 +244,14 @@ __global__ void k_compact_terms(const int32_t* __restrict__ freq, int64_t n, Lat
 
 // TAB: 0 split tables in shared memory, 1 split tables in global memory,
 //      2 one full table exp(2 pi i r / M) in global memory (L2-resident).
-template <typename R, int TAB, bool REAL>
+template <typename R, int TAB>
 __global__ void __launch_bounds__(kSampThreads) k_sample(int64_t M, int bl, int64_t H,
                                                          const typename C2<R>::T* __restrict__ lo_g,
                                                          const typename C2<R>::T* __restrict__ hi_g,
                                                          const int64_t* __restrict__ q, const int64_t* __restrict__ step,
-                                                         const double2* __restrict__ coef, int64_t n_terms, R* out) {
+                                                         const double2* __restrict__ coef,
+                                                         const int64_t* __restrict__ n_terms_dev, R* out) {
+  const int64_t n_terms = *n_terms_dev;
   using T2 = typename C2<R>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t L = 1ll << bl;
@@ -283,21 +298,14 @@ __global__ void __launch_bounds__(kSampThreads) k_sample(int64_t M, int bl, int6
 #pragma unroll
         for (int m = 0; m < kSampPerThread; ++m) e[m] = __ldg(lo + rr[m]);
 #pragma unroll
-        for (int m = 0; m < kSampPerThread; ++m) {
-          if (REAL) acc[m] += c.x * e[m].x;
-          else acc[m] += c.x * e[m].x - c.y * e[m].y;
-        }
+        for (int m = 0; m < kSampPerThread; ++m) acc[m] += c.x * e[m].x - c.y * e[m].y;
       } else {
 #pragma unroll
         for (int m = 0; m < kSampPerThread; ++m) {
           const T2 h = hi[r >> bl], l = lo[r & lmask];
           const R er = h.x * l.x - h.y * l.y;   // cos(2 pi r / M)
-          if (REAL) {
-            acc[m] += c.x * er;
-          } else {
-            const R ei = h.x * l.y + h.y * l.x;   // sin(2 pi r / M)
-            acc[m] += c.x * er - c.y * ei;
-          }
+          const R ei = h.x * l.y + h.y * l.x;   // sin(2 pi r / M)
+          acc[m] += c.x * er - c.y * ei;
           r += st;
           if (r >= (uint32_t)M) r -= (uint32_t)M;
         }
@@ -437,24 +445,20 @@ ss_status get_plan(int64_t M, ss_precision prec, cudaStream_t st, std::shared_pt
 }
 
 template <typename R, int TAB>
-ss_status launch_sample(const SftPlan& P, bool real, unsigned grid, size_t sm, const int64_t* q, const int64_t* step,
-                        const double2* coef, int64_t n, void* out, cudaStream_t st) {
+ss_status launch_sample(const SftPlan& P, unsigned grid, size_t sm, const int64_t* q, const int64_t* step,
+                        const double2* coef, const int64_t* n_dev, void* out, cudaStream_t st) {
   using T2 = typename C2<R>::T;
   auto lo = reinterpret_cast<const T2*>(TAB == 2 ? P.full.get() : P.lo.get());
   auto hi = reinterpret_cast<const T2*>(P.hi.get());
-  if (real) {
-    SS_CUDA(cudaFuncSetAttribute(k_sample<R, TAB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_sample<R, TAB, true><<<grid, kSampThreads, sm, st>>>(P.M, P.bl, P.H, lo, hi, q, step, coef, n,
-                                                           reinterpret_cast<R*>(out));
-  } else {
-    SS_CUDA(cudaFuncSetAttribute(k_sample<R, TAB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_sample<R, TAB, false><<<grid, kSampThreads, sm, st>>>(P.M, P.bl, P.H, lo, hi, q, step, coef, n,
-                                                            reinterpret_cast<R*>(out));
-  }
+  SS_CUDA(cudaFuncSetAttribute(k_sample<R, TAB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_sample<R, TAB><<<grid, kSampThreads, sm, st>>>(P.M, P.bl, P.H, lo, hi, q, step, coef, n_dev,
+                                                   reinterpret_cast<R*>(out));
   SS_LAUNCH_CHECK();
   return SS_OK;
 }
 
+// Merge +-p terms (exact rewrite of the real sum) and evaluate; no host
+// synchronisation (term counts stay on the device).
 ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, void* out, cudaStream_t st) {
   const int64_t n = g->n_terms;
   const int64_t Lsz = 1ll << P.bl;
@@ -463,9 +467,9 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
     SS_CUDA(cudaMemsetAsync(out, 0, P.M * (P.prec == SS_FP64 ? sizeof(double) : sizeof(float)), st));
     return SS_OK;
   }
-  // merge +-p terms (exact rewrite of the real sum), then evaluate
+  if (n > 46340) SS_FAIL(SS_ERR_INVALID, "lattice_sample: more than 46340 terms");
   DevBuf<int64_t> q, step, total;
-  DevBuf<int32_t> flag, pos, imag;
+  DevBuf<int32_t> flag, pos, imag, first;
   DevBuf<double2> merged, coef;
   SS_TRY(q.alloc(n, st));
   SS_TRY(step.alloc(n, st));
@@ -473,12 +477,10 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
   SS_TRY(flag.alloc(n, st));
   SS_TRY(pos.alloc(n, st));
   SS_TRY(imag.alloc(1, st));
+  SS_TRY(first.alloc(n, st));
   SS_TRY(merged.alloc(n, st));
   SS_TRY(coef.alloc(n, st));
   SS_CUDA(cudaMemsetAsync(imag.get(), 0, sizeof(int32_t), st));
-  if (n > 46340) SS_FAIL(SS_ERR_INVALID, "lattice_sample: more than 46340 terms");
-  DevBuf<int32_t> first;
-  SS_TRY(first.alloc(n, st));
   k_fill_first<<<nblk(n), 256, 0, st>>>(first.get(), n);
   k_merge_first<<<nblk(n * n), 256, 0, st>>>(g->freq, n, L.d, first.get());
   k_merge_sum<<<nblk(n), 256, 0, st>>>(g->freq, reinterpret_cast<const double2*>(g->coef), n, L.d, first.get(),
@@ -488,49 +490,57 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
   k_compact_terms<<<nblk(n), 256, 0, st>>>(g->freq, n, L, flag.get(), pos.get(), merged.get(), q.get(), step.get(),
                                            coef.get());
   SS_LAUNCH_CHECK();
-  int64_t nm = 0;
-  int32_t has_imag = 0;
-  SS_CUDA(cudaMemcpyAsync(&nm, total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaMemcpyAsync(&has_imag, imag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
-  const bool real = has_imag == 0;
   if (P.prec == SS_FP64) {
-    const size_t terms_sm = kTermChunk * (2 * sizeof(int64_t) + sizeof(double2));
     if (P.full.get() && P.df) {
       auto tab = reinterpret_cast<const float4*>(P.full.get());
-      if (real)
-        k_sample_df<true><<<grid, kSampThreads, 0, st>>>(P.M, tab, q.get(), step.get(), coef.get(), nm,
-                                                         reinterpret_cast<double*>(out));
-      else
-        k_sample_df<false><<<grid, kSampThreads, 0, st>>>(P.M, tab, q.get(), step.get(), coef.get(), nm,
-                                                          reinterpret_cast<double*>(out));
+      DevBuf<float4> W;
+      SS_TRY(W.alloc(n * kSampPerThread, st));
+      k_term_powers<<<nblk(n), 256, 0, st>>>(step.get(), total.get(), P.M, tab, W.get());
+      k_sample_df<<<grid, kSampThreads, 0, st>>>(P.M, tab, q.get(), W.get(), coef.get(), total.get(),
+                                                 reinterpret_cast<double*>(out));
       SS_LAUNCH_CHECK();
       return SS_OK;
     }
+    const size_t terms_sm = kTermChunk * (2 * sizeof(int64_t) + sizeof(double2));
     if (P.full.get())
-      return launch_sample<double, 2>(P, real, grid, terms_sm, q.get(), step.get(), coef.get(), nm, out, st);
+      return launch_sample<double, 2>(P, grid, terms_sm, q.get(), step.get(), coef.get(), total.get(), out, st);
     const size_t tab_sm = (Lsz + P.H) * sizeof(double2);
     const bool smem = tab_sm + terms_sm <= 200 * 1024;
     const size_t sm = (smem ? tab_sm : 0) + terms_sm;
-    if (smem) return launch_sample<double, 0>(P, real, grid, sm, q.get(), step.get(), coef.get(), nm, out, st);
-    return launch_sample<double, 1>(P, real, grid, sm, q.get(), step.get(), coef.get(), nm, out, st);
+    if (smem) return launch_sample<double, 0>(P, grid, sm, q.get(), step.get(), coef.get(), total.get(), out, st);
+    return launch_sample<double, 1>(P, grid, sm, q.get(), step.get(), coef.get(), total.get(), out, st);
   }
   const size_t terms_sm = kTermChunk * (2 * sizeof(int64_t) + sizeof(float2));
   const size_t tab_sm = (Lsz + P.H) * sizeof(float2);
   const bool smem = tab_sm + terms_sm <= 200 * 1024;
   const size_t sm = (smem ? tab_sm : 0) + terms_sm;
-  if (smem) return launch_sample<float, 0>(P, real, grid, sm, q.get(), step.get(), coef.get(), nm, out, st);
-  return launch_sample<float, 1>(P, real, grid, sm, q.get(), step.get(), coef.get(), nm, out, st);
+  if (smem) return launch_sample<float, 0>(P, grid, sm, q.get(), step.get(), coef.get(), total.get(), out, st);
+  return launch_sample<float, 1>(P, grid, sm, q.get(), step.get(), coef.get(), total.get(), out, st);
 }
 
+// Bins, threshold and compaction in candidate order; the reconstructing and
+// symmetry checks run on the device beside them and are read back with the
+// kept count in one synchronisation at the end.
 ss_status recover_from(const SftPlan& P, const LatticeDev& L, const void* samples, const int32_t* cand, int64_t n_cand,
                        int64_t s_max, double tau, int32_t* freq_out, double* val_out, int64_t* n_out, cudaStream_t st) {
-  // reconstructing + symmetric candidate set
-  DevBuf<int64_t> res;
+  DevBuf<int64_t> res, total;
+  DevBuf<unsigned long long> table, maxbits;
+  DevBuf<int32_t> flags, flag, pos;
+  DevBuf<double2> val;
+  DevBuf<double> mag;
+  uint64_t cap = 1;
+  while (cap < (uint64_t)(2 * n_cand)) cap <<= 1;
   SS_TRY(res.alloc(n_cand, st));
+  SS_TRY(table.alloc(cap, st));
+  SS_TRY(flags.alloc(4, st));
+  SS_TRY(val.alloc(n_cand, st));
+  SS_TRY(mag.alloc(n_cand, st));
+  SS_TRY(maxbits.alloc(1, st));
+  SS_TRY(flag.alloc(n_cand, st));
+  SS_TRY(pos.alloc(n_cand, st));
+  SS_TRY(total.alloc(1, st));
   SS_TRY(residues(cand, n_cand, L, res.get(), st));
-  SS_TRY(check_reconstructing(cand, n_cand, L, res.get(), true, st));
-  // FFT
+  SS_TRY(check_reconstructing_async(cand, n_cand, L, res.get(), true, table.get(), cap, flags.get(), st));
   cufftResult r = cufftSetStream(P.fft, st);
   if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cufftSetStream failed: %d", (int)r);
   if (P.prec == SS_FP64)
@@ -540,18 +550,6 @@ ss_status recover_from(const SftPlan& P, const LatticeDev& L, const void* sample
     r = cufftExecR2C(P.fft, reinterpret_cast<cufftReal*>(const_cast<void*>(samples)),
                      reinterpret_cast<cufftComplex*>(P.spectrum.get()));
   if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cuFFT exec failed: %d", (int)r);
-  // bins, threshold, compaction in candidate order
-  DevBuf<double2> val;
-  DevBuf<double> mag;
-  DevBuf<unsigned long long> maxbits;
-  DevBuf<int32_t> flag, pos;
-  DevBuf<int64_t> total;
-  SS_TRY(val.alloc(n_cand, st));
-  SS_TRY(mag.alloc(n_cand, st));
-  SS_TRY(maxbits.alloc(1, st));
-  SS_TRY(flag.alloc(n_cand, st));
-  SS_TRY(pos.alloc(n_cand, st));
-  SS_TRY(total.alloc(1, st));
   SS_CUDA(cudaMemsetAsync(maxbits.get(), 0, sizeof(unsigned long long), st));
   if (P.prec == SS_FP64)
     k_extract<double2><<<nblk(n_cand), 256, 0, st>>>(cand, n_cand, L, reinterpret_cast<const double2*>(P.spectrum.get()),
@@ -562,16 +560,18 @@ ss_status recover_from(const SftPlan& P, const LatticeDev& L, const void* sample
   k_keep<<<nblk(n_cand), 256, 0, st>>>(mag.get(), n_cand, maxbits.get(), tau, flag.get());
   SS_LAUNCH_CHECK();
   SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), n_cand, total.get(), st));
-  int64_t kept = 0;
-  SS_CUDA(cudaMemcpyAsync(&kept, total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
-  if (s_max > 0 && kept > s_max)
-    SS_FAIL(SS_ERR_INVALID, "sft_recover: %lld terms above threshold exceed s_max = %lld", (long long)kept,
-            (long long)s_max);
   k_compact<<<nblk(n_cand), 256, 0, st>>>(cand, val.get(), n_cand, L.d, flag.get(), pos.get(), freq_out,
                                           reinterpret_cast<double2*>(val_out));
   SS_LAUNCH_CHECK();
+  int64_t kept = 0;
+  int32_t hf[4];
+  SS_CUDA(cudaMemcpyAsync(&kept, total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaMemcpyAsync(hf, flags.get(), sizeof(hf), cudaMemcpyDeviceToHost, st));
   SS_CUDA(cudaStreamSynchronize(st));
+  SS_TRY(reconstructing_status(hf, L.M));
+  if (s_max > 0 && kept > s_max)
+    SS_FAIL(SS_ERR_INVALID, "sft_recover: %lld terms above threshold exceed s_max = %lld", (long long)kept,
+            (long long)s_max);
   *n_out = kept;
   return SS_OK;
 }

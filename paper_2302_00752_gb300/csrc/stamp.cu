@@ -34,18 +34,24 @@ __device__ int lexcmp(const int32_t* a, const int32_t* b, int d) {
   return 0;
 }
 
-// Stable lexicographic rank of every row; flags duplicates.
+// Stable lexicographic rank of every row (rank must start at zero); flags
+// duplicates.  Thread (i, c) compares row i with rows [64c, 64c + 64).
+constexpr int kRankChunk = 64;
+
 __global__ void k_lex_rank(const int32_t* __restrict__ f, int64_t n, int d, int32_t* rank, int32_t* dup) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int64_t nc = (n + kRankChunk - 1) / kRankChunk;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * nc) return;
+  const int64_t i = t / nc, c = t - i * nc;
+  const int64_t j1 = min(n, (c + 1) * kRankChunk);
   int32_t r = 0;
   bool du = false;
-  for (int64_t j = 0; j < n; ++j) {
-    const int c = lexcmp(f + j * d, f + i * d, d);
-    if (c < 0 || (c == 0 && j < i)) ++r;
-    if (c == 0 && j != i) du = true;
+  for (int64_t j = c * kRankChunk; j < j1; ++j) {
+    const int cmp = lexcmp(f + j * d, f + i * d, d);
+    if (cmp < 0 || (cmp == 0 && j < i)) ++r;
+    if (cmp == 0 && j != i) du = true;
   }
-  rank[i] = r;
+  if (r) atomicAdd(rank + i, r);
   if (du) atomicExch(dup, 1);
 }
 
@@ -247,9 +253,10 @@ __global__ void k_finalize(KeyParams P, uint64_t* keys, int64_t par0, int s_a, c
 template <int WT>
 __global__ void k_neighbors(KeyParams P, const uint64_t* __restrict__ keys, int64_t size, int s_a,
                             const uint64_t* __restrict__ stepkey, const uint64_t* __restrict__ table,
-                            uint64_t capmask, int64_t zero_idx, int32_t* nbr) {
+                            uint64_t capmask, const int64_t* __restrict__ zero_dev, int32_t* nbr) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= size * s_a) return;
+  const int64_t zero_idx = *zero_dev;
   const int64_t i = c / s_a;
   const int j = (int)(c - i * s_a);
   int32_t out = -1;
@@ -391,7 +398,7 @@ static ss_status grow_keys(ss_stamp_s* S, int64_t need, cudaStream_t st) {
     SS_CUDA(cudaMemcpyAsync(l2.get(), S->level.get(), S->size, cudaMemcpyDeviceToDevice, st));
     SS_CUDA(cudaMemcpyAsync(n2.get(), S->norm.get(), S->size * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   }
-  SS_CUDA(cudaStreamSynchronize(st));
+  // the old buffers are released on their stream after the copies (stream order)
   std::swap(S->keys.p, k2.p); std::swap(S->keys.n, k2.n); std::swap(S->keys.s, k2.s);
   std::swap(S->level.p, l2.p); std::swap(S->level.n, l2.n); std::swap(S->level.s, l2.s);
   std::swap(S->norm.p, n2.p); std::swap(S->norm.n, n2.n); std::swap(S->norm.s, n2.s);
@@ -419,9 +426,12 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   SS_CUDA(cudaMemsetAsync(err.get(), 0, 4 * sizeof(int32_t), st));
 
   // signed lexicographic order of F and supp a_hat
-  k_lex_rank<<<nblk(n_f), 256, 0, st>>>(f_freq, n_f, d, rank.get(), err.get() + 1);
+  const int64_t ncf = (n_f + kRankChunk - 1) / kRankChunk, nca = (s_a + kRankChunk - 1) / kRankChunk;
+  SS_CUDA(cudaMemsetAsync(rank.get(), 0, std::max<int64_t>(n_f, s_a) * sizeof(int32_t), st));
+  k_lex_rank<<<nblk(n_f * ncf), 256, 0, st>>>(f_freq, n_f, d, rank.get(), err.get() + 1);
   k_scatter_rows<<<nblk(n_f), 256, 0, st>>>(f_freq, nullptr, n_f, d, rank.get(), Fs.get(), nullptr);
-  k_lex_rank<<<nblk(s_a), 256, 0, st>>>(a_hat->freq, s_a, d, rank.get(), err.get() + 2);
+  SS_CUDA(cudaMemsetAsync(rank.get(), 0, std::max<int64_t>(n_f, s_a) * sizeof(int32_t), st));
+  k_lex_rank<<<nblk(s_a * nca), 256, 0, st>>>(a_hat->freq, s_a, d, rank.get(), err.get() + 2);
   k_scatter_rows<<<nblk(s_a), 256, 0, st>>>(a_hat->freq, reinterpret_cast<const double2*>(a_hat->val), s_a, d,
                                             rank.get(), As.get(), avs.get());
   k_prep<<<1, 256, 0, st>>>(Fs.get(), n_f, As.get(), avs.get(), s_a, d, prep.get());
@@ -523,11 +533,9 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
                                                                       S->size, n, S->level.get(), S->norm.get(),
                                                                       S->table.get(), zidx.get())));
     SS_LAUNCH_CHECK();
-    SS_CUDA(cudaStreamSynchronize(st));
     S->size += added;
     S->level_start.push_back(S->size);
   }
-  SS_CUDA(cudaMemcpyAsync(&S->zero_idx, zidx.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
 
   // neighbour table
   S->rows_pad = (S->size + kSlice - 1) / kSlice * kSlice;
@@ -537,7 +545,6 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
             colbits_of(S->jbits));
   SS_TRY(grow_keys(S, S->rows_pad + 1, st));   // norm padded to rows_pad + 1
   SS_CUDA(cudaMemsetAsync(S->norm.get() + S->size, 0, (S->rows_pad + 1 - S->size) * sizeof(int32_t), st));
-  SS_CUDA(cudaStreamSynchronize(st));
   DevBuf<int32_t> nbr, slice_w;
   DevBuf<unsigned long long> d_nnz;
   SS_TRY(nbr.alloc((size_t)S->size * s_a, st));
@@ -547,7 +554,7 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   SS_CUDA(cudaMemsetAsync(slice_w.get(), 0, (S->n_slices + 1) * sizeof(int32_t), st));
   SS_DISPATCH_WT(L.WT, (k_neighbors<WT><<<nblk(S->size * s_a), 256, 0, st>>>(
                            P, S->keys.get(), S->size, s_a, S->stepkey.get(), S->table.get(), (uint64_t)S->cap - 1,
-                           S->zero_idx, nbr.get())));
+                           zidx.get(), nbr.get())));
   k_row_counts<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, slice_w.get(), d_nnz.get());
   SS_LAUNCH_CHECK();
   SS_TRY(S->slice_off.alloc(S->n_slices + 1, st));
@@ -556,6 +563,7 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   unsigned long long hnnz = 0;
   SS_CUDA(cudaMemcpyAsync(&total_w, d_total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   SS_CUDA(cudaMemcpyAsync(&hnnz, d_nnz.get(), sizeof(hnnz), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaMemcpyAsync(&S->zero_idx, zidx.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   SS_CUDA(cudaStreamSynchronize(st));
   S->nnz = (int64_t)hnnz;
   S->n_ent = total_w * kSlice;
