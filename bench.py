@@ -3,7 +3,10 @@
 Workload (default): the d = 10 plain-FP64 configuration - a with 10 cosines in
 [-8,8]^10 (s_a = 21), manufactured u with 20 +-pairs, f_hat = L[a_hat] u_hat
 (|supp f_hat| = 840), N = 3 (|S| = 334,440, 2.51e6 operator nonzeros), CBC
-lattice with M = 1,000,003.  Synthetic, seeded (workloads.make_cfg2).
+lattice with M = 10^6.  Synthetic, seeded (workloads.make_cfg2).  Secondary
+sections: the d = 100 workload (FP32 sampling and FFT at M = 2^26 + 15, |S| =
+1.15e6, FP32-refined solve) and the 512-instance batched solve (persistent,
+graph-replayed) against a loop of single solves.
 
 One step = the whole path: CBC lattice choice, sft_recover(a), sft_recover(f)
 (lattice sampling + length-M FFT + bin extraction), stamp_build (S^3 and the
@@ -50,6 +53,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the d=100 and batched sections")
     return ap.parse_args()
 
 
@@ -169,6 +173,133 @@ def run_reference(args, inst):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+# ---------------------------------------------------------------- helpers
+
+def count_launches(fn):
+    """Kernels of this library launched by fn() (CUPTI through torch.profiler);
+    None when the profiler is unavailable."""
+    import torch
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize()
+        names = [e.name for e in prof.events() if "ss::" in e.name]
+        return len(names)
+    except Exception:
+        return None
+
+
+def fp64_peak_gflops(sm_mhz):
+    """FP64 ALU peak: one FP64 FMA per SM clock (GB300; the per-SM rate comes
+    from the ncu FP64-pipe counters of k_sample<double>) x 152
+    SMs x 2 flops x clock."""
+    return 152 * 2 * sm_mhz * 1e6 / 1e9
+
+
+def d100_section(B, gp, flush, steps=2):
+    """The d = 100 workload: FP32 samples and FFT at M = 2^26 + 15, |S| = 1.15e6,
+    FP32-refined solve.  Times the whole path and its stages."""
+    import torch
+    inst = W.make_cfg5()
+    prep = gp.prepare(inst)
+    out = {"workload": "cfg5: d=100, s_a=41, 50 f pairs, N=3, FP32 sampling/FFT, FP32-refined solve"}
+    times = []
+    for it in range(steps + 1):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record()
+        prep.z, prep.M = gp.choose_lattice(prep.extra["lattice"], prep.cand)
+        ev[1].record()
+        af, av = B.sft_recover(prep.z, prep.M, prep.a_freq, prep.a_coef, prep.cand, tau=1e-4, precision="fp32")
+        ff, fv = B.sft_recover(prep.z, prep.M, prep.f_freq, prep.f_coef, prep.cand, tau=1e-4, precision="fp32")
+        ev[2].record()
+        stamp = B.stamp_build(af, av, ff, inst.N)
+        f_on, _ = stamp.scatter(ff, fv)
+        ev[3].record()
+        u, st = B.solve(stamp, f_on, 1e-12, 1000, "fp32")
+        ev[4].record()
+        ev[4].synchronize()
+        if it:
+            times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)] + [st["kernel_ms"]])
+        if it < steps:
+            stamp.destroy()
+    med = np.median(np.array(times), axis=0)
+    out.update({"M": int(prep.M), "stamp_size": stamp.size, "nnz": stamp.nnz,
+                "ms_per_step": float(sum(med[:4])),
+                "breakdown_ms": {"lattice": med[0], "sft": med[1], "stamp": med[2], "solve": med[3],
+                                 "solve_kernel": med[4]},
+                "solve": {"applies": st["applies"], "outer_iters": st["outer_iters"], "inner_iters": st["inner_iters"],
+                          "rel_residual": st["rel_residual"], "status": st["status"]},
+                "nnz_per_s": stamp.nnz * st["applies"] / (sum(med[:4]) / 1e3)})
+    # FP32 operator alone (the inner-CG kernel): algorithmic bytes per apply
+    x = torch.randn(stamp.size, dtype=torch.complex64, device="cuda")
+    for _ in range(3):
+        B.galerkin_apply(stamp, x)
+    reps = 20
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        B.galerkin_apply(stamp, x)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / reps
+    out["apply_fp32"] = {"ms": ms, "nnz_per_s": stamp.nnz / (ms / 1e3),
+                         "note": "standalone galerkin_apply (pack + operator), L2-warm back-to-back"}
+    stamp.destroy()
+    return out
+
+
+def batched_section(B, flush, n_inst=512, reps=3):
+    """The batched workload: 512 instances of uneven d, s_a and |S| (1e3..1e5),
+    FP32-refined, in one persistent graph-replayed launch vs a loop of single
+    solves.  Instance set-up (recovery and stamping) is not timed here."""
+    import torch
+    from paper_2302_00752_gb300 import pipeline as gp
+    insts = W.make_cfg4(n=n_inst)
+    stamps, fs = [], []
+    t0 = time.perf_counter()
+    for inst in insts:
+        p = gp.prepare(inst)
+        r = gp.run(p, tol=1e-12, solve_precision=None, solve=False)
+        stamps.append(r.stamp)
+        fs.append(r.f_on_S)
+    setup_s = time.perf_counter() - t0
+    batch = B.Batch(stamps)
+    us = [torch.empty_like(f) for f in fs]
+    best_ms, cfg = batch.autotune(fs, us, tol=1e-12, max_iter=500, precision="fp32")
+    batch.solve(fs, us, tol=1e-12, max_iter=500, precision="fp32", use_graph=True)
+    bt, lt = [], []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        _, stats = batch.solve(fs, us, tol=1e-12, max_iter=500, precision="fp32", use_graph=True)
+        b.record()
+        b.synchronize()
+        bt.append(a.elapsed_time(b))
+        flush.zero_()
+        a.record()
+        single = [B.solve(s, f, 1e-12, 500, "fp32") for s, f in zip(stamps, fs)]
+        b.record()
+        b.synchronize()
+        lt.append(a.elapsed_time(b))
+    applies = sum(st["applies"] for st in stats)
+    nnz_applied = sum(s.nnz * st["applies"] for s, st in zip(stamps, stats))
+    ok = all(st["status"] == "SS_OK" for st in stats)
+    sizes = [s.size for s in stamps]
+    out = {"workload": f"cfg4: {n_inst} instances, d 6..30, s_a 5..41, |S| {min(sizes)}..{max(sizes)}",
+           "total_rows": int(sum(sizes)), "total_nnz": int(sum(s.nnz for s in stamps)),
+           "persistent_graph_ms": statistics.median(bt), "loop_of_single_solves_ms": statistics.median(lt),
+           "speedup": statistics.median(lt) / statistics.median(bt),
+           "nnz_per_s": nnz_applied / (statistics.median(bt) / 1e3), "applies": applies, "all_converged": ok,
+           "autotuned": cfg, "autotune_best_ms": best_ms, "setup_s": setup_s}
+    batch.destroy()
+    for s in stamps:
+        s.destroy()
+    return out
 
 
 # ---------------------------------------------------------------- our path
@@ -301,21 +432,35 @@ def main():
         e2e_work += r["nnz"] * r["applies"]
     e2e_value = world * e2e_work / (sum(e2e_ms) / 1e3)
 
-    # roofline of the dominant kernel (see the design doc for the byte/flop model)
+    # roofline of the dominant kernel: the persistent FP64 CG (FP64 ALU bound;
+    # algorithmic flops: 8 per stored nonzero and application, 30 per row and
+    # CG iteration - see the design doc)
     med = {k: statistics.median(v) for k, v in stage.items()}
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
     nnz, size, iters = r["nnz"], r["size"], r["iters"]
-    solve_bytes = iters * (4 * nnz + 212 * size)
+    applies = r["applies"]
+    solve_flops = 8.0 * nnz * applies + 30.0 * size * iters
     kms = med["solve_kernel"]
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    achieved = solve_bytes / (kms / 1e3) / 1e9
-    roofline = {"kernel": "k_solve<FP64> (persistent CG)", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    clk = clocks.summary()
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak64 = fp64_peak_gflops(sm_max)
+    achieved = solve_flops / (kms / 1e3) / 1e9
+    roofline = {"kernel": "k_solve<0> (persistent FP64 CG)", "bound": "alu", "achieved": achieved, "peak": peak64,
+                "unit": "GFLOP/s (FP64)", "frac": achieved / peak64, "traffic": None,
+                "peak_source": "derived: 1 FP64 FMA/clk/SM (ncu FP64-pipe counters) x 152 SMs x 2 x sm_max_mhz",
+                "flops_per_launch": solve_flops, "kernel_ms": kms}
+    launches_per_step = count_launches(lambda: step(prep))
+    gpu_launches = launches_per_step * args.steps if launches_per_step is not None else None
+
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        try:
+            extra["d100"] = d100_section(B, gp, flush)
+        except Exception as e:  # reported, not hidden
+            extra["d100"] = {"error": repr(e)}
+        try:
+            extra["batched"] = batched_section(B, flush)
+        except Exception as e:
+            extra["batched"] = {"error": repr(e)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -338,9 +483,12 @@ def main():
             "breakdown_ms": med,
             "solve_only": tts,
             "roofline": roofline,
+            "gpu_launches": gpu_launches,
+            "gpu_launches_per_step": launches_per_step,
             "cpu_baseline": cpu,
-            "clocks": clocks.summary(),
+            "clocks": clk,
         }
+        line.update(extra)
         print(json.dumps(line))
     if world > 1:
         torch.distributed.barrier()

@@ -104,8 +104,9 @@ class Result:
     stats: dict
 
 
-def run(p: Prepared, tol=1e-12, max_iter=1000, tau=None, solve_precision=None, lattice=True):
-    """Algorithm 1: lattice, sft_recover(a), sft_recover(f), stamp_build, solve."""
+def run(p: Prepared, tol=1e-12, max_iter=1000, tau=None, solve_precision=None, lattice=True, solve=True):
+    """Algorithm 1: lattice, sft_recover(a), sft_recover(f), stamp_build, solve
+    (solve=False stops after the right-hand side on S)."""
     if lattice or p.z is None:
         p.z, p.M = choose_lattice(p.extra["lattice"], p.cand)
     tau = (1e-9 if p.sft_precision == "fp64" else 1e-4) if tau is None else tau
@@ -113,5 +114,7 @@ def run(p: Prepared, tol=1e-12, max_iter=1000, tau=None, solve_precision=None, l
     ff, fv = B.sft_recover(p.z, p.M, p.f_freq, p.f_coef, p.cand, tau=tau, precision=p.sft_precision)
     stamp = B.stamp_build(af, av, ff, p.N)
     f_on, _ = stamp.scatter(ff, fv)
+    if not solve:
+        return Result(p.z, p.M, af, av, ff, fv, stamp, f_on, None, {})
     u, stats = B.solve(stamp, f_on, tol, max_iter, solve_precision or p.solve_precision)
     return Result(p.z, p.M, af, av, ff, fv, stamp, f_on, u, stats)
