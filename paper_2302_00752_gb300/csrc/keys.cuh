@@ -85,17 +85,29 @@ __device__ __forceinline__ int32_t key_norm(const uint64_t* key, const KeyParams
   return s;
 }
 
+// Slot words: kEmpty, or [63] pending flag | [62:32] fingerprint | [31:0]
+// canonical index (final) or candidate id (pending).  The fingerprint is 31
+// bits of the key hash disjoint from the bits that pick the slot, so a probe
+// reads a stored key only when the fingerprints agree.
+__device__ __forceinline__ uint64_t slot_fp(uint64_t h) { return (h >> 33) & 0x7fffffffull; }
+__device__ __forceinline__ uint64_t slot_word(uint64_t fp, uint64_t low) { return (fp << 32) | low; }
+__device__ __forceinline__ uint64_t word_fp(uint64_t v) { return (v >> 32) & 0x7fffffffull; }
+__device__ __forceinline__ uint64_t word_low(uint64_t v) { return v & 0xffffffffull; }
+
 // Lookup of a finalised key: the canonical index, or -1.
 template <int WT>
 __device__ __forceinline__ int64_t table_find(const uint64_t* __restrict__ table, uint64_t capmask,
                                               const uint64_t* __restrict__ keys, const uint64_t* k) {
-  uint64_t h = hash_key<WT>(k) & capmask;
+  const uint64_t hh = hash_key<WT>(k), fp = slot_fp(hh);
+  uint64_t h = hh & capmask;
   for (uint64_t probe = 0; probe <= capmask; ++probe) {
     const uint64_t v = __ldg(table + h);
     if (v == kEmpty) return -1;
-    uint64_t o[WT];
-    load_key<WT>(keys, (int64_t)v, o);
-    if (key_eq<WT>(o, k)) return (int64_t)v;
+    if (word_fp(v) == fp) {
+      uint64_t o[WT];
+      load_key<WT>(keys, (int64_t)word_low(v), o);
+      if (key_eq<WT>(o, k)) return (int64_t)word_low(v);
+    }
     h = (h + 1) & capmask;
   }
   return -1;
@@ -107,6 +119,7 @@ __device__ __forceinline__ int64_t table_find(const uint64_t* __restrict__ table
     case 2: { constexpr int WT = 2; __VA_ARGS__; } break;    \
     case 4: { constexpr int WT = 4; __VA_ARGS__; } break;    \
     case 8: { constexpr int WT = 8; __VA_ARGS__; } break;    \
+    case 12: { constexpr int WT = 12; __VA_ARGS__; } break;  \
     case 16: { constexpr int WT = 16; __VA_ARGS__; } break;  \
     default: SS_FAIL(SS_ERR_KEY_RANGE, "unsupported key width %d", (int)(wt)); \
   }

@@ -87,7 +87,7 @@ struct DevBuf {
 
 constexpr double kTwoPiSq = 19.739208802178716;   // 2 pi^2 (half of the 4 pi^2 in eq. GF)
 constexpr uint64_t kEmpty = ~0ull;                // unused hash slot
-constexpr uint64_t kPending = 1ull << 62;         // slot claimed during the current level
+constexpr uint64_t kPending = 1ull << 63;         // slot claimed during the current level
 constexpr int kMaxWords = 16;                     // packed key words supported
 constexpr int kSlice = 32;                        // rows per neighbour-table slice (one warp)
 

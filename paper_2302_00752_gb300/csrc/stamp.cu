@@ -11,7 +11,9 @@
 // prefix sum over the winners in discovery order gives the canonical order
 // (first discovery over parents in index order and steps in lexicographic
 // order).  Keys of pending slots are never stored: they are re-derived from
-// the parent key and the step, so a claim is one 64-bit CAS.
+// the parent key and the step, so a claim is one 64-bit CAS.  Every slot word
+// also carries a 31-bit fingerprint of the key hash, so probes compare stored
+// keys (up to 12 words at d = 100) only when the fingerprints agree.
 #include <algorithm>
 #include <cmath>
 
@@ -135,10 +137,12 @@ __global__ void k_steps(KeyParams P, const int32_t* __restrict__ A, const double
 // Insert a finalised key with value idx (no duplicates present).
 template <int WT>
 __device__ bool table_insert_final(uint64_t* table, uint64_t capmask, const uint64_t* k, uint64_t idx) {
-  uint64_t h = hash_key<WT>(k) & capmask;
+  const uint64_t hh = hash_key<WT>(k);
+  const uint64_t word = slot_word(slot_fp(hh), idx);
+  uint64_t h = hh & capmask;
   for (uint64_t probe = 0; probe <= capmask; ++probe) {
     const uint64_t old = atomicCAS((unsigned long long*)(table + h), (unsigned long long)kEmpty,
-                                   (unsigned long long)idx);
+                                   (unsigned long long)word);
     if (old == kEmpty) return true;
     h = (h + 1) & capmask;
   }
@@ -183,8 +187,9 @@ __global__ void k_insert(KeyParams P, const uint64_t* __restrict__ keys, int64_t
   load_key<WT>(keys, par0 + par, pk);
   load_key<WT>(stepkey, j, sk);
   add_keys<WT>(pk, sk, P, ck);
-  const uint64_t mine = kPending | (uint64_t)c;
-  uint64_t h = hash_key<WT>(ck) & capmask;
+  const uint64_t hh = hash_key<WT>(ck), fp = slot_fp(hh);
+  const uint64_t mine = kPending | slot_word(fp, (uint64_t)c);
+  uint64_t h = hh & capmask;
   for (uint64_t probe = 0; probe <= capmask; ++probe) {
     uint64_t v = __ldcg((const unsigned long long*)(table + h));
     if (v == kEmpty) {
@@ -193,23 +198,26 @@ __global__ void k_insert(KeyParams P, const uint64_t* __restrict__ keys, int64_t
       if (old == kEmpty) { slot_of[c] = (int64_t)h; return; }
       v = old;
     }
-    uint64_t ok[WT];
-    if (v & kPending) {
-      const int64_t oc = (int64_t)(v & ~kPending);
-      const int64_t opar = oc / s_a;
-      const int oj = (int)(oc - opar * s_a);
-      uint64_t opk[WT], osk[WT];
-      load_key<WT>(keys, par0 + opar, opk);
-      load_key<WT>(stepkey, oj, osk);
-      add_keys<WT>(opk, osk, P, ok);
-      if (key_eq<WT>(ok, ck)) {
-        atomicMin((unsigned long long*)(table + h), (unsigned long long)mine);
-        slot_of[c] = (int64_t)h;
-        return;
+    if (word_fp(v) == fp) {
+      uint64_t ok[WT];
+      if (v & kPending) {
+        const int64_t oc = (int64_t)word_low(v);
+        const int64_t opar = oc / s_a;
+        const int oj = (int)(oc - opar * s_a);
+        uint64_t opk[WT], osk[WT];
+        load_key<WT>(keys, par0 + opar, opk);
+        load_key<WT>(stepkey, oj, osk);
+        add_keys<WT>(opk, osk, P, ok);
+        if (key_eq<WT>(ok, ck)) {
+          // same key, same fingerprint: the minimum keeps the smallest candidate id
+          atomicMin((unsigned long long*)(table + h), (unsigned long long)mine);
+          slot_of[c] = (int64_t)h;
+          return;
+        }
+      } else {
+        load_key<WT>(keys, (int64_t)word_low(v), ok);
+        if (key_eq<WT>(ok, ck)) { slot_of[c] = -1; return; }
       }
-    } else {
-      load_key<WT>(keys, (int64_t)v, ok);
-      if (key_eq<WT>(ok, ck)) { slot_of[c] = -1; return; }
     }
     h = (h + 1) & capmask;
   }
@@ -222,7 +230,8 @@ __global__ void k_winner_flags(const int64_t* __restrict__ slot_of, const uint64
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   const int64_t s = slot_of[c];
-  flag[c] = (s >= 0 && __ldg(table + s) == (kPending | (uint64_t)c)) ? 1 : 0;
+  const uint64_t v = s >= 0 ? __ldg(table + s) : kEmpty;
+  flag[c] = (s >= 0 && (v & kPending) && word_low(v) == (uint64_t)c) ? 1 : 0;
 }
 
 template <int WT>
@@ -245,7 +254,7 @@ __global__ void k_finalize(KeyParams P, uint64_t* keys, int64_t par0, int s_a, c
   const int32_t nr = key_norm<WT>(ck, P);
   norm[idx] = nr;
   if (nr == 0) *zero_idx = idx;
-  table[slot_of[c]] = (uint64_t)idx;
+  table[slot_of[c]] = slot_word(slot_fp(hash_key<WT>(ck)), (uint64_t)idx);
 }
 
 // Neighbour lookups: nbr[i*s_a + j] = index of k_i - p_j (= k_i + p_{s_a-1-j})
@@ -467,6 +476,7 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   L.W = (d + L.fpw - 1) / L.fpw;
   L.WT = 1;
   while (L.WT < L.W) L.WT <<= 1;
+  if (L.W > 8 && L.W <= 12) L.WT = 12;
   if (L.WT > kMaxWords) SS_FAIL(SS_ERR_KEY_RANGE, "stamp_build: key needs %d words (max %d)", L.W, kMaxWords);
   S->key = L;
   const KeyParams P = make_key_params(L);
@@ -508,7 +518,7 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   for (int n = 1; n <= N; ++n) {
     const int64_t par0 = S->level_start[n - 1], n_par = S->level_start[n] - par0;
     const int64_t ncand = n_par * s_a;
-    if (ncand > ((int64_t)1 << 40)) SS_FAIL(SS_ERR_KEY_RANGE, "stamp_build: too many candidates at level %d", n);
+    if (ncand >= ((int64_t)1 << 32) - 1) SS_FAIL(SS_ERR_KEY_RANGE, "stamp_build: too many candidates at level %d", n);
     if (ncand == 0) { S->level_start.push_back(S->size); continue; }
     SS_TRY(grow_table(S, S->size + n_par * (s_a - 1), P, st, err.get()));
     SS_TRY(grow_keys(S, S->size + n_par * (s_a - 1), st));
@@ -538,6 +548,7 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   }
 
   // neighbour table
+  if (S->size >= ((int64_t)1 << 31)) SS_FAIL(SS_ERR_KEY_RANGE, "stamp_build: |S| = %lld too large", (long long)S->size);
   S->rows_pad = (S->size + kSlice - 1) / kSlice * kSlice;
   S->n_slices = S->rows_pad / kSlice;
   if (S->rows_pad + 1 > ((int64_t)1 << colbits_of(S->jbits)))
