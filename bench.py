@@ -187,7 +187,7 @@ def count_launches(fn):
             fn()
             torch.cuda.synchronize()
         import re
-        mine = re.compile(r"\bk_[a-z]")          # this library's kernels are named k_*
+        mine = re.compile(r"(^|[^A-Za-z])k_[a-z]")   # this library's kernels are k_* (mangled or not)
         names = [e.name for e in prof.events() if mine.search(e.name) and "at::" not in e.name]
         return len(names)
     except Exception:

@@ -105,6 +105,98 @@ __global__ void k_term_powers(const int64_t* __restrict__ step, const int64_t* _
   for (int m = 0; m < kSampPerThread; ++m) W[t * kSampPerThread + m] = tab[((uint64_t)m * st) % (uint64_t)M];
 }
 
+// FP32 path: W_m = exp(2 pi i (m * step mod M) / M) in FP32 (from FP64 sincospi).
+__global__ void k_term_powers32(const int64_t* __restrict__ step, const int64_t* __restrict__ n_terms, int64_t M,
+                                float2* W) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= *n_terms) return;
+  const uint64_t st = (uint64_t)step[t];
+#pragma unroll
+  for (int m = 0; m < kSampPerThread; ++m) {
+    double s, c;
+    sincospi(2.0 * (double)(((uint64_t)m * st) % (uint64_t)M) / (double)M, &s, &c);
+    W[t * kSampPerThread + m] = make_float2((float)c, (float)s);
+  }
+}
+
+// Three-level FP32 tables: exp(2 pi i r / M) = T2[r >> 2b] T1[(r >> b) & m] T0[r & m]
+// with b = kT3Bits, each level tabulated from FP64 sincospi.
+constexpr int kT3Bits = 9;
+constexpr int kT3Size = 1 << kT3Bits;
+
+__global__ void k_twiddles3(int64_t M, int64_t n2, float2* t0, float2* t1, float2* t2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double s, c;
+  if (i < kT3Size) {
+    sincospi(2.0 * (double)i / (double)M, &s, &c);
+    t0[i] = make_float2((float)c, (float)s);
+    sincospi(2.0 * (double)((i << kT3Bits) % M) / (double)M, &s, &c);
+    t1[i] = make_float2((float)c, (float)s);
+  }
+  if (i < n2) {
+    sincospi(2.0 * (double)((i << (2 * kT3Bits)) % M) / (double)M, &s, &c);
+    t2[i] = make_float2((float)c, (float)s);
+  }
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// FP32 lattice evaluation: B = c exp(2 pi i r0 / M) from the shared-memory
+// tables once per term and thread, then Re(B W_m) per sample (W_m broadcast
+// from shared memory): two FP32 FMAs per term-sample.
+__global__ void __launch_bounds__(kSampThreads) k_sample32(int64_t M, int64_t n2, const float2* __restrict__ t0g,
+                                                           const float2* __restrict__ t1g,
+                                                           const float2* __restrict__ t2g,
+                                                           const int64_t* __restrict__ q,
+                                                           const float2* __restrict__ W,
+                                                           const double2* __restrict__ coef,
+                                                           const int64_t* __restrict__ n_terms_dev, float* out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* s_t0 = reinterpret_cast<float2*>(smem);
+  float2* s_t1 = s_t0 + kT3Size;
+  float2* s_t2 = s_t1 + kT3Size;
+  float2* s_w = s_t2 + n2;
+  float2* s_c = s_w + kTermChunk * kSampPerThread;
+  uint32_t* s_q = reinterpret_cast<uint32_t*>(s_c + kTermChunk);
+  for (int i = threadIdx.x; i < kT3Size; i += blockDim.x) {
+    s_t0[i] = t0g[i];
+    s_t1[i] = t1g[i];
+  }
+  for (int64_t i = threadIdx.x; i < n2; i += blockDim.x) s_t2[i] = t2g[i];
+  const int64_t n_terms = *n_terms_dev;
+  const uint32_t mask = kT3Size - 1;
+  const int64_t j0 = (int64_t)blockIdx.x * (kSampThreads * kSampPerThread) + threadIdx.x;
+  float acc[kSampPerThread];
+#pragma unroll
+  for (int m = 0; m < kSampPerThread; ++m) acc[m] = 0.f;
+  for (int64_t t0 = 0; t0 < n_terms; t0 += kTermChunk) {
+    const int tc = (n_terms - t0 < kTermChunk) ? (int)(n_terms - t0) : kTermChunk;
+    __syncthreads();
+    for (int i = threadIdx.x; i < tc; i += blockDim.x) {
+      s_q[i] = (uint32_t)q[t0 + i];
+      const double2 c = coef[t0 + i];
+      s_c[i] = make_float2((float)c.x, (float)c.y);
+    }
+    for (int i = threadIdx.x; i < tc * kSampPerThread; i += blockDim.x) s_w[i] = W[t0 * kSampPerThread + i];
+    __syncthreads();
+    for (int t = 0; t < tc; ++t) {
+      const uint32_t r0 = (uint32_t)(((uint64_t)j0 * (uint64_t)s_q[t]) % (uint64_t)M);
+      const float2 e = cmulf(cmulf(s_t2[r0 >> (2 * kT3Bits)], s_t1[(r0 >> kT3Bits) & mask]), s_t0[r0 & mask]);
+      const float2 b = cmulf(s_c[t], e);
+      const float2* w = s_w + t * kSampPerThread;
+#pragma unroll
+      for (int m = 0; m < kSampPerThread; ++m) acc[m] = fmaf(b.x, w[m].x, fmaf(-b.y, w[m].y, acc[m]));
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < kSampPerThread; ++m) {
+    const int64_t j = j0 + (int64_t)m * kSampThreads;
+    if (j < M) out[j] = acc[m];
+  }
+}
+
 // Lattice evaluation in double-float for the FP64 path.  Thread samples are
 // j0 + 256 m; with r0 = j0 q mod M and B = c exp(2 pi i r0 / M) (one table
 // gather and one double-float complex product per term and thread), sample m
@@ -370,6 +462,8 @@ struct SftPlan {
   cufftHandle fft = 0;
   bool has_fft = false;
   DevBuf<unsigned char> samples, spectrum, lo, hi, full;   // full: exp(2 pi i r/M), r < M
+  DevBuf<float2> t3[3];                                    // FP32 three-level tables
+  int64_t n2 = 0;
   bool df = false;                                         // full table in double-float form
   ~SftPlan() {
     if (has_fft) cufftDestroy(fft);
@@ -423,6 +517,15 @@ ss_status get_plan(int64_t M, ss_precision prec, cudaStream_t st, std::shared_pt
     k_twiddles<float><<<nblk(nt), 256, 0, st>>>(M, p->bl, p->H, reinterpret_cast<float2*>(p->lo.get()),
                                                 reinterpret_cast<float2*>(p->hi.get()));
   SS_LAUNCH_CHECK();
+  if (prec == SS_FP32) {
+    p->n2 = (M + (1ll << (2 * kT3Bits)) - 1) >> (2 * kT3Bits);
+    SS_TRY(p->t3[0].alloc(kT3Size, st));
+    SS_TRY(p->t3[1].alloc(kT3Size, st));
+    SS_TRY(p->t3[2].alloc(p->n2, st));
+    k_twiddles3<<<nblk(std::max<int64_t>(kT3Size, p->n2)), 256, 0, st>>>(M, p->n2, p->t3[0].get(), p->t3[1].get(),
+                                                                         p->t3[2].get());
+    SS_LAUNCH_CHECK();
+  }
   if (prec == SS_FP64 && M <= kFullTableMax) {
     SS_TRY(p->full.alloc(M * sizeof(double2), st));   // 16 bytes per entry in either form
     if (native_fp64_sampling())
@@ -438,6 +541,7 @@ ss_status get_plan(int64_t M, ss_precision prec, cudaStream_t st, std::shared_pt
   // the plan is cached across calls and streams
   SS_CUDA(cudaStreamSynchronize(st));
   p->samples.settle(); p->spectrum.settle(); p->lo.settle(); p->hi.settle(); p->full.settle();
+  for (auto& t : p->t3) t.settle();
   g_plans.push_front(p);
   while (g_plans.size() > kMaxPlans) g_plans.pop_back();
   *out = p;
@@ -510,12 +614,21 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
     if (smem) return launch_sample<double, 0>(P, grid, sm, q.get(), step.get(), coef.get(), total.get(), out, st);
     return launch_sample<double, 1>(P, grid, sm, q.get(), step.get(), coef.get(), total.get(), out, st);
   }
+  const size_t tab_sm = (2 * kT3Size + P.n2) * sizeof(float2);
+  const size_t w_sm = kTermChunk * (kSampPerThread * sizeof(float2) + sizeof(float2) + sizeof(uint32_t));
+  if (tab_sm + w_sm <= 200 * 1024) {
+    DevBuf<float2> W;
+    SS_TRY(W.alloc(n * kSampPerThread, st));
+    k_term_powers32<<<nblk(n), 256, 0, st>>>(step.get(), total.get(), P.M, W.get());
+    const size_t sm = tab_sm + w_sm;
+    SS_CUDA(cudaFuncSetAttribute(k_sample32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_sample32<<<grid, kSampThreads, sm, st>>>(P.M, P.n2, P.t3[0].get(), P.t3[1].get(), P.t3[2].get(), q.get(),
+                                               W.get(), coef.get(), total.get(), reinterpret_cast<float*>(out));
+    SS_LAUNCH_CHECK();
+    return SS_OK;
+  }
   const size_t terms_sm = kTermChunk * (2 * sizeof(int64_t) + sizeof(float2));
-  const size_t tab_sm = (Lsz + P.H) * sizeof(float2);
-  const bool smem = tab_sm + terms_sm <= 200 * 1024;
-  const size_t sm = (smem ? tab_sm : 0) + terms_sm;
-  if (smem) return launch_sample<float, 0>(P, grid, sm, q.get(), step.get(), coef.get(), total.get(), out, st);
-  return launch_sample<float, 1>(P, grid, sm, q.get(), step.get(), coef.get(), total.get(), out, st);
+  return launch_sample<float, 1>(P, grid, terms_sm, q.get(), step.get(), coef.get(), total.get(), out, st);
 }
 
 // Bins, threshold and compaction in candidate order; the reconstructing and
