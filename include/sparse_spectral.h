@@ -181,6 +181,15 @@ ss_status stamp_lookup(ss_stamp s, const int32_t* freq, int64_t n, int64_t* idx_
  * synchronises `stream`). */
 ss_status stamp_scatter(ss_stamp s, const ss_sparse* g, double* out, int64_t* n_outside, void* stream);
 
+/* Grow S^N to S^{N+levels} in place (eq. StampSet applied `levels` more times;
+ * the paper re-solves on successive stamping levels, Section "Low
+ * sparsity").  Canonical indices of the existing frequencies do not change: a
+ * vector on S^N is the prefix of the same vector on S^{N+levels}.  The key
+ * layout is widened when the new levels need it; the neighbour table is
+ * rebuilt.  Synchronises `stream` once per new level.  On error the stamp may
+ * only be destroyed. */
+ss_status stamp_extend(ss_stamp s, int32_t levels, void* stream);
+
 void stamp_destroy(ss_stamp s);
 
 /* -------------------------------------------------------------- operator */
@@ -192,6 +201,15 @@ void stamp_destroy(ss_stamp s);
  * FP32 per `prec` (FP32: FP32 values, FP32 accumulation).  Uses the stamp's
  * scratch: concurrent calls on one stamp must be on one stream. */
 ss_status galerkin_apply(ss_stamp s, const void* u, void* y, ss_precision prec, void* stream);
+
+/* Exact proxy error of Lemma ProxyError: with u given on the first n_u
+ * frequencies of S (u_prefix: device FP64 complex [n_u], zero elsewhere) and
+ * f_on_S (device FP64 complex [|S|]), writes out2[0] = ||f - L u||_2^2 and
+ * out2[1] = ||f||_2^2 over S (host, 2 doubles).  When S = S^{N+1} and u solves
+ * on S^N, L[a_hat] u is supported in S^{N+1} (Proposition LExpansion), so the
+ * sum is exact.  FP64 operator; deterministic reduction; synchronises `stream`. */
+ss_status proxy_residual(ss_stamp s, const double* u_prefix, int64_t n_u, const double* f_on_S, double* out2,
+                         void* stream);
 
 /* ----------------------------------------------------------------- solve */
 

@@ -15,6 +15,9 @@ factor l.k): when 0 is in S its row is replaced by the identity row, which
 pins u_hat_0 = 0 given f_hat_0 = 0.  Column-0 entries are zero and are not
 stored; neither the identity row nor zero-column entries count as nonzeros.
 
+The exact proxy error of Lemma ProxyError, ||f_hat - L[a_hat] u_hat||_2 /
+||f_hat||_2, is evaluated over all of Z^d by the same convolution (``proxy_error``).
+
 Pins: the bilinear-form identity (Proposition GalerkinBilinearForm) against
 trapezoidal quadrature of  integral a grad u . conj(grad v)  on a grid; the
 manufactured f_hat against the Fourier coefficients of -div(a grad u) computed
@@ -110,3 +113,15 @@ def nnz_count(S, a_freq):
             if any(l) and l in idx:
                 n += 1
     return n
+
+
+def proxy_error(a_freq, a_val, u_freq, u_val, f_freq, f_val):
+    """Lemma ProxyError: ||f_hat - L[a_hat] u_hat||_2 / ||f_hat||_2 over Z^d,
+    with L[a_hat] u_hat from ``convolve`` (exact support)."""
+    Lf, Lv = convolve(a_freq, a_val, u_freq, u_val)
+    r = {tuple(int(x) for x in k): v for k, v in zip(Lf.tolist(), Lv)}
+    for k, v in zip(np.asarray(f_freq, np.int64).tolist(), np.asarray(f_val)):
+        r[tuple(k)] = r.get(tuple(k), 0j) - v
+    num = np.sqrt(sum(abs(v) ** 2 for v in r.values()))
+    den = np.linalg.norm(np.asarray(f_val))
+    return float(num / den)

@@ -74,6 +74,8 @@ def _load():
         "stamp_lookup": (i32, [vp, vp, i64, vp, vp]),
         "stamp_scatter": (i32, [vp, P(Sparse), vp, P(i64), vp]),
         "stamp_destroy": (None, [vp]),
+        "stamp_extend": (i32, [vp, i32, vp]),
+        "proxy_residual": (i32, [vp, vp, i64, vp, P(dbl), vp]),
         "galerkin_apply": (i32, [vp, vp, vp, i32, vp]),
         "solve": (i32, [vp, vp, vp, dbl, i32, i32, P(SolveStats), vp]),
         "solve_set_config": (i32, [vp, i32, i32, i32]),
@@ -267,6 +269,15 @@ class Stamp:
         _check(lib.stamp_scatter(self.handle, C.byref(sp), _ptr(out), C.byref(outside), _stream()))
         return out, outside.value
 
+    def extend(self, levels=1):
+        """Grow S^N to S^{N+levels} in place (existing indices unchanged)."""
+        _check(lib.stamp_extend(self.handle, int(levels), _stream()))
+        size, nnz, zero = C.c_int64(), C.c_int64(), C.c_int64()
+        lv = C.c_int32()
+        _check(lib.stamp_info(self._h, C.byref(size), C.byref(nnz), C.byref(zero), C.byref(lv)))
+        self.size, self.nnz, self.zero_index, self.n_levels = size.value, nnz.value, zero.value, lv.value
+        return self
+
     def set_solve_config(self, block, blocks_per_sm, chunks_per_block):
         """Tile shape of the persistent solve (see solve_set_config)."""
         _check(lib.solve_set_config(self.handle, int(block), int(blocks_per_sm), int(chunks_per_block)))
@@ -299,6 +310,15 @@ def stamp_build(a_freq, a_val, f_freq, N):
     h = C.c_void_p()
     _check(lib.stamp_build(C.byref(sp), _ptr(ff), ff.shape[0], int(N), C.byref(h), _stream()))
     return Stamp(h.value, d)
+
+
+def proxy_residual(stamp, u_prefix, f_on_S):
+    """(||f - L u||^2, ||f||^2) over S with u on the first len(u_prefix) frequencies."""
+    u = _dev_c128(u_prefix)
+    f = _dev_c128(f_on_S)
+    out = (C.c_double * 2)()
+    _check(lib.proxy_residual(stamp.handle, _ptr(u), u.numel(), _ptr(f), out, _stream()))
+    return out[0], out[1]
 
 
 def galerkin_apply(stamp, u, precision=None):

@@ -2,6 +2,8 @@
 // One thread per row, one warp per 32-row slice of the sliced-ELL table: the
 // index stream is read coalesced (column-major inside a slice) and the values
 // of u are gathered from a record array that carries |l|^2 beside u_l.
+#include <algorithm>
+
 #include "apply.cuh"
 
 namespace ss {
@@ -63,6 +65,49 @@ __global__ void __launch_bounds__(256) k_apply32(OpView op, int64_t size, int64_
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// u on the first n_u rows (a solution on S^N is the prefix of S^{N+L}), zero after.
+__global__ void k_pack64_prefix(const double2* __restrict__ u, int64_t n_u, int64_t size, double2* rec) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < size) rec[2 * i] = i < n_u ? u[i] : make_double2(0.0, 0.0);
+}
+
+constexpr int kNormThreads = 256;
+
+// Per block: sum |f - y|^2 and |f|^2 over a fixed row range, fixed tree.
+__global__ void k_resid_partials(const double2* __restrict__ f, const double2* __restrict__ y, int64_t n,
+                                 int64_t rows_per_block, double2* part) {
+  __shared__ double2 sh[kNormThreads];
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = min(n, r0 + rows_per_block);
+  double num = 0.0, den = 0.0;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const double2 a = f[i], b = y[i];
+    const double ex = a.x - b.x, ey = a.y - b.y;
+    num += ex * ex + ey * ey;
+    den += a.x * a.x + a.y * a.y;
+  }
+  sh[threadIdx.x] = make_double2(num, den);
+  __syncthreads();
+  for (int o = kNormThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sh[threadIdx.x].x += sh[threadIdx.x + o].x;
+      sh[threadIdx.x].y += sh[threadIdx.x + o].y;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum_partials(const double2* __restrict__ part, int n, double2* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int i = 0; i < n; ++i) {
+    s.x += part[i].x;
+    s.y += part[i].y;
+  }
+  *out = s;
+}
+
 }  // namespace
 
 OpView op_view(const ss_stamp_s* s) {
@@ -118,4 +163,31 @@ extern "C" ss_status galerkin_apply(ss_stamp s, const void* u, void* y, ss_preci
     return launch_apply32(s, reinterpret_cast<float2*>(y), st);
   }
   SS_FAIL(SS_ERR_INVALID, "galerkin_apply: unknown precision %d", (int)prec);
+}
+
+extern "C" ss_status proxy_residual(ss_stamp s, const double* u_prefix, int64_t n_u, const double* f_on_S,
+                                    double* out2, void* stream) {
+  if (!s || !f_on_S || !out2 || (n_u > 0 && !u_prefix)) SS_FAIL(SS_ERR_INVALID, "proxy_residual: null argument");
+  if (n_u < 0 || n_u > s->size) SS_FAIL(SS_ERR_INVALID, "proxy_residual: n_u = %lld outside [0, |S|]", (long long)n_u);
+  cudaStream_t st = as_stream(stream);
+  k_pack64_prefix<<<nblk(s->size), 256, 0, st>>>(reinterpret_cast<const double2*>(u_prefix), n_u, s->size,
+                                                 s->rec64.get());
+  SS_LAUNCH_CHECK();
+  DevBuf<double2> y, part, sum;
+  const int64_t rows_per_block = 4096;
+  const int nb = (int)std::max<int64_t>(1, (s->size + rows_per_block - 1) / rows_per_block);
+  SS_TRY(y.alloc(s->size, st));
+  SS_TRY(part.alloc(nb, st));
+  SS_TRY(sum.alloc(1, st));
+  SS_TRY(launch_apply64(s, y.get(), st));
+  k_resid_partials<<<nb, kNormThreads, 0, st>>>(reinterpret_cast<const double2*>(f_on_S), y.get(), s->size,
+                                                rows_per_block, part.get());
+  k_sum_partials<<<1, 32, 0, st>>>(part.get(), nb, sum.get());
+  SS_LAUNCH_CHECK();
+  double2 h;
+  SS_CUDA(cudaMemcpyAsync(&h, sum.get(), sizeof(h), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  out2[0] = h.x;
+  out2[1] = h.y;
+  return SS_OK;
 }

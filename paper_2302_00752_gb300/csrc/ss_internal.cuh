@@ -133,6 +133,10 @@ struct ss_stamp_s {
   // scratch for galerkin_apply
   ss::DevBuf<float4> rec32;           // [rows_pad + 1]
   ss::DevBuf<double2> rec64;          // [2 * (rows_pad + 1)] (value, norm|pad) pairs
+  // build state kept for stamp_extend
+  int maxabs_f = 0, maxabs_a = 0;     // largest |coordinate| of F and of supp a_hat
+  ss::DevBuf<int32_t> err_dev;        // [4] device-side error words
+  ss::DevBuf<int64_t> zidx_dev;       // canonical index of k = 0, or -1
 };
 
 namespace ss {

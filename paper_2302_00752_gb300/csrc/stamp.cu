@@ -164,6 +164,16 @@ __global__ void k_level0(KeyParams P, const int32_t* __restrict__ F, int64_t n_f
 }
 
 template <int WT>
+__global__ void k_pack_rows(KeyParams P, const int32_t* __restrict__ freq, int64_t n, uint64_t* keys) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t k[WT];
+  pack_key<WT>(freq + i * P.d, P, k);
+#pragma unroll
+  for (int w = 0; w < WT; ++w) keys[i * WT + w] = k[w];
+}
+
+template <int WT>
 __global__ void k_rehash(const uint64_t* __restrict__ keys, int64_t size, uint64_t* table, uint64_t capmask,
                          int32_t* err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -407,64 +417,19 @@ static ss_status grow_keys(ss_stamp_s* S, int64_t need, cudaStream_t st) {
     SS_CUDA(cudaMemcpyAsync(l2.get(), S->level.get(), S->size, cudaMemcpyDeviceToDevice, st));
     SS_CUDA(cudaMemcpyAsync(n2.get(), S->norm.get(), S->size * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   }
-  // the old buffers are released on their stream after the copies (stream order)
+  // the old buffers are released on this stream, after the copies
   std::swap(S->keys.p, k2.p); std::swap(S->keys.n, k2.n); std::swap(S->keys.s, k2.s);
   std::swap(S->level.p, l2.p); std::swap(S->level.n, l2.n); std::swap(S->level.s, l2.s);
   std::swap(S->norm.p, n2.p); std::swap(S->norm.n, n2.n); std::swap(S->norm.s, n2.s);
+  k2.s = st;
+  l2.s = st;
+  n2.s = st;
   return SS_OK;
 }
 
-static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t* f_freq, int64_t n_f, int N,
-                            cudaStream_t st) {
-  const int d = a_hat->d;
-  const int s_a = (int)a_hat->n;
-  S->d = d;
-  S->N = N;
-  S->s_a = s_a;
-
-  DevBuf<int32_t> Fs, As, rank, scratch_i;
-  DevBuf<double2> avs;
-  DevBuf<PrepOut> prep;
-  DevBuf<int32_t> err;
-  SS_TRY(Fs.alloc(n_f * d, st));
-  SS_TRY(As.alloc((size_t)s_a * d, st));
-  SS_TRY(avs.alloc(s_a, st));
-  SS_TRY(rank.alloc(std::max<int64_t>(n_f, s_a), st));
-  SS_TRY(prep.alloc(1, st));
-  SS_TRY(err.alloc(4, st));
-  SS_CUDA(cudaMemsetAsync(err.get(), 0, 4 * sizeof(int32_t), st));
-
-  // signed lexicographic order of F and supp a_hat
-  const int64_t ncf = (n_f + kRankChunk - 1) / kRankChunk, nca = (s_a + kRankChunk - 1) / kRankChunk;
-  SS_CUDA(cudaMemsetAsync(rank.get(), 0, std::max<int64_t>(n_f, s_a) * sizeof(int32_t), st));
-  k_lex_rank<<<nblk(n_f * ncf), 256, 0, st>>>(f_freq, n_f, d, rank.get(), err.get() + 1);
-  k_scatter_rows<<<nblk(n_f), 256, 0, st>>>(f_freq, nullptr, n_f, d, rank.get(), Fs.get(), nullptr);
-  SS_CUDA(cudaMemsetAsync(rank.get(), 0, std::max<int64_t>(n_f, s_a) * sizeof(int32_t), st));
-  k_lex_rank<<<nblk(s_a * nca), 256, 0, st>>>(a_hat->freq, s_a, d, rank.get(), err.get() + 2);
-  k_scatter_rows<<<nblk(s_a), 256, 0, st>>>(a_hat->freq, reinterpret_cast<const double2*>(a_hat->val), s_a, d,
-                                            rank.get(), As.get(), avs.get());
-  k_prep<<<1, 256, 0, st>>>(Fs.get(), n_f, As.get(), avs.get(), s_a, d, prep.get());
-  SS_LAUNCH_CHECK();
-  PrepOut h{};
-  int32_t herr[4];
-  SS_CUDA(cudaMemcpyAsync(&h, prep.get(), sizeof(h), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaMemcpyAsync(herr, err.get(), sizeof(herr), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
-  if (herr[1]) SS_FAIL(SS_ERR_INVALID, "stamp_build: duplicate frequencies in F");
-  if (herr[2]) SS_FAIL(SS_ERR_INVALID, "stamp_build: duplicate frequencies in supp a_hat");
-  if (h.zero_in_f) SS_FAIL(SS_ERR_INVALID, "stamp_build: F contains k = 0 (f_hat_0 must vanish)");
-  if (h.bad_sym) SS_FAIL(SS_ERR_INVALID, "stamp_build: supp a_hat must contain 0 and be closed under negation");
-  if (h.bad_herm) SS_FAIL(SS_ERR_INVALID, "stamp_build: a_hat is not Hermitian (a must be real)");
-  if (!(h.off_l1 < h.a0_abs)) SS_FAIL(SS_ERR_NOT_ELLIPTIC, "stamp_build: ||a_hat - a_hat_0||_1 = %g >= |a_hat_0| = %g",
-                                       h.off_l1, h.a0_abs);
-  if (!(h.a0_re > 0)) SS_FAIL(SS_ERR_NOT_ELLIPTIC, "stamp_build: Re(a_hat_0) must be positive");
-  S->a0 = h.a0_re;
-  S->j0 = h.j0;
-
-  // key layout: every frequency of S^{N+1} must fit (neighbour lookups reach one level further)
-  const int64_t maxabs = (int64_t)h.maxabs_f + (int64_t)(N + 1) * h.maxabs_a;
+static ss_status make_layout(int d, int64_t maxabs, KeyLayout* out) {
   if ((double)d * (double)maxabs * (double)maxabs >= (double)(1 << 29))
-    SS_FAIL(SS_ERR_KEY_RANGE, "stamp_build: |k|^2 may reach %g; integer dot products need < 2^29",
+    SS_FAIL(SS_ERR_KEY_RANGE, "stamp: |k|^2 may reach %g; integer dot products need < 2^29",
             (double)d * maxabs * maxabs);
   int b = 1;
   while (((int64_t)1 << (b - 1)) - 1 < maxabs) ++b;
@@ -477,7 +442,194 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   L.WT = 1;
   while (L.WT < L.W) L.WT <<= 1;
   if (L.W > 8 && L.W <= 12) L.WT = 12;
-  if (L.WT > kMaxWords) SS_FAIL(SS_ERR_KEY_RANGE, "stamp_build: key needs %d words (max %d)", L.W, kMaxWords);
+  if (L.WT > kMaxWords) SS_FAIL(SS_ERR_KEY_RANGE, "stamp: key needs %d words (max %d)", L.W, kMaxWords);
+  *out = L;
+  return SS_OK;
+}
+
+// Levels n_from..n_to of the breadth-first construction (see the file comment).
+static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st) {
+  const KeyParams P = make_key_params(S->key);
+  const int s_a = S->s_a;
+  DevBuf<int64_t> slot_of, d_total;
+  DevBuf<int32_t> flag;
+  SS_TRY(d_total.alloc(1, st));
+  for (int n = n_from; n <= n_to; ++n) {
+    const int64_t par0 = S->level_start[n - 1], n_par = S->level_start[n] - par0;
+    const int64_t ncand = n_par * s_a;
+    if (ncand >= ((int64_t)1 << 32) - 1) SS_FAIL(SS_ERR_KEY_RANGE, "stamp: too many candidates at level %d", n);
+    if (ncand == 0) { S->level_start.push_back(S->size); continue; }
+    SS_TRY(grow_table(S, S->size + n_par * (s_a - 1), P, st, S->err_dev.get()));
+    SS_TRY(grow_keys(S, S->size + n_par * (s_a - 1), st));
+    SS_TRY(slot_of.ensure(ncand, st));
+    SS_TRY(flag.ensure(ncand, st));
+    SS_DISPATCH_WT(S->key.WT, (k_insert<WT><<<nblk(ncand), 256, 0, st>>>(P, S->keys.get(), par0, n_par, s_a, S->j0,
+                                                                         S->stepkey.get(), S->table.get(),
+                                                                         (uint64_t)S->cap - 1, slot_of.get(),
+                                                                         S->err_dev.get())));
+    k_winner_flags<<<nblk(ncand), 256, 0, st>>>(slot_of.get(), S->table.get(), ncand, flag.get());
+    SS_LAUNCH_CHECK();
+    DevBuf<int32_t> pos;
+    SS_TRY(pos.alloc(ncand, st));
+    SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), ncand, d_total.get(), st));
+    int64_t added = 0;
+    int32_t e = 0;
+    SS_CUDA(cudaMemcpyAsync(&added, d_total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SS_CUDA(cudaMemcpyAsync(&e, S->err_dev.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SS_CUDA(cudaStreamSynchronize(st));
+    if (e) SS_FAIL((ss_status)e, "stamp: hash table exhausted at level %d", n);
+    SS_DISPATCH_WT(S->key.WT, (k_finalize<WT><<<nblk(ncand), 256, 0, st>>>(P, S->keys.get(), par0, s_a,
+                                                                           S->stepkey.get(), slot_of.get(), flag.get(),
+                                                                           pos.get(), ncand, S->size, n,
+                                                                           S->level.get(), S->norm.get(),
+                                                                           S->table.get(), S->zidx_dev.get())));
+    SS_LAUNCH_CHECK();
+    S->size += added;
+    S->level_start.push_back(S->size);
+  }
+  return SS_OK;
+}
+
+// Neighbour table (sliced ELL), FP64 entry coefficients and apply scratch
+// for the current set; synchronises and settles the stamp's buffers.
+static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
+  const KeyParams P = make_key_params(S->key);
+  const int s_a = S->s_a;
+  if (S->size >= ((int64_t)1 << 31)) SS_FAIL(SS_ERR_KEY_RANGE, "stamp: |S| = %lld too large", (long long)S->size);
+  S->rows_pad = (S->size + kSlice - 1) / kSlice * kSlice;
+  S->n_slices = S->rows_pad / kSlice;
+  if (S->rows_pad + 1 > ((int64_t)1 << colbits_of(S->jbits)))
+    SS_FAIL(SS_ERR_KEY_RANGE, "stamp: |S| = %lld too large for %d-bit columns", (long long)S->size,
+            colbits_of(S->jbits));
+  SS_TRY(grow_keys(S, S->rows_pad + 1, st));   // norm padded to rows_pad + 1
+  SS_CUDA(cudaMemsetAsync(S->norm.get() + S->size, 0, (S->rows_pad + 1 - S->size) * sizeof(int32_t), st));
+  DevBuf<int32_t> nbr, slice_w;
+  DevBuf<unsigned long long> d_nnz;
+  DevBuf<int64_t> d_total;
+  SS_TRY(nbr.alloc((size_t)S->size * s_a, st));
+  SS_TRY(slice_w.alloc(S->n_slices + 1, st));
+  SS_TRY(d_nnz.alloc(1, st));
+  SS_TRY(d_total.alloc(1, st));
+  SS_CUDA(cudaMemsetAsync(d_nnz.get(), 0, sizeof(unsigned long long), st));
+  SS_CUDA(cudaMemsetAsync(slice_w.get(), 0, (S->n_slices + 1) * sizeof(int32_t), st));
+  SS_DISPATCH_WT(S->key.WT, (k_neighbors<WT><<<nblk(S->size * s_a), 256, 0, st>>>(
+                                P, S->keys.get(), S->size, s_a, S->stepkey.get(), S->table.get(),
+                                (uint64_t)S->cap - 1, S->zidx_dev.get(), nbr.get())));
+  k_row_counts<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, slice_w.get(), d_nnz.get());
+  SS_LAUNCH_CHECK();
+  SS_TRY(S->slice_off.alloc(S->n_slices + 1, st));
+  SS_TRY(exclusive_scan_i32(slice_w.get(), S->slice_off.get(), S->n_slices + 1, d_total.get(), st));
+  int64_t total_w = 0;
+  unsigned long long hnnz = 0;
+  SS_CUDA(cudaMemcpyAsync(&total_w, d_total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaMemcpyAsync(&hnnz, d_nnz.get(), sizeof(hnnz), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaMemcpyAsync(&S->zero_idx, S->zidx_dev.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  S->nnz = (int64_t)hnnz;
+  S->n_ent = total_w * kSlice;
+  SS_TRY(S->ent.alloc(S->n_ent + 1, st));
+  SS_TRY(S->ecoef64.alloc(S->n_ent + 1, st));
+  k_fill_slices<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, S->j0, S->slice_off.get(),
+                                                   colbits_of(S->jbits), S->norm.get(), S->pnorm.get(), S->ca64.get(),
+                                                   S->ent.get(), S->ecoef64.get());
+  SS_LAUNCH_CHECK();
+  SS_TRY(S->rec32.alloc(S->rows_pad + 1, st));
+  SS_TRY(S->rec64.alloc(2 * (S->rows_pad + 1), st));
+  k_init_records<<<nblk(S->rows_pad + 1), 256, 0, st>>>(S->norm.get(), S->rows_pad + 1, S->rec32.get(),
+                                                        S->rec64.get());
+  SS_LAUNCH_CHECK();
+  int32_t e = 0;
+  SS_CUDA(cudaMemcpyAsync(&e, S->err_dev.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  if (e) SS_FAIL((ss_status)e, "stamp: hash table exhausted");
+  // the stamp's buffers outlive this call's stream (synchronised above)
+  S->keys.settle(); S->level.settle(); S->norm.settle(); S->table.settle();
+  S->afreq.settle(); S->stepkey.settle(); S->pnorm.settle(); S->aval.settle();
+  S->ca64.settle(); S->ca32.settle(); S->slice_off.settle(); S->ent.settle(); S->ecoef64.settle();
+  S->rec32.settle(); S->rec64.settle(); S->err_dev.settle(); S->zidx_dev.settle();
+  return SS_OK;
+}
+
+// Re-pack every key (and step) into a wider layout and rebuild the table.
+static ss_status relayout(ss_stamp_s* S, const KeyLayout& L2, cudaStream_t st) {
+  const KeyParams P1 = make_key_params(S->key), P2 = make_key_params(L2);
+  const int d = S->d;
+  DevBuf<int32_t> freq;
+  SS_TRY(freq.alloc((size_t)std::max<int64_t>(S->size, 1) * d, st));
+  SS_DISPATCH_WT(S->key.WT, (k_export<WT><<<nblk(S->size), 256, 0, st>>>(P1, S->keys.get(), S->size, freq.get())));
+  SS_LAUNCH_CHECK();
+  const int64_t cap_rows = (int64_t)(S->keys.n / S->key.WT);
+  DevBuf<uint64_t> k2;
+  SS_TRY(k2.alloc((size_t)cap_rows * L2.WT, st));
+  SS_DISPATCH_WT(L2.WT, (k_pack_rows<WT><<<nblk(S->size), 256, 0, st>>>(P2, freq.get(), S->size, k2.get())));
+  SS_LAUNCH_CHECK();
+  std::swap(S->keys.p, k2.p); std::swap(S->keys.n, k2.n); std::swap(S->keys.s, k2.s);
+  k2.s = st;   // the old keys are freed on this stream, after the export
+  S->key = L2;
+  SS_TRY(S->stepkey.alloc((size_t)S->s_a * L2.WT, st));
+  SS_DISPATCH_WT(L2.WT, (k_steps<WT><<<nblk(S->s_a), 256, 0, st>>>(P2, S->afreq.get(), S->aval.get(), S->s_a,
+                                                                   S->stepkey.get(), S->pnorm.get(), S->ca64.get(),
+                                                                   S->ca32.get())));
+  SS_LAUNCH_CHECK();
+  const int64_t cap = S->cap;
+  S->cap = 0;
+  return grow_table(S, std::max<int64_t>(cap / 2, S->size), P2, st, S->err_dev.get());
+}
+
+static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t* f_freq, int64_t n_f, int N,
+                            cudaStream_t st) {
+  const int d = a_hat->d;
+  const int s_a = (int)a_hat->n;
+  S->d = d;
+  S->N = N;
+  S->s_a = s_a;
+
+  DevBuf<int32_t> Fs, As, rank;
+  DevBuf<double2> avs;
+  DevBuf<PrepOut> prep;
+  SS_TRY(Fs.alloc(n_f * d, st));
+  SS_TRY(As.alloc((size_t)s_a * d, st));
+  SS_TRY(avs.alloc(s_a, st));
+  SS_TRY(rank.alloc(std::max<int64_t>(n_f, s_a), st));
+  SS_TRY(prep.alloc(1, st));
+  SS_TRY(S->err_dev.alloc(4, st));
+  SS_TRY(S->zidx_dev.alloc(1, st));
+  int32_t* err = S->err_dev.get();
+  SS_CUDA(cudaMemsetAsync(err, 0, 4 * sizeof(int32_t), st));
+  SS_CUDA(cudaMemsetAsync(S->zidx_dev.get(), 0xff, sizeof(int64_t), st));
+
+  // signed lexicographic order of F and supp a_hat
+  const int64_t ncf = (n_f + kRankChunk - 1) / kRankChunk, nca = (s_a + kRankChunk - 1) / kRankChunk;
+  SS_CUDA(cudaMemsetAsync(rank.get(), 0, std::max<int64_t>(n_f, s_a) * sizeof(int32_t), st));
+  k_lex_rank<<<nblk(n_f * ncf), 256, 0, st>>>(f_freq, n_f, d, rank.get(), err + 1);
+  k_scatter_rows<<<nblk(n_f), 256, 0, st>>>(f_freq, nullptr, n_f, d, rank.get(), Fs.get(), nullptr);
+  SS_CUDA(cudaMemsetAsync(rank.get(), 0, std::max<int64_t>(n_f, s_a) * sizeof(int32_t), st));
+  k_lex_rank<<<nblk(s_a * nca), 256, 0, st>>>(a_hat->freq, s_a, d, rank.get(), err + 2);
+  k_scatter_rows<<<nblk(s_a), 256, 0, st>>>(a_hat->freq, reinterpret_cast<const double2*>(a_hat->val), s_a, d,
+                                            rank.get(), As.get(), avs.get());
+  k_prep<<<1, 256, 0, st>>>(Fs.get(), n_f, As.get(), avs.get(), s_a, d, prep.get());
+  SS_LAUNCH_CHECK();
+  PrepOut h{};
+  int32_t herr[4];
+  SS_CUDA(cudaMemcpyAsync(&h, prep.get(), sizeof(h), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  if (herr[1]) SS_FAIL(SS_ERR_INVALID, "stamp_build: duplicate frequencies in F");
+  if (herr[2]) SS_FAIL(SS_ERR_INVALID, "stamp_build: duplicate frequencies in supp a_hat");
+  if (h.zero_in_f) SS_FAIL(SS_ERR_INVALID, "stamp_build: F contains k = 0 (f_hat_0 must vanish)");
+  if (h.bad_sym) SS_FAIL(SS_ERR_INVALID, "stamp_build: supp a_hat must contain 0 and be closed under negation");
+  if (h.bad_herm) SS_FAIL(SS_ERR_INVALID, "stamp_build: a_hat is not Hermitian (a must be real)");
+  if (!(h.off_l1 < h.a0_abs)) SS_FAIL(SS_ERR_NOT_ELLIPTIC, "stamp_build: ||a_hat - a_hat_0||_1 = %g >= |a_hat_0| = %g",
+                                       h.off_l1, h.a0_abs);
+  if (!(h.a0_re > 0)) SS_FAIL(SS_ERR_NOT_ELLIPTIC, "stamp_build: Re(a_hat_0) must be positive");
+  S->a0 = h.a0_re;
+  S->j0 = h.j0;
+  S->maxabs_f = h.maxabs_f;
+  S->maxabs_a = h.maxabs_a;
+
+  // key layout: every frequency of S^{N+1} must fit (neighbour lookups reach one level further)
+  KeyLayout L;
+  SS_TRY(make_layout(d, (int64_t)h.maxabs_f + (int64_t)(N + 1) * h.maxabs_a, &L));
   S->key = L;
   const KeyParams P = make_key_params(L);
   int jb = 0;
@@ -500,107 +652,46 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   // level 0
   S->level_start.assign(1, 0);
   SS_TRY(grow_keys(S, n_f, st));
-  SS_TRY(grow_table(S, n_f, P, st, err.get()));
-  DevBuf<int64_t> zidx;
-  SS_TRY(zidx.alloc(1, st));
-  SS_CUDA(cudaMemsetAsync(zidx.get(), 0xff, sizeof(int64_t), st));
+  SS_TRY(grow_table(S, n_f, P, st, err));
   SS_DISPATCH_WT(L.WT, (k_level0<WT><<<nblk(n_f), 256, 0, st>>>(P, Fs.get(), n_f, S->keys.get(), S->level.get(),
                                                                 S->norm.get(), S->table.get(),
-                                                                (uint64_t)S->cap - 1, err.get())));
+                                                                (uint64_t)S->cap - 1, err)));
   SS_LAUNCH_CHECK();
   S->size = n_f;
   S->level_start.push_back(n_f);
-
-  // levels 1..N
-  DevBuf<int64_t> slot_of, d_total;
-  DevBuf<int32_t> flag;
-  SS_TRY(d_total.alloc(1, st));
-  for (int n = 1; n <= N; ++n) {
-    const int64_t par0 = S->level_start[n - 1], n_par = S->level_start[n] - par0;
-    const int64_t ncand = n_par * s_a;
-    if (ncand >= ((int64_t)1 << 32) - 1) SS_FAIL(SS_ERR_KEY_RANGE, "stamp_build: too many candidates at level %d", n);
-    if (ncand == 0) { S->level_start.push_back(S->size); continue; }
-    SS_TRY(grow_table(S, S->size + n_par * (s_a - 1), P, st, err.get()));
-    SS_TRY(grow_keys(S, S->size + n_par * (s_a - 1), st));
-    SS_TRY(slot_of.ensure(ncand, st));
-    SS_TRY(flag.ensure(ncand, st));
-    SS_DISPATCH_WT(L.WT, (k_insert<WT><<<nblk(ncand), 256, 0, st>>>(P, S->keys.get(), par0, n_par, s_a, S->j0,
-                                                                    S->stepkey.get(), S->table.get(),
-                                                                    (uint64_t)S->cap - 1, slot_of.get(), err.get())));
-    k_winner_flags<<<nblk(ncand), 256, 0, st>>>(slot_of.get(), S->table.get(), ncand, flag.get());
-    SS_LAUNCH_CHECK();
-    DevBuf<int32_t> pos;
-    SS_TRY(pos.alloc(ncand, st));
-    SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), ncand, d_total.get(), st));
-    int64_t added = 0;
-    int32_t e = 0;
-    SS_CUDA(cudaMemcpyAsync(&added, d_total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    SS_CUDA(cudaMemcpyAsync(&e, err.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    SS_CUDA(cudaStreamSynchronize(st));
-    if (e) SS_FAIL((ss_status)e, "stamp_build: hash table exhausted at level %d", n);
-    SS_DISPATCH_WT(L.WT, (k_finalize<WT><<<nblk(ncand), 256, 0, st>>>(P, S->keys.get(), par0, s_a, S->stepkey.get(),
-                                                                      slot_of.get(), flag.get(), pos.get(), ncand,
-                                                                      S->size, n, S->level.get(), S->norm.get(),
-                                                                      S->table.get(), zidx.get())));
-    SS_LAUNCH_CHECK();
-    S->size += added;
-    S->level_start.push_back(S->size);
-  }
-
-  // neighbour table
-  if (S->size >= ((int64_t)1 << 31)) SS_FAIL(SS_ERR_KEY_RANGE, "stamp_build: |S| = %lld too large", (long long)S->size);
-  S->rows_pad = (S->size + kSlice - 1) / kSlice * kSlice;
-  S->n_slices = S->rows_pad / kSlice;
-  if (S->rows_pad + 1 > ((int64_t)1 << colbits_of(S->jbits)))
-    SS_FAIL(SS_ERR_KEY_RANGE, "stamp_build: |S| = %lld too large for %d-bit columns", (long long)S->size,
-            colbits_of(S->jbits));
-  SS_TRY(grow_keys(S, S->rows_pad + 1, st));   // norm padded to rows_pad + 1
-  SS_CUDA(cudaMemsetAsync(S->norm.get() + S->size, 0, (S->rows_pad + 1 - S->size) * sizeof(int32_t), st));
-  DevBuf<int32_t> nbr, slice_w;
-  DevBuf<unsigned long long> d_nnz;
-  SS_TRY(nbr.alloc((size_t)S->size * s_a, st));
-  SS_TRY(slice_w.alloc(S->n_slices + 1, st));
-  SS_TRY(d_nnz.alloc(1, st));
-  SS_CUDA(cudaMemsetAsync(d_nnz.get(), 0, sizeof(unsigned long long), st));
-  SS_CUDA(cudaMemsetAsync(slice_w.get(), 0, (S->n_slices + 1) * sizeof(int32_t), st));
-  SS_DISPATCH_WT(L.WT, (k_neighbors<WT><<<nblk(S->size * s_a), 256, 0, st>>>(
-                           P, S->keys.get(), S->size, s_a, S->stepkey.get(), S->table.get(), (uint64_t)S->cap - 1,
-                           zidx.get(), nbr.get())));
-  k_row_counts<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, slice_w.get(), d_nnz.get());
-  SS_LAUNCH_CHECK();
-  SS_TRY(S->slice_off.alloc(S->n_slices + 1, st));
-  SS_TRY(exclusive_scan_i32(slice_w.get(), S->slice_off.get(), S->n_slices + 1, d_total.get(), st));
-  int64_t total_w = 0;
-  unsigned long long hnnz = 0;
-  SS_CUDA(cudaMemcpyAsync(&total_w, d_total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaMemcpyAsync(&hnnz, d_nnz.get(), sizeof(hnnz), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaMemcpyAsync(&S->zero_idx, zidx.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
-  S->nnz = (int64_t)hnnz;
-  S->n_ent = total_w * kSlice;
-  SS_TRY(S->ent.alloc(S->n_ent + 1, st));
-  SS_TRY(S->ecoef64.alloc(S->n_ent + 1, st));
-  k_fill_slices<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, S->j0, S->slice_off.get(),
-                                                   colbits_of(S->jbits), S->norm.get(), S->pnorm.get(), S->ca64.get(),
-                                                   S->ent.get(), S->ecoef64.get());
-  SS_LAUNCH_CHECK();
-  SS_TRY(S->rec32.alloc(S->rows_pad + 1, st));
-  SS_TRY(S->rec64.alloc(2 * (S->rows_pad + 1), st));
-  k_init_records<<<nblk(S->rows_pad + 1), 256, 0, st>>>(S->norm.get(), S->rows_pad + 1, S->rec32.get(),
-                                                        S->rec64.get());
-  SS_LAUNCH_CHECK();
-  int32_t e = 0;
-  SS_CUDA(cudaMemcpyAsync(&e, err.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
-  if (e) SS_FAIL((ss_status)e, "stamp_build: hash table exhausted");
-  // the stamp's buffers outlive this call's stream (synchronised above)
-  S->keys.settle(); S->level.settle(); S->norm.settle(); S->table.settle();
-  S->afreq.settle(); S->stepkey.settle(); S->pnorm.settle(); S->aval.settle();
-  S->ca64.settle(); S->ca32.settle(); S->slice_off.settle(); S->ent.settle(); S->ecoef64.settle();
-  S->rec32.settle(); S->rec64.settle();
-  return SS_OK;
+  SS_TRY(run_levels(S, 1, N, st));
+  return build_operator(S, st);
 }
 
+// Buffers replaced during an extension are freed on the extension's stream,
+// after the work already queued there.
+static void rebind(ss_stamp_s* S, cudaStream_t st) {
+  S->keys.s = st;
+  S->level.s = st;
+  S->norm.s = st;
+  S->table.s = st;
+  S->stepkey.s = st;
+  S->slice_off.s = st;
+  S->ent.s = st;
+  S->ecoef64.s = st;
+  S->rec32.s = st;
+  S->rec64.s = st;
+}
+
+static ss_status extend_impl(ss_stamp_s* S, int levels, cudaStream_t st) {
+  rebind(S, st);
+  const int N2 = S->N + levels;
+  const int64_t need = (int64_t)S->maxabs_f + (int64_t)(N2 + 1) * S->maxabs_a;
+  const int64_t have = ((int64_t)1 << (S->key.b - 1)) - 1;
+  if (need > have) {
+    KeyLayout L2;
+    SS_TRY(make_layout(S->d, need, &L2));
+    SS_TRY(relayout(S, L2, st));
+  }
+  SS_TRY(run_levels(S, S->N + 1, N2, st));
+  S->N = N2;
+  return build_operator(S, st);
+}
 }  // namespace ss
 
 using namespace ss;
@@ -622,6 +713,16 @@ extern "C" ss_status stamp_build(const ss_sparse* a_hat, const int32_t* f_freq, 
   }
   *out = S;
   return SS_OK;
+}
+
+extern "C" ss_status stamp_extend(ss_stamp s, int32_t levels, void* stream) {
+  if (!s || levels < 0 || s->N + levels > 120) SS_FAIL(SS_ERR_INVALID, "stamp_extend: bad argument");
+  if (levels == 0) return SS_OK;
+  cudaStream_t st = as_stream(stream);
+  drop_solve_ctx(s);   // the solver's work split belongs to the old set
+  const ss_status r = extend_impl(s, levels, st);
+  if (r != SS_OK) cudaStreamSynchronize(st);
+  return r;
 }
 
 extern "C" void stamp_destroy(ss_stamp s) {

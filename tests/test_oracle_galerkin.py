@@ -149,3 +149,29 @@ def test_apply_rows_matches_matrix():
     u = rng.standard_normal(len(S)) + 1j * rng.standard_normal(len(S))
     rows = rng.choice(len(S), 10, replace=False)
     np.testing.assert_allclose(galerkin.apply_rows(S, af, av, u, rows), (L @ u)[rows], rtol=1e-13, atol=1e-12)
+
+
+def test_proxy_error_against_pointwise_residual():
+    # Lemma ProxyError by Plancherel: ||f - L[a]u||_{L2} from the pointwise
+    # residual -div(a grad u) - f on a grid (trapezoidal rule, exact here)
+    af, av, uf, uv = random_problem(11)
+    rng = np.random.default_rng(12)
+    ff = np.unique(rng.integers(-5, 6, size=(6, 2)), axis=0)
+    ff = ff[ff.any(axis=1)]
+    fv = rng.standard_normal(len(ff)) + 1j * rng.standard_normal(len(ff))
+    n = 32
+    x = grid(n, 2)
+    a_x, ga = series(x, af, av)
+    _, gu = series(x, uf, uv)
+    lap_u, _ = series(x, uf, -4 * np.pi ** 2 * (uf ** 2).sum(1) * uv)
+    f_x, _ = series(x, ff, fv)
+    res = -(np.sum(ga * gu, axis=1) + a_x * lap_u) - f_x
+    want = np.sqrt(np.mean(np.abs(res) ** 2)) / np.linalg.norm(fv)
+    got = galerkin.proxy_error(af, av, uf, uv, ff, fv)
+    assert abs(got - want) <= 1e-12 * want
+
+
+def test_proxy_error_vanishes_for_manufactured_data():
+    af, av, uf, uv = random_problem(13)
+    Lf, Lv = galerkin.convolve(af, av, uf, uv)
+    assert galerkin.proxy_error(af, av, uf, uv, Lf, Lv) < 1e-15
