@@ -254,13 +254,20 @@ def d100_section(B, gp, flush, steps=2):
     return out
 
 
-def batched_section(B, flush, n_inst=512, reps=3):
+def batched_section(B, flush, n_inst=512, reps=3, world=1, rank=0):
     """The batched workload: 512 instances of uneven d, s_a and |S| (1e3..1e5),
     FP32-refined, in one persistent graph-replayed launch vs a loop of single
-    solves.  Instance set-up (recovery and stamping) is not timed here."""
+    solves.  With several ranks the instances are split by estimated cost
+    (paper_2302_00752_gb300.shard; no data-path collective) and the time is the
+    slowest rank's.  Instance set-up (recovery and stamping) is not timed."""
     import torch
     from paper_2302_00752_gb300 import pipeline as gp
+    from paper_2302_00752_gb300.shard import partition_instances
     insts = W.make_cfg4(n=n_inst)
+    cost = [W.generic_stamp_count(2 * len(i.f.freq), 2 * len(i.a.freq) - 1, i.N) * (2 * len(i.a.freq) - 1)
+            for i in insts]
+    mine = partition_instances(cost, world)[rank]
+    insts = [insts[i] for i in mine]
     stamps, fs = [], []
     t0 = time.perf_counter()
     for inst in insts:
@@ -292,12 +299,21 @@ def batched_section(B, flush, n_inst=512, reps=3):
     nnz_applied = sum(s.nnz * st["applies"] for s, st in zip(stamps, stats))
     ok = all(st["status"] == "SS_OK" for st in stats)
     sizes = [s.size for s in stamps]
-    out = {"workload": f"cfg4: {n_inst} instances, d 6..30, s_a 5..41, |S| {min(sizes)}..{max(sizes)}",
-           "total_rows": int(sum(sizes)), "total_nnz": int(sum(s.nnz for s in stamps)),
-           "persistent_graph_ms": statistics.median(bt), "loop_of_single_solves_ms": statistics.median(lt),
-           "speedup": statistics.median(lt) / statistics.median(bt),
-           "nnz_per_s": nnz_applied / (statistics.median(bt) / 1e3), "applies": applies, "all_converged": ok,
-           "autotuned": cfg, "autotune_best_ms": best_ms, "setup_s": setup_s}
+    t_b, t_l = statistics.median(bt), statistics.median(lt)
+    if world > 1:
+        dev = torch.device("cuda", torch.cuda.current_device())
+        v = torch.tensor([t_b, t_l], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(v, op=torch.distributed.ReduceOp.MAX)
+        w = torch.tensor([nnz_applied, float(ok is False)], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(w)
+        t_b, t_l = float(v[0]), float(v[1])
+        nnz_applied, ok = float(w[0]), bool(w[1] == 0)
+    out = {"workload": f"cfg4: {n_inst} instances, d 6..30, s_a 5..41, |S| {min(sizes)}..{max(sizes)} (rank 0)",
+           "ranks": world, "instances_rank0": len(stamps),
+           "total_rows_rank0": int(sum(sizes)), "total_nnz_rank0": int(sum(s.nnz for s in stamps)),
+           "persistent_graph_ms": t_b, "loop_of_single_solves_ms": t_l,
+           "speedup": t_l / t_b, "nnz_per_s": nnz_applied / (t_b / 1e3), "applies_rank0": applies,
+           "all_converged": ok, "autotuned": cfg, "autotune_best_ms": best_ms, "setup_s": setup_s}
     batch.destroy()
     for s in stamps:
         s.destroy()
@@ -454,15 +470,15 @@ def main():
     gpu_launches = launches_per_step * args.steps if launches_per_step is not None else None
 
     extra = {}
-    if rank == 0 and not args.no_extra:
-        try:
-            extra["d100"] = d100_section(B, gp, flush)
-        except Exception as e:  # reported, not hidden
-            extra["d100"] = {"error": repr(e)}
-        try:
-            extra["batched"] = batched_section(B, flush)
-        except Exception as e:
-            extra["batched"] = {"error": repr(e)}
+    if not args.no_extra:
+        if rank == 0:
+            try:
+                extra["d100"] = d100_section(B, gp, flush)
+            except Exception as e:  # reported, not hidden
+                extra["d100"] = {"error": repr(e)}
+        if world > 1:
+            torch.distributed.barrier()
+        extra["batched"] = batched_section(B, flush, world=world, rank=rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
