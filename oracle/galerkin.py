@@ -17,8 +17,14 @@ stored; neither the identity row nor zero-column entries count as nonzeros.
 
 The exact proxy error of Lemma ProxyError, ||f_hat - L[a_hat] u_hat||_2 /
 ||f_hat||_2, is evaluated over all of Z^d by the same convolution (``proxy_error``).
+Its Monte Carlo form, ||f - f^{s,N}||_{L2} / ||f||_{L2} estimated from point
+values at uniform random points of T^d (Section "Code and testing overview"),
+is ``proxy_mc``: points on the grid (2^-32 Z)^d, so that every phase k.x mod 1
+is an exact integer fraction.
 
-Pins: the bilinear-form identity (Proposition GalerkinBilinearForm) against
+Pins: the Monte Carlo values against closed-form sines at chosen points and,
+averaged over a reconstructing power-of-two rank-1 lattice, against the exact
+proxy (Parseval); the bilinear-form identity (Proposition GalerkinBilinearForm) against
 trapezoidal quadrature of  integral a grad u . conj(grad v)  on a grid; the
 manufactured f_hat against the Fourier coefficients of -div(a grad u) computed
 pointwise; Hermitian symmetry; the constant-coefficient diagonal; the level
@@ -125,3 +131,32 @@ def proxy_error(a_freq, a_val, u_freq, u_val, f_freq, f_val):
     num = np.sqrt(sum(abs(v) ** 2 for v in r.values()))
     den = np.linalg.norm(np.asarray(f_val))
     return float(num / den)
+
+
+MC_GRID = 1 << 32
+
+
+def trig_at(freq, coef, X):
+    """sum_t Re(coef_t exp(2 pi i freq_t.x)) at the points x = X / 2^32
+    (X: integer [Q, d] in [0, 2^32)); the phase freq_t.X mod 2^32 is formed in
+    exact integers before the exponential."""
+    X = np.asarray(X, np.int64)
+    out = np.zeros(len(X), np.float64)
+    for k, c in zip(np.asarray(freq, np.int64).tolist(), np.asarray(coef, np.complex128)):
+        ph = (X @ np.array(k, np.int64)) % MC_GRID   # int64 wrap-around is harmless: 2^32 divides 2^64
+        out += (c * np.exp(2j * np.pi * (ph / MC_GRID))).real
+    return out
+
+
+def proxy_mc(a_freq, a_val, u_freq, u_val, f_freq, f_coef, X):
+    """Point values for the Monte Carlo proxy of Lemma ProxyError:
+    r(x) = f(x) - f^{s,N}(x) and f(x) at x = X / 2^32, where f is the trig sum
+    (f_freq, f_coef) and f^{s,N} = L[a_hat] u^{s,N} is taken on its exact
+    support (``convolve``).  The estimate is sqrt(sum r^2 / sum f^2)."""
+    g_freq, g_val = convolve(a_freq, a_val, u_freq, u_val)
+    fx = trig_at(f_freq, f_coef, X)
+    return fx - trig_at(g_freq, g_val, X), fx
+
+
+def mc_estimate(r, fx):
+    return float(np.sqrt(np.sum(np.square(r)) / np.sum(np.square(fx))))

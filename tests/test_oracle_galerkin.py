@@ -33,6 +33,12 @@ def random_problem(seed, dim=2, deg_a=3, deg_u=4, n_a=3, n_u=4, hermitian_u=Fals
     uf = np.unique(rng.integers(-deg_u, deg_u + 1, size=(n_u, dim)), axis=0)
     uf = uf[uf.any(axis=1)]
     uv = rng.standard_normal(len(uf)) + 1j * rng.standard_normal(len(uf))
+    if hermitian_u:      # u real: u_hat_{-k} = conj(u_hat_k)
+        d = {}
+        for k, v in zip(uf.tolist(), uv):
+            d[tuple(k)] = d.get(tuple(k), 0) + v / 2
+            d[tuple(-x for x in k)] = d.get(tuple(-x for x in k), 0) + np.conj(v) / 2
+        uf, uv = coeff_arrays(d)
     return af, av, uf, uv
 
 
@@ -175,3 +181,70 @@ def test_proxy_error_vanishes_for_manufactured_data():
     af, av, uf, uv = random_problem(13)
     Lf, Lv = galerkin.convolve(af, av, uf, uv)
     assert galerkin.proxy_error(af, av, uf, uv, Lf, Lv) < 1e-15
+
+
+def test_mc_point_values_against_closed_form():
+    # sin(2 pi k.x) and cos(2 pi k.x) written as Re(-i e_k) and Re(e_k), at
+    # points whose coordinates are exact binary fractions
+    rng = np.random.default_rng(21)
+    k = np.array([[3, -5, 7]])
+    X = rng.integers(0, 1 << 32, size=(50, 3), dtype=np.int64)
+    x = X / 2.0 ** 32
+    np.testing.assert_allclose(galerkin.trig_at(k, [-1j], X), np.sin(2 * np.pi * x @ k[0]), atol=1e-9)
+    np.testing.assert_allclose(galerkin.trig_at(k, [2.0], X), 2 * np.cos(2 * np.pi * x @ k[0]), atol=1e-9)
+    # a point where k.x = 1/4 exactly: sin = 1, cos = 0
+    Xq = np.array([[1 << 30, 0, 0]])
+    assert abs(galerkin.trig_at([[1, 0, 0]], [-1j], Xq)[0] - 1.0) < 1e-15
+    assert abs(galerkin.trig_at([[1, 0, 0]], [1.0], Xq)[0]) < 1e-15
+    # coordinates far out: the phase is taken mod 1 in integers
+    big = np.array([[2 ** 30 + 1, -(2 ** 30) + 3, 5]])
+    np.testing.assert_allclose(galerkin.trig_at(big, [1.0], X[:5]),
+                               np.cos(2 * np.pi * ((X[:5] @ big[0]) % (1 << 32)) / 2.0 ** 32), atol=1e-12)
+
+
+def power_of_two_lattice(freq, m, seed):
+    from oracle.lattice import is_reconstructing
+    rng = np.random.default_rng(seed)
+    M = 1 << m
+    for _ in range(1000):
+        z = rng.integers(1, M, size=freq.shape[1]) | 1
+        if is_reconstructing(freq, z, M):
+            return z, M
+    raise AssertionError("no reconstructing lattice")
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_mc_on_a_reconstructing_lattice_equals_exact_proxy(seed):
+    # averaging |r|^2 over a rank-1 lattice that separates supp(r_hat) is exact
+    # (Parseval on the lattice), so the Monte Carlo form reproduces the exact
+    # proxy to rounding
+    af, av, uf, uv = random_problem(40 + seed, hermitian_u=True)
+    rng = np.random.default_rng(seed)
+    f_trig = np.unique(rng.integers(-6, 7, size=(5, 2)), axis=0)
+    f_trig = f_trig[f_trig.any(axis=1)]
+    f_coef = rng.standard_normal(len(f_trig)) + 1j * rng.standard_normal(len(f_trig))
+    fF, fV = coeff_arrays(true_coefficients(f_trig, f_coef))
+    gF, _ = galerkin.convolve(af, av, uf, uv)
+    z, M = power_of_two_lattice(np.vstack([fF, gF]), 12, seed)
+    j = np.arange(M, dtype=np.int64)
+    X = ((j[:, None] * z[None, :]) % M) * ((1 << 32) // M)
+    r, fx = galerkin.proxy_mc(af, av, uf, uv, f_trig, f_coef, X)
+    want = galerkin.proxy_error(af, av, uf, uv, fF, fV)
+    assert want > 1e-3
+    assert abs(galerkin.mc_estimate(r, fx) - want) <= 1e-12 * want
+    # and the pointwise r is real-valued data: r = f - f^{s,N} with f^{s,N} real
+    assert np.isfinite(r).all()
+
+
+def test_mc_estimate_is_statistically_consistent():
+    af, av, uf, uv = random_problem(50, hermitian_u=True)
+    rng = np.random.default_rng(51)
+    f_trig = np.array([[1, 2], [3, -1], [0, 4]])
+    f_coef = np.array([1.0, 0.5j, -0.7 + 0.2j])
+    fF, fV = coeff_arrays(true_coefficients(f_trig, f_coef))
+    X = rng.integers(0, 1 << 32, size=(20000, 2), dtype=np.int64)
+    r, fx = galerkin.proxy_mc(af, av, uf, uv, f_trig, f_coef, X)
+    want = galerkin.proxy_error(af, av, uf, uv, fF, fV)
+    num, den = np.mean(r ** 2), np.mean(fx ** 2)
+    se = np.std(r ** 2) / np.sqrt(len(r)) / np.sum(np.abs(fV) ** 2)
+    assert abs(num / den - want ** 2) < 5 * se + 5 * np.std(fx ** 2) / np.sqrt(len(r)) * want ** 2
