@@ -182,13 +182,16 @@ def count_launches(fn):
     None when the profiler is unavailable."""
     import torch
     try:
+        from torch.autograd import DeviceType
         from torch.profiler import ProfilerActivity, profile
-        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        # device events are listed only beside CPU activity
+        with profile(activities=[ProfilerActivity.CPU, ProfilerActivity.CUDA]) as prof:
             fn()
             torch.cuda.synchronize()
         import re
         mine = re.compile(r"(^|[^A-Za-z])k_[a-z]")   # this library's kernels are k_* (mangled or not)
-        names = [e.name for e in prof.events() if mine.search(e.name) and "at::" not in e.name]
+        names = [e.name for e in prof.events()
+                 if e.device_type == DeviceType.CUDA and mine.search(e.name) and "at::" not in e.name]
         return len(names)
     except Exception:
         return None

@@ -211,6 +211,22 @@ ss_status galerkin_apply(ss_stamp s, const void* u, void* y, ss_precision prec, 
 ss_status proxy_residual(ss_stamp s, const double* u_prefix, int64_t n_u, const double* f_on_S, double* out2,
                          void* stream);
 
+/* Monte Carlo proxy error (Lemma ProxyError; Section "Code and testing
+ * overview"): point values at x_q = X[q] / 2^32 (X: device uint32 [Q][d], the
+ * caller's uniform random draws on the grid (2^-32 Z)^d):
+ *   f_out[q] = f(x_q) = sum_t Re(f.coef[t] exp(2 pi i f.freq[t] . x_q)),
+ *   r_out[q] = f(x_q) - f^{s,N}(x_q),  f^{s,N}(x) = sum_{k in S} (L u)_k exp(2 pi i k.x),
+ * with u on the first n_u frequencies of S (u_prefix: device FP64 complex
+ * [n_u], zero elsewhere) and L the operator on S's rows, (L u)_0 = 0.  When
+ * S = S^{N+1} and u solves on S^N, f^{s,N} = L[a_hat] u is exact (Proposition
+ * LExpansion).  The estimate of ||f - f^{s,N}||_{L2} / ||f||_{L2} is
+ * sqrt(sum r^2 / sum f^2).  Phases k.X mod 2^32 are exact integers; each
+ * term is evaluated in double-float arithmetic (about 1e-13 of |coef| per
+ * term).  r_out, f_out: device FP64 [Q].  Deterministic; asynchronous on
+ * `stream`; uses the stamp's operator scratch. */
+ss_status proxy_mc(ss_stamp s, const double* u_prefix, int64_t n_u, const ss_trig* f, const uint32_t* X, int64_t Q,
+                   double* r_out, double* f_out, void* stream);
+
 /* ----------------------------------------------------------------- solve */
 
 /* Solve L_{N,s} u = f on S (eq. SparseSpectralSFTEquation) by Jacobi-

@@ -76,6 +76,7 @@ def _load():
         "stamp_destroy": (None, [vp]),
         "stamp_extend": (i32, [vp, i32, vp]),
         "proxy_residual": (i32, [vp, vp, i64, vp, P(dbl), vp]),
+        "proxy_mc": (i32, [vp, vp, i64, P(Trig), vp, i64, vp, vp, vp]),
         "galerkin_apply": (i32, [vp, vp, vp, i32, vp]),
         "solve": (i32, [vp, vp, vp, dbl, i32, i32, P(SolveStats), vp]),
         "solve_set_config": (i32, [vp, i32, i32, i32]),
@@ -319,6 +320,20 @@ def proxy_residual(stamp, u_prefix, f_on_S):
     out = (C.c_double * 2)()
     _check(lib.proxy_residual(stamp.handle, _ptr(u), u.numel(), _ptr(f), out, _stream()))
     return out[0], out[1]
+
+
+def proxy_mc(stamp, u_prefix, f_freq, f_coef, X):
+    """Point values (r, f) of the Monte Carlo proxy at x = X / 2^32 (X uint32
+    [Q, d], numpy or tensor); the estimate is sqrt(sum r^2 / sum f^2)."""
+    u = _dev_c128(u_prefix)
+    g = _trig(f_freq, f_coef, stamp.d)
+    Xn = X.cpu().numpy() if torch.is_tensor(X) else np.asarray(X)
+    Xd = torch.from_numpy(np.ascontiguousarray(Xn.astype(np.uint32)).view(np.int32)).cuda()
+    Q = int(Xd.shape[0]) if Xd.dim() == 2 else 0
+    r = torch.empty(Q, dtype=torch.float64, device="cuda")
+    f = torch.empty(Q, dtype=torch.float64, device="cuda")
+    _check(lib.proxy_mc(stamp.handle, _ptr(u), u.numel(), C.byref(g), _ptr(Xd), Q, _ptr(r), _ptr(f), _stream()))
+    return r, f
 
 
 def galerkin_apply(stamp, u, precision=None):

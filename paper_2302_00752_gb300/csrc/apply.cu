@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(256) k_apply64(OpView op, int64_t size, int64_
   if (row < size) y[row] = acc;
 }
 
-__global__ void __launch_bounds__(256) k_apply32(OpView op, int64_t size, int64_t rows_pad, const int32_t* __restrict__ norm,
+__global__ void __launch_bounds__(256) k_apply32(OpView op, int64_t size, int64_t rows_pad, const int64_t* __restrict__ norm,
+                                                 bool wide,
                                                  const float4* __restrict__ rec, const float2* __restrict__ ca,
                                                  const int32_t* __restrict__ pn, int s_a, int64_t zero_idx,
                                                  float2* __restrict__ y) {
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(256) k_apply32(OpView op, int64_t size, int64_
   if (row >= rows_pad) return;
   const int64_t s = row / kSlice;
   const int lane = (int)(row % kSlice);
-  float2 acc = row_apply32(op, s, lane, __ldg(norm + row), rec, s_ca, s_pn);
+  float2 acc = row_apply32(op, s, lane, __ldg(norm + row), wide, rec, s_ca, s_pn);
   if (row == zero_idx) {
     const float4 r = rec[row];
     acc = make_float2(r.x, r.y);
@@ -132,6 +133,12 @@ ss_status launch_pack32(const ss_stamp_s* s, const float2* u, cudaStream_t st) {
   return SS_OK;
 }
 
+ss_status launch_pack64_prefix(const ss_stamp_s* s, const double2* u, int64_t n_u, cudaStream_t st) {
+  k_pack64_prefix<<<nblk(s->size), 256, 0, st>>>(u, n_u, s->size, s->rec64.get());
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
 ss_status launch_apply64(const ss_stamp_s* s, double2* y, cudaStream_t st) {
   k_apply64<<<nblk(s->rows_pad), 256, 0, st>>>(op_view(s), s->size, s->rows_pad, s->rec64.get(), s->zero_idx, y);
   SS_LAUNCH_CHECK();
@@ -140,8 +147,8 @@ ss_status launch_apply64(const ss_stamp_s* s, double2* y, cudaStream_t st) {
 
 ss_status launch_apply32(const ss_stamp_s* s, float2* y, cudaStream_t st) {
   const size_t sm = s->s_a * (sizeof(float2) + sizeof(int32_t)) + 16;
-  k_apply32<<<nblk(s->rows_pad), 256, sm, st>>>(op_view(s), s->size, s->rows_pad, s->norm.get(), s->rec32.get(),
-                                                s->ca32.get(), s->pnorm.get(), s->s_a, s->zero_idx, y);
+  k_apply32<<<nblk(s->rows_pad), 256, sm, st>>>(op_view(s), s->size, s->rows_pad, s->norm.get(), s->wide,
+                                                s->rec32.get(), s->ca32.get(), s->pn32.get(), s->s_a, s->zero_idx, y);
   SS_LAUNCH_CHECK();
   return SS_OK;
 }
@@ -170,9 +177,7 @@ extern "C" ss_status proxy_residual(ss_stamp s, const double* u_prefix, int64_t 
   if (!s || !f_on_S || !out2 || (n_u > 0 && !u_prefix)) SS_FAIL(SS_ERR_INVALID, "proxy_residual: null argument");
   if (n_u < 0 || n_u > s->size) SS_FAIL(SS_ERR_INVALID, "proxy_residual: n_u = %lld outside [0, |S|]", (long long)n_u);
   cudaStream_t st = as_stream(stream);
-  k_pack64_prefix<<<nblk(s->size), 256, 0, st>>>(reinterpret_cast<const double2*>(u_prefix), n_u, s->size,
-                                                 s->rec64.get());
-  SS_LAUNCH_CHECK();
+  SS_TRY(launch_pack64_prefix(s, reinterpret_cast<const double2*>(u_prefix), n_u, st));
   DevBuf<double2> y, part, sum;
   const int64_t rows_per_block = 4096;
   const int nb = (int)std::max<int64_t>(1, (s->size + rows_per_block - 1) / rows_per_block);

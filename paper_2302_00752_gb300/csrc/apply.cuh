@@ -3,13 +3,13 @@
 //
 // For a row k and a stored neighbour l = k - p_j:
 //     4 pi^2 (k.l) a_hat_j u_l = 2 pi^2 (|k|^2 + |l|^2 - |p_j|^2) a_hat_j u_l,
-// the integer (|k|^2 + |l|^2 - |p_j|^2) = 2 k.l is exact in int32 (|k|^2 < 2^29
-// is checked when the set is built) and ca_j = 2 pi^2 a_hat_j is tabulated.
-// The FP32 operator forms the coefficient on the fly from the gathered norm
-// (FP32 arithmetic is cheap); the FP64 operator reads it, precomputed per
-// entry, beside the index stream.
+// the integer (|k|^2 + |l|^2 - |p_j|^2) = 2 k.l is formed exactly in int64 for
+// the FP64 operator, which reads the product with ca_j = 2 pi^2 a_hat_j,
+// precomputed per entry, beside the index stream.  The FP32 operator forms
+// the coefficient on the fly from the gathered norm word (FP32 arithmetic is
+// cheap): exact in int32 when every |k|^2 < 2^29, else in FP32 (norm_word).
 //
-// Gather source ("records"): FP32  float4 (re, im, |l|^2 as int bits, 0);
+// Gather source ("records"): FP32  float4 (re, im, norm word of |l|^2, 0);
 //                            FP64  two double2 (re, im), (|l|^2 as int64 bits, 0),
 // so one 16- or 32-byte sector brings both the value and the norm.
 #pragma once
@@ -73,11 +73,19 @@ __device__ __forceinline__ double2 row_apply64(const OpView& op, int64_t s, int 
   return make_double2(ar, ai);
 }
 
-// Same in FP32 (FP32 values, FP32 accumulation).
-template <bool CG = false>
-__device__ __forceinline__ float2 row_apply32(const OpView& op, int64_t s, int lane, int32_t nk,
-                                              const float4* __restrict__ rec, const float2* ca,
-                                              const int32_t* pn) {
+// Same in FP32 (FP32 values, FP32 accumulation).  nk, the records' third
+// word and pn are FP32 norm words (norm_word): int32 norms, or FP32 values
+// when WIDE.
+template <bool WIDE>
+__device__ __forceinline__ float entry_scale(int32_t nk, float rec_z, int32_t pnj) {
+  if constexpr (WIDE) return (__int_as_float(nk) + rec_z) - __int_as_float(pnj);
+  else return (float)(nk + __float_as_int(rec_z) - pnj);
+}
+
+template <bool CG, bool WIDE>
+__device__ __forceinline__ float2 row_apply32_t(const OpView& op, int64_t s, int lane, int32_t nk,
+                                                const float4* __restrict__ rec, const float2* ca,
+                                                const int32_t* pn) {
   const int32_t w0 = __ldg(op.woff + s), w1 = __ldg(op.woff + s + 1);
   const uint32_t* e = op.ent + (int64_t)w0 * kSlice + lane;
   float ar = 0.f, ai = 0.f;
@@ -93,7 +101,7 @@ __device__ __forceinline__ float2 row_apply32(const OpView& op, int64_t s, int l
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = (int)(ee[q] >> op.colbits);
-      const float sc = (float)(nk + __float_as_int(v[q].z) - pn[j]);
+      const float sc = entry_scale<WIDE>(nk, v[q].z, pn[j]);
       const float2 a = ca[j];
       const float tr = sc * a.x, ti = sc * a.y;
       ar = fmaf(tr, v[q].x, ar); ar = fmaf(-ti, v[q].y, ar);
@@ -104,13 +112,21 @@ __device__ __forceinline__ float2 row_apply32(const OpView& op, int64_t s, int l
     const uint32_t ee = __ldg(e + (int64_t)t * kSlice);
     const float4 v = ldv<CG>(rec + (ee & op.colmask));
     const int j = (int)(ee >> op.colbits);
-    const float sc = (float)(nk + __float_as_int(v.z) - pn[j]);
+    const float sc = entry_scale<WIDE>(nk, v.z, pn[j]);
     const float2 a = ca[j];
     const float tr = sc * a.x, ti = sc * a.y;
     ar = fmaf(tr, v.x, ar); ar = fmaf(-ti, v.y, ar);
     ai = fmaf(tr, v.y, ai); ai = fmaf(ti, v.x, ai);
   }
   return make_float2(ar, ai);
+}
+
+template <bool CG = false>
+__device__ __forceinline__ float2 row_apply32(const OpView& op, int64_t s, int lane, int64_t nk, bool wide,
+                                              const float4* __restrict__ rec, const float2* ca,
+                                              const int32_t* pn) {
+  return wide ? row_apply32_t<CG, true>(op, s, lane, norm_word(nk, true), rec, ca, pn)
+              : row_apply32_t<CG, false>(op, s, lane, norm_word(nk, false), rec, ca, pn);
 }
 
 }  // namespace ss

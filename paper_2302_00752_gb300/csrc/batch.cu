@@ -18,7 +18,8 @@ struct ss_batch_s {
   int n_inst = 0;
   int64_t rows_total = 0, n_slices = 0, n_ent = 0;
   int jbits = 1;
-  ss::DevBuf<int32_t> norm, woff, slice_inst, pn;
+  ss::DevBuf<int64_t> norm;
+  ss::DevBuf<int32_t> woff, slice_inst, pn;
   ss::DevBuf<uint32_t> ent;
   ss::DevBuf<double2> ca64, ecoef64;
   ss::DevBuf<float2> ca32;
@@ -181,6 +182,9 @@ static ss_status batch_create_impl(ss_batch_s* b, int32_t n, const ss_stamp* sta
   SS_TRY(b->ca64.alloc(coefs, st));
   SS_TRY(b->ca32.alloc(coefs, st));
   SS_TRY(b->pn.alloc(coefs, st));
+  DevBuf<int8_t> wide_rows;
+  SS_TRY(wide_rows.alloc(b->rows_total, st));
+  SS_CUDA(cudaMemsetAsync(wide_rows.get(), 0, b->rows_total, st));
   b->woff_h.assign(slices + 1, 0);
   b->slice_inst_h.assign(slices, 0);
   b->plan.inst.assign(n, SolveInst{});
@@ -188,8 +192,9 @@ static ss_status batch_create_impl(ss_batch_s* b, int32_t n, const ss_stamp* sta
   const uint32_t global_dummy = (uint32_t)(b->rows_total - 1);
   for (int i = 0; i < n; ++i) {
     const ss_stamp_s* s = stamps[i];
-    SS_CUDA(cudaMemcpyAsync(b->norm.get() + row0, s->norm.get(), s->rows_pad * sizeof(int32_t),
+    SS_CUDA(cudaMemcpyAsync(b->norm.get() + row0, s->norm.get(), s->rows_pad * sizeof(int64_t),
                             cudaMemcpyDeviceToDevice, st));
+    if (s->wide) SS_CUDA(cudaMemsetAsync(wide_rows.get() + row0, 1, s->rows_pad, st));
     k_woff<<<nblk(s->n_slices + 1), 256, 0, st>>>(s->slice_off.get(), s->n_slices, (int32_t)(e0 / kSlice),
                                                   b->woff.get() + s0);
     k_remap<<<nblk(s->n_ent), 256, 0, st>>>(s->ent.get(), s->n_ent, colbits_of(s->jbits), colmask_of(s->jbits),
@@ -201,7 +206,7 @@ static ss_status batch_create_impl(ss_batch_s* b, int32_t n, const ss_stamp* sta
     SS_LAUNCH_CHECK();
     SS_CUDA(cudaMemcpyAsync(b->ca64.get() + c0, s->ca64.get(), s->s_a * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     SS_CUDA(cudaMemcpyAsync(b->ca32.get() + c0, s->ca32.get(), s->s_a * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-    SS_CUDA(cudaMemcpyAsync(b->pn.get() + c0, s->pnorm.get(), s->s_a * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    SS_CUDA(cudaMemcpyAsync(b->pn.get() + c0, s->pn32.get(), s->s_a * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     std::vector<int32_t> w(s->n_slices + 1);
     SS_CUDA(cudaMemcpyAsync(w.data(), s->slice_off.get(), w.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     SS_CUDA(cudaStreamSynchronize(st));
@@ -214,13 +219,14 @@ static ss_status batch_create_impl(ss_batch_s* b, int32_t n, const ss_stamp* sta
     in.zero_row = s->zero_idx >= 0 ? row0 + s->zero_idx : -1;
     in.coef_off = (int32_t)c0;
     in.dscale = 2.0 * kTwoPiSq * s->a0;
+    in.wide = s->wide ? 1 : 0;
     row0 += s->rows_pad;
     s0 += s->n_slices;
     e0 += s->n_ent;
     c0 += s->s_a;
   }
-  SS_CUDA(cudaMemsetAsync(b->norm.get() + (b->rows_total - 1), 0, sizeof(int32_t), st));
-  SS_TRY(work_alloc(b->work, b->rows_total, b->norm.get(), st));
+  SS_CUDA(cudaMemsetAsync(b->norm.get() + (b->rows_total - 1), 0, sizeof(int64_t), st));
+  SS_TRY(work_alloc(b->work, b->rows_total, b->norm.get(), wide_rows.get(), false, st));
   SS_CUDA(cudaStreamSynchronize(st));
   b->norm.settle(); b->woff.settle(); b->slice_inst.settle(); b->ent.settle();
   b->ca64.settle(); b->ca32.settle(); b->pn.settle(); b->ecoef64.settle();

@@ -69,8 +69,8 @@ __device__ __forceinline__ void load_key(const uint64_t* __restrict__ base, int6
 }
 
 template <int WT>
-__device__ __forceinline__ int32_t key_norm(const uint64_t* key, const KeyParams& P) {
-  int32_t s = 0;
+__device__ __forceinline__ int64_t key_norm(const uint64_t* key, const KeyParams& P) {
+  int64_t s = 0;
 #pragma unroll
   for (int w = 0; w < WT; ++w) {
     const uint64_t x = key[w];
@@ -78,7 +78,7 @@ __device__ __forceinline__ int32_t key_norm(const uint64_t* key, const KeyParams
       const int c = w * P.fpw + f;
       if (c >= P.d) break;
       const int sh = 64 - P.fb * (f + 1);
-      const int32_t v = (int32_t)((int64_t)((x >> sh) & P.fieldmask) - P.bias_val);
+      const int64_t v = (int64_t)((x >> sh) & P.fieldmask) - P.bias_val;
       s += v * v;
     }
   }

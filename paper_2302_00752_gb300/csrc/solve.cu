@@ -194,12 +194,12 @@ __device__ void run_phase(const SolveParams& P, Smem& sm, unsigned qmask, Scal s
 }
 
 __device__ __forceinline__ double jacobi(const SolveParams& P, const SolveInst& in, int64_t g) {
-  const int32_t nk = __ldg(P.norm + g);
+  const int64_t nk = __ldg(P.norm + g);
   return nk > 0 ? in.dscale * (double)nk : 1.0;
 }
 
 __device__ __forceinline__ float jacobi32(const SolveParams& P, const SolveInst& in, int64_t g) {
-  const int32_t nk = __ldg(P.norm + g);
+  const int64_t nk = __ldg(P.norm + g);
   return nk > 0 ? (float)in.dscale * (float)nk : 1.0f;
 }
 
@@ -220,7 +220,8 @@ __device__ __forceinline__ float2 apply32_row(const SolveParams& P, const SolveI
     const float4 v = __ldcg(P.urec32 + g);
     return make_float2(v.x, v.y);
   }
-  return row_apply32<true>(P.op, s, lane, __ldg(P.norm + g), P.urec32, P.ca32 + in.coef_off, P.pn + in.coef_off);
+  return row_apply32<true>(P.op, s, lane, __ldg(P.norm + g), in.wide != 0, P.urec32, P.ca32 + in.coef_off,
+                           P.pn + in.coef_off);
 }
 
 __device__ __forceinline__ void owner_done(const SolveParams& P, InstState& st, int status) {
@@ -551,17 +552,18 @@ __global__ void __launch_bounds__(1024) k_solve(SolveParams P) {
   else solve_refined(P, sm);
 }
 
-__global__ void k_init_solve_records(const int32_t* __restrict__ norm, int64_t n, double2* xrec, double2* prec64,
-                                     float4* prec32) {
+__global__ void k_init_solve_records(const int64_t* __restrict__ norm, int64_t n, const int8_t* __restrict__ wide_rows,
+                                     bool wide, double2* xrec, double2* prec64, float4* prec32) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n) return;
-  const int32_t nr = norm[g];
+  const int64_t nr = norm[g];
+  const bool wd = wide_rows ? wide_rows[g] != 0 : wide;
   const double2 nb = make_double2(__longlong_as_double((long long)nr), 0.0);
   xrec[2 * g] = make_double2(0.0, 0.0);
   xrec[2 * g + 1] = nb;
   prec64[2 * g] = make_double2(0.0, 0.0);
   prec64[2 * g + 1] = nb;
-  prec32[g] = make_float4(0.f, 0.f, __int_as_float(nr), 0.f);
+  prec32[g] = make_float4(0.f, 0.f, __int_as_float(norm_word(nr, wd)), 0.f);
 }
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -611,7 +613,8 @@ ss_status plan_chunks(SolvePlan& plan, const std::vector<int32_t>& woff, const s
   return SS_OK;
 }
 
-ss_status work_alloc(SolveWork& W, int64_t rows_total, const int32_t* norm, cudaStream_t st) {
+ss_status work_alloc(SolveWork& W, int64_t rows_total, const int64_t* norm, const int8_t* wide_rows, bool wide,
+                     cudaStream_t st) {
   if (W.rows_total == rows_total) return SS_OK;
   W.rows_total = rows_total;
   SS_TRY(W.xrec.alloc(2 * rows_total, st));
@@ -632,8 +635,8 @@ ss_status work_alloc(SolveWork& W, int64_t rows_total, const int32_t* norm, cuda
   SS_TRY(W.bar.alloc(2, st));
   SS_TRY(W.counters.alloc(4, st));
   SS_TRY(W.err.alloc(1, st));
-  k_init_solve_records<<<nblk(rows_total), 256, 0, st>>>(norm, rows_total, W.xrec.get(), W.urec64.get(),
-                                                        W.urec32.get());
+  k_init_solve_records<<<nblk(rows_total), 256, 0, st>>>(norm, rows_total, wide_rows, wide, W.xrec.get(),
+                                                         W.urec64.get(), W.urec32.get());
   SS_LAUNCH_CHECK();
   // the workspace is reused by later calls, possibly on other streams
   SS_CUDA(cudaStreamSynchronize(st));
@@ -665,7 +668,7 @@ ss_status max_grid(int mode, int block, int* grid) {
 
 // Fill params and launch (capturable: no host synchronisation).
 ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, const int32_t* slice_inst,
-                              const int32_t* norm, const double2* ca64, const float2* ca32, const int32_t* pn,
+                              const int64_t* norm, const double2* ca64, const float2* ca32, const int32_t* pn,
                               double tol, int max_iter, ss_precision prec, cudaStream_t st, cudaEvent_t ev_begin,
                        cudaEvent_t ev_end) {
   SolveParams P{};
@@ -787,6 +790,7 @@ static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream
   in.zero_row = s->zero_idx;
   in.coef_off = 0;
   in.dscale = 2.0 * kTwoPiSq * s->a0;   // 4 pi^2 Re(a_hat_0)
+  in.wide = s->wide ? 1 : 0;
   int grid = 0;
   C.plan.block = C.block;
   SS_TRY(max_grid(mode, C.plan.block, &grid));
@@ -795,7 +799,7 @@ static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream
   const int target = std::min<int64_t>((int64_t)grid * C.chunks_per_block, by_size);
   SS_TRY(plan_chunks(C.plan, woff, {}, target));
   C.plan.grid = std::min<int>(grid, (int)C.plan.chunk.size());
-  SS_TRY(work_alloc(C.work, s->rows_pad + 1, s->norm.get(), st));
+  SS_TRY(work_alloc(C.work, s->rows_pad + 1, s->norm.get(), nullptr, s->wide, st));
   SS_TRY(work_upload(C.work, C.plan, st));
   C.planned_mode = mode;
   return SS_OK;
@@ -871,7 +875,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
     SS_CUDA(cudaEventCreate(&C->work.ev[0]));
     SS_CUDA(cudaEventCreate(&C->work.ev[1]));
   }
-  SS_TRY(launch_solve(C->work, C->plan, op, nullptr, s->norm.get(), s->ca64.get(), s->ca32.get(), s->pnorm.get(), tol,
+  SS_TRY(launch_solve(C->work, C->plan, op, nullptr, s->norm.get(), s->ca64.get(), s->ca32.get(), s->pn32.get(), tol,
                       max_iter, prec, st, C->work.ev[0], C->work.ev[1]));
   ss_status worst;
   ss_solve_stats one{};
@@ -993,6 +997,7 @@ extern "C" ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_o
   in.zero_row = s->zero_idx;
   in.coef_off = 0;
   in.dscale = 2.0 * kTwoPiSq * s->a0;
+  in.wide = s->wide ? 1 : 0;
   in.f = reinterpret_cast<const double2*>(f_on_S);
   in.u = reinterpret_cast<double2*>(u_on_S);
   plan.block = 1024;
@@ -1021,7 +1026,8 @@ extern "C" ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_o
   SS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
   SS_CUDA(cudaMemsetAsync(d_state, 0, sizeof(InstState), st));
   const int64_t recs = s->rows_pad + 1;
-  k_init_solve_records<<<nblk(recs), 256, 0, st>>>(s->norm.get(), recs, static_cast<double2*>(at(kOffXrec)),
+  k_init_solve_records<<<nblk(recs), 256, 0, st>>>(s->norm.get(), recs, nullptr, s->wide,
+                                                  static_cast<double2*>(at(kOffXrec)),
                                                   static_cast<double2*>(at(kOffU64)), static_cast<float4*>(at(kOffU32)));
   SS_LAUNCH_CHECK();
   SolveParams P{};
@@ -1039,7 +1045,7 @@ extern "C" ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_o
   P.norm = s->norm.get();
   P.ca64 = s->ca64.get();
   P.ca32 = s->ca32.get();
-  P.pn = s->pnorm.get();
+  P.pn = s->pn32.get();
   P.xrec = static_cast<double2*>(at(kOffXrec));
   P.urec64 = static_cast<double2*>(at(kOffU64));
   P.urec32 = static_cast<float4*>(at(kOffU32));

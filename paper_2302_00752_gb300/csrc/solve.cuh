@@ -12,6 +12,7 @@ constexpr int kMaxWarps = 32;
 struct SolveInst {
   int64_t row0, rows, rows_pad, zero_row;
   int32_t coef_off, c_first, c_last, part_base;
+  int32_t wide, pad_;       // FP32 norm words of this instance hold FP32 values (norm_word)
   double dscale;            // 4 pi^2 Re(a_hat_0)
   const double2* f;         // caller input, rows entries
   double2* u;               // caller output, rows entries
@@ -39,10 +40,10 @@ struct SolveParams {
   InstState* state;
   OpView op;
   const int32_t* slice_inst;   // null for a single instance
-  const int32_t* norm;
+  const int64_t* norm;         // |k|^2 per row
   const double2* ca64;
   const float2* ca32;
-  const int32_t* pn;
+  const int32_t* pn;           // FP32 norm words of |p_j|^2
   double2* xrec;               // FP64 records (value, norm) of x: gathered for f - L x
   double2* urec64;             // FP64 records of u = D^-1 r: gathered by the FP64 operator
   float4* urec32;              // FP32 records of u: gathered by the FP32 operator
@@ -97,11 +98,14 @@ struct SolveWork {
   int cap_inst = 0, cap_chunk = 0;
 };
 
-ss_status work_alloc(SolveWork& W, int64_t rows_total, const int32_t* norm, cudaStream_t st);
+// The records' norm words are encoded per row: wide_rows (device, one byte per
+// row) or, when null, `wide` for every row.
+ss_status work_alloc(SolveWork& W, int64_t rows_total, const int64_t* norm, const int8_t* wide_rows, bool wide,
+                     cudaStream_t st);
 ss_status work_upload(SolveWork& W, const SolvePlan& plan, cudaStream_t st);
 ss_status max_grid(int mode, int block, int* grid);
 ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, const int32_t* slice_inst,
-                       const int32_t* norm, const double2* ca64, const float2* ca32, const int32_t* pn,
+                       const int64_t* norm, const double2* ca64, const float2* ca32, const int32_t* pn,
                        double tol, int max_iter, ss_precision prec, cudaStream_t st,
                        cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 ss_status read_stats(SolveWork& W, int n_inst, ss_solve_stats* stats, ss_status* worst, cudaStream_t st,

@@ -112,17 +112,18 @@ struct ss_stamp_s {
   int64_t size = 0, rows_pad = 0, nnz = 0, zero_idx = -1, n_slices = 0, n_ent = 0;
   std::vector<int64_t> level_start;   // N + 2 entries
   double a0 = 0.0;                    // Re(a_hat_0)
-  int max_norm = 0;                   // max |k|^2 over S (and |p|^2)
+  bool wide = false;                  // |k|^2 may reach 2^29: FP32 norm words hold FP32 values
   // set
   ss::DevBuf<uint64_t> keys;          // [size][WT]
   ss::DevBuf<int8_t> level;           // [size]
-  ss::DevBuf<int32_t> norm;           // [rows_pad + 1] |k|^2 (0 on padding and the dummy row)
+  ss::DevBuf<int64_t> norm;           // [rows_pad + 1] |k|^2 (0 on padding and the dummy row)
   ss::DevBuf<uint64_t> table;         // open-addressing slots
   int64_t cap = 0;
   // coefficient data in canonical step order (supp a_hat sorted lexicographically)
   ss::DevBuf<int32_t> afreq;          // [s_a][d]
   ss::DevBuf<uint64_t> stepkey;       // [s_a][WT] packed p_j
-  ss::DevBuf<int32_t> pnorm;          // [s_a] |p_j|^2
+  ss::DevBuf<int64_t> pnorm;          // [s_a] |p_j|^2
+  ss::DevBuf<int32_t> pn32;           // [s_a] FP32 norm words of |p_j|^2 (see norm_word)
   ss::DevBuf<double2> aval;           // [s_a] a_hat_j
   ss::DevBuf<double2> ca64;           // [s_a] 2 pi^2 a_hat_j
   ss::DevBuf<float2> ca32;            // [s_a] same in FP32
@@ -156,6 +157,9 @@ __host__ __device__ inline int colbits_of(int jbits) { return 32 - jbits; }
 ss_status launch_pack64(const ss_stamp_s* s, const double2* u, cudaStream_t st);
 ss_status launch_pack32(const ss_stamp_s* s, const float2* u, cudaStream_t st);
 ss_status launch_apply64(const ss_stamp_s* s, double2* y, cudaStream_t st);
+// u on the first n_u rows of S (a vector on S^N is the prefix of one on
+// S^{N+L}), zero on the rest, into the FP64 record array.
+ss_status launch_pack64_prefix(const ss_stamp_s* s, const double2* u, int64_t n_u, cudaStream_t st);
 ss_status launch_apply32(const ss_stamp_s* s, float2* y, cudaStream_t st);
 
 int sm_count();
@@ -168,6 +172,23 @@ void drop_solve_ctx(const ss_stamp_s* s);
 // -------------------------------------------------------- device helpers
 
 namespace ss {
+
+// FP32 operator norm words: |k|^2 as int32 when every norm of the set is below
+// 2^29 (then |k|^2 + |l|^2 - |p|^2 = 2 k.l is exact in int32 and rounded to
+// FP32 once), otherwise the FP32 value of |k|^2 (2 k.l formed in FP32: k.l is
+// close to |k|^2 there, so the sum carries no cancellation beyond FP32
+// rounding of the operands; the FP64 operator stays exact).
+__host__ __device__ __forceinline__ int32_t norm_word(int64_t n, bool wide) {
+#ifdef __CUDA_ARCH__
+  return wide ? __float_as_int((float)n) : (int32_t)n;
+#else
+  if (!wide) return (int32_t)n;
+  const float f = (float)n;
+  int32_t w;
+  std::memcpy(&w, &f, sizeof(w));
+  return w;
+#endif
+}
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   // finaliser of MurmurHash3 (public domain)

@@ -119,16 +119,17 @@ __global__ void k_prep(const int32_t* __restrict__ F, int64_t n_f, const int32_t
 
 template <int WT>
 __global__ void k_steps(KeyParams P, const int32_t* __restrict__ A, const double2* __restrict__ av, int s_a,
-                        uint64_t* stepkey, int32_t* pnorm, double2* ca64, float2* ca32) {
+                        uint64_t* stepkey, int64_t* pnorm, int32_t* pn32, bool wide, double2* ca64, float2* ca32) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= s_a) return;
   uint64_t k[WT];
   pack_key<WT>(A + (int64_t)j * P.d, P, k);
 #pragma unroll
   for (int w = 0; w < WT; ++w) stepkey[(int64_t)j * WT + w] = k[w];
-  int32_t s = 0;
-  for (int c = 0; c < P.d; ++c) s += A[(int64_t)j * P.d + c] * A[(int64_t)j * P.d + c];
+  int64_t s = 0;
+  for (int c = 0; c < P.d; ++c) s += (int64_t)A[(int64_t)j * P.d + c] * A[(int64_t)j * P.d + c];
   pnorm[j] = s;
+  pn32[j] = norm_word(s, wide);
   const double2 a = av[j];
   ca64[j] = make_double2(kTwoPiSq * a.x, kTwoPiSq * a.y);
   ca32[j] = make_float2((float)(kTwoPiSq * a.x), (float)(kTwoPiSq * a.y));
@@ -151,7 +152,7 @@ __device__ bool table_insert_final(uint64_t* table, uint64_t capmask, const uint
 
 template <int WT>
 __global__ void k_level0(KeyParams P, const int32_t* __restrict__ F, int64_t n_f, uint64_t* keys, int8_t* level,
-                         int32_t* norm, uint64_t* table, uint64_t capmask, int32_t* err) {
+                         int64_t* norm, uint64_t* table, uint64_t capmask, int32_t* err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_f) return;
   uint64_t k[WT];
@@ -248,7 +249,7 @@ template <int WT>
 __global__ void k_finalize(KeyParams P, uint64_t* keys, int64_t par0, int s_a, const uint64_t* __restrict__ stepkey,
                            const int64_t* __restrict__ slot_of, const int32_t* __restrict__ flag,
                            const int32_t* __restrict__ pos, int64_t n, int64_t base, int lvl, int8_t* level,
-                           int32_t* norm, uint64_t* table, int64_t* zero_idx) {
+                           int64_t* norm, uint64_t* table, int64_t* zero_idx) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n || !flag[c]) return;
   const int64_t par = c / s_a;
@@ -261,7 +262,7 @@ __global__ void k_finalize(KeyParams P, uint64_t* keys, int64_t par0, int s_a, c
 #pragma unroll
   for (int w = 0; w < WT; ++w) keys[idx * WT + w] = ck[w];
   level[idx] = (int8_t)lvl;
-  const int32_t nr = key_norm<WT>(ck, P);
+  const int64_t nr = key_norm<WT>(ck, P);
   norm[idx] = nr;
   if (nr == 0) *zero_idx = idx;
   table[slot_of[c]] = slot_word(slot_fp(hash_key<WT>(ck)), (uint64_t)idx);
@@ -311,8 +312,8 @@ __global__ void k_row_counts(const int32_t* __restrict__ nbr, int64_t size, int6
 // (|k|^2 + |l|^2 - |p_j|^2) * 2 pi^2 a_hat_j = 4 pi^2 (k.l) a_hat_j (eq. GF), so
 // that the FP64 operator spends four FP64 FMAs per nonzero.
 __global__ void k_fill_slices(const int32_t* __restrict__ nbr, int64_t size, int64_t rows_pad, int s_a, int j0,
-                              const int32_t* __restrict__ woff, int colbits, const int32_t* __restrict__ norm,
-                              const int32_t* __restrict__ pnorm, const double2* __restrict__ ca64, uint32_t* ent,
+                              const int32_t* __restrict__ woff, int colbits, const int64_t* __restrict__ norm,
+                              const int64_t* __restrict__ pnorm, const double2* __restrict__ ca64, uint32_t* ent,
                               double2* ecoef) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows_pad) return;
@@ -322,7 +323,7 @@ __global__ void k_fill_slices(const int32_t* __restrict__ nbr, int64_t size, int
   const int w = woff[s + 1] - woff[s];
   int t = 0;
   if (i < size) {
-    const int32_t nk = norm[i];
+    const int64_t nk = norm[i];
     for (int j = 0; j < s_a; ++j) {
       const int32_t v = nbr[i * s_a + j];
       if (v >= 0) {
@@ -340,11 +341,12 @@ __global__ void k_fill_slices(const int32_t* __restrict__ nbr, int64_t size, int
   }
 }
 
-__global__ void k_init_records(const int32_t* __restrict__ norm, int64_t n, float4* rec32, double2* rec64) {
+__global__ void k_init_records(const int64_t* __restrict__ norm, int64_t n, bool wide, float4* rec32,
+                               double2* rec64) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int32_t nr = norm[i];
-  rec32[i] = make_float4(0.f, 0.f, __int_as_float(nr), 0.f);
+  const int64_t nr = norm[i];
+  rec32[i] = make_float4(0.f, 0.f, __int_as_float(norm_word(nr, wide)), 0.f);
   rec64[2 * i] = make_double2(0.0, 0.0);
   rec64[2 * i + 1] = make_double2(__longlong_as_double((long long)nr), 0.0);
 }
@@ -408,14 +410,14 @@ static ss_status grow_keys(ss_stamp_s* S, int64_t need, cudaStream_t st) {
   const int64_t cap = std::max<int64_t>(need, (int64_t)(S->keys.n / WT) * 2);
   DevBuf<uint64_t> k2;
   DevBuf<int8_t> l2;
-  DevBuf<int32_t> n2;
+  DevBuf<int64_t> n2;
   SS_TRY(k2.alloc(cap * WT, st));
   SS_TRY(l2.alloc(cap, st));
   SS_TRY(n2.alloc(cap + kSlice + 1, st));
   if (S->size > 0) {
     SS_CUDA(cudaMemcpyAsync(k2.get(), S->keys.get(), S->size * WT * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
     SS_CUDA(cudaMemcpyAsync(l2.get(), S->level.get(), S->size, cudaMemcpyDeviceToDevice, st));
-    SS_CUDA(cudaMemcpyAsync(n2.get(), S->norm.get(), S->size * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    SS_CUDA(cudaMemcpyAsync(n2.get(), S->norm.get(), S->size * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
   }
   // the old buffers are released on this stream, after the copies
   std::swap(S->keys.p, k2.p); std::swap(S->keys.n, k2.n); std::swap(S->keys.s, k2.s);
@@ -427,9 +429,13 @@ static ss_status grow_keys(ss_stamp_s* S, int64_t need, cudaStream_t st) {
   return SS_OK;
 }
 
+// Norm range: |k|^2 <= d maxabs^2 is formed in int64 (and the FP64 entry
+// coefficients from |k|^2 + |l|^2 - |p|^2 exactly in FP64 below 2^53).
+static bool norms_wide(int d, int64_t maxabs) { return (double)d * (double)maxabs * (double)maxabs >= (double)(1 << 29); }
+
 static ss_status make_layout(int d, int64_t maxabs, KeyLayout* out) {
-  if ((double)d * (double)maxabs * (double)maxabs >= (double)(1 << 29))
-    SS_FAIL(SS_ERR_KEY_RANGE, "stamp: |k|^2 may reach %g; integer dot products need < 2^29",
+  if ((double)d * (double)maxabs * (double)maxabs >= 0x1p51)
+    SS_FAIL(SS_ERR_KEY_RANGE, "stamp: |k|^2 may reach %g; exact operator coefficients need < 2^51",
             (double)d * maxabs * maxabs);
   int b = 1;
   while (((int64_t)1 << (b - 1)) - 1 < maxabs) ++b;
@@ -502,7 +508,7 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
     SS_FAIL(SS_ERR_KEY_RANGE, "stamp: |S| = %lld too large for %d-bit columns", (long long)S->size,
             colbits_of(S->jbits));
   SS_TRY(grow_keys(S, S->rows_pad + 1, st));   // norm padded to rows_pad + 1
-  SS_CUDA(cudaMemsetAsync(S->norm.get() + S->size, 0, (S->rows_pad + 1 - S->size) * sizeof(int32_t), st));
+  SS_CUDA(cudaMemsetAsync(S->norm.get() + S->size, 0, (S->rows_pad + 1 - S->size) * sizeof(int64_t), st));
   DevBuf<int32_t> nbr, slice_w;
   DevBuf<unsigned long long> d_nnz;
   DevBuf<int64_t> d_total;
@@ -535,7 +541,7 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   SS_LAUNCH_CHECK();
   SS_TRY(S->rec32.alloc(S->rows_pad + 1, st));
   SS_TRY(S->rec64.alloc(2 * (S->rows_pad + 1), st));
-  k_init_records<<<nblk(S->rows_pad + 1), 256, 0, st>>>(S->norm.get(), S->rows_pad + 1, S->rec32.get(),
+  k_init_records<<<nblk(S->rows_pad + 1), 256, 0, st>>>(S->norm.get(), S->rows_pad + 1, S->wide, S->rec32.get(),
                                                         S->rec64.get());
   SS_LAUNCH_CHECK();
   int32_t e = 0;
@@ -544,7 +550,7 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   if (e) SS_FAIL((ss_status)e, "stamp: hash table exhausted");
   // the stamp's buffers outlive this call's stream (synchronised above)
   S->keys.settle(); S->level.settle(); S->norm.settle(); S->table.settle();
-  S->afreq.settle(); S->stepkey.settle(); S->pnorm.settle(); S->aval.settle();
+  S->afreq.settle(); S->stepkey.settle(); S->pnorm.settle(); S->pn32.settle(); S->aval.settle();
   S->ca64.settle(); S->ca32.settle(); S->slice_off.settle(); S->ent.settle(); S->ecoef64.settle();
   S->rec32.settle(); S->rec64.settle(); S->err_dev.settle(); S->zidx_dev.settle();
   return SS_OK;
@@ -568,8 +574,8 @@ static ss_status relayout(ss_stamp_s* S, const KeyLayout& L2, cudaStream_t st) {
   S->key = L2;
   SS_TRY(S->stepkey.alloc((size_t)S->s_a * L2.WT, st));
   SS_DISPATCH_WT(L2.WT, (k_steps<WT><<<nblk(S->s_a), 256, 0, st>>>(P2, S->afreq.get(), S->aval.get(), S->s_a,
-                                                                   S->stepkey.get(), S->pnorm.get(), S->ca64.get(),
-                                                                   S->ca32.get())));
+                                                                   S->stepkey.get(), S->pnorm.get(), S->pn32.get(),
+                                                                   S->wide, S->ca64.get(), S->ca32.get())));
   SS_LAUNCH_CHECK();
   const int64_t cap = S->cap;
   S->cap = 0;
@@ -629,8 +635,10 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
 
   // key layout: every frequency of S^{N+1} must fit (neighbour lookups reach one level further)
   KeyLayout L;
-  SS_TRY(make_layout(d, (int64_t)h.maxabs_f + (int64_t)(N + 1) * h.maxabs_a, &L));
+  const int64_t maxabs = (int64_t)h.maxabs_f + (int64_t)(N + 1) * h.maxabs_a;
+  SS_TRY(make_layout(d, maxabs, &L));
   S->key = L;
+  S->wide = norms_wide(d, maxabs);
   const KeyParams P = make_key_params(L);
   int jb = 0;
   while ((1 << jb) < s_a) ++jb;
@@ -643,10 +651,12 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   SS_CUDA(cudaMemcpyAsync(S->aval.get(), avs.get(), s_a * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   SS_TRY(S->stepkey.alloc((size_t)s_a * L.WT, st));
   SS_TRY(S->pnorm.alloc(s_a, st));
+  SS_TRY(S->pn32.alloc(s_a, st));
   SS_TRY(S->ca64.alloc(s_a, st));
   SS_TRY(S->ca32.alloc(s_a, st));
   SS_DISPATCH_WT(L.WT, (k_steps<WT><<<nblk(s_a), 256, 0, st>>>(P, As.get(), avs.get(), s_a, S->stepkey.get(),
-                                                               S->pnorm.get(), S->ca64.get(), S->ca32.get())));
+                                                               S->pnorm.get(), S->pn32.get(), S->wide,
+                                                               S->ca64.get(), S->ca32.get())));
   SS_LAUNCH_CHECK();
 
   // level 0
@@ -683,10 +693,22 @@ static ss_status extend_impl(ss_stamp_s* S, int levels, cudaStream_t st) {
   const int N2 = S->N + levels;
   const int64_t need = (int64_t)S->maxabs_f + (int64_t)(N2 + 1) * S->maxabs_a;
   const int64_t have = ((int64_t)1 << (S->key.b - 1)) - 1;
+  const bool wide2 = norms_wide(S->d, need);
   if (need > have) {
     KeyLayout L2;
     SS_TRY(make_layout(S->d, need, &L2));
+    S->wide = wide2;
     SS_TRY(relayout(S, L2, st));
+  } else if (wide2 != S->wide) {
+    // the FP32 norm words of the steps change encoding (the records are
+    // rewritten by build_operator)
+    S->wide = wide2;
+    const KeyParams P = make_key_params(S->key);
+    SS_DISPATCH_WT(S->key.WT, (k_steps<WT><<<nblk(S->s_a), 256, 0, st>>>(P, S->afreq.get(), S->aval.get(), S->s_a,
+                                                                         S->stepkey.get(), S->pnorm.get(),
+                                                                         S->pn32.get(), S->wide, S->ca64.get(),
+                                                                         S->ca32.get())));
+    SS_LAUNCH_CHECK();
   }
   SS_TRY(run_levels(S, S->N + 1, N2, st));
   S->N = N2;

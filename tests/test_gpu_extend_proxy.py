@@ -70,21 +70,21 @@ def test_solve_after_extend(B, prec):
 
 @pytest.mark.parametrize("name,N", [("tiny", 1), ("tiny", 2), ("cfg3", 2)])
 def test_proxy_matches_oracle(B, name, N):
+    # the same seeded u on S^N on both sides (any u: the proxy is a residual)
     inst = W.make_tiny(5, d=3, n_cos=2, n_u=2, N=N, manufactured_u=False) if name == "tiny" else W.make_cfg3()
     _, af, av, ff, fv = stamp_inputs(inst)
+    S, _ = ostamp.stamp_bfs(af, ff, N)
+    rng = np.random.default_rng(N)
+    u = rng.standard_normal(len(S)) + 1j * rng.standard_normal(len(S))
+    u[~S.any(axis=1)] = 0.0                 # the solver's pinned mean
     with B.stamp_build(af, av, ff, N) as s:
-        f_on, _ = s.scatter(ff, fv)
-        u, _ = B.solve(s, f_on, 1e-13, 1000, "fp64")
-        S = s.export()[0].cpu().numpy()
-        n_u = s.size
         s.extend(1)
         f1, outside = s.scatter(ff, fv)
         assert outside == 0
-        num, den = B.proxy_residual(s, u, f1)
+        num, den = B.proxy_residual(s, torch.as_tensor(u), f1)
     got = np.sqrt(num / den)
-    want = ogal.proxy_error(af, av, S, u.cpu().numpy(), ff, fv)
-    assert want > 1e-8                     # a truncation error, not rounding
-    assert abs(got - want) <= 1e-9 * want
+    want = ogal.proxy_error(af, av, S, u, ff, fv)
+    assert abs(got - want) <= 1e-12 * want
 
 
 def test_proxy_decays_with_stamping_level(B):

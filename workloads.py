@@ -274,6 +274,18 @@ def make_one_term(d, seed=0, kmax=500, a0=4.0, c=None):
                     "fp64", "fp64", None, (seed,))
 
 
+def make_wide(seed=0, d=4, scale=20000, n_cos=3, n_f=3, N=2):
+    """Multiscale data with large frequencies (|k|^2 ~ 1e10, past the int32
+    norm range): a = 2 + n_cos cosines with sum |c| = 0.8, f = n_f cos/sin
+    terms, all frequencies uniform in [-scale, scale]^d."""
+    rng = np.random.default_rng([seed, 0x77])
+    pa, taken = draw_freqs(rng, n_cos, d, -scale, scale)
+    a = cosine_sum(d, 2.0, pa, draw_l1_coefs(rng, n_cos, 0.8))
+    pf, _ = draw_freqs(rng, n_f, d, -scale, scale, taken)
+    return Instance(f"wide_d{d}", d, N, a, random_cos_sin(rng, pf), None, None, random_lattice_draws(rng, d),
+                    "fp64", "fp64", None, (seed,))
+
+
 def make_tiny(seed=0, d=2, n_cos=2, n_u=2, N=2, box=3, ubox=4, manufactured_u=True):
     """Small instances for brute-force checks (d <= 3, few terms)."""
     rng = np.random.default_rng(seed)
@@ -295,3 +307,10 @@ CONFIGS = {
     "cfg3": make_cfg3,
     "cfg5": make_cfg5,
 }
+
+
+def mc_points(seed, Q, d):
+    """Q uniform random points of T^d on the grid (2^-32 Z)^d, as the integer
+    numerators X (uint32 [Q, d]); x = X / 2^32 (Monte Carlo proxy draws)."""
+    rng = np.random.default_rng([seed, 0x6d63])
+    return rng.integers(0, 1 << 32, size=(Q, d), dtype=np.uint64).astype(np.uint32)
