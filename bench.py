@@ -257,6 +257,55 @@ def d100_section(B, gp, flush, steps=2):
     return out
 
 
+DF_OPS_PER_PAIR = 150   # ten double-float multiply-adds of 15 FP32 instructions per (term, point)
+
+
+def proxy_section(B, gp, flush, Q=1000):
+    """Lemma ProxyError after the solve: extension to S^{N+1}, the exact proxy
+    and its Monte Carlo estimate at Q = 1000 uniform points (the paper uses 200
+    and 1000), for the d = 3 multiscale workload (given f, truncation error
+    visible) and the d = 10 workload (manufactured: the proxy is the solver's
+    tolerance)."""
+    import torch
+    out = {}
+    for name, inst in (("cfg3", W.make_cfg3()), ("cfg2", W.make_cfg2())):
+        prep = gp.prepare(inst)
+        res = gp.run(prep, tol=1e-12)
+        X = W.mc_points(0, Q, inst.d)
+        n_u = res.stamp.size
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record()
+        res.stamp.extend(1)
+        ev[1].record()
+        f1, _ = res.stamp.scatter(res.f_freq, res.f_val)
+        num, den = B.proxy_residual(res.stamp, res.u.to(torch.complex128), f1)
+        ev[2].record()
+        u128 = res.u.to(torch.complex128)
+        r, fx = B.proxy_mc(res.stamp, u128, prep.f_freq, prep.f_coef, X)   # warm
+        reps = 3
+        ev[2].synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            r, fx = B.proxy_mc(res.stamp, u128, prep.f_freq, prep.f_coef, X)
+        b.record()
+        b.synchronize()
+        mc_ms = a.elapsed_time(b) / reps
+        pairs = (res.stamp.size + len(prep.f_freq)) * Q
+        mc = float(torch.sqrt((r * r).sum() / (fx * fx).sum()))
+        peak = 152 * 128 * 2070e6   # FP32 instructions per second at the maximum SM clock
+        out[name] = {"n_u": n_u, "size_N_plus_1": res.stamp.size, "extend_ms": ev[0].elapsed_time(ev[1]),
+                     "exact_proxy_ms": ev[1].elapsed_time(ev[2]), "exact": float(np.sqrt(num / den)),
+                     "mc": mc, "points": Q, "mc_ms": mc_ms, "term_point_pairs": pairs,
+                     "pairs_per_s": pairs / (mc_ms / 1e3),
+                     "mc_fp32_frac": pairs * DF_OPS_PER_PAIR / (mc_ms / 1e3) / peak,
+                     "note": "mc_ms: whole proxy_mc call (operator, export, three kernels); fraction of the "
+                             "FP32 instruction peak at 150 double-float instructions per pair"}
+        res.stamp.destroy()
+    return out
+
+
 def batched_section(B, flush, n_inst=512, reps=3, world=1, rank=0):
     """The batched workload: 512 instances of uneven d, s_a and |S| (1e3..1e5),
     FP32-refined, in one persistent graph-replayed launch vs a loop of single
@@ -479,6 +528,10 @@ def main():
                 extra["d100"] = d100_section(B, gp, flush)
             except Exception as e:  # reported, not hidden
                 extra["d100"] = {"error": repr(e)}
+            try:
+                extra["proxy"] = proxy_section(B, gp, flush)
+            except Exception as e:
+                extra["proxy"] = {"error": repr(e)}
         if world > 1:
             torch.distributed.barrier()
         extra["batched"] = batched_section(B, flush, world=world, rank=rank)

@@ -193,6 +193,15 @@ __device__ void run_phase(const SolveParams& P, Smem& sm, unsigned qmask, Scal s
   }
 }
 
+// Power-of-two scale of an inner (FP32) solve: the residual handed to it has
+// RMS entry near 1, so that the FP32 inner products r.D^-1 r and p.Lp stay far
+// from FP32 underflow however small the outer residual and however large the
+// Jacobi diagonal 4 pi^2 a_0 |k|^2 get.  Exact in FP64; 1 when rr = 0.
+__device__ __forceinline__ double inner_scale(double rr, int64_t rows) {
+  if (!(rr > 0.0)) return 1.0;
+  return ldexp(1.0, -ilogb(sqrt(rr / (double)(rows > 0 ? rows : 1))));
+}
+
 __device__ __forceinline__ double jacobi(const SolveParams& P, const SolveInst& in, int64_t g) {
   const int64_t nk = __ldg(P.norm + g);
   return nk > 0 ? in.dscale * (double)nk : 1.0;
@@ -413,7 +422,7 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
       v[2] = r.x * r.x + r.y * r.y;
     });
     if (!grid_sync(P)) return;
-    // outer test; inner start (all FP32): r = rhat, delta = 0, u = D^-1 r, p = s = 0
+    // outer test; inner start (all FP32): r = rhat * scale, delta = 0, u = D^-1 r, p = s = 0
     run_phase(P, sm, 0u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
       double t[kNQ];
       inst_sums(P, i, t);
@@ -424,6 +433,7 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
         const bool cap = ot >= P.max_outer;
         const bool go = act && !conv && !cap;
         sm.flag[k] = go;
+        sm.ca[k] = inner_scale(t[2], P.inst[i].rows);
         if (owner) {
           st.act[onxt] = go;
           st.inn[0] = go;
@@ -443,7 +453,8 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
       if (!sm.flag[k]) return;
       const SolveInst& in = P.inst[i];
       const double2 rh = P.rhat[g];
-      const float2 r = make_float2((float)rh.x, (float)rh.y);
+      const double sc = sm.ca[k];
+      const float2 r = make_float2((float)(rh.x * sc), (float)(rh.y * sc));
       const float rD = 1.0f / jacobi32(P, in, g);
       P.r32[g] = r;
       P.d32[g] = make_float2(0.f, 0.f);
@@ -480,7 +491,8 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
         if (lane == 0) {
           InstState& st = P.state[i];
           const int act = __ldcg(&st.inn[cur]);
-          const bool conv = t[2] <= itol2 * __ldcg(&st.rr);
+          const double rr = __ldcg(&st.rr), sc = inner_scale(rr, P.inst[i].rows);
+          const bool conv = t[2] <= itol2 * rr * sc * sc;     // r32 carries the scale
           const bool cap = it >= P.max_inner;
           const Coeffs cf = cg_coeffs(it, t[0], t[1], it ? __ldcg(&st.rho[cur]) : 0.0,
                                       it ? __ldcg(&st.alpha[cur]) : 0.0);
@@ -527,13 +539,17 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
     }
     // x += delta
     run_phase(P, sm, 0u, [&](int, const Chunk&, int k, int i, bool, int lane) {
-      if (lane == 0) sm.flag[k] = __ldcg(&P.state[i].act[onxt]);
+      if (lane == 0) {
+        sm.flag[k] = __ldcg(&P.state[i].act[onxt]);
+        sm.ca[k] = 1.0 / inner_scale(__ldcg(&P.state[i].rr), P.inst[i].rows);
+      }
     }, [&](int64_t g, int64_t, int, int, int k, double*) {
       if (!sm.flag[k]) return;
       double2 x = P.xrec[2 * g];
       const float2 dl = P.d32[g];
-      x.x += (double)dl.x;
-      x.y += (double)dl.y;
+      const double us = sm.ca[k];
+      x.x += (double)dl.x * us;
+      x.y += (double)dl.y * us;
       P.xrec[2 * g] = x;
     });
     if (!grid_sync(P)) return;

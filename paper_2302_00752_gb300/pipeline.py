@@ -118,3 +118,21 @@ def run(p: Prepared, tol=1e-12, max_iter=1000, tau=None, solve_precision=None, l
         return Result(p.z, p.M, af, av, ff, fv, stamp, f_on, None, {})
     u, stats = B.solve(stamp, f_on, tol, max_iter, solve_precision or p.solve_precision)
     return Result(p.z, p.M, af, av, ff, fv, stamp, f_on, u, stats)
+
+
+def proxy_errors(res: Result, p: Prepared, X=None):
+    """Lemma ProxyError after a solve: extends res.stamp by one level (S^{N+1}
+    holds the support of L[a_hat] u^{s,N}, Proposition LExpansion) and returns
+    the exact relative proxy ||f_hat - L u||_2 / ||f_hat||_2 and, given
+    Monte Carlo points X (uint32 [Q, d], x = X / 2^32), its Monte Carlo
+    estimate from the point values of f (the input trigonometric sum) and of
+    f^{s,N}.  The stamp is left at level N + 1."""
+    n_u = res.stamp.size
+    res.stamp.extend(1)
+    f1, _ = res.stamp.scatter(res.f_freq, res.f_val)
+    num, den = B.proxy_residual(res.stamp, res.u.to(torch.complex128), f1)
+    out = {"exact": float(np.sqrt(num / den)), "n_u": n_u, "size": res.stamp.size}
+    if X is not None:
+        r, fx = B.proxy_mc(res.stamp, res.u.to(torch.complex128), p.f_freq, p.f_coef, X)
+        out["mc"] = float(torch.sqrt((r * r).sum() / (fx * fx).sum()))
+    return out
