@@ -184,7 +184,11 @@ def count_launches(fn):
     try:
         from torch.autograd import DeviceType
         from torch.profiler import ProfilerActivity, profile
-        # device events are listed only beside CPU activity
+        # device events are listed only beside CPU activity, and the first
+        # profiling session of a process records none: open one to warm up
+        with profile(activities=[ProfilerActivity.CPU, ProfilerActivity.CUDA]):
+            torch.zeros(1, device="cuda").add_(1)
+            torch.cuda.synchronize()
         with profile(activities=[ProfilerActivity.CPU, ProfilerActivity.CUDA]) as prof:
             fn()
             torch.cuda.synchronize()
