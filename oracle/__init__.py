@@ -24,6 +24,8 @@ Modules and the parts of the paper they follow:
   solve     Jacobi-preconditioned CG, dense LU and the tridiagonal chain solve
             for the one-term problem (Algorithm 1, last step; the diagonal
             rearrangement in the proof of Proposition SolutionSupport).
+  adr       the advection-diffusion-reaction operator of Remark ADR (union
+            step set, explicit matrix, exact convolution, direct solve, proxy).
 
 Parity status of every function is stated in its module header.
 """

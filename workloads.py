@@ -286,6 +286,56 @@ def make_wide(seed=0, d=4, scale=20000, n_cos=3, n_f=3, N=2):
                     "fp64", "fp64", None, (seed,))
 
 
+@dataclass
+class AdrInstance:
+    """Data of -div(a grad u) + b.grad u + c u = f (Remark ADR)."""
+    name: str
+    d: int
+    N: int
+    a: TrigSum
+    b: list                     # d TrigSums, one per component of b
+    c: TrigSum
+    f: TrigSum | None = None
+    u_freq: np.ndarray | None = None
+    u_val: np.ndarray | None = None
+    seed: tuple = ()
+
+
+def _sin_cos(rng, n_sin, n_cos, d, lo, hi, amp_lo, amp_hi):
+    freq, _ = draw_freqs(rng, n_sin + n_cos, d, lo, hi)
+    amp = rng.uniform(amp_lo, amp_hi, size=n_sin + n_cos)
+    coef = np.concatenate([-1j * amp[:n_sin], amp[n_sin:] + 0j])
+    return freq, coef.astype(np.complex128), amp
+
+
+def make_adr(seed=0, N=1, d=3, kmax=50, n_a=2, n_bc=5, n_f=(2, 3), manufactured_u=None):
+    """The three-dimensional exactly sparse ADR data of Section "Three-dimensional
+    exactly sparse advection-diffusion-reaction equation": a = a0 + 2 sines + 2
+    cosines (amplitudes U[-1,1]), each b_j and c (minus its mean) 5 sines + 5
+    cosines (amplitudes U[0,1]), f = 2 sines + 3 cosines (U[-1,1]); every
+    frequency uniform in [-(kmax-1), kmax]^d; a0 and c0 are 4 ceil(l2 norm of
+    the other amplitudes).  manufactured_u = n draws a Hermitian u with n pairs
+    in the same box instead of f (f then follows from the operator)."""
+    rng = np.random.default_rng([seed, 0xadc])
+    lo, hi = -(kmax - 1), kmax
+    fa, ca, amp_a = _sin_cos(rng, n_a, n_a, d, lo, hi, -1.0, 1.0)
+    a = TrigSum(np.vstack([np.zeros((1, d), np.int32), fa]).astype(np.int32),
+                np.concatenate([[4.0 * np.ceil(np.linalg.norm(amp_a))], ca]).astype(np.complex128))
+    b = []
+    for _ in range(d):
+        fb, cb, _ = _sin_cos(rng, n_bc, n_bc, d, lo, hi, 0.0, 1.0)
+        b.append(TrigSum(fb.astype(np.int32), cb))
+    fc, cc, amp_c = _sin_cos(rng, n_bc, n_bc, d, lo, hi, 0.0, 1.0)
+    c = TrigSum(np.vstack([np.zeros((1, d), np.int32), fc]).astype(np.int32),
+                np.concatenate([[4.0 * np.ceil(np.linalg.norm(amp_c))], cc]).astype(np.complex128))
+    if manufactured_u:
+        qs, _ = draw_freqs(rng, manufactured_u, d, lo, hi)
+        uf, uv = manufactured(rng, qs)
+        return AdrInstance(f"adr_d{d}_N{N}_u", d, N, a, b, c, None, uf, uv, (seed,))
+    ff, cf, _ = _sin_cos(rng, n_f[0], n_f[1], d, lo, hi, -1.0, 1.0)
+    return AdrInstance(f"adr_d{d}_N{N}", d, N, a, b, c, TrigSum(ff.astype(np.int32), cf), None, None, (seed,))
+
+
 def make_tiny(seed=0, d=2, n_cos=2, n_u=2, N=2, box=3, ubox=4, manufactured_u=True):
     """Small instances for brute-force checks (d <= 3, few terms)."""
     rng = np.random.default_rng(seed)
