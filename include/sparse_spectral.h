@@ -163,6 +163,23 @@ ss_status sft_recover(const ss_lattice* lat, const ss_trig* g, ss_precision prec
 ss_status stamp_build(const ss_sparse* a_hat, const int32_t* f_freq, int64_t n_f, int32_t N,
                       ss_stamp* out, void* stream);
 
+/* Stamping set and operator of the advection-diffusion-reaction problem
+ * -div(a grad u) + b.grad u + c u = f (Remark ADR).  a_hat and c_hat as in
+ * stamp_build's a_hat; b_hat: host array of d sparse lists, component j of
+ * the vector field b (device frequencies and values, possibly empty).  All
+ * Hermitian (real data); a_hat must pass the positivity check.  The step set
+ * of eq. StampSet is the union U of supp a_hat, supp b_hat_j and supp c_hat
+ * (their Minkowski sum would add frequencies with no coupling); the canonical
+ * order is stamp_build's with U in place of supp a_hat.  The operator entry
+ * of row k and l = k - p, p in U, is
+ *   4 pi^2 (k.l) a_hat_p + 2 pi i (l . b_hat_p) + c_hat_p
+ * (b_hat_p = (b_hat_{1,p}, ..., b_hat_{d,p})); k = 0 is an ordinary row and
+ * column, and F may contain 0.  Solved by solve in SS_FP64 (BiCGStab);
+ * galerkin_apply, proxy_residual, proxy_mc and stamp_extend apply; the FP32
+ * operator, solve_noalloc and batches do not (SS_ERR_INVALID).  d <= 64. */
+ss_status stamp_build_adr(const ss_sparse* a_hat, const ss_sparse* b_hat, const ss_sparse* c_hat,
+                          const int32_t* f_freq, int64_t n_f, int32_t N, ss_stamp* out, void* stream);
+
 /* |S|, operator nonzeros #{(k,p): k in S\{0}, k-p in S\{0}}, the canonical
  * index of k = 0 (-1 if absent), and the number of levels (N + 1).  Host. */
 ss_status stamp_info(ss_stamp s, int64_t* size, int64_t* nnz, int64_t* zero_index, int32_t* n_levels);
@@ -197,7 +214,8 @@ void stamp_destroy(ss_stamp s);
 /* y = L_{N,s} u on S (eq. FiniteGalerkinOperator):
  *   y_k = sum_{p in supp a_hat, k-p in S} 4 pi^2 (k.(k-p)) a_hat_p u_{k-p},
  * the integer k.(k-p) formed exactly as (|k|^2 + |k-p|^2 - |p|^2)/2; the row of
- * k = 0 is the identity (pins u_hat_0).  u, y: device complex [|S|], FP64 or
+ * k = 0 is the identity (pins u_hat_0).  ADR stamps: the entries of
+ * stamp_build_adr, no identity row, SS_FP64 only.  u, y: device complex [|S|], FP64 or
  * FP32 per `prec` (FP32: FP32 values, FP32 accumulation).  Uses the stamp's
  * scratch: concurrent calls on one stamp must be on one stream. */
 ss_status galerkin_apply(ss_stamp s, const void* u, void* y, ss_precision prec, void* stream);
@@ -217,7 +235,8 @@ ss_status proxy_residual(ss_stamp s, const double* u_prefix, int64_t n_u, const 
  *   f_out[q] = f(x_q) = sum_t Re(f.coef[t] exp(2 pi i f.freq[t] . x_q)),
  *   r_out[q] = f(x_q) - f^{s,N}(x_q),  f^{s,N}(x) = sum_{k in S} (L u)_k exp(2 pi i k.x),
  * with u on the first n_u frequencies of S (u_prefix: device FP64 complex
- * [n_u], zero elsewhere) and L the operator on S's rows, (L u)_0 = 0.  When
+ * [n_u], zero elsewhere) and L the operator on S's rows ((L u)_0 = 0 for the
+ * diffusion operator; an ordinary row for ADR stamps).  When
  * S = S^{N+1} and u solves on S^N, f^{s,N} = L[a_hat] u is exact (Proposition
  * LExpansion).  The estimate of ||f - f^{s,N}||_{L2} / ||f||_{L2} is
  * sqrt(sum r^2 / sum f^2).  Phases k.X mod 2^32 are exact integers; each
@@ -237,7 +256,10 @@ ss_status proxy_mc(ss_stamp s, const double* u_prefix, int64_t n_u, const ss_tri
  *            refinement whose residual f - L u is formed with the FP64 operator.
  * f_on_S, u_on_S: device FP64 complex [|S|].  One persistent cooperative
  * launch.  Writes stats (host, may be NULL) and synchronises `stream`.
- * f_hat_0 must be 0 (SS_ERR_INVALID otherwise). */
+ * f_hat_0 must be 0 (SS_ERR_INVALID otherwise).  ADR stamps (stamp_build_adr)
+ * take SS_FP64 only and are solved by BiCGStab with the operator's complex
+ * diagonal as right Jacobi preconditioner, to the same stopping rule; f_hat_0
+ * is unrestricted there. */
 ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, double tol, int32_t max_iter,
                 ss_precision prec, ss_solve_stats* stats, void* stream);
 

@@ -10,7 +10,7 @@ import importlib
 
 _EXPORTS = ("SS_FP32", "SS_FP64", "Batch", "SSError", "Stamp", "galerkin_apply", "lattice_cbc", "lattice_check",
             "lattice_random", "lattice_sample", "lattice_size", "sft_recover", "sft_recover_samples", "solve",
-            "stamp_build", "version", "proxy_residual", "proxy_mc", "solve_noalloc")
+            "stamp_build", "stamp_build_adr", "version", "proxy_residual", "proxy_mc", "solve_noalloc")
 
 __all__ = list(_EXPORTS)
 

@@ -69,6 +69,7 @@ def _load():
         "sft_recover_samples": (i32, [P(Lattice), vp, i32, vp, i64, i64, dbl, vp, vp, P(i64), vp]),
         "sft_recover": (i32, [P(Lattice), P(Trig), i32, vp, i64, i64, dbl, vp, vp, P(i64), vp]),
         "stamp_build": (i32, [P(Sparse), vp, i64, i32, P(vp), vp]),
+        "stamp_build_adr": (i32, [P(Sparse), P(Sparse), P(Sparse), vp, i64, i32, P(vp), vp]),
         "stamp_info": (i32, [vp, P(i64), P(i64), P(i64), P(i32)]),
         "stamp_export": (i32, [vp, vp, vp, vp]),
         "stamp_lookup": (i32, [vp, vp, i64, vp, vp]),
@@ -311,6 +312,37 @@ def stamp_build(a_freq, a_val, f_freq, N):
     h = C.c_void_p()
     _check(lib.stamp_build(C.byref(sp), _ptr(ff), ff.shape[0], int(N), C.byref(h), _stream()))
     return Stamp(h.value, d)
+
+
+def _sparse(freq, val, d):
+    f = _dev_i32(np.asarray(freq).reshape(-1, d) if not torch.is_tensor(freq) else freq, d)
+    v = _dev_c128(val)
+    sp = Sparse(d, f.shape[0], _ptr(f) if f.numel() else None, _ptr(v) if v.numel() else None)
+    sp._keep = (f, v)
+    return sp
+
+
+def stamp_build_adr(a_freq, a_val, b, c_freq, c_val, f_freq, N):
+    """Stamping set and operator of -div(a grad u) + b.grad u + c u = f
+    (Remark ADR); b: d pairs (freq, val), one per component of b."""
+    af = np.asarray(a_freq.cpu() if torch.is_tensor(a_freq) else a_freq)
+    d = int(af.shape[1])
+    if len(b) != d:
+        raise ValueError("b needs one (freq, val) pair per coordinate")
+    sa = _sparse(a_freq, a_val, d)
+    sc = _sparse(c_freq, c_val, d)
+    sb = (Sparse * d)()
+    keep = []
+    for j, (bf, bv) in enumerate(b):
+        one = _sparse(bf, bv, d)
+        sb[j] = one
+        keep.append(one._keep)
+    ff = _dev_i32(f_freq, d)
+    h = C.c_void_p()
+    _check(lib.stamp_build_adr(C.byref(sa), sb, C.byref(sc), _ptr(ff), ff.shape[0], int(N), C.byref(h), _stream()))
+    st = Stamp(h.value, d)
+    st.adr = True
+    return st
 
 
 def proxy_residual(stamp, u_prefix, f_on_S):

@@ -140,12 +140,13 @@ ss_status launch_pack64_prefix(const ss_stamp_s* s, const double2* u, int64_t n_
 }
 
 ss_status launch_apply64(const ss_stamp_s* s, double2* y, cudaStream_t st) {
-  k_apply64<<<nblk(s->rows_pad), 256, 0, st>>>(op_view(s), s->size, s->rows_pad, s->rec64.get(), s->zero_idx, y);
+  k_apply64<<<nblk(s->rows_pad), 256, 0, st>>>(op_view(s), s->size, s->rows_pad, s->rec64.get(), identity_row(s), y);
   SS_LAUNCH_CHECK();
   return SS_OK;
 }
 
 ss_status launch_apply32(const ss_stamp_s* s, float2* y, cudaStream_t st) {
+  if (s->adr) SS_FAIL(SS_ERR_INVALID, "the FP32 operator is not available for ADR stamps (use SS_FP64)");
   const size_t sm = s->s_a * (sizeof(float2) + sizeof(int32_t)) + 16;
   k_apply32<<<nblk(s->rows_pad), 256, sm, st>>>(op_view(s), s->size, s->rows_pad, s->norm.get(), s->wide,
                                                 s->rec32.get(), s->ca32.get(), s->pn32.get(), s->s_a, s->zero_idx, y);

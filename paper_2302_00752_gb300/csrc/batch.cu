@@ -235,6 +235,8 @@ static ss_status batch_create_impl(ss_batch_s* b, int32_t n, const ss_stamp* sta
 
 extern "C" ss_status batch_create(int32_t n_inst, const ss_stamp* stamps, ss_batch* out, void* stream) {
   if (!out || !stamps || n_inst < 1) SS_FAIL(SS_ERR_INVALID, "batch_create: bad argument");
+  for (int i = 0; i < n_inst; ++i)
+    if (stamps[i] && stamps[i]->adr) SS_FAIL(SS_ERR_INVALID, "batch_create: ADR stamps are solved one at a time");
   *out = nullptr;
   ss_batch_s* b = new ss_batch_s();
   ss_status s = batch_create_impl(b, n_inst, stamps, as_stream(stream));

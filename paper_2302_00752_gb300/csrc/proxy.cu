@@ -209,8 +209,9 @@ extern "C" ss_status proxy_mc(ss_stamp s, const double* u_prefix, int64_t n_u, c
     SS_TRY(launch_pack64_prefix(s, reinterpret_cast<const double2*>(u_prefix), n_u, st));
     SS_TRY(y.alloc(ng, st));
     SS_TRY(launch_apply64(s, y.get(), st));
-    // (L u)_0 = 0 exactly (the factor k.l); the stored identity row is for the solve
-    if (s->zero_idx >= 0) SS_CUDA(cudaMemsetAsync(y.get() + s->zero_idx, 0, sizeof(double2), st));
+    // (L u)_0 = 0 exactly for the diffusion operator (the factor k.l); its
+    // stored identity row is for the solve
+    if (identity_row(s) >= 0) SS_CUDA(cudaMemsetAsync(y.get() + identity_row(s), 0, sizeof(double2), st));
     SS_TRY(cf_g.alloc(ng, st));
     k_coef_df<<<nblk(ng), 256, 0, st>>>(y.get(), ng, -1.0, cf_g.get());
     SS_LAUNCH_CHECK();

@@ -18,7 +18,9 @@
 //         the FP32 operator with FP32 vectors (inner products reduced in FP64,
 //         FP64 scalars) to a relative reduction inner_tol, then x += delta in
 //         FP64.
-// The Jacobi preconditioner is D_k = 4 pi^2 Re(a_hat_0) |k|^2 (the diagonal of L),
+//   ADR   BiCGStab on the FP64 operator of Remark ADR (not Hermitian), right
+//         Jacobi preconditioning with its complex diagonal.
+// The CG preconditioner is D_k = 4 pi^2 Re(a_hat_0) |k|^2 (the diagonal of L),
 // 1 on the zero row and on padding rows.
 #include <algorithm>
 #include <cmath>
@@ -32,6 +34,8 @@ struct Smem {
   double acc[kMaxWarps][kMaxInstPerChunk][kNQ];
   double ca[kMaxInstPerChunk];
   double cb[kMaxInstPerChunk];
+  double cc[kMaxInstPerChunk];
+  double cd[kMaxInstPerChunk];
   int32_t flag[kMaxInstPerChunk];
 };
 
@@ -561,11 +565,217 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
   });
 }
 
+// ------------------------------------------------- BiCGStab (ADR operator)
+//
+// The operator of Remark ADR is not Hermitian.  BiCGStab (van der Vorst, 1992)
+// with right Jacobi preconditioning y = D^-1 p, D = diag L (complex), and the
+// shadow residual r^ = r_0 = f:
+//   rho = <r^, r>, beta = (rho / rho_prev) (alpha / omega)
+//   p = r + beta (p - omega v),  v = L D^-1 p
+//   alpha = rho / <r^, v>,  s = r - alpha v,  x += alpha D^-1 p
+//   t = L D^-1 s,  omega = <t, s> / <t, t>,  x += omega D^-1 s,  r = s - omega t
+// with <a, b> = sum conj(a) b.  Five phases per iteration, each closed by a
+// grid barrier; every block recomputes the scalars from the deterministic
+// partial sums, and the owner keeps rho, alpha and omega by iteration parity.
+// A vanishing denominator restarts the direction (beta = 0) or skips the
+// step (alpha or omega = 0); the iteration cap then reports non-convergence.
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double n = b.x * b.x + b.y * b.y;
+  if (n == 0.0) return make_double2(0.0, 0.0);
+  return make_double2((a.x * b.x + a.y * b.y) / n, (a.y * b.x - a.x * b.y) / n);
+}
+// conj(a) b
+__device__ __forceinline__ double2 cdot(double2 a, double2 b) {
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+__device__ void solve_bicgstab(const SolveParams& P, Smem& sm) {
+  const double tol2 = P.tol * P.tol;
+  auto noscal = [](int, const Chunk&, int, int, bool, int) {};
+  // x = 0, r = r^ = f, p = v = 0, dlt = D^-1;  <r^, r> = |f|^2 (q0), |r|^2 (q2), |f|^2 (q3)
+  run_phase(P, sm, 0b1101u, noscal, [&](int64_t g, int64_t, int, int i, int, double* v) {
+    const double2 f = f_at(P.inst[i], g);
+    P.xrec[2 * g] = make_double2(0.0, 0.0);
+    P.r[g] = f;
+    P.rhat[g] = f;
+    P.pd[g] = make_double2(0.0, 0.0);
+    P.w64[g] = make_double2(0.0, 0.0);
+    P.dlt[g] = cdiv(make_double2(1.0, 0.0), __ldg(P.cdiag + g));
+    const double ff = f.x * f.x + f.y * f.y;
+    v[0] = ff;
+    v[2] = ff;
+    v[3] = ff;
+  });
+  if (!grid_sync(P)) return;
+  for (int it = 0;; ++it) {
+    const int cur = it & 1, nxt = cur ^ 1;
+    // A: test, beta; p = r + beta (p - omega v); y = D^-1 p (records of urec64)
+    run_phase(P, sm, 0u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
+      double t[kNQ];
+      inst_sums(P, i, t);
+      if (lane == 0) {
+        InstState& st = P.state[i];
+        const int act = it == 0 ? 1 : __ldcg(&st.act[cur]);
+        const double bb = it == 0 ? t[3] : __ldcg(&st.bb);
+        const bool conv = t[2] <= tol2 * bb;
+        const bool cap = it >= P.max_iter;
+        const bool go = act && !conv && !cap;
+        const double2 rho = make_double2(t[0], t[1]);
+        double2 beta = make_double2(0.0, 0.0), om = make_double2(0.0, 0.0);
+        if (it > 0) {
+          om = __ldcg(&st.zomega[cur]);
+          beta = cmul(cdiv(rho, __ldcg(&st.zrho[cur])), cdiv(__ldcg(&st.zalpha[cur]), om));
+        }
+        sm.flag[k] = go;
+        sm.ca[k] = beta.x;
+        sm.cb[k] = beta.y;
+        sm.cc[k] = om.x;
+        sm.cd[k] = om.y;
+        if (owner) {
+          if (it == 0) {
+            st.bb = bb;
+            st.outer_iters = 1;
+          }
+          st.act[nxt] = go;
+          st.zrho[nxt] = rho;
+          if (act) {
+            st.rr = t[2];
+            st.iters = it;
+            if (conv) owner_done(P, st, SS_OK);
+            else if (cap) owner_done(P, st, SS_ERR_NOT_CONVERGED);
+          }
+        }
+      }
+    }, [&](int64_t g, int64_t, int, int, int k, double*) {
+      if (!sm.flag[k]) return;
+      const double2 beta = make_double2(sm.ca[k], sm.cb[k]), om = make_double2(sm.cc[k], sm.cd[k]);
+      const double2 r = P.r[g], v = P.w64[g];
+      double2 p = P.pd[g];
+      const double2 q = make_double2(p.x - (om.x * v.x - om.y * v.y), p.y - (om.x * v.y + om.y * v.x));
+      p = make_double2(r.x + (beta.x * q.x - beta.y * q.y), r.y + (beta.x * q.y + beta.y * q.x));
+      P.pd[g] = p;
+      P.urec64[2 * g] = cmul(P.dlt[g], p);
+    });
+    if (!grid_sync(P)) return;
+    if (block_counter(P, 0) >= P.n_inst) break;
+    // B: v = L y;  <r^, v>
+    run_phase(P, sm, 0b0011u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
+      if (lane == 0) {
+        sm.flag[k] = __ldcg(&P.state[i].act[nxt]);
+        if (owner && sm.flag[k]) P.state[i].applies += 1;
+      }
+    }, [&](int64_t g, int64_t s, int lane, int i, int k, double* v) {
+      if (!sm.flag[k]) return;
+      const double2 w = apply64_row(P, P.inst[i], s, lane, g, P.urec64);
+      P.w64[g] = w;
+      const double2 q = cdot(P.rhat[g], w);
+      v[0] = q.x;
+      v[1] = q.y;
+    });
+    if (!grid_sync(P)) return;
+    // C: alpha = rho / <r^, v>; s = r - alpha v; x += alpha y; z = D^-1 s
+    run_phase(P, sm, 0u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
+      double t[kNQ];
+      inst_sums(P, i, t);
+      if (lane == 0) {
+        InstState& st = P.state[i];
+        const double2 alpha = cdiv(__ldcg(&st.zrho[nxt]), make_double2(t[0], t[1]));
+        sm.flag[k] = __ldcg(&st.act[nxt]);
+        sm.ca[k] = alpha.x;
+        sm.cb[k] = alpha.y;
+        if (owner) st.zalpha[nxt] = alpha;
+      }
+    }, [&](int64_t g, int64_t, int, int, int k, double*) {
+      if (!sm.flag[k]) return;
+      const double2 alpha = make_double2(sm.ca[k], sm.cb[k]);
+      const double2 r = P.r[g], v = P.w64[g], y = P.urec64[2 * g];
+      const double2 av = cmul(alpha, v), ay = cmul(alpha, y);
+      const double2 s = make_double2(r.x - av.x, r.y - av.y);
+      double2 x = P.xrec[2 * g];
+      x.x += ay.x;
+      x.y += ay.y;
+      P.xrec[2 * g] = x;
+      P.sd[g] = s;
+      P.zrec[2 * g] = cmul(P.dlt[g], s);
+    });
+    if (!grid_sync(P)) return;
+    // D: t = L z;  <t, s>, <t, t>
+    run_phase(P, sm, 0b0111u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
+      if (lane == 0) {
+        sm.flag[k] = __ldcg(&P.state[i].act[nxt]);
+        if (owner && sm.flag[k]) P.state[i].applies += 1;
+      }
+    }, [&](int64_t g, int64_t s, int lane, int i, int k, double* v) {
+      if (!sm.flag[k]) return;
+      const double2 t = apply64_row(P, P.inst[i], s, lane, g, P.zrec);
+      P.tv[g] = t;
+      const double2 q = cdot(t, P.sd[g]);
+      v[0] = q.x;
+      v[1] = q.y;
+      v[2] = t.x * t.x + t.y * t.y;
+    });
+    if (!grid_sync(P)) return;
+    // E: omega = <t, s> / <t, t>; x += omega z; r = s - omega t;  <r^, r>, |r|^2
+    run_phase(P, sm, 0b0111u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
+      double t[kNQ];
+      inst_sums(P, i, t);
+      if (lane == 0) {
+        InstState& st = P.state[i];
+        const double2 om = t[2] > 0.0 ? make_double2(t[0] / t[2], t[1] / t[2]) : make_double2(0.0, 0.0);
+        sm.flag[k] = __ldcg(&st.act[nxt]);
+        sm.ca[k] = om.x;
+        sm.cb[k] = om.y;
+        if (owner) st.zomega[nxt] = om;
+      }
+    }, [&](int64_t g, int64_t, int, int, int k, double* v) {
+      if (!sm.flag[k]) return;
+      const double2 om = make_double2(sm.ca[k], sm.cb[k]);
+      const double2 s = P.sd[g], t = P.tv[g], z = P.zrec[2 * g];
+      const double2 oz = cmul(om, z), ot = cmul(om, t);
+      double2 x = P.xrec[2 * g];
+      x.x += oz.x;
+      x.y += oz.y;
+      P.xrec[2 * g] = x;
+      const double2 r = make_double2(s.x - ot.x, s.y - ot.y);
+      P.r[g] = r;
+      const double2 q = cdot(P.rhat[g], r);
+      v[0] = q.x;
+      v[1] = q.y;
+      v[2] = r.x * r.x + r.y * r.y;
+    });
+    if (!grid_sync(P)) return;
+  }
+  // true residual f - L x in FP64, and the output
+  run_phase(P, sm, 0b0100u, noscal, [&](int64_t g, int64_t s, int lane, int i, int, double* v) {
+    const SolveInst& in = P.inst[i];
+    const double2 y = apply64_row(P, in, s, lane, g, P.xrec);
+    const double2 f = f_at(in, g);
+    const double2 r = make_double2(f.x - y.x, f.y - y.y);
+    v[2] = r.x * r.x + r.y * r.y;
+    const int64_t l = g - in.row0;
+    if (l < in.rows) in.u[l] = P.xrec[2 * g];
+  });
+  if (!grid_sync(P)) return;
+  run_phase(P, sm, 0u, [&](int, const Chunk&, int, int i, bool owner, int lane) {
+    double t[kNQ];
+    inst_sums(P, i, t);
+    if (owner && lane == 0) {
+      P.state[i].rr = t[2];
+      P.state[i].applies += 1;
+    }
+  }, [](int64_t, int64_t, int, int, int, double*) {});
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(1024) k_solve(SolveParams P) {
   __shared__ Smem sm;
-  if (MODE == 0) solve_fp64(P, sm);
-  else solve_refined(P, sm);
+  if constexpr (MODE == 0) solve_fp64(P, sm);
+  else if constexpr (MODE == 1) solve_refined(P, sm);
+  else solve_bicgstab(P, sm);
 }
 
 __global__ void k_init_solve_records(const int64_t* __restrict__ norm, int64_t n, const int8_t* __restrict__ wide_rows,
@@ -662,6 +872,18 @@ ss_status work_alloc(SolveWork& W, int64_t rows_total, const int64_t* norm, cons
   return SS_OK;
 }
 
+ss_status work_alloc_bicgstab(SolveWork& W, cudaStream_t st) {
+  if (W.zrec.n >= (size_t)(2 * W.rows_total) && W.tv.n >= (size_t)W.rows_total) return SS_OK;
+  SS_TRY(W.zrec.alloc(2 * W.rows_total, st));
+  SS_TRY(W.tv.alloc(W.rows_total, st));
+  // the odd halves of the z records are never read by the FP64 operator
+  SS_CUDA(cudaMemsetAsync(W.zrec.get(), 0, 2 * W.rows_total * sizeof(double2), st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  W.zrec.settle();
+  W.tv.settle();
+  return SS_OK;
+}
+
 ss_status work_upload(SolveWork& W, const SolvePlan& plan, cudaStream_t st) {
   const int n_inst = (int)plan.inst.size(), n_chunk = (int)plan.chunk.size();
   if (n_inst > W.cap_inst) { SS_TRY(W.inst.alloc(n_inst, st)); SS_TRY(W.state.alloc(n_inst, st)); W.cap_inst = n_inst; }
@@ -676,7 +898,8 @@ ss_status work_upload(SolveWork& W, const SolvePlan& plan, cudaStream_t st) {
 ss_status max_grid(int mode, int block, int* grid) {
   int nb = 0;
   if (mode == 0) SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<0>, block, 0));
-  else SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<1>, block, 0));
+  else if (mode == 1) SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<1>, block, 0));
+  else SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<2>, block, 0));
   if (nb < 1) SS_FAIL(SS_ERR_CUDA, "solve: kernel does not fit on an SM with %d threads", block);
   *grid = nb * sm_count();
   return SS_OK;
@@ -684,9 +907,11 @@ ss_status max_grid(int mode, int block, int* grid) {
 
 // Fill params and launch (capturable: no host synchronisation).
 ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, const int32_t* slice_inst,
-                              const int64_t* norm, const double2* ca64, const float2* ca32, const int32_t* pn,
-                              double tol, int max_iter, ss_precision prec, cudaStream_t st, cudaEvent_t ev_begin,
-                       cudaEvent_t ev_end) {
+                       const int64_t* norm, const double2* ca64, const float2* ca32, const int32_t* pn,
+                       double tol, int max_iter, int mode, cudaStream_t st, cudaEvent_t ev_begin,
+                       cudaEvent_t ev_end, const double2* cdiag) {
+  if (mode == 2 && (!cdiag || !W.zrec.get() || !W.tv.get()))
+    SS_FAIL(SS_ERR_INVALID, "solve: BiCGStab needs the operator diagonal and its workspace");
   SolveParams P{};
   P.n_inst = (int)plan.inst.size();
   P.n_chunks = (int)plan.chunk.size();
@@ -714,6 +939,9 @@ ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, co
   P.s32 = W.s32.get();
   P.d32 = W.d32.get();
   P.rdiag = W.rdiag.get();
+  P.cdiag = cdiag;
+  P.zrec = W.zrec.get();
+  P.tv = W.tv.get();
   P.part = W.part.get();
   P.bar = W.bar.get();
   P.counters = W.counters.get();
@@ -741,8 +969,9 @@ ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, co
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (ev_begin) SS_CUDA(cudaEventRecord(ev_begin, st));
-  if (prec == SS_FP64) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<0>, P));
-  else SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<1>, P));
+  if (mode == 0) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<0>, P));
+  else if (mode == 1) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<1>, P));
+  else SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<2>, P));
   if (ev_end) SS_CUDA(cudaEventRecord(ev_end, st));
   return SS_OK;
 }
@@ -803,7 +1032,7 @@ static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream
   in.row0 = 0;
   in.rows = s->size;
   in.rows_pad = s->rows_pad;
-  in.zero_row = s->zero_idx;
+  in.zero_row = identity_row(s);
   in.coef_off = 0;
   in.dscale = 2.0 * kTwoPiSq * s->a0;   // 4 pi^2 Re(a_hat_0)
   in.wide = s->wide ? 1 : 0;
@@ -816,6 +1045,7 @@ static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream
   SS_TRY(plan_chunks(C.plan, woff, {}, target));
   C.plan.grid = std::min<int>(grid, (int)C.plan.chunk.size());
   SS_TRY(work_alloc(C.work, s->rows_pad + 1, s->norm.get(), nullptr, s->wide, st));
+  if (mode == 2) SS_TRY(work_alloc_bicgstab(C.work, st));
   SS_TRY(work_upload(C.work, C.plan, st));
   C.planned_mode = mode;
   return SS_OK;
@@ -868,7 +1098,8 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
   if (!(tol > 0.0) || max_iter < 1) SS_FAIL(SS_ERR_INVALID, "solve: need tol > 0 and max_iter >= 1");
   if (prec != SS_FP64 && prec != SS_FP32) SS_FAIL(SS_ERR_INVALID, "solve: bad precision");
   cudaStream_t st = as_stream(stream);
-  if (s->zero_idx >= 0) {
+  if (s->adr && prec != SS_FP64) SS_FAIL(SS_ERR_INVALID, "solve: ADR stamps solve in SS_FP64 (BiCGStab)");
+  if (!s->adr && s->zero_idx >= 0) {
     double2 f0;
     SS_CUDA(cudaMemcpyAsync(&f0, reinterpret_cast<const double2*>(f_on_S) + s->zero_idx, sizeof(f0),
                             cudaMemcpyDeviceToHost, st));
@@ -876,7 +1107,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
     if (f0.x != 0.0 || f0.y != 0.0) SS_FAIL(SS_ERR_INVALID, "solve: f_hat_0 must be 0 (mean-zero forcing)");
   }
   ss_solve_ctx* C = solve_ctx(s);
-  const int mode = prec == SS_FP64 ? 0 : 1;
+  const int mode = s->adr ? 2 : (prec == SS_FP64 ? 0 : 1);
   SS_TRY(stamp_plan(s, *C, mode, st));
   C->plan.inst[0].f = reinterpret_cast<const double2*>(f_on_S);
   C->plan.inst[0].u = reinterpret_cast<double2*>(u_on_S);
@@ -892,7 +1123,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
     SS_CUDA(cudaEventCreate(&C->work.ev[1]));
   }
   SS_TRY(launch_solve(C->work, C->plan, op, nullptr, s->norm.get(), s->ca64.get(), s->ca32.get(), s->pn32.get(), tol,
-                      max_iter, prec, st, C->work.ev[0], C->work.ev[1]));
+                      max_iter, mode, st, C->work.ev[0], C->work.ev[1], s->adr ? s->diag64.get() : nullptr));
   ss_status worst;
   ss_solve_stats one{};
   SS_TRY(read_stats(C->work, 1, &one, &worst, st, C->work.ev[0], C->work.ev[1]));
@@ -985,6 +1216,7 @@ extern "C" ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_o
   if (!s || !f_on_S || !u_on_S) SS_FAIL(SS_ERR_INVALID, "solve_noalloc: null argument");
   if (!(tol > 0.0) || max_iter < 1) SS_FAIL(SS_ERR_INVALID, "solve_noalloc: need tol > 0 and max_iter >= 1");
   if (prec != SS_FP64 && prec != SS_FP32) SS_FAIL(SS_ERR_INVALID, "solve_noalloc: bad precision");
+  if (s->adr) SS_FAIL(SS_ERR_INVALID, "solve_noalloc: ADR stamps are solved by solve (BiCGStab)");
   if (s->rows_pad > kNoAllocRows)
     SS_FAIL(SS_ERR_INVALID,
             "solve_noalloc: |S| = %lld (%lld padded rows) exceeds the allocation-free workspace of %lld rows",

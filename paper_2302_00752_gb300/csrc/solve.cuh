@@ -31,6 +31,7 @@ struct InstState {
   int32_t act[2];           // by iteration parity: CG (FP64) / refinement (FP32) running
   int32_t inn[2];           // by inner-iteration parity: inner CG running (FP32 mode)
   int32_t iters, inner_iters, outer_iters, applies, status, pad_;
+  double2 zrho[2], zalpha[2], zomega[2];   // BiCGStab scalars by iteration parity (ADR)
 };
 
 struct SolveParams {
@@ -59,6 +60,9 @@ struct SolveParams {
   float2* s32;
   float2* d32;
   double* rdiag;               // 1 / D (FP64 mode)
+  const double2* cdiag;        // complex diagonal of the ADR operator (BiCGStab), else null
+  double2* zrec;               // BiCGStab: records of z = D^-1 s
+  double2* tv;                 // BiCGStab: t = L z
   double* part;                // [slots][kNQ]
   unsigned* bar;               // barrier count, generation
   int* counters;               // done, inner started, inner finished
@@ -85,6 +89,7 @@ struct SolveWork {
     if (ev[1]) cudaEventDestroy(ev[1]);
   }
   DevBuf<double2> xrec, urec64, r, w64, pd, sd, rhat, dlt;
+  DevBuf<double2> zrec, tv;                // BiCGStab only (allocated on first use)
   DevBuf<float4> urec32;
   DevBuf<float2> w32, r32, p32, s32, d32;
   DevBuf<double> rdiag;
@@ -104,10 +109,13 @@ ss_status work_alloc(SolveWork& W, int64_t rows_total, const int64_t* norm, cons
                      cudaStream_t st);
 ss_status work_upload(SolveWork& W, const SolvePlan& plan, cudaStream_t st);
 ss_status max_grid(int mode, int block, int* grid);
+// mode: 0 FP64 CG, 1 FP32-refined CG, 2 FP64 BiCGStab (ADR operator; cdiag
+// = its complex diagonal, workspace from work_alloc_bicgstab).
 ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, const int32_t* slice_inst,
                        const int64_t* norm, const double2* ca64, const float2* ca32, const int32_t* pn,
-                       double tol, int max_iter, ss_precision prec, cudaStream_t st,
-                       cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
+                       double tol, int max_iter, int mode, cudaStream_t st,
+                       cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr, const double2* cdiag = nullptr);
+ss_status work_alloc_bicgstab(SolveWork& W, cudaStream_t st);
 ss_status read_stats(SolveWork& W, int n_inst, ss_solve_stats* stats, ss_status* worst, cudaStream_t st,
                      cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 

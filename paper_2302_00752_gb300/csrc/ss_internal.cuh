@@ -86,6 +86,7 @@ struct DevBuf {
 // ------------------------------------------------------------ constants
 
 constexpr double kTwoPiSq = 19.739208802178716;   // 2 pi^2 (half of the 4 pi^2 in eq. GF)
+constexpr double kTwoPi = 6.283185307179586;       // 2 pi (the advection factor 2 pi i of Remark ADR)
 constexpr uint64_t kEmpty = ~0ull;                // unused hash slot
 constexpr uint64_t kPending = 1ull << 63;         // slot claimed during the current level
 constexpr int kMaxWords = 16;                     // packed key words supported
@@ -136,6 +137,12 @@ struct ss_stamp_s {
   ss::DevBuf<double2> rec64;          // [2 * (rows_pad + 1)] (value, norm|pad) pairs
   // build state kept for stamp_extend
   int maxabs_f = 0, maxabs_a = 0;     // largest |coordinate| of F and of supp a_hat
+  // operator of Remark ADR (advection b.grad u and reaction c u added; not
+  // Hermitian; the zero frequency is an ordinary row and column)
+  bool adr = false;
+  ss::DevBuf<double2> bval;           // [s_a][d] b_hat_p per step (ADR)
+  ss::DevBuf<double2> cval;           // [s_a] c_hat_p per step (ADR)
+  ss::DevBuf<double2> diag64;         // [rows_pad + 1] diagonal of the operator (ADR; 1 on padding)
   ss::DevBuf<int32_t> err_dev;        // [4] device-side error words
   ss::DevBuf<int64_t> zidx_dev;       // canonical index of k = 0, or -1
 };
@@ -163,6 +170,10 @@ ss_status launch_pack64_prefix(const ss_stamp_s* s, const double2* u, int64_t n_
 ss_status launch_apply32(const ss_stamp_s* s, float2* y, cudaStream_t st);
 
 int sm_count();
+
+// Row replaced by the identity in the operator (the pinned zero frequency of
+// the diffusion problem), or -1 (none; the ADR operator keeps row 0).
+inline int64_t identity_row(const ss_stamp_s* s) { return s->adr ? -1 : s->zero_idx; }
 
 // Releases the solver workspace cached for a stamp (solve.cu).
 void drop_solve_ctx(const ss_stamp_s* s);

@@ -16,6 +16,7 @@
 // keys (up to 12 words at d = 100) only when the fingerprints agree.
 #include <algorithm>
 #include <cmath>
+#include <map>
 
 #include "keys.cuh"
 
@@ -152,7 +153,7 @@ __device__ bool table_insert_final(uint64_t* table, uint64_t capmask, const uint
 
 template <int WT>
 __global__ void k_level0(KeyParams P, const int32_t* __restrict__ F, int64_t n_f, uint64_t* keys, int8_t* level,
-                         int64_t* norm, uint64_t* table, uint64_t capmask, int32_t* err) {
+                         int64_t* norm, uint64_t* table, uint64_t capmask, int32_t* err, int64_t* zero_idx) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_f) return;
   uint64_t k[WT];
@@ -161,6 +162,7 @@ __global__ void k_level0(KeyParams P, const int32_t* __restrict__ F, int64_t n_f
   for (int w = 0; w < WT; ++w) keys[i * WT + w] = k[w];
   level[i] = 0;
   norm[i] = key_norm<WT>(k, P);
+  if (norm[i] == 0) *zero_idx = i;   // only when 0 is in F (allowed for the ADR operator)
   if (!table_insert_final<WT>(table, capmask, k, (uint64_t)i)) atomicExch(err, SS_ERR_HASH_FULL);
 }
 
@@ -269,14 +271,15 @@ __global__ void k_finalize(KeyParams P, uint64_t* keys, int64_t par0, int s_a, c
 }
 
 // Neighbour lookups: nbr[i*s_a + j] = index of k_i - p_j (= k_i + p_{s_a-1-j})
-// when it lies in S, is not 0, and k_i is not 0; else -1.
+// when it lies in S, is not 0, and k_i is not 0; else -1.  With keep_zero
+// (the ADR operator) the zero frequency is an ordinary row and column.
 template <int WT>
 __global__ void k_neighbors(KeyParams P, const uint64_t* __restrict__ keys, int64_t size, int s_a,
                             const uint64_t* __restrict__ stepkey, const uint64_t* __restrict__ table,
-                            uint64_t capmask, const int64_t* __restrict__ zero_dev, int32_t* nbr) {
+                            uint64_t capmask, const int64_t* __restrict__ zero_dev, bool keep_zero, int32_t* nbr) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= size * s_a) return;
-  const int64_t zero_idx = *zero_dev;
+  const int64_t zero_idx = keep_zero ? -1 : *zero_dev;
   const int64_t i = c / s_a;
   const int j = (int)(c - i * s_a);
   int32_t out = -1;
@@ -333,6 +336,62 @@ __global__ void k_fill_slices(const int32_t* __restrict__ nbr, int64_t size, int
         ecoef[e] = make_double2(sc * ca64[j].x, sc * ca64[j].y);
       }
     }
+  }
+  const uint32_t pad = (uint32_t)rows_pad | ((uint32_t)j0 << colbits);
+  for (; t < w; ++t) {
+    ent[base + (int64_t)t * kSlice] = pad;
+    ecoef[base + (int64_t)t * kSlice] = make_double2(0.0, 0.0);
+  }
+}
+
+// ADR entries (Remark ADR): for row k and neighbour l = k - p_j,
+//   4 pi^2 (k.l) a_hat_j + 2 pi i (l . b_hat_j) + c_hat_j,
+// with 4 pi^2 (k.l) a_hat_j = (|k|^2 + |l|^2 - |p_j|^2) * 2 pi^2 a_hat_j formed
+// exactly as for the diffusion operator and l . b_hat_j summed over the d
+// coordinates of l unpacked from its key.  The entry with l = k (p_j = 0) is
+// also the row's Jacobi diagonal.
+template <int WT>
+__global__ void k_fill_slices_adr(KeyParams P, const uint64_t* __restrict__ keys, const int32_t* __restrict__ nbr,
+                                  int64_t size, int64_t rows_pad, int s_a, int j0, const int32_t* __restrict__ woff,
+                                  int colbits, const int64_t* __restrict__ norm, const int64_t* __restrict__ pnorm,
+                                  const double2* __restrict__ ca64, const double2* __restrict__ bval,
+                                  const double2* __restrict__ cval, uint32_t* ent, double2* ecoef, double2* diag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > rows_pad) return;
+  if (i >= size) {
+    diag[i] = make_double2(1.0, 0.0);
+    if (i == rows_pad) return;
+  }
+  const int64_t s = i / kSlice;
+  const int lane = (int)(i % kSlice);
+  const int64_t base = (int64_t)woff[s] * kSlice + lane;
+  const int w = woff[s + 1] - woff[s];
+  int t = 0;
+  if (i < size) {
+    const int64_t nk = norm[i];
+    double2 dg = make_double2(1.0, 0.0);
+    for (int j = 0; j < s_a; ++j) {
+      const int32_t v = nbr[i * s_a + j];
+      if (v < 0) continue;
+      const int64_t e = base + (int64_t)t++ * kSlice;
+      ent[e] = (uint32_t)v | ((uint32_t)j << colbits);
+      const double sc = (double)(nk + norm[v] - pnorm[j]);
+      double br = 0.0, bi = 0.0;
+      const uint64_t* lk = keys + (int64_t)v * WT;
+      for (int c = 0; c < P.d; ++c) {
+        const double lc = (double)unpack_coord(lk, P, c);
+        const double2 b = bval[(int64_t)j * P.d + c];
+        br += lc * b.x;
+        bi += lc * b.y;
+      }
+      const double2 cj = cval[j];
+      // 2 pi i (br + i bi) = (-2 pi bi) + i (2 pi br)
+      const double2 cf = make_double2(sc * ca64[j].x - kTwoPi * bi + cj.x, sc * ca64[j].y + kTwoPi * br + cj.y);
+      ecoef[e] = cf;
+      if (j == j0) dg = cf;
+    }
+    if (dg.x == 0.0 && dg.y == 0.0) dg = make_double2(1.0, 0.0);
+    diag[i] = dg;
   }
   const uint32_t pad = (uint32_t)rows_pad | ((uint32_t)j0 << colbits);
   for (; t < w; ++t) {
@@ -520,7 +579,7 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   SS_CUDA(cudaMemsetAsync(slice_w.get(), 0, (S->n_slices + 1) * sizeof(int32_t), st));
   SS_DISPATCH_WT(S->key.WT, (k_neighbors<WT><<<nblk(S->size * s_a), 256, 0, st>>>(
                                 P, S->keys.get(), S->size, s_a, S->stepkey.get(), S->table.get(),
-                                (uint64_t)S->cap - 1, S->zidx_dev.get(), nbr.get())));
+                                (uint64_t)S->cap - 1, S->zidx_dev.get(), S->adr, nbr.get())));
   k_row_counts<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, slice_w.get(), d_nnz.get());
   SS_LAUNCH_CHECK();
   SS_TRY(S->slice_off.alloc(S->n_slices + 1, st));
@@ -535,9 +594,17 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   S->n_ent = total_w * kSlice;
   SS_TRY(S->ent.alloc(S->n_ent + 1, st));
   SS_TRY(S->ecoef64.alloc(S->n_ent + 1, st));
-  k_fill_slices<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, S->j0, S->slice_off.get(),
-                                                   colbits_of(S->jbits), S->norm.get(), S->pnorm.get(), S->ca64.get(),
-                                                   S->ent.get(), S->ecoef64.get());
+  if (S->adr) {
+    SS_TRY(S->diag64.alloc(S->rows_pad + 1, st));
+    SS_DISPATCH_WT(S->key.WT, (k_fill_slices_adr<WT><<<nblk(S->rows_pad + 1), 256, 0, st>>>(
+                                  P, S->keys.get(), nbr.get(), S->size, S->rows_pad, s_a, S->j0, S->slice_off.get(),
+                                  colbits_of(S->jbits), S->norm.get(), S->pnorm.get(), S->ca64.get(), S->bval.get(),
+                                  S->cval.get(), S->ent.get(), S->ecoef64.get(), S->diag64.get())));
+  } else {
+    k_fill_slices<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, S->j0,
+                                                     S->slice_off.get(), colbits_of(S->jbits), S->norm.get(),
+                                                     S->pnorm.get(), S->ca64.get(), S->ent.get(), S->ecoef64.get());
+  }
   SS_LAUNCH_CHECK();
   SS_TRY(S->rec32.alloc(S->rows_pad + 1, st));
   SS_TRY(S->rec64.alloc(2 * (S->rows_pad + 1), st));
@@ -553,6 +620,7 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   S->afreq.settle(); S->stepkey.settle(); S->pnorm.settle(); S->pn32.settle(); S->aval.settle();
   S->ca64.settle(); S->ca32.settle(); S->slice_off.settle(); S->ent.settle(); S->ecoef64.settle();
   S->rec32.settle(); S->rec64.settle(); S->err_dev.settle(); S->zidx_dev.settle();
+  S->bval.settle(); S->cval.settle(); S->diag64.settle();
   return SS_OK;
 }
 
@@ -622,7 +690,8 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   SS_CUDA(cudaStreamSynchronize(st));
   if (herr[1]) SS_FAIL(SS_ERR_INVALID, "stamp_build: duplicate frequencies in F");
   if (herr[2]) SS_FAIL(SS_ERR_INVALID, "stamp_build: duplicate frequencies in supp a_hat");
-  if (h.zero_in_f) SS_FAIL(SS_ERR_INVALID, "stamp_build: F contains k = 0 (f_hat_0 must vanish)");
+  // the ADR operator's reaction term makes u_hat_0 part of the solution, so f_hat_0 may be nonzero there
+  if (h.zero_in_f && !S->adr) SS_FAIL(SS_ERR_INVALID, "stamp_build: F contains k = 0 (f_hat_0 must vanish)");
   if (h.bad_sym) SS_FAIL(SS_ERR_INVALID, "stamp_build: supp a_hat must contain 0 and be closed under negation");
   if (h.bad_herm) SS_FAIL(SS_ERR_INVALID, "stamp_build: a_hat is not Hermitian (a must be real)");
   if (!(h.off_l1 < h.a0_abs)) SS_FAIL(SS_ERR_NOT_ELLIPTIC, "stamp_build: ||a_hat - a_hat_0||_1 = %g >= |a_hat_0| = %g",
@@ -665,7 +734,7 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   SS_TRY(grow_table(S, n_f, P, st, err));
   SS_DISPATCH_WT(L.WT, (k_level0<WT><<<nblk(n_f), 256, 0, st>>>(P, Fs.get(), n_f, S->keys.get(), S->level.get(),
                                                                 S->norm.get(), S->table.get(),
-                                                                (uint64_t)S->cap - 1, err)));
+                                                                (uint64_t)S->cap - 1, err, S->zidx_dev.get())));
   SS_LAUNCH_CHECK();
   S->size = n_f;
   S->level_start.push_back(n_f);
@@ -686,6 +755,7 @@ static void rebind(ss_stamp_s* S, cudaStream_t st) {
   S->ecoef64.s = st;
   S->rec32.s = st;
   S->rec64.s = st;
+  S->diag64.s = st;
 }
 
 static ss_status extend_impl(ss_stamp_s* S, int levels, cudaStream_t st) {
@@ -732,6 +802,125 @@ extern "C" ss_status stamp_build(const ss_sparse* a_hat, const int32_t* f_freq, 
     cudaStreamSynchronize(as_stream(stream));
     delete S;
     return s;
+  }
+  *out = S;
+  return SS_OK;
+}
+
+namespace {
+
+// Host copy of a device sparse list (small: supports of the data).
+ss_status host_sparse(const ss_sparse* g, int d, std::vector<int32_t>* f, std::vector<double2>* v,
+                      cudaStream_t st, const char* what) {
+  if (!g || g->d != d || g->n < 0 || (g->n > 0 && (!g->freq || !g->val)))
+    SS_FAIL(SS_ERR_INVALID, "stamp_build_adr: bad %s", what);
+  if (g->n > 4096) SS_FAIL(SS_ERR_INVALID, "stamp_build_adr: |supp %s| > 4096", what);
+  f->resize((size_t)g->n * d);
+  v->resize((size_t)g->n);
+  if (g->n > 0) {
+    SS_CUDA(cudaMemcpyAsync(f->data(), g->freq, f->size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SS_CUDA(cudaMemcpyAsync(v->data(), g->val, v->size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  }
+  return SS_OK;
+}
+
+// Hermitian: -k present with the conjugate value (a real function).
+bool hermitian(const std::map<std::vector<int32_t>, double2>& m) {
+  for (const auto& [k, v] : m) {
+    std::vector<int32_t> nk(k.size());
+    for (size_t c = 0; c < k.size(); ++c) nk[c] = -k[c];
+    auto it = m.find(nk);
+    if (it == m.end()) return false;
+    const double sc = 1e-12 * std::max(1.0, std::hypot(v.x, v.y));
+    if (std::fabs(it->second.x - v.x) > sc || std::fabs(it->second.y + v.y) > sc) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" ss_status stamp_build_adr(const ss_sparse* a_hat, const ss_sparse* b_hat, const ss_sparse* c_hat,
+                                     const int32_t* f_freq, int64_t n_f, int32_t N, ss_stamp* out, void* stream) {
+  if (!a_hat || !b_hat || !c_hat || !out || !f_freq) SS_FAIL(SS_ERR_INVALID, "stamp_build_adr: null argument");
+  const int d = a_hat->d;
+  if (d < 1 || d > 64 || n_f < 1 || N < 0 || N > 120)
+    SS_FAIL(SS_ERR_INVALID, "stamp_build_adr: need 1 <= d <= 64, |F| >= 1, 0 <= N <= 120");
+  *out = nullptr;
+  cudaStream_t st = as_stream(stream);
+  // gather a_hat, the d components of b_hat and c_hat on the host
+  std::vector<int32_t> fa, fc;
+  std::vector<double2> va, vc;
+  std::vector<std::vector<int32_t>> fb(d);
+  std::vector<std::vector<double2>> vb(d);
+  SS_TRY(host_sparse(a_hat, d, &fa, &va, st, "a_hat"));
+  for (int j = 0; j < d; ++j) SS_TRY(host_sparse(b_hat + j, d, &fb[j], &vb[j], st, "b_hat"));
+  SS_TRY(host_sparse(c_hat, d, &fc, &vc, st, "c_hat"));
+  SS_CUDA(cudaStreamSynchronize(st));
+  // union U of the supports in signed lexicographic order (std::map orders
+  // int vectors lexicographically), with every coefficient on U
+  struct Coef {
+    double2 a{0.0, 0.0}, c{0.0, 0.0};
+    std::vector<double2> b;
+  };
+  std::map<std::vector<int32_t>, Coef> U;
+  std::map<std::vector<int32_t>, double2> ma, mc;
+  std::vector<std::map<std::vector<int32_t>, double2>> mb(d);
+  auto add = [&](const std::vector<int32_t>& f, const std::vector<double2>& v, std::map<std::vector<int32_t>, double2>* m,
+                 int which) -> bool {
+    for (size_t t = 0; t < v.size(); ++t) {
+      std::vector<int32_t> k(f.begin() + t * d, f.begin() + (t + 1) * d);
+      if (m->count(k)) return false;
+      (*m)[k] = v[t];
+      Coef& e = U[k];
+      if (e.b.empty()) e.b.assign(d, double2{0.0, 0.0});
+      if (which < 0) e.a = v[t];
+      else if (which == d) e.c = v[t];
+      else e.b[which] = v[t];
+    }
+    return true;
+  };
+  if (!add(fa, va, &ma, -1)) SS_FAIL(SS_ERR_INVALID, "stamp_build_adr: duplicate frequencies in a_hat");
+  for (int j = 0; j < d; ++j)
+    if (!add(fb[j], vb[j], &mb[j], j)) SS_FAIL(SS_ERR_INVALID, "stamp_build_adr: duplicate frequencies in b_hat");
+  if (!add(fc, vc, &mc, d)) SS_FAIL(SS_ERR_INVALID, "stamp_build_adr: duplicate frequencies in c_hat");
+  bool herm = hermitian(ma) && hermitian(mc);
+  for (int j = 0; j < d; ++j) herm = herm && hermitian(mb[j]);
+  if (!herm) SS_FAIL(SS_ERR_INVALID, "stamp_build_adr: a_hat, b_hat and c_hat must be Hermitian (real data)");
+  if ((int64_t)U.size() > 4096) SS_FAIL(SS_ERR_INVALID, "stamp_build_adr: union of the supports > 4096");
+  const int64_t s_u = (int64_t)U.size();
+  std::vector<int32_t> uf((size_t)s_u * d);
+  std::vector<double2> ua(s_u), uc(s_u), ub((size_t)s_u * d);
+  int64_t t = 0;
+  for (const auto& [k, e] : U) {
+    std::copy(k.begin(), k.end(), uf.begin() + t * d);
+    ua[t] = e.a;
+    uc[t] = e.c;
+    std::copy(e.b.begin(), e.b.end(), ub.begin() + t * d);
+    ++t;
+  }
+  ss_stamp_s* S = new ss_stamp_s();
+  S->adr = true;
+  DevBuf<int32_t> dU;
+  DevBuf<double2> dA;
+  ss_status r = SS_OK;
+  auto up = [&]() -> ss_status {
+    SS_TRY(dU.alloc(uf.size(), st));
+    SS_TRY(dA.alloc(ua.size(), st));
+    SS_TRY(S->bval.alloc(ub.size(), st));
+    SS_TRY(S->cval.alloc(uc.size(), st));
+    SS_CUDA(cudaMemcpyAsync(dU.get(), uf.data(), uf.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    SS_CUDA(cudaMemcpyAsync(dA.get(), ua.data(), ua.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    SS_CUDA(cudaMemcpyAsync(S->bval.get(), ub.data(), ub.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    SS_CUDA(cudaMemcpyAsync(S->cval.get(), uc.data(), uc.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    const ss_sparse au{d, s_u, dU.get(), reinterpret_cast<const double*>(dA.get())};
+    // U is already in canonical step order, so the build keeps bval / cval aligned
+    return build_impl(S, &au, f_freq, n_f, N, st);
+  };
+  r = up();
+  if (r != SS_OK) {
+    cudaStreamSynchronize(st);
+    delete S;
+    return r;
   }
   *out = S;
   return SS_OK;
