@@ -577,8 +577,10 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
 // with <a, b> = sum conj(a) b.  Five phases per iteration, each closed by a
 // grid barrier; every block recomputes the scalars from the deterministic
 // partial sums, and the owner keeps rho, alpha and omega by iteration parity.
-// A vanishing denominator restarts the direction (beta = 0) or skips the
-// step (alpha or omega = 0); the iteration cap then reports non-convergence.
+// The half step stops the iteration when |s| already meets the tolerance
+// (x = x + alpha y is then the answer).  A vanishing or non-finite scalar
+// restarts the direction (beta = 0) or skips the step (alpha or omega = 0);
+// the iteration cap then reports non-convergence.
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -587,6 +589,9 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
   const double n = b.x * b.x + b.y * b.y;
   if (n == 0.0) return make_double2(0.0, 0.0);
   return make_double2((a.x * b.x + a.y * b.y) / n, (a.y * b.x - a.x * b.y) / n);
+}
+__device__ __forceinline__ double2 finite_or_zero(double2 a) {
+  return (isfinite(a.x) && isfinite(a.y)) ? a : make_double2(0.0, 0.0);
 }
 // conj(a) b
 __device__ __forceinline__ double2 cdot(double2 a, double2 b) {
@@ -619,7 +624,8 @@ __device__ void solve_bicgstab(const SolveParams& P, Smem& sm) {
       inst_sums(P, i, t);
       if (lane == 0) {
         InstState& st = P.state[i];
-        const int act = it == 0 ? 1 : __ldcg(&st.act[cur]);
+        // inn[par]: the instance finished at the half step of that iteration
+        const int act = it == 0 ? 1 : (__ldcg(&st.act[cur]) && !__ldcg(&st.inn[cur]));
         const double bb = it == 0 ? t[3] : __ldcg(&st.bb);
         const bool conv = t[2] <= tol2 * bb;
         const bool cap = it >= P.max_iter;
@@ -628,7 +634,7 @@ __device__ void solve_bicgstab(const SolveParams& P, Smem& sm) {
         double2 beta = make_double2(0.0, 0.0), om = make_double2(0.0, 0.0);
         if (it > 0) {
           om = __ldcg(&st.zomega[cur]);
-          beta = cmul(cdiv(rho, __ldcg(&st.zrho[cur])), cdiv(__ldcg(&st.zalpha[cur]), om));
+          beta = finite_or_zero(cmul(cdiv(rho, __ldcg(&st.zrho[cur])), cdiv(__ldcg(&st.zalpha[cur]), om)));
         }
         sm.flag[k] = go;
         sm.ca[k] = beta.x;
@@ -677,19 +683,19 @@ __device__ void solve_bicgstab(const SolveParams& P, Smem& sm) {
       v[1] = q.y;
     });
     if (!grid_sync(P)) return;
-    // C: alpha = rho / <r^, v>; s = r - alpha v; x += alpha y; z = D^-1 s
-    run_phase(P, sm, 0u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
+    // C: alpha = rho / <r^, v>; s = r - alpha v; x += alpha y; z = D^-1 s;  |s|^2
+    run_phase(P, sm, 0b0100u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
       double t[kNQ];
       inst_sums(P, i, t);
       if (lane == 0) {
         InstState& st = P.state[i];
-        const double2 alpha = cdiv(__ldcg(&st.zrho[nxt]), make_double2(t[0], t[1]));
+        const double2 alpha = finite_or_zero(cdiv(__ldcg(&st.zrho[nxt]), make_double2(t[0], t[1])));
         sm.flag[k] = __ldcg(&st.act[nxt]);
         sm.ca[k] = alpha.x;
         sm.cb[k] = alpha.y;
         if (owner) st.zalpha[nxt] = alpha;
       }
-    }, [&](int64_t g, int64_t, int, int, int k, double*) {
+    }, [&](int64_t g, int64_t, int, int, int k, double* vq) {
       if (!sm.flag[k]) return;
       const double2 alpha = make_double2(sm.ca[k], sm.cb[k]);
       const double2 r = P.r[g], v = P.w64[g], y = P.urec64[2 * g];
@@ -701,13 +707,28 @@ __device__ void solve_bicgstab(const SolveParams& P, Smem& sm) {
       P.xrec[2 * g] = x;
       P.sd[g] = s;
       P.zrec[2 * g] = cmul(P.dlt[g], s);
+      vq[2] = s.x * s.x + s.y * s.y;
     });
     if (!grid_sync(P)) return;
-    // D: t = L z;  <t, s>, <t, t>
+    // D: half-step test on |s|; t = L z;  <t, s>, <t, t>
     run_phase(P, sm, 0b0111u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
+      double t[kNQ];
+      inst_sums(P, i, t);
       if (lane == 0) {
-        sm.flag[k] = __ldcg(&P.state[i].act[nxt]);
-        if (owner && sm.flag[k]) P.state[i].applies += 1;
+        InstState& st = P.state[i];
+        const int act = __ldcg(&st.act[nxt]);
+        const bool half = act && t[2] <= tol2 * __ldcg(&st.bb);
+        sm.flag[k] = act && !half;
+        if (owner) {
+          st.inn[nxt] = half;
+          if (half) {
+            st.rr = t[2];
+            st.iters = it + 1;
+            owner_done(P, st, SS_OK);
+          } else if (act) {
+            st.applies += 1;
+          }
+        }
       }
     }, [&](int64_t g, int64_t s, int lane, int i, int k, double* v) {
       if (!sm.flag[k]) return;
@@ -725,8 +746,9 @@ __device__ void solve_bicgstab(const SolveParams& P, Smem& sm) {
       inst_sums(P, i, t);
       if (lane == 0) {
         InstState& st = P.state[i];
-        const double2 om = t[2] > 0.0 ? make_double2(t[0] / t[2], t[1] / t[2]) : make_double2(0.0, 0.0);
-        sm.flag[k] = __ldcg(&st.act[nxt]);
+        const double2 om =
+            finite_or_zero(t[2] > 0.0 ? make_double2(t[0] / t[2], t[1] / t[2]) : make_double2(0.0, 0.0));
+        sm.flag[k] = __ldcg(&st.act[nxt]) && !__ldcg(&st.inn[nxt]);
         sm.ca[k] = om.x;
         sm.cb[k] = om.y;
         if (owner) st.zomega[nxt] = om;
