@@ -201,6 +201,16 @@ def count_launches(fn):
         return None
 
 
+def load_peaks():
+    """The measured copy bandwidth and GEMM peaks of this GPU type, when present."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
 def fp64_peak_gflops(sm_mhz):
     """FP64 ALU peak: one FP64 FMA per SM clock (GB300; the per-SM rate comes
     from the ncu FP64-pipe counters of k_sample<double>) x 152
@@ -258,6 +268,102 @@ def d100_section(B, gp, flush, steps=2):
     out["apply_fp32"] = {"ms": ms, "nnz_per_s": stamp.nnz / (ms / 1e3),
                          "note": "standalone galerkin_apply (pack + operator), L2-warm back-to-back"}
     stamp.destroy()
+    return out
+
+
+def apply_section(B, gp, flush, peaks, reps=10):
+    """galerkin_apply alone (pack of u into gather records + the operator), L2
+    flushed before every call, on the d = 100 set (FP32 operator) and the
+    d = 10 set (FP64 and FP32).  Algorithmic HBM bytes per call: the index
+    stream (4 B per nonzero) plus, per row, u read, |k|^2 read and y written
+    (FP32: 8 + 8 + 8 B; FP64 also reads the 16 B entry coefficient per
+    nonzero and moves 16 B values).  FP64 is also given as FP64 flops (four
+    FMAs per nonzero) against the FP64 ALU peak."""
+    import torch
+    out = {}
+    hbm = peaks.get("hbm_gbs", 6783.5)
+    for name, inst, precs in (("cfg5", W.make_cfg5(), ("fp32",)), ("cfg2", W.make_cfg2(), ("fp64", "fp32"))):
+        p = gp.prepare(inst)
+        r = gp.run(p, solve=False)
+        st = r.stamp
+        res = {"size": st.size, "nnz": st.nnz}
+        for prec in precs:
+            dt = torch.complex64 if prec == "fp32" else torch.complex128
+            x = torch.randn(st.size, dtype=dt, device="cuda")
+            y = B.galerkin_apply(st, x, prec)
+            for _ in range(3):
+                B.galerkin_apply(st, x, prec)
+            # everything is queued before the first wait, so the host never
+            # holds the GPU back: each apply starts right after its flush
+            evs = []
+            for _ in range(reps):
+                flush.zero_()
+                flush.sum()        # evicts the flush's dirty lines outside the timed region
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                B.galerkin_apply(st, x, prec)
+                b.record()
+                evs.append((a, b))
+            torch.cuda.synchronize()
+            ms = statistics.median([a.elapsed_time(b) for a, b in evs])
+            if prec == "fp32":
+                byts = 4 * st.nnz + st.size * (8 + 8 + 8)
+            else:
+                byts = (4 + 16) * st.nnz + st.size * (16 + 8 + 16)
+            d = {"ms": ms, "nnz_per_s": st.nnz / (ms / 1e3), "algorithmic_bytes": byts,
+                 "achieved_gbs": byts / (ms / 1e3) / 1e9, "hbm_frac": byts / (ms / 1e3) / 1e9 / hbm}
+            if prec == "fp64":
+                d["fp64_gflops"] = 8.0 * st.nnz / (ms / 1e3) / 1e9
+            res[prec] = d
+        st.destroy()
+        out[name] = res
+    out["note"] = ("CUDA events around one galerkin_apply call (two kernels) after a 512 MB L2 flush (write, "
+                   "then read so that no dirty line is written back inside the timed call), all calls queued "
+                   "before the first wait; fraction of the measured HBM copy bandwidth")
+    return out
+
+
+def adr_section(B, gp, flush, Q=1000):
+    """The three-dimensional advection-diffusion-reaction data (Remark ADR,
+    Section "Three-dimensional exactly sparse advection-diffusion-reaction
+    equation"): 45 operator terms, 5 forcing terms, frequencies in
+    [-49, 50]^3, N = 1 and 2.  Whole pipeline (lattice, 6 SFTs, union stamp,
+    BiCGStab), then the exact and Monte Carlo proxy on S^{N+1}."""
+    import torch
+    out = {}
+    for N in (1, 2):
+        inst = W.make_adr(0, N=N)
+        for it in range(2):   # the first pass warms up
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            res = gp.run_adr(inst)
+            b.record()
+            b.synchronize()
+            if it == 0:
+                res.stamp.destroy()
+        st = res.stamp
+        d = {"size": st.size, "nnz": st.nnz, "pipeline_ms": a.elapsed_time(b),
+             "solve_kernel_ms": res.stats["kernel_ms"], "iterations": res.stats["inner_iters"],
+             "applies": res.stats["applies"], "rel_residual": res.stats["rel_residual"],
+             "status": res.stats["status"]}
+        X = W.mc_points(0, Q, inst.d)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record()
+        st.extend(1)
+        e[1].record()
+        f1, _ = st.scatter(res.f_freq, res.f_val)
+        num, den = B.proxy_residual(st, res.u, f1)
+        e[2].record()
+        r, fx = B.proxy_mc(st, res.u, inst.f.freq, inst.f.coef, X)
+        e[3].record()
+        e[3].synchronize()
+        d.update({"size_N_plus_1": st.size, "extend_ms": e[0].elapsed_time(e[1]),
+                  "exact_proxy": float(np.sqrt(num / den)), "exact_proxy_ms": e[1].elapsed_time(e[2]),
+                  "mc_proxy": float(torch.sqrt((r * r).sum() / (fx * fx).sum())), "mc_points": Q,
+                  "mc_ms": e[2].elapsed_time(e[3])})
+        st.destroy()
+        out[f"N{N}"] = d
     return out
 
 
@@ -532,6 +638,14 @@ def main():
                 extra["d100"] = d100_section(B, gp, flush)
             except Exception as e:  # reported, not hidden
                 extra["d100"] = {"error": repr(e)}
+            try:
+                extra["apply"] = apply_section(B, gp, flush, load_peaks())
+            except Exception as e:
+                extra["apply"] = {"error": repr(e)}
+            try:
+                extra["adr"] = adr_section(B, gp, flush)
+            except Exception as e:
+                extra["adr"] = {"error": repr(e)}
             try:
                 extra["proxy"] = proxy_section(B, gp, flush)
             except Exception as e:

@@ -14,11 +14,20 @@ __global__ void k_pack64(const double2* __restrict__ u, int64_t size, double2* r
   if (i < size) rec[2 * i] = u[i];
 }
 
+// Four rows per thread, loads issued before stores (one DRAM round trip).
 __global__ void k_pack32(const float2* __restrict__ u, int64_t size, float4* rec) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < size) {
-    const float2 v = u[i];
-    reinterpret_cast<float2*>(rec + i)[0] = v;
+  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  float2 v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t i = i0 + q * stride;
+    v[q] = i < size ? __ldg(u + i) : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t i = i0 + q * stride;
+    if (i < size) reinterpret_cast<float2*>(rec + i)[0] = v[q];
   }
 }
 
@@ -56,7 +65,7 @@ __global__ void __launch_bounds__(256) k_apply32(OpView op, int64_t size, int64_
   if (row >= rows_pad) return;
   const int64_t s = row / kSlice;
   const int lane = (int)(row % kSlice);
-  float2 acc = row_apply32(op, s, lane, __ldg(norm + row), wide, rec, s_ca, s_pn);
+  float2 acc = row_apply32<false, 8>(op, s, lane, __ldg(norm + row), wide, rec, s_ca, s_pn);
   if (row == zero_idx) {
     const float4 r = rec[row];
     acc = make_float2(r.x, r.y);
@@ -128,7 +137,7 @@ ss_status launch_pack64(const ss_stamp_s* s, const double2* u, cudaStream_t st) 
 }
 
 ss_status launch_pack32(const ss_stamp_s* s, const float2* u, cudaStream_t st) {
-  k_pack32<<<nblk(s->size), 256, 0, st>>>(u, s->size, s->rec32.get());
+  k_pack32<<<nblk((s->size + 3) / 4), 256, 0, st>>>(u, s->size, s->rec32.get());
   SS_LAUNCH_CHECK();
   return SS_OK;
 }

@@ -82,51 +82,45 @@ __device__ __forceinline__ float entry_scale(int32_t nk, float rec_z, int32_t pn
   else return (float)(nk + __float_as_int(rec_z) - pnj);
 }
 
-template <bool CG, bool WIDE>
+// U index words per lane are loaded before their U gathers are issued, so a
+// row of width <= U costs one index round trip and one gather round trip.
+template <bool CG, bool WIDE, int U>
 __device__ __forceinline__ float2 row_apply32_t(const OpView& op, int64_t s, int lane, int32_t nk,
                                                 const float4* __restrict__ rec, const float2* ca,
                                                 const int32_t* pn) {
   const int32_t w0 = __ldg(op.woff + s), w1 = __ldg(op.woff + s + 1);
   const uint32_t* e = op.ent + (int64_t)w0 * kSlice + lane;
   float ar = 0.f, ai = 0.f;
-  int t = 0;
   const int w = w1 - w0;
-  for (; t + 4 <= w; t += 4) {
-    uint32_t ee[4];
-    float4 v[4];
+  for (int t = 0; t < w; t += U) {
+    uint32_t ee[U];
+    float4 v[U];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) ee[q] = __ldg(e + (int64_t)(t + q) * kSlice);
+    for (int q = 0; q < U; ++q) ee[q] = t + q < w ? __ldg(e + (int64_t)(t + q) * kSlice) : 0u;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = ldv<CG>(rec + (ee[q] & op.colmask));
+    for (int q = 0; q < U; ++q)
+      v[q] = t + q < w ? ldv<CG>(rec + (ee[q] & op.colmask)) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = (int)(ee[q] >> op.colbits);
-      const float sc = entry_scale<WIDE>(nk, v[q].z, pn[j]);
-      const float2 a = ca[j];
-      const float tr = sc * a.x, ti = sc * a.y;
-      ar = fmaf(tr, v[q].x, ar); ar = fmaf(-ti, v[q].y, ar);
-      ai = fmaf(tr, v[q].y, ai); ai = fmaf(ti, v[q].x, ai);
+    for (int q = 0; q < U; ++q) {
+      if (t + q < w) {
+        const int j = (int)(ee[q] >> op.colbits);
+        const float sc = entry_scale<WIDE>(nk, v[q].z, pn[j]);
+        const float2 a = ca[j];
+        const float tr = sc * a.x, ti = sc * a.y;
+        ar = fmaf(tr, v[q].x, ar); ar = fmaf(-ti, v[q].y, ar);
+        ai = fmaf(tr, v[q].y, ai); ai = fmaf(ti, v[q].x, ai);
+      }
     }
-  }
-  for (; t < w; ++t) {
-    const uint32_t ee = __ldg(e + (int64_t)t * kSlice);
-    const float4 v = ldv<CG>(rec + (ee & op.colmask));
-    const int j = (int)(ee >> op.colbits);
-    const float sc = entry_scale<WIDE>(nk, v.z, pn[j]);
-    const float2 a = ca[j];
-    const float tr = sc * a.x, ti = sc * a.y;
-    ar = fmaf(tr, v.x, ar); ar = fmaf(-ti, v.y, ar);
-    ai = fmaf(tr, v.y, ai); ai = fmaf(ti, v.x, ai);
   }
   return make_float2(ar, ai);
 }
 
-template <bool CG = false>
+template <bool CG = false, int U = 4>
 __device__ __forceinline__ float2 row_apply32(const OpView& op, int64_t s, int lane, int64_t nk, bool wide,
                                               const float4* __restrict__ rec, const float2* ca,
                                               const int32_t* pn) {
-  return wide ? row_apply32_t<CG, true>(op, s, lane, norm_word(nk, true), rec, ca, pn)
-              : row_apply32_t<CG, false>(op, s, lane, norm_word(nk, false), rec, ca, pn);
+  return wide ? row_apply32_t<CG, true, U>(op, s, lane, norm_word(nk, true), rec, ca, pn)
+              : row_apply32_t<CG, false, U>(op, s, lane, norm_word(nk, false), rec, ca, pn);
 }
 
 }  // namespace ss

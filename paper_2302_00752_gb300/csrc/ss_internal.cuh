@@ -129,7 +129,7 @@ struct ss_stamp_s {
   ss::DevBuf<double2> ca64;           // [s_a] 2 pi^2 a_hat_j
   ss::DevBuf<float2> ca32;            // [s_a] same in FP32
   // neighbour table, sliced ELL with 32-row slices, column-major in a slice
-  ss::DevBuf<int32_t> slice_off;      // [n_slices + 1], in entries (multiple of 32)
+  ss::DevBuf<int32_t> slice_off;      // [n_slices + 1], in units of 32 entries (one per row of a slice)
   ss::DevBuf<uint32_t> ent;           // [n_ent] col | (j << colbits)
   ss::DevBuf<double2> ecoef64;        // [n_ent] 2 pi^2 (|k|^2 + |l|^2 - |p_j|^2) a_hat_j per entry (FP64 operator)
   // scratch for galerkin_apply

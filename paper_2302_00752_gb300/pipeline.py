@@ -136,3 +136,19 @@ def proxy_errors(res: Result, p: Prepared, X=None):
         r, fx = B.proxy_mc(res.stamp, res.u.to(torch.complex128), p.f_freq, p.f_coef, X)
         out["mc"] = float(torch.sqrt((r * r).sum() / (fx * fx).sum()))
     return out
+
+
+def run_adr(inst, tol=1e-12, max_iter=2000, tau=1e-9):
+    """Algorithm 1 with the modifications of Remark ADR: one reconstructing
+    lattice for the union of the data's supports, sft_recover of a, of every
+    component of b, of c and of f, stamp_build_adr (union step set) and the
+    FP64 BiCGStab solve."""
+    funcs = [inst.a, *inst.b, inst.c, inst.f]
+    cand = np.unique(np.vstack([support_of(g.freq) for g in funcs]), axis=0)
+    z, M = choose_lattice(inst.lattice, cand)
+    rec = [B.sft_recover(z, M, g.freq, g.coef, cand, tau=tau) for g in funcs]
+    a, c, f = rec[0], rec[-2], rec[-1]
+    stamp = B.stamp_build_adr(a[0], a[1], rec[1:-2], c[0], c[1], f[0], inst.N)
+    f_on, _ = stamp.scatter(*f)
+    u, stats = B.solve(stamp, f_on, tol, max_iter, "fp64")
+    return Result(z, M, a[0], a[1], f[0], f[1], stamp, f_on, u, stats)

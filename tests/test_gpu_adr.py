@@ -167,3 +167,43 @@ def test_paths_without_adr_support_refuse(B):
         # and the stamp is still usable
         u, st = B.solve(s, f_on, 1e-12, 2000, "fp64")
         assert st["status"] == "SS_OK"
+
+
+def test_pipeline_recovers_and_solves(B):
+    # Remark ADR's pipeline: lattice for the union of the supports, SFT of
+    # a, b_1..b_d, c and f, union stamp, BiCGStab; against the oracle's direct
+    # solve on the exact coefficients
+    from paper_2302_00752_gb300 import pipeline as gp
+    inst = W.make_adr(13, N=1)
+    a, b, c, f = data(inst)
+    res = gp.run_adr(inst)
+    try:
+        S = res.stamp.export()[0].cpu().numpy()
+        U, _, _, _ = oadr.coefficient_maps(a, b, c)
+        S_ref, _ = ostamp.stamp_bfs(U, f[0], 1)
+        assert np.array_equal(S, S_ref)
+        u_ref, _ = oadr.solve(S, a, b, c, *f)
+        assert res.stats["status"] == "SS_OK"
+        assert rel_l2(res.u.cpu().numpy(), u_ref) < 1e-10
+    finally:
+        res.stamp.destroy()
+
+
+def test_monte_carlo_proxy_matches_oracle(B):
+    from oracle import galerkin as ogal
+    inst = W.make_adr(14, N=1, **SMALL)
+    a, b, c, f = data(inst)
+    U, _, _, _ = oadr.coefficient_maps(a, b, c)
+    S, _ = ostamp.stamp_bfs(U, f[0], 1)
+    rng = np.random.default_rng(14)
+    u = rng.standard_normal(len(S)) + 1j * rng.standard_normal(len(S))
+    X = W.mc_points(5, 300, 3)
+    with build(B, a, b, c, f, 1) as s:
+        s.extend(1)
+        r, fx = B.proxy_mc(s, torch.as_tensor(u), inst.f.freq, inst.f.coef, X)
+    gf, gv = oadr.convolve(a, b, c, S, u)
+    f_ref = ogal.trig_at(inst.f.freq, inst.f.coef, X)
+    r_ref = f_ref - ogal.trig_at(gf, gv, X)
+    tol = 1e-12 * (np.abs(gv).sum() + np.abs(inst.f.coef).sum())
+    assert np.max(np.abs(fx.cpu().numpy() - f_ref)) <= tol
+    assert np.max(np.abs(r.cpu().numpy() - r_ref)) <= tol

@@ -299,6 +299,7 @@ class AdrInstance:
     u_freq: np.ndarray | None = None
     u_val: np.ndarray | None = None
     seed: tuple = ()
+    lattice: dict = field(default_factory=dict)
 
 
 def _sin_cos(rng, n_sin, n_cos, d, lo, hi, amp_lo, amp_hi):
@@ -331,9 +332,10 @@ def make_adr(seed=0, N=1, d=3, kmax=50, n_a=2, n_bc=5, n_f=(2, 3), manufactured_
     if manufactured_u:
         qs, _ = draw_freqs(rng, manufactured_u, d, lo, hi)
         uf, uv = manufactured(rng, qs)
-        return AdrInstance(f"adr_d{d}_N{N}_u", d, N, a, b, c, None, uf, uv, (seed,))
+        return AdrInstance(f"adr_d{d}_N{N}_u", d, N, a, b, c, None, uf, uv, (seed,), random_lattice_draws(rng, d))
     ff, cf, _ = _sin_cos(rng, n_f[0], n_f[1], d, lo, hi, -1.0, 1.0)
-    return AdrInstance(f"adr_d{d}_N{N}", d, N, a, b, c, TrigSum(ff.astype(np.int32), cf), None, None, (seed,))
+    return AdrInstance(f"adr_d{d}_N{N}", d, N, a, b, c, TrigSum(ff.astype(np.int32), cf), None, None, (seed,),
+                       random_lattice_draws(rng, d))
 
 
 def make_tiny(seed=0, d=2, n_cos=2, n_u=2, N=2, box=3, ubox=4, manufactured_u=True):
