@@ -572,7 +572,7 @@ def main():
     for k, v in zip(inst.u_freq.tolist(), inst.u_val):
         exact[idx[tuple(k)]] = v
     tts = {}
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "fp32", "df64"):
         times, kern = [], []
         for _ in range(5):
             flush.zero_()

@@ -53,7 +53,9 @@ typedef enum {
 
 typedef enum {
     SS_FP64 = 0,   /* FP64 samples and FFT; FP64 operator; plain FP64 CG */
-    SS_FP32 = 1    /* FP32 samples and FFT; FP32 operator; FP32 CG inside FP64 iterative refinement */
+    SS_FP32 = 1,   /* FP32 samples and FFT; FP32 operator; FP32 CG inside FP64 iterative refinement */
+    SS_DF64 = 2    /* solve only: the FP64 CG in double-float arithmetic (float pairs, ~2^-48 relative per
+                      operation) on the FP32 pipes, FP64 scalars and final residual */
 } ss_precision;
 
 /* Rank-1 lattice Lambda(z, M) = { (j z / M) mod 1 : j < M } (Section "Previous

@@ -16,7 +16,7 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsparse_spectral.so")
 
-SS_FP64, SS_FP32 = 0, 1
+SS_FP64, SS_FP32, SS_DF64 = 0, 1, 2
 STATUS = {0: "SS_OK", 1: "SS_ERR_INVALID", 2: "SS_ERR_OOM", 3: "SS_ERR_CUDA", 4: "SS_ERR_NOT_RECONSTRUCTING",
           5: "SS_ERR_HASH_FULL", 6: "SS_ERR_NOT_ELLIPTIC", 7: "SS_ERR_NOT_CONVERGED", 8: "SS_ERR_TIMEOUT",
           9: "SS_ERR_KEY_RANGE"}
@@ -138,6 +138,8 @@ def _prec(p):
         return SS_FP64
     if p in (SS_FP32, "fp32", "float32", "fp32_refined"):
         return SS_FP32
+    if p in (SS_DF64, "df64"):
+        return SS_DF64
     raise ValueError(f"unknown precision {p!r}")
 
 

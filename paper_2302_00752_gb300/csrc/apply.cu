@@ -118,13 +118,32 @@ __global__ void k_sum_partials(const double2* __restrict__ part, int n, double2*
   *out = s;
 }
 
+__global__ void k_ecoef_df(const double2* __restrict__ in, int64_t n, float4* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 c = in[i];
+  out[i] = cdf(df_split(c.x), df_split(c.y));
+}
+
 }  // namespace
+
+ss_status ensure_ecoefdf(ss_stamp_s* s, cudaStream_t st) {
+  if (s->ecoefdf.get()) return SS_OK;
+  const int64_t n = s->n_ent + 1;
+  SS_TRY(s->ecoefdf.alloc(n, st));
+  k_ecoef_df<<<nblk(n), 256, 0, st>>>(s->ecoef64.get(), n, s->ecoefdf.get());
+  SS_LAUNCH_CHECK();
+  SS_CUDA(cudaStreamSynchronize(st));
+  s->ecoefdf.settle();
+  return SS_OK;
+}
 
 OpView op_view(const ss_stamp_s* s) {
   OpView op;
   op.woff = s->slice_off.get();
   op.ent = s->ent.get();
   op.ecoef = s->ecoef64.get();
+  op.ecoefdf = s->ecoefdf.get();
   op.colbits = colbits_of(s->jbits);
   op.colmask = colmask_of(s->jbits);
   return op;

@@ -14,6 +14,7 @@
 // so one 16- or 32-byte sector brings both the value and the norm.
 #pragma once
 
+#include "df.cuh"
 #include "ss_internal.cuh"
 
 namespace ss {
@@ -30,6 +31,7 @@ struct OpView {
   const int32_t* woff;     // slice offsets in units of 32 entries
   const uint32_t* ent;     // col | (j << colbits)
   const double2* ecoef;    // FP64 coefficient of every entry
+  const float4* ecoefdf;   // the same as double-float (re.hi, re.lo, im.hi, im.lo), or null
   int colbits;
   uint32_t colmask;
 };
@@ -71,6 +73,48 @@ __device__ __forceinline__ double2 row_apply64(const OpView& op, int64_t s, int 
     ai = fma(c.x, v.y, ai); ai = fma(c.y, v.x, ai);
   }
   return make_double2(ar, ai);
+}
+
+// Same in double-float (DF64 mode): the FP64 entry coefficient and u_l as
+// unevaluated float pairs, four double-float multiply-adds per nonzero on the
+// FP32 pipe (about 2^-48 relative per operation).  rec: float4 per column.
+template <bool CG = false>
+__device__ __forceinline__ float4 row_applydf(const OpView& op, int64_t s, int lane, const float4* __restrict__ rec) {
+  const int32_t w0 = __ldg(op.woff + s), w1 = __ldg(op.woff + s + 1);
+  const int64_t base = (int64_t)w0 * kSlice + lane;
+  const uint32_t* e = op.ent + base;
+  const float4* cf = op.ecoefdf + base;
+  DF ar{0.f, 0.f}, ai{0.f, 0.f};
+  int t = 0;
+  const int w = w1 - w0;
+  for (; t + 4 <= w; t += 4) {
+    uint32_t ee[4];
+    float4 c[4], v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ee[q] = __ldg(e + (int64_t)(t + q) * kSlice);
+      c[q] = __ldg(cf + (int64_t)(t + q) * kSlice);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = ldv<CG>(rec + (ee[q] & op.colmask));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      df_fma(ar, re_of(c[q]), re_of(v[q]));
+      df_fma(ar, df_neg(im_of(c[q])), im_of(v[q]));
+      df_fma(ai, re_of(c[q]), im_of(v[q]));
+      df_fma(ai, im_of(c[q]), re_of(v[q]));
+    }
+  }
+  for (; t < w; ++t) {
+    const uint32_t ee = __ldg(e + (int64_t)t * kSlice);
+    const float4 c = __ldg(cf + (int64_t)t * kSlice);
+    const float4 v = ldv<CG>(rec + (ee & op.colmask));
+    df_fma(ar, re_of(c), re_of(v));
+    df_fma(ar, df_neg(im_of(c)), im_of(v));
+    df_fma(ai, re_of(c), im_of(v));
+    df_fma(ai, im_of(c), re_of(v));
+  }
+  return cdf(ar, ai);
 }
 
 // Same in FP32 (FP32 values, FP32 accumulation).  nk, the records' third

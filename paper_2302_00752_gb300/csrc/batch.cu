@@ -91,6 +91,7 @@ OpView batch_op(const ss_batch_s* b) {
   op.woff = b->woff.get();
   op.ent = b->ent.get();
   op.ecoef = b->ecoef64.get();
+  op.ecoefdf = nullptr;
   op.colbits = colbits_of(b->jbits);
   op.colmask = colmask_of(b->jbits);
   return op;

@@ -34,4 +34,31 @@ __device__ __forceinline__ void df_fma(DF& acc, const DF a, const DF b) {
   acc.hi = hi;
 }
 
+// a + b (TwoSum of the high parts, the low parts added, renormalised).
+__device__ __forceinline__ DF df_add(const DF a, const DF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  const float lo = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float hi = __fadd_rn(s, lo);
+  return DF{hi, __fsub_rn(lo, __fsub_rn(hi, s))};
+}
+
+__device__ __forceinline__ DF df_neg(const DF a) { return DF{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ double df_to_double(const DF a) { return (double)a.hi + (double)a.lo; }
+
+// Sum over the warp (fixed butterfly; every lane gets the result).
+__device__ __forceinline__ DF df_warp_sum(DF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = df_add(v, DF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+  return v;
+}
+
+// Complex double-float values as float4 (re.hi, re.lo, im.hi, im.lo).
+__device__ __forceinline__ DF re_of(const float4 a) { return DF{a.x, a.y}; }
+__device__ __forceinline__ DF im_of(const float4 a) { return DF{a.z, a.w}; }
+__device__ __forceinline__ float4 cdf(const DF re, const DF im) { return make_float4(re.hi, re.lo, im.hi, im.lo); }
+
 }  // namespace ss

@@ -5,8 +5,9 @@
 // (one warp each).  The slices are split once into contiguous chunks (static
 // work units); every CG phase walks the block's chunks, and a grid-wide barrier
 // separates phases.  Inner products are reduced deterministically: per chunk
-// and instance, warps add their slices in order, the block adds its warps in
-// order into one partial slot, and every block that needs a scalar sums that
+// and instance, each lane adds its rows in slice order, each warp folds its
+// lanes with a fixed butterfly, the block adds its warps in order into one
+// partial slot, and every block that needs a scalar sums that
 // instance's slots with the same fixed warp reduction.  Per-instance state that
 // crosses phases (rho, active flags) is double-buffered by iteration parity and
 // written only by the instance's owner block (the one holding its first
@@ -36,6 +37,7 @@ struct Smem {
   double cb[kMaxInstPerChunk];
   double cc[kMaxInstPerChunk];
   double cd[kMaxInstPerChunk];
+  float dfs[kMaxInstPerChunk][4];   // DF64 CG: alpha and beta as double-float
   int32_t flag[kMaxInstPerChunk];
 };
 
@@ -142,11 +144,20 @@ __device__ __forceinline__ double warp_reduce(double v) {
   return v;
 }
 
-// Run one phase over the block's chunks.
+// Lane accumulators of run_phase: FP64, or double-float for the DF64 CG (kept
+// on the FP32 pipe, converted to FP64 once per warp fold).
+__device__ __forceinline__ void acc_add(double& a, double b) { a += b; }
+__device__ __forceinline__ void acc_add(DF& a, DF b) { a = df_add(a, b); }
+__device__ __forceinline__ double acc_fold(double v) { return warp_reduce(v); }
+__device__ __forceinline__ double acc_fold(DF v) { return df_to_double(df_warp_sum(v)); }
+
+// Run one phase over the block's chunks.  Partial sums: every lane adds its
+// rows' values in slice order, the warp folds its lanes once per run of slices
+// of one instance (fixed butterfly), the block adds its warps in order.
 //   scal(c, ch, k, i, owner): per instance of the chunk (one warp each), fills
 //                             sm.ca/cb/flag[k] and does the owner's bookkeeping;
 //   row(g, s, lane, i, k, vals): per row, adds to vals[q] for q in qmask.
-template <class Scal, class Row>
+template <class Acc = double, class Scal, class Row>
 __device__ void run_phase(const SolveParams& P, Smem& sm, unsigned qmask, Scal scal, Row row) {
   const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int c = blockIdx.x; c < P.n_chunks; c += gridDim.x) {
@@ -161,27 +172,39 @@ __device__ void run_phase(const SolveParams& P, Smem& sm, unsigned qmask, Scal s
     }
     __syncthreads();
     int cur_k = -1;
-    double run[kNQ] = {0.0, 0.0, 0.0, 0.0};
+    Acc run[kNQ] = {};
     for (int64_t s = ch.s0 + warp; s < ch.s1; s += nw) {
       const int i = P.slice_inst ? __ldg(P.slice_inst + s) : 0;
       const int k = i - ch.inst0;
       const int64_t g = s * kSlice + lane;
-      double vals[kNQ] = {0.0, 0.0, 0.0, 0.0};
+      Acc vals[kNQ] = {};
       row(g, s, lane, i, k, vals);
       if (qmask) {
+        // lanes keep their own running sums; the butterfly runs once per
+        // instance run of the warp (warp-uniform branch), not once per slice
         if (k != cur_k) {
-          if (cur_k >= 0 && lane == 0)
-            for (int q = 0; q < kNQ; ++q) sm.acc[warp][cur_k][q] += run[q];
-          for (int q = 0; q < kNQ; ++q) run[q] = 0.0;
+          if (cur_k >= 0) {
+#pragma unroll
+            for (int q = 0; q < kNQ; ++q) {
+              const double t = (qmask & (1u << q)) ? acc_fold(run[q]) : 0.0;
+              if (lane == 0) sm.acc[warp][cur_k][q] += t;
+            }
+          }
+          for (int q = 0; q < kNQ; ++q) run[q] = Acc{};
           cur_k = k;
         }
 #pragma unroll
         for (int q = 0; q < kNQ; ++q)
-          if (qmask & (1u << q)) run[q] += warp_reduce(vals[q]);
+          if (qmask & (1u << q)) acc_add(run[q], vals[q]);
       }
     }
-    if (qmask && cur_k >= 0 && lane == 0)
-      for (int q = 0; q < kNQ; ++q) sm.acc[warp][cur_k][q] += run[q];
+    if (qmask && cur_k >= 0) {
+#pragma unroll
+      for (int q = 0; q < kNQ; ++q) {
+        const double t = (qmask & (1u << q)) ? acc_fold(run[q]) : 0.0;
+        if (lane == 0) sm.acc[warp][cur_k][q] += t;
+      }
+    }
     __syncthreads();
     if (qmask) {
       for (int t = threadIdx.x; t < ni * kNQ; t += blockDim.x) {
@@ -372,6 +395,156 @@ __device__ void solve_fp64(const SolveParams& P, Smem& sm) {
     v[2] = r.x * r.x + r.y * r.y;
     const int64_t l = g - in.row0;
     if (l < in.rows) in.u[l] = P.xrec[2 * g];
+  });
+  if (!grid_sync(P)) return;
+  run_phase(P, sm, 0u, [&](int, const Chunk&, int, int i, bool owner, int lane) {
+    double t[kNQ];
+    inst_sums(P, i, t);
+    if (owner && lane == 0) {
+      P.state[i].rr = t[2];
+      P.state[i].applies += 1;
+    }
+  }, [](int64_t, int64_t, int, int, int, double*) {});
+}
+
+// ------------------------------------------------------------ DF64 CG
+//
+// The FP64 CG above in double-float arithmetic: vectors, records, entry
+// coefficients and the Jacobi factors are unevaluated float pairs, every
+// product and sum is an error-free-transformation double-float operation on
+// the FP32 pipe (about 2^-48 relative each), partial sums stay double-float
+// until the warp fold; the CG scalars, the stopping test and the final
+// residual f - L x are FP64.  Same recurrences, same phases.
+
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  DF r{0.f, 0.f};
+  df_fma(r, a, b);
+  return r;
+}
+
+__device__ void solve_df64(const SolveParams& P, Smem& sm) {
+  const double tol2 = P.tol * P.tol;
+  auto noscal = [](int, const Chunk&, int, int, bool, int) {};
+  float4* r4 = reinterpret_cast<float4*>(P.r);
+  float4* w4 = reinterpret_cast<float4*>(P.w64);
+  float4* p4 = reinterpret_cast<float4*>(P.pd);
+  float4* s4 = reinterpret_cast<float4*>(P.sd);
+  // r = f, x = 0, u = D^-1 r, p = s = 0; |f|^2 (FP64)
+  run_phase(P, sm, 0b1000u, noscal, [&](int64_t g, int64_t, int, int i, int, double* v) {
+    const SolveInst& in = P.inst[i];
+    const double2 f = f_at(in, g);
+    const DF rD = df_split(1.0 / jacobi(P, in, g));
+    P.d32[g] = make_float2(rD.hi, rD.lo);
+    const DF fr = df_split(f.x), fi = df_split(f.y);
+    r4[g] = cdf(fr, fi);
+    P.xdf[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+    P.udf[g] = cdf(df_mul(rD, fr), df_mul(rD, fi));
+    p4[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+    s4[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+    v[3] = f.x * f.x + f.y * f.y;
+  });
+  if (!grid_sync(P)) return;
+  auto phase_y = [&](unsigned par) {
+    run_phase<DF>(P, sm, 0b0111u, [&](int, const Chunk&, int k, int i, bool, int lane) {
+      if (lane == 0) sm.flag[k] = par > 1 ? 1 : __ldcg(&P.state[i].act[par]);
+    }, [&](int64_t g, int64_t s, int lane, int i, int k, DF* v) {
+      if (!sm.flag[k]) return;
+      const SolveInst& in = P.inst[i];
+      const float4 w = (g == in.zero_row) ? __ldcg(P.udf + g) : row_applydf<true>(P.op, s, lane, P.udf);
+      const float4 u = P.udf[g], r = r4[g];
+      w4[g] = w;
+      DF a{0.f, 0.f}, b{0.f, 0.f}, c{0.f, 0.f};
+      df_fma(a, re_of(r), re_of(u));
+      df_fma(a, im_of(r), im_of(u));
+      df_fma(b, re_of(w), re_of(u));
+      df_fma(b, im_of(w), im_of(u));
+      df_fma(c, re_of(r), re_of(r));
+      df_fma(c, im_of(r), im_of(r));
+      v[0] = a;
+      v[1] = b;
+      v[2] = c;
+    });
+  };
+  phase_y(2);   // every instance
+  if (!grid_sync(P)) return;
+  for (int it = 0;; ++it) {
+    const int cur = it & 1, nxt = cur ^ 1;
+    run_phase(P, sm, 0u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
+      double t[kNQ];
+      inst_sums(P, i, t);
+      if (lane == 0) {
+        InstState& st = P.state[i];
+        const int act = it == 0 ? 1 : __ldcg(&st.act[cur]);
+        const double bb = it == 0 ? t[3] : __ldcg(&st.bb);
+        const bool conv = t[2] <= tol2 * bb;
+        const bool cap = it >= P.max_iter;
+        const Coeffs cf = cg_coeffs(it, t[0], t[1], it ? __ldcg(&st.rho[cur]) : 0.0,
+                                    it ? __ldcg(&st.alpha[cur]) : 0.0);
+        const bool go = act && !conv && !cap;
+        sm.flag[k] = go;
+        const DF a = df_split(cf.alpha), b = df_split(cf.beta);
+        sm.dfs[k][0] = a.hi;
+        sm.dfs[k][1] = a.lo;
+        sm.dfs[k][2] = b.hi;
+        sm.dfs[k][3] = b.lo;
+        if (owner) {
+          if (it == 0) {
+            st.bb = bb;
+            st.applies = 1;
+            st.outer_iters = 1;
+          }
+          st.act[nxt] = go;
+          st.rho[nxt] = t[0];
+          st.alpha[nxt] = cf.alpha;
+          if (act) {
+            st.rr = t[2];
+            st.iters = it;
+            if (conv) owner_done(P, st, SS_OK);
+            else if (cap) owner_done(P, st, SS_ERR_NOT_CONVERGED);
+            else st.applies += 1;
+          }
+        }
+      }
+    }, [&](int64_t g, int64_t, int, int, int k, double*) {
+      if (!sm.flag[k]) return;
+      const DF a{sm.dfs[k][0], sm.dfs[k][1]}, b{sm.dfs[k][2], sm.dfs[k][3]};
+      const float4 u = P.udf[g], w = w4[g], po = p4[g], so = s4[g], xo = P.xdf[g], ro = r4[g];
+      // p = u + beta p, s = w + beta s
+      DF pr = re_of(u), pi = im_of(u), sr = re_of(w), si = im_of(w);
+      df_fma(pr, b, re_of(po));
+      df_fma(pi, b, im_of(po));
+      df_fma(sr, b, re_of(so));
+      df_fma(si, b, im_of(so));
+      // x += alpha p, r -= alpha s
+      DF xr = re_of(xo), xi = im_of(xo), rr = re_of(ro), ri = im_of(ro);
+      df_fma(xr, a, pr);
+      df_fma(xi, a, pi);
+      const DF na = df_neg(a);
+      df_fma(rr, na, sr);
+      df_fma(ri, na, si);
+      const float2 d = P.d32[g];
+      const DF rD{d.x, d.y};
+      p4[g] = cdf(pr, pi);
+      s4[g] = cdf(sr, si);
+      P.xdf[g] = cdf(xr, xi);
+      r4[g] = cdf(rr, ri);
+      P.udf[g] = cdf(df_mul(rD, rr), df_mul(rD, ri));
+    });
+    if (!grid_sync(P)) return;
+    if (block_counter(P, 0) >= P.n_inst) break;
+    phase_y(nxt);
+    if (!grid_sync(P)) return;
+  }
+  // true residual f - L x (double-float operator, FP64 difference), and the output
+  run_phase(P, sm, 0b0100u, noscal, [&](int64_t g, int64_t s, int lane, int i, int, double* v) {
+    const SolveInst& in = P.inst[i];
+    const float4 y4 = (g == in.zero_row) ? __ldcg(P.xdf + g) : row_applydf<true>(P.op, s, lane, P.xdf);
+    const double2 f = f_at(in, g);
+    const double2 r = make_double2(f.x - df_to_double(re_of(y4)), f.y - df_to_double(im_of(y4)));
+    v[2] = r.x * r.x + r.y * r.y;
+    const int64_t l = g - in.row0;
+    const float4 x = P.xdf[g];
+    if (l < in.rows) in.u[l] = make_double2(df_to_double(re_of(x)), df_to_double(im_of(x)));
   });
   if (!grid_sync(P)) return;
   run_phase(P, sm, 0u, [&](int, const Chunk&, int, int i, bool owner, int lane) {
@@ -797,7 +970,8 @@ __global__ void __launch_bounds__(1024) k_solve(SolveParams P) {
   __shared__ Smem sm;
   if constexpr (MODE == 0) solve_fp64(P, sm);
   else if constexpr (MODE == 1) solve_refined(P, sm);
-  else solve_bicgstab(P, sm);
+  else if constexpr (MODE == 2) solve_bicgstab(P, sm);
+  else solve_df64(P, sm);
 }
 
 __global__ void k_init_solve_records(const int64_t* __restrict__ norm, int64_t n, const int8_t* __restrict__ wide_rows,
@@ -906,6 +1080,19 @@ ss_status work_alloc_bicgstab(SolveWork& W, cudaStream_t st) {
   return SS_OK;
 }
 
+ss_status work_alloc_df64(SolveWork& W, cudaStream_t st) {
+  if (W.xdf.n >= (size_t)W.rows_total && W.udf.n >= (size_t)W.rows_total) return SS_OK;
+  SS_TRY(W.xdf.alloc(W.rows_total, st));
+  SS_TRY(W.udf.alloc(W.rows_total, st));
+  // the dummy record (last row) must read as zero
+  SS_CUDA(cudaMemsetAsync(W.xdf.get(), 0, W.rows_total * sizeof(float4), st));
+  SS_CUDA(cudaMemsetAsync(W.udf.get(), 0, W.rows_total * sizeof(float4), st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  W.xdf.settle();
+  W.udf.settle();
+  return SS_OK;
+}
+
 ss_status work_upload(SolveWork& W, const SolvePlan& plan, cudaStream_t st) {
   const int n_inst = (int)plan.inst.size(), n_chunk = (int)plan.chunk.size();
   if (n_inst > W.cap_inst) { SS_TRY(W.inst.alloc(n_inst, st)); SS_TRY(W.state.alloc(n_inst, st)); W.cap_inst = n_inst; }
@@ -921,7 +1108,8 @@ ss_status max_grid(int mode, int block, int* grid) {
   int nb = 0;
   if (mode == 0) SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<0>, block, 0));
   else if (mode == 1) SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<1>, block, 0));
-  else SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<2>, block, 0));
+  else if (mode == 2) SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<2>, block, 0));
+  else SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<3>, block, 0));
   if (nb < 1) SS_FAIL(SS_ERR_CUDA, "solve: kernel does not fit on an SM with %d threads", block);
   *grid = nb * sm_count();
   return SS_OK;
@@ -934,6 +1122,8 @@ ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, co
                        cudaEvent_t ev_end, const double2* cdiag) {
   if (mode == 2 && (!cdiag || !W.zrec.get() || !W.tv.get()))
     SS_FAIL(SS_ERR_INVALID, "solve: BiCGStab needs the operator diagonal and its workspace");
+  if (mode == 3 && (!op.ecoefdf || !W.xdf.get() || !W.udf.get()))
+    SS_FAIL(SS_ERR_INVALID, "solve: DF64 CG needs double-float coefficients and its workspace");
   SolveParams P{};
   P.n_inst = (int)plan.inst.size();
   P.n_chunks = (int)plan.chunk.size();
@@ -964,6 +1154,8 @@ ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, co
   P.cdiag = cdiag;
   P.zrec = W.zrec.get();
   P.tv = W.tv.get();
+  P.xdf = W.xdf.get();
+  P.udf = W.udf.get();
   P.part = W.part.get();
   P.bar = W.bar.get();
   P.counters = W.counters.get();
@@ -993,7 +1185,8 @@ ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, co
   if (ev_begin) SS_CUDA(cudaEventRecord(ev_begin, st));
   if (mode == 0) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<0>, P));
   else if (mode == 1) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<1>, P));
-  else SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<2>, P));
+  else if (mode == 2) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<2>, P));
+  else SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<3>, P));
   if (ev_end) SS_CUDA(cudaEventRecord(ev_end, st));
   return SS_OK;
 }
@@ -1068,6 +1261,10 @@ static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream
   C.plan.grid = std::min<int>(grid, (int)C.plan.chunk.size());
   SS_TRY(work_alloc(C.work, s->rows_pad + 1, s->norm.get(), nullptr, s->wide, st));
   if (mode == 2) SS_TRY(work_alloc_bicgstab(C.work, st));
+  if (mode == 3) {
+    SS_TRY(ensure_ecoefdf(s, st));
+    SS_TRY(work_alloc_df64(C.work, st));
+  }
   SS_TRY(work_upload(C.work, C.plan, st));
   C.planned_mode = mode;
   return SS_OK;
@@ -1118,7 +1315,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
                            ss_precision prec, ss_solve_stats* stats, void* stream) {
   if (!s || !f_on_S || !u_on_S) SS_FAIL(SS_ERR_INVALID, "solve: null argument");
   if (!(tol > 0.0) || max_iter < 1) SS_FAIL(SS_ERR_INVALID, "solve: need tol > 0 and max_iter >= 1");
-  if (prec != SS_FP64 && prec != SS_FP32) SS_FAIL(SS_ERR_INVALID, "solve: bad precision");
+  if (prec != SS_FP64 && prec != SS_FP32 && prec != SS_DF64) SS_FAIL(SS_ERR_INVALID, "solve: bad precision");
   cudaStream_t st = as_stream(stream);
   if (s->adr && prec != SS_FP64) SS_FAIL(SS_ERR_INVALID, "solve: ADR stamps solve in SS_FP64 (BiCGStab)");
   if (!s->adr && s->zero_idx >= 0) {
@@ -1129,7 +1326,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
     if (f0.x != 0.0 || f0.y != 0.0) SS_FAIL(SS_ERR_INVALID, "solve: f_hat_0 must be 0 (mean-zero forcing)");
   }
   ss_solve_ctx* C = solve_ctx(s);
-  const int mode = s->adr ? 2 : (prec == SS_FP64 ? 0 : 1);
+  const int mode = s->adr ? 2 : (prec == SS_FP64 ? 0 : (prec == SS_FP32 ? 1 : 3));
   SS_TRY(stamp_plan(s, *C, mode, st));
   C->plan.inst[0].f = reinterpret_cast<const double2*>(f_on_S);
   C->plan.inst[0].u = reinterpret_cast<double2*>(u_on_S);
@@ -1138,6 +1335,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
   op.woff = s->slice_off.get();
   op.ent = s->ent.get();
   op.ecoef = s->ecoef64.get();
+  op.ecoefdf = s->ecoefdf.get();
   op.colbits = colbits_of(s->jbits);
   op.colmask = colmask_of(s->jbits);
   if (!C->work.ev[0]) {

@@ -63,6 +63,8 @@ struct SolveParams {
   const double2* cdiag;        // complex diagonal of the ADR operator (BiCGStab), else null
   double2* zrec;               // BiCGStab: records of z = D^-1 s
   double2* tv;                 // BiCGStab: t = L z
+  float4* xdf;                 // DF64 CG: x and u = D^-1 r as double-float records
+  float4* udf;
   double* part;                // [slots][kNQ]
   unsigned* bar;               // barrier count, generation
   int* counters;               // done, inner started, inner finished
@@ -90,6 +92,7 @@ struct SolveWork {
   }
   DevBuf<double2> xrec, urec64, r, w64, pd, sd, rhat, dlt;
   DevBuf<double2> zrec, tv;                // BiCGStab only (allocated on first use)
+  DevBuf<float4> xdf, udf;                 // DF64 CG only (allocated on first use)
   DevBuf<float4> urec32;
   DevBuf<float2> w32, r32, p32, s32, d32;
   DevBuf<double> rdiag;
@@ -110,12 +113,14 @@ ss_status work_alloc(SolveWork& W, int64_t rows_total, const int64_t* norm, cons
 ss_status work_upload(SolveWork& W, const SolvePlan& plan, cudaStream_t st);
 ss_status max_grid(int mode, int block, int* grid);
 // mode: 0 FP64 CG, 1 FP32-refined CG, 2 FP64 BiCGStab (ADR operator; cdiag
-// = its complex diagonal, workspace from work_alloc_bicgstab).
+// = its complex diagonal, workspace from work_alloc_bicgstab), 3 double-float
+// CG (op.ecoefdf set, workspace from work_alloc_df64).
 ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, const int32_t* slice_inst,
                        const int64_t* norm, const double2* ca64, const float2* ca32, const int32_t* pn,
                        double tol, int max_iter, int mode, cudaStream_t st,
                        cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr, const double2* cdiag = nullptr);
 ss_status work_alloc_bicgstab(SolveWork& W, cudaStream_t st);
+ss_status work_alloc_df64(SolveWork& W, cudaStream_t st);
 ss_status read_stats(SolveWork& W, int n_inst, ss_solve_stats* stats, ss_status* worst, cudaStream_t st,
                      cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 

@@ -132,6 +132,7 @@ struct ss_stamp_s {
   ss::DevBuf<int32_t> slice_off;      // [n_slices + 1], in units of 32 entries (one per row of a slice)
   ss::DevBuf<uint32_t> ent;           // [n_ent] col | (j << colbits)
   ss::DevBuf<double2> ecoef64;        // [n_ent] 2 pi^2 (|k|^2 + |l|^2 - |p_j|^2) a_hat_j per entry (FP64 operator)
+  ss::DevBuf<float4> ecoefdf;         // [n_ent + 1] the same as double-float, built on first DF64 solve
   // scratch for galerkin_apply
   ss::DevBuf<float4> rec32;           // [rows_pad + 1]
   ss::DevBuf<double2> rec64;          // [2 * (rows_pad + 1)] (value, norm|pad) pairs
@@ -168,6 +169,8 @@ ss_status launch_apply64(const ss_stamp_s* s, double2* y, cudaStream_t st);
 // S^{N+L}), zero on the rest, into the FP64 record array.
 ss_status launch_pack64_prefix(const ss_stamp_s* s, const double2* u, int64_t n_u, cudaStream_t st);
 ss_status launch_apply32(const ss_stamp_s* s, float2* y, cudaStream_t st);
+// Double-float copy of the FP64 entry coefficients (built once per operator).
+ss_status ensure_ecoefdf(ss_stamp_s* s, cudaStream_t st);
 
 int sm_count();
 

@@ -594,6 +594,7 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   S->n_ent = total_w * kSlice;
   SS_TRY(S->ent.alloc(S->n_ent + 1, st));
   SS_TRY(S->ecoef64.alloc(S->n_ent + 1, st));
+  S->ecoefdf.release();   // rebuilt from ecoef64 by the next DF64 solve
   if (S->adr) {
     SS_TRY(S->diag64.alloc(S->rows_pad + 1, st));
     SS_DISPATCH_WT(S->key.WT, (k_fill_slices_adr<WT><<<nblk(S->rows_pad + 1), 256, 0, st>>>(
@@ -753,6 +754,7 @@ static void rebind(ss_stamp_s* S, cudaStream_t st) {
   S->slice_off.s = st;
   S->ent.s = st;
   S->ecoef64.s = st;
+  S->ecoefdf.s = st;
   S->rec32.s = st;
   S->rec64.s = st;
   S->diag64.s = st;

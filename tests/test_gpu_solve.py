@@ -113,3 +113,32 @@ def test_iteration_cap_reports_not_converged(B):
         assert st["status"] == "SS_ERR_NOT_CONVERGED"
         u, st = B.solve(s, f_on, 1e-12, 500, "fp64")
         assert st["status"] == "SS_OK"
+
+
+@pytest.mark.parametrize("name", ["cfg1", "cfg3"])
+def test_df64_matches_oracle(B, name):
+    # the FP64 CG in double-float arithmetic: same answer as the oracle within
+    # the FP64 tolerance
+    inst, af, av, ff, fv = stamp_inputs(name)
+    ref = opipe.solve_recovered(inst.N, af, av, ff, fv, tol=1e-14)
+    with B.stamp_build(af, av, ff, inst.N) as s:
+        f_on, _ = s.scatter(ff, fv)
+        u, st = B.solve(s, f_on, 1e-12, 1000, "df64")
+        u64, st64 = B.solve(s, f_on, 1e-12, 1000, "fp64")
+        u2, _ = B.solve(s, f_on, 1e-12, 1000, "df64")
+    assert st["status"] == "SS_OK" and st["rel_residual"] <= 1e-12
+    assert rel_l2(u.cpu().numpy(), ref.u) < TOL
+    assert torch.equal(u, u2)                       # deterministic
+    assert abs(st["applies"] - st64["applies"]) <= 2  # same recurrences
+
+
+def test_df64_manufactured_cfg2(B, gp):
+    inst = W.make_cfg2()
+    res = gp.run(gp.prepare(inst), tol=1e-12, solve=False)
+    try:
+        u, st = B.solve(res.stamp, res.f_on_S, 1e-12, 1000, "df64")
+        want, outside = res.stamp.scatter(inst.u_freq, inst.u_val)
+        assert outside == 0 and st["status"] == "SS_OK"
+        assert rel_l2(u.cpu().numpy(), want.cpu().numpy()) < TOL
+    finally:
+        res.stamp.destroy()
