@@ -19,9 +19,23 @@ Hermitian coefficients), and keep |g_hat_k| > tau * max |g_hat| (the paper
 gives no threshold: tau is a parameter, 1e-9 in FP64 by default).  More than
 ``s_max`` survivors is an error (the paper's SFT returns at most 2s terms).
 
+Support identification (no candidate set; the paper delegates it to the SFT
+of its reference [gross_sparse_2021], which is not available, so this is the
+reading used here): sample g also on the d shifted lattices x_j + e_i / P with
+P a prime above 2 max |k_i|.  g(. + e_i/P) has coefficients
+g_hat_k exp(2 pi i k_i / P), so in every bin b that holds a frequency k the
+ratio X_i[b] / X_0[b] of the shifted to the plain spectrum is
+exp(2 pi i k_i / P) and k_i = round(P arg(ratio) / (2 pi)) taken in
+(-P/2, P/2].  The bins kept are those of the half spectrum 0 <= b <= M/2 with
+|X_0[b]| > tau max |X_0|; a bin whose identified k does not satisfy
+k.z = b (mod M) betrays a collision.  Values g_hat_k = X_0[b] / M; -k gets the
+conjugate.  The spectra are numpy FFTs of the samples (a library step).
+
 Pins: closed forms of cosine, sine and constant terms; equality with a full
 length-M FFT from numpy when I is a bijective box; direct evaluation of g at
-floating-point lattice points (tests/test_oracle_sft.py).
+floating-point lattice points; exact support and values identified for
+random sparse sums; the shifted-spectrum ratio of a single term in closed form
+(tests/test_oracle_sft.py).
 """
 from __future__ import annotations
 
@@ -98,3 +112,47 @@ def true_coefficients(freq, coef):
             out[k] = out.get(k, 0) + c / 2
             out[mk] = out.get(mk, 0) + np.conj(c) / 2
     return out
+
+
+def sample_shifted(freq, coef, z, M, P, i):
+    """g(x_j + e_i / P) for j < M: the phase p.x_j + p_i / P is the exact
+    rational ((j q mod M) P + p_i M) / (M P) mod 1, q = p.z mod M."""
+    M, P = int(M), int(P)
+    js = np.arange(M, dtype=np.int64)
+    q = residues(freq, z, M)
+    out = np.zeros(M, np.float64)
+    for qt, pt, ct in zip(q, np.asarray(freq, np.int64), np.asarray(coef, np.complex128)):
+        num = (((js * int(qt)) % M) * P + int(pt[i]) * M) % (M * P)
+        out += (ct * np.exp(2j * np.pi * (num / (M * P)))).real
+    return out
+
+
+def identify(freq, coef, z, M, P, tau=1e-9, s_max=None):
+    """Support identification of g = sum_t Re(c_t e_{p_t}) (see the module
+    header).  Returns (freq [n, d] int32, val [n]) with every kept bin's k
+    followed by -k (bin 0 alone), bins ascending."""
+    M, P = int(M), int(P)
+    d = np.asarray(freq).shape[1]
+    X0 = np.fft.fft(sample(freq, coef, z, M))
+    half = X0[: M // 2 + 1]
+    mag = np.abs(half)
+    bins = np.nonzero(mag > tau * mag.max())[0]
+    ks = np.zeros((len(bins), d), np.int64)
+    for i in range(d):
+        Xi = np.fft.fft(sample_shifted(freq, coef, z, M, P, i))
+        ang = np.angle(Xi[bins] / X0[bins])
+        k = np.rint(P * ang / (2 * np.pi)).astype(np.int64) % P
+        ks[:, i] = np.where(k > P // 2, k - P, k)
+    if np.any(residues(ks, z, M) != bins):
+        raise ValueError("identified frequency does not sit in its bin (collision)")
+    out_f, out_v = [], []
+    for b, k in zip(bins.tolist(), ks):
+        v = X0[b] / M
+        out_f.append(k)
+        out_v.append(v)
+        if b != 0:
+            out_f.append(-k)
+            out_v.append(np.conj(v))
+    if s_max is not None and len(out_f) > s_max:
+        raise ValueError("more terms above threshold than s_max")
+    return np.array(out_f, np.int32).reshape(len(out_f), d), np.array(out_v, np.complex128)

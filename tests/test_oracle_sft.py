@@ -84,3 +84,42 @@ def test_threshold_and_cap():
     assert sorted(kf.ravel().tolist()) == [-5, -3, 3, 5]
     with pytest.raises(ValueError):
         sft.recover_known(s, cand, [1], M, tau=1e-14, s_max=3)
+
+
+def test_identify_single_term_phase_ratio():
+    # g = cos(2 pi p.x): the shifted spectrum at p's bin is the plain one
+    # times exp(2 pi i p_i / P)
+    from oracle.sft import sample, sample_shifted
+    p = np.array([[5, -3, 7]])
+    z, M, P = np.array([1, 23, 529]), 12167, 17
+    b = int((p[0] @ z) % M)
+    X0 = np.fft.fft(sample(p, [1.0], z, M))
+    for i in range(3):
+        Xi = np.fft.fft(sample_shifted(p, [1.0], z, M, P, i))
+        np.testing.assert_allclose(Xi[b] / X0[b], np.exp(2j * np.pi * p[0, i] / P), atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_identify_recovers_random_sparse_sums(seed):
+    from oracle.lattice import is_reconstructing, next_prime
+    from oracle.sft import identify, true_coefficients
+    rng = np.random.default_rng(seed)
+    d, K = 3, 12
+    freqs = np.unique(rng.integers(-K, K + 1, size=(6, d)), axis=0)
+    freqs = freqs[freqs.any(axis=1)]
+    coef = rng.uniform(-1, 1, len(freqs)) + 1j * rng.uniform(-1, 1, len(freqs))
+    freqs = np.vstack([np.zeros((1, d), int), freqs])
+    coef = np.concatenate([[0.7], coef])
+    true = true_coefficients(freqs, coef)
+    I = np.array(sorted(true))
+    M = next_prime(4000)
+    while True:
+        z = rng.integers(1, M, size=d)
+        if is_reconstructing(I, z, M):
+            break
+    P = next_prime(2 * K + 1)
+    f, v = identify(freqs, coef, z, M, P, tau=1e-9)
+    got = {tuple(int(x) for x in k): val for k, val in zip(f.tolist(), v)}
+    assert set(got) == set(true)
+    for k in true:
+        assert abs(got[k] - true[k]) < 1e-12
