@@ -367,6 +367,46 @@ def adr_section(B, gp, flush, Q=1000):
     return out
 
 
+def identify_section(B, gp, flush):
+    """Support identification without candidates (d + 1 shifted samplings and
+    FFTs) of the d = 10 workload's forcing: 840 frequencies on the
+    component-by-component lattice (M = 10^6) chosen for the known support."""
+    import torch
+    inst = W.make_cfg2()
+    p = gp.prepare(inst)
+    z, M = gp.choose_lattice(p.extra["lattice"], p.cand)
+    K = int(p.cand.abs().max())
+    P = next_prime_py(2 * K + 1)
+    n_true = int(len(p.f_freq))
+    times = []
+    for it in range(3):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        f, v = B.sft_identify(z, M, p.f_freq, p.f_coef, P, s_max=4 * n_true + 8, tau=1e-9)
+        b.record()
+        b.synchronize()
+        if it:
+            times.append(a.elapsed_time(b))
+    return {"workload": "cfg2 forcing (d=10, M=10^6)", "P": P, "identified": int(len(f)),
+            "ms": statistics.median(times), "samplings_and_ffts": inst.d + 1}
+
+
+def next_prime_py(n):
+    def prime(m):
+        if m < 2:
+            return False
+        i = 2
+        while i * i <= m:
+            if m % i == 0:
+                return False
+            i += 1
+        return True
+    while not prime(n):
+        n += 1
+    return n
+
+
 DF_OPS_PER_PAIR = 150   # ten double-float multiply-adds of 15 FP32 instructions per (term, point)
 
 
@@ -642,6 +682,10 @@ def main():
                 extra["apply"] = apply_section(B, gp, flush, load_peaks())
             except Exception as e:
                 extra["apply"] = {"error": repr(e)}
+            try:
+                extra["identify"] = identify_section(B, gp, flush)
+            except Exception as e:
+                extra["identify"] = {"error": repr(e)}
             try:
                 extra["adr"] = adr_section(B, gp, flush)
             except Exception as e:

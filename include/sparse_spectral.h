@@ -150,6 +150,23 @@ ss_status sft_recover(const ss_lattice* lat, const ss_trig* g, ss_precision prec
                       int64_t n_cand, int64_t s_max, double tau, int32_t* freq_out, double* val_out,
                       int64_t* n_out, void* stream);
 
+/* Support identification when no candidate set is known (the paper delegates
+ * it to the SFT of its reference [gross_sparse_2021]; this is the reading
+ * used here).  Samples g on the lattice and on the d shifted lattices
+ * x_j + e_i / P (P > 2 max |k_i|, e.g. the smallest prime above 2K + 1 for
+ * bandwidth K): the shifted sum has the coefficients g_hat_k exp(2 pi i k_i / P),
+ * so in each kept bin b (0 <= b <= M/2, |X_0[b]| > tau max |X_0|) the ratio of
+ * the shifted to the plain spectrum gives k_i = round(P arg(X_i[b] / X_0[b]) / (2 pi))
+ * in (-P/2, P/2].  g_hat_k = X_0[b] / M; -k gets the conjugate.  Output in
+ * increasing bin order, each k followed by -k (k = 0 alone): freq_out device
+ * [s_max][d], val_out device FP64 complex [s_max], the count in *n_out; more
+ * than s_max terms is SS_ERR_INVALID; a k that does not map back to its bin
+ * (k.z mod M != b: the lattice is not reconstructing for the support) is
+ * SS_ERR_NOT_RECONSTRUCTING.  Costs d + 1 samplings and FFTs of length M.
+ * Synchronises `stream`. */
+ss_status sft_identify(const ss_lattice* lat, const ss_trig* g, ss_precision prec, int32_t P, int64_t s_max,
+                       double tau, int32_t* freq_out, double* val_out, int64_t* n_out, void* stream);
+
 /* ------------------------------------------------------------------ stamp */
 
 /* S^N[a_hat](F) of eq. StampSet with F = f_freq (device [n_f][d], distinct,

@@ -68,6 +68,7 @@ def _load():
         "lattice_sample": (i32, [P(Lattice), P(Trig), i32, vp, vp]),
         "sft_recover_samples": (i32, [P(Lattice), vp, i32, vp, i64, i64, dbl, vp, vp, P(i64), vp]),
         "sft_recover": (i32, [P(Lattice), P(Trig), i32, vp, i64, i64, dbl, vp, vp, P(i64), vp]),
+        "sft_identify": (i32, [P(Lattice), P(Trig), i32, i32, i64, dbl, vp, vp, P(i64), vp]),
         "stamp_build": (i32, [P(Sparse), vp, i64, i32, P(vp), vp]),
         "stamp_build_adr": (i32, [P(Sparse), P(Sparse), P(Sparse), vp, i64, i32, P(vp), vp]),
         "stamp_info": (i32, [vp, P(i64), P(i64), P(i64), P(i32)]),
@@ -230,6 +231,21 @@ def sft_recover(z, M, freq, coef, cand, s_max=0, tau=1e-9, precision="fp64"):
     n = C.c_int64()
     _check(lib.sft_recover(C.byref(lat), C.byref(g), p, _ptr(cd), cd.shape[0], int(s_max), float(tau), _ptr(fo),
                            _ptr(vo), C.byref(n), _stream()))
+    return fo[: n.value], vo[: n.value]
+
+
+def sft_identify(z, M, freq, coef, P, s_max, tau=1e-9, precision="fp64"):
+    """Support identification from the d shifted lattices x_j + e_i / P
+    (P > 2 max |k_i|); returns (freq, val) with each k followed by -k."""
+    p = _prec(precision)
+    lat = _lattice(z, M)
+    d = len(z)
+    g = _trig(freq, coef, d)
+    fo = torch.empty((int(s_max), d), dtype=torch.int32, device="cuda")
+    vo = torch.empty(int(s_max), dtype=torch.complex128, device="cuda")
+    n = C.c_int64()
+    _check(lib.sft_identify(C.byref(lat), C.byref(g), p, int(P), int(s_max), float(tau), _ptr(fo), _ptr(vo),
+                            C.byref(n), _stream()))
     return fo[: n.value], vo[: n.value]
 
 

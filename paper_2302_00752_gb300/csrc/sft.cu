@@ -661,6 +661,171 @@ ss_status recover_from(const SftPlan& P, const LatticeDev& L, const void* sample
   return SS_OK;
 }
 
+// ---------------------------------------------------- support identification
+//
+// No candidate set: the kept bins are those of the half spectrum with
+// |X_0[b]| > tau max |X_0|, and the coordinates of the frequency in bin b come
+// from the d shifted lattices x_j + e_i / P: g(. + e_i / P) has the
+// coefficients g_hat_k exp(2 pi i k_i / P), i.e. the same trigonometric sum
+// with every coefficient c_t turned by exp(2 pi i p_{t,i} / P), so its spectrum
+// satisfies X_i[b] / X_0[b] = exp(2 pi i k_i / P) and k_i is the nearest
+// integer to P arg(X_i[b] / X_0[b]) / (2 pi), taken in (-P/2, P/2] (P > 2 max |k_i|).
+
+template <typename T2>
+__global__ void k_spec_max(const T2* __restrict__ spec, int64_t nh, unsigned long long* maxbits) {
+  double m = 0.0;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nh; b += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, hypot((double)spec[b].x, (double)spec[b].y));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxbits, (unsigned long long)__double_as_longlong(m));
+}
+
+template <typename T2>
+__global__ void k_spec_keep(const T2* __restrict__ spec, int64_t nh, const unsigned long long* __restrict__ maxbits,
+                            double tau, int32_t* flag) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nh) return;
+  const double mx = __longlong_as_double((long long)*maxbits);
+  flag[b] = hypot((double)spec[b].x, (double)spec[b].y) > tau * mx ? 1 : 0;
+}
+
+template <typename T2>
+__global__ void k_spec_compact(const T2* __restrict__ spec, int64_t nh, const int32_t* __restrict__ flag,
+                               const int32_t* __restrict__ pos, int64_t* bins, double2* x0) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nh || !flag[b]) return;
+  bins[pos[b]] = b;
+  x0[pos[b]] = make_double2((double)spec[b].x, (double)spec[b].y);
+}
+
+// c_t exp(2 pi i p_{t,i} / P)
+__global__ void k_rotate_coef(const int32_t* __restrict__ freq, const double2* __restrict__ coef, int64_t n, int d,
+                              int i, int P, double2* out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double sn, cs;
+  sincospi(2.0 * (double)freq[t * d + i] / (double)P, &sn, &cs);
+  const double2 c = coef[t];
+  out[t] = make_double2(c.x * cs - c.y * sn, c.x * sn + c.y * cs);
+}
+
+template <typename T2>
+__global__ void k_identify_coord(const T2* __restrict__ spec, const int64_t* __restrict__ bins,
+                                 const double2* __restrict__ x0, int64_t nb, int d, int i, int P, int32_t* kf) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nb) return;
+  const T2 v = spec[bins[t]];
+  const double2 a = x0[t];
+  // arg(X_i / X_0) = arg(X_i conj(X_0))
+  const double re = (double)v.x * a.x + (double)v.y * a.y, im = (double)v.y * a.x - (double)v.x * a.y;
+  long long k = llrint((double)P * atan2(im, re) / (2.0 * 3.141592653589793)) % P;
+  if (k < 0) k += P;
+  if (2 * k > P) k -= P;
+  kf[t * d + i] = (int32_t)k;
+}
+
+// Each kept bin's k, then -k (bin 0 alone); a bin whose k does not reproduce
+// it (k.z mod M != b) is a collision.
+__global__ void k_identify_finish(const int32_t* __restrict__ kf, const int64_t* __restrict__ bins,
+                                  const double2* __restrict__ x0, int64_t nb, LatticeDev L, int32_t* fo, double2* vo,
+                                  int32_t* err) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nb) return;
+  const int d = L.d;
+  const int64_t b = bins[t];
+  if (residue_of(kf + t * d, d, L) != b) atomicExch(err, 1);
+  const int64_t z0 = bins[0] == 0 ? 1 : 0;
+  const int64_t o = t == 0 ? 0 : 2 * t - z0;
+  const double sc = 1.0 / (double)L.M;
+  const double2 v = make_double2(x0[t].x * sc, x0[t].y * sc);
+  for (int c = 0; c < d; ++c) fo[o * d + c] = kf[t * d + c];
+  vo[o] = v;
+  if (b != 0) {
+    for (int c = 0; c < d; ++c) fo[(o + 1) * d + c] = -kf[t * d + c];
+    vo[o + 1] = make_double2(v.x, -v.y);
+  }
+}
+
+ss_status exec_fft(const SftPlan& P, const void* samples, cudaStream_t st) {
+  cufftResult r = cufftSetStream(P.fft, st);
+  if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cufftSetStream failed: %d", (int)r);
+  if (P.prec == SS_FP64)
+    r = cufftExecD2Z(P.fft, reinterpret_cast<cufftDoubleReal*>(const_cast<void*>(samples)),
+                     reinterpret_cast<cufftDoubleComplex*>(P.spectrum.get()));
+  else
+    r = cufftExecR2C(P.fft, reinterpret_cast<cufftReal*>(const_cast<void*>(samples)),
+                     reinterpret_cast<cufftComplex*>(P.spectrum.get()));
+  if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cuFFT exec failed: %d", (int)r);
+  return SS_OK;
+}
+
+template <typename T2>
+ss_status identify_impl(const SftPlan& P, const LatticeDev& L, const ss_trig* g, int Pp, int64_t s_max, double tau,
+                        int32_t* freq_out, double* val_out, int64_t* n_out, cudaStream_t st) {
+  const int64_t nh = L.M / 2 + 1;
+  const T2* spec = reinterpret_cast<const T2*>(P.spectrum.get());
+  DevBuf<unsigned long long> maxbits;
+  DevBuf<int32_t> flag, pos, err;
+  DevBuf<int64_t> total, bins;
+  DevBuf<double2> x0;
+  SS_TRY(maxbits.alloc(1, st));
+  SS_TRY(flag.alloc(nh, st));
+  SS_TRY(pos.alloc(nh, st));
+  SS_TRY(total.alloc(1, st));
+  SS_TRY(err.alloc(1, st));
+  SS_TRY(sample_into(P, L, g, P.samples.get(), st));
+  SS_TRY(exec_fft(P, P.samples.get(), st));
+  SS_CUDA(cudaMemsetAsync(maxbits.get(), 0, sizeof(unsigned long long), st));
+  SS_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), st));
+  const unsigned gmax = (unsigned)std::min<int64_t>(nblk(nh), 4 * 152);
+  k_spec_max<T2><<<gmax, 256, 0, st>>>(spec, nh, maxbits.get());
+  k_spec_keep<T2><<<nblk(nh), 256, 0, st>>>(spec, nh, maxbits.get(), tau, flag.get());
+  SS_LAUNCH_CHECK();
+  SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), nh, total.get(), st));
+  int64_t nb = 0;
+  int32_t keep0 = 0;
+  SS_CUDA(cudaMemcpyAsync(&nb, total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaMemcpyAsync(&keep0, flag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  const int64_t n = 2 * nb - (keep0 ? 1 : 0);
+  if (nb == 0) {
+    *n_out = 0;
+    return SS_OK;
+  }
+  if (s_max > 0 && n > s_max)
+    SS_FAIL(SS_ERR_INVALID, "sft_identify: %lld terms above threshold exceed s_max = %lld", (long long)n,
+            (long long)s_max);
+  SS_TRY(bins.alloc(nb, st));
+  SS_TRY(x0.alloc(nb, st));
+  k_spec_compact<T2><<<nblk(nh), 256, 0, st>>>(spec, nh, flag.get(), pos.get(), bins.get(), x0.get());
+  SS_LAUNCH_CHECK();
+  DevBuf<int32_t> kf;
+  DevBuf<double2> rot;
+  SS_TRY(kf.alloc((size_t)nb * L.d, st));
+  SS_TRY(rot.alloc(std::max<int64_t>(g->n_terms, 1), st));
+  for (int i = 0; i < L.d; ++i) {
+    k_rotate_coef<<<nblk(g->n_terms), 256, 0, st>>>(g->freq, reinterpret_cast<const double2*>(g->coef), g->n_terms,
+                                                    L.d, i, Pp, rot.get());
+    SS_LAUNCH_CHECK();
+    const ss_trig gi{g->d, g->n_terms, g->freq, reinterpret_cast<const double*>(rot.get())};
+    SS_TRY(sample_into(P, L, &gi, P.samples.get(), st));
+    SS_TRY(exec_fft(P, P.samples.get(), st));
+    k_identify_coord<T2><<<nblk(nb), 256, 0, st>>>(spec, bins.get(), x0.get(), nb, L.d, i, Pp, kf.get());
+    SS_LAUNCH_CHECK();
+  }
+  k_identify_finish<<<nblk(nb), 256, 0, st>>>(kf.get(), bins.get(), x0.get(), nb, L, freq_out,
+                                              reinterpret_cast<double2*>(val_out), err.get());
+  SS_LAUNCH_CHECK();
+  int32_t herr = 0;
+  SS_CUDA(cudaMemcpyAsync(&herr, err.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  if (herr)
+    SS_FAIL(SS_ERR_NOT_RECONSTRUCTING, "sft_identify: a bin holds a frequency that does not map to it (collision)");
+  *n_out = n;
+  return SS_OK;
+}
+
 ss_status check_trig(const ss_trig* g, int d) {
   if (!g) SS_FAIL(SS_ERR_INVALID, "null trigonometric sum");
   if (g->d != d) SS_FAIL(SS_ERR_INVALID, "trigonometric sum has d = %d, lattice d = %d", g->d, d);
@@ -715,4 +880,22 @@ extern "C" ss_status sft_recover(const ss_lattice* lat, const ss_trig* g, ss_pre
   SS_TRY(get_plan(L.M, prec, st, &P));
   SS_TRY(sample_into(*P, L, g, P->samples.get(), st));
   return recover_from(*P, L, P->samples.get(), cand, n_cand, s_max, tau, freq_out, val_out, n_out, st);
+}
+
+extern "C" ss_status sft_identify(const ss_lattice* lat, const ss_trig* g, ss_precision prec, int32_t P,
+                                  int64_t s_max, double tau, int32_t* freq_out, double* val_out, int64_t* n_out,
+                                  void* stream) {
+  LatticeDev L;
+  SS_TRY(make_lattice_dev(lat, &L));
+  SS_TRY(check_trig(g, L.d));
+  if (!freq_out || !val_out || !n_out || s_max < 1) SS_FAIL(SS_ERR_INVALID, "sft_identify: bad argument");
+  if (P < 3) SS_FAIL(SS_ERR_INVALID, "sft_identify: P must be > 2 max |k_i| >= 3");
+  if (!(tau >= 0.0)) SS_FAIL(SS_ERR_INVALID, "sft_identify: tau must be >= 0");
+  if (prec != SS_FP64 && prec != SS_FP32) SS_FAIL(SS_ERR_INVALID, "sft_identify: bad precision");
+  cudaStream_t st = as_stream(stream);
+  std::shared_ptr<SftPlan> Pl;
+  SS_TRY(get_plan(L.M, prec, st, &Pl));
+  if (prec == SS_FP64)
+    return identify_impl<double2>(*Pl, L, g, P, s_max, tau, freq_out, val_out, n_out, st);
+  return identify_impl<float2>(*Pl, L, g, P, s_max, tau, freq_out, val_out, n_out, st);
 }
