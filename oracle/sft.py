@@ -127,24 +127,33 @@ def sample_shifted(freq, coef, z, M, P, i):
     return out
 
 
-def identify(freq, coef, z, M, P, tau=1e-9, s_max=None):
-    """Support identification of g = sum_t Re(c_t e_{p_t}) (see the module
-    header).  Returns (freq [n, d] int32, val [n]) with every kept bin's k
-    followed by -k (bin 0 alone), bins ascending."""
+def identify_samples(samples, z, M, P, tau=1e-9, s_max=None, keep=None, robust=False):
+    """Support identification from given samples: row 0 of ``samples`` holds
+    g(x_j), row i holds g(x_j + e_i / P) (i = 1..d).  Bins: the half
+    spectrum 0 <= b <= M/2 with |X_0[b]| > tau max |X_0|; with ``keep``, at
+    most that many, namely those strictly larger than the (keep+1)-th largest
+    magnitude (compressible data, Section "Compressible"-type inputs).
+    ``robust``: a bin whose identified k does not map back to it (aliasing of
+    the neglected tail, or a collision) is dropped instead of raising."""
     M, P = int(M), int(P)
-    d = np.asarray(freq).shape[1]
-    X0 = np.fft.fft(sample(freq, coef, z, M))
-    half = X0[: M // 2 + 1]
-    mag = np.abs(half)
+    samples = np.asarray(samples, np.float64)
+    d = samples.shape[0] - 1
+    X0 = np.fft.fft(samples[0])
+    mag = np.abs(X0[: M // 2 + 1])
     bins = np.nonzero(mag > tau * mag.max())[0]
+    if keep is not None and len(bins) > keep:
+        cut = np.sort(mag[bins])[::-1][keep]
+        bins = bins[mag[bins] > cut]
     ks = np.zeros((len(bins), d), np.int64)
     for i in range(d):
-        Xi = np.fft.fft(sample_shifted(freq, coef, z, M, P, i))
+        Xi = np.fft.fft(samples[i + 1])
         ang = np.angle(Xi[bins] / X0[bins])
         k = np.rint(P * ang / (2 * np.pi)).astype(np.int64) % P
         ks[:, i] = np.where(k > P // 2, k - P, k)
-    if np.any(residues(ks, z, M) != bins):
+    ok = residues(ks, z, M) == bins if len(bins) else np.zeros(0, bool)
+    if not robust and not np.all(ok):
         raise ValueError("identified frequency does not sit in its bin (collision)")
+    bins, ks = bins[ok], ks[ok]
     out_f, out_v = [], []
     for b, k in zip(bins.tolist(), ks):
         v = X0[b] / M
@@ -156,3 +165,12 @@ def identify(freq, coef, z, M, P, tau=1e-9, s_max=None):
     if s_max is not None and len(out_f) > s_max:
         raise ValueError("more terms above threshold than s_max")
     return np.array(out_f, np.int32).reshape(len(out_f), d), np.array(out_v, np.complex128)
+
+
+def identify(freq, coef, z, M, P, tau=1e-9, s_max=None):
+    """Support identification of g = sum_t Re(c_t e_{p_t}) (see the module
+    header).  Returns (freq [n, d] int32, val [n]) with every kept bin's k
+    followed by -k (bin 0 alone), bins ascending."""
+    d = np.asarray(freq).shape[1]
+    rows = [sample(freq, coef, z, M)] + [sample_shifted(freq, coef, z, M, P, i) for i in range(d)]
+    return identify_samples(np.stack(rows), z, M, P, tau=tau, s_max=s_max)

@@ -123,3 +123,52 @@ def test_identify_recovers_random_sparse_sums(seed):
     assert set(got) == set(true)
     for k in true:
         assert abs(got[k] - true[k]) < 1e-12
+
+
+def poisson_samples(k0, r, z, M, P):
+    """Samples of the Poisson kernel along k0, g(x) = (1 - r^2)/(1 - 2 r cos(2 pi k0.x) + r^2)
+    (coefficients r^|m| at m k0), on the lattice and the d shifted lattices,
+    phases k0.x taken as exact rationals."""
+    M, P = int(M), int(P)
+    j = np.arange(M, dtype=np.int64)
+    q = int(np.dot(k0, z) % M)
+    rows = []
+    for i in [None] + list(range(len(k0))):
+        num = ((j * q) % M) * P + (0 if i is None else int(k0[i]) * M)
+        th = 2 * np.pi * ((num % (M * P)) / (M * P))
+        rows.append((1 - r * r) / (1 - 2 * r * np.cos(th) + r * r))
+    return np.stack(rows)
+
+
+def test_identify_compressible_poisson_kernel():
+    # compressible data: the s largest coefficients r^|m| (m = 0, +-1, ...) are
+    # identified at the right frequencies; their values carry only the
+    # aliasing of the tail, sum over |m| >= M / |.| of r^|m|, below 1e-12 here
+    from oracle.sft import identify_samples
+    k0 = np.array([3, -2, 5])
+    z = np.array([1, 77, 340])
+    M, P, r, keep = 1021, 101, 0.5, 6
+    X = poisson_samples(k0, r, z, M, P)
+    f, v = identify_samples(X, z, M, P, tau=1e-12, keep=keep, robust=True)
+    got = {tuple(k): val for k, val in zip(f.tolist(), v)}
+    want = {tuple(m * k0): r ** abs(m) for m in range(-5, 6)}
+    assert set(got) == set(want)
+    for k in want:
+        assert abs(got[k] - want[k]) < 1e-12
+
+
+def test_identify_robust_drops_aliased_bins():
+    # with keep large enough to reach bins where the tail aliases, robust
+    # mode keeps only bins whose k maps back, and never raises
+    from oracle.sft import identify_samples
+    k0 = np.array([3, -2, 5])
+    z = np.array([1, 77, 340])
+    M, P, r = 1021, 101, 0.9
+    X = poisson_samples(k0, r, z, M, P)
+    f, v = identify_samples(X, z, M, P, tau=0.0, keep=200, robust=True)
+    assert len(f) > 0
+    assert len({tuple(k) for k in f.tolist()}) == len(f)        # no frequency twice
+    # every output frequency lies on the line m k0 with |m| < P/2
+    for k in f.tolist():
+        m = k[0] // 3
+        assert k == [3 * m, -2 * m, 5 * m]
