@@ -167,6 +167,18 @@ ss_status sft_recover(const ss_lattice* lat, const ss_trig* g, ss_precision prec
 ss_status sft_identify(const ss_lattice* lat, const ss_trig* g, ss_precision prec, int32_t P, int64_t s_max,
                        double tau, int32_t* freq_out, double* val_out, int64_t* n_out, void* stream);
 
+/* The same from given samples (black-box access to g):
+ * samples: device, (d + 1) rows of M reals in `prec`, row 0 = g(x_j), row i =
+ * g(x_j + e_i / P).  For compressible (not exactly sparse) data, keep > 0
+ * limits the bins to the keep largest magnitudes above the threshold (exact
+ * selection: values strictly above the (keep+1)-th largest, found by radix
+ * passes over their bit patterns), and robust != 0 drops the bins whose
+ * identified k does not map back to them (aliasing of the neglected tail)
+ * instead of failing.  keep = 0, robust = 0 is sft_identify's behaviour. */
+ss_status sft_identify_samples(const ss_lattice* lat, int32_t P, const void* samples, ss_precision prec,
+                               int64_t s_max, double tau, int64_t keep, int32_t robust, int32_t* freq_out,
+                               double* val_out, int64_t* n_out, void* stream);
+
 /* ------------------------------------------------------------------ stamp */
 
 /* S^N[a_hat](F) of eq. StampSet with F = f_freq (device [n_f][d], distinct,

@@ -69,6 +69,7 @@ def _load():
         "sft_recover_samples": (i32, [P(Lattice), vp, i32, vp, i64, i64, dbl, vp, vp, P(i64), vp]),
         "sft_recover": (i32, [P(Lattice), P(Trig), i32, vp, i64, i64, dbl, vp, vp, P(i64), vp]),
         "sft_identify": (i32, [P(Lattice), P(Trig), i32, i32, i64, dbl, vp, vp, P(i64), vp]),
+        "sft_identify_samples": (i32, [P(Lattice), i32, vp, i32, i64, dbl, i64, i32, vp, vp, P(i64), vp]),
         "stamp_build": (i32, [P(Sparse), vp, i64, i32, P(vp), vp]),
         "stamp_build_adr": (i32, [P(Sparse), P(Sparse), P(Sparse), vp, i64, i32, P(vp), vp]),
         "stamp_info": (i32, [vp, P(i64), P(i64), P(i64), P(i32)]),
@@ -246,6 +247,25 @@ def sft_identify(z, M, freq, coef, P, s_max, tau=1e-9, precision="fp64"):
     n = C.c_int64()
     _check(lib.sft_identify(C.byref(lat), C.byref(g), p, int(P), int(s_max), float(tau), _ptr(fo), _ptr(vo),
                             C.byref(n), _stream()))
+    return fo[: n.value], vo[: n.value]
+
+
+def sft_identify_samples(z, M, samples, P, s_max, tau=1e-9, keep=0, robust=False, precision="fp64"):
+    """Identification from given samples ((d+1) x M: the lattice, then the d
+    shifted lattices); keep / robust for compressible data."""
+    p = _prec(precision)
+    lat = _lattice(z, M)
+    d = len(z)
+    dt = torch.float64 if p == SS_FP64 else torch.float32
+    x = samples if torch.is_tensor(samples) else torch.as_tensor(np.asarray(samples))
+    x = x.to(device="cuda", dtype=dt).contiguous()
+    if x.shape != (d + 1, int(M)):
+        raise ValueError("samples must be (d + 1) x M")
+    fo = torch.empty((int(s_max), d), dtype=torch.int32, device="cuda")
+    vo = torch.empty(int(s_max), dtype=torch.complex128, device="cuda")
+    n = C.c_int64()
+    _check(lib.sft_identify_samples(C.byref(lat), int(P), _ptr(x), p, int(s_max), float(tau), int(keep),
+                                    int(bool(robust)), _ptr(fo), _ptr(vo), C.byref(n), _stream()))
     return fo[: n.value], vo[: n.value]
 
 

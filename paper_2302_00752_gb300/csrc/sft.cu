@@ -725,18 +725,28 @@ __global__ void k_identify_coord(const T2* __restrict__ spec, const int64_t* __r
   kf[t * d + i] = (int32_t)k;
 }
 
-// Each kept bin's k, then -k (bin 0 alone); a bin whose k does not reproduce
-// it (k.z mod M != b) is a collision.
-__global__ void k_identify_finish(const int32_t* __restrict__ kf, const int64_t* __restrict__ bins,
-                                  const double2* __restrict__ x0, int64_t nb, LatticeDev L, int32_t* fo, double2* vo,
-                                  int32_t* err) {
+// valid[t]: the identified k reproduces its bin (k.z mod M == b); otherwise
+// the bin holds an aliased tail or a collision.
+__global__ void k_identify_check(const int32_t* __restrict__ kf, const int64_t* __restrict__ bins, int64_t nb,
+                                 LatticeDev L, int32_t* valid, int32_t* err) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nb) return;
+  const bool ok = residue_of(kf + t * L.d, L.d, L) == bins[t];
+  valid[t] = ok ? 1 : 0;
+  if (!ok) atomicExch(err, 1);
+}
+
+// Each valid bin's k, then -k (bin 0 alone), in increasing bin order.
+__global__ void k_identify_write(const int32_t* __restrict__ kf, const int64_t* __restrict__ bins,
+                                 const double2* __restrict__ x0, const int32_t* __restrict__ valid,
+                                 const int32_t* __restrict__ vpos, int64_t nb, LatticeDev L, int32_t* fo,
+                                 double2* vo) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nb || !valid[t]) return;
   const int d = L.d;
   const int64_t b = bins[t];
-  if (residue_of(kf + t * d, d, L) != b) atomicExch(err, 1);
-  const int64_t z0 = bins[0] == 0 ? 1 : 0;
-  const int64_t o = t == 0 ? 0 : 2 * t - z0;
+  const int64_t z0 = (bins[0] == 0 && valid[0]) ? 1 : 0;
+  const int64_t o = b == 0 ? 0 : 2 * (int64_t)vpos[t] - z0;
   const double sc = 1.0 / (double)L.M;
   const double2 v = make_double2(x0[t].x * sc, x0[t].y * sc);
   for (int c = 0; c < d; ++c) fo[o * d + c] = kf[t * d + c];
@@ -745,6 +755,59 @@ __global__ void k_identify_finish(const int32_t* __restrict__ kf, const int64_t*
     for (int c = 0; c < d; ++c) fo[(o + 1) * d + c] = -kf[t * d + c];
     vo[o + 1] = make_double2(v.x, -v.y);
   }
+}
+
+// Exact selection of the `keep` largest magnitudes among the flagged bins:
+// the (keep+1)-th largest value is found digit by digit (eight 8-bit radix
+// passes over the magnitudes' bit patterns, which order like the values for
+// non-negative doubles), then only values strictly above it stay flagged.
+struct RadixState {
+  unsigned long long prefix, mask;
+  long long k;
+};
+
+template <typename T2>
+__global__ void k_mag_bits(const T2* __restrict__ spec, int64_t nh, unsigned long long* bits) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nh) return;
+  bits[b] = (unsigned long long)__double_as_longlong(hypot((double)spec[b].x, (double)spec[b].y));
+}
+
+__global__ void k_radix_hist(const unsigned long long* __restrict__ bits, const int32_t* __restrict__ flag, int64_t nh,
+                             const RadixState* __restrict__ st, int shift, unsigned int* hist) {
+  __shared__ unsigned int sh[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const unsigned long long prefix = st->prefix, mask = st->mask;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nh; b += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long v = bits[b];
+    if (flag[b] && (v & mask) == prefix) atomicAdd(&sh[(v >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (sh[i]) atomicAdd(hist + i, sh[i]);
+}
+
+__global__ void k_radix_pick(RadixState* st, int shift, unsigned int* hist) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  long long cum = 0;
+  for (int dgt = 255; dgt >= 0; --dgt) {
+    if (cum + (long long)hist[dgt] >= st->k) {
+      st->prefix |= (unsigned long long)dgt << shift;
+      st->mask |= 255ull << shift;
+      st->k -= cum;
+      break;
+    }
+    cum += hist[dgt];
+  }
+  for (int i = 0; i < 256; ++i) hist[i] = 0;
+}
+
+__global__ void k_radix_cut(const unsigned long long* __restrict__ bits, int64_t nh, const RadixState* __restrict__ st,
+                            int32_t* flag) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nh) return;
+  if (flag[b] && bits[b] <= st->prefix) flag[b] = 0;
 }
 
 ss_status exec_fft(const SftPlan& P, const void* samples, cudaStream_t st) {
@@ -760,9 +823,12 @@ ss_status exec_fft(const SftPlan& P, const void* samples, cudaStream_t st) {
   return SS_OK;
 }
 
-template <typename T2>
-ss_status identify_impl(const SftPlan& P, const LatticeDev& L, const ss_trig* g, int Pp, int64_t s_max, double tau,
-                        int32_t* freq_out, double* val_out, int64_t* n_out, cudaStream_t st) {
+// Rows of the identification: row(i) leaves the samples of row i (0: the
+// lattice, i >= 1: the lattice shifted by e_i / P) in device memory and
+// returns them.
+template <typename T2, class Rows>
+ss_status identify_impl(const SftPlan& P, const LatticeDev& L, Rows row, int Pp, int64_t s_max, int64_t keep,
+                        bool robust, double tau, int32_t* freq_out, double* val_out, int64_t* n_out, cudaStream_t st) {
   const int64_t nh = L.M / 2 + 1;
   const T2* spec = reinterpret_cast<const T2*>(P.spectrum.get());
   DevBuf<unsigned long long> maxbits;
@@ -774,8 +840,9 @@ ss_status identify_impl(const SftPlan& P, const LatticeDev& L, const ss_trig* g,
   SS_TRY(pos.alloc(nh, st));
   SS_TRY(total.alloc(1, st));
   SS_TRY(err.alloc(1, st));
-  SS_TRY(sample_into(P, L, g, P.samples.get(), st));
-  SS_TRY(exec_fft(P, P.samples.get(), st));
+  const void* r0 = nullptr;
+  SS_TRY(row(0, &r0));
+  SS_TRY(exec_fft(P, r0, st));
   SS_CUDA(cudaMemsetAsync(maxbits.get(), 0, sizeof(unsigned long long), st));
   SS_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), st));
   const unsigned gmax = (unsigned)std::min<int64_t>(nblk(nh), 4 * 152);
@@ -784,44 +851,71 @@ ss_status identify_impl(const SftPlan& P, const LatticeDev& L, const ss_trig* g,
   SS_LAUNCH_CHECK();
   SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), nh, total.get(), st));
   int64_t nb = 0;
-  int32_t keep0 = 0;
   SS_CUDA(cudaMemcpyAsync(&nb, total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaMemcpyAsync(&keep0, flag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   SS_CUDA(cudaStreamSynchronize(st));
-  const int64_t n = 2 * nb - (keep0 ? 1 : 0);
+  if (keep > 0 && nb > keep) {
+    DevBuf<unsigned long long> bits;
+    DevBuf<unsigned int> hist;
+    DevBuf<RadixState> rs;
+    SS_TRY(bits.alloc(nh, st));
+    SS_TRY(hist.alloc(256, st));
+    SS_TRY(rs.alloc(1, st));
+    const RadixState init{0ull, 0ull, (long long)keep + 1};
+    SS_CUDA(cudaMemcpyAsync(rs.get(), &init, sizeof(init), cudaMemcpyHostToDevice, st));
+    SS_CUDA(cudaMemsetAsync(hist.get(), 0, 256 * sizeof(unsigned int), st));
+    k_mag_bits<T2><<<nblk(nh), 256, 0, st>>>(spec, nh, bits.get());
+    for (int shift = 56; shift >= 0; shift -= 8) {
+      k_radix_hist<<<gmax, 256, 0, st>>>(bits.get(), flag.get(), nh, rs.get(), shift, hist.get());
+      k_radix_pick<<<1, 32, 0, st>>>(rs.get(), shift, hist.get());
+    }
+    k_radix_cut<<<nblk(nh), 256, 0, st>>>(bits.get(), nh, rs.get(), flag.get());
+    SS_LAUNCH_CHECK();
+    SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), nh, total.get(), st));
+    SS_CUDA(cudaMemcpyAsync(&nb, total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SS_CUDA(cudaStreamSynchronize(st));
+  }
   if (nb == 0) {
     *n_out = 0;
     return SS_OK;
   }
-  if (s_max > 0 && n > s_max)
-    SS_FAIL(SS_ERR_INVALID, "sft_identify: %lld terms above threshold exceed s_max = %lld", (long long)n,
-            (long long)s_max);
+  if (!robust && s_max > 0 && 2 * nb - 1 > s_max)
+    SS_FAIL(SS_ERR_INVALID, "sft_identify: at least %lld terms above threshold exceed s_max = %lld",
+            (long long)(2 * nb - 1), (long long)s_max);
   SS_TRY(bins.alloc(nb, st));
   SS_TRY(x0.alloc(nb, st));
   k_spec_compact<T2><<<nblk(nh), 256, 0, st>>>(spec, nh, flag.get(), pos.get(), bins.get(), x0.get());
   SS_LAUNCH_CHECK();
-  DevBuf<int32_t> kf;
-  DevBuf<double2> rot;
+  DevBuf<int32_t> kf, valid, vpos;
   SS_TRY(kf.alloc((size_t)nb * L.d, st));
-  SS_TRY(rot.alloc(std::max<int64_t>(g->n_terms, 1), st));
+  SS_TRY(valid.alloc(nb, st));
+  SS_TRY(vpos.alloc(nb, st));
   for (int i = 0; i < L.d; ++i) {
-    k_rotate_coef<<<nblk(g->n_terms), 256, 0, st>>>(g->freq, reinterpret_cast<const double2*>(g->coef), g->n_terms,
-                                                    L.d, i, Pp, rot.get());
-    SS_LAUNCH_CHECK();
-    const ss_trig gi{g->d, g->n_terms, g->freq, reinterpret_cast<const double*>(rot.get())};
-    SS_TRY(sample_into(P, L, &gi, P.samples.get(), st));
-    SS_TRY(exec_fft(P, P.samples.get(), st));
+    const void* ri = nullptr;
+    SS_TRY(row(i + 1, &ri));
+    SS_TRY(exec_fft(P, ri, st));
     k_identify_coord<T2><<<nblk(nb), 256, 0, st>>>(spec, bins.get(), x0.get(), nb, L.d, i, Pp, kf.get());
     SS_LAUNCH_CHECK();
   }
-  k_identify_finish<<<nblk(nb), 256, 0, st>>>(kf.get(), bins.get(), x0.get(), nb, L, freq_out,
-                                              reinterpret_cast<double2*>(val_out), err.get());
+  k_identify_check<<<nblk(nb), 256, 0, st>>>(kf.get(), bins.get(), nb, L, valid.get(), err.get());
   SS_LAUNCH_CHECK();
-  int32_t herr = 0;
+  SS_TRY(exclusive_scan_i32(valid.get(), vpos.get(), nb, total.get(), st));
+  int64_t nv = 0;
+  int32_t herr = 0, z0 = 0;
+  int64_t b0 = -1;
+  SS_CUDA(cudaMemcpyAsync(&nv, total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   SS_CUDA(cudaMemcpyAsync(&herr, err.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaMemcpyAsync(&b0, bins.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaMemcpyAsync(&z0, valid.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   SS_CUDA(cudaStreamSynchronize(st));
-  if (herr)
+  if (herr && !robust)
     SS_FAIL(SS_ERR_NOT_RECONSTRUCTING, "sft_identify: a bin holds a frequency that does not map to it (collision)");
+  const int64_t n = 2 * nv - ((b0 == 0 && z0) ? 1 : 0);
+  if (s_max > 0 && n > s_max)
+    SS_FAIL(SS_ERR_INVALID, "sft_identify: %lld terms exceed s_max = %lld", (long long)n, (long long)s_max);
+  k_identify_write<<<nblk(nb), 256, 0, st>>>(kf.get(), bins.get(), x0.get(), valid.get(), vpos.get(), nb, L, freq_out,
+                                             reinterpret_cast<double2*>(val_out));
+  SS_LAUNCH_CHECK();
+  SS_CUDA(cudaStreamSynchronize(st));
   *n_out = n;
   return SS_OK;
 }
@@ -895,7 +989,51 @@ extern "C" ss_status sft_identify(const ss_lattice* lat, const ss_trig* g, ss_pr
   cudaStream_t st = as_stream(stream);
   std::shared_ptr<SftPlan> Pl;
   SS_TRY(get_plan(L.M, prec, st, &Pl));
+  DevBuf<double2> rot;
+  SS_TRY(rot.alloc(std::max<int64_t>(g->n_terms, 1), st));
+  const SftPlan& PP = *Pl;
+  // row 0: g on the lattice; row i: the coefficients turned by exp(2 pi i p_i / P)
+  auto rows = [&](int i, const void** out) -> ss_status {
+    if (i == 0) {
+      SS_TRY(sample_into(PP, L, g, PP.samples.get(), st));
+    } else {
+      k_rotate_coef<<<nblk(g->n_terms), 256, 0, st>>>(g->freq, reinterpret_cast<const double2*>(g->coef),
+                                                      g->n_terms, L.d, i - 1, P, rot.get());
+      SS_LAUNCH_CHECK();
+      const ss_trig gi{g->d, g->n_terms, g->freq, reinterpret_cast<const double*>(rot.get())};
+      SS_TRY(sample_into(PP, L, &gi, PP.samples.get(), st));
+    }
+    *out = PP.samples.get();
+    return SS_OK;
+  };
   if (prec == SS_FP64)
-    return identify_impl<double2>(*Pl, L, g, P, s_max, tau, freq_out, val_out, n_out, st);
-  return identify_impl<float2>(*Pl, L, g, P, s_max, tau, freq_out, val_out, n_out, st);
+    return identify_impl<double2>(PP, L, rows, P, s_max, 0, false, tau, freq_out, val_out, n_out, st);
+  return identify_impl<float2>(PP, L, rows, P, s_max, 0, false, tau, freq_out, val_out, n_out, st);
+}
+
+extern "C" ss_status sft_identify_samples(const ss_lattice* lat, int32_t P, const void* samples, ss_precision prec,
+                                          int64_t s_max, double tau, int64_t keep, int32_t robust, int32_t* freq_out,
+                                          double* val_out, int64_t* n_out, void* stream) {
+  LatticeDev L;
+  SS_TRY(make_lattice_dev(lat, &L));
+  if (!samples || !freq_out || !val_out || !n_out || s_max < 1 || keep < 0)
+    SS_FAIL(SS_ERR_INVALID, "sft_identify_samples: bad argument");
+  if (P < 3) SS_FAIL(SS_ERR_INVALID, "sft_identify_samples: P must be > 2 max |k_i| >= 3");
+  if (!(tau >= 0.0)) SS_FAIL(SS_ERR_INVALID, "sft_identify_samples: tau must be >= 0");
+  if (prec != SS_FP64 && prec != SS_FP32) SS_FAIL(SS_ERR_INVALID, "sft_identify_samples: bad precision");
+  cudaStream_t st = as_stream(stream);
+  std::shared_ptr<SftPlan> Pl;
+  SS_TRY(get_plan(L.M, prec, st, &Pl));
+  const size_t es = prec == SS_FP64 ? sizeof(double) : sizeof(float);
+  // rows are copied into the plan's aligned sample buffer (cuFFT's real input
+  // wants more than element alignment, and row i starts at i * M elements)
+  auto rows = [&](int i, const void** out) -> ss_status {
+    SS_CUDA(cudaMemcpyAsync(Pl->samples.get(), static_cast<const unsigned char*>(samples) + (size_t)i * (size_t)L.M * es,
+                            (size_t)L.M * es, cudaMemcpyDeviceToDevice, st));
+    *out = Pl->samples.get();
+    return SS_OK;
+  };
+  if (prec == SS_FP64)
+    return identify_impl<double2>(*Pl, L, rows, P, s_max, keep, robust != 0, tau, freq_out, val_out, n_out, st);
+  return identify_impl<float2>(*Pl, L, rows, P, s_max, keep, robust != 0, tau, freq_out, val_out, n_out, st);
 }
