@@ -144,9 +144,16 @@ __device__ __forceinline__ double warp_reduce(double v) {
   return v;
 }
 
-// Lane accumulators of run_phase: FP64, or double-float for the DF64 CG (kept
-// on the FP32 pipe, converted to FP64 once per warp fold).
+// Lane accumulators of run_phase: FP64; double-float for the DF64 CG and FP32
+// for the FP32 inner solve (kept on the FP32 pipe, converted to FP64 once per
+// warp fold).
 __device__ __forceinline__ void acc_add(double& a, double b) { a += b; }
+__device__ __forceinline__ void acc_add(float& a, float b) { a += b; }
+__device__ __forceinline__ double acc_fold(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return (double)v;
+}
 __device__ __forceinline__ void acc_add(DF& a, DF b) { a = df_add(a, b); }
 __device__ __forceinline__ double acc_fold(double v) { return warp_reduce(v); }
 __device__ __forceinline__ double acc_fold(DF v) { return df_to_double(df_warp_sum(v)); }
@@ -643,19 +650,21 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
     if (block_counter(P, 0) >= P.n_inst) break;
     // inner CG on the FP32 operator with FP32 vectors; inner products are
     // formed per row in FP32 and reduced in FP64, scalars stay FP64
+    // the inner products of the FP32 inner solve (relative tolerance 1e-5)
+    // are summed in FP32 per lane and in FP64 from the warp fold on
     auto phase_y = [&](int par) {
-      run_phase(P, sm, 0b0111u, [&](int, const Chunk&, int k, int i, bool, int lane) {
+      run_phase<float>(P, sm, 0b0111u, [&](int, const Chunk&, int k, int i, bool, int lane) {
         if (lane == 0) sm.flag[k] = __ldcg(&P.state[i].inn[par]);
-      }, [&](int64_t g, int64_t s, int lane, int i, int k, double* v) {
+      }, [&](int64_t g, int64_t s, int lane, int i, int k, float* v) {
         if (!sm.flag[k]) return;
         const SolveInst& in = P.inst[i];
         const float2 w = apply32_row(P, in, s, lane, g);
         const float4 u = P.urec32[g];
         const float2 r = P.r32[g];
         P.w32[g] = w;
-        v[0] = (double)(r.x * u.x + r.y * u.y);
-        v[1] = (double)(w.x * u.x + w.y * u.y);
-        v[2] = (double)(r.x * r.x + r.y * r.y);
+        v[0] = r.x * u.x + r.y * u.y;
+        v[1] = w.x * u.x + w.y * u.y;
+        v[2] = r.x * r.x + r.y * r.y;
       });
     };
     phase_y(0);
