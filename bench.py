@@ -497,6 +497,18 @@ def batched_section(B, flush, n_inst=512, reps=3, world=1, rank=0):
         b.record()
         b.synchronize()
         lt.append(a.elapsed_time(b))
+    # the same batch in the plain FP64 form (graph, same tiles), for comparison
+    batch.solve(fs, us, tol=1e-12, max_iter=500, precision="fp64", use_graph=True)
+    ft = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        _, stats64 = batch.solve(fs, us, tol=1e-12, max_iter=500, precision="fp64", use_graph=True)
+        b.record()
+        b.synchronize()
+        ft.append(a.elapsed_time(b))
+    fp64_ok = all(st["status"] == "SS_OK" for st in stats64)
     applies = sum(st["applies"] for st in stats)
     nnz_applied = sum(s.nnz * st["applies"] for s, st in zip(stamps, stats))
     ok = all(st["status"] == "SS_OK" for st in stats)
@@ -515,7 +527,9 @@ def batched_section(B, flush, n_inst=512, reps=3, world=1, rank=0):
            "total_rows_rank0": int(sum(sizes)), "total_nnz_rank0": int(sum(s.nnz for s in stamps)),
            "persistent_graph_ms": t_b, "loop_of_single_solves_ms": t_l,
            "speedup": t_l / t_b, "nnz_per_s": nnz_applied / (t_b / 1e3), "applies_rank0": applies,
-           "all_converged": ok, "autotuned": cfg, "autotune_best_ms": best_ms, "setup_s": setup_s}
+           "all_converged": ok, "autotuned": cfg, "autotune_best_ms": best_ms, "setup_s": setup_s,
+           "fp64_persistent_graph_ms_rank0": statistics.median(ft), "fp64_all_converged_rank0": fp64_ok,
+           "fp32_refined_vs_fp64_speedup_rank0": statistics.median(ft) / statistics.median(bt)}
     batch.destroy()
     for s in stamps:
         s.destroy()

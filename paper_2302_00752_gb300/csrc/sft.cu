@@ -28,6 +28,18 @@
 namespace ss {
 namespace {
 
+// (a b) mod M for a, b < M < 2^31 without a 64-bit division in the inner
+// loops: Barrett reduction with inv = floor((2^64 - 1) / M); the quotient
+// estimate __umul64hi(a b, inv) is at most two below floor(a b / M).
+__device__ __forceinline__ uint32_t mulmod(uint64_t a, uint64_t b, uint64_t M, uint64_t inv) {
+  const uint64_t x = a * b;
+  uint64_t r = x - __umul64hi(x, inv) * M;
+  r = r >= M ? r - M : r;
+  r = r >= M ? r - M : r;
+  return (uint32_t)r;
+}
+
+
 constexpr int kSampThreads = 256;
 constexpr int kSampPerThread = 8;
 constexpr int kTermChunk = 256;
@@ -140,6 +152,7 @@ __global__ void __launch_bounds__(kSampThreads) k_sample32(int64_t M, int64_t n2
   const int64_t n_terms = *n_terms_dev;
   const uint32_t mask = kT3Size - 1;
   const int64_t j0 = (int64_t)blockIdx.x * (kSampThreads * kSampPerThread) + threadIdx.x;
+  const uint64_t inv = ~0ull / (uint64_t)M;   // once per thread (Barrett constant of mulmod)
   float acc[kSampPerThread];
 #pragma unroll
   for (int m = 0; m < kSampPerThread; ++m) acc[m] = 0.f;
@@ -154,7 +167,7 @@ __global__ void __launch_bounds__(kSampThreads) k_sample32(int64_t M, int64_t n2
     for (int i = threadIdx.x; i < tc * kSampPerThread; i += blockDim.x) s_w[i] = W[t0 * kSampPerThread + i];
     __syncthreads();
     for (int t = 0; t < tc; ++t) {
-      const uint32_t r0 = (uint32_t)(((uint64_t)j0 * (uint64_t)s_q[t]) % (uint64_t)M);
+      const uint32_t r0 = mulmod((uint64_t)j0, s_q[t], (uint64_t)M, inv);
       const float2 e = cmulf(cmulf(s_t2[r0 >> (2 * kT3Bits)], s_t1[(r0 >> kT3Bits) & mask]), s_t0[r0 & mask]);
       const float2 b = cmulf(s_c[t], e);
       const float2* w = s_w + t * kSampPerThread;
@@ -183,6 +196,7 @@ __global__ void __launch_bounds__(kSampThreads) k_sample_df(int64_t M, const flo
   __shared__ float4 s_w[kTermChunk * kSampPerThread];
   const int64_t n_terms = *n_terms_dev;
   const int64_t j0 = (int64_t)blockIdx.x * (kSampThreads * kSampPerThread) + threadIdx.x;
+  const uint64_t inv = ~0ull / (uint64_t)M;   // once per thread (Barrett constant of mulmod)
   DF acc[kSampPerThread];
 #pragma unroll
   for (int m = 0; m < kSampPerThread; ++m) acc[m] = DF{0.f, 0.f};
@@ -198,7 +212,7 @@ __global__ void __launch_bounds__(kSampThreads) k_sample_df(int64_t M, const flo
     for (int i = threadIdx.x; i < tc * kSampPerThread; i += blockDim.x) s_w[i] = W[t0 * kSampPerThread + i];
     __syncthreads();
     for (int t = 0; t < tc; ++t) {
-      const uint32_t r0 = (uint32_t)(((uint64_t)j0 * (uint64_t)s_q[t]) % (uint64_t)M);
+      const uint32_t r0 = mulmod((uint64_t)j0, s_q[t], (uint64_t)M, inv);
       const float4 e = __ldg(tab + r0);
       const float4 c = s_c[t];
       // B = c e (double-float complex product)
@@ -332,6 +346,7 @@ __global__ void __launch_bounds__(kSampThreads) k_sample(int64_t M, int bl, int6
   const T2* hi = TAB == 0 ? s_hi : hi_g;
   const uint32_t lmask = (uint32_t)(L - 1);
   const int64_t j0 = (int64_t)blockIdx.x * (kSampThreads * kSampPerThread) + threadIdx.x;
+  const uint64_t inv = ~0ull / (uint64_t)M;   // once per thread (Barrett constant of mulmod)
   R acc[kSampPerThread];
 #pragma unroll
   for (int m = 0; m < kSampPerThread; ++m) acc[m] = (R)0;
@@ -348,7 +363,7 @@ __global__ void __launch_bounds__(kSampThreads) k_sample(int64_t M, int bl, int6
     __syncthreads();
     for (int t = 0; t < tc; ++t) {
       const uint32_t st = (uint32_t)s_step[t];
-      uint32_t r = (uint32_t)(((uint64_t)j0 * (uint64_t)s_q[t]) % (uint64_t)M);
+      uint32_t r = mulmod((uint64_t)j0, (uint64_t)s_q[t], (uint64_t)M, inv);
       const T2 c = s_c[t];
       if (TAB == 2) {
         uint32_t rr[kSampPerThread];
