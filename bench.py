@@ -218,13 +218,15 @@ def fp64_peak_gflops(sm_mhz):
     return 152 * 2 * sm_mhz * 1e6 / 1e9
 
 
-def d100_section(B, gp, flush, steps=2):
-    """The d = 100 workload: FP32 samples and FFT at M = 2^26 + 15, |S| = 1.15e6,
+def d100_section(B, gp, flush, steps=2, smooth=False):
+    """The d = 100 workload: FP32 samples and FFT at M = 2^26 + 15 (prime; with
+    smooth=True the 7-smooth M = 2^26, no Bluestein chirp), |S| = 1.15e6,
     FP32-refined solve.  Times the whole path and its stages."""
     import torch
-    inst = W.make_cfg5()
+    inst = W.make_cfg5(smooth=smooth)
     prep = gp.prepare(inst)
-    out = {"workload": "cfg5: d=100, s_a=41, 50 f pairs, N=3, FP32 sampling/FFT, FP32-refined solve"}
+    out = {"workload": "cfg5: d=100, s_a=41, 50 f pairs, N=3, FP32 sampling/FFT, FP32-refined solve"
+                       + (", 7-smooth M" if smooth else ", prime M")}
     times = []
     for it in range(steps + 1):
         flush.zero_()
@@ -692,6 +694,10 @@ def main():
                 extra["d100"] = d100_section(B, gp, flush)
             except Exception as e:  # reported, not hidden
                 extra["d100"] = {"error": repr(e)}
+            try:
+                extra["d100_smooth_M"] = d100_section(B, gp, flush, smooth=True)
+            except Exception as e:
+                extra["d100_smooth_M"] = {"error": repr(e)}
             try:
                 extra["apply"] = apply_section(B, gp, flush, load_peaks())
             except Exception as e:

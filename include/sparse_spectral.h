@@ -112,6 +112,16 @@ ss_status lattice_random(const int32_t* freq, int64_t n, int32_t d, double sigma
                          const int64_t* raw, int32_t attempts, int64_t* z_out, int64_t* M_out,
                          int32_t* attempt_out, void* stream);
 
+/* lattice_random with an FFT-friendly size: M = the smallest 7-smooth integer
+ * (prime factors 2, 3, 5, 7) >= max(K + 1, |I|^2 / sigma, M_min), then the
+ * same draws.  Lemma RandomRank1Lattice's probability bound is for prime M;
+ * here the exact reconstructing check of every draw stands in for it (a draw
+ * that fails is skipped), so the result is as reliable and the length-M FFT
+ * needs no Bluestein chirp. */
+ss_status lattice_random_smooth(const int32_t* freq, int64_t n, int32_t d, double sigma, int64_t M_min,
+                                const int64_t* raw, int32_t attempts, int64_t* z_out, int64_t* M_out,
+                                int32_t* attempt_out, void* stream);
+
 /* Component-by-component lattice (named in Section "Improvements with
  * randomized lattices"; criterion not given by the paper): M = smallest
  * 7-smooth integer (prime factors 2, 3, 5, 7: a mixed-radix FFT length)

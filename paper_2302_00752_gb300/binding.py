@@ -64,6 +64,7 @@ def _load():
         "lattice_size": (i32, [i64, i64, dbl, i64, P(i64)]),
         "lattice_check": (i32, [P(Lattice), vp, i64, vp]),
         "lattice_random": (i32, [vp, i64, i32, dbl, i64, P(i64), i32, P(i64), P(i64), P(i32), vp]),
+        "lattice_random_smooth": (i32, [vp, i64, i32, dbl, i64, P(i64), i32, P(i64), P(i64), P(i32), vp]),
         "lattice_cbc": (i32, [vp, i64, i32, i64, P(i64), i32, P(i64), P(i64), vp]),
         "lattice_sample": (i32, [P(Lattice), P(Trig), i32, vp, vp]),
         "sft_recover_samples": (i32, [P(Lattice), vp, i32, vp, i64, i64, dbl, vp, vp, P(i64), vp]),
@@ -163,16 +164,18 @@ def lattice_check(z, M, freq):
     _check(lib.lattice_check(C.byref(lat), _ptr(f), f.shape[0], _stream()))
 
 
-def lattice_random(freq, raw, sigma=0.05, M_min=0):
+def lattice_random(freq, raw, sigma=0.05, M_min=0, smooth=False):
+    """Random rank-1 lattice (Lemma RandomRank1Lattice): prime M, or with
+    smooth=True the FFT-friendly 7-smooth M (lattice_random_smooth)."""
     raw = np.ascontiguousarray(np.asarray(raw, dtype=np.int64))
     attempts, d = raw.shape
     f = _dev_i32(freq, d)
     z = (C.c_int64 * d)()
     M = C.c_int64()
     att = C.c_int32()
-    _check(lib.lattice_random(_ptr(f), f.shape[0], d, float(sigma), int(M_min),
-                              raw.ctypes.data_as(C.POINTER(C.c_int64)), attempts, z, C.byref(M), C.byref(att),
-                              _stream()))
+    fn = lib.lattice_random_smooth if smooth else lib.lattice_random
+    _check(fn(_ptr(f), f.shape[0], d, float(sigma), int(M_min), raw.ctypes.data_as(C.POINTER(C.c_int64)), attempts,
+              z, C.byref(M), C.byref(att), _stream()))
     return np.array(z[:], dtype=np.int64), M.value, att.value
 
 

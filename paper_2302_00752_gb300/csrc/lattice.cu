@@ -318,15 +318,13 @@ extern "C" ss_status lattice_check(const ss_lattice* lat, const int32_t* freq, i
   return check_reconstructing(freq, n, L, res.get(), false, st);
 }
 
-extern "C" ss_status lattice_random(const int32_t* freq, int64_t n, int32_t d, double sigma, int64_t M_min,
-                                    const int64_t* raw, int32_t attempts, int64_t* z_out, int64_t* M_out,
-                                    int32_t* attempt_out, void* stream) {
-  if (!freq || !raw || !z_out || !M_out || d < 1 || d > kMaxLatticeDim || attempts < 1)
-    SS_FAIL(SS_ERR_INVALID, "lattice_random: bad argument");
-  cudaStream_t st = as_stream(stream);
-  int64_t K = 0, M = 0;
-  SS_TRY(expansion_of(freq, n, d, &K, st));
-  SS_TRY(lattice_size(K, n, sigma, M_min, &M));
+namespace ss {
+namespace {
+
+// The first of `attempts` draws z_c = 1 + raw[a][c] mod (M - 1) that is
+// reconstructing for freq (exact check).
+ss_status random_draws(const int32_t* freq, int64_t n, int32_t d, int64_t M, const int64_t* raw, int32_t attempts,
+                       int64_t* z_out, int32_t* attempt_out, cudaStream_t st) {
   DevBuf<int64_t> res;
   SS_TRY(res.alloc(n, st));
   std::vector<int64_t> z(d);
@@ -343,7 +341,6 @@ extern "C" ss_status lattice_random(const int32_t* freq, int64_t n, int32_t d, d
     ss_status s = check_reconstructing(freq, n, L, res.get(), false, st);
     if (s == SS_OK) {
       for (int c = 0; c < d; ++c) z_out[c] = z[c];
-      *M_out = M;
       if (attempt_out) *attempt_out = a;
       return SS_OK;
     }
@@ -351,6 +348,40 @@ extern "C" ss_status lattice_random(const int32_t* freq, int64_t n, int32_t d, d
   }
   SS_FAIL(SS_ERR_NOT_RECONSTRUCTING, "lattice_random: no reconstructing draw among %d attempts (M = %lld)", attempts,
           (long long)M);
+}
+
+}  // namespace
+}  // namespace ss
+
+extern "C" ss_status lattice_random(const int32_t* freq, int64_t n, int32_t d, double sigma, int64_t M_min,
+                                    const int64_t* raw, int32_t attempts, int64_t* z_out, int64_t* M_out,
+                                    int32_t* attempt_out, void* stream) {
+  if (!freq || !raw || !z_out || !M_out || d < 1 || d > kMaxLatticeDim || attempts < 1)
+    SS_FAIL(SS_ERR_INVALID, "lattice_random: bad argument");
+  cudaStream_t st = as_stream(stream);
+  int64_t K = 0, M = 0;
+  SS_TRY(expansion_of(freq, n, d, &K, st));
+  SS_TRY(lattice_size(K, n, sigma, M_min, &M));
+  SS_TRY(random_draws(freq, n, d, M, raw, attempts, z_out, attempt_out, st));
+  *M_out = M;
+  return SS_OK;
+}
+
+extern "C" ss_status lattice_random_smooth(const int32_t* freq, int64_t n, int32_t d, double sigma, int64_t M_min,
+                                           const int64_t* raw, int32_t attempts, int64_t* z_out, int64_t* M_out,
+                                           int32_t* attempt_out, void* stream) {
+  if (!freq || !raw || !z_out || !M_out || d < 1 || d > kMaxLatticeDim || attempts < 1 || !(sigma > 0.0) ||
+      sigma >= 1.0)
+    SS_FAIL(SS_ERR_INVALID, "lattice_random_smooth: bad argument");
+  cudaStream_t st = as_stream(stream);
+  int64_t K = 0;
+  SS_TRY(expansion_of(freq, n, d, &K, st));
+  const double bound = std::max({(double)K + 1.0, std::ceil((double)n * (double)n / sigma), (double)M_min, 2.0});
+  if (bound >= 2147483647.0) SS_FAIL(SS_ERR_INVALID, "lattice_random_smooth: M would exceed 2^31");
+  const int64_t M = next_smooth_host((int64_t)bound);
+  SS_TRY(random_draws(freq, n, d, M, raw, attempts, z_out, attempt_out, st));
+  *M_out = M;
+  return SS_OK;
 }
 
 extern "C" ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int64_t M_min, const int64_t* raw,

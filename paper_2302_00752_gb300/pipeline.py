@@ -52,7 +52,8 @@ def choose_lattice(lat_spec, cand):
         return np.asarray(lat_spec["z"], np.int64), int(lat_spec["M"])
     if lat_spec["kind"] == "cbc":
         return B.lattice_cbc(cand, lat_spec["raw"], lat_spec["M_min"])
-    z, M, _ = B.lattice_random(cand, lat_spec["raw"], lat_spec["sigma"], lat_spec["M_min"])
+    z, M, _ = B.lattice_random(cand, lat_spec["raw"], lat_spec["sigma"], lat_spec["M_min"],
+                               smooth=lat_spec.get("smooth", False))
     return z, M
 
 

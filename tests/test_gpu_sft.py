@@ -138,3 +138,18 @@ def test_recover_cfg5_fp32_sampled(B):
     g = B.lattice_sample(z, M, inst.a.freq, inst.a.coef, "fp32").double().cpu().numpy()
     ref = osft.sample(inst.a.freq, inst.a.coef, z, M, js)
     assert np.abs(g[js] - ref).max() <= 2e-6 * np.abs(inst.a.coef).sum()
+
+
+def test_random_lattice_smooth_size(B):
+    # 7-smooth M >= the Lemma's bound, reconstructing (exact check) for I
+    from oracle import lattice as olat
+    inst = W.make_cfg3()
+    rng = np.random.default_rng(3)
+    I = np.unique(rng.integers(-40, 41, size=(60, 3)), axis=0)
+    I = np.unique(np.vstack([I, -I]), axis=0)
+    raw = rng.integers(0, 2**62, size=(16, 3), dtype=np.int64)
+    z, M, att = B.lattice_random(I, raw, sigma=0.05, M_min=1000, smooth=True)
+    assert olat.is_smooth(M) and M >= max(len(I) ** 2 / 0.05, 1000)
+    assert M == olat.next_smooth(int(max(np.ceil(len(I) ** 2 / 0.05), olat.expansion(I) + 1, 1000)))
+    assert olat.is_reconstructing(I, z, M)
+    assert np.array_equal(z, 1 + raw[att] % (M - 1))

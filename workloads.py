@@ -219,10 +219,11 @@ def make_cfg3(seed=0):
                     "fp32_refined", "fp64", None, (seed,))
 
 
-def make_cfg5(seed=0):
+def make_cfg5(seed=0, smooth=False):
     """d=100, 20 cosines with 3 nonzero coordinates in [-4,4] (sum|c| = 0.5),
     f with 50 +-pairs of the same form, N=3, random lattice with M the
-    smallest prime >= 2^26, FP32 samples and FFT, FP32-refined solve."""
+    smallest prime >= 2^26 (smooth=True: the smallest 7-smooth M >= 2^26, i.e.
+    2^26), FP32 samples and FFT, FP32-refined solve."""
     rng = np.random.default_rng(seed)
     d = 100
     p, _ = draw_sparse_freqs(rng, 20, d, 3, -4, 4)
@@ -230,6 +231,7 @@ def make_cfg5(seed=0):
     q, _ = draw_sparse_freqs(rng, 50, d, 3, -4, 4)
     f = random_cos_sin(rng, q)
     lat = random_lattice_draws(rng, d, M_min=2**26)
+    lat["smooth"] = bool(smooth)
     return Instance("cfg5_d100_fp32ir", d, 3, a, f, None, None, lat,
                     "fp32_refined", "fp32", None, (seed,))
 
