@@ -47,37 +47,49 @@ __device__ __forceinline__ long long gtimer() {
   return t;
 }
 
-// Grid-wide barrier (all blocks are co-resident: cooperative launch).  A wait
-// longer than spin_limit ns sets SS_ERR_TIMEOUT and returns false; so does any
-// error already posted by another block.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned arrive_acq_rel(unsigned* p) {
+  unsigned v;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier (all blocks are co-resident: cooperative launch).  The
+// arrival is a release-acquire add on the count; the last block resets the
+// count and publishes the next generation with a release add, which the others
+// poll with acquire loads (no sleep between polls: the waits are short).  A
+// wait longer than spin_limit ns sets SS_ERR_TIMEOUT and returns false; so
+// does any error already posted by another block.
 __device__ bool grid_sync(const SolveParams& P) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = P.bar + 1;
-    const unsigned g = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(P.bar, 1u) + 1u;
+    unsigned* gen = P.bar + 1;
+    const unsigned g = ld_acquire(gen);
+    const unsigned arrived = arrive_acq_rel(P.bar) + 1u;
     int ok = 1;
     if (arrived == gridDim.x) {
-      atomicExch(P.bar, 0u);
-      __threadfence();
-      atomicAdd(P.bar + 1, 1u);
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(P.bar) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(gen) : "memory");
     } else {
       const long long t0 = gtimer();
-      while (*gen == g) {
-        if (*(volatile int*)P.err) { ok = 0; break; }
-        if (gtimer() - t0 > P.spin_limit) {
-          atomicCAS(P.err, 0, (int)SS_ERR_TIMEOUT);
-          ok = 0;
-          break;
+      for (unsigned it = 1; ld_acquire(gen) == g; ++it) {
+        if ((it & 255u) == 0) {
+          if (*(volatile int*)P.err) { ok = 0; break; }
+          if (gtimer() - t0 > P.spin_limit) {
+            atomicCAS(P.err, 0, (int)SS_ERR_TIMEOUT);
+            ok = 0;
+            break;
+          }
         }
-        __nanosleep(32);
       }
     }
-    __threadfence();
-    if (*(volatile int*)P.err) ok = 0;
-    s_ok = ok;
+    s_ok = ok;   // an error posted elsewhere stops the waiters in their poll loop
   }
   __syncthreads();
   return s_ok != 0;
