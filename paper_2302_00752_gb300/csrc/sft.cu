@@ -194,14 +194,18 @@ __global__ void __launch_bounds__(kSampThreads) k_sample_df(int64_t M, const flo
   __shared__ uint32_t s_q[kTermChunk];
   __shared__ float4 s_c[kTermChunk];
   __shared__ float4 s_w[kTermChunk * kSampPerThread];
-  const int64_t n_terms = *n_terms_dev;
+  // blockIdx.y takes the terms [T y / S, T (y+1) / S) (S = gridDim.y); with
+  // S > 1 the block writes its partial sums to out + y M
+  const int64_t n_all = *n_terms_dev;
+  const int64_t tb = n_all * blockIdx.y / gridDim.y, te = n_all * (blockIdx.y + 1) / gridDim.y;
+  out += (int64_t)blockIdx.y * M;
   const int64_t j0 = (int64_t)blockIdx.x * (kSampThreads * kSampPerThread) + threadIdx.x;
   const uint64_t inv = ~0ull / (uint64_t)M;   // once per thread (Barrett constant of mulmod)
   DF acc[kSampPerThread];
 #pragma unroll
   for (int m = 0; m < kSampPerThread; ++m) acc[m] = DF{0.f, 0.f};
-  for (int64_t t0 = 0; t0 < n_terms; t0 += kTermChunk) {
-    const int tc = (n_terms - t0 < kTermChunk) ? (int)(n_terms - t0) : kTermChunk;
+  for (int64_t t0 = tb; t0 < te; t0 += kTermChunk) {
+    const int tc = (te - t0 < kTermChunk) ? (int)(te - t0) : kTermChunk;
     __syncthreads();
     for (int i = threadIdx.x; i < tc; i += blockDim.x) {
       s_q[i] = (uint32_t)q[t0 + i];
@@ -236,6 +240,15 @@ __global__ void __launch_bounds__(kSampThreads) k_sample_df(int64_t M, const flo
     const int64_t j = j0 + (int64_t)m * kSampThreads;
     if (j < M) out[j] = (double)acc[m].hi + (double)acc[m].lo;
   }
+}
+
+// out[j] = sum_y part[y][j], y in order.
+__global__ void k_sum_splits(const double* __restrict__ part, int n_split, int64_t M, double* __restrict__ out) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  double v = 0.0;
+  for (int y = 0; y < n_split; ++y) v += part[(int64_t)y * M + j];
+  out[j] = v;
 }
 
 // Full table exp(2 pi i r / M), r < M (FP64 path, L2-resident for M <= 4M).
@@ -587,8 +600,21 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
       DevBuf<float4> W;
       SS_TRY(W.alloc(n * kSampPerThread, st));
       k_term_powers<<<nblk(n), 256, 0, st>>>(step.get(), total.get(), P.M, tab, W.get());
-      k_sample_df<<<grid, kSampThreads, 0, st>>>(P.M, tab, q.get(), W.get(), coef.get(), total.get(),
-                                                 reinterpret_cast<double*>(out));
+      // split the terms over gridDim.y when the sample blocks alone would not
+      // fill the SMs several times over (n bounds the merged term count)
+      const int64_t want = 8LL * sm_count();
+      int n_split = (int)std::min<int64_t>(8, std::max<int64_t>(1, (want + grid - 1) / grid));
+      n_split = (int)std::max<int64_t>(1, std::min<int64_t>(n_split, n / 64));
+      if (n_split == 1) {
+        k_sample_df<<<grid, kSampThreads, 0, st>>>(P.M, tab, q.get(), W.get(), coef.get(), total.get(),
+                                                   reinterpret_cast<double*>(out));
+      } else {
+        DevBuf<double> part;
+        SS_TRY(part.alloc((size_t)n_split * P.M, st));
+        k_sample_df<<<dim3(grid, n_split), kSampThreads, 0, st>>>(P.M, tab, q.get(), W.get(), coef.get(),
+                                                                  total.get(), part.get());
+        k_sum_splits<<<nblk(P.M), 256, 0, st>>>(part.get(), n_split, P.M, reinterpret_cast<double*>(out));
+      }
       SS_LAUNCH_CHECK();
       return SS_OK;
     }
