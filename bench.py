@@ -569,7 +569,7 @@ def main():
         ff, fv = B.sft_recover(p.z, p.M, p.f_freq, p.f_coef, p.cand, tau=1e-9, precision="fp64")
         ev[2].record()
         stamp = B.stamp_build(af, av, ff, inst.N)
-        f_on, _ = stamp.scatter(ff, fv)
+        f_on, _ = stamp.scatter(ff, fv, count_outside=False)
         ev[3].record()
         u, st = B.solve(stamp, f_on, 1e-12, 1000, "fp64")
         ev[4].record()

@@ -235,8 +235,8 @@ ss_status stamp_lookup(ss_stamp s, const int32_t* freq, int64_t n, int64_t* idx_
 
 /* Scatter a sparse list onto S: out (device FP64 complex [|S|]) is zeroed,
  * then out[index(k)] = val for every entry whose k lies in S; *n_outside
- * (host, may be NULL) receives the number of entries that do not (the call then
- * synchronises `stream`). */
+ * (host) receives the number of entries that do not, and the call then
+ * synchronises `stream`; with n_outside NULL it stays asynchronous. */
 ss_status stamp_scatter(ss_stamp s, const ss_sparse* g, double* out, int64_t* n_outside, void* stream);
 
 /* Grow S^N to S^{N+levels} in place (eq. StampSet applied `levels` more times;

@@ -303,14 +303,17 @@ class Stamp:
         _check(lib.stamp_lookup(self.handle, _ptr(f), f.shape[0], _ptr(idx), _stream()))
         return idx
 
-    def scatter(self, freq, val):
+    def scatter(self, freq, val, count_outside=True):
+        """(values on S, number of input frequencies outside S); without the
+        count the call stays asynchronous (count returned as None)."""
         f = _dev_i32(freq, self.d)
         v = _dev_c128(val)
         sp = Sparse(self.d, f.shape[0], _ptr(f), _ptr(v))
         out = torch.empty(self.size, dtype=torch.complex128, device="cuda")
         outside = C.c_int64()
-        _check(lib.stamp_scatter(self.handle, C.byref(sp), _ptr(out), C.byref(outside), _stream()))
-        return out, outside.value
+        _check(lib.stamp_scatter(self.handle, C.byref(sp), _ptr(out), C.byref(outside) if count_outside else None,
+                                 _stream()))
+        return out, (outside.value if count_outside else None)
 
     def extend(self, levels=1):
         """Grow S^N to S^{N+levels} in place (existing indices unchanged)."""

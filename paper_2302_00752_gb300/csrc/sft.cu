@@ -295,24 +295,32 @@ __global__ void k_merge_first(const int32_t* __restrict__ freq, int64_t n, int d
   if (same_rep(pu, rep_sign(pu, d), pt, rep_sign(pt, d), d)) atomicMin(first + t, (int32_t)u);
 }
 
-// Leaders sum their group in index order (deterministic).
+// Leaders sum their group: one warp per term, lanes take the members in a
+// fixed stride, then a fixed butterfly (deterministic).
 __global__ void k_merge_sum(const int32_t* __restrict__ freq, const double2* __restrict__ coef, int64_t n, int d,
                             const int32_t* __restrict__ first, int32_t* leader_flag, double2* merged,
                             int32_t* imag_nonzero) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (t >= n) return;
   const bool leader = first[t] == (int32_t)n;
-  leader_flag[t] = leader ? 1 : 0;
+  if (lane == 0) leader_flag[t] = leader ? 1 : 0;
   if (!leader) return;
   const int st = rep_sign(freq + t * d, d);
   double re = 0.0, im = 0.0;
-  for (int64_t u = t; u < n; ++u) {
+  for (int64_t u = t + lane; u < n; u += 32) {
     if (u != t && first[u] != (int32_t)t) continue;
     const int su = rep_sign(freq + u * d, d);
     const double2 c = coef[u];
     re += c.x;
     im += (su == st) ? c.y : -c.y;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if (lane != 0) return;
   if (st == 0) im = 0.0;
   merged[t] = make_double2(re, im);
   if (im != 0.0) atomicExch(imag_nonzero, 1);
@@ -587,8 +595,8 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
   SS_CUDA(cudaMemsetAsync(imag.get(), 0, sizeof(int32_t), st));
   k_fill_first<<<nblk(n), 256, 0, st>>>(first.get(), n);
   k_merge_first<<<nblk(n * n), 256, 0, st>>>(g->freq, n, L.d, first.get());
-  k_merge_sum<<<nblk(n), 256, 0, st>>>(g->freq, reinterpret_cast<const double2*>(g->coef), n, L.d, first.get(),
-                                       flag.get(), merged.get(), imag.get());
+  k_merge_sum<<<nblk(n * 32), 256, 0, st>>>(g->freq, reinterpret_cast<const double2*>(g->coef), n, L.d,
+                                            first.get(), flag.get(), merged.get(), imag.get());
   SS_LAUNCH_CHECK();
   SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), n, total.get(), st));
   k_compact_terms<<<nblk(n), 256, 0, st>>>(g->freq, n, L, flag.get(), pos.get(), merged.get(), q.get(), step.get(),

@@ -995,9 +995,10 @@ extern "C" ss_status stamp_scatter(ss_stamp s, const ss_sparse* g, double* out, 
   k_scatter_vals<<<nblk(g->n), 256, 0, st>>>(idx.get(), reinterpret_cast<const double2*>(g->val), g->n,
                                              reinterpret_cast<double2*>(out), outside.get());
   SS_LAUNCH_CHECK();
+  if (!n_outside) return SS_OK;   // no count asked for: stays asynchronous
   unsigned long long h = 0;
   SS_CUDA(cudaMemcpyAsync(&h, outside.get(), sizeof(h), cudaMemcpyDeviceToHost, st));
   SS_CUDA(cudaStreamSynchronize(st));
-  if (n_outside) *n_outside = (int64_t)h;
+  *n_outside = (int64_t)h;
   return SS_OK;
 }

@@ -114,7 +114,7 @@ def run(p: Prepared, tol=1e-12, max_iter=1000, tau=None, solve_precision=None, l
     af, av = B.sft_recover(p.z, p.M, p.a_freq, p.a_coef, p.cand, tau=tau, precision=p.sft_precision)
     ff, fv = B.sft_recover(p.z, p.M, p.f_freq, p.f_coef, p.cand, tau=tau, precision=p.sft_precision)
     stamp = B.stamp_build(af, av, ff, p.N)
-    f_on, _ = stamp.scatter(ff, fv)
+    f_on, _ = stamp.scatter(ff, fv, count_outside=False)
     if not solve:
         return Result(p.z, p.M, af, av, ff, fv, stamp, f_on, None, {})
     u, stats = B.solve(stamp, f_on, tol, max_iter, solve_precision or p.solve_precision)

@@ -142,3 +142,22 @@ def test_df64_manufactured_cfg2(B, gp):
         assert rel_l2(u.cpu().numpy(), want.cpu().numpy()) < TOL
     finally:
         res.stamp.destroy()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "df64"])
+def test_nonzero_mean_forcing_is_rejected(B, prec):
+    # the diffusion problem is mean-zero: f_hat_0 != 0 on S is SS_ERR_INVALID
+    A = np.array([[-1, 0], [0, 0], [1, 0]])
+    av = np.array([0.2, 1.0, 0.2], complex)
+    F = np.array([[1, 0], [-1, 0], [0, 2], [0, -2]])
+    with B.stamp_build(A, av, F, 1) as s:
+        assert s.zero_index >= 0
+        f_on, _ = s.scatter(F, np.array([1, 1, 0.5, 0.5], complex))
+        u, st = B.solve(s, f_on, 1e-12, 100, prec)
+        assert st["status"] == "SS_OK"
+        f_on[s.zero_index] = 0.25
+        with pytest.raises(B.SSError):
+            B.solve(s, f_on, 1e-12, 100, prec)
+        f_on[s.zero_index] = 0.0
+        u, st = B.solve(s, f_on, 1e-12, 100, prec)   # the context is still usable
+        assert st["status"] == "SS_OK"
