@@ -634,7 +634,17 @@ def main():
     # solve-only time to solution, FP64 vs FP32-refined, errors against the exact solution
     keep = step(prep, keep=True)
     stamp, f_on = keep["stamp"], keep["f_on"]
-    S = stamp.export()[0].cpu().numpy()
+    S, lv = stamp.export()
+    S = S.cpu().numpy()
+    # stamping throughput: every set member of levels 0..N-1 tries every step of supp a_hat
+    counts = np.bincount(lv.cpu().numpy().astype(np.int64), minlength=inst.N + 1)
+    af = np.asarray(inst.a.freq, np.int64)
+    s_a = len({tuple(k) for k in np.vstack([af, -af]).tolist()})   # |supp a_hat| of the real coefficient
+    cand = int(sum(counts[n] for n in range(inst.N)) * s_a)
+    stamp_stats = {"level_sizes": counts.tolist(), "candidates": cand,
+                   "candidates_per_s": cand / (statistics.median(stage["stamp"]) / 1e3),
+                   "stamp_ms": statistics.median(stage["stamp"]),
+                   "note": "whole stamp_build + scatter call (levels, hash, neighbour table, coefficients)"}
     idx = {tuple(k): i for i, k in enumerate(S.tolist())}
     exact = np.zeros(len(S), complex)
     for k, v in zip(inst.u_freq.tolist(), inst.u_val):
@@ -742,6 +752,18 @@ def main():
                          f"the explicit operator of the full workload; its assembly (BFS stamping + matrix, "
                          f"{o['seconds']:.1f} s) and the DFT recovery are not in the time",
                "full_path_nnz_per_s": o["nnz"] * (it + 1) / (dt + o["seconds"])}
+        try:
+            from oracle import cpu_pcg
+            t0 = time.perf_counter()
+            n_cores = len(os.sched_getaffinity(0))
+            _, it_c = cpu_pcg.pcg(o["L"], o["b"], o["D"], 1e-12, n_threads=n_cores)
+            dt_c = time.perf_counter() - t0
+            cpu["all_cores"] = {"value": o["nnz"] * (it_c + 1) / dt_c, "unit": "nnz/s", "cores": n_cores,
+                                "kind": "oracle (C, OpenMP)",
+                                "sample": f"the same Jacobi PCG in C with OpenMP row-parallel products on the same "
+                                          f"CSR operator ({it_c + 1} applications, {dt_c:.2f} s)"}
+        except Exception as e:
+            cpu["all_cores"] = {"error": repr(e)}
 
     if rank == 0:
         line = {
@@ -755,6 +777,7 @@ def main():
                     "ms_per_step": sum(e2e_ms) / len(e2e_ms)},
             "breakdown_ms": med,
             "solve_only": tts,
+            "stamp": stamp_stats,
             "roofline": roofline,
             "gpu_launches": gpu_launches,
             "gpu_launches_per_step": launches_per_step,
