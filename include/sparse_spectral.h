@@ -311,9 +311,10 @@ ss_status solve_set_config(ss_stamp s, int32_t block, int32_t blocks_per_sm, int
 
 /* Allocation-free variant of solve() (the paper has no counterpart: this is a
  * deployment convenience).  For callers that may not allocate device memory
- * while they run - code inside a region being captured into a CUDA graph,
- * latency-bound loops that must not stall on cudaMalloc (which synchronises
- * the device), or processes with a device-memory budget fixed at start-up.
+ * while they run - plug-ins inside a host application that owns all device
+ * memory, latency-bound loops that must not stall on cudaMalloc (which
+ * synchronises the device), or processes with a device-memory budget fixed at
+ * start-up.
  * The caller passes f_on_S and u_on_S exactly as for solve(); all workspace
  * comes from one file-scope device array of about 7.4 MB that every GPU which
  * loads the library holds until exit, sized for a stamping set of at most

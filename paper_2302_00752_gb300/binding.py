@@ -436,8 +436,8 @@ def solve(stamp, f_on_S, tol=1e-12, max_iter=1000, precision="fp64", out=None, r
 
 def solve_noalloc(stamp, f_on_S, out, tol=1e-12, max_iter=1000, precision="fp64"):
     """Allocation-free solve: for callers that must not allocate device memory
-    while they run (inside CUDA-graph capture regions, allocation-free loops,
-    fixed memory budgets).  ``f_on_S`` and ``out`` are caller-owned complex128
+    while they run (plug-ins in a host application that owns all device
+    memory, loops that must not stall on an allocation, fixed memory budgets).  ``f_on_S`` and ``out`` are caller-owned complex128
     device tensors of length |S|; the workspace is a fixed library array for
     |S| <= 32768 (larger sets raise SSError).  Calls that overlap on the GPU
     share that array and race."""

@@ -1385,11 +1385,10 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
 //
 // solve_noalloc runs the same persistent solver as solve() but takes all of
 // its workspace from one file-scope device array instead of allocating it.
-// It serves callers that may not allocate device memory once they run: code
-// that executes inside a region where an allocation would break a CUDA graph
-// being captured, or that must not let a first call stall on cudaMalloc
-// (allocation synchronises the device), or that runs under a fixed
-// device-memory budget set at start-up.  The array holds a stamping set of at
+// It serves callers that may not allocate device memory once they run:
+// plug-ins inside a host application that owns all device memory, code that
+// must not stall on cudaMalloc (allocation synchronises the device), or code
+// that runs under a fixed device-memory budget set at start-up.  The array holds a stamping set of at
 // most kNoAllocRows padded rows (stamps of up to 32,736 frequencies, a few MB
 // of device memory on every GPU that loads the library, kept until exit).
 

@@ -1,8 +1,8 @@
 """The allocation-free solve (solve_noalloc) against the regular solve.
 
 solve_noalloc exists for callers that may not allocate device memory while
-they run (code inside a CUDA-graph capture region, loops that must not stall on
-an allocation, fixed device-memory budgets): its workspace is one fixed library
+they run (plug-ins inside a host application that owns all device memory, loops
+that must not stall on an allocation, fixed device-memory budgets): its workspace is one fixed library
 array, sized for stamping sets of at most 32,768 padded rows, shared by every
 call.  This file runs last (pytest collects it after the other test files) so
 that a failure here leaves every other test already run."""
