@@ -795,8 +795,10 @@ __device__ __forceinline__ double2 cdot(double2 a, double2 b) {
 __device__ void solve_bicgstab(const SolveParams& P, Smem& sm) {
   const double tol2 = P.tol * P.tol;
   auto noscal = [](int, const Chunk&, int, int, bool, int) {};
-  // x = 0, r = r^ = f, p = v = 0, dlt = D^-1;  <r^, r> = |f|^2 (q0), |r|^2 (q2), |f|^2 (q3)
-  run_phase(P, sm, 0b1101u, noscal, [&](int64_t g, int64_t, int, int i, int, double* v) {
+  // x = 0, r = r^ = f, p = v = 0, dlt = D^-1;  <r^, r> = |f|^2 + 0 i (q0, q1), |r|^2 (q2), |f|^2 (q3).
+  // q1 is written (as zero) too: the first iteration reads rho = (q0, q1),
+  // and a slot left out would hold whatever an earlier phase or solve left there.
+  run_phase(P, sm, 0b1111u, noscal, [&](int64_t g, int64_t, int, int i, int, double* v) {
     const double2 f = f_at(P.inst[i], g);
     P.xrec[2 * g] = make_double2(0.0, 0.0);
     P.r[g] = f;

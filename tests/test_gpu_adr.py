@@ -207,3 +207,21 @@ def test_monte_carlo_proxy_matches_oracle(B):
     tol = 1e-12 * (np.abs(gv).sum() + np.abs(inst.f.coef).sum())
     assert np.max(np.abs(fx.cpu().numpy() - f_ref)) <= tol
     assert np.max(np.abs(r.cpu().numpy() - r_ref)) <= tol
+
+
+def test_repeated_solves_identical(B):
+    # every partial sum a BiCGStab phase reads is written by the phase before
+    # it: a second solve on the same stamp reuses the workspace the first one
+    # left behind and must return the same bits
+    inst = W.make_adr(15, N=1)
+    a, b, c, f = data(inst)
+    with build(B, a, b, c, f, 1) as s:
+        f_on, _ = scatter_rhs(s, f)
+        u1, st1 = B.solve(s, f_on, 1e-12, 2000, "fp64")
+        u2, st2 = B.solve(s, f_on, 1e-12, 2000, "fp64")
+        S = s.export()[0].cpu().numpy()
+    assert st1["status"] == st2["status"] == "SS_OK"
+    assert st1["rel_residual"] <= 1e-11 and st2["rel_residual"] <= 1e-11
+    assert torch.equal(u1, u2)
+    u_ref, _ = oadr.solve(S, a, b, c, *f)
+    assert rel_l2(u2.cpu().numpy(), u_ref) < 1e-10
