@@ -280,7 +280,7 @@ def d100_section(B, gp, flush, steps=2, smooth=False):
     b.synchronize()
     ms = a.elapsed_time(b) / reps
     out["apply_fp32"] = {"ms": ms, "nnz_per_s": stamp.nnz / (ms / 1e3),
-                         "note": "standalone galerkin_apply (pack + operator), L2-warm back-to-back"}
+                         "note": "standalone FP32 galerkin_apply (one kernel), L2-warm back-to-back (host launch rate included)"}
     stamp.destroy()
     return out
 
@@ -290,8 +290,9 @@ def apply_section(B, gp, flush, peaks, reps=10):
     flushed before every call, on the d = 100 set (FP32 operator) and the
     d = 10 set (FP64 and FP32).  Algorithmic HBM bytes per call: the index
     stream (4 B per nonzero) plus, per row, u read, |k|^2 read and y written
-    (FP32: 8 + 8 + 8 B; FP64 also reads the 16 B entry coefficient per
-    nonzero and moves 16 B values).  FP64 is also given as FP64 flops (four
+    (FP32: 8 + 4 + 8 B, the norm as its 4-byte FP32 norm word; FP64 also reads
+    the 16 B entry coefficient per nonzero and moves 16 B values with the
+    8 B int64 norm).  FP64 is also given as FP64 flops (four
     FMAs per nonzero) against the FP64 ALU peak."""
     import torch
     out = {}
@@ -321,7 +322,7 @@ def apply_section(B, gp, flush, peaks, reps=10):
             torch.cuda.synchronize()
             ms = statistics.median([a.elapsed_time(b) for a, b in evs])
             if prec == "fp32":
-                byts = 4 * st.nnz + st.size * (8 + 8 + 8)
+                byts = 4 * st.nnz + st.size * (8 + 4 + 8)
             else:
                 byts = (4 + 16) * st.nnz + st.size * (16 + 8 + 16)
             d = {"ms": ms, "nnz_per_s": st.nnz / (ms / 1e3), "algorithmic_bytes": byts,
@@ -331,7 +332,8 @@ def apply_section(B, gp, flush, peaks, reps=10):
             res[prec] = d
         st.destroy()
         out[name] = res
-    out["note"] = ("CUDA events around one galerkin_apply call (two kernels) after a 512 MB L2 flush (write, "
+    out["note"] = ("CUDA events around one galerkin_apply call (FP32: one kernel; FP64: pack + operator) after "
+                   "a 512 MB L2 flush (write, "
                    "then read so that no dirty line is written back inside the timed call), all calls queued "
                    "before the first wait; fraction of the measured HBM copy bandwidth")
     return out

@@ -1,7 +1,9 @@
 // galerkin_apply: y = L_{N,s} u on the stamping set (eq. FiniteGalerkinOperator).
 // One thread per row, one warp per 32-row slice of the sliced-ELL table: the
-// index stream is read coalesced (column-major inside a slice) and the values
-// of u are gathered from a record array that carries |l|^2 beside u_l.
+// index stream is read coalesced (column-major inside a slice).  FP64: the
+// values of u are first packed into a record array and gathered from there
+// beside the stored entry coefficients.  FP32: u_l is gathered straight from
+// the caller's array and |l|^2 from the stamp's norm words.
 #include <algorithm>
 
 #include "apply.cuh"
@@ -12,32 +14,6 @@ namespace {
 __global__ void k_pack64(const double2* __restrict__ u, int64_t size, double2* rec) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < size) rec[2 * i] = u[i];
-}
-
-// Four rows per thread, loads issued before stores (one DRAM round trip).
-__global__ void k_pack32(const float2* __restrict__ u, int64_t size, float4* rec) {
-  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  float2 v[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int64_t i = i0 + q * stride;
-    v[q] = i < size ? __ldg(u + i) : make_float2(0.f, 0.f);
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int64_t i = i0 + q * stride;
-    if (i < size) reinterpret_cast<float2*>(rec + i)[0] = v[q];
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void load_coef(T* s_ca, int32_t* s_pn, const T* ca, const int32_t* pn, int s_a) {
-  for (int j = threadIdx.x; j < s_a; j += blockDim.x) {
-    s_ca[j] = ca[j];
-    s_pn[j] = pn[j];
-  }
-  __syncthreads();
 }
 
 __global__ void __launch_bounds__(256) k_apply64(OpView op, int64_t size, int64_t rows_pad,
@@ -52,25 +28,19 @@ __global__ void __launch_bounds__(256) k_apply64(OpView op, int64_t size, int64_
   if (row < size) y[row] = acc;
 }
 
-__global__ void __launch_bounds__(256) k_apply32(OpView op, int64_t size, int64_t rows_pad, const int64_t* __restrict__ norm,
-                                                 bool wide,
-                                                 const float4* __restrict__ rec, const float2* __restrict__ ca,
-                                                 const int32_t* __restrict__ pn, int s_a, int64_t zero_idx,
-                                                 float2* __restrict__ y) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  float2* s_ca = reinterpret_cast<float2*>(smem);
-  int32_t* s_pn = reinterpret_cast<int32_t*>(s_ca + s_a);
-  load_coef(s_ca, s_pn, ca, pn, s_a);
+// One row per thread; 40 registers (six 256-thread blocks per SM) keep four
+// index words and eight gathers in flight per thread.
+template <bool WIDE>
+__global__ void __launch_bounds__(256, 6) k_apply32(OpView op, int64_t size, int64_t rows_pad,
+                                                    const int32_t* __restrict__ nw, const float2* __restrict__ u,
+                                                    const float2* __restrict__ ca, const int32_t* __restrict__ pn,
+                                                    int64_t zero_idx, float2* __restrict__ y) {
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= rows_pad) return;
   const int64_t s = row / kSlice;
   const int lane = (int)(row % kSlice);
-  float2 acc = row_apply32<false, 8>(op, s, lane, __ldg(norm + row), wide, rec, s_ca, s_pn);
-  if (row == zero_idx) {
-    const float4 r = rec[row];
-    acc = make_float2(r.x, r.y);
-  }
-  if (row < size) y[row] = acc;
+  float2 acc = row_apply32_direct<WIDE, 4>(op, s, lane, __ldg(nw + row), size, u, nw, ca, pn);
+  if (row < size) y[row] = row == zero_idx ? u[row] : acc;
 }
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -155,12 +125,6 @@ ss_status launch_pack64(const ss_stamp_s* s, const double2* u, cudaStream_t st) 
   return SS_OK;
 }
 
-ss_status launch_pack32(const ss_stamp_s* s, const float2* u, cudaStream_t st) {
-  k_pack32<<<nblk((s->size + 3) / 4), 256, 0, st>>>(u, s->size, s->rec32.get());
-  SS_LAUNCH_CHECK();
-  return SS_OK;
-}
-
 ss_status launch_pack64_prefix(const ss_stamp_s* s, const double2* u, int64_t n_u, cudaStream_t st) {
   k_pack64_prefix<<<nblk(s->size), 256, 0, st>>>(u, n_u, s->size, s->rec64.get());
   SS_LAUNCH_CHECK();
@@ -173,11 +137,14 @@ ss_status launch_apply64(const ss_stamp_s* s, double2* y, cudaStream_t st) {
   return SS_OK;
 }
 
-ss_status launch_apply32(const ss_stamp_s* s, float2* y, cudaStream_t st) {
+ss_status launch_apply32(const ss_stamp_s* s, const float2* u, float2* y, cudaStream_t st) {
   if (s->adr) SS_FAIL(SS_ERR_INVALID, "the FP32 operator is not available for ADR stamps (use SS_FP64)");
-  const size_t sm = s->s_a * (sizeof(float2) + sizeof(int32_t)) + 16;
-  k_apply32<<<nblk(s->rows_pad), 256, sm, st>>>(op_view(s), s->size, s->rows_pad, s->norm.get(), s->wide,
-                                                s->rec32.get(), s->ca32.get(), s->pn32.get(), s->s_a, s->zero_idx, y);
+  if (s->wide)
+    k_apply32<true><<<nblk(s->rows_pad), 256, 0, st>>>(op_view(s), s->size, s->rows_pad, s->nw32.get(), u,
+                                                       s->ca32.get(), s->pn32.get(), s->zero_idx, y);
+  else
+    k_apply32<false><<<nblk(s->rows_pad), 256, 0, st>>>(op_view(s), s->size, s->rows_pad, s->nw32.get(), u,
+                                                        s->ca32.get(), s->pn32.get(), s->zero_idx, y);
   SS_LAUNCH_CHECK();
   return SS_OK;
 }
@@ -194,10 +161,8 @@ extern "C" ss_status galerkin_apply(ss_stamp s, const void* u, void* y, ss_preci
     SS_TRY(launch_pack64(s, reinterpret_cast<const double2*>(u), st));
     return launch_apply64(s, reinterpret_cast<double2*>(y), st);
   }
-  if (prec == SS_FP32) {
-    SS_TRY(launch_pack32(s, reinterpret_cast<const float2*>(u), st));
-    return launch_apply32(s, reinterpret_cast<float2*>(y), st);
-  }
+  if (prec == SS_FP32)
+    return launch_apply32(s, reinterpret_cast<const float2*>(u), reinterpret_cast<float2*>(y), st);
   SS_FAIL(SS_ERR_INVALID, "galerkin_apply: unknown precision %d", (int)prec);
 }
 

@@ -159,6 +159,46 @@ __device__ __forceinline__ float2 row_apply32_t(const OpView& op, int64_t s, int
   return make_float2(ar, ai);
 }
 
+// Standalone FP32 operator on the caller's u: the value u_l and the norm word
+// of |l|^2 are two gathers (u from the caller's array, guarded because padding
+// entries name column rows_pad, one past any row of u; the norm word from the
+// stamp's nw32).  No packing step rewrites u first.
+template <bool WIDE, int U>
+__device__ __forceinline__ float2 row_apply32_direct(const OpView& op, int64_t s, int lane, int32_t nk, int64_t size,
+                                                     const float2* __restrict__ u, const int32_t* __restrict__ nw,
+                                                     const float2* __restrict__ ca, const int32_t* __restrict__ pn) {
+  const int32_t w0 = __ldg(op.woff + s), w1 = __ldg(op.woff + s + 1);
+  const uint32_t* e = op.ent + (int64_t)w0 * kSlice + lane;
+  float ar = 0.f, ai = 0.f;
+  const int w = w1 - w0;
+  for (int t = 0; t < w; t += U) {
+    uint32_t ee[U];
+    float2 v[U];
+    int32_t nl[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) ee[q] = t + q < w ? __ldg(e + (int64_t)(t + q) * kSlice) : 0u;
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const uint32_t c = ee[q] & op.colmask;
+      const bool ok = t + q < w && (int64_t)c < size;
+      v[q] = ok ? __ldg(u + c) : make_float2(0.f, 0.f);
+      nl[q] = ok ? __ldg(nw + c) : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      if (t + q < w) {
+        const int j = (int)(ee[q] >> op.colbits);
+        const float sc = entry_scale<WIDE>(nk, __int_as_float(nl[q]), __ldg(pn + j));
+        const float2 a = __ldg(ca + j);
+        const float tr = sc * a.x, ti = sc * a.y;
+        ar = fmaf(tr, v[q].x, ar); ar = fmaf(-ti, v[q].y, ar);
+        ai = fmaf(tr, v[q].y, ai); ai = fmaf(ti, v[q].x, ai);
+      }
+    }
+  }
+  return make_float2(ar, ai);
+}
+
 template <bool CG = false, int U = 4>
 __device__ __forceinline__ float2 row_apply32(const OpView& op, int64_t s, int lane, int64_t nk, bool wide,
                                               const float4* __restrict__ rec, const float2* ca,

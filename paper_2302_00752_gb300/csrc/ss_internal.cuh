@@ -133,8 +133,8 @@ struct ss_stamp_s {
   ss::DevBuf<uint32_t> ent;           // [n_ent] col | (j << colbits)
   ss::DevBuf<double2> ecoef64;        // [n_ent] 2 pi^2 (|k|^2 + |l|^2 - |p_j|^2) a_hat_j per entry (FP64 operator)
   ss::DevBuf<float4> ecoefdf;         // [n_ent + 1] the same as double-float, built on first DF64 solve
-  // scratch for galerkin_apply
-  ss::DevBuf<float4> rec32;           // [rows_pad + 1]
+  ss::DevBuf<int32_t> nw32;           // [rows_pad + 1] FP32 norm words of |k|^2 (norm_word; 0 on padding)
+  // scratch for galerkin_apply (FP64)
   ss::DevBuf<double2> rec64;          // [2 * (rows_pad + 1)] (value, norm|pad) pairs
   // build state kept for stamp_extend
   int maxabs_f = 0, maxabs_a = 0;     // largest |coordinate| of F and of supp a_hat
@@ -163,12 +163,12 @@ __host__ __device__ inline int colbits_of(int jbits) { return 32 - jbits; }
 
 // Apply launchers used by galerkin_apply and the solver (apply.cu).
 ss_status launch_pack64(const ss_stamp_s* s, const double2* u, cudaStream_t st);
-ss_status launch_pack32(const ss_stamp_s* s, const float2* u, cudaStream_t st);
 ss_status launch_apply64(const ss_stamp_s* s, double2* y, cudaStream_t st);
 // u on the first n_u rows of S (a vector on S^N is the prefix of one on
 // S^{N+L}), zero on the rest, into the FP64 record array.
 ss_status launch_pack64_prefix(const ss_stamp_s* s, const double2* u, int64_t n_u, cudaStream_t st);
-ss_status launch_apply32(const ss_stamp_s* s, float2* y, cudaStream_t st);
+// FP32 operator straight from the caller's u (no packing step).
+ss_status launch_apply32(const ss_stamp_s* s, const float2* u, float2* y, cudaStream_t st);
 // Double-float copy of the FP64 entry coefficients (built once per operator).
 ss_status ensure_ecoefdf(ss_stamp_s* s, cudaStream_t st);
 

@@ -400,12 +400,12 @@ __global__ void k_fill_slices_adr(KeyParams P, const uint64_t* __restrict__ keys
   }
 }
 
-__global__ void k_init_records(const int64_t* __restrict__ norm, int64_t n, bool wide, float4* rec32,
+__global__ void k_init_records(const int64_t* __restrict__ norm, int64_t n, bool wide, int32_t* nw32,
                                double2* rec64) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t nr = norm[i];
-  rec32[i] = make_float4(0.f, 0.f, __int_as_float(norm_word(nr, wide)), 0.f);
+  nw32[i] = norm_word(nr, wide);
   rec64[2 * i] = make_double2(0.0, 0.0);
   rec64[2 * i + 1] = make_double2(__longlong_as_double((long long)nr), 0.0);
 }
@@ -607,9 +607,9 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
                                                      S->pnorm.get(), S->ca64.get(), S->ent.get(), S->ecoef64.get());
   }
   SS_LAUNCH_CHECK();
-  SS_TRY(S->rec32.alloc(S->rows_pad + 1, st));
+  SS_TRY(S->nw32.alloc(S->rows_pad + 1, st));
   SS_TRY(S->rec64.alloc(2 * (S->rows_pad + 1), st));
-  k_init_records<<<nblk(S->rows_pad + 1), 256, 0, st>>>(S->norm.get(), S->rows_pad + 1, S->wide, S->rec32.get(),
+  k_init_records<<<nblk(S->rows_pad + 1), 256, 0, st>>>(S->norm.get(), S->rows_pad + 1, S->wide, S->nw32.get(),
                                                         S->rec64.get());
   SS_LAUNCH_CHECK();
   int32_t e = 0;
@@ -620,7 +620,7 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   S->keys.settle(); S->level.settle(); S->norm.settle(); S->table.settle();
   S->afreq.settle(); S->stepkey.settle(); S->pnorm.settle(); S->pn32.settle(); S->aval.settle();
   S->ca64.settle(); S->ca32.settle(); S->slice_off.settle(); S->ent.settle(); S->ecoef64.settle();
-  S->rec32.settle(); S->rec64.settle(); S->err_dev.settle(); S->zidx_dev.settle();
+  S->nw32.settle(); S->rec64.settle(); S->err_dev.settle(); S->zidx_dev.settle();
   S->bval.settle(); S->cval.settle(); S->diag64.settle();
   return SS_OK;
 }
@@ -755,7 +755,7 @@ static void rebind(ss_stamp_s* S, cudaStream_t st) {
   S->ent.s = st;
   S->ecoef64.s = st;
   S->ecoefdf.s = st;
-  S->rec32.s = st;
+  S->nw32.s = st;
   S->rec64.s = st;
   S->diag64.s = st;
 }
