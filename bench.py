@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the d=100 and batched sections")
+    ap.add_argument("--apply-only", action="store_true",
+                    help="run only the galerkin_apply section and print it (profiling the operator kernels)")
     return ap.parse_args()
 
 
@@ -561,6 +563,12 @@ def main():
         run_reference(args, inst)
         return
     import torch
+    if args.apply_only:
+        from paper_2302_00752_gb300 import binding as B
+        from paper_2302_00752_gb300 import pipeline as gp
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        print(json.dumps({"apply": apply_section(B, gp, flush, load_peaks())}))
+        return
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
