@@ -361,6 +361,51 @@ ss_status batch_set_config(ss_batch b, int32_t block, int32_t blocks_per_sm, int
 
 void batch_destroy(ss_batch b);
 
+/* ------------------------------------------------------ the whole method */
+
+/* How sparse_spectral_solve picks its rank-1 lattice. */
+typedef enum {
+    SS_LATTICE_GIVEN = 0,          /* z and M as given */
+    SS_LATTICE_CBC = 1,            /* lattice_cbc(cand, M_min, raw [d][n_raw]) */
+    SS_LATTICE_RANDOM = 2,         /* lattice_random(cand, sigma, M_min, raw [n_raw][d]) */
+    SS_LATTICE_RANDOM_SMOOTH = 3   /* lattice_random_smooth, same arguments */
+} ss_lattice_kind;
+
+typedef struct {
+    int32_t kind;          /* ss_lattice_kind */
+    int32_t d;
+    const int64_t* z;      /* GIVEN: host [d] */
+    int64_t M;             /* GIVEN */
+    const int64_t* raw;    /* CBC, RANDOM*: host draws (layouts above), non-negative */
+    int32_t n_raw;         /* CBC: candidates per coordinate; RANDOM*: attempts */
+    int64_t M_min;         /* CBC, RANDOM* */
+    double sigma;          /* RANDOM* */
+} ss_lattice_spec;
+
+/* Algorithm 1 (Section "Sparse spectral method", Algorithm SparseSFT) in one
+ * call: the lattice for the candidate set `cand` (device int32 [n_cand][d],
+ * the frequency set I of Theorem SFTRecovery), a_hat = SFT(a) and
+ * f_hat = SFT(f) on it (sft_recover with threshold tau, precision sft_prec),
+ * S^N[a_hat](supp f_hat) (stamp_build), f_hat scattered onto S and the solve
+ * of L_{N,s} u = f_hat (solve with tol, max_iter, solve_prec).  The stages
+ * run back to back on `stream` without returning to the caller in between;
+ * each synchronises where its own entry point does.  Outputs: the lattice
+ * (z_out host [d], M_out), the stamping set (*stamp_out, caller destroys it;
+ * the solution is kept in it, see stamp_solution) and the solve statistics
+ * (stats, host, may be NULL).  Returns the first failing stage's status;
+ * SS_ERR_NOT_CONVERGED still returns the stamp, any other error destroys it
+ * and leaves *stamp_out NULL. */
+ss_status sparse_spectral_solve(const ss_lattice_spec* lat, const ss_trig* a, const ss_trig* f,
+                                const int32_t* cand, int64_t n_cand, int32_t N, double tau,
+                                ss_precision sft_prec, ss_precision solve_prec, double tol, int32_t max_iter,
+                                int64_t* z_out, int64_t* M_out, ss_stamp* stamp_out, ss_solve_stats* stats,
+                                void* stream);
+
+/* Copy the solution that sparse_spectral_solve left in the stamp into u_out
+ * (device FP64 complex, as many rows as S had at the solve: after
+ * stamp_extend it is the prefix of the extended set).  Asynchronous. */
+ss_status stamp_solution(ss_stamp s, double* u_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

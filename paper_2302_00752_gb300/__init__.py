@@ -10,7 +10,8 @@ import importlib
 
 _EXPORTS = ("SS_FP32", "SS_FP64", "SS_DF64", "Batch", "SSError", "Stamp", "galerkin_apply", "lattice_cbc", "lattice_check",
             "lattice_random", "lattice_sample", "lattice_size", "sft_recover", "sft_identify", "sft_identify_samples", "sft_recover_samples", "solve",
-            "stamp_build", "stamp_build_adr", "version", "proxy_residual", "proxy_mc", "solve_noalloc")
+            "stamp_build", "stamp_build_adr", "version", "proxy_residual", "proxy_mc", "solve_noalloc",
+            "sparse_spectral_solve")
 
 __all__ = list(_EXPORTS)
 

@@ -41,6 +41,11 @@ class Sparse(C.Structure):
     _fields_ = [("d", C.c_int32), ("n", C.c_int64), ("freq", C.c_void_p), ("val", C.c_void_p)]
 
 
+class LatticeSpec(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("d", C.c_int32), ("z", C.POINTER(C.c_int64)), ("M", C.c_int64),
+                ("raw", C.POINTER(C.c_int64)), ("n_raw", C.c_int32), ("M_min", C.c_int64), ("sigma", C.c_double)]
+
+
 class SolveStats(C.Structure):
     _fields_ = [("status", C.c_int32), ("outer_iters", C.c_int32), ("inner_iters", C.c_int32),
                 ("applies", C.c_int32), ("rel_residual", C.c_double), ("kernel_ms", C.c_double)]
@@ -91,6 +96,9 @@ def _load():
         "batch_config": (i32, [vp, P(i32), P(i32), P(i32), P(i32), P(i32)]),
         "batch_set_config": (i32, [vp, i32, i32, i32]),
         "batch_destroy": (None, [vp]),
+        "sparse_spectral_solve": (i32, [P(LatticeSpec), P(Trig), P(Trig), vp, i64, i32, dbl, i32, i32, dbl, i32,
+                                        P(i64), P(i64), P(vp), P(SolveStats), vp]),
+        "stamp_solution": (i32, [vp, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -116,14 +124,23 @@ def _ptr(t):
 
 
 def _dev_i32(x, d=None):
-    t = torch.as_tensor(np.asarray(x) if not torch.is_tensor(x) else x)
-    t = t.to(device="cuda", dtype=torch.int32).contiguous()
-    if d is not None:
+    # device tensors that already have the layout are passed through untouched
+    # (each torch call costs host time on the path between two library calls)
+    if (torch.is_tensor(x) and x.is_cuda and x.dtype == torch.int32 and x.is_contiguous()
+            and x.device.index == torch.cuda.current_device()):
+        t = x
+    else:
+        t = torch.as_tensor(np.asarray(x) if not torch.is_tensor(x) else x)
+        t = t.to(device="cuda", dtype=torch.int32).contiguous()
+    if d is not None and (t.dim() != 2 or t.shape[1] != d):
         t = t.reshape(-1, d)
     return t
 
 
 def _dev_c128(x):
+    if (torch.is_tensor(x) and x.is_cuda and x.dtype == torch.complex128 and x.is_contiguous()
+            and x.device.index == torch.cuda.current_device()):
+        return x
     t = x if torch.is_tensor(x) else torch.as_tensor(np.asarray(x, dtype=np.complex128))
     return t.to(device="cuda", dtype=torch.complex128).contiguous()
 
@@ -437,7 +454,8 @@ def solve(stamp, f_on_S, tol=1e-12, max_iter=1000, precision="fp64", out=None, r
 def solve_noalloc(stamp, f_on_S, out, tol=1e-12, max_iter=1000, precision="fp64"):
     """Allocation-free solve: for callers that must not allocate device memory
     while they run (plug-ins in a host application that owns all device
-    memory, loops that must not stall on an allocation, fixed memory budgets).  ``f_on_S`` and ``out`` are caller-owned complex128
+    memory, loops that must not stall on an allocation, fixed memory
+    budgets).  ``f_on_S`` and ``out`` are caller-owned complex128
     device tensors of length |S|; the workspace is a fixed library array for
     |S| <= 32768 (larger sets raise SSError).  Calls that overlap on the GPU
     share that array and race."""
@@ -505,3 +523,64 @@ class Batch:
             self.destroy()
         except Exception:
             pass
+
+
+# ------------------------------------------------------ the whole method
+
+LATTICE_KINDS = {"box": 0, "given": 0, "cbc": 1, "random": 2, "random_smooth": 3}
+
+
+def _lattice_spec(spec, d):
+    """ss_lattice_spec from the pipeline's lattice dictionaries ({"kind": "box",
+    "z", "M"}, {"kind": "cbc", "raw", "M_min"}, {"kind": "random", "raw",
+    "sigma", "M_min", "smooth"})."""
+    kind = spec["kind"]
+    if kind == "random" and spec.get("smooth", False):
+        kind = "random_smooth"
+    ls = LatticeSpec()
+    ls.kind = LATTICE_KINDS[kind]
+    ls.d = d
+    keep = []
+    if ls.kind == 0:
+        z = np.ascontiguousarray(np.asarray(spec["z"], dtype=np.int64))
+        keep.append(z)
+        ls.z = z.ctypes.data_as(C.POINTER(C.c_int64))
+        ls.M = int(spec["M"])
+    else:
+        raw = np.ascontiguousarray(np.asarray(spec["raw"], dtype=np.int64))
+        keep.append(raw)
+        ls.raw = raw.ctypes.data_as(C.POINTER(C.c_int64))
+        ls.n_raw = raw.shape[1] if ls.kind == 1 else raw.shape[0]
+        ls.M_min = int(spec.get("M_min", 0))
+        ls.sigma = float(spec.get("sigma", 0.05))
+    ls._keep = keep
+    return ls
+
+
+def sparse_spectral_solve(lattice, a_freq, a_coef, f_freq, f_coef, cand, N, tau=1e-9, sft_precision="fp64",
+                          solve_precision="fp64", tol=1e-12, max_iter=1000, raise_on_error=True):
+    """Algorithm 1 in one library call (lattice, SFT of a and f, stamping
+    set, right-hand side, solve).  Returns (Stamp, u on S, solve statistics,
+    z, M); the caller destroys the stamp."""
+    cd = _dev_i32(cand)
+    d = int(cd.shape[1])
+    ls = _lattice_spec(lattice, d)
+    a = _trig(a_freq, a_coef, d)
+    f = _trig(f_freq, f_coef, d)
+    z = (C.c_int64 * d)()
+    M = C.c_int64()
+    h = C.c_void_p()
+    st = SolveStats()
+    status = lib.sparse_spectral_solve(C.byref(ls), C.byref(a), C.byref(f), _ptr(cd), cd.shape[0], int(N), float(tau),
+                                       _prec(sft_precision), _prec(solve_precision), float(tol), int(max_iter), z,
+                                       C.byref(M), C.byref(h), C.byref(st), _stream())
+    if not h.value:
+        _check(status if status != 0 else 1)
+    stamp = Stamp(h.value, d)
+    if status != 0 and raise_on_error:
+        msg = lib.ss_last_error().decode(errors="replace")
+        stamp.destroy()
+        raise SSError(status, msg)
+    u = torch.empty(stamp.size, dtype=torch.complex128, device="cuda")
+    _check(lib.stamp_solution(stamp.handle, _ptr(u), _stream()))
+    return stamp, u, st.as_dict(), np.array(z[:], dtype=np.int64), M.value

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsparse_spectral.so")
-SOURCES = ["api.cu", "scan.cu", "stamp.cu", "apply.cu", "lattice.cu", "sft.cu", "solve.cu", "batch.cu", "proxy.cu"]
+SOURCES = ["api.cu", "scan.cu", "stamp.cu", "apply.cu", "lattice.cu", "sft.cu", "solve.cu", "batch.cu", "proxy.cu",
+           "pipeline.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

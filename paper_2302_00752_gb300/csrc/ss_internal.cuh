@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "../../include/sparse_spectral.h"
@@ -144,6 +145,9 @@ struct ss_stamp_s {
   ss::DevBuf<double2> bval;           // [s_a][d] b_hat_p per step (ADR)
   ss::DevBuf<double2> cval;           // [s_a] c_hat_p per step (ADR)
   ss::DevBuf<double2> diag64;         // [rows_pad + 1] diagonal of the operator (ADR; 1 on padding)
+  // right-hand side and solution kept by sparse_spectral_solve (sol_size rows)
+  ss::DevBuf<double2> rhs, sol;
+  int64_t sol_size = 0;
   ss::DevBuf<int32_t> err_dev;        // [4] device-side error words
   ss::DevBuf<int64_t> zidx_dev;       // canonical index of k = 0, or -1
 };

@@ -121,6 +121,19 @@ def run(p: Prepared, tol=1e-12, max_iter=1000, tau=None, solve_precision=None, l
     return Result(p.z, p.M, af, av, ff, fv, stamp, f_on, u, stats)
 
 
+def run_fused(p: Prepared, tol=1e-12, max_iter=1000, tau=None, solve_precision=None):
+    """Algorithm 1 through the single library call sparse_spectral_solve: the
+    same stages as run(), without returning to Python between them.  The
+    recovered coefficient lists and the right-hand side stay inside the
+    library (None here)."""
+    tau = (1e-9 if p.sft_precision == "fp64" else 1e-4) if tau is None else tau
+    stamp, u, stats, p.z, p.M = B.sparse_spectral_solve(
+        p.extra["lattice"], p.a_freq, p.a_coef, p.f_freq, p.f_coef, p.cand, p.N, tau=tau,
+        sft_precision=p.sft_precision, solve_precision=solve_precision or p.solve_precision, tol=tol,
+        max_iter=max_iter)
+    return Result(p.z, p.M, None, None, None, None, stamp, None, u, stats)
+
+
 def proxy_errors(res: Result, p: Prepared, X=None):
     """Lemma ProxyError after a solve: extends res.stamp by one level (S^{N+1}
     holds the support of L[a_hat] u^{s,N}, Proposition LExpansion) and returns

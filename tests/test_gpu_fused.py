@@ -1,0 +1,72 @@
+"""Algorithm 1 in one library call (sparse_spectral_solve) against the same
+stages called one by one: the same lattice, the same stamping set and the
+same bits of the solution; against the oracle on a small instance; and the
+error paths of the one-call form."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import pipeline as opipe
+from oracle.solve import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    from paper_2302_00752_gb300 import binding, pipeline
+    return binding, pipeline
+
+
+@pytest.mark.parametrize("make,prec", [(lambda: W.make_tiny(3, d=3, n_cos=2, n_u=3, N=2), "fp64"),
+                                       (W.make_cfg1, "fp64"), (W.make_cfg1, "fp32_refined"),
+                                       (W.make_cfg2, "fp64"), (lambda: W.make_cfg5(smooth=True), "fp32_refined")])
+def test_fused_equals_staged(mods, make, prec):
+    B, gp = mods
+    inst = make()
+    p = gp.prepare(inst)
+    staged = gp.run(p, solve_precision=prec)
+    z, M = p.z.copy(), p.M
+    fused = gp.run_fused(p, solve_precision=prec)
+    try:
+        assert np.array_equal(fused.z, z) and fused.M == M
+        assert fused.stamp.size == staged.stamp.size and fused.stamp.nnz == staged.stamp.nnz
+        assert torch.equal(fused.stamp.export()[0], staged.stamp.export()[0])
+        assert fused.stats["status"] == staged.stats["status"] == "SS_OK"
+        assert fused.stats["applies"] == staged.stats["applies"]
+        assert torch.equal(fused.u, staged.u)
+    finally:
+        fused.stamp.destroy()
+        staged.stamp.destroy()
+
+
+def test_fused_matches_oracle(mods):
+    B, gp = mods
+    inst = W.make_tiny(5, d=3, n_cos=2, n_u=3, N=2)
+    ref = opipe.run(inst)
+    res = gp.run_fused(gp.prepare(inst))
+    try:
+        S = res.stamp.export()[0].cpu().numpy()
+        assert np.array_equal(S, ref.S)
+        assert rel_l2(res.u.cpu().numpy(), ref.u) < 1e-10
+    finally:
+        res.stamp.destroy()
+
+
+def test_fused_errors_leave_no_stamp(mods):
+    B, gp = mods
+    inst = W.make_tiny(6, d=3, n_cos=2, n_u=3, N=1)
+    p = gp.prepare(inst)
+    # a box lattice that is not reconstructing for the candidate set
+    bad = {"kind": "box", "z": np.ones(3, np.int64), "M": 5}
+    with pytest.raises(B.SSError) as e:
+        B.sparse_spectral_solve(bad, p.a_freq, p.a_coef, p.f_freq, p.f_coef, p.cand, 1)
+    assert e.value.status in (1, 4)
+    # and a good call afterwards works
+    stamp, u, st, z, M = B.sparse_spectral_solve(p.extra["lattice"], p.a_freq, p.a_coef, p.f_freq, p.f_coef, p.cand,
+                                                 1)
+    try:
+        assert st["status"] == "SS_OK" and u.shape[0] == stamp.size
+    finally:
+        stamp.destroy()
