@@ -581,10 +581,12 @@ def main():
     prep = gp.prepare(inst)                         # manufactured f_hat built by the library (untimed)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    u_buf = torch.empty(1 << 20, dtype=torch.complex128, device=dev)   # solution buffer, reused by every step
+
     def step(p, keep=False):
         """One pass of Algorithm 1 through the single library call
         (sparse_spectral_solve): the timed step."""
-        r = gp.run_fused(p, tol=1e-12, max_iter=1000, tau=1e-9, solve_precision="fp64")
+        r = gp.run_fused(p, tol=1e-12, max_iter=1000, tau=1e-9, solve_precision="fp64", out=u_buf)
         st = r.stats
         if st["status"] != "SS_OK":
             raise RuntimeError(f"solve failed: {st}")

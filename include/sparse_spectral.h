@@ -391,15 +391,17 @@ typedef struct {
  * run back to back on `stream` without returning to the caller in between;
  * each synchronises where its own entry point does.  Outputs: the lattice
  * (z_out host [d], M_out), the stamping set (*stamp_out, caller destroys it;
- * the solution is kept in it, see stamp_solution) and the solve statistics
- * (stats, host, may be NULL).  Returns the first failing stage's status;
+ * the solution is kept in it, see stamp_solution), the solution copied into
+ * u_out (device FP64 complex, capacity u_cap rows; skipped when u_out is
+ * NULL or |S| > u_cap) and the solve statistics (stats, host, may be NULL).
+ * Returns the first failing stage's status;
  * SS_ERR_NOT_CONVERGED still returns the stamp, any other error destroys it
  * and leaves *stamp_out NULL. */
 ss_status sparse_spectral_solve(const ss_lattice_spec* lat, const ss_trig* a, const ss_trig* f,
                                 const int32_t* cand, int64_t n_cand, int32_t N, double tau,
                                 ss_precision sft_prec, ss_precision solve_prec, double tol, int32_t max_iter,
-                                int64_t* z_out, int64_t* M_out, ss_stamp* stamp_out, ss_solve_stats* stats,
-                                void* stream);
+                                int64_t* z_out, int64_t* M_out, ss_stamp* stamp_out, double* u_out, int64_t u_cap,
+                                ss_solve_stats* stats, void* stream);
 
 /* Copy the solution that sparse_spectral_solve left in the stamp into u_out
  * (device FP64 complex, as many rows as S had at the solve: after

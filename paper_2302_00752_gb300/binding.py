@@ -97,7 +97,7 @@ def _load():
         "batch_set_config": (i32, [vp, i32, i32, i32]),
         "batch_destroy": (None, [vp]),
         "sparse_spectral_solve": (i32, [P(LatticeSpec), P(Trig), P(Trig), vp, i64, i32, dbl, i32, i32, dbl, i32,
-                                        P(i64), P(i64), P(vp), P(SolveStats), vp]),
+                                        P(i64), P(i64), P(vp), vp, i64, P(SolveStats), vp]),
         "stamp_solution": (i32, [vp, vp, vp]),
     }
     for name, (res, args) in sigs.items():
@@ -558,10 +558,12 @@ def _lattice_spec(spec, d):
 
 
 def sparse_spectral_solve(lattice, a_freq, a_coef, f_freq, f_coef, cand, N, tau=1e-9, sft_precision="fp64",
-                          solve_precision="fp64", tol=1e-12, max_iter=1000, raise_on_error=True):
+                          solve_precision="fp64", tol=1e-12, max_iter=1000, raise_on_error=True, out=None):
     """Algorithm 1 in one library call (lattice, SFT of a and f, stamping
     set, right-hand side, solve).  Returns (Stamp, u on S, solve statistics,
-    z, M); the caller destroys the stamp."""
+    z, M); the caller destroys the stamp.  ``out``: optional complex128
+    device tensor; when it holds |S| rows the solution is written into it
+    within the call and u is its first |S| rows."""
     cd = _dev_i32(cand)
     d = int(cd.shape[1])
     ls = _lattice_spec(lattice, d)
@@ -571,9 +573,13 @@ def sparse_spectral_solve(lattice, a_freq, a_coef, f_freq, f_coef, cand, N, tau=
     M = C.c_int64()
     h = C.c_void_p()
     st = SolveStats()
+    if out is not None and not (torch.is_tensor(out) and out.is_cuda and out.dtype == torch.complex128
+                                and out.is_contiguous()):
+        raise TypeError("out must be a contiguous complex128 CUDA tensor")
+    cap = out.shape[0] if out is not None else 0
     status = lib.sparse_spectral_solve(C.byref(ls), C.byref(a), C.byref(f), _ptr(cd), cd.shape[0], int(N), float(tau),
                                        _prec(sft_precision), _prec(solve_precision), float(tol), int(max_iter), z,
-                                       C.byref(M), C.byref(h), C.byref(st), _stream())
+                                       C.byref(M), C.byref(h), _ptr(out), cap, C.byref(st), _stream())
     if not h.value:
         _check(status if status != 0 else 1)
     stamp = Stamp(h.value, d)
@@ -581,6 +587,9 @@ def sparse_spectral_solve(lattice, a_freq, a_coef, f_freq, f_coef, cand, N, tau=
         msg = lib.ss_last_error().decode(errors="replace")
         stamp.destroy()
         raise SSError(status, msg)
-    u = torch.empty(stamp.size, dtype=torch.complex128, device="cuda")
-    _check(lib.stamp_solution(stamp.handle, _ptr(u), _stream()))
+    if out is not None and stamp.size <= cap:
+        u = out[: stamp.size]
+    else:
+        u = torch.empty(stamp.size, dtype=torch.complex128, device="cuda")
+        _check(lib.stamp_solution(stamp.handle, _ptr(u), _stream()))
     return stamp, u, st.as_dict(), np.array(z[:], dtype=np.int64), M.value

@@ -1,5 +1,6 @@
 // Library-wide helpers behind the C ABI: per-thread error text, version,
 // device properties.
+#include <algorithm>
 #include <cstdarg>
 
 #include "ss_internal.cuh"
@@ -25,6 +26,48 @@ void retain_pool() {
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
   done_dev = dev;
+}
+
+namespace {
+
+struct PinnedBlock {
+  void* p = nullptr;
+  size_t n = 0;
+  ~PinnedBlock() {
+    if (p) cudaFreeHost(p);
+  }
+};
+
+thread_local PinnedBlock g_pinned;
+
+}  // namespace
+
+ss_status read_back(cudaStream_t st, std::initializer_list<HostRead> parts) {
+  size_t total = 0;
+  for (const HostRead& r : parts) total += (r.bytes + 15) / 16 * 16;
+  if (total > g_pinned.n) {
+    if (g_pinned.p) {
+      cudaFreeHost(g_pinned.p);
+      g_pinned.p = nullptr;
+      g_pinned.n = 0;
+    }
+    const size_t n = std::max<size_t>(total, 64 * 1024);
+    SS_CUDA(cudaMallocHost(&g_pinned.p, n));
+    g_pinned.n = n;
+  }
+  char* base = static_cast<char*>(g_pinned.p);
+  size_t off = 0;
+  for (const HostRead& r : parts) {
+    if (r.bytes) SS_CUDA(cudaMemcpyAsync(base + off, r.src, r.bytes, cudaMemcpyDeviceToHost, st));
+    off += (r.bytes + 15) / 16 * 16;
+  }
+  SS_CUDA(cudaStreamSynchronize(st));
+  off = 0;
+  for (const HostRead& r : parts) {
+    if (r.bytes) std::memcpy(r.dst, base + off, r.bytes);
+    off += (r.bytes + 15) / 16 * 16;
+  }
+  return SS_OK;
 }
 
 int sm_count() {

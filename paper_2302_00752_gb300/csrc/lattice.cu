@@ -267,8 +267,7 @@ ss_status check_reconstructing(const int32_t* freq, int64_t n, const LatticeDev&
   if (need_symmetric) k_check_symmetric<<<nblk(n), 256, 0, st>>>(freq, res, n, L.d, L.M, table.get(), cap - 1, flags.get());
   SS_LAUNCH_CHECK();
   int32_t h[4];
-  SS_CUDA(cudaMemcpyAsync(h, flags.get(), sizeof(h), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
+  SS_TRY(read_back(st, {{h, flags.get(), sizeof(h)}}));
   if (h[0]) SS_FAIL(SS_ERR_INVALID, "lattice: duplicate frequencies in the candidate set");
   if (h[2]) SS_FAIL(SS_ERR_HASH_FULL, "lattice: residue table exhausted");
   if (h[1]) SS_FAIL(SS_ERR_NOT_RECONSTRUCTING, "lattice (M = %lld) is not reconstructing for the candidate set",
@@ -285,8 +284,7 @@ static ss_status expansion_of(const int32_t* freq, int64_t n, int d, int64_t* K,
   SS_CUDA(cudaMemcpyAsync(mm.get(), init.data(), 2 * d * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   if (n > 0) k_minmax<<<nblk(n * d), 256, 0, st>>>(freq, n, d, mm.get(), mm.get() + d);
   SS_LAUNCH_CHECK();
-  SS_CUDA(cudaMemcpyAsync(init.data(), mm.get(), 2 * d * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
+  SS_TRY(read_back(st, {{init.data(), mm.get(), 2 * d * sizeof(int32_t)}}));
   int64_t k = 0;
   for (int c = 0; c < d && n > 0; ++c) k = std::max<int64_t>(k, (int64_t)init[d + c] - init[c]);
   *K = k;
@@ -445,9 +443,7 @@ extern "C" ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int6
     SS_LAUNCH_CHECK();
   }
   int32_t herr = 0;
-  SS_CUDA(cudaMemcpyAsync(z.data(), zdev.get(), d * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaMemcpyAsync(&herr, err.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
+  SS_TRY(read_back(st, {{z.data(), zdev.get(), d * sizeof(int64_t)}, {&herr, err.get(), sizeof(int32_t)}}));
   if (herr) SS_FAIL(SS_ERR_NOT_RECONSTRUCTING, "lattice_cbc: no candidate for coordinate %d", herr);
   for (int c = 0; c < d; ++c) z_out[c] = z[c];
   *M_out = M;

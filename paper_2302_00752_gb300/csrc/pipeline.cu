@@ -37,7 +37,8 @@ ss_status choose_lattice(const ss_lattice_spec* ls, const int32_t* cand, int64_t
 
 ss_status run(const ss_lattice_spec* ls, const ss_trig* a, const ss_trig* f, const int32_t* cand, int64_t n_cand,
               int32_t N, double tau, ss_precision sft_prec, ss_precision solve_prec, double tol, int32_t max_iter,
-              int64_t* z_out, int64_t* M_out, ss_stamp* stamp_out, ss_solve_stats* stats, cudaStream_t st) {
+              int64_t* z_out, int64_t* M_out, ss_stamp* stamp_out, double* u_out, int64_t u_cap,
+              ss_solve_stats* stats, cudaStream_t st) {
   const int d = ls->d;
   std::vector<int64_t> z(d, 1);
   int64_t M = 0;
@@ -70,6 +71,14 @@ ss_status run(const ss_lattice_spec* ls, const ss_trig* a, const ss_trig* f, con
     r = solve(s, reinterpret_cast<const double*>(s->rhs.get()), reinterpret_cast<double*>(s->sol.get()), tol,
               max_iter, solve_prec, stats, st);
     s->sol_size = s->size;
+    if (u_out && s->size <= u_cap) {
+      const cudaError_t e = cudaMemcpyAsync(u_out, s->sol.get(), s->size * sizeof(double2),
+                                            cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) {
+        set_error("sparse_spectral_solve: copy of the solution failed: %s", cudaGetErrorString(e));
+        r = SS_ERR_CUDA;
+      }
+    }
     // both buffers outlive this call (solve synchronised the stream)
     s->sol.settle();
     s->rhs.settle();
@@ -91,14 +100,14 @@ extern "C" ss_status sparse_spectral_solve(const ss_lattice_spec* lat, const ss_
                                            const int32_t* cand, int64_t n_cand, int32_t N, double tau,
                                            ss_precision sft_prec, ss_precision solve_prec, double tol,
                                            int32_t max_iter, int64_t* z_out, int64_t* M_out, ss_stamp* stamp_out,
-                                           ss_solve_stats* stats, void* stream) {
+                                           double* u_out, int64_t u_cap, ss_solve_stats* stats, void* stream) {
   if (!lat || !a || !f || !cand || n_cand < 1 || !z_out || !M_out || !stamp_out)
     SS_FAIL(SS_ERR_INVALID, "sparse_spectral_solve: null argument");
   *stamp_out = nullptr;
   if (lat->d < 1 || a->d != lat->d || f->d != lat->d)
     SS_FAIL(SS_ERR_INVALID, "sparse_spectral_solve: dimensions of the lattice, a and f differ");
-  return run(lat, a, f, cand, n_cand, N, tau, sft_prec, solve_prec, tol, max_iter, z_out, M_out, stamp_out, stats,
-             as_stream(stream));
+  return run(lat, a, f, cand, n_cand, N, tau, sft_prec, solve_prec, tol, max_iter, z_out, M_out, stamp_out, u_out,
+             u_cap, stats, as_stream(stream));
 }
 
 extern "C" ss_status stamp_solution(ss_stamp s, double* u_out, void* stream) {

@@ -699,9 +699,7 @@ ss_status recover_from(const SftPlan& P, const LatticeDev& L, const void* sample
   SS_LAUNCH_CHECK();
   int64_t kept = 0;
   int32_t hf[4];
-  SS_CUDA(cudaMemcpyAsync(&kept, total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaMemcpyAsync(hf, flags.get(), sizeof(hf), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
+  SS_TRY(read_back(st, {{&kept, total.get(), sizeof(int64_t)}, {hf, flags.get(), sizeof(hf)}}));
   SS_TRY(reconstructing_status(hf, L.M));
   if (s_max > 0 && kept > s_max)
     SS_FAIL(SS_ERR_INVALID, "sft_recover: %lld terms above threshold exceed s_max = %lld", (long long)kept,

@@ -1218,9 +1218,7 @@ ss_status read_stats(SolveWork& W, int n_inst, ss_solve_stats* stats, ss_status*
                      cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   std::vector<InstState> hs(n_inst);
   int herr = 0;
-  SS_CUDA(cudaMemcpyAsync(hs.data(), W.state.get(), n_inst * sizeof(InstState), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaMemcpyAsync(&herr, W.err.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
+  SS_TRY(read_back(st, {{hs.data(), W.state.get(), n_inst * sizeof(InstState)}, {&herr, W.err.get(), sizeof(int)}}));
   float kms = 0.f;
   if (ev_begin && ev_end) cudaEventElapsedTime(&kms, ev_begin, ev_end);
   *worst = SS_OK;
@@ -1267,8 +1265,7 @@ namespace ss {
 static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream_t st) {
   if (C.planned_mode == mode) return SS_OK;
   std::vector<int32_t> woff(s->n_slices + 1);
-  SS_CUDA(cudaMemcpyAsync(woff.data(), s->slice_off.get(), woff.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
+  SS_TRY(read_back(st, {{woff.data(), s->slice_off.get(), woff.size() * sizeof(int32_t)}}));
   C.plan.inst.assign(1, SolveInst{});
   SolveInst& in = C.plan.inst[0];
   in.row0 = 0;

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -40,6 +41,17 @@ void set_error(const char* fmt, ...);
 #define SS_LAUNCH_CHECK() SS_CUDA(cudaGetLastError())
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Small device-to-host reads.  The pieces are copied into a pinned staging
+// block of the calling thread (a copy into pageable memory is a staged,
+// blocking transfer of its own), the stream is synchronised once, and the
+// bytes are then moved to their destinations.
+struct HostRead {
+  void* dst;
+  const void* src;
+  size_t bytes;
+};
+ss_status read_back(cudaStream_t st, std::initializer_list<HostRead> parts);
 
 // ----------------------------------------------------------- device memory
 

@@ -539,9 +539,7 @@ static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st
     SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), ncand, d_total.get(), st));
     int64_t added = 0;
     int32_t e = 0;
-    SS_CUDA(cudaMemcpyAsync(&added, d_total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    SS_CUDA(cudaMemcpyAsync(&e, S->err_dev.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    SS_CUDA(cudaStreamSynchronize(st));
+    SS_TRY(read_back(st, {{&added, d_total.get(), sizeof(int64_t)}, {&e, S->err_dev.get(), sizeof(int32_t)}}));
     if (e) SS_FAIL((ss_status)e, "stamp: hash table exhausted at level %d", n);
     SS_DISPATCH_WT(S->key.WT, (k_finalize<WT><<<nblk(ncand), 256, 0, st>>>(P, S->keys.get(), par0, s_a,
                                                                            S->stepkey.get(), slot_of.get(), flag.get(),
@@ -586,10 +584,9 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   SS_TRY(exclusive_scan_i32(slice_w.get(), S->slice_off.get(), S->n_slices + 1, d_total.get(), st));
   int64_t total_w = 0;
   unsigned long long hnnz = 0;
-  SS_CUDA(cudaMemcpyAsync(&total_w, d_total.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaMemcpyAsync(&hnnz, d_nnz.get(), sizeof(hnnz), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaMemcpyAsync(&S->zero_idx, S->zidx_dev.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
+  SS_TRY(read_back(st, {{&total_w, d_total.get(), sizeof(int64_t)},
+                        {&hnnz, d_nnz.get(), sizeof(hnnz)},
+                        {&S->zero_idx, S->zidx_dev.get(), sizeof(int64_t)}}));
   S->nnz = (int64_t)hnnz;
   S->n_ent = total_w * kSlice;
   SS_TRY(S->ent.alloc(S->n_ent + 1, st));
@@ -613,8 +610,7 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
                                                         S->rec64.get());
   SS_LAUNCH_CHECK();
   int32_t e = 0;
-  SS_CUDA(cudaMemcpyAsync(&e, S->err_dev.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
+  SS_TRY(read_back(st, {{&e, S->err_dev.get(), sizeof(int32_t)}}));
   if (e) SS_FAIL((ss_status)e, "stamp: hash table exhausted");
   // the stamp's buffers outlive this call's stream (synchronised above)
   S->keys.settle(); S->level.settle(); S->norm.settle(); S->table.settle();
@@ -686,9 +682,7 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   SS_LAUNCH_CHECK();
   PrepOut h{};
   int32_t herr[4];
-  SS_CUDA(cudaMemcpyAsync(&h, prep.get(), sizeof(h), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
+  SS_TRY(read_back(st, {{&h, prep.get(), sizeof(h)}, {herr, err, sizeof(herr)}}));
   if (herr[1]) SS_FAIL(SS_ERR_INVALID, "stamp_build: duplicate frequencies in F");
   if (herr[2]) SS_FAIL(SS_ERR_INVALID, "stamp_build: duplicate frequencies in supp a_hat");
   // the ADR operator's reaction term makes u_hat_0 part of the solution, so f_hat_0 may be nonzero there
@@ -997,8 +991,7 @@ extern "C" ss_status stamp_scatter(ss_stamp s, const ss_sparse* g, double* out, 
   SS_LAUNCH_CHECK();
   if (!n_outside) return SS_OK;   // no count asked for: stays asynchronous
   unsigned long long h = 0;
-  SS_CUDA(cudaMemcpyAsync(&h, outside.get(), sizeof(h), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
+  SS_TRY(read_back(st, {{&h, outside.get(), sizeof(h)}}));
   *n_outside = (int64_t)h;
   return SS_OK;
 }

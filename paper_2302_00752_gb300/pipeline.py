@@ -121,7 +121,7 @@ def run(p: Prepared, tol=1e-12, max_iter=1000, tau=None, solve_precision=None, l
     return Result(p.z, p.M, af, av, ff, fv, stamp, f_on, u, stats)
 
 
-def run_fused(p: Prepared, tol=1e-12, max_iter=1000, tau=None, solve_precision=None):
+def run_fused(p: Prepared, tol=1e-12, max_iter=1000, tau=None, solve_precision=None, out=None):
     """Algorithm 1 through the single library call sparse_spectral_solve: the
     same stages as run(), without returning to Python between them.  The
     recovered coefficient lists and the right-hand side stay inside the
@@ -130,7 +130,7 @@ def run_fused(p: Prepared, tol=1e-12, max_iter=1000, tau=None, solve_precision=N
     stamp, u, stats, p.z, p.M = B.sparse_spectral_solve(
         p.extra["lattice"], p.a_freq, p.a_coef, p.f_freq, p.f_coef, p.cand, p.N, tau=tau,
         sft_precision=p.sft_precision, solve_precision=solve_precision or p.solve_precision, tol=tol,
-        max_iter=max_iter)
+        max_iter=max_iter, out=out)
     return Result(p.z, p.M, None, None, None, None, stamp, None, u, stats)
 
 

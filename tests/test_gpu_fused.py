@@ -41,6 +41,23 @@ def test_fused_equals_staged(mods, make, prec):
         staged.stamp.destroy()
 
 
+def test_fused_into_caller_buffer(mods):
+    B, gp = mods
+    p = gp.prepare(W.make_cfg1())
+    plain = gp.run_fused(p)
+    buf = torch.full((plain.stamp.size + 7,), 3.0 + 1j, dtype=torch.complex128, device="cuda")
+    small = torch.zeros(plain.stamp.size - 1, dtype=torch.complex128, device="cuda")
+    into = gp.run_fused(p, out=buf)
+    too_small = gp.run_fused(p, out=small)
+    try:
+        assert into.u.data_ptr() == buf.data_ptr() and torch.equal(into.u, plain.u)
+        assert torch.all(buf[plain.stamp.size:] == 3.0 + 1j)
+        assert torch.equal(too_small.u, plain.u) and not small.any()
+    finally:
+        for r in (plain, into, too_small):
+            r.stamp.destroy()
+
+
 def test_fused_matches_oracle(mods):
     B, gp = mods
     inst = W.make_tiny(5, d=3, n_cos=2, n_u=3, N=2)
