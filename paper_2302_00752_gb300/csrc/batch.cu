@@ -208,9 +208,8 @@ static ss_status batch_create_impl(ss_batch_s* b, int32_t n, const ss_stamp* sta
     SS_CUDA(cudaMemcpyAsync(b->ca64.get() + c0, s->ca64.get(), s->s_a * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     SS_CUDA(cudaMemcpyAsync(b->ca32.get() + c0, s->ca32.get(), s->s_a * sizeof(float2), cudaMemcpyDeviceToDevice, st));
     SS_CUDA(cudaMemcpyAsync(b->pn.get() + c0, s->pn32.get(), s->s_a * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-    std::vector<int32_t> w(s->n_slices + 1);
-    SS_CUDA(cudaMemcpyAsync(w.data(), s->slice_off.get(), w.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    SS_CUDA(cudaStreamSynchronize(st));
+    const std::vector<int32_t>& w = s->woff_host;
+    if ((int64_t)w.size() != s->n_slices + 1) SS_FAIL(SS_ERR_INVALID, "batch_create: stamp %d has no slice table", i);
     for (int64_t q = 0; q <= s->n_slices; ++q) b->woff_h[s0 + q] = w[q] + (int32_t)(e0 / kSlice);
     for (int64_t q = 0; q < s->n_slices; ++q) b->slice_inst_h[s0 + q] = i;
     SolveInst& in = b->plan.inst[i];

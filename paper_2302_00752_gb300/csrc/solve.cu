@@ -1264,8 +1264,8 @@ namespace ss {
 
 static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream_t st) {
   if (C.planned_mode == mode) return SS_OK;
-  std::vector<int32_t> woff(s->n_slices + 1);
-  SS_TRY(read_back(st, {{woff.data(), s->slice_off.get(), woff.size() * sizeof(int32_t)}}));
+  if ((int64_t)s->woff_host.size() != s->n_slices + 1) SS_FAIL(SS_ERR_INVALID, "solve: stamp has no slice table");
+  const std::vector<int32_t>& woff = s->woff_host;
   C.plan.inst.assign(1, SolveInst{});
   SolveInst& in = C.plan.inst[0];
   in.row0 = 0;

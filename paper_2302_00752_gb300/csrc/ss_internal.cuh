@@ -143,6 +143,7 @@ struct ss_stamp_s {
   ss::DevBuf<float2> ca32;            // [s_a] same in FP32
   // neighbour table, sliced ELL with 32-row slices, column-major in a slice
   ss::DevBuf<int32_t> slice_off;      // [n_slices + 1], in units of 32 entries (one per row of a slice)
+  std::vector<int32_t> woff_host;     // host copy of slice_off (read back with the build's sizes; solve plans)
   ss::DevBuf<uint32_t> ent;           // [n_ent] col | (j << colbits)
   ss::DevBuf<double2> ecoef64;        // [n_ent] 2 pi^2 (|k|^2 + |l|^2 - |p_j|^2) a_hat_j per entry (FP64 operator)
   ss::DevBuf<float4> ecoefdf;         // [n_ent + 1] the same as double-float, built on first DF64 solve

@@ -584,9 +584,11 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   SS_TRY(exclusive_scan_i32(slice_w.get(), S->slice_off.get(), S->n_slices + 1, d_total.get(), st));
   int64_t total_w = 0;
   unsigned long long hnnz = 0;
+  S->woff_host.resize(S->n_slices + 1);
   SS_TRY(read_back(st, {{&total_w, d_total.get(), sizeof(int64_t)},
                         {&hnnz, d_nnz.get(), sizeof(hnnz)},
-                        {&S->zero_idx, S->zidx_dev.get(), sizeof(int64_t)}}));
+                        {&S->zero_idx, S->zidx_dev.get(), sizeof(int64_t)},
+                        {S->woff_host.data(), S->slice_off.get(), (S->n_slices + 1) * sizeof(int32_t)}}));
   S->nnz = (int64_t)hnnz;
   S->n_ent = total_w * kSlice;
   SS_TRY(S->ent.alloc(S->n_ent + 1, st));
