@@ -207,6 +207,104 @@ __global__ void k_cbc_pick(const int32_t* __restrict__ fail, const int64_t* __re
   zdev[j] = z;
 }
 
+// The whole component-by-component search in one cooperative launch: block c
+// tests candidate c of every coordinate in turn.  Each block keeps the partial
+// residues rho_i = sum_{c' < j} k_{ic'} z_{c'} mod M of all frequencies in
+// shared memory, publishes pass/fail of its candidate for coordinate j, waits
+// for the other blocks (bounded wait: on timeout it records SS_ERR_TIMEOUT in
+// err[1] and returns), then takes the first candidate that passed - the same
+// pick in every block - and adds its column to rho.  Same result as the
+// per-coordinate launches below.
+__device__ __forceinline__ uint64_t modm(uint64_t x, uint64_t M, uint64_t inv) {
+  uint64_t r = x - __umul64hi(x, inv) * M;   // x < 2^62, M < 2^31: quotient estimate short by at most 2
+  r = r >= M ? r - M : r;
+  return r >= M ? r - M : r;
+}
+
+__device__ __forceinline__ uint64_t coord_mod(int32_t k, int64_t M) {
+  int64_t r = (int64_t)k % M;
+  return (uint64_t)(r < 0 ? r + M : r);
+}
+
+__device__ __forceinline__ long long cbc_timer() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__global__ void __launch_bounds__(256) k_cbc_all(const int32_t* __restrict__ f, int64_t n, int d, int64_t M,
+                                                 const int64_t* __restrict__ cand, int n_cand, int cap,
+                                                 int32_t* fail, unsigned* arrive, int64_t* zdev, int32_t* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int64_t* rho = reinterpret_cast<int64_t*>(smem);
+  int64_t* rp = rho + n;
+  int32_t* tab = reinterpret_cast<int32_t*>(rp + n);
+  __shared__ int bad, pick_s, ok_s;
+  const uint64_t inv = ~0ull / (uint64_t)M;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) rho[i] = (int64_t)coord_mod(f[i * d], M);   // z_1 = 1
+  if (blockIdx.x == 0 && threadIdx.x == 0) zdev[0] = 1;
+  const uint32_t mask = (uint32_t)cap - 1;
+  for (int j = 1; j < d; ++j) {
+    const uint64_t z = (uint64_t)cand[(int64_t)j * n_cand + blockIdx.x];
+    if (threadIdx.x == 0) bad = 0;
+    for (int i = threadIdx.x; i < cap; i += blockDim.x) tab[i] = -1;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+      rp[i] = (int64_t)modm((uint64_t)rho[i] + modm(coord_mod(f[i * d + j], M) * z, M, inv), M, inv);
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const int64_t r = rp[i];
+      uint32_t h = (uint32_t)(rhash((uint64_t)r) & mask);
+      for (int probe = 0; probe < cap; ++probe) {
+        const int32_t old = atomicCAS(tab + h, -1, (int32_t)i);
+        if (old == -1) break;
+        if (rp[old] == r) {
+          bool same = true;
+          for (int c = 0; c <= j; ++c) same &= (f[i * d + c] == f[(int64_t)old * d + c]);
+          if (!same) atomicExch(&bad, 1);
+          break;
+        }
+        h = (h + 1) & mask;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      fail[(int64_t)j * n_cand + blockIdx.x] = bad;
+      unsigned* a = arrive + j;
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a) : "memory");
+      const long long t0 = cbc_timer();
+      int ok = 1;
+      for (;;) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+        if (v >= (unsigned)gridDim.x) break;
+        if (cbc_timer() - t0 > 2000000000ll) {
+          atomicCAS(err + 1, 0, (int)SS_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+      int pick = -1;
+      if (ok)
+        for (int c = 0; c < n_cand; ++c)
+          if (!__ldcg(fail + (int64_t)j * n_cand + c)) { pick = c; break; }
+      ok_s = ok;
+      pick_s = pick;
+    }
+    __syncthreads();
+    if (!ok_s) return;
+    const int pick = pick_s;
+    const uint64_t zj = pick >= 0 ? (uint64_t)cand[(int64_t)j * n_cand + pick] : 1ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      zdev[j] = (int64_t)zj;
+      if (pick < 0 && err[0] == 0) err[0] = j + 1;
+    }
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+      rho[i] = (int64_t)modm((uint64_t)rho[i] + modm(coord_mod(f[i * d + j], M) * zj, M, inv), M, inv);
+    __syncthreads();
+  }
+}
+
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -427,6 +525,46 @@ extern "C" ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int6
   SS_CUDA(cudaMemcpyAsync(cand.get(), hc.data(), hc.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
   SS_CUDA(cudaMemsetAsync(rho.get(), 0, n * sizeof(int64_t), st));
   SS_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), st));
+  // one cooperative launch for all coordinates when the per-block tables fit
+  // in shared memory and every candidate's block can be resident at once
+  const size_t all_smem = 2 * (size_t)n * sizeof(int64_t) + (size_t)hash_cap * sizeof(int32_t);
+  int per_sm = 0;
+  bool fused = all_smem <= 200 * 1024 && d > 1;
+  if (fused) {
+    SS_CUDA(cudaFuncSetAttribute(k_cbc_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)all_smem));
+    SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cbc_all, 256, all_smem));
+    fused = (int64_t)per_sm * sm_count() >= n_cand;
+  }
+  if (fused) {
+    DevBuf<int32_t> fails;
+    DevBuf<unsigned> arrive;
+    DevBuf<int32_t> err2;
+    SS_TRY(fails.alloc((size_t)d * n_cand, st));
+    SS_TRY(arrive.alloc(d, st));
+    SS_TRY(err2.alloc(2, st));
+    SS_CUDA(cudaMemsetAsync(arrive.get(), 0, d * sizeof(unsigned), st));
+    SS_CUDA(cudaMemsetAsync(err2.get(), 0, 2 * sizeof(int32_t), st));
+    const int32_t* fa = freq;
+    int64_t na = n;
+    int da = d;
+    int64_t Ma = M;
+    const int64_t* ca = cand.get();
+    int nc = n_cand, hc = hash_cap;
+    int32_t* fp = fails.get();
+    unsigned* ap = arrive.get();
+    int64_t* zp = zdev.get();
+    int32_t* ep = err2.get();
+    void* args[] = {&fa, &na, &da, &Ma, &ca, &nc, &hc, &fp, &ap, &zp, &ep};
+    SS_CUDA(cudaLaunchCooperativeKernel((void*)k_cbc_all, dim3(n_cand), dim3(256), args, all_smem, st));
+    SS_LAUNCH_CHECK();
+    int32_t herr2[2] = {0, 0};
+    SS_TRY(read_back(st, {{z.data(), zdev.get(), d * sizeof(int64_t)}, {herr2, err2.get(), sizeof(herr2)}}));
+    if (herr2[1]) SS_FAIL((ss_status)herr2[1], "lattice_cbc: a block of the search timed out waiting for the others");
+    if (herr2[0]) SS_FAIL(SS_ERR_NOT_RECONSTRUCTING, "lattice_cbc: no candidate for coordinate %d", herr2[0]);
+    for (int c = 0; c < d; ++c) z_out[c] = z[c];
+    *M_out = M;
+    return SS_OK;
+  }
   // coordinate 0: z_1 = 1 (distinct first coordinates have distinct residues since M > K)
   SS_CUDA(cudaMemcpyAsync(zdev.get(), z.data(), sizeof(int64_t), cudaMemcpyHostToDevice, st));
   k_cbc_accept<<<nblk(n), 256, 0, st>>>(freq, n, d, 0, M, zdev.get(), rho.get());

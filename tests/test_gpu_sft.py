@@ -61,6 +61,39 @@ def test_cbc_lattice_matches_oracle(B):
     assert gM == M and np.array_equal(gz, z)
 
 
+@pytest.mark.parametrize("seed,M_min,n_cand", [(6, 5000, 48), (7, 3000, 64), (8, 20000, 8)])
+def test_cbc_lattice_later_candidates(B, seed, M_min, n_cand):
+    # M close to |I|^2 / 2: many candidates collide, so the first passing one
+    # is often not the first drawn (the pick that every block of the
+    # one-launch search must agree on)
+    rng = np.random.default_rng(seed)
+    I = np.unique(rng.integers(-9, 10, size=(120, 5)), axis=0)
+    I = np.unique(np.vstack([I, -I]), axis=0)
+    draws = {"raw": rng.integers(0, 2**62, size=(5, n_cand)), "M_min": M_min}
+    M = olat.next_smooth(max(M_min, olat.expansion(I) + 1))
+    try:
+        z, Mo = olat.cbc_lattice(I, draws)
+    except ValueError:
+        with pytest.raises(B.SSError) as e:
+            B.lattice_cbc(I, draws["raw"], draws["M_min"])
+        assert e.value.status == 4
+        return
+    gz, gM = B.lattice_cbc(I, draws["raw"], draws["M_min"])
+    assert gM == Mo == M and np.array_equal(gz, z)
+
+
+def test_cbc_lattice_no_candidate(B):
+    rng = np.random.default_rng(9)
+    I = np.unique(rng.integers(-9, 10, size=(200, 4)), axis=0)
+    I = np.unique(np.vstack([I, -I]), axis=0)
+    draws = {"raw": rng.integers(0, 2**62, size=(4, 2)), "M_min": 400}
+    with pytest.raises(ValueError):
+        olat.cbc_lattice(I, draws)
+    with pytest.raises(B.SSError) as e:
+        B.lattice_cbc(I, draws["raw"], draws["M_min"])
+    assert e.value.status == 4
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
 def test_sampling_matches_oracle(B, prec, tol):
     rng = np.random.default_rng(1)
