@@ -221,9 +221,16 @@ __device__ __forceinline__ uint64_t modm(uint64_t x, uint64_t M, uint64_t inv) {
   return r >= M ? r - M : r;
 }
 
+// k mod M in [0, M) by a 32-bit remainder (M < 2^31).
 __device__ __forceinline__ uint64_t coord_mod(int32_t k, int64_t M) {
-  int64_t r = (int64_t)k % M;
-  return (uint64_t)(r < 0 ? r + M : r);
+  const int32_t r = k % (int32_t)M;
+  return (uint64_t)(r < 0 ? r + (int32_t)M : r);
+}
+
+// (a + b) mod M for a, b in [0, M).
+__device__ __forceinline__ uint64_t addm(uint64_t a, uint64_t b, uint64_t M) {
+  const uint64_t s = a + b;
+  return s >= M ? s - M : s;
 }
 
 __device__ __forceinline__ long long cbc_timer() {
@@ -232,7 +239,9 @@ __device__ __forceinline__ long long cbc_timer() {
   return t;
 }
 
-__global__ void __launch_bounds__(256) k_cbc_all(const int32_t* __restrict__ f, int64_t n, int d, int64_t M,
+constexpr int kCbcThreads = 1024;
+
+__global__ void __launch_bounds__(kCbcThreads) k_cbc_all(const int32_t* __restrict__ f, int64_t n, int d, int64_t M,
                                                  const int64_t* __restrict__ cand, int n_cand, int cap,
                                                  int32_t* fail, unsigned* arrive, int64_t* zdev, int32_t* err) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -250,7 +259,7 @@ __global__ void __launch_bounds__(256) k_cbc_all(const int32_t* __restrict__ f, 
     for (int i = threadIdx.x; i < cap; i += blockDim.x) tab[i] = -1;
     __syncthreads();
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
-      rp[i] = (int64_t)modm((uint64_t)rho[i] + modm(coord_mod(f[i * d + j], M) * z, M, inv), M, inv);
+      rp[i] = (int64_t)addm((uint64_t)rho[i], modm(coord_mod(f[i * d + j], M) * z, M, inv), M);
     __syncthreads();
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
       const int64_t r = rp[i];
@@ -300,7 +309,7 @@ __global__ void __launch_bounds__(256) k_cbc_all(const int32_t* __restrict__ f, 
       if (pick < 0 && err[0] == 0) err[0] = j + 1;
     }
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
-      rho[i] = (int64_t)modm((uint64_t)rho[i] + modm(coord_mod(f[i * d + j], M) * zj, M, inv), M, inv);
+      rho[i] = (int64_t)addm((uint64_t)rho[i], modm(coord_mod(f[i * d + j], M) * zj, M, inv), M);
     __syncthreads();
   }
 }
@@ -532,7 +541,7 @@ extern "C" ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int6
   bool fused = all_smem <= 200 * 1024 && d > 1;
   if (fused) {
     SS_CUDA(cudaFuncSetAttribute(k_cbc_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)all_smem));
-    SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cbc_all, 256, all_smem));
+    SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cbc_all, kCbcThreads, all_smem));
     fused = (int64_t)per_sm * sm_count() >= n_cand;
   }
   if (fused) {
@@ -555,7 +564,7 @@ extern "C" ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int6
     int64_t* zp = zdev.get();
     int32_t* ep = err2.get();
     void* args[] = {&fa, &na, &da, &Ma, &ca, &nc, &hc, &fp, &ap, &zp, &ep};
-    SS_CUDA(cudaLaunchCooperativeKernel((void*)k_cbc_all, dim3(n_cand), dim3(256), args, all_smem, st));
+    SS_CUDA(cudaLaunchCooperativeKernel((void*)k_cbc_all, dim3(n_cand), dim3(kCbcThreads), args, all_smem, st));
     SS_LAUNCH_CHECK();
     int32_t herr2[2] = {0, 0};
     SS_TRY(read_back(st, {{z.data(), zdev.get(), d * sizeof(int64_t)}, {herr2, err2.get(), sizeof(herr2)}}));
