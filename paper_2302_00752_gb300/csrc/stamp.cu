@@ -38,14 +38,15 @@ __device__ int lexcmp(const int32_t* a, const int32_t* b, int d) {
 }
 
 // Stable lexicographic rank of every row (rank must start at zero); flags
-// duplicates.  Thread (i, c) compares row i with rows [64c, 64c + 64).
+// duplicates.  Thread (i, c) compares row i with rows [64c, 64c + 64); the
+// threads of a warp share c, so the rows of the chunk are broadcast loads.
 constexpr int kRankChunk = 64;
 
 __global__ void k_lex_rank(const int32_t* __restrict__ f, int64_t n, int d, int32_t* rank, int32_t* dup) {
   const int64_t nc = (n + kRankChunk - 1) / kRankChunk;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * nc) return;
-  const int64_t i = t / nc, c = t - i * nc;
+  const int64_t c = t / n, i = t - c * n;
   const int64_t j1 = min(n, (c + 1) * kRankChunk);
   int32_t r = 0;
   bool du = false;
@@ -69,10 +70,18 @@ __global__ void k_scatter_rows(const int32_t* __restrict__ f, const double2* __r
 
 // One block: ranges, symmetry of supp a_hat (a sorted symmetric set satisfies
 // A[j] = -A[s-1-j]), the zero step, Hermitian values, positivity check.
-__global__ void k_prep(const int32_t* __restrict__ F, int64_t n_f, const int32_t* __restrict__ A,
-                       const double2* __restrict__ av, int s_a, int d, PrepOut* out) {
-  __shared__ int32_t s_maxf, s_maxa, s_zf;
-  if (threadIdx.x == 0) { s_maxf = 0; s_maxa = 0; s_zf = 0; }
+// Input checks and ranges in one block: every thread takes its share of the
+// rows, the pairs (p_j, p_{s_a-1-j}) and the |a_hat_j|; thread 0 only adds
+// the |a_hat_j| in index order (deterministic) and writes the result.
+constexpr int kPrepThreads = 512;
+
+__global__ void __launch_bounds__(kPrepThreads) k_prep(const int32_t* __restrict__ F, int64_t n_f,
+                                                       const int32_t* __restrict__ A,
+                                                       const double2* __restrict__ av, int s_a, int d, PrepOut* out) {
+  __shared__ int32_t s_maxf, s_maxa, s_zf, s_sym, s_herm;
+  __shared__ unsigned long long s_amax;
+  __shared__ double s_hyp[4096];
+  if (threadIdx.x == 0) { s_maxf = 0; s_maxa = 0; s_zf = 0; s_sym = (s_a % 2 == 0); s_herm = 0; s_amax = 0; }
   __syncthreads();
   int32_t mf = 0;
   for (int64_t i = threadIdx.x; i < n_f; i += blockDim.x) {
@@ -88,28 +97,35 @@ __global__ void k_prep(const int32_t* __restrict__ F, int64_t n_f, const int32_t
   int32_t ma = 0;
   for (int64_t i = threadIdx.x; i < (int64_t)s_a * d; i += blockDim.x) ma = max(ma, abs(A[i]));
   atomicMax(&s_maxa, ma);
+  const int j0 = (s_a - 1) / 2;
+  for (int j = threadIdx.x; j < s_a; j += blockDim.x) {
+    const double h = hypot(av[j].x, av[j].y);
+    s_hyp[j] = h;
+    atomicMax(&s_amax, (unsigned long long)__double_as_longlong(h));   // h >= 0: integer order is value order
+    const int m = s_a - 1 - j;
+    for (int c = 0; c < d; ++c)
+      if (A[j * d + c] != -A[m * d + c]) atomicExch(&s_sym, 1);
+  }
+  if (threadIdx.x == 0 && s_a % 2 == 1)
+    for (int c = 0; c < d; ++c)
+      if (A[j0 * d + c] != 0) atomicExch(&s_sym, 1);
+  __syncthreads();
+  const double amax = __longlong_as_double((long long)s_amax);
+  for (int j = threadIdx.x; j < s_a; j += blockDim.x) {
+    const int m = s_a - 1 - j;
+    if (fabs(av[j].x - av[m].x) > 1e-12 * amax || fabs(av[j].y + av[m].y) > 1e-12 * amax) atomicExch(&s_herm, 1);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     out->maxabs_f = s_maxf;
     out->maxabs_a = s_maxa;
     out->zero_in_f = s_zf;
-    int bad_sym = (s_a % 2 == 0);
-    int bad_herm = 0;
-    const int j0 = (s_a - 1) / 2;
-    double amax = 0, off = 0;
-    for (int j = 0; j < s_a; ++j) amax = fmax(amax, hypot(av[j].x, av[j].y));
-    for (int j = 0; j < s_a && !bad_sym; ++j) {
-      const int m = s_a - 1 - j;
-      for (int c = 0; c < d; ++c)
-        if (A[j * d + c] != -A[m * d + c]) bad_sym = 1;
-      if (fabs(av[j].x - av[m].x) > 1e-12 * amax || fabs(av[j].y + av[m].y) > 1e-12 * amax) bad_herm = 1;
-      if (j != j0) off += hypot(av[j].x, av[j].y);
-    }
-    if (!bad_sym)
-      for (int c = 0; c < d; ++c)
-        if (A[j0 * d + c] != 0) bad_sym = 1;
+    const int bad_sym = s_sym;
+    double off = 0;
+    for (int j = 0; j < s_a; ++j)
+      if (j != j0) off += s_hyp[j];
     out->bad_sym = bad_sym;
-    out->bad_herm = bad_herm;
+    out->bad_herm = bad_sym ? 0 : s_herm;
     out->j0 = j0;
     out->a0_re = bad_sym ? 0.0 : av[j0].x;
     out->a0_abs = bad_sym ? 0.0 : hypot(av[j0].x, av[j0].y);
@@ -680,7 +696,7 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   k_lex_rank<<<nblk(s_a * nca), 256, 0, st>>>(a_hat->freq, s_a, d, rank.get(), err + 2);
   k_scatter_rows<<<nblk(s_a), 256, 0, st>>>(a_hat->freq, reinterpret_cast<const double2*>(a_hat->val), s_a, d,
                                             rank.get(), As.get(), avs.get());
-  k_prep<<<1, 256, 0, st>>>(Fs.get(), n_f, As.get(), avs.get(), s_a, d, prep.get());
+  k_prep<<<1, kPrepThreads, 0, st>>>(Fs.get(), n_f, As.get(), avs.get(), s_a, d, prep.get());
   SS_LAUNCH_CHECK();
   PrepOut h{};
   int32_t herr[4];
