@@ -52,8 +52,8 @@ ss_status run(const ss_lattice_spec* ls, const ss_trig* a, const ss_trig* f, con
   SS_TRY(av.alloc(n_cand, st));
   SS_TRY(fv.alloc(n_cand, st));
   int64_t n_a = 0, n_f = 0;
-  SS_TRY(sft_recover(&lat, a, sft_prec, cand, n_cand, 0, tau, af.get(), reinterpret_cast<double*>(av.get()), &n_a, st));
-  SS_TRY(sft_recover(&lat, f, sft_prec, cand, n_cand, 0, tau, ff.get(), reinterpret_cast<double*>(fv.get()), &n_f, st));
+  SS_TRY(sft_recover_both(&lat, a, f, sft_prec, cand, n_cand, tau, af.get(), reinterpret_cast<double*>(av.get()), &n_a,
+                          ff.get(), reinterpret_cast<double*>(fv.get()), &n_f, st));
   if (n_a < 1 || n_f < 1)
     SS_FAIL(SS_ERR_INVALID, "sparse_spectral_solve: %s has no coefficient above the threshold", n_a < 1 ? "a" : "f");
   const ss_sparse a_hat{d, n_a, af.get(), reinterpret_cast<const double*>(av.get())};

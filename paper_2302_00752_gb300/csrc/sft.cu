@@ -975,6 +975,80 @@ ss_status check_trig(const ss_trig* g, int d) {
 }
 
 }  // namespace
+
+ss_status sft_recover_both(const ss_lattice* lat, const ss_trig* a, const ss_trig* f, ss_precision prec,
+                           const int32_t* cand, int64_t n_cand, double tau, int32_t* a_freq, double* a_val,
+                           int64_t* n_a, int32_t* f_freq, double* f_val, int64_t* n_f, cudaStream_t st) {
+  LatticeDev L;
+  SS_TRY(make_lattice_dev(lat, &L));
+  SS_TRY(check_trig(a, L.d));
+  SS_TRY(check_trig(f, L.d));
+  if (!cand || n_cand < 1 || !a_freq || !a_val || !n_a || !f_freq || !f_val || !n_f)
+    SS_FAIL(SS_ERR_INVALID, "sft_recover: bad argument");
+  if (!(tau >= 0.0)) SS_FAIL(SS_ERR_INVALID, "sft_recover: tau must be >= 0");
+  if (prec != SS_FP64 && prec != SS_FP32) SS_FAIL(SS_ERR_INVALID, "sft_recover: bad precision");
+  std::shared_ptr<SftPlan> Pp;
+  SS_TRY(get_plan(L.M, prec, st, &Pp));
+  const SftPlan& P = *Pp;
+  DevBuf<int64_t> res, total;
+  DevBuf<unsigned long long> table, maxbits;
+  DevBuf<int32_t> flags, flag, pos;
+  DevBuf<double2> val;
+  DevBuf<double> mag;
+  uint64_t cap = 1;
+  while (cap < (uint64_t)(2 * n_cand)) cap <<= 1;
+  SS_TRY(res.alloc(n_cand, st));
+  SS_TRY(table.alloc(cap, st));
+  SS_TRY(flags.alloc(4, st));
+  SS_TRY(val.alloc(n_cand, st));
+  SS_TRY(mag.alloc(n_cand, st));
+  SS_TRY(maxbits.alloc(2, st));
+  SS_TRY(flag.alloc(n_cand, st));
+  SS_TRY(pos.alloc(n_cand, st));
+  SS_TRY(total.alloc(2, st));
+  // one candidate set and one lattice: residues and the check once
+  SS_TRY(residues(cand, n_cand, L, res.get(), st));
+  SS_TRY(check_reconstructing_async(cand, n_cand, L, res.get(), true, table.get(), cap, flags.get(), st));
+  cufftResult r = cufftSetStream(P.fft, st);
+  if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cufftSetStream failed: %d", (int)r);
+  SS_CUDA(cudaMemsetAsync(maxbits.get(), 0, 2 * sizeof(unsigned long long), st));
+  const ss_trig* g[2] = {a, f};
+  int32_t* fo[2] = {a_freq, f_freq};
+  double* vo[2] = {a_val, f_val};
+  for (int k = 0; k < 2; ++k) {
+    // the plan's sample and spectrum buffers serve both sums in stream order
+    SS_TRY(sample_into(P, L, g[k], P.samples.get(), st));
+    if (P.prec == SS_FP64)
+      r = cufftExecD2Z(P.fft, reinterpret_cast<cufftDoubleReal*>(P.samples.get()),
+                       reinterpret_cast<cufftDoubleComplex*>(P.spectrum.get()));
+    else
+      r = cufftExecR2C(P.fft, reinterpret_cast<cufftReal*>(P.samples.get()),
+                       reinterpret_cast<cufftComplex*>(P.spectrum.get()));
+    if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cuFFT exec failed: %d", (int)r);
+    if (P.prec == SS_FP64)
+      k_extract<double2><<<nblk(n_cand), 256, 0, st>>>(cand, n_cand, L,
+                                                       reinterpret_cast<const double2*>(P.spectrum.get()), val.get(),
+                                                       mag.get(), maxbits.get() + k);
+    else
+      k_extract<float2><<<nblk(n_cand), 256, 0, st>>>(cand, n_cand, L,
+                                                      reinterpret_cast<const float2*>(P.spectrum.get()), val.get(),
+                                                      mag.get(), maxbits.get() + k);
+    k_keep<<<nblk(n_cand), 256, 0, st>>>(mag.get(), n_cand, maxbits.get() + k, tau, flag.get());
+    SS_LAUNCH_CHECK();
+    SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), n_cand, total.get() + k, st));
+    k_compact<<<nblk(n_cand), 256, 0, st>>>(cand, val.get(), n_cand, L.d, flag.get(), pos.get(), fo[k],
+                                            reinterpret_cast<double2*>(vo[k]));
+    SS_LAUNCH_CHECK();
+  }
+  int64_t kept[2] = {0, 0};
+  int32_t hf[4];
+  SS_TRY(read_back(st, {{kept, total.get(), sizeof(kept)}, {hf, flags.get(), sizeof(hf)}}));
+  SS_TRY(reconstructing_status(hf, L.M));
+  *n_a = kept[0];
+  *n_f = kept[1];
+  return SS_OK;
+}
+
 }  // namespace ss
 
 using namespace ss;

@@ -195,6 +195,13 @@ int sm_count();
 // the diffusion problem), or -1 (none; the ADR operator keeps row 0).
 inline int64_t identity_row(const ss_stamp_s* s) { return s->adr ? -1 : s->zero_idx; }
 
+// sft_recover of a and of f on one lattice and one candidate set (sft.cu):
+// the residues and the reconstructing check once, the plan's buffers shared
+// in stream order, one read-back for both kept counts.  No s_max limit.
+ss_status sft_recover_both(const ss_lattice* lat, const ss_trig* a, const ss_trig* f, ss_precision prec,
+                           const int32_t* cand, int64_t n_cand, double tau, int32_t* a_freq, double* a_val,
+                           int64_t* n_a, int32_t* f_freq, double* f_val, int64_t* n_f, cudaStream_t st);
+
 // Releases the solver workspace cached for a stamp (solve.cu).
 void drop_solve_ctx(const ss_stamp_s* s);
 
