@@ -40,7 +40,48 @@ struct PinnedBlock {
 
 thread_local PinnedBlock g_pinned;
 
+struct UploadBlock {
+  void* p = nullptr;
+  size_t n = 0;
+  cudaEvent_t done = nullptr;   // recorded after the last copy out of the block
+  ~UploadBlock() {
+    if (done) cudaEventDestroy(done);
+    if (p) cudaFreeHost(p);
+  }
+};
+
+thread_local UploadBlock g_up;
+
 }  // namespace
+
+ss_status upload(cudaStream_t st, std::initializer_list<HostWrite> parts) {
+  size_t total = 0;
+  for (const HostWrite& w : parts) total += (w.bytes + 15) / 16 * 16;
+  if (!g_up.done) SS_CUDA(cudaEventCreateWithFlags(&g_up.done, cudaEventDisableTiming));
+  // the copies queued from the block last time must have run before it is refilled
+  SS_CUDA(cudaEventSynchronize(g_up.done));
+  if (total > g_up.n) {
+    if (g_up.p) {
+      cudaFreeHost(g_up.p);
+      g_up.p = nullptr;
+      g_up.n = 0;
+    }
+    const size_t n = std::max<size_t>(total, 64 * 1024);
+    SS_CUDA(cudaMallocHost(&g_up.p, n));
+    g_up.n = n;
+  }
+  char* base = static_cast<char*>(g_up.p);
+  size_t off = 0;
+  for (const HostWrite& w : parts) {
+    if (w.bytes) {
+      std::memcpy(base + off, w.src, w.bytes);
+      SS_CUDA(cudaMemcpyAsync(w.dst, base + off, w.bytes, cudaMemcpyHostToDevice, st));
+    }
+    off += (w.bytes + 15) / 16 * 16;
+  }
+  SS_CUDA(cudaEventRecord(g_up.done, st));
+  return SS_OK;
+}
 
 ss_status read_back(cudaStream_t st, std::initializer_list<HostRead> parts) {
   size_t total = 0;

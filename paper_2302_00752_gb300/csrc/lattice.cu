@@ -388,7 +388,7 @@ static ss_status expansion_of(const int32_t* freq, int64_t n, int d, int64_t* K,
   SS_TRY(mm.alloc(2 * d, st));
   std::vector<int32_t> init(2 * d);
   for (int c = 0; c < d; ++c) { init[c] = INT32_MAX; init[d + c] = INT32_MIN; }
-  SS_CUDA(cudaMemcpyAsync(mm.get(), init.data(), 2 * d * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  SS_TRY(upload(st, {{mm.get(), init.data(), 2 * d * sizeof(int32_t)}}));
   if (n > 0) k_minmax<<<nblk(n * d), 256, 0, st>>>(freq, n, d, mm.get(), mm.get() + d);
   SS_LAUNCH_CHECK();
   SS_TRY(read_back(st, {{init.data(), mm.get(), 2 * d * sizeof(int32_t)}}));
@@ -531,7 +531,7 @@ extern "C" ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int6
       if (r < 0) SS_FAIL(SS_ERR_INVALID, "lattice_cbc: raw draws must be non-negative");
       hc[(size_t)j * n_cand + c] = 1 + r % (M - 1);
     }
-  SS_CUDA(cudaMemcpyAsync(cand.get(), hc.data(), hc.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  SS_TRY(upload(st, {{cand.get(), hc.data(), hc.size() * sizeof(int64_t)}}));
   SS_CUDA(cudaMemsetAsync(rho.get(), 0, n * sizeof(int64_t), st));
   SS_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), st));
   // one cooperative launch for all coordinates when the per-block tables fit

@@ -1122,9 +1122,8 @@ ss_status work_upload(SolveWork& W, const SolvePlan& plan, cudaStream_t st) {
   if (n_chunk > W.cap_chunk) { SS_TRY(W.chunk.alloc(n_chunk, st)); W.cap_chunk = n_chunk; }
   if (plan.n_parts > W.cap_parts) { SS_TRY(W.part.alloc(plan.n_parts * kNQ, st)); W.cap_parts = plan.n_parts; }
   W.inst.settle(); W.state.settle(); W.chunk.settle(); W.part.settle();   // reused across calls (see read_stats)
-  SS_CUDA(cudaMemcpyAsync(W.inst.get(), plan.inst.data(), n_inst * sizeof(SolveInst), cudaMemcpyHostToDevice, st));
-  SS_CUDA(cudaMemcpyAsync(W.chunk.get(), plan.chunk.data(), n_chunk * sizeof(Chunk), cudaMemcpyHostToDevice, st));
-  return SS_OK;
+  return upload(st, {{W.inst.get(), plan.inst.data(), n_inst * sizeof(SolveInst)},
+                     {W.chunk.get(), plan.chunk.data(), n_chunk * sizeof(Chunk)}});
 }
 
 ss_status max_grid(int mode, int block, int* grid) {
@@ -1289,8 +1288,7 @@ static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream
     SS_TRY(ensure_ecoefdf(s, st));
     SS_TRY(work_alloc_df64(C.work, st));
   }
-  SS_TRY(work_upload(C.work, C.plan, st));
-  C.planned_mode = mode;
+  C.planned_mode = mode;   // the plan goes to the device with the call's f and u (solve)
   return SS_OK;
 }
 

@@ -53,6 +53,16 @@ struct HostRead {
 };
 ss_status read_back(cudaStream_t st, std::initializer_list<HostRead> parts);
 
+// Small host-to-device writes, queued on `st` from a pinned block of the
+// calling thread (a pageable source makes the runtime stage each copy while
+// the host waits).  The block is reused once the previous upload has run.
+struct HostWrite {
+  void* dst;
+  const void* src;
+  size_t bytes;
+};
+ss_status upload(cudaStream_t st, std::initializer_list<HostWrite> parts);
+
 // ----------------------------------------------------------- device memory
 
 // Keeps freed device memory in the default stream-ordered pool (set once per
