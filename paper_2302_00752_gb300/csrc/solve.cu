@@ -1083,8 +1083,10 @@ ss_status work_alloc(SolveWork& W, int64_t rows_total, const int64_t* norm, cons
   k_init_solve_records<<<nblk(rows_total), 256, 0, st>>>(norm, rows_total, wide_rows, wide, W.xrec.get(),
                                                          W.urec64.get(), W.urec32.get());
   SS_LAUNCH_CHECK();
-  // the workspace is reused by later calls, possibly on other streams
-  SS_CUDA(cudaStreamSynchronize(st));
+  // The workspace is reused by later calls, possibly on other streams: both
+  // callers synchronise `st` before they return (solve when it reads the
+  // statistics, batch_create right after this), which orders those calls
+  // after these allocations.
   W.xrec.settle(); W.urec64.settle(); W.urec32.settle(); W.r.settle(); W.w64.settle(); W.w32.settle();
   W.pd.settle(); W.sd.settle(); W.rhat.settle(); W.dlt.settle(); W.bar.settle(); W.counters.settle();
   W.err.settle(); W.r32.settle(); W.p32.settle(); W.s32.settle(); W.d32.settle(); W.rdiag.settle();
