@@ -590,8 +590,8 @@ def main():
         st = r.stats
         if st["status"] != "SS_OK":
             raise RuntimeError(f"solve failed: {st}")
-        out = {"nnz": r.stamp.nnz, "size": r.stamp.size, "applies": st["applies"], "iters": st["inner_iters"],
-               "times": {"solve_kernel": st["kernel_ms"]}, "u": r.u, "stats": st}
+        out = {"nnz": r.stamp.nnz, "size": r.stamp.size, "zero_index": r.stamp.zero_index, "applies": st["applies"],
+               "iters": st["inner_iters"], "times": {"solve_kernel": st["kernel_ms"]}, "u": r.u, "stats": st}
         if keep:
             out["stamp"] = r.stamp
         else:
@@ -693,13 +693,14 @@ def main():
     for k, v in zip(inst.u_freq.tolist(), inst.u_val):
         exact[idx[tuple(k)]] = v
     tts = {}
-    for prec in ("fp64", "fp32", "df64"):
+    for prec in ("fp64", "fp64_full", "fp32", "df64"):
         times, kern = [], []
+        stamp.set_symmetry(prec != "fp64_full")        # fp64_full: the full system, for comparison
         for _ in range(5):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            u, st = B.solve(stamp, f_on, 1e-12, 1000, prec)
+            u, st = B.solve(stamp, f_on, 1e-12, 1000, "fp64" if prec == "fp64_full" else prec)
             b.record()
             b.synchronize()
             times.append(a.elapsed_time(b))
@@ -709,6 +710,7 @@ def main():
         tts[prec] = {"time_to_solution_ms": statistics.median(times), "kernel_ms": statistics.median(kern),
                      "rel_l2_err_vs_exact": err, "rel_residual": st["rel_residual"], "applies": st["applies"],
                      "outer_iters": st["outer_iters"], "inner_iters": st["inner_iters"],
+                     "half_system": st["half_system"],
                      "nnz_per_s": stamp.nnz * st["applies"] / (statistics.median(kern) / 1e3)}
 
     # end to end through the C ABI with host buffers: H2D of the data, D2H of u
@@ -734,12 +736,17 @@ def main():
     e2e_value = world * e2e_work / (sum(e2e_ms) / 1e3)
 
     # roofline of the dominant kernel: the persistent FP64 CG (FP64 ALU bound;
-    # algorithmic flops: 8 per stored nonzero and application, 30 per row and
-    # CG iteration - see the design doc)
+    # algorithmic flops: 8 per processed nonzero and application, 30 per
+    # processed row and CG iteration - see the design doc).  With the Hermitian
+    # half system the CG processes the rows k >lex 0 and their nonzeros, half
+    # of S and half of L's nonzeros (symmetric S; the zero row stores none).
     med = {k: statistics.median(v) for k, v in stage.items()}
     nnz, size, iters = r["nnz"], r["size"], r["iters"]
     applies = r["applies"]
-    solve_flops = 8.0 * nnz * applies + 30.0 * size * iters
+    half = bool(r["stats"].get("half_system"))
+    nnz_p = nnz / 2 if half else nnz
+    rows_p = (size - (1 if r["zero_index"] >= 0 else 0)) // 2 if half else size
+    solve_flops = 8.0 * nnz_p * applies + 30.0 * rows_p * iters
     kms = med["solve_kernel"]
     clk = clocks.summary()
     sm_max = clk.get("sm_max_mhz") or 2070.0
@@ -748,7 +755,8 @@ def main():
     roofline = {"kernel": "k_solve<0> (persistent FP64 CG)", "bound": "alu", "achieved": achieved, "peak": peak64,
                 "unit": "GFLOP/s (FP64)", "frac": achieved / peak64, "traffic": None,
                 "peak_source": "derived: 1 FP64 FMA/clk/SM (ncu FP64-pipe counters) x 152 SMs x 2 x sm_max_mhz",
-                "flops_per_launch": solve_flops, "kernel_ms": kms}
+                "flops_per_launch": solve_flops, "kernel_ms": kms, "half_system": half,
+                "processed_nnz": nnz_p, "processed_rows": rows_p}
     launches_per_step = count_launches(lambda: step(prep))
     gpu_launches = launches_per_step * args.steps if launches_per_step is not None else None
 
@@ -815,6 +823,10 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "cfg2: d=10 plain FP64, s_a=21, manufactured u (20 pairs), |supp f|=840, N=3",
                        "stamp_size": size, "nnz": nnz, "M": int(prep.M), "l2_flush": True,
+                       "nnz_counting": ("value counts the nonzeros of L_{N,s} per operator application; the FP64 "
+                                        "CG runs the Hermitian half system (rows k >lex 0, half of the stored "
+                                        "nonzeros per application, the rest by u_{-k} = conj(u_k)) when "
+                                        "half_system is true; processed_nnz_per_s counts the nonzeros it reads"),
                        "parallelism": "replicas" if world > 1 else "single"},
             "e2e": {"value": e2e_value, "unit": "nnz/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": sum(e2e_ms) / len(e2e_ms)},
@@ -823,6 +835,8 @@ def main():
             "step_form": ("timed step: sparse_spectral_solve (one library call for lattice, both SFTs, stamp, "
                           "right-hand side, solve); breakdown_ms and staged_ms_per_step from the same stages "
                           "called one by one from Python with events between them"),
+            "processed_nnz_per_s": value * (nnz_p / nnz if nnz else 1.0),
+            "half_system": half,
             "solve_only": tts,
             "stamp": stamp_stats,
             "roofline": roofline,

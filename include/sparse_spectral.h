@@ -84,6 +84,7 @@ typedef struct {
     int32_t applies;       /* operator applications (FP64 + FP32) */
     double rel_residual;   /* ||f - L u||_2 / ||f||_2 in FP64 at exit */
     double kernel_ms;      /* duration of the persistent solver launch (CUDA events on the stream) */
+    int32_t half_system;   /* 1 when the Hermitian half system was solved (see solve) */
 } ss_solve_stats;
 
 const char* ss_last_error(void);
@@ -303,6 +304,19 @@ ss_status proxy_mc(ss_stamp s, const double* u_prefix, int64_t n_u, const ss_tri
  * is unrestricted there. */
 ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, double tol, int32_t max_iter,
                 ss_precision prec, ss_solve_stats* stats, void* stream);
+
+/* Hermitian half system (no counterpart in the paper, which solves the full
+ * system): for real data - F = -F and a_hat_{-p} = conj(a_hat_p) bit for bit,
+ * which stamp_build detects - S is symmetric and L maps Hermitian vectors
+ * (u_{-k} = conj(u_k)) to Hermitian vectors, so for a Hermitian f the rows
+ * k >lex 0 carry the whole solution.  solve in SS_FP64 then runs the same CG
+ * on those rows only, reading a neighbour l <lex 0 as conj(u_{-l}) (half the
+ * rows and half the stored nonzeros per application; CG scalars and the
+ * residual ratio are those of the full system up to rounding), and unfolds u
+ * over S; stats->half_system = 1.  An f that is not Hermitian bit for bit
+ * falls back to the full system within the same call.  use_half = 0 always
+ * solves the full system (default 1). */
+ss_status solve_set_symmetry(ss_stamp s, int32_t use_half);
 
 /* Tile shape of this stamp's persistent solve: threads per block (128, 256,
  * 512 or 1024), resident blocks per SM (0 = as many as fit) and static work

@@ -48,12 +48,13 @@ class LatticeSpec(C.Structure):
 
 class SolveStats(C.Structure):
     _fields_ = [("status", C.c_int32), ("outer_iters", C.c_int32), ("inner_iters", C.c_int32),
-                ("applies", C.c_int32), ("rel_residual", C.c_double), ("kernel_ms", C.c_double)]
+                ("applies", C.c_int32), ("rel_residual", C.c_double), ("kernel_ms", C.c_double),
+                ("half_system", C.c_int32)]
 
     def as_dict(self):
         return {"status": STATUS.get(self.status, self.status), "outer_iters": self.outer_iters,
                 "inner_iters": self.inner_iters, "applies": self.applies, "rel_residual": self.rel_residual,
-                "kernel_ms": self.kernel_ms}
+                "kernel_ms": self.kernel_ms, "half_system": bool(self.half_system)}
 
 
 def _load():
@@ -89,6 +90,7 @@ def _load():
         "galerkin_apply": (i32, [vp, vp, vp, i32, vp]),
         "solve": (i32, [vp, vp, vp, dbl, i32, i32, P(SolveStats), vp]),
         "solve_set_config": (i32, [vp, i32, i32, i32]),
+        "solve_set_symmetry": (i32, [vp, i32]),
         "solve_noalloc": (i32, [vp, vp, vp, dbl, i32, i32, P(SolveStats), vp]),
         "batch_create": (i32, [i32, P(vp), P(vp), vp]),
         "batch_solve": (i32, [vp, P(vp), P(vp), dbl, i32, i32, i32, P(SolveStats), vp]),
@@ -340,6 +342,10 @@ class Stamp:
         _check(lib.stamp_info(self._h, C.byref(size), C.byref(nnz), C.byref(zero), C.byref(lv)))
         self.size, self.nnz, self.zero_index, self.n_levels = size.value, nnz.value, zero.value, lv.value
         return self
+
+    def set_symmetry(self, use_half):
+        """Solve real data through the Hermitian half system (default True)."""
+        _check(lib.solve_set_symmetry(self.handle, int(bool(use_half))))
 
     def set_solve_config(self, block, blocks_per_sm, chunks_per_block):
         """Tile shape of the persistent solve (see solve_set_config)."""

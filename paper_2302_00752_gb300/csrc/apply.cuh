@@ -34,7 +34,16 @@ struct OpView {
   const float4* ecoefdf;   // the same as double-float (re.hi, re.lo, im.hi, im.lo), or null
   int colbits;
   uint32_t colmask;
+  bool conj = false;       // half system: entry bit 31 set = the neighbour's value is conjugated
 };
+
+// Imaginary part of a gathered value, negated (the value conjugated) when the
+// table is a half-system table and the entry's bit 31 is set: a sign flip on
+// the integer pipe.
+__device__ __forceinline__ double conj_if(double y, bool conj, uint32_t ent) {
+  const unsigned long long m = conj ? (unsigned long long)(ent >> 31) << 63 : 0ull;
+  return __longlong_as_double(__double_as_longlong(y) ^ (long long)m);
+}
 
 // Accumulate row `row` (lane of slice s) of L u in FP64 from the stored entry
 // coefficients (four FP64 FMAs per nonzero: GB300 issues one FP64 FMA per SM
@@ -58,7 +67,10 @@ __device__ __forceinline__ double2 row_apply64(const OpView& op, int64_t s, int 
       c[q] = __ldg(cf + (int64_t)(t + q) * kSlice);
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = ldv<CG>(rec + 2 * (int64_t)(ee[q] & op.colmask));
+    for (int q = 0; q < 4; ++q) {
+      v[q] = ldv<CG>(rec + 2 * (int64_t)(ee[q] & op.colmask));
+      v[q].y = conj_if(v[q].y, op.conj, ee[q]);
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       ar = fma(c[q].x, v[q].x, ar); ar = fma(-c[q].y, v[q].y, ar);
@@ -68,7 +80,8 @@ __device__ __forceinline__ double2 row_apply64(const OpView& op, int64_t s, int 
   for (; t < w; ++t) {
     const uint32_t ee = __ldg(e + (int64_t)t * kSlice);
     const double2 c = __ldg(cf + (int64_t)t * kSlice);
-    const double2 v = ldv<CG>(rec + 2 * (int64_t)(ee & op.colmask));
+    double2 v = ldv<CG>(rec + 2 * (int64_t)(ee & op.colmask));
+    v.y = conj_if(v.y, op.conj, ee);
     ar = fma(c.x, v.x, ar); ar = fma(-c.y, v.y, ar);
     ai = fma(c.x, v.y, ai); ai = fma(c.y, v.x, ai);
   }

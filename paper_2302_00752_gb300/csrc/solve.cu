@@ -1236,6 +1236,7 @@ ss_status read_stats(SolveWork& W, int n_inst, ss_solve_stats* stats, ss_status*
       stats[i].applies = s.applies;
       stats[i].rel_residual = s.bb > 0 ? std::sqrt(s.rr / s.bb) : 0.0;
       stats[i].kernel_ms = kms;
+      stats[i].half_system = 0;
     }
     if (*worst == SS_OK && s.status != SS_OK) {
       *worst = (ss_status)s.status;
@@ -1256,8 +1257,17 @@ struct ss_solve_ctx {
   int planned_mode = -1;
   int block = 1024, blocks_per_sm = 1, chunks_per_block = 1;   // tile shape (solve_set_config)
   double2* f0_host = nullptr;   // pinned copy of f_hat_0, checked after the solve's own synchronisation
+  // Hermitian half system (FP64 CG): its own plan and workspace, the compact
+  // right-hand side and solution, and the "f is not Hermitian" flag
+  bool use_half = true;
+  ss_solve_ctx* half = nullptr;
+  ss::DevBuf<double2> fh, uh;
+  ss::DevBuf<int32_t> hflag;
+  int32_t* hflag_host = nullptr;
   ~ss_solve_ctx() {
     if (f0_host) cudaFreeHost(f0_host);
+    if (hflag_host) cudaFreeHost(hflag_host);
+    delete half;
   }
 };
 
@@ -1293,6 +1303,64 @@ static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream
   C.planned_mode = mode;   // the plan goes to the device with the call's f and u (solve)
   return SS_OK;
 }
+
+// Plan and workspace of the Hermitian half system (FP64 CG only).
+static ss_status stamp_plan_half(ss_stamp_s* s, ss_solve_ctx& H, cudaStream_t st) {
+  if (H.planned_mode == 0) return SS_OK;
+  if ((int64_t)s->woff_h_host.size() != s->n_slices_h + 1) SS_FAIL(SS_ERR_INVALID, "solve: no half-system table");
+  H.plan.inst.assign(1, SolveInst{});
+  SolveInst& in = H.plan.inst[0];
+  in.row0 = 0;
+  in.rows = s->n_plus;
+  in.rows_pad = s->rows_pad_h;
+  in.zero_row = -1;                      // k = 0 is not a row of the half system
+  in.coef_off = 0;
+  in.dscale = 2.0 * kTwoPiSq * s->a0;
+  in.wide = s->wide ? 1 : 0;
+  int grid = 0;
+  H.plan.block = H.block;
+  SS_TRY(max_grid(0, H.plan.block, &grid));
+  if (H.blocks_per_sm > 0) grid = std::min(grid, H.blocks_per_sm * sm_count());
+  const int by_size = (int)std::max<int64_t>(1, s->n_slices_h / 8);
+  const int target = std::min<int64_t>((int64_t)grid * H.chunks_per_block, by_size);
+  SS_TRY(plan_chunks(H.plan, s->woff_h_host, {}, target));
+  H.plan.grid = std::min<int>(grid, (int)H.plan.chunk.size());
+  SS_TRY(work_alloc(H.work, s->rows_pad_h + 1, s->norm_h.get(), nullptr, s->wide, st));
+  H.planned_mode = 0;
+  return SS_OK;
+}
+
+namespace {
+
+// Compact right-hand side f_h[i] = f[k_i] (k_i > 0); flags an f that is not
+// Hermitian (f_{-k} != conj(f_k) bit for bit) so the full system is solved instead.
+__global__ void k_half_gather(const double2* __restrict__ f, const int32_t* __restrict__ plus_rows,
+                              const int64_t* __restrict__ mirror, int64_t n_plus, double2* f_h, int32_t* flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_plus) return;
+  const int64_t g = plus_rows[i];
+  const double2 a = f[g], b = f[mirror[g]];
+  if (!(a.x == b.x && a.y == -b.y)) atomicExch(flag, 1);
+  f_h[i] = a;
+}
+
+// u on S from the compact solution: u_k (k > 0), conj(u_{-k}) (k < 0), 0 (k = 0).
+__global__ void k_half_scatter(const double2* __restrict__ u_h, const int32_t* __restrict__ hpos, int64_t size,
+                               double2* u) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= size) return;
+  const int32_t h = hpos[g];
+  if (h == -1) {
+    u[g] = make_double2(0.0, 0.0);
+  } else if (h >= 0) {
+    u[g] = u_h[h];
+  } else {
+    const double2 v = u_h[-2 - h];
+    u[g] = make_double2(v.x, -v.y);
+  }
+}
+
+}  // namespace
 
 }  // namespace ss
 
@@ -1335,6 +1403,12 @@ extern "C" ss_status solve_set_config(ss_stamp s, int32_t block, int32_t blocks_
   return SS_OK;
 }
 
+extern "C" ss_status solve_set_symmetry(ss_stamp s, int32_t use_half) {
+  if (!s) SS_FAIL(SS_ERR_INVALID, "solve_set_symmetry: null stamp");
+  solve_ctx(s)->use_half = use_half != 0;
+  return SS_OK;
+}
+
 extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, double tol, int32_t max_iter,
                            ss_precision prec, ss_solve_stats* stats, void* stream) {
   if (!s || !f_on_S || !u_on_S) SS_FAIL(SS_ERR_INVALID, "solve: null argument");
@@ -1351,6 +1425,65 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
                             cudaMemcpyDeviceToHost, st));
   }
   const int mode = s->adr ? 2 : (prec == SS_FP64 ? 0 : (prec == SS_FP32 ? 1 : 3));
+  if (mode == 0 && s->half_ok && C->use_half) {
+    // Real data: solve the Hermitian half system (rows k >lex 0, neighbours
+    // below read as conjugates), then unfold; if f turns out not to be
+    // Hermitian the full system below is solved instead.
+    if (!C->half) C->half = new ss_solve_ctx();
+    ss_solve_ctx* H = C->half;
+    if (H->block != C->block || H->blocks_per_sm != C->blocks_per_sm || H->chunks_per_block != C->chunks_per_block) {
+      H->block = C->block;
+      H->blocks_per_sm = C->blocks_per_sm;
+      H->chunks_per_block = C->chunks_per_block;
+      H->planned_mode = -1;
+    }
+    SS_TRY(stamp_plan_half(s, *H, st));
+    SS_TRY(C->fh.ensure(s->rows_pad_h, st));
+    SS_TRY(C->uh.ensure(s->rows_pad_h, st));
+    SS_TRY(C->hflag.ensure(1, st));
+    if (!C->hflag_host) SS_CUDA(cudaMallocHost(&C->hflag_host, sizeof(int32_t)));
+    SS_CUDA(cudaMemsetAsync(C->hflag.get(), 0, sizeof(int32_t), st));
+    const unsigned gb = (unsigned)((s->n_plus + 255) / 256), sb = (unsigned)((s->size + 255) / 256);
+    k_half_gather<<<gb, 256, 0, st>>>(reinterpret_cast<const double2*>(f_on_S), s->plus_rows.get(), s->mirror.get(),
+                                      s->n_plus, C->fh.get(), C->hflag.get());
+    SS_LAUNCH_CHECK();
+    H->plan.inst[0].f = C->fh.get();
+    H->plan.inst[0].u = C->uh.get();
+    SS_TRY(work_upload(H->work, H->plan, st));
+    OpView hop;
+    hop.woff = s->woff_h.get();
+    hop.ent = s->ent_h.get();
+    hop.ecoef = s->ecoef_h.get();
+    hop.ecoefdf = nullptr;
+    hop.colbits = 31;
+    hop.colmask = 0x7fffffffu;
+    hop.conj = true;
+    if (!H->work.ev[0]) {
+      SS_CUDA(cudaEventCreate(&H->work.ev[0]));
+      SS_CUDA(cudaEventCreate(&H->work.ev[1]));
+    }
+    SS_TRY(launch_solve(H->work, H->plan, hop, nullptr, s->norm_h.get(), s->ca64.get(), s->ca32.get(), s->pn32.get(),
+                        tol, max_iter, 0, st, H->work.ev[0], H->work.ev[1], nullptr));
+    k_half_scatter<<<sb, 256, 0, st>>>(C->uh.get(), s->hpos.get(), s->size, reinterpret_cast<double2*>(u_on_S));
+    SS_LAUNCH_CHECK();
+    SS_CUDA(cudaMemcpyAsync(C->hflag_host, C->hflag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    ss_status worst;
+    ss_solve_stats one{};
+    SS_TRY(read_stats(H->work, 1, &one, &worst, st, H->work.ev[0], H->work.ev[1]));
+    C->fh.settle();
+    C->uh.settle();
+    C->hflag.settle();
+    if (*C->hflag_host == 0) {
+      one.half_system = 1;
+      if (check_f0 && (C->f0_host->x != 0.0 || C->f0_host->y != 0.0)) {
+        one.status = SS_ERR_INVALID;
+        if (stats) *stats = one;
+        SS_FAIL(SS_ERR_INVALID, "solve: f_hat_0 must be 0 (mean-zero forcing)");
+      }
+      if (stats) *stats = one;
+      return worst;
+    }
+  }
   SS_TRY(stamp_plan(s, *C, mode, st));
   C->plan.inst[0].f = reinterpret_cast<const double2*>(f_on_S);
   C->plan.inst[0].u = reinterpret_cast<double2*>(u_on_S);

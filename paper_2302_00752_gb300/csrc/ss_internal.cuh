@@ -168,6 +168,19 @@ struct ss_stamp_s {
   ss::DevBuf<double2> bval;           // [s_a][d] b_hat_p per step (ADR)
   ss::DevBuf<double2> cval;           // [s_a] c_hat_p per step (ADR)
   ss::DevBuf<double2> diag64;         // [rows_pad + 1] diagonal of the operator (ADR; 1 on padding)
+  // Hermitian half system (real data): compact rows k >lex 0 in canonical
+  // order; a neighbour l < 0 is read as conj(u_{-l}) (entry bit 31).
+  bool half_cand = false;             // F = -F and a_hat exactly Hermitian (set by the build)
+  bool half_ok = false;               // half system built for the current set
+  int64_t n_plus = 0, rows_pad_h = 0, n_slices_h = 0;
+  ss::DevBuf<int64_t> mirror;         // [size] canonical index of -k
+  ss::DevBuf<int32_t> hpos;           // [size] i (k > 0), -2 - i (k < 0, i the row of -k), -1 (k = 0)
+  ss::DevBuf<int32_t> plus_rows;      // [rows_pad_h] canonical index of compact row i
+  ss::DevBuf<int32_t> woff_h;         // [n_slices_h + 1]
+  ss::DevBuf<uint32_t> ent_h;         // col | conj << 31 (dummy column rows_pad_h)
+  ss::DevBuf<double2> ecoef_h;        // FP64 entry coefficients of the half table
+  ss::DevBuf<int64_t> norm_h;         // [rows_pad_h + 1] |k|^2 of the compact rows (0 on padding)
+  std::vector<int32_t> woff_h_host;
   // right-hand side and solution kept by sparse_spectral_solve (sol_size rows)
   ss::DevBuf<double2> rhs, sol;
   int64_t sol_size = 0;

@@ -27,6 +27,7 @@ struct PrepOut {
   int32_t maxabs_f, maxabs_a;
   int32_t dup_f, dup_a;
   int32_t bad_sym, zero_in_f, bad_herm, j0;
+  int32_t f_sym, herm_exact;   // F = -F (F sorted); a_hat_{-p} == conj(a_hat_p) bit for bit
   double a0_re, a0_abs, off_l1, amax;
 };
 
@@ -78,10 +79,12 @@ constexpr int kPrepThreads = 512;
 __global__ void __launch_bounds__(kPrepThreads) k_prep(const int32_t* __restrict__ F, int64_t n_f,
                                                        const int32_t* __restrict__ A,
                                                        const double2* __restrict__ av, int s_a, int d, PrepOut* out) {
-  __shared__ int32_t s_maxf, s_maxa, s_zf, s_sym, s_herm;
+  __shared__ int32_t s_maxf, s_maxa, s_zf, s_sym, s_herm, s_fasym, s_hinexact;
   __shared__ unsigned long long s_amax;
   __shared__ double s_hyp[4096];
-  if (threadIdx.x == 0) { s_maxf = 0; s_maxa = 0; s_zf = 0; s_sym = (s_a % 2 == 0); s_herm = 0; s_amax = 0; }
+  if (threadIdx.x == 0) {
+    s_maxf = 0; s_maxa = 0; s_zf = 0; s_sym = (s_a % 2 == 0); s_herm = 0; s_amax = 0; s_fasym = 0; s_hinexact = 0;
+  }
   __syncthreads();
   int32_t mf = 0;
   for (int64_t i = threadIdx.x; i < n_f; i += blockDim.x) {
@@ -92,6 +95,10 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const int32_t* __restrict
       zero &= (x == 0);
     }
     if (zero) atomicExch(&s_zf, 1);
+    // F sorted lexicographically: F = -F iff row i is minus row n_f - 1 - i
+    const int64_t m = n_f - 1 - i;
+    for (int c = 0; c < d; ++c)
+      if (F[i * d + c] != -F[m * d + c]) atomicExch(&s_fasym, 1);
   }
   atomicMax(&s_maxf, mf);
   int32_t ma = 0;
@@ -114,6 +121,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const int32_t* __restrict
   for (int j = threadIdx.x; j < s_a; j += blockDim.x) {
     const int m = s_a - 1 - j;
     if (fabs(av[j].x - av[m].x) > 1e-12 * amax || fabs(av[j].y + av[m].y) > 1e-12 * amax) atomicExch(&s_herm, 1);
+    if (!(av[j].x == av[m].x && av[j].y == -av[m].y)) atomicExch(&s_hinexact, 1);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -131,6 +139,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const int32_t* __restrict
     out->a0_abs = bad_sym ? 0.0 : hypot(av[j0].x, av[j0].y);
     out->off_l1 = off;
     out->amax = amax;
+    out->f_sym = !s_fasym;
+    out->herm_exact = !bad_sym && !s_hinexact;
   }
 }
 
@@ -569,6 +579,163 @@ static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st
   return SS_OK;
 }
 
+// ---------------------------------------------------- Hermitian half system
+//
+// For real data (F = -F, a_hat_{-p} = conj(a_hat_p)) S is symmetric and the
+// operator maps Hermitian vectors (u_{-k} = conj(u_k)) to Hermitian vectors,
+// so for a Hermitian right-hand side the rows k >lex 0 carry the whole
+// solution.  The half system keeps those rows ("compact rows", canonical
+// order) and reads a neighbour l <lex 0 as conj(u_{-l}).
+
+// mirror[g] = index of -k_g (negation is field-wise 2 bias - v on the packed
+// key, no carries since |k_c| < 2^(b-1)); plus[g] = 1 if k_g >lex 0.
+template <int WT>
+__global__ void k_half_index(KeyParams P, const uint64_t* __restrict__ keys, int64_t size,
+                             const uint64_t* __restrict__ table, uint64_t capmask, int64_t* mirror, int32_t* plus,
+                             int32_t* err) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= size) return;
+  uint64_t k[WT], n[WT];
+  load_key<WT>(keys, g, k);
+#pragma unroll
+  for (int w = 0; w < WT; ++w) n[w] = 2 * P.bias[w] - k[w];
+  const int64_t m = table_find<WT>(table, capmask, keys, n);
+  if (m < 0) atomicExch(err, 1);
+  mirror[g] = m;
+  int p = 0;
+  for (int c = 0; c < P.d; ++c) {
+    const int32_t x = unpack_coord(k, P, c);
+    if (x != 0) { p = x > 0; break; }
+  }
+  plus[g] = p;
+}
+
+// Indices stay in range even for a set that is not symmetric (a missing -k
+// sets the error word and the half system is dropped after the read-back).
+__global__ void k_half_rows(const int32_t* __restrict__ plus, const int32_t* __restrict__ ppos,
+                            const int64_t* __restrict__ mirror, const int64_t* __restrict__ norm, int64_t size,
+                            int64_t zero_idx, int64_t n_plus, int32_t* hpos, int32_t* plus_rows, int64_t* norm_h) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= size) return;
+  if (plus[g]) {
+    const int32_t i = ppos[g];
+    hpos[g] = i;
+    if (i < n_plus) {
+      plus_rows[i] = (int32_t)g;
+      norm_h[i] = norm[g];
+    }
+  } else if (g == zero_idx || mirror[g] < 0) {
+    hpos[g] = -1;
+  } else {
+    hpos[g] = -2 - ppos[mirror[g]];
+  }
+}
+
+// Width of every compact row (its stored entries), warp maximum per slice.
+__global__ void k_half_widths(const int32_t* __restrict__ plus_rows, int64_t n_plus, int64_t rows_pad_h,
+                              const int32_t* __restrict__ woff, const uint32_t* __restrict__ ent, uint32_t colmask,
+                              int64_t pad_col, int32_t* slice_w) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows_pad_h) return;
+  int32_t cnt = 0;
+  if (i < n_plus) {
+    const int64_t g = plus_rows[i];
+    const int64_t s = g / kSlice;
+    const int64_t base = (int64_t)woff[s] * kSlice + (g % kSlice);
+    const int w = woff[s + 1] - woff[s];
+    for (int t = 0; t < w; ++t)
+      if ((int64_t)(ent[base + (int64_t)t * kSlice] & colmask) != pad_col) ++cnt;
+  }
+  const int32_t m = __reduce_max_sync(0xffffffffu, cnt);
+  if ((threadIdx.x & 31) == 0) slice_w[i / kSlice] = m;
+}
+
+__global__ void k_half_fill(const int32_t* __restrict__ plus_rows, int64_t n_plus, int64_t rows_pad_h,
+                            const int32_t* __restrict__ woff, const uint32_t* __restrict__ ent,
+                            const double2* __restrict__ ecoef, uint32_t colmask, int64_t pad_col,
+                            const int32_t* __restrict__ hpos, const int32_t* __restrict__ woff_h, uint32_t* ent_h,
+                            double2* ecoef_h) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows_pad_h) return;
+  const int64_t sh = i / kSlice;
+  const int64_t base_h = (int64_t)woff_h[sh] * kSlice + (i % kSlice);
+  const int w_h = woff_h[sh + 1] - woff_h[sh];
+  int t = 0;
+  if (i < n_plus) {
+    const int64_t g = plus_rows[i];
+    const int64_t s = g / kSlice;
+    const int64_t base = (int64_t)woff[s] * kSlice + (g % kSlice);
+    const int w = woff[s + 1] - woff[s];
+    for (int tf = 0; tf < w; ++tf) {
+      const int64_t e = base + (int64_t)tf * kSlice;
+      const int64_t c = ent[e] & colmask;
+      if (c == pad_col) continue;
+      const int32_t h = hpos[c];
+      if (h == -1) continue;   // the zero column is never stored; kept for safety
+      const uint32_t col = h >= 0 ? (uint32_t)h : (uint32_t)(-2 - h);
+      ent_h[base_h + (int64_t)t * kSlice] = col | (h < 0 ? 0x80000000u : 0u);
+      ecoef_h[base_h + (int64_t)t * kSlice] = ecoef[e];
+      ++t;
+    }
+  }
+  for (; t < w_h; ++t) {
+    ent_h[base_h + (int64_t)t * kSlice] = (uint32_t)rows_pad_h;
+    ecoef_h[base_h + (int64_t)t * kSlice] = make_double2(0.0, 0.0);
+  }
+}
+
+// Queue the half system of the current set (no synchronisation; the caller's
+// read-back returns woff_h and the mirror error flag).
+static ss_status build_half(ss_stamp_s* S, cudaStream_t st) {
+  S->half_ok = false;
+  const int64_t n_plus = (S->size - (S->zero_idx >= 0 ? 1 : 0)) / 2;
+  if (!S->half_cand || n_plus < 1 || 2 * n_plus + (S->zero_idx >= 0 ? 1 : 0) != S->size) return SS_OK;
+  S->n_plus = n_plus;
+  S->rows_pad_h = (n_plus + kSlice - 1) / kSlice * kSlice;
+  S->n_slices_h = S->rows_pad_h / kSlice;
+  int32_t max_w = 0;
+  for (int64_t q = 0; q < S->n_slices; ++q) max_w = std::max(max_w, S->woff_host[q + 1] - S->woff_host[q]);
+  const KeyParams P = make_key_params(S->key);
+  DevBuf<int32_t> plus, ppos, slice_w;
+  DevBuf<int64_t> total;
+  SS_TRY(plus.alloc(S->size, st));
+  SS_TRY(ppos.alloc(S->size, st));
+  SS_TRY(slice_w.alloc(S->n_slices_h + 1, st));
+  SS_TRY(total.alloc(1, st));
+  SS_TRY(S->mirror.alloc(S->size, st));
+  SS_TRY(S->hpos.alloc(S->size, st));
+  SS_TRY(S->plus_rows.alloc(S->rows_pad_h, st));
+  SS_TRY(S->norm_h.alloc(S->rows_pad_h + 1, st));
+  SS_TRY(S->woff_h.alloc(S->n_slices_h + 1, st));
+  const int64_t cap_h = S->n_slices_h * (int64_t)max_w * kSlice + 1;
+  SS_TRY(S->ent_h.alloc(cap_h, st));
+  SS_TRY(S->ecoef_h.alloc(cap_h, st));
+  SS_CUDA(cudaMemsetAsync(S->norm_h.get(), 0, (S->rows_pad_h + 1) * sizeof(int64_t), st));
+  SS_CUDA(cudaMemsetAsync(S->plus_rows.get(), 0, S->rows_pad_h * sizeof(int32_t), st));
+  SS_CUDA(cudaMemsetAsync(slice_w.get(), 0, (S->n_slices_h + 1) * sizeof(int32_t), st));
+  SS_CUDA(cudaMemsetAsync(S->err_dev.get() + 3, 0, sizeof(int32_t), st));
+  SS_DISPATCH_WT(S->key.WT, (k_half_index<WT><<<nblk(S->size), 256, 0, st>>>(
+                                P, S->keys.get(), S->size, S->table.get(), (uint64_t)S->cap - 1, S->mirror.get(),
+                                plus.get(), S->err_dev.get() + 3)));
+  SS_LAUNCH_CHECK();
+  SS_TRY(exclusive_scan_i32(plus.get(), ppos.get(), S->size, total.get(), st));
+  k_half_rows<<<nblk(S->size), 256, 0, st>>>(plus.get(), ppos.get(), S->mirror.get(), S->norm.get(), S->size,
+                                             S->zero_idx, n_plus, S->hpos.get(), S->plus_rows.get(),
+                                             S->norm_h.get());
+  const uint32_t colmask = colmask_of(S->jbits);
+  k_half_widths<<<nblk(S->rows_pad_h), 256, 0, st>>>(S->plus_rows.get(), n_plus, S->rows_pad_h, S->slice_off.get(),
+                                                     S->ent.get(), colmask, S->rows_pad, slice_w.get());
+  SS_LAUNCH_CHECK();
+  SS_TRY(exclusive_scan_i32(slice_w.get(), S->woff_h.get(), S->n_slices_h + 1, total.get(), st));
+  k_half_fill<<<nblk(S->rows_pad_h), 256, 0, st>>>(S->plus_rows.get(), n_plus, S->rows_pad_h, S->slice_off.get(),
+                                                   S->ent.get(), S->ecoef64.get(), colmask, S->rows_pad,
+                                                   S->hpos.get(), S->woff_h.get(), S->ent_h.get(), S->ecoef_h.get());
+  SS_LAUNCH_CHECK();
+  S->woff_h_host.resize(S->n_slices_h + 1);
+  S->half_ok = true;   // confirmed by the caller's read-back of the mirror flag
+  return SS_OK;
+}
+
 // Neighbour table (sliced ELL), FP64 entry coefficients and apply scratch
 // for the current set; synchronises and settles the stamp's buffers.
 static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
@@ -627,14 +794,22 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   k_init_records<<<nblk(S->rows_pad + 1), 256, 0, st>>>(S->norm.get(), S->rows_pad + 1, S->wide, S->nw32.get(),
                                                         S->rec64.get());
   SS_LAUNCH_CHECK();
-  int32_t e = 0;
-  SS_TRY(read_back(st, {{&e, S->err_dev.get(), sizeof(int32_t)}}));
-  if (e) SS_FAIL((ss_status)e, "stamp: hash table exhausted");
+  SS_TRY(build_half(S, st));
+  int32_t e[4] = {0, 0, 0, 0};
+  if (S->half_ok)
+    SS_TRY(read_back(st, {{e, S->err_dev.get(), sizeof(e)},
+                          {S->woff_h_host.data(), S->woff_h.get(), (S->n_slices_h + 1) * sizeof(int32_t)}}));
+  else
+    SS_TRY(read_back(st, {{e, S->err_dev.get(), sizeof(e)}}));
+  if (e[0]) SS_FAIL((ss_status)e[0], "stamp: hash table exhausted");
+  if (S->half_ok && e[3]) S->half_ok = false;   // some -k not in S: no half system
   // the stamp's buffers outlive this call's stream (synchronised above)
   S->keys.settle(); S->level.settle(); S->norm.settle(); S->table.settle();
   S->afreq.settle(); S->stepkey.settle(); S->pnorm.settle(); S->pn32.settle(); S->aval.settle();
   S->ca64.settle(); S->ca32.settle(); S->slice_off.settle(); S->ent.settle(); S->ecoef64.settle();
   S->nw32.settle(); S->rec64.settle(); S->err_dev.settle(); S->zidx_dev.settle();
+  S->mirror.settle(); S->hpos.settle(); S->plus_rows.settle(); S->woff_h.settle(); S->ent_h.settle();
+  S->ecoef_h.settle(); S->norm_h.settle();
   S->bval.settle(); S->cval.settle(); S->diag64.settle();
   return SS_OK;
 }
@@ -711,6 +886,7 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
                                        h.off_l1, h.a0_abs);
   if (!(h.a0_re > 0)) SS_FAIL(SS_ERR_NOT_ELLIPTIC, "stamp_build: Re(a_hat_0) must be positive");
   S->a0 = h.a0_re;
+  S->half_cand = !S->adr && h.f_sym && h.herm_exact;
   S->j0 = h.j0;
   S->maxabs_f = h.maxabs_f;
   S->maxabs_a = h.maxabs_a;
@@ -770,6 +946,13 @@ static void rebind(ss_stamp_s* S, cudaStream_t st) {
   S->nw32.s = st;
   S->rec64.s = st;
   S->diag64.s = st;
+  S->mirror.s = st;
+  S->hpos.s = st;
+  S->plus_rows.s = st;
+  S->woff_h.s = st;
+  S->ent_h.s = st;
+  S->ecoef_h.s = st;
+  S->norm_h.s = st;
 }
 
 static ss_status extend_impl(ss_stamp_s* S, int levels, cudaStream_t st) {

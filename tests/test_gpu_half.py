@@ -1,0 +1,139 @@
+"""The Hermitian half system of the FP64 solve (real data: F = -F and a_hat
+exactly Hermitian): the same solution as the full system (relative l2 1e-12)
+and the manufactured solution (1e-10), the same CG iteration count (to one),
+a bit-for-bit fallback to the full system when f is not Hermitian, no half
+system when F or a_hat breaks the symmetry, rebuilt by stamp_extend."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import stamp as ostamp
+from tests.helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2302_00752_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def gp():
+    from paper_2302_00752_gb300 import pipeline
+    return pipeline
+
+
+def exact_on(stamp, inst):
+    S = stamp.export()[0].cpu().numpy()
+    idx = ostamp.index_map(S)
+    want = np.zeros(len(S), complex)
+    for k, v in zip(inst.u_freq.tolist(), inst.u_val):
+        want[idx[tuple(k)]] = v
+    return want
+
+
+def both(B, stamp, f_on, tol=1e-12):
+    u_h, st_h = B.solve(stamp, f_on, tol, 2000, "fp64")
+    stamp.set_symmetry(False)
+    u_f, st_f = B.solve(stamp, f_on, tol, 2000, "fp64")
+    stamp.set_symmetry(True)
+    return (u_h, st_h), (u_f, st_f)
+
+
+@pytest.mark.parametrize("make", [lambda: W.make_tiny(1, d=3, n_cos=2, n_u=3, N=2), W.make_cfg1, W.make_cfg2,
+                                  lambda: W.make_cfg5(smooth=True)])
+def test_half_equals_full(B, gp, make):
+    inst = make()
+    res = gp.run(gp.prepare(inst), solve=False)
+    try:
+        (u_h, st_h), (u_f, st_f) = both(B, res.stamp, res.f_on_S)
+        assert st_h["half_system"] and not st_f["half_system"]
+        assert st_h["status"] == st_f["status"] == "SS_OK"
+        assert abs(st_h["inner_iters"] - st_f["inner_iters"]) <= 1
+        assert rel_l2(u_h.cpu().numpy(), u_f.cpu().numpy()) < 1e-12
+        if res.stamp.size > 400000:
+            return                         # the host-side checks below are for the smaller sets
+        want = exact_on(res.stamp, inst)
+        assert rel_l2(u_h.cpu().numpy(), want) < 1e-10
+        # the unfolded solution is Hermitian and zero at k = 0
+        S = res.stamp.export()[0].cpu().numpy()
+        idx = ostamp.index_map(S)
+        uh = u_h.cpu().numpy()
+        neg = np.array([idx[tuple(-x for x in k)] for k in S.tolist()])
+        assert np.array_equal(uh[neg], np.conj(uh))
+        if res.stamp.zero_index >= 0:
+            assert uh[res.stamp.zero_index] == 0
+    finally:
+        res.stamp.destroy()
+
+
+def test_non_hermitian_f_falls_back(B, gp):
+    inst = W.make_cfg1()
+    res = gp.run(gp.prepare(inst), solve=False)
+    try:
+        f = res.f_on_S.clone()
+        nz = torch.nonzero(f.abs() > 0).flatten()
+        f[nz[0]] = f[nz[0]] * (1 + 1e-9)          # one entry no longer conj of its mirror
+        (u_h, st_h), (u_f, st_f) = both(B, res.stamp, f)
+        assert not st_h["half_system"] and not st_f["half_system"]
+        assert torch.equal(u_h, u_f)
+    finally:
+        res.stamp.destroy()
+
+
+def test_no_half_system_without_symmetry(B):
+    rng = np.random.default_rng(3)
+    d = 3
+    p = rng.integers(-3, 4, size=(2, d))
+    p = p[p.any(axis=1)]
+    af = np.vstack([np.zeros((1, d), int), p, -p])
+    c = 0.1 * (rng.standard_normal(len(p)) + 1j * rng.standard_normal(len(p)))
+    av = np.concatenate([[1.0 + 0j], c, np.conj(c)])
+    q = rng.integers(-4, 5, size=(4, d))
+    q = q[q.any(axis=1)]
+    fv = rng.standard_normal(len(q)) + 1j * rng.standard_normal(len(q))
+    # F without its negatives: complex data, S not symmetric
+    with B.stamp_build(af, av, q, 2) as s:
+        f_on, _ = s.scatter(q, fv)
+        u, st = B.solve(s, f_on, 1e-12, 500, "fp64")
+        assert st["status"] == "SS_OK" and not st["half_system"]
+    # a_hat Hermitian only to rounding: the full system, as before
+    av2 = av.copy()
+    av2[1] = av2[1] * (1 + 1e-15)
+    F = np.vstack([q, -q])
+    fval = np.concatenate([fv, np.conj(fv)])
+    with B.stamp_build(af, av2, F, 2) as s:
+        f_on, _ = s.scatter(F, fval)
+        u, st = B.solve(s, f_on, 1e-12, 500, "fp64")
+        assert st["status"] == "SS_OK" and not st["half_system"]
+    with B.stamp_build(af, av, F, 2) as s:
+        f_on, _ = s.scatter(F, fval)
+        u, st = B.solve(s, f_on, 1e-12, 500, "fp64")
+        assert st["status"] == "SS_OK" and st["half_system"]
+
+
+def test_half_after_extend(B, gp):
+    inst = W.make_tiny(2, d=3, n_cos=2, n_u=3, N=1)
+    res = gp.run(gp.prepare(inst), solve=False)
+    try:
+        res.stamp.extend(1)
+        f_on, _ = res.stamp.scatter(res.f_freq, res.f_val)
+        (u_h, st_h), (u_f, st_f) = both(B, res.stamp, f_on)
+        assert st_h["half_system"]
+        assert rel_l2(u_h.cpu().numpy(), u_f.cpu().numpy()) < 1e-12
+    finally:
+        res.stamp.destroy()
+
+
+def test_other_precisions_use_the_full_system(B, gp):
+    inst = W.make_cfg1()
+    res = gp.run(gp.prepare(inst), solve=False)
+    try:
+        for prec in ("fp32", "df64"):
+            u, st = B.solve(res.stamp, res.f_on_S, 1e-12, 500, prec)
+            assert st["status"] == "SS_OK" and not st["half_system"]
+    finally:
+        res.stamp.destroy()
