@@ -35,6 +35,7 @@ struct OpView {
   int colbits;
   uint32_t colmask;
   bool conj = false;       // half system: entry bit 31 set = the neighbour's value is conjugated
+  uint32_t jmask = 0xffffffffu;   // step index = (entry >> colbits) & jmask
 };
 
 // Imaginary part of a gathered value, negated (the value conjugated) when the
@@ -43,6 +44,11 @@ struct OpView {
 __device__ __forceinline__ double conj_if(double y, bool conj, uint32_t ent) {
   const unsigned long long m = conj ? (unsigned long long)(ent >> 31) << 63 : 0ull;
   return __longlong_as_double(__double_as_longlong(y) ^ (long long)m);
+}
+
+__device__ __forceinline__ float conj_if(float y, bool conj, uint32_t ent) {
+  const uint32_t m = conj ? (ent & 0x80000000u) : 0u;
+  return __uint_as_float(__float_as_uint(y) ^ m);
 }
 
 // Accumulate row `row` (lane of slice s) of L u in FP64 from the stored entry
@@ -155,12 +161,14 @@ __device__ __forceinline__ float2 row_apply32_t(const OpView& op, int64_t s, int
 #pragma unroll
     for (int q = 0; q < U; ++q) ee[q] = t + q < w ? __ldg(e + (int64_t)(t + q) * kSlice) : 0u;
 #pragma unroll
-    for (int q = 0; q < U; ++q)
+    for (int q = 0; q < U; ++q) {
       v[q] = t + q < w ? ldv<CG>(rec + (ee[q] & op.colmask)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      v[q].y = conj_if(v[q].y, op.conj, ee[q]);
+    }
 #pragma unroll
     for (int q = 0; q < U; ++q) {
       if (t + q < w) {
-        const int j = (int)(ee[q] >> op.colbits);
+        const int j = (int)((ee[q] >> op.colbits) & op.jmask);
         const float sc = entry_scale<WIDE>(nk, v[q].z, pn[j]);
         const float2 a = ca[j];
         const float tr = sc * a.x, ti = sc * a.y;
@@ -200,7 +208,7 @@ __device__ __forceinline__ float2 row_apply32_direct(const OpView& op, int64_t s
 #pragma unroll
     for (int q = 0; q < U; ++q) {
       if (t + q < w) {
-        const int j = (int)(ee[q] >> op.colbits);
+        const int j = (int)((ee[q] >> op.colbits) & op.jmask);
         const float sc = entry_scale<WIDE>(nk, __int_as_float(nl[q]), __ldg(pn + j));
         const float2 a = __ldg(ca + j);
         const float tr = sc * a.x, ti = sc * a.y;

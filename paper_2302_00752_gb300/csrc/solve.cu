@@ -1304,9 +1304,9 @@ static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream
   return SS_OK;
 }
 
-// Plan and workspace of the Hermitian half system (FP64 CG only).
-static ss_status stamp_plan_half(ss_stamp_s* s, ss_solve_ctx& H, cudaStream_t st) {
-  if (H.planned_mode == 0) return SS_OK;
+// Plan and workspace of the Hermitian half system (FP64 CG and FP32-refined).
+static ss_status stamp_plan_half(ss_stamp_s* s, ss_solve_ctx& H, int mode, cudaStream_t st) {
+  if (H.planned_mode == mode) return SS_OK;
   if ((int64_t)s->woff_h_host.size() != s->n_slices_h + 1) SS_FAIL(SS_ERR_INVALID, "solve: no half-system table");
   H.plan.inst.assign(1, SolveInst{});
   SolveInst& in = H.plan.inst[0];
@@ -1319,14 +1319,14 @@ static ss_status stamp_plan_half(ss_stamp_s* s, ss_solve_ctx& H, cudaStream_t st
   in.wide = s->wide ? 1 : 0;
   int grid = 0;
   H.plan.block = H.block;
-  SS_TRY(max_grid(0, H.plan.block, &grid));
+  SS_TRY(max_grid(mode, H.plan.block, &grid));
   if (H.blocks_per_sm > 0) grid = std::min(grid, H.blocks_per_sm * sm_count());
   const int by_size = (int)std::max<int64_t>(1, s->n_slices_h / 8);
   const int target = std::min<int64_t>((int64_t)grid * H.chunks_per_block, by_size);
   SS_TRY(plan_chunks(H.plan, s->woff_h_host, {}, target));
   H.plan.grid = std::min<int>(grid, (int)H.plan.chunk.size());
   SS_TRY(work_alloc(H.work, s->rows_pad_h + 1, s->norm_h.get(), nullptr, s->wide, st));
-  H.planned_mode = 0;
+  H.planned_mode = mode;
   return SS_OK;
 }
 
@@ -1425,7 +1425,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
                             cudaMemcpyDeviceToHost, st));
   }
   const int mode = s->adr ? 2 : (prec == SS_FP64 ? 0 : (prec == SS_FP32 ? 1 : 3));
-  if (mode == 0 && s->half_ok && C->use_half) {
+  if ((mode == 0 || mode == 1) && s->half_ok && C->use_half) {
     // Real data: solve the Hermitian half system (rows k >lex 0, neighbours
     // below read as conjugates), then unfold; if f turns out not to be
     // Hermitian the full system below is solved instead.
@@ -1437,7 +1437,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
       H->chunks_per_block = C->chunks_per_block;
       H->planned_mode = -1;
     }
-    SS_TRY(stamp_plan_half(s, *H, st));
+    SS_TRY(stamp_plan_half(s, *H, mode, st));
     SS_TRY(C->fh.ensure(s->rows_pad_h, st));
     SS_TRY(C->uh.ensure(s->rows_pad_h, st));
     SS_TRY(C->hflag.ensure(1, st));
@@ -1455,15 +1455,16 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
     hop.ent = s->ent_h.get();
     hop.ecoef = s->ecoef_h.get();
     hop.ecoefdf = nullptr;
-    hop.colbits = 31;
-    hop.colmask = 0x7fffffffu;
+    hop.colbits = s->colbits_h;
+    hop.colmask = (1u << s->colbits_h) - 1u;
+    hop.jmask = (1u << s->jbits) - 1u;
     hop.conj = true;
     if (!H->work.ev[0]) {
       SS_CUDA(cudaEventCreate(&H->work.ev[0]));
       SS_CUDA(cudaEventCreate(&H->work.ev[1]));
     }
     SS_TRY(launch_solve(H->work, H->plan, hop, nullptr, s->norm_h.get(), s->ca64.get(), s->ca32.get(), s->pn32.get(),
-                        tol, max_iter, 0, st, H->work.ev[0], H->work.ev[1], nullptr));
+                        tol, max_iter, mode, st, H->work.ev[0], H->work.ev[1], nullptr));
     k_half_scatter<<<sb, 256, 0, st>>>(C->uh.get(), s->hpos.get(), s->size, reinterpret_cast<double2*>(u_on_S));
     SS_LAUNCH_CHECK();
     SS_CUDA(cudaMemcpyAsync(C->hflag_host, C->hflag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));

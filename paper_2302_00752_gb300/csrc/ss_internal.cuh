@@ -173,6 +173,7 @@ struct ss_stamp_s {
   bool half_cand = false;             // F = -F and a_hat exactly Hermitian (set by the build)
   bool half_ok = false;               // half system built for the current set
   int64_t n_plus = 0, rows_pad_h = 0, n_slices_h = 0;
+  int colbits_h = 0;                  // half entries: col | j << colbits_h | conj << 31
   ss::DevBuf<int64_t> mirror;         // [size] canonical index of -k
   ss::DevBuf<int32_t> hpos;           // [size] i (k > 0), -2 - i (k < 0, i the row of -k), -1 (k = 0)
   ss::DevBuf<int32_t> plus_rows;      // [rows_pad_h] canonical index of compact row i

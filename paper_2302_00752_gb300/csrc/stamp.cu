@@ -652,9 +652,9 @@ __global__ void k_half_widths(const int32_t* __restrict__ plus_rows, int64_t n_p
 
 __global__ void k_half_fill(const int32_t* __restrict__ plus_rows, int64_t n_plus, int64_t rows_pad_h,
                             const int32_t* __restrict__ woff, const uint32_t* __restrict__ ent,
-                            const double2* __restrict__ ecoef, uint32_t colmask, int64_t pad_col,
-                            const int32_t* __restrict__ hpos, const int32_t* __restrict__ woff_h, uint32_t* ent_h,
-                            double2* ecoef_h) {
+                            const double2* __restrict__ ecoef, uint32_t colmask, int colbits, int64_t pad_col,
+                            int colbits_h, int j0, const int32_t* __restrict__ hpos,
+                            const int32_t* __restrict__ woff_h, uint32_t* ent_h, double2* ecoef_h) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows_pad_h) return;
   const int64_t sh = i / kSlice;
@@ -673,13 +673,14 @@ __global__ void k_half_fill(const int32_t* __restrict__ plus_rows, int64_t n_plu
       const int32_t h = hpos[c];
       if (h == -1) continue;   // the zero column is never stored; kept for safety
       const uint32_t col = h >= 0 ? (uint32_t)h : (uint32_t)(-2 - h);
-      ent_h[base_h + (int64_t)t * kSlice] = col | (h < 0 ? 0x80000000u : 0u);
+      const uint32_t j = ent[e] >> colbits;
+      ent_h[base_h + (int64_t)t * kSlice] = col | (j << colbits_h) | (h < 0 ? 0x80000000u : 0u);
       ecoef_h[base_h + (int64_t)t * kSlice] = ecoef[e];
       ++t;
     }
   }
   for (; t < w_h; ++t) {
-    ent_h[base_h + (int64_t)t * kSlice] = (uint32_t)rows_pad_h;
+    ent_h[base_h + (int64_t)t * kSlice] = (uint32_t)rows_pad_h | ((uint32_t)j0 << colbits_h);
     ecoef_h[base_h + (int64_t)t * kSlice] = make_double2(0.0, 0.0);
   }
 }
@@ -693,6 +694,8 @@ static ss_status build_half(ss_stamp_s* S, cudaStream_t st) {
   S->n_plus = n_plus;
   S->rows_pad_h = (n_plus + kSlice - 1) / kSlice * kSlice;
   S->n_slices_h = S->rows_pad_h / kSlice;
+  S->colbits_h = 31 - S->jbits;
+  if (S->colbits_h < 1 || S->rows_pad_h + 1 > ((int64_t)1 << S->colbits_h)) return SS_OK;   // no room for the conj bit
   int32_t max_w = 0;
   for (int64_t q = 0; q < S->n_slices; ++q) max_w = std::max(max_w, S->woff_host[q + 1] - S->woff_host[q]);
   const KeyParams P = make_key_params(S->key);
@@ -728,8 +731,9 @@ static ss_status build_half(ss_stamp_s* S, cudaStream_t st) {
   SS_LAUNCH_CHECK();
   SS_TRY(exclusive_scan_i32(slice_w.get(), S->woff_h.get(), S->n_slices_h + 1, total.get(), st));
   k_half_fill<<<nblk(S->rows_pad_h), 256, 0, st>>>(S->plus_rows.get(), n_plus, S->rows_pad_h, S->slice_off.get(),
-                                                   S->ent.get(), S->ecoef64.get(), colmask, S->rows_pad,
-                                                   S->hpos.get(), S->woff_h.get(), S->ent_h.get(), S->ecoef_h.get());
+                                                   S->ent.get(), S->ecoef64.get(), colmask, colbits_of(S->jbits),
+                                                   S->rows_pad, S->colbits_h, S->j0, S->hpos.get(), S->woff_h.get(),
+                                                   S->ent_h.get(), S->ecoef_h.get());
   SS_LAUNCH_CHECK();
   S->woff_h_host.resize(S->n_slices_h + 1);
   S->half_ok = true;   // confirmed by the caller's read-back of the mirror flag
