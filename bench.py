@@ -428,6 +428,38 @@ def next_prime_py(n):
 DF_OPS_PER_PAIR = 150   # ten double-float multiply-adds of 15 FP32 instructions per (term, point)
 
 
+def multiscale_section(B, gp, flush, reps=5):
+    """The d = 3 multiscale workload (frequencies up to 2^10 per coordinate,
+    N = 4): FP32-refined against plain FP64 on the same stamp, time to
+    solution at relative residual 1e-10 and 1e-12, and the relative l2
+    difference of the two solutions."""
+    import torch
+    inst = W.make_cfg3()
+    res = gp.run(gp.prepare(inst), solve=False)
+    st_ = res.stamp
+    out = {"size": st_.size, "nnz": st_.nnz}
+    for tol in (1e-10, 1e-12):
+        sols = {}
+        for prec in ("fp64", "fp32"):
+            times = []
+            for _ in range(reps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                u, stt = B.solve(st_, res.f_on_S, tol, 2000, prec)
+                b.record()
+                b.synchronize()
+                times.append(a.elapsed_time(b))
+            sols[prec] = u
+            out[f"{prec}@{tol:g}"] = {"time_to_solution_ms": statistics.median(times), "kernel_ms": stt["kernel_ms"],
+                                      "applies": stt["applies"], "rel_residual": stt["rel_residual"],
+                                      "half_system": stt["half_system"], "status": stt["status"]}
+        out[f"rel_l2_fp32_vs_fp64@{tol:g}"] = float(torch.linalg.norm(sols["fp32"] - sols["fp64"]) /
+                                                   torch.linalg.norm(sols["fp64"]))
+    st_.destroy()
+    return out
+
+
 def proxy_section(B, gp, flush, Q=1000):
     """Lemma ProxyError after the solve: extension to S^{N+1}, the exact proxy
     and its Monte Carlo estimate at Q = 1000 uniform points (the paper uses 200
@@ -693,14 +725,15 @@ def main():
     for k, v in zip(inst.u_freq.tolist(), inst.u_val):
         exact[idx[tuple(k)]] = v
     tts = {}
-    for prec in ("fp64", "fp64_full", "fp32", "df64"):
+    for prec in ("fp64", "fp64_full", "fp32", "df64", "fp64@1e-10", "fp32@1e-10"):
         times, kern = [], []
         stamp.set_symmetry(prec != "fp64_full")        # fp64_full: the full system, for comparison
+        base, tol_p = (prec.split("@")[0], 1e-10) if "@" in prec else (prec, 1e-12)
         for _ in range(5):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            u, st = B.solve(stamp, f_on, 1e-12, 1000, "fp64" if prec == "fp64_full" else prec)
+            u, st = B.solve(stamp, f_on, tol_p, 1000, "fp64" if base == "fp64_full" else base)
             b.record()
             b.synchronize()
             times.append(a.elapsed_time(b))
@@ -783,6 +816,10 @@ def main():
                 extra["adr"] = adr_section(B, gp, flush)
             except Exception as e:
                 extra["adr"] = {"error": repr(e)}
+            try:
+                extra["multiscale"] = multiscale_section(B, gp, flush)
+            except Exception as e:
+                extra["multiscale"] = {"error": repr(e)}
             try:
                 extra["proxy"] = proxy_section(B, gp, flush)
             except Exception as e:
