@@ -373,6 +373,16 @@ ss_status batch_config(ss_batch b, int32_t* block, int32_t* blocks_per_sm, int32
  * (0 = as many as fit), chunks_per_block >= 1 (static work units per block). */
 ss_status batch_set_config(ss_batch b, int32_t block, int32_t blocks_per_sm, int32_t chunks_per_block);
 
+/* When every stamp of the batch has a Hermitian half system (see
+ * solve_set_symmetry), batch_create also builds the batch of the half systems
+ * and batch_solve runs it: the callers' f are gathered onto the compact rows
+ * (and checked to be Hermitian bit for bit), the half batch is solved, and
+ * every u is unfolded over its S; stats[i].half_system = 1.  A non-Hermitian
+ * f makes the call solve the full batch instead.  use_half = 0 always solves
+ * the full batch (default 1).  batch_autotune and batch_config act on the
+ * batch that batch_solve runs. */
+ss_status batch_set_symmetry(ss_batch b, int32_t use_half);
+
 void batch_destroy(ss_batch b);
 
 /* ------------------------------------------------------ the whole method */

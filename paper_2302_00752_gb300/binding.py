@@ -97,6 +97,7 @@ def _load():
         "batch_autotune": (i32, [vp, P(vp), P(vp), dbl, i32, i32, P(dbl), vp]),
         "batch_config": (i32, [vp, P(i32), P(i32), P(i32), P(i32), P(i32)]),
         "batch_set_config": (i32, [vp, i32, i32, i32]),
+        "batch_set_symmetry": (i32, [vp, i32]),
         "batch_destroy": (None, [vp]),
         "sparse_spectral_solve": (i32, [P(LatticeSpec), P(Trig), P(Trig), vp, i64, i32, dbl, i32, i32, dbl, i32,
                                         P(i64), P(i64), P(vp), vp, i64, P(SolveStats), vp]),
@@ -518,6 +519,10 @@ class Batch:
 
     def set_config(self, block, blocks_per_sm, chunks_per_block):
         _check(lib.batch_set_config(self._h, int(block), int(blocks_per_sm), int(chunks_per_block)))
+
+    def set_symmetry(self, use_half):
+        """Solve real data through the instances' Hermitian half systems (default True)."""
+        _check(lib.batch_set_symmetry(self._h, int(bool(use_half))))
 
     def destroy(self):
         if self._h:

@@ -710,7 +710,11 @@ static ss_status build_half(ss_stamp_s* S, cudaStream_t st) {
   SS_TRY(S->plus_rows.alloc(S->rows_pad_h, st));
   SS_TRY(S->norm_h.alloc(S->rows_pad_h + 1, st));
   SS_TRY(S->woff_h.alloc(S->n_slices_h + 1, st));
-  const int64_t cap_h = S->n_slices_h * (int64_t)max_w * kSlice + 1;
+  // Entries of the half table: every compact slice is at most as wide as the
+  // widest row it holds; the plus rows of one full slice are consecutive
+  // compact rows, so they fall in at most two compact slices and the half
+  // table holds at most twice the full table's entries.
+  const int64_t cap_h = std::min<int64_t>(S->n_slices_h * (int64_t)max_w * kSlice, 2 * S->n_ent) + 1;
   SS_TRY(S->ent_h.alloc(cap_h, st));
   SS_TRY(S->ecoef_h.alloc(cap_h, st));
   SS_CUDA(cudaMemsetAsync(S->norm_h.get(), 0, (S->rows_pad_h + 1) * sizeof(int64_t), st));

@@ -78,3 +78,37 @@ def test_autotune_and_config(B, built):
     for u, ref in zip(us, refs):
         assert rel_l2(u.cpu().numpy(), ref.u) < 1e-10
     batch.destroy()
+
+
+def test_half_batch_equals_full_batch(B, built):
+    stamps, fs, refs = built
+    batch = B.Batch(stamps)
+    try:
+        for prec in ("fp64", "fp32"):
+            us_h, st_h = batch.solve(fs, tol=1e-12, precision=prec)
+            batch.set_symmetry(False)
+            us_f, st_f = batch.solve(fs, tol=1e-12, precision=prec)
+            batch.set_symmetry(True)
+            assert all(s["half_system"] for s in st_h) and not any(s["half_system"] for s in st_f)
+            for uh, uf, s in zip(us_h, us_f, st_h):
+                assert s["status"] == "SS_OK"
+                assert rel_l2(uh.cpu().numpy(), uf.cpu().numpy()) < 1e-11
+    finally:
+        batch.destroy()
+
+
+def test_half_batch_falls_back_for_a_non_hermitian_f(B, built):
+    stamps, fs, refs = built
+    fs2 = [f.clone() for f in fs]
+    nz = torch.nonzero(fs2[3].abs() > 0).flatten()
+    fs2[3][nz[0]] *= 1 + 1e-9
+    batch = B.Batch(stamps)
+    try:
+        us, st = batch.solve(fs2, tol=1e-12, precision="fp64")
+        assert not any(s["half_system"] for s in st)
+        batch.set_symmetry(False)
+        us_f, _ = batch.solve(fs2, tol=1e-12, precision="fp64")
+        for a, b in zip(us, us_f):
+            assert torch.equal(a, b)
+    finally:
+        batch.destroy()
