@@ -309,8 +309,8 @@ ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, double tol, in
  * system): for real data - F = -F and a_hat_{-p} = conj(a_hat_p) bit for bit,
  * which stamp_build detects - S is symmetric and L maps Hermitian vectors
  * (u_{-k} = conj(u_k)) to Hermitian vectors, so for a Hermitian f the rows
- * k >lex 0 carry the whole solution.  solve in SS_FP64 and SS_FP32 then runs
- * the same solver on those rows only, reading a neighbour l <lex 0 as conj(u_{-l}) (half the
+ * k >lex 0 carry the whole solution.  solve (every precision; not ADR stamps)
+ * then runs the same solver on those rows only, reading a neighbour l <lex 0 as conj(u_{-l}) (half the
  * rows and half the stored nonzeros per application; CG scalars and the
  * residual ratio are those of the full system up to rounding), and unfolds u
  * over S; stats->half_system = 1.  An f that is not Hermitian bit for bit

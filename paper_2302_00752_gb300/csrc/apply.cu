@@ -108,6 +108,17 @@ ss_status ensure_ecoefdf(ss_stamp_s* s, cudaStream_t st) {
   return SS_OK;
 }
 
+ss_status ensure_ecoefdf_half(ss_stamp_s* s, cudaStream_t st) {
+  if (s->ecoefdf_h.get()) return SS_OK;
+  const int64_t n = s->ecoef_h.n;
+  SS_TRY(s->ecoefdf_h.alloc(n, st));
+  k_ecoef_df<<<nblk(n), 256, 0, st>>>(s->ecoef_h.get(), n, s->ecoefdf_h.get());
+  SS_LAUNCH_CHECK();
+  SS_CUDA(cudaStreamSynchronize(st));
+  s->ecoefdf_h.settle();
+  return SS_OK;
+}
+
 OpView op_view(const ss_stamp_s* s) {
   OpView op;
   op.woff = s->slice_off.get();

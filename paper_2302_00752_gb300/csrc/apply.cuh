@@ -115,7 +115,11 @@ __device__ __forceinline__ float4 row_applydf(const OpView& op, int64_t s, int l
       c[q] = __ldg(cf + (int64_t)(t + q) * kSlice);
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = ldv<CG>(rec + (ee[q] & op.colmask));
+    for (int q = 0; q < 4; ++q) {
+      v[q] = ldv<CG>(rec + (ee[q] & op.colmask));
+      v[q].z = conj_if(v[q].z, op.conj, ee[q]);
+      v[q].w = conj_if(v[q].w, op.conj, ee[q]);
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       df_fma(ar, re_of(c[q]), re_of(v[q]));
@@ -127,7 +131,9 @@ __device__ __forceinline__ float4 row_applydf(const OpView& op, int64_t s, int l
   for (; t < w; ++t) {
     const uint32_t ee = __ldg(e + (int64_t)t * kSlice);
     const float4 c = __ldg(cf + (int64_t)t * kSlice);
-    const float4 v = ldv<CG>(rec + (ee & op.colmask));
+    float4 v = ldv<CG>(rec + (ee & op.colmask));
+    v.z = conj_if(v.z, op.conj, ee);
+    v.w = conj_if(v.w, op.conj, ee);
     df_fma(ar, re_of(c), re_of(v));
     df_fma(ar, df_neg(im_of(c)), im_of(v));
     df_fma(ai, re_of(c), im_of(v));

@@ -1304,7 +1304,7 @@ static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream
   return SS_OK;
 }
 
-// Plan and workspace of the Hermitian half system (FP64 CG and FP32-refined).
+// Plan and workspace of the Hermitian half system (FP64, FP32-refined and DF64 modes).
 static ss_status stamp_plan_half(ss_stamp_s* s, ss_solve_ctx& H, int mode, cudaStream_t st) {
   if (H.planned_mode == mode) return SS_OK;
   if ((int64_t)s->woff_h_host.size() != s->n_slices_h + 1) SS_FAIL(SS_ERR_INVALID, "solve: no half-system table");
@@ -1326,6 +1326,10 @@ static ss_status stamp_plan_half(ss_stamp_s* s, ss_solve_ctx& H, int mode, cudaS
   SS_TRY(plan_chunks(H.plan, s->woff_h_host, {}, target));
   H.plan.grid = std::min<int>(grid, (int)H.plan.chunk.size());
   SS_TRY(work_alloc(H.work, s->rows_pad_h + 1, s->norm_h.get(), nullptr, s->wide, st));
+  if (mode == 3) {
+    SS_TRY(ensure_ecoefdf_half(s, st));
+    SS_TRY(work_alloc_df64(H.work, st));
+  }
   H.planned_mode = mode;
   return SS_OK;
 }
@@ -1425,7 +1429,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
                             cudaMemcpyDeviceToHost, st));
   }
   const int mode = s->adr ? 2 : (prec == SS_FP64 ? 0 : (prec == SS_FP32 ? 1 : 3));
-  if ((mode == 0 || mode == 1) && s->half_ok && C->use_half) {
+  if (mode != 2 && s->half_ok && C->use_half) {
     // Real data: solve the Hermitian half system (rows k >lex 0, neighbours
     // below read as conjugates), then unfold; if f turns out not to be
     // Hermitian the full system below is solved instead.
@@ -1454,7 +1458,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
     hop.woff = s->woff_h.get();
     hop.ent = s->ent_h.get();
     hop.ecoef = s->ecoef_h.get();
-    hop.ecoefdf = nullptr;
+    hop.ecoefdf = s->ecoefdf_h.get();
     hop.colbits = s->colbits_h;
     hop.colmask = (1u << s->colbits_h) - 1u;
     hop.jmask = (1u << s->jbits) - 1u;

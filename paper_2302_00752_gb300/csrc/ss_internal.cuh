@@ -181,6 +181,7 @@ struct ss_stamp_s {
   ss::DevBuf<uint32_t> ent_h;         // col | conj << 31 (dummy column rows_pad_h)
   ss::DevBuf<double2> ecoef_h;        // FP64 entry coefficients of the half table
   ss::DevBuf<int64_t> norm_h;         // [rows_pad_h + 1] |k|^2 of the compact rows (0 on padding)
+  ss::DevBuf<float4> ecoefdf_h;       // the half table's coefficients as double-float (first DF64 solve)
   std::vector<int32_t> woff_h_host;
   // right-hand side and solution kept by sparse_spectral_solve (sol_size rows)
   ss::DevBuf<double2> rhs, sol;
@@ -212,6 +213,7 @@ ss_status launch_pack64_prefix(const ss_stamp_s* s, const double2* u, int64_t n_
 ss_status launch_apply32(const ss_stamp_s* s, const float2* u, float2* y, cudaStream_t st);
 // Double-float copy of the FP64 entry coefficients (built once per operator).
 ss_status ensure_ecoefdf(ss_stamp_s* s, cudaStream_t st);
+ss_status ensure_ecoefdf_half(ss_stamp_s* s, cudaStream_t st);
 
 int sm_count();
 

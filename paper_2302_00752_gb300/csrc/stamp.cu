@@ -785,6 +785,7 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   SS_TRY(S->ent.alloc(S->n_ent + 1, st));
   SS_TRY(S->ecoef64.alloc(S->n_ent + 1, st));
   S->ecoefdf.release();   // rebuilt from ecoef64 by the next DF64 solve
+  S->ecoefdf_h.release();
   if (S->adr) {
     SS_TRY(S->diag64.alloc(S->rows_pad + 1, st));
     SS_DISPATCH_WT(S->key.WT, (k_fill_slices_adr<WT><<<nblk(S->rows_pad + 1), 256, 0, st>>>(
@@ -951,6 +952,7 @@ static void rebind(ss_stamp_s* S, cudaStream_t st) {
   S->ent.s = st;
   S->ecoef64.s = st;
   S->ecoefdf.s = st;
+  S->ecoefdf_h.s = st;
   S->nw32.s = st;
   S->rec64.s = st;
   S->diag64.s = st;

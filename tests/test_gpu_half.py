@@ -147,11 +147,18 @@ def test_refined_half_equals_full(B, gp, make):
         res.stamp.destroy()
 
 
-def test_df64_uses_the_full_system(B, gp):
-    inst = W.make_cfg1()
+@pytest.mark.parametrize("make", [W.make_cfg1, W.make_cfg2])
+def test_df64_half_equals_full(B, gp, make):
+    inst = make()
     res = gp.run(gp.prepare(inst), solve=False)
     try:
-        u, st = B.solve(res.stamp, res.f_on_S, 1e-12, 500, "df64")
-        assert st["status"] == "SS_OK" and not st["half_system"]
+        u_h, st_h = B.solve(res.stamp, res.f_on_S, 1e-12, 500, "df64")
+        res.stamp.set_symmetry(False)
+        u_f, st_f = B.solve(res.stamp, res.f_on_S, 1e-12, 500, "df64")
+        res.stamp.set_symmetry(True)
+        assert st_h["half_system"] and not st_f["half_system"]
+        assert st_h["status"] == st_f["status"] == "SS_OK"
+        assert rel_l2(u_h.cpu().numpy(), u_f.cpu().numpy()) < 1e-11
+        assert rel_l2(u_h.cpu().numpy(), exact_on(res.stamp, inst)) < 1e-10
     finally:
         res.stamp.destroy()
