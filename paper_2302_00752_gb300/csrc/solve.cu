@@ -24,6 +24,7 @@
 // The CG preconditioner is D_k = 4 pi^2 Re(a_hat_0) |k|^2 (the diagonal of L),
 // 1 on the zero row and on padding rows.
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 
 #include "solve.cuh"
@@ -1061,7 +1062,17 @@ ss_status plan_chunks(SolvePlan& plan, const std::vector<int32_t>& woff, const s
 ss_status work_alloc(SolveWork& W, int64_t rows_total, const int64_t* norm, const int8_t* wide_rows, bool wide,
                      cudaStream_t st) {
   if (W.rows_total == rows_total) return SS_OK;
+  if (W.cap_rows >= rows_total) {
+    // a workspace kept from an earlier stamp: new records, same buffers
+    W.rows_total = rows_total;
+    k_init_solve_records<<<nblk(rows_total), 256, 0, st>>>(norm, rows_total, wide_rows, wide, W.xrec.get(),
+                                                           W.urec64.get(), W.urec32.get());
+    SS_LAUNCH_CHECK();
+    return SS_OK;
+  }
   W.rows_total = rows_total;
+  W.cap_rows = rows_total;
+  W.df_rows = W.bi_rows = -1;
   SS_TRY(W.xrec.alloc(2 * rows_total, st));
   SS_TRY(W.urec64.alloc(2 * rows_total, st));
   SS_TRY(W.urec32.alloc(rows_total, st));
@@ -1094,7 +1105,14 @@ ss_status work_alloc(SolveWork& W, int64_t rows_total, const int64_t* norm, cons
 }
 
 ss_status work_alloc_bicgstab(SolveWork& W, cudaStream_t st) {
-  if (W.zrec.n >= (size_t)(2 * W.rows_total) && W.tv.n >= (size_t)W.rows_total) return SS_OK;
+  if (W.zrec.n >= (size_t)(2 * W.rows_total) && W.tv.n >= (size_t)W.rows_total) {
+    if (W.bi_rows != W.rows_total) {   // the dummy record of this row count must read as zero
+      SS_CUDA(cudaMemsetAsync(W.zrec.get() + 2 * (W.rows_total - 1), 0, 2 * sizeof(double2), st));
+      W.bi_rows = W.rows_total;
+    }
+    return SS_OK;
+  }
+  W.bi_rows = W.rows_total;
   SS_TRY(W.zrec.alloc(2 * W.rows_total, st));
   SS_TRY(W.tv.alloc(W.rows_total, st));
   // the odd halves of the z records are never read by the FP64 operator
@@ -1106,7 +1124,15 @@ ss_status work_alloc_bicgstab(SolveWork& W, cudaStream_t st) {
 }
 
 ss_status work_alloc_df64(SolveWork& W, cudaStream_t st) {
-  if (W.xdf.n >= (size_t)W.rows_total && W.udf.n >= (size_t)W.rows_total) return SS_OK;
+  if (W.xdf.n >= (size_t)W.rows_total && W.udf.n >= (size_t)W.rows_total) {
+    if (W.df_rows != W.rows_total) {   // the dummy record of this row count must read as zero
+      SS_CUDA(cudaMemsetAsync(W.xdf.get() + (W.rows_total - 1), 0, sizeof(float4), st));
+      SS_CUDA(cudaMemsetAsync(W.udf.get() + (W.rows_total - 1), 0, sizeof(float4), st));
+      W.df_rows = W.rows_total;
+    }
+    return SS_OK;
+  }
+  W.df_rows = W.rows_total;
   SS_TRY(W.xdf.alloc(W.rows_total, st));
   SS_TRY(W.udf.alloc(W.rows_total, st));
   // the dummy record (last row) must read as zero
@@ -1129,12 +1155,29 @@ ss_status work_upload(SolveWork& W, const SolvePlan& plan, cudaStream_t st) {
 }
 
 ss_status max_grid(int mode, int block, int* grid) {
+  // resident blocks per SM, looked up once per device, mode and block size
+  static std::mutex mu;
+  static int cache[64][4][4] = {};
+  int dev = 0;
+  SS_CUDA(cudaGetDevice(&dev));
+  const int bi = block == 128 ? 0 : block == 256 ? 1 : block == 512 ? 2 : 3;
+  if (dev >= 0 && dev < 64 && mode >= 0 && mode < 4) {
+    std::lock_guard<std::mutex> lk(mu);
+    if (cache[dev][mode][bi] > 0) {
+      *grid = cache[dev][mode][bi] * sm_count();
+      return SS_OK;
+    }
+  }
   int nb = 0;
   if (mode == 0) SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<0>, block, 0));
   else if (mode == 1) SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<1>, block, 0));
   else if (mode == 2) SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<2>, block, 0));
   else SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<3>, block, 0));
   if (nb < 1) SS_FAIL(SS_ERR_CUDA, "solve: kernel does not fit on an SM with %d threads", block);
+  if (dev >= 0 && dev < 64 && mode >= 0 && mode < 4) {
+    std::lock_guard<std::mutex> lk(mu);
+    cache[dev][mode][bi] = nb;
+  }
   *grid = nb * sm_count();
   return SS_OK;
 }
@@ -1378,12 +1421,34 @@ static std::mutex g_ctx_mu;
 static std::unordered_map<const ss_stamp_s*, ss_solve_ctx*> g_ctx;
 
 namespace ss {
+// Contexts of destroyed stamps are kept (a few) with their device buffers and
+// given to the next stamps: a new stamp then needs no allocation for its
+// solves, only new records (work_alloc re-initialises them for its rows).
+static std::vector<ss_solve_ctx*> g_spare_ctx;
+constexpr size_t kMaxSpareCtx = 4;
+
+static void reset_ctx(ss_solve_ctx* C) {
+  C->planned_mode = -1;
+  C->work.rows_total = 0;
+  C->block = 1024;
+  C->blocks_per_sm = 1;
+  C->chunks_per_block = 1;
+  C->use_half = true;
+  if (C->half) reset_ctx(C->half);
+}
+
 void drop_solve_ctx(const ss_stamp_s* s) {
   std::lock_guard<std::mutex> lk(g_ctx_mu);
   auto it = g_ctx.find(s);
   if (it != g_ctx.end()) {
-    delete it->second;
+    ss_solve_ctx* C = it->second;
     g_ctx.erase(it);
+    if (g_spare_ctx.size() < kMaxSpareCtx) {
+      reset_ctx(C);
+      g_spare_ctx.push_back(C);
+    } else {
+      delete C;
+    }
   }
 }
 }  // namespace ss
@@ -1391,7 +1456,14 @@ void drop_solve_ctx(const ss_stamp_s* s) {
 static ss_solve_ctx* solve_ctx(const ss_stamp_s* s) {
   std::lock_guard<std::mutex> lk(g_ctx_mu);
   auto& slot = g_ctx[s];
-  if (!slot) slot = new ss_solve_ctx();
+  if (!slot) {
+    if (!g_spare_ctx.empty()) {
+      slot = g_spare_ctx.back();
+      g_spare_ctx.pop_back();
+    } else {
+      slot = new ss_solve_ctx();
+    }
+  }
   return slot;
 }
 

@@ -84,7 +84,9 @@ struct SolvePlan {
 
 // Device workspace of one solve context (single stamp or batch).
 struct SolveWork {
-  int64_t rows_total = 0;   // padded rows, plus one dummy record
+  int64_t rows_total = 0;   // padded rows, plus one dummy record (0: records not set up for this stamp)
+  int64_t cap_rows = 0;     // rows the vector and record buffers hold
+  int64_t df_rows = -1, bi_rows = -1;   // rows_total the DF64 / BiCGStab dummy records were cleared for
   cudaEvent_t ev[2] = {nullptr, nullptr};
   ~SolveWork() {
     if (ev[0]) cudaEventDestroy(ev[0]);
