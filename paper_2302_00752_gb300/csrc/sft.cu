@@ -14,6 +14,9 @@
 // one 16-byte gather and ~15 (real) or ~30 (complex) FP32 operations instead of
 // FP64 instructions, which GB300 issues at one per SM clock.  The samples are
 // real, so the FFT is real-to-complex (bins b > M/2 are conj(X[M-b])).
+// With many terms (FP64, M up to 2^25) the samples come instead from one
+// complex-to-real inverse FFT of the terms binned by residue: evaluation at
+// the nodes of a rank-1 lattice is a length-M inverse DFT.
 #include <cufft.h>
 
 #include <cstdlib>
@@ -473,8 +476,13 @@ struct SftPlan {
   DevBuf<float2> t3[3];                                    // FP32 three-level tables
   int64_t n2 = 0;
   bool df = false;                                         // full table in double-float form
+  // inverse (Z2D) plan of the FFT evaluation path, made on first use
+  mutable std::mutex ifft_mu;
+  mutable cufftHandle ifft = 0;
+  mutable bool has_ifft = false;
   ~SftPlan() {
     if (has_fft) cufftDestroy(fft);
+    if (has_ifft) cufftDestroy(ifft);
   }
 };
 
@@ -556,6 +564,76 @@ ss_status get_plan(int64_t M, ss_precision prec, cudaStream_t st, std::shared_pt
   return SS_OK;
 }
 
+// FFT evaluation (FP64): g_j = Re sum_t c_t w^{j r_t}, w = exp(2 pi i / M),
+// is the inverse DFT of the Hermitian spectrum X with X_{r_t} += c_t / 2 and
+// X_{M - r_t} += conj(c_t) / 2 (bins 0 and M/2 take Re c_t), so one Z2D
+// transform of the half spectrum (bins b <= M/2) gives all M samples in
+// O(M log M) instead of O(M T).  It pays for many terms on a size cuFFT
+// factors into small primes.
+constexpr int64_t kFftEvalMaxM = 1ll << 25;
+constexpr int64_t kFftEvalTermsSmooth = 64;     // unmerged terms, M 7-smooth
+constexpr int64_t kFftEvalTermsOther = 512;     // unmerged terms, other M (Bluestein)
+constexpr int kBinTile = 1024;
+
+bool smooth7(int64_t M) {
+  for (int64_t p : {2, 3, 5, 7})
+    while (M % p == 0) M /= p;
+  return M == 1;
+}
+
+bool use_fft_eval(const SftPlan& P, int64_t n) {
+  if (P.prec != SS_FP64 || P.M < 2 || P.M > kFftEvalMaxM) return false;
+  return n >= (smooth7(P.M) ? kFftEvalTermsSmooth : kFftEvalTermsOther);
+}
+
+ss_status ensure_ifft(const SftPlan& P) {
+  std::lock_guard<std::mutex> lk(P.ifft_mu);
+  if (P.has_ifft) return SS_OK;
+  const cufftResult r = cufftPlan1d(&P.ifft, (int)P.M, CUFFT_Z2D, 1);
+  if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cufftPlan1d(%lld, Z2D) failed: %d", (long long)P.M, (int)r);
+  P.has_ifft = true;
+  return SS_OK;
+}
+
+// bins[b] for the b that some compacted term t < *n_dev reaches (the rest
+// stay as the caller zeroed them).  Terms sharing a bin are summed, in term
+// order, by the first of them; the others write nothing.
+__global__ void k_bin_terms(const int64_t* __restrict__ q, const double2* __restrict__ coef,
+                            const int64_t* __restrict__ n_dev, int64_t M, double2* __restrict__ bins) {
+  __shared__ int64_t s_r[kBinTile];
+  const int64_t n = *n_dev;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool leader = t < n;
+  int64_t b = -1;
+  if (leader) {
+    const int64_t r = q[t];
+    b = 2 * r <= M ? r : M - r;
+  }
+  double re = 0.0, im = 0.0;
+  for (int64_t u0 = 0; u0 < n; u0 += kBinTile) {
+    const int m = (int)(n - u0 < kBinTile ? n - u0 : kBinTile);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s_r[i] = q[u0 + i];
+    __syncthreads();
+    if (!leader) continue;
+    for (int i = 0; i < m; ++i) {
+      const int64_t r = s_r[i];
+      const bool lo = 2 * r <= M;
+      if ((lo ? r : M - r) != b) continue;
+      const int64_t u = u0 + i;
+      if (u < t) {
+        leader = false;
+        break;
+      }
+      const double2 c = coef[u];
+      re += c.x;
+      im += lo ? c.y : -c.y;
+    }
+  }
+  if (!leader) return;
+  bins[b] = (b == 0 || 2 * b == M) ? make_double2(re, 0.0) : make_double2(0.5 * re, 0.5 * im);
+}
+
 template <typename R, int TAB>
 ss_status launch_sample(const SftPlan& P, unsigned grid, size_t sm, const int64_t* q, const int64_t* step,
                         const double2* coef, const int64_t* n_dev, void* out, cudaStream_t st) {
@@ -602,6 +680,20 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
   k_compact_terms<<<nblk(n), 256, 0, st>>>(g->freq, n, L, flag.get(), pos.get(), merged.get(), q.get(), step.get(),
                                            coef.get());
   SS_LAUNCH_CHECK();
+  if (use_fft_eval(P, n)) {
+    // the spectrum buffer holds the bins; its next reader (the forward
+    // transform of recovery) follows in stream order
+    SS_TRY(ensure_ifft(P));
+    auto bins = reinterpret_cast<double2*>(P.spectrum.get());
+    SS_CUDA(cudaMemsetAsync(bins, 0, (P.M / 2 + 1) * sizeof(double2), st));
+    k_bin_terms<<<nblk(n), 256, 0, st>>>(q.get(), coef.get(), total.get(), P.M, bins);
+    SS_LAUNCH_CHECK();
+    cufftResult r = cufftSetStream(P.ifft, st);
+    if (r == CUFFT_SUCCESS)
+      r = cufftExecZ2D(P.ifft, reinterpret_cast<cufftDoubleComplex*>(bins), reinterpret_cast<cufftDoubleReal*>(out));
+    if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cuFFT Z2D exec failed: %d", (int)r);
+    return SS_OK;
+  }
   if (P.prec == SS_FP64) {
     if (P.full.get() && P.df) {
       auto tab = reinterpret_cast<const float4*>(P.full.get());

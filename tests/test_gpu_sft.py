@@ -108,6 +108,32 @@ def test_sampling_matches_oracle(B, prec, tol):
     assert np.abs(g[js] - ref).max() <= tol * scale
 
 
+@pytest.mark.parametrize("M,n_terms", [(2 ** 5 * 3 ** 4 * 5 ** 2 * 7, 300), (100003, 700)])
+def test_many_term_sampling_matches_oracle(B, M, n_terms):
+    # many terms: the FP64 samples come from one inverse FFT of the binned
+    # terms; residue collisions are planted (a frequency aliasing to bin 0,
+    # one on bin M/2 when M is even, pairs sharing a residue or its negative)
+    rng = np.random.default_rng(2)
+    d = 4
+    z = np.concatenate([[1], rng.integers(1, M, size=d - 1)])
+    freq = rng.integers(-40, 41, size=(n_terms, d))
+    e1 = np.array([M, 0, 0, 0])
+    freq[1] = e1
+    freq[2] = freq[10] + e1
+    freq[3] = e1 - freq[11]
+    freq[4] = -freq[12] - e1
+    if M % 2 == 0:
+        freq[5] = [M // 2, 0, 0, 0]
+        freq[6] = [-M // 2, 0, 0, 0]
+    freq[7] = freq[13]            # a repeated frequency
+    freq[8] = -freq[14]           # and its negative
+    coef = rng.standard_normal(n_terms) + 1j * rng.standard_normal(n_terms)
+    g = B.lattice_sample(z, M, freq, coef, "fp64").double().cpu().numpy()
+    js = np.concatenate([np.arange(0, M, 11), [M // 2, M - 1]])
+    ref = osft.sample(freq, coef, z, M, js)
+    assert np.abs(g[js] - ref).max() <= 1e-13 * np.abs(coef).sum()
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 def test_recover_cfg1_matches_oracle(B, prec, tol):
     inst = W.make_cfg1()
