@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsparse_spectral.so")
 SOURCES = ["api.cu", "scan.cu", "stamp.cu", "apply.cu", "lattice.cu", "sft.cu", "solve.cu", "batch.cu", "proxy.cu",
-           "pipeline.cu"]
+           "pipeline.cu", "fft_df.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -46,6 +46,36 @@ __device__ __forceinline__ DF df_add(const DF a, const DF b) {
 
 __device__ __forceinline__ DF df_neg(const DF a) { return DF{-a.hi, -a.lo}; }
 
+__device__ __forceinline__ DF df_sub(const DF a, const DF b) { return df_add(a, df_neg(b)); }
+
+// a * b (TwoProd of the high parts plus the cross terms, renormalised).
+__device__ __forceinline__ DF df_mul(const DF a, const DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float hi = __fadd_rn(p, e);
+  return DF{hi, __fsub_rn(e, __fsub_rn(hi, p))};
+}
+
+// a1 b1 + a2 b2: both TwoProds, one TwoSum of the products, the errors added.
+__device__ __forceinline__ DF df_dot2(const DF a1, const DF b1, const DF a2, const DF b2) {
+  const float p1 = __fmul_rn(a1.hi, b1.hi);
+  float e1 = __fmaf_rn(a1.hi, b1.hi, -p1);
+  e1 = __fmaf_rn(a1.hi, b1.lo, e1);
+  e1 = __fmaf_rn(a1.lo, b1.hi, e1);
+  const float p2 = __fmul_rn(a2.hi, b2.hi);
+  float e2 = __fmaf_rn(a2.hi, b2.hi, -p2);
+  e2 = __fmaf_rn(a2.hi, b2.lo, e2);
+  e2 = __fmaf_rn(a2.lo, b2.hi, e2);
+  const float s = __fadd_rn(p1, p2);
+  const float bb = __fsub_rn(s, p1);
+  const float t = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bb)), __fsub_rn(p2, bb));
+  const float lo = __fadd_rn(t, __fadd_rn(e1, e2));
+  const float hi = __fadd_rn(s, lo);
+  return DF{hi, __fsub_rn(lo, __fsub_rn(hi, s))};
+}
+
 __device__ __forceinline__ double df_to_double(const DF a) { return (double)a.hi + (double)a.lo; }
 
 // Sum over the warp (fixed butterfly; every lane gets the result).

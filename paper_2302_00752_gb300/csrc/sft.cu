@@ -26,6 +26,7 @@
 #include <mutex>
 
 #include "df.cuh"
+#include "fft_df.cuh"
 #include "lattice.cuh"
 
 namespace ss {
@@ -476,6 +477,11 @@ struct SftPlan {
   DevBuf<float2> t3[3];                                    // FP32 three-level tables
   int64_t n2 = 0;
   bool df = false;                                         // full table in double-float form
+  // double-float complex FFT (FP64 recovery of two real sums at once)
+  bool has_dff = false;
+  DfFftPlan dff;
+  DevBuf<float4> dfz, dftmp;
+  DevBuf<double> dfscale;   // the two sums' scales of the last round trip
   // inverse (Z2D) plan of the FFT evaluation path, made on first use
   mutable std::mutex ifft_mu;
   mutable cufftHandle ifft = 0;
@@ -550,6 +556,12 @@ ss_status get_plan(int64_t M, ss_precision prec, cudaStream_t st, std::shared_pt
       k_twiddles_df<<<nblk(M), 256, 0, st>>>(M, reinterpret_cast<float4*>(p->full.get()));
     SS_LAUNCH_CHECK();
     p->df = !native_fp64_sampling();
+    if (p->df && df_fft_plan(M, &p->dff)) {
+      SS_TRY(p->dfz.alloc(M, st));
+      SS_TRY(p->dftmp.alloc(M, st));
+      SS_TRY(p->dfscale.alloc(2, st));
+      p->has_dff = true;
+    }
   }
   const cufftResult r = cufftPlan1d(&p->fft, (int)M, prec == SS_FP64 ? CUFFT_D2Z : CUFFT_R2C, 1);
   if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cufftPlan1d(%lld) failed: %d", (long long)M, (int)r);
@@ -557,6 +569,7 @@ ss_status get_plan(int64_t M, ss_precision prec, cudaStream_t st, std::shared_pt
   // the plan is cached across calls and streams
   SS_CUDA(cudaStreamSynchronize(st));
   p->samples.settle(); p->spectrum.settle(); p->lo.settle(); p->hi.settle(); p->full.settle();
+  p->dfz.settle(); p->dftmp.settle(); p->dfscale.settle();
   for (auto& t : p->t3) t.settle();
   g_plans.push_front(p);
   while (g_plans.size() > kMaxPlans) g_plans.pop_back();
@@ -634,6 +647,119 @@ __global__ void k_bin_terms(const int64_t* __restrict__ q, const double2* __rest
   bins[b] = (b == 0 || 2 * b == M) ? make_double2(re, 0.0) : make_double2(0.5 * re, 0.5 * im);
 }
 
+// scale[w] = the power of two at or below sum_t |c_t| of sum w (1 if zero):
+// the two sums share one transform at comparable magnitudes, so each keeps its
+// own relative rounding error; powers of two scale exactly.
+constexpr int kScaleThreads = 512;
+__global__ void __launch_bounds__(kScaleThreads) k_pair_scale(const double2* __restrict__ ca,
+                                                              const int64_t* __restrict__ na_dev,
+                                                              const double2* __restrict__ cf,
+                                                              const int64_t* __restrict__ nf_dev, double* scale) {
+  __shared__ double s_part[kScaleThreads];
+  const double2* c[2] = {ca, cf};
+  const int64_t n[2] = {*na_dev, *nf_dev};
+  for (int w = 0; w < 2; ++w) {
+    double acc = 0.0;
+    for (int64_t t = threadIdx.x; t < n[w]; t += kScaleThreads) acc += hypot(c[w][t].x, c[w][t].y);
+    s_part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kScaleThreads / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) s_part[threadIdx.x] += s_part[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) scale[w] = s_part[0] > 0.0 ? ldexp(1.0, ilogb(s_part[0])) : 1.0;
+    __syncthreads();
+  }
+}
+
+// Two real sums a and f at once: Z = S_a + i S_f with S_a, S_f their
+// Hermitian spectra (as in k_bin_terms), over the whole length M, so that the
+// inverse transform of Z is s_a + i s_f (real and imaginary parts are the two
+// sample vectors).  Terms are a's (u < na) then f's; the first term of each
+// bin sums the bin's a and f terms in this order and writes Z[b] and Z[M - b]
+// (each sum divided by its scale).  Z must be zero on entry.
+__global__ void k_bin_pair(const int64_t* __restrict__ qa, const double2* __restrict__ ca,
+                           const int64_t* __restrict__ na_dev, const int64_t* __restrict__ qf,
+                           const double2* __restrict__ cf, const int64_t* __restrict__ nf_dev,
+                           const double* __restrict__ scale, int64_t M, float4* __restrict__ Z) {
+  __shared__ int64_t s_r[kBinTile];
+  const int64_t na = *na_dev, n = na + *nf_dev;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool leader = t < n;
+  int64_t b = -1;
+  if (leader) {
+    const int64_t r = t < na ? qa[t] : qf[t - na];
+    b = 2 * r <= M ? r : M - r;
+  }
+  double are = 0.0, aim = 0.0, fre = 0.0, fim = 0.0;
+  for (int64_t u0 = 0; u0 < n; u0 += kBinTile) {
+    const int m = (int)(n - u0 < kBinTile ? n - u0 : kBinTile);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const int64_t u = u0 + i;
+      s_r[i] = u < na ? qa[u] : qf[u - na];
+    }
+    __syncthreads();
+    if (!leader) continue;
+    for (int i = 0; i < m; ++i) {
+      const int64_t r = s_r[i];
+      const bool lo = 2 * r <= M;
+      if ((lo ? r : M - r) != b) continue;
+      const int64_t u = u0 + i;
+      if (u < t) {
+        leader = false;
+        break;
+      }
+      if (u < na) {
+        const double2 c = ca[u];
+        are += c.x;
+        aim += lo ? c.y : -c.y;
+      } else {
+        const double2 c = cf[u - na];
+        fre += c.x;
+        fim += lo ? c.y : -c.y;
+      }
+    }
+  }
+  if (!leader) return;
+  const double ia = 1.0 / scale[0], jf = 1.0 / scale[1];   // exact: powers of two
+  are *= ia; aim *= ia; fre *= jf; fim *= jf;
+  if (b == 0 || 2 * b == M) {
+    const DF zr = df_split(are), zi = df_split(fre);
+    Z[b] = make_float4(zr.hi, zr.lo, zi.hi, zi.lo);
+    return;
+  }
+  are *= 0.5; aim *= 0.5; fre *= 0.5; fim *= 0.5;
+  DF x = df_split(are - fim), y = df_split(aim + fre);
+  Z[b] = make_float4(x.hi, x.lo, y.hi, y.lo);
+  x = df_split(are + fim);
+  y = df_split(fre - aim);
+  Z[M - b] = make_float4(x.hi, x.lo, y.hi, y.lo);
+}
+
+// Recovery from the forward transform Zh of s_a + i s_f: with x = Zh[b] and
+// y = Zh[M - b], the bin of the real sum a is (x + conj(y)) / 2 and that of f
+// is (x - conj(y)) / (2 i), each scaled by 1 / M.
+template <int WHICH>
+__global__ void k_extract_pair(const int32_t* __restrict__ cand, int64_t n, LatticeDev L, const float4* __restrict__ Zh,
+                               const double* __restrict__ scale, double2* val, double* mag,
+                               unsigned long long* maxbits) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t b = residue_of(cand + i * L.d, L.d, L);
+  const int64_t nb = (L.M - b) % L.M;
+  const float4 xs = Zh[b], ys = Zh[nb];
+  const double xr = (double)xs.x + (double)xs.y, xi = (double)xs.z + (double)xs.w;
+  const double yr = (double)ys.x + (double)ys.y, yi = (double)ys.z + (double)ys.w;
+  const double sc = 0.5 / (double)L.M * scale[WHICH];
+  const double2 v = WHICH == 0 ? make_double2((xr + yr) * sc, (xi - yi) * sc)
+                               : make_double2((xi + yi) * sc, (yr - xr) * sc);
+  val[i] = v;
+  const double m = hypot(v.x, v.y);
+  mag[i] = m;
+  atomicMax(maxbits, (unsigned long long)__double_as_longlong(m));
+}
+
 template <typename R, int TAB>
 ss_status launch_sample(const SftPlan& P, unsigned grid, size_t sm, const int64_t* q, const int64_t* step,
                         const double2* coef, const int64_t* n_dev, void* out, cudaStream_t st) {
@@ -647,8 +773,47 @@ ss_status launch_sample(const SftPlan& P, unsigned grid, size_t sm, const int64_
   return SS_OK;
 }
 
-// Merge +-p terms (exact rewrite of the real sum) and evaluate; no host
-// synchronisation (term counts stay on the device).
+// The merged terms of one real sum: residues q, phase steps, coefficients and
+// their count (on the device).
+struct Terms {
+  DevBuf<int64_t> q, step, total;
+  DevBuf<double2> coef;
+};
+
+// Merge +-p terms (exact rewrite of the real sum) and compact them; no host
+// synchronisation (the merged count stays on the device).
+ss_status prep_terms(const LatticeDev& L, const ss_trig* g, Terms* T, cudaStream_t st) {
+  const int64_t n = g->n_terms;
+  SS_TRY(T->total.alloc(1, st));
+  if (n == 0) {
+    SS_CUDA(cudaMemsetAsync(T->total.get(), 0, sizeof(int64_t), st));
+    return SS_OK;
+  }
+  if (n > 46340) SS_FAIL(SS_ERR_INVALID, "lattice_sample: more than 46340 terms");
+  DevBuf<int32_t> flag, pos, imag, first;
+  DevBuf<double2> merged;
+  SS_TRY(T->q.alloc(n, st));
+  SS_TRY(T->step.alloc(n, st));
+  SS_TRY(flag.alloc(n, st));
+  SS_TRY(pos.alloc(n, st));
+  SS_TRY(imag.alloc(1, st));
+  SS_TRY(first.alloc(n, st));
+  SS_TRY(merged.alloc(n, st));
+  SS_TRY(T->coef.alloc(n, st));
+  SS_CUDA(cudaMemsetAsync(imag.get(), 0, sizeof(int32_t), st));
+  k_fill_first<<<nblk(n), 256, 0, st>>>(first.get(), n);
+  k_merge_first<<<nblk(n * n), 256, 0, st>>>(g->freq, n, L.d, first.get());
+  k_merge_sum<<<nblk(n * 32), 256, 0, st>>>(g->freq, reinterpret_cast<const double2*>(g->coef), n, L.d,
+                                            first.get(), flag.get(), merged.get(), imag.get());
+  SS_LAUNCH_CHECK();
+  SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), n, T->total.get(), st));
+  k_compact_terms<<<nblk(n), 256, 0, st>>>(g->freq, n, L, flag.get(), pos.get(), merged.get(), T->q.get(),
+                                           T->step.get(), T->coef.get());
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
+// Evaluate a real sum on the lattice; no host synchronisation.
 ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, void* out, cudaStream_t st) {
   const int64_t n = g->n_terms;
   const int64_t Lsz = 1ll << P.bl;
@@ -657,29 +822,12 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
     SS_CUDA(cudaMemsetAsync(out, 0, P.M * (P.prec == SS_FP64 ? sizeof(double) : sizeof(float)), st));
     return SS_OK;
   }
-  if (n > 46340) SS_FAIL(SS_ERR_INVALID, "lattice_sample: more than 46340 terms");
-  DevBuf<int64_t> q, step, total;
-  DevBuf<int32_t> flag, pos, imag, first;
-  DevBuf<double2> merged, coef;
-  SS_TRY(q.alloc(n, st));
-  SS_TRY(step.alloc(n, st));
-  SS_TRY(total.alloc(1, st));
-  SS_TRY(flag.alloc(n, st));
-  SS_TRY(pos.alloc(n, st));
-  SS_TRY(imag.alloc(1, st));
-  SS_TRY(first.alloc(n, st));
-  SS_TRY(merged.alloc(n, st));
-  SS_TRY(coef.alloc(n, st));
-  SS_CUDA(cudaMemsetAsync(imag.get(), 0, sizeof(int32_t), st));
-  k_fill_first<<<nblk(n), 256, 0, st>>>(first.get(), n);
-  k_merge_first<<<nblk(n * n), 256, 0, st>>>(g->freq, n, L.d, first.get());
-  k_merge_sum<<<nblk(n * 32), 256, 0, st>>>(g->freq, reinterpret_cast<const double2*>(g->coef), n, L.d,
-                                            first.get(), flag.get(), merged.get(), imag.get());
-  SS_LAUNCH_CHECK();
-  SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), n, total.get(), st));
-  k_compact_terms<<<nblk(n), 256, 0, st>>>(g->freq, n, L, flag.get(), pos.get(), merged.get(), q.get(), step.get(),
-                                           coef.get());
-  SS_LAUNCH_CHECK();
+  Terms T;
+  SS_TRY(prep_terms(L, g, &T, st));
+  DevBuf<int64_t>& q = T.q;
+  DevBuf<int64_t>& step = T.step;
+  DevBuf<int64_t>& total = T.total;
+  DevBuf<double2>& coef = T.coef;
   if (use_fft_eval(P, n)) {
     // the spectrum buffer holds the bins; its next reader (the forward
     // transform of recovery) follows in stream order
@@ -747,8 +895,36 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
 // Bins, threshold and compaction in candidate order; the reconstructing and
 // symmetry checks run on the device beside them and are read back with the
 // kept count in one synchronisation at the end.
+// FP64 plans with the double-float transform: the sums a and f (f may be
+// null) are sampled by one inverse transform of Z = S_a + i S_f and the
+// samples s_a + i s_f transformed forward again; on return P.dfz holds that
+// spectrum (read by k_extract_pair).
+ss_status dff_round_trip(const SftPlan& P, const LatticeDev& L, const ss_trig* a, const ss_trig* f, cudaStream_t st) {
+  const ss_trig none{L.d, 0, nullptr, nullptr};
+  if (!f) f = &none;
+  Terms ta, tf;
+  SS_TRY(prep_terms(L, a, &ta, st));
+  SS_TRY(prep_terms(L, f, &tf, st));
+  float4* Z = P.dfz.get();
+  const float4* tab = reinterpret_cast<const float4*>(P.full.get());
+  SS_CUDA(cudaMemsetAsync(Z, 0, P.M * sizeof(float4), st));
+  double* scale = P.dfscale.get();
+  k_pair_scale<<<1, kScaleThreads, 0, st>>>(ta.coef.get(), ta.total.get(), tf.coef.get(), tf.total.get(), scale);
+  SS_LAUNCH_CHECK();
+  if (a->n_terms + f->n_terms > 0) {
+    k_bin_pair<<<nblk(a->n_terms + f->n_terms), 256, 0, st>>>(ta.q.get(), ta.coef.get(), ta.total.get(), tf.q.get(),
+                                                              tf.coef.get(), tf.total.get(), scale, P.M, Z);
+    SS_LAUNCH_CHECK();
+  }
+  SS_TRY(df_fft(P.dff, tab, Z, P.dftmp.get(), Z, +1, st));
+  return df_fft(P.dff, tab, Z, P.dftmp.get(), Z, -1, st);
+}
+
+// zh non-null: the bins come from the double-float spectrum zh (real part
+// sum, as left by dff_round_trip) instead of a transform of samples.
 ss_status recover_from(const SftPlan& P, const LatticeDev& L, const void* samples, const int32_t* cand, int64_t n_cand,
-                       int64_t s_max, double tau, int32_t* freq_out, double* val_out, int64_t* n_out, cudaStream_t st) {
+                       int64_t s_max, double tau, int32_t* freq_out, double* val_out, int64_t* n_out, cudaStream_t st,
+                       const float4* zh = nullptr) {
   DevBuf<int64_t> res, total;
   DevBuf<unsigned long long> table, maxbits;
   DevBuf<int32_t> flags, flag, pos;
@@ -767,17 +943,22 @@ ss_status recover_from(const SftPlan& P, const LatticeDev& L, const void* sample
   SS_TRY(total.alloc(1, st));
   SS_TRY(residues(cand, n_cand, L, res.get(), st));
   SS_TRY(check_reconstructing_async(cand, n_cand, L, res.get(), true, table.get(), cap, flags.get(), st));
-  cufftResult r = cufftSetStream(P.fft, st);
-  if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cufftSetStream failed: %d", (int)r);
-  if (P.prec == SS_FP64)
-    r = cufftExecD2Z(P.fft, reinterpret_cast<cufftDoubleReal*>(const_cast<void*>(samples)),
-                     reinterpret_cast<cufftDoubleComplex*>(P.spectrum.get()));
-  else
-    r = cufftExecR2C(P.fft, reinterpret_cast<cufftReal*>(const_cast<void*>(samples)),
-                     reinterpret_cast<cufftComplex*>(P.spectrum.get()));
-  if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cuFFT exec failed: %d", (int)r);
+  if (!zh) {
+    cufftResult r = cufftSetStream(P.fft, st);
+    if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cufftSetStream failed: %d", (int)r);
+    if (P.prec == SS_FP64)
+      r = cufftExecD2Z(P.fft, reinterpret_cast<cufftDoubleReal*>(const_cast<void*>(samples)),
+                       reinterpret_cast<cufftDoubleComplex*>(P.spectrum.get()));
+    else
+      r = cufftExecR2C(P.fft, reinterpret_cast<cufftReal*>(const_cast<void*>(samples)),
+                       reinterpret_cast<cufftComplex*>(P.spectrum.get()));
+    if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cuFFT exec failed: %d", (int)r);
+  }
   SS_CUDA(cudaMemsetAsync(maxbits.get(), 0, sizeof(unsigned long long), st));
-  if (P.prec == SS_FP64)
+  if (zh)
+    k_extract_pair<0><<<nblk(n_cand), 256, 0, st>>>(cand, n_cand, L, zh, P.dfscale.get(), val.get(), mag.get(),
+                                                    maxbits.get());
+  else if (P.prec == SS_FP64)
     k_extract<double2><<<nblk(n_cand), 256, 0, st>>>(cand, n_cand, L, reinterpret_cast<const double2*>(P.spectrum.get()),
                                                      val.get(), mag.get(), maxbits.get());
   else
@@ -1107,7 +1288,27 @@ ss_status sft_recover_both(const ss_lattice* lat, const ss_trig* a, const ss_tri
   const ss_trig* g[2] = {a, f};
   int32_t* fo[2] = {a_freq, f_freq};
   double* vo[2] = {a_val, f_val};
-  for (int k = 0; k < 2; ++k) {
+  if (P.has_dff) {
+    // FP64: both sums sampled by one inverse and recovered by one forward
+    // double-float transform of length M
+    SS_TRY(dff_round_trip(P, L, a, f, st));
+    const float4* Z = P.dfz.get();
+    for (int k = 0; k < 2; ++k) {
+      if (k == 0)
+        k_extract_pair<0><<<nblk(n_cand), 256, 0, st>>>(cand, n_cand, L, Z, P.dfscale.get(), val.get(), mag.get(),
+                                                        maxbits.get());
+      else
+        k_extract_pair<1><<<nblk(n_cand), 256, 0, st>>>(cand, n_cand, L, Z, P.dfscale.get(), val.get(), mag.get(),
+                                                        maxbits.get() + 1);
+      k_keep<<<nblk(n_cand), 256, 0, st>>>(mag.get(), n_cand, maxbits.get() + k, tau, flag.get());
+      SS_LAUNCH_CHECK();
+      SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), n_cand, total.get() + k, st));
+      k_compact<<<nblk(n_cand), 256, 0, st>>>(cand, val.get(), n_cand, L.d, flag.get(), pos.get(), fo[k],
+                                              reinterpret_cast<double2*>(vo[k]));
+      SS_LAUNCH_CHECK();
+    }
+  }
+  for (int k = 0; k < 2 && !P.has_dff; ++k) {
     // the plan's sample and spectrum buffers serve both sums in stream order
     SS_TRY(sample_into(P, L, g[k], P.samples.get(), st));
     if (P.prec == SS_FP64)
@@ -1185,6 +1386,10 @@ extern "C" ss_status sft_recover(const ss_lattice* lat, const ss_trig* g, ss_pre
   cudaStream_t st = as_stream(stream);
   std::shared_ptr<SftPlan> P;
   SS_TRY(get_plan(L.M, prec, st, &P));
+  if (P->has_dff) {
+    SS_TRY(dff_round_trip(*P, L, g, nullptr, st));
+    return recover_from(*P, L, nullptr, cand, n_cand, s_max, tau, freq_out, val_out, n_out, st, P->dfz.get());
+  }
   SS_TRY(sample_into(*P, L, g, P->samples.get(), st));
   return recover_from(*P, L, P->samples.get(), cand, n_cand, s_max, tau, freq_out, val_out, n_out, st);
 }

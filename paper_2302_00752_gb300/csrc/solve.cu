@@ -436,12 +436,6 @@ __device__ void solve_fp64(const SolveParams& P, Smem& sm) {
 // until the warp fold; the CG scalars, the stopping test and the final
 // residual f - L x are FP64.  Same recurrences, same phases.
 
-__device__ __forceinline__ DF df_mul(DF a, DF b) {
-  DF r{0.f, 0.f};
-  df_fma(r, a, b);
-  return r;
-}
-
 __device__ void solve_df64(const SolveParams& P, Smem& sm) {
   const double tol2 = P.tol * P.tol;
   auto noscal = [](int, const Chunk&, int, int, bool, int) {};

@@ -7,6 +7,7 @@ import pytest
 import torch
 
 import workloads as W
+from oracle import lattice as olat
 from oracle import pipeline as opipe
 from oracle.solve import rel_l2
 
@@ -34,8 +35,15 @@ def test_fused_equals_staged(mods, make, prec):
         assert fused.stamp.size == staged.stamp.size and fused.stamp.nnz == staged.stamp.nnz
         assert torch.equal(fused.stamp.export()[0], staged.stamp.export()[0])
         assert fused.stats["status"] == staged.stats["status"] == "SS_OK"
-        assert fused.stats["applies"] == staged.stats["applies"]
-        assert torch.equal(fused.u, staged.u)
+        if p.sft_precision == "fp64" and olat.is_smooth(M) and M <= 2 ** 22:
+            # the fused call transforms a and f together (one complex
+            # double-float transform of s_a + i s_f), the staged calls one at a
+            # time: the same support and stamp, the values within rounding
+            assert abs(fused.stats["applies"] - staged.stats["applies"]) <= 1
+            assert rel_l2(fused.u.cpu().numpy(), staged.u.cpu().numpy()) < 1e-12
+        else:
+            assert fused.stats["applies"] == staged.stats["applies"]
+            assert torch.equal(fused.u, staged.u)
     finally:
         fused.stamp.destroy()
         staged.stamp.destroy()

@@ -134,6 +134,41 @@ def test_many_term_sampling_matches_oracle(B, M, n_terms):
     assert np.abs(g[js] - ref).max() <= 1e-13 * np.abs(coef).sum()
 
 
+@pytest.mark.parametrize("M,d,span", [(453600, 3, 12),   # 672 x 675: radices 8 4 3 7 | 5 5 3 3 3
+                                      (18816, 3, 6),     # 128 x 147: radices 8 8 2 | 3 7 7
+                                      (48, 1, 3),        # 6 x 8: radices 2 3 | 8
+                                      (14, 1, 3),        # 2 x 7
+                                      (2 ** 20, 2, 20)])  # 1024 x 1024: radices 8 8 8 2
+def test_recover_smooth_sizes_matches_oracle(B, M, d, span):
+    # FP64 recovery on 7-smooth M runs the double-float transform (two
+    # launches of per-block Stockham passes): every radix and uneven factor
+    # pairs, against the exact coefficients and the oracle's plain DFT
+    rng = np.random.default_rng(M)
+    n_terms = 40 if d > 1 else 3
+    freq = rng.integers(-span, span + 1, size=(n_terms, d))
+    if d == 1:
+        freq = np.array([[0], [1], [3]])
+    coef = rng.standard_normal(n_terms) + 1j * rng.standard_normal(n_terms)
+    extra = rng.integers(-span, span + 1, size=(2 * n_terms, d))
+    I = np.unique(np.vstack([freq, -freq, extra, -extra]), axis=0)
+    for _ in range(200):
+        z = rng.integers(1, M, size=d) if d > 1 else np.array([1])
+        if olat.is_reconstructing(I, z, M):
+            break
+    assert olat.is_reconstructing(I, z, M)
+    gf, gv = B.sft_recover(z, M, freq, coef, I, tau=1e-9)
+    want = osft.true_coefficients(freq, coef)
+    got = {tuple(k): v for k, v in zip(gf.cpu().numpy().tolist(), gv.cpu().numpy())}
+    scale = np.abs(coef).sum()
+    assert set(got) == {k for k, v in want.items() if abs(v) > 1e-9 * scale}
+    for k, v in got.items():
+        assert abs(v - want[k]) <= 1e-12 * scale
+    if M <= 20000:   # the plain DFT costs M |I| exponentials
+        kf, kv = osft.recover_known(osft.sample(freq, coef, z, M), I, z, M, tau=1e-9)
+        assert np.array_equal(gf.cpu().numpy(), kf)
+        assert np.abs(gv.cpu().numpy() - kv).max() <= 1e-12 * scale
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 def test_recover_cfg1_matches_oracle(B, prec, tol):
     inst = W.make_cfg1()
