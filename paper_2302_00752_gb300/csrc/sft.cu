@@ -586,7 +586,6 @@ ss_status get_plan(int64_t M, ss_precision prec, cudaStream_t st, std::shared_pt
 constexpr int64_t kFftEvalMaxM = 1ll << 25;
 constexpr int64_t kFftEvalTermsSmooth = 64;     // unmerged terms, M 7-smooth
 constexpr int64_t kFftEvalTermsOther = 512;     // unmerged terms, other M (Bluestein)
-constexpr int kBinTile = 1024;
 
 bool smooth7(int64_t M) {
   for (int64_t p : {2, 3, 5, 7})
@@ -609,41 +608,38 @@ ss_status ensure_ifft(const SftPlan& P) {
 }
 
 // bins[b] for the b that some compacted term t < *n_dev reaches (the rest
-// stay as the caller zeroed them).  Terms sharing a bin are summed, in term
-// order, by the first of them; the others write nothing.
+// stay as the caller zeroed them).  One warp per term: a term with an earlier
+// term in its bin writes nothing; the first one sums the bin's terms (lanes in
+// a fixed stride, then a fixed butterfly: deterministic).
+__device__ __forceinline__ int64_t half_bin(int64_t r, int64_t M) { return 2 * r <= M ? r : M - r; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __global__ void k_bin_terms(const int64_t* __restrict__ q, const double2* __restrict__ coef,
                             const int64_t* __restrict__ n_dev, int64_t M, double2* __restrict__ bins) {
-  __shared__ int64_t s_r[kBinTile];
   const int64_t n = *n_dev;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool leader = t < n;
-  int64_t b = -1;
-  if (leader) {
-    const int64_t r = q[t];
-    b = 2 * r <= M ? r : M - r;
-  }
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= n) return;   // warp-uniform
+  const int64_t b = half_bin(q[t], M);
+  bool earlier = false;
+  for (int64_t u = lane; u < t && !earlier; u += 32) earlier = half_bin(q[u], M) == b;
+  if (__any_sync(0xffffffffu, earlier)) return;
   double re = 0.0, im = 0.0;
-  for (int64_t u0 = 0; u0 < n; u0 += kBinTile) {
-    const int m = (int)(n - u0 < kBinTile ? n - u0 : kBinTile);
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) s_r[i] = q[u0 + i];
-    __syncthreads();
-    if (!leader) continue;
-    for (int i = 0; i < m; ++i) {
-      const int64_t r = s_r[i];
-      const bool lo = 2 * r <= M;
-      if ((lo ? r : M - r) != b) continue;
-      const int64_t u = u0 + i;
-      if (u < t) {
-        leader = false;
-        break;
-      }
-      const double2 c = coef[u];
-      re += c.x;
-      im += lo ? c.y : -c.y;
-    }
+  for (int64_t u = t + lane; u < n; u += 32) {
+    const int64_t r = q[u];
+    if (half_bin(r, M) != b) continue;
+    const double2 c = coef[u];
+    re += c.x;
+    im += 2 * r <= M ? c.y : -c.y;
   }
-  if (!leader) return;
+  re = warp_sum(re);
+  im = warp_sum(im);
+  if (lane) return;
   bins[b] = (b == 0 || 2 * b == M) ? make_double2(re, 0.0) : make_double2(0.5 * re, 0.5 * im);
 }
 
@@ -675,53 +671,42 @@ __global__ void __launch_bounds__(kScaleThreads) k_pair_scale(const double2* __r
 // Two real sums a and f at once: Z = S_a + i S_f with S_a, S_f their
 // Hermitian spectra (as in k_bin_terms), over the whole length M, so that the
 // inverse transform of Z is s_a + i s_f (real and imaginary parts are the two
-// sample vectors).  Terms are a's (u < na) then f's; the first term of each
-// bin sums the bin's a and f terms in this order and writes Z[b] and Z[M - b]
-// (each sum divided by its scale).  Z must be zero on entry.
+// sample vectors).  Terms are a's (u < na) then f's; as in k_bin_terms the
+// first term of each bin sums the bin's a and f terms and writes Z[b] and
+// Z[M - b] (each sum divided by its scale).  Z must be zero on entry.
 __global__ void k_bin_pair(const int64_t* __restrict__ qa, const double2* __restrict__ ca,
                            const int64_t* __restrict__ na_dev, const int64_t* __restrict__ qf,
                            const double2* __restrict__ cf, const int64_t* __restrict__ nf_dev,
                            const double* __restrict__ scale, int64_t M, float4* __restrict__ Z) {
-  __shared__ int64_t s_r[kBinTile];
   const int64_t na = *na_dev, n = na + *nf_dev;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool leader = t < n;
-  int64_t b = -1;
-  if (leader) {
-    const int64_t r = t < na ? qa[t] : qf[t - na];
-    b = 2 * r <= M ? r : M - r;
-  }
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= n) return;   // warp-uniform
+  auto res = [&](int64_t u) { return u < na ? qa[u] : qf[u - na]; };
+  const int64_t b = half_bin(res(t), M);
+  bool earlier = false;
+  for (int64_t u = lane; u < t && !earlier; u += 32) earlier = half_bin(res(u), M) == b;
+  if (__any_sync(0xffffffffu, earlier)) return;
   double are = 0.0, aim = 0.0, fre = 0.0, fim = 0.0;
-  for (int64_t u0 = 0; u0 < n; u0 += kBinTile) {
-    const int m = (int)(n - u0 < kBinTile ? n - u0 : kBinTile);
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      const int64_t u = u0 + i;
-      s_r[i] = u < na ? qa[u] : qf[u - na];
-    }
-    __syncthreads();
-    if (!leader) continue;
-    for (int i = 0; i < m; ++i) {
-      const int64_t r = s_r[i];
-      const bool lo = 2 * r <= M;
-      if ((lo ? r : M - r) != b) continue;
-      const int64_t u = u0 + i;
-      if (u < t) {
-        leader = false;
-        break;
-      }
-      if (u < na) {
-        const double2 c = ca[u];
-        are += c.x;
-        aim += lo ? c.y : -c.y;
-      } else {
-        const double2 c = cf[u - na];
-        fre += c.x;
-        fim += lo ? c.y : -c.y;
-      }
+  for (int64_t u = t + lane; u < n; u += 32) {
+    const int64_t r = res(u);
+    if (half_bin(r, M) != b) continue;
+    const bool lo = 2 * r <= M;
+    if (u < na) {
+      const double2 c = ca[u];
+      are += c.x;
+      aim += lo ? c.y : -c.y;
+    } else {
+      const double2 c = cf[u - na];
+      fre += c.x;
+      fim += lo ? c.y : -c.y;
     }
   }
-  if (!leader) return;
+  are = warp_sum(are);
+  aim = warp_sum(aim);
+  fre = warp_sum(fre);
+  fim = warp_sum(fim);
+  if (lane) return;
   const double ia = 1.0 / scale[0], jf = 1.0 / scale[1];   // exact: powers of two
   are *= ia; aim *= ia; fre *= jf; fim *= jf;
   if (b == 0 || 2 * b == M) {
@@ -834,7 +819,7 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
     SS_TRY(ensure_ifft(P));
     auto bins = reinterpret_cast<double2*>(P.spectrum.get());
     SS_CUDA(cudaMemsetAsync(bins, 0, (P.M / 2 + 1) * sizeof(double2), st));
-    k_bin_terms<<<nblk(n), 256, 0, st>>>(q.get(), coef.get(), total.get(), P.M, bins);
+    k_bin_terms<<<nblk(n * 32), 256, 0, st>>>(q.get(), coef.get(), total.get(), P.M, bins);
     SS_LAUNCH_CHECK();
     cufftResult r = cufftSetStream(P.ifft, st);
     if (r == CUFFT_SUCCESS)
@@ -912,7 +897,7 @@ ss_status dff_round_trip(const SftPlan& P, const LatticeDev& L, const ss_trig* a
   k_pair_scale<<<1, kScaleThreads, 0, st>>>(ta.coef.get(), ta.total.get(), tf.coef.get(), tf.total.get(), scale);
   SS_LAUNCH_CHECK();
   if (a->n_terms + f->n_terms > 0) {
-    k_bin_pair<<<nblk(a->n_terms + f->n_terms), 256, 0, st>>>(ta.q.get(), ta.coef.get(), ta.total.get(), tf.q.get(),
+    k_bin_pair<<<nblk((a->n_terms + f->n_terms) * 32), 256, 0, st>>>(ta.q.get(), ta.coef.get(), ta.total.get(), tf.q.get(),
                                                               tf.coef.get(), tf.total.get(), scale, P.M, Z);
     SS_LAUNCH_CHECK();
   }

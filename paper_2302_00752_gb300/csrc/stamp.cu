@@ -489,10 +489,17 @@ static ss_status grow_table(ss_stamp_s* S, int64_t need, const KeyParams& P, cud
   return SS_OK;
 }
 
+static ss_status resize_keys(ss_stamp_s* S, int64_t cap, cudaStream_t st);
+
 static ss_status grow_keys(ss_stamp_s* S, int64_t need, cudaStream_t st) {
   const int WT = S->key.WT;
   if ((int64_t)S->keys.n >= need * WT) return SS_OK;
-  const int64_t cap = std::max<int64_t>(need, (int64_t)(S->keys.n / WT) * 2);
+  return resize_keys(S, std::max<int64_t>(need, (int64_t)(S->keys.n / WT) * 2), st);
+}
+
+// Keys, levels and norms moved to buffers of cap rows (cap >= size).
+static ss_status resize_keys(ss_stamp_s* S, int64_t cap, cudaStream_t st) {
+  const int WT = S->key.WT;
   DevBuf<uint64_t> k2;
   DevBuf<int8_t> l2;
   DevBuf<int64_t> n2;
@@ -512,6 +519,18 @@ static ss_status grow_keys(ss_stamp_s* S, int64_t need, cudaStream_t st) {
   l2.s = st;
   n2.s = st;
   return SS_OK;
+}
+
+// |S^N| <= |F| C(s_a - 1 + N, N): an element is some k in F plus a multiset of
+// at most N of the s_a - 1 nonzero steps.  Returns min(that, cap).
+constexpr int64_t kPresizeCap = 1ll << 22;
+static int64_t stamp_size_bound(int64_t n_f, int s_a, int N, int64_t cap) {
+  double c = 1.0;   // C(m + i, i), m = s_a - 1, exact while below 2^53
+  for (int i = 1; i <= N; ++i) {
+    c = c * (double)(s_a - 1 + i) / (double)i;
+    if (c * (double)n_f >= (double)cap) return cap;
+  }
+  return std::min<int64_t>(cap, (int64_t)(c * (double)n_f));
 }
 
 // Norm range: |k|^2 <= d maxabs^2 is formed in int64 (and the FP64 entry
@@ -926,10 +945,12 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
                                                                S->ca64.get(), S->ca32.get())));
   SS_LAUNCH_CHECK();
 
-  // level 0
+  // level 0; keys and table sized at once for the whole construction when
+  // the bound fits, so that the levels do not grow (copy, rehash) them
   S->level_start.assign(1, 0);
-  SS_TRY(grow_keys(S, n_f, st));
-  SS_TRY(grow_table(S, n_f, P, st, err));
+  const int64_t pre = std::max<int64_t>(n_f, stamp_size_bound(n_f, s_a, N, kPresizeCap));
+  SS_TRY(grow_keys(S, pre, st));
+  SS_TRY(grow_table(S, pre, P, st, err));
   SS_DISPATCH_WT(L.WT, (k_level0<WT><<<nblk(n_f), 256, 0, st>>>(P, Fs.get(), n_f, S->keys.get(), S->level.get(),
                                                                 S->norm.get(), S->table.get(),
                                                                 (uint64_t)S->cap - 1, err, S->zidx_dev.get())));
@@ -937,6 +958,10 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   S->size = n_f;
   S->level_start.push_back(n_f);
   SS_TRY(run_levels(S, 1, N, st));
+  // give back a large over-reservation of the size bound (the keys stay for
+  // lookups, extension and export; the norms are read up to rows_pad + 1)
+  const int64_t rows = (int64_t)(S->keys.n / L.WT), keep = S->size + kSlice + 1;
+  if (rows > 4 * keep && (double)rows * (8.0 * L.WT + 9.0) > 64e6) SS_TRY(resize_keys(S, keep, st));
   return build_operator(S, st);
 }
 
