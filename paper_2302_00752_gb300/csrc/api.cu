@@ -1,5 +1,6 @@
 // Library-wide helpers behind the C ABI: per-thread error text, version,
 // device properties.
+#include <vector>
 #include <algorithm>
 #include <cstdarg>
 
@@ -26,6 +27,87 @@ void retain_pool() {
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
   done_dev = dev;
+}
+
+namespace {
+
+struct ScratchBlock {
+  size_t off, bytes;
+  bool live;
+};
+
+struct Scratch {
+  unsigned char* base = nullptr;
+  size_t cap = 0, top = 0, want = 0;
+  int64_t spill = 0;
+  int dev = -1;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  std::vector<ScratchBlock> blocks;
+};
+
+Scratch& scratch() {
+  thread_local Scratch S;
+  return S;
+}
+
+}  // namespace
+
+void scratch_spill(int64_t bytes) { scratch().spill += bytes; }
+
+void* scratch_take(size_t bytes, cudaStream_t st) {
+  Scratch& A = scratch();
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  bytes = (bytes + 255) & ~(size_t)255;
+  const size_t need = A.top + bytes + (size_t)(A.spill > 0 ? A.spill : 0);
+  if (need > A.want) A.want = need;
+  if (A.blocks.empty()) {
+    if (A.base && (A.dev != dev || A.want > A.cap)) {
+      cudaFreeAsync(A.base, A.st);   // after the work queued on the stream that used it
+      A.base = nullptr;
+      A.cap = 0;
+    }
+    if (!A.base && A.want > 0) {
+      retain_pool();
+      const size_t cap = A.want + A.want / 4;
+      if (cudaMallocAsync(reinterpret_cast<void**>(&A.base), cap, st) != cudaSuccess) {
+        cudaGetLastError();
+        A.base = nullptr;
+        return nullptr;
+      }
+      A.cap = cap;
+      A.dev = dev;
+      A.st = st;
+    }
+    if (A.base && st != A.st) {
+      // the new stream waits for the old stream's use of the block
+      if (!A.ev && cudaEventCreateWithFlags(&A.ev, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+      if (cudaEventRecord(A.ev, A.st) != cudaSuccess || cudaStreamWaitEvent(st, A.ev, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+      A.st = st;
+    }
+  }
+  if (!A.base || A.dev != dev || st != A.st || A.top + bytes > A.cap) return nullptr;
+  A.blocks.push_back(ScratchBlock{A.top, bytes, true});
+  A.top += bytes;
+  return A.base + A.blocks.back().off;
+}
+
+void scratch_give(void* p) {
+  Scratch& A = scratch();
+  const size_t off = static_cast<unsigned char*>(p) - A.base;
+  for (auto it = A.blocks.rbegin(); it != A.blocks.rend(); ++it)
+    if (it->off == off && it->live) {
+      it->live = false;
+      break;
+    }
+  while (!A.blocks.empty() && !A.blocks.back().live) {
+    A.top = A.blocks.back().off;
+    A.blocks.pop_back();
+  }
 }
 
 namespace {

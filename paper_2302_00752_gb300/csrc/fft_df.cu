@@ -14,7 +14,8 @@
 // Radices 8, 4, 2 use the usual split forms; 3, 5 and 7 the symmetric form
 // y_s = v_0 + sum_r cos(2 pi r s / R) (v_r + v_{R-r}) + sign i sin(2 pi r s / R) (v_r - v_{R-r}).
 // Every twiddle and constant is an entry of the double-float table
-// exp(2 pi i r / M), conjugated for sign = -1.
+// exp(2 pi i r / M), conjugated for sign = -1; a block stages the L-th roots
+// exp(2 pi i m / L) = tab[m M / L] it uses in shared memory.
 //
 // On this part an FP64 instruction issues at 1/64 of the FP32 rate; a
 // double-float operation costs 7 to 19 FP32 instructions, so the transform
@@ -125,18 +126,16 @@ __device__ __forceinline__ void dft(C4 (&v)[R], const C4* cs) {
   }
 }
 
+// tw[m] = exp(2 pi i m / L), m < L, in shared memory.
 template <int R, int SIGN>
-__device__ __forceinline__ void pass(const float4* __restrict__ a, float4* __restrict__ b, int L, int Ns, int64_t M,
-                                     const float4* __restrict__ tab) {
+__device__ __forceinline__ void pass(const float4* __restrict__ a, float4* __restrict__ b, int L, int Ns,
+                                     const float4* __restrict__ tw) {
   constexpr int NC = R == 8 ? 1 : (R - 1) / 2;
   C4 cs[NC > 0 ? NC : 1];
 #pragma unroll
-  for (int m = 0; m < NC; ++m) {
-    const float4 e = __ldg(tab + (M / R) * (m + 1));
-    cs[m] = C4{DF{e.x, e.y}, DF{e.z, e.w}};
-  }
+  for (int m = 0; m < NC; ++m) cs[m] = ld(tw[(L / R) * (m + 1)]);
   const int nb = L / R;
-  const int64_t tstride = M / ((int64_t)Ns * R);
+  const int tstride = L / (Ns * R);
   for (int j = threadIdx.x; j < nb; j += blockDim.x) {
     const int k = j % Ns;
     C4 v[R];
@@ -144,7 +143,10 @@ __device__ __forceinline__ void pass(const float4* __restrict__ a, float4* __res
     for (int r = 0; r < R; ++r) v[r] = ld(a[j + r * nb]);
     if (Ns > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle<SIGN>(tab, tstride * (int64_t)(k * r)));
+      for (int r = 1; r < R; ++r) {
+        const C4 w = ld(tw[tstride * (k * r)]);
+        v[r] = cmul(v[r], SIGN > 0 ? w : C4{w.re, df_neg(w.im)});
+      }
     }
     dft<R, SIGN>(v, cs);
     const int base = (j / Ns) * Ns * R + k;
@@ -162,20 +164,24 @@ __global__ void k_fft_df(const float4* __restrict__ in, float4* __restrict__ out
   const int L = SECOND ? L2 : L1;
   float4* a = sbuf;
   float4* b = sbuf + L;
+  float4* tw = sbuf + 2 * L;
   const int64_t blk = blockIdx.x;
-  for (int i = threadIdx.x; i < L; i += blockDim.x)
+  const int64_t tstep = M / L;
+  for (int i = threadIdx.x; i < L; i += blockDim.x) {
     a[i] = SECOND ? in[blk * L2 + i] : in[(int64_t)i * L2 + blk];
+    tw[i] = __ldg(tab + tstep * i);
+  }
   __syncthreads();
   int Ns = 1;
   for (int p = 0; p < rad.n; ++p) {
     const int R = rad.r[p];
     switch (R) {
-      case 8: pass<8, SIGN>(a, b, L, Ns, M, tab); break;
-      case 4: pass<4, SIGN>(a, b, L, Ns, M, tab); break;
-      case 2: pass<2, SIGN>(a, b, L, Ns, M, tab); break;
-      case 5: pass<5, SIGN>(a, b, L, Ns, M, tab); break;
-      case 3: pass<3, SIGN>(a, b, L, Ns, M, tab); break;
-      default: pass<7, SIGN>(a, b, L, Ns, M, tab); break;
+      case 8: pass<8, SIGN>(a, b, L, Ns, tw); break;
+      case 4: pass<4, SIGN>(a, b, L, Ns, tw); break;
+      case 2: pass<2, SIGN>(a, b, L, Ns, tw); break;
+      case 5: pass<5, SIGN>(a, b, L, Ns, tw); break;
+      case 3: pass<3, SIGN>(a, b, L, Ns, tw); break;
+      default: pass<7, SIGN>(a, b, L, Ns, tw); break;
     }
     __syncthreads();
     float4* t = a;
@@ -194,7 +200,9 @@ __global__ void k_fft_df(const float4* __restrict__ in, float4* __restrict__ out
 
 DfRadices radices(int L) {
   DfRadices d;
-  for (int R : {8, 4, 2, 5, 3, 7})
+  // odd radices first: the first pass (Ns = 1) writes at stride R, free of
+  // shared-memory bank conflicts for odd R
+  for (int R : {7, 5, 3, 8, 4, 2})
     while (L > 1 && L % R == 0 && d.n < kDfFftMaxPasses) {
       d.r[d.n++] = R;
       L /= R;
@@ -213,7 +221,7 @@ template <int SIGN, bool SECOND>
 ss_status launch(const DfFftPlan& F, const float4* tab, const float4* in, float4* out, cudaStream_t st) {
   const int L = SECOND ? F.L2 : F.L1;
   const DfRadices& rad = SECOND ? F.rad2 : F.rad1;
-  const size_t sm = 2 * (size_t)L * sizeof(float4);
+  const size_t sm = 3 * (size_t)L * sizeof(float4);
   int threads = (L / min_radix(rad) + 31) / 32 * 32;
   threads = threads < 64 ? 64 : (threads > 512 ? 512 : threads);
   if (sm > 48 * 1024)

@@ -366,8 +366,8 @@ ss_status check_reconstructing(const int32_t* freq, int64_t n, const LatticeDev&
   while (cap < (uint64_t)(2 * n)) cap <<= 1;
   DevBuf<unsigned long long> table;
   DevBuf<int32_t> flags;
-  SS_TRY(table.alloc(cap, st));
-  SS_TRY(flags.alloc(4, st));
+  SS_TRY(table.alloc_tmp(cap, st));
+  SS_TRY(flags.alloc_tmp(4, st));
   SS_CUDA(cudaMemsetAsync(table.get(), 0, cap * sizeof(unsigned long long), st));
   SS_CUDA(cudaMemsetAsync(flags.get(), 0, 4 * sizeof(int32_t), st));
   k_check_insert<<<nblk(n), 256, 0, st>>>(freq, res, n, L.d, table.get(), cap - 1, flags.get());
@@ -385,7 +385,7 @@ ss_status check_reconstructing(const int32_t* freq, int64_t n, const LatticeDev&
 
 static ss_status expansion_of(const int32_t* freq, int64_t n, int d, int64_t* K, cudaStream_t st) {
   DevBuf<int32_t> mm;
-  SS_TRY(mm.alloc(2 * d, st));
+  SS_TRY(mm.alloc_tmp(2 * d, st));
   std::vector<int32_t> init(2 * d);
   for (int c = 0; c < d; ++c) { init[c] = INT32_MAX; init[d + c] = INT32_MIN; }
   SS_TRY(upload(st, {{mm.get(), init.data(), 2 * d * sizeof(int32_t)}}));
@@ -418,7 +418,7 @@ extern "C" ss_status lattice_check(const ss_lattice* lat, const int32_t* freq, i
   if (n > 0 && !freq) SS_FAIL(SS_ERR_INVALID, "lattice_check: null frequencies");
   cudaStream_t st = as_stream(stream);
   DevBuf<int64_t> res;
-  SS_TRY(res.alloc(n, st));
+  SS_TRY(res.alloc_tmp(n, st));
   SS_TRY(residues(freq, n, L, res.get(), st));
   return check_reconstructing(freq, n, L, res.get(), false, st);
 }
@@ -431,7 +431,7 @@ namespace {
 ss_status random_draws(const int32_t* freq, int64_t n, int32_t d, int64_t M, const int64_t* raw, int32_t attempts,
                        int64_t* z_out, int32_t* attempt_out, cudaStream_t st) {
   DevBuf<int64_t> res;
-  SS_TRY(res.alloc(n, st));
+  SS_TRY(res.alloc_tmp(n, st));
   std::vector<int64_t> z(d);
   for (int a = 0; a < attempts; ++a) {
     for (int c = 0; c < d; ++c) {
@@ -508,20 +508,20 @@ extern "C" ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int6
   }
   DevBuf<int64_t> rho, cand, scratch, zdev;
   DevBuf<int32_t> fail, err;
-  SS_TRY(rho.alloc(n, st));
-  SS_TRY(cand.alloc((size_t)d * n_cand, st));
-  SS_TRY(fail.alloc(n_cand, st));
-  SS_TRY(zdev.alloc(d, st));
-  SS_TRY(err.alloc(1, st));
+  SS_TRY(rho.alloc_tmp(n, st));
+  SS_TRY(cand.alloc_tmp((size_t)d * n_cand, st));
+  SS_TRY(fail.alloc_tmp(n_cand, st));
+  SS_TRY(zdev.alloc_tmp(d, st));
+  SS_TRY(err.alloc_tmp(1, st));
   int hash_cap = 1;
   while (hash_cap < 2 * n) hash_cap <<= 1;
   const size_t hash_smem = (size_t)n * sizeof(int64_t) + (size_t)hash_cap * sizeof(int32_t);
   if (hash_smem <= 200 * 1024) {
     if (hash_smem > 48 * 1024)
       SS_CUDA(cudaFuncSetAttribute(k_cbc_try_hash, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hash_smem));
-    SS_TRY(scratch.alloc(1, st));
+    SS_TRY(scratch.alloc_tmp(1, st));
   } else {
-    SS_TRY(scratch.alloc((size_t)n_cand * n, st));
+    SS_TRY(scratch.alloc_tmp((size_t)n_cand * n, st));
   }
   // all candidates up front; each coordinate's pick stays on the device
   std::vector<int64_t> hc((size_t)d * n_cand, 1), z(d, 1);
@@ -548,9 +548,9 @@ extern "C" ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int6
     DevBuf<int32_t> fails;
     DevBuf<unsigned> arrive;
     DevBuf<int32_t> err2;
-    SS_TRY(fails.alloc((size_t)d * n_cand, st));
-    SS_TRY(arrive.alloc(d, st));
-    SS_TRY(err2.alloc(2, st));
+    SS_TRY(fails.alloc_tmp((size_t)d * n_cand, st));
+    SS_TRY(arrive.alloc_tmp(d, st));
+    SS_TRY(err2.alloc_tmp(2, st));
     SS_CUDA(cudaMemsetAsync(arrive.get(), 0, d * sizeof(unsigned), st));
     SS_CUDA(cudaMemsetAsync(err2.get(), 0, 2 * sizeof(int32_t), st));
     const int32_t* fa = freq;

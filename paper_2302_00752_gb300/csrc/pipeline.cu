@@ -47,10 +47,10 @@ ss_status run(const ss_lattice_spec* ls, const ss_trig* a, const ss_trig* f, con
   // recovered coefficients: at most one per candidate
   DevBuf<int32_t> af, ff;
   DevBuf<double2> av, fv;
-  SS_TRY(af.alloc((size_t)n_cand * d, st));
-  SS_TRY(ff.alloc((size_t)n_cand * d, st));
-  SS_TRY(av.alloc(n_cand, st));
-  SS_TRY(fv.alloc(n_cand, st));
+  SS_TRY(af.alloc_tmp((size_t)n_cand * d, st));
+  SS_TRY(ff.alloc_tmp((size_t)n_cand * d, st));
+  SS_TRY(av.alloc_tmp(n_cand, st));
+  SS_TRY(fv.alloc_tmp(n_cand, st));
   int64_t n_a = 0, n_f = 0;
   SS_TRY(sft_recover_both(&lat, a, f, sft_prec, cand, n_cand, tau, af.get(), reinterpret_cast<double*>(av.get()), &n_a,
                           ff.get(), reinterpret_cast<double*>(fv.get()), &n_f, st));

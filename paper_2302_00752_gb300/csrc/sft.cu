@@ -769,7 +769,7 @@ struct Terms {
 // synchronisation (the merged count stays on the device).
 ss_status prep_terms(const LatticeDev& L, const ss_trig* g, Terms* T, cudaStream_t st) {
   const int64_t n = g->n_terms;
-  SS_TRY(T->total.alloc(1, st));
+  SS_TRY(T->total.alloc_tmp(1, st));
   if (n == 0) {
     SS_CUDA(cudaMemsetAsync(T->total.get(), 0, sizeof(int64_t), st));
     return SS_OK;
@@ -777,14 +777,14 @@ ss_status prep_terms(const LatticeDev& L, const ss_trig* g, Terms* T, cudaStream
   if (n > 46340) SS_FAIL(SS_ERR_INVALID, "lattice_sample: more than 46340 terms");
   DevBuf<int32_t> flag, pos, imag, first;
   DevBuf<double2> merged;
-  SS_TRY(T->q.alloc(n, st));
-  SS_TRY(T->step.alloc(n, st));
-  SS_TRY(flag.alloc(n, st));
-  SS_TRY(pos.alloc(n, st));
-  SS_TRY(imag.alloc(1, st));
-  SS_TRY(first.alloc(n, st));
-  SS_TRY(merged.alloc(n, st));
-  SS_TRY(T->coef.alloc(n, st));
+  SS_TRY(T->q.alloc_tmp(n, st));
+  SS_TRY(T->step.alloc_tmp(n, st));
+  SS_TRY(flag.alloc_tmp(n, st));
+  SS_TRY(pos.alloc_tmp(n, st));
+  SS_TRY(imag.alloc_tmp(1, st));
+  SS_TRY(first.alloc_tmp(n, st));
+  SS_TRY(merged.alloc_tmp(n, st));
+  SS_TRY(T->coef.alloc_tmp(n, st));
   SS_CUDA(cudaMemsetAsync(imag.get(), 0, sizeof(int32_t), st));
   k_fill_first<<<nblk(n), 256, 0, st>>>(first.get(), n);
   k_merge_first<<<nblk(n * n), 256, 0, st>>>(g->freq, n, L.d, first.get());
@@ -831,7 +831,7 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
     if (P.full.get() && P.df) {
       auto tab = reinterpret_cast<const float4*>(P.full.get());
       DevBuf<float4> W;
-      SS_TRY(W.alloc(n * kSampPerThread, st));
+      SS_TRY(W.alloc_tmp(n * kSampPerThread, st));
       k_term_powers<<<nblk(n), 256, 0, st>>>(step.get(), total.get(), P.M, tab, W.get());
       // split the terms over gridDim.y when the sample blocks alone would not
       // fill the SMs several times over (n bounds the merged term count)
@@ -843,7 +843,7 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
                                                    reinterpret_cast<double*>(out));
       } else {
         DevBuf<double> part;
-        SS_TRY(part.alloc((size_t)n_split * P.M, st));
+        SS_TRY(part.alloc_tmp((size_t)n_split * P.M, st));
         k_sample_df<<<dim3(grid, n_split), kSampThreads, 0, st>>>(P.M, tab, q.get(), W.get(), coef.get(),
                                                                   total.get(), part.get());
         k_sum_splits<<<nblk(P.M), 256, 0, st>>>(part.get(), n_split, P.M, reinterpret_cast<double*>(out));
@@ -864,7 +864,7 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
   const size_t w_sm = kTermChunk * (kSampPerThread * sizeof(float2) + sizeof(float2) + sizeof(uint32_t));
   if (tab_sm + w_sm <= 200 * 1024) {
     DevBuf<float2> W;
-    SS_TRY(W.alloc(n * kSampPerThread, st));
+    SS_TRY(W.alloc_tmp(n * kSampPerThread, st));
     k_term_powers32<<<nblk(n), 256, 0, st>>>(step.get(), total.get(), P.M, W.get());
     const size_t sm = tab_sm + w_sm;
     SS_CUDA(cudaFuncSetAttribute(k_sample32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -917,15 +917,15 @@ ss_status recover_from(const SftPlan& P, const LatticeDev& L, const void* sample
   DevBuf<double> mag;
   uint64_t cap = 1;
   while (cap < (uint64_t)(2 * n_cand)) cap <<= 1;
-  SS_TRY(res.alloc(n_cand, st));
-  SS_TRY(table.alloc(cap, st));
-  SS_TRY(flags.alloc(4, st));
-  SS_TRY(val.alloc(n_cand, st));
-  SS_TRY(mag.alloc(n_cand, st));
-  SS_TRY(maxbits.alloc(1, st));
-  SS_TRY(flag.alloc(n_cand, st));
-  SS_TRY(pos.alloc(n_cand, st));
-  SS_TRY(total.alloc(1, st));
+  SS_TRY(res.alloc_tmp(n_cand, st));
+  SS_TRY(table.alloc_tmp(cap, st));
+  SS_TRY(flags.alloc_tmp(4, st));
+  SS_TRY(val.alloc_tmp(n_cand, st));
+  SS_TRY(mag.alloc_tmp(n_cand, st));
+  SS_TRY(maxbits.alloc_tmp(1, st));
+  SS_TRY(flag.alloc_tmp(n_cand, st));
+  SS_TRY(pos.alloc_tmp(n_cand, st));
+  SS_TRY(total.alloc_tmp(1, st));
   SS_TRY(residues(cand, n_cand, L, res.get(), st));
   SS_TRY(check_reconstructing_async(cand, n_cand, L, res.get(), true, table.get(), cap, flags.get(), st));
   if (!zh) {
@@ -1255,15 +1255,15 @@ ss_status sft_recover_both(const ss_lattice* lat, const ss_trig* a, const ss_tri
   DevBuf<double> mag;
   uint64_t cap = 1;
   while (cap < (uint64_t)(2 * n_cand)) cap <<= 1;
-  SS_TRY(res.alloc(n_cand, st));
-  SS_TRY(table.alloc(cap, st));
-  SS_TRY(flags.alloc(4, st));
-  SS_TRY(val.alloc(n_cand, st));
-  SS_TRY(mag.alloc(n_cand, st));
-  SS_TRY(maxbits.alloc(2, st));
-  SS_TRY(flag.alloc(n_cand, st));
-  SS_TRY(pos.alloc(n_cand, st));
-  SS_TRY(total.alloc(2, st));
+  SS_TRY(res.alloc_tmp(n_cand, st));
+  SS_TRY(table.alloc_tmp(cap, st));
+  SS_TRY(flags.alloc_tmp(4, st));
+  SS_TRY(val.alloc_tmp(n_cand, st));
+  SS_TRY(mag.alloc_tmp(n_cand, st));
+  SS_TRY(maxbits.alloc_tmp(2, st));
+  SS_TRY(flag.alloc_tmp(n_cand, st));
+  SS_TRY(pos.alloc_tmp(n_cand, st));
+  SS_TRY(total.alloc_tmp(2, st));
   // one candidate set and one lattice: residues and the check once
   SS_TRY(residues(cand, n_cand, L, res.get(), st));
   SS_TRY(check_reconstructing_async(cand, n_cand, L, res.get(), true, table.get(), cap, flags.get(), st));

@@ -69,24 +69,64 @@ ss_status upload(cudaStream_t st, std::initializer_list<HostWrite> parts);
 // device) so that repeated builds do not go back to the driver.
 void retain_pool();
 
+// Scratch for call-local temporaries: one device block per host thread and
+// device, handed out in 256-byte units from the bottom up and given back in
+// any order (the top comes down once the blocks above are free).  A block is
+// reused in stream order: the scratch follows one stream at a time, and a
+// temporary on another stream waits (one event) for what the previous stream
+// queued, taken only while nothing is live.  A request that does not fit comes
+// from the pool and raises the size the block is regrown to when next idle.
+// Not for memory that a captured graph or a persistent object keeps.
+void* scratch_take(size_t bytes, cudaStream_t st);   // nullptr: use the pool
+void scratch_give(void* p);
+void scratch_spill(int64_t bytes);                  // pool fallbacks alive (+/-)
+
 // Owning device buffer from the stream-ordered pool: allocated on a stream
 // and freed on the same stream (work queued there before the free still sees
 // the memory).  settle() moves the free to the legacy stream for buffers that
 // outlive the call that made them (the caller synchronised that call's stream).
+// alloc_tmp / ensure_tmp take call-local temporaries from the thread's scratch.
 template <typename T>
 struct DevBuf {
   T* p = nullptr;
   size_t n = 0;
   cudaStream_t s = nullptr;
+  int tmp = 0;   // 1: scratch block, 2: pool fallback of alloc_tmp
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFreeAsync(p, s);
+    if (p) {
+      if (tmp == 1) {
+        scratch_give(p);
+      } else {
+        cudaFreeAsync(p, s);
+        if (tmp == 2) scratch_spill(-(int64_t)(n * sizeof(T)));
+      }
+    }
     p = nullptr;
     n = 0;
+    tmp = 0;
   }
+  ss_status alloc_tmp(size_t count, cudaStream_t stream) {
+    release();
+    if (count == 0) count = 1;
+    if (void* q = scratch_take(count * sizeof(T), stream)) {
+      p = static_cast<T*>(q);
+      n = count;
+      s = stream;
+      tmp = 1;
+      return SS_OK;
+    }
+    const ss_status r = alloc(count, stream);
+    if (r == SS_OK) {
+      tmp = 2;
+      scratch_spill((int64_t)(count * sizeof(T)));
+    }
+    return r;
+  }
+  ss_status ensure_tmp(size_t count, cudaStream_t stream) { return count <= n ? SS_OK : alloc_tmp(count, stream); }
   void settle() { s = nullptr; }
   ss_status alloc(size_t count, cudaStream_t stream = nullptr) {
     release();

@@ -563,7 +563,7 @@ static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st
   const int s_a = S->s_a;
   DevBuf<int64_t> slot_of, d_total;
   DevBuf<int32_t> flag;
-  SS_TRY(d_total.alloc(1, st));
+  SS_TRY(d_total.alloc_tmp(1, st));
   for (int n = n_from; n <= n_to; ++n) {
     const int64_t par0 = S->level_start[n - 1], n_par = S->level_start[n] - par0;
     const int64_t ncand = n_par * s_a;
@@ -571,8 +571,8 @@ static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st
     if (ncand == 0) { S->level_start.push_back(S->size); continue; }
     SS_TRY(grow_table(S, S->size + n_par * (s_a - 1), P, st, S->err_dev.get()));
     SS_TRY(grow_keys(S, S->size + n_par * (s_a - 1), st));
-    SS_TRY(slot_of.ensure(ncand, st));
-    SS_TRY(flag.ensure(ncand, st));
+    SS_TRY(slot_of.ensure_tmp(ncand, st));
+    SS_TRY(flag.ensure_tmp(ncand, st));
     SS_DISPATCH_WT(S->key.WT, (k_insert<WT><<<nblk(ncand), 256, 0, st>>>(P, S->keys.get(), par0, n_par, s_a, S->j0,
                                                                          S->stepkey.get(), S->table.get(),
                                                                          (uint64_t)S->cap - 1, slot_of.get(),
@@ -580,7 +580,7 @@ static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st
     k_winner_flags<<<nblk(ncand), 256, 0, st>>>(slot_of.get(), S->table.get(), ncand, flag.get());
     SS_LAUNCH_CHECK();
     DevBuf<int32_t> pos;
-    SS_TRY(pos.alloc(ncand, st));
+    SS_TRY(pos.alloc_tmp(ncand, st));
     SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), ncand, d_total.get(), st));
     int64_t added = 0;
     int32_t e = 0;
@@ -720,10 +720,10 @@ static ss_status build_half(ss_stamp_s* S, cudaStream_t st) {
   const KeyParams P = make_key_params(S->key);
   DevBuf<int32_t> plus, ppos, slice_w;
   DevBuf<int64_t> total;
-  SS_TRY(plus.alloc(S->size, st));
-  SS_TRY(ppos.alloc(S->size, st));
-  SS_TRY(slice_w.alloc(S->n_slices_h + 1, st));
-  SS_TRY(total.alloc(1, st));
+  SS_TRY(plus.alloc_tmp(S->size, st));
+  SS_TRY(ppos.alloc_tmp(S->size, st));
+  SS_TRY(slice_w.alloc_tmp(S->n_slices_h + 1, st));
+  SS_TRY(total.alloc_tmp(1, st));
   SS_TRY(S->mirror.alloc(S->size, st));
   SS_TRY(S->hpos.alloc(S->size, st));
   SS_TRY(S->plus_rows.alloc(S->rows_pad_h, st));
@@ -779,10 +779,10 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   DevBuf<int32_t> nbr, slice_w;
   DevBuf<unsigned long long> d_nnz;
   DevBuf<int64_t> d_total;
-  SS_TRY(nbr.alloc((size_t)S->size * s_a, st));
-  SS_TRY(slice_w.alloc(S->n_slices + 1, st));
-  SS_TRY(d_nnz.alloc(1, st));
-  SS_TRY(d_total.alloc(1, st));
+  SS_TRY(nbr.alloc_tmp((size_t)S->size * s_a, st));
+  SS_TRY(slice_w.alloc_tmp(S->n_slices + 1, st));
+  SS_TRY(d_nnz.alloc_tmp(1, st));
+  SS_TRY(d_total.alloc_tmp(1, st));
   SS_CUDA(cudaMemsetAsync(d_nnz.get(), 0, sizeof(unsigned long long), st));
   SS_CUDA(cudaMemsetAsync(slice_w.get(), 0, (S->n_slices + 1) * sizeof(int32_t), st));
   SS_DISPATCH_WT(S->key.WT, (k_neighbors<WT><<<nblk(S->size * s_a), 256, 0, st>>>(
@@ -879,11 +879,11 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   DevBuf<int32_t> Fs, As, rank;
   DevBuf<double2> avs;
   DevBuf<PrepOut> prep;
-  SS_TRY(Fs.alloc(n_f * d, st));
-  SS_TRY(As.alloc((size_t)s_a * d, st));
-  SS_TRY(avs.alloc(s_a, st));
-  SS_TRY(rank.alloc(std::max<int64_t>(n_f, s_a), st));
-  SS_TRY(prep.alloc(1, st));
+  SS_TRY(Fs.alloc_tmp(n_f * d, st));
+  SS_TRY(As.alloc_tmp((size_t)s_a * d, st));
+  SS_TRY(avs.alloc_tmp(s_a, st));
+  SS_TRY(rank.alloc_tmp(std::max<int64_t>(n_f, s_a), st));
+  SS_TRY(prep.alloc_tmp(1, st));
   SS_TRY(S->err_dev.alloc(4, st));
   SS_TRY(S->zidx_dev.alloc(1, st));
   int32_t* err = S->err_dev.get();
@@ -1218,8 +1218,8 @@ extern "C" ss_status stamp_scatter(ss_stamp s, const ss_sparse* g, double* out, 
   }
   DevBuf<int64_t> idx;
   DevBuf<unsigned long long> outside;
-  SS_TRY(idx.alloc(g->n, st));
-  SS_TRY(outside.alloc(1, st));
+  SS_TRY(idx.alloc_tmp(g->n, st));
+  SS_TRY(outside.alloc_tmp(1, st));
   SS_CUDA(cudaMemsetAsync(outside.get(), 0, sizeof(unsigned long long), st));
   SS_TRY(stamp_lookup(s, g->freq, g->n, idx.get(), stream));
   k_scatter_vals<<<nblk(g->n), 256, 0, st>>>(idx.get(), reinterpret_cast<const double2*>(g->val), g->n,
