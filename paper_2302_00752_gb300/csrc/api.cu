@@ -61,7 +61,7 @@ void* scratch_take(size_t bytes, cudaStream_t st) {
   if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
   bytes = (bytes + 255) & ~(size_t)255;
   const size_t need = A.top + bytes + (size_t)(A.spill > 0 ? A.spill : 0);
-  if (need > A.want) A.want = need;
+  if (need > A.want) A.want = need < kScratchMaxCap ? need : kScratchMaxCap;
   if (A.blocks.empty()) {
     if (A.base && (A.dev != dev || A.want > A.cap)) {
       cudaFreeAsync(A.base, A.st);   // after the work queued on the stream that used it
@@ -70,7 +70,7 @@ void* scratch_take(size_t bytes, cudaStream_t st) {
     }
     if (!A.base && A.want > 0) {
       retain_pool();
-      const size_t cap = A.want + A.want / 4;
+      const size_t cap = std::min(A.want + A.want / 4, kScratchMaxCap);
       if (cudaMallocAsync(reinterpret_cast<void**>(&A.base), cap, st) != cudaSuccess) {
         cudaGetLastError();
         A.base = nullptr;

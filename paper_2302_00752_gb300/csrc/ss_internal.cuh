@@ -76,7 +76,12 @@ void retain_pool();
 // temporary on another stream waits (one event) for what the previous stream
 // queued, taken only while nothing is live.  A request that does not fit comes
 // from the pool and raises the size the block is regrown to when next idle.
+// Requests above kScratchMaxTake go to the pool directly (the scratch saves
+// calls, which matters for many small temporaries, not for a few large ones)
+// and the block stays below kScratchMaxCap.
 // Not for memory that a captured graph or a persistent object keeps.
+constexpr size_t kScratchMaxTake = 16u << 20;
+constexpr size_t kScratchMaxCap = 96u << 20;
 void* scratch_take(size_t bytes, cudaStream_t st);   // nullptr: use the pool
 void scratch_give(void* p);
 void scratch_spill(int64_t bytes);                  // pool fallbacks alive (+/-)
@@ -112,6 +117,7 @@ struct DevBuf {
   ss_status alloc_tmp(size_t count, cudaStream_t stream) {
     release();
     if (count == 0) count = 1;
+    if (count * sizeof(T) > kScratchMaxTake) return alloc(count, stream);
     if (void* q = scratch_take(count * sizeof(T), stream)) {
       p = static_cast<T*>(q);
       n = count;
