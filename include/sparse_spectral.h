@@ -137,6 +137,10 @@ ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int64_t M_min, 
 
 /* Lattice sampling: samples[j] = g(x_j), x_j = (j z / M) mod 1, j < M, with the
  * phase of each term taken from the exact residue (j (p.z mod M)) mod M.
+ * Terms are evaluated directly, O(M T).  An FP64 sum with many terms (at
+ * least 64 on a 7-smooth M up to 2^25, at least 512 on another M) is instead
+ * evaluated as the length-M inverse DFT of its terms binned by residue; a
+ * residue shared by several terms is summed in term order.
  * samples: device, M doubles (SS_FP64) or M floats (SS_FP32). */
 ss_status lattice_sample(const ss_lattice* lat, const ss_trig* g, ss_precision prec, void* samples,
                          void* stream);
@@ -156,7 +160,11 @@ ss_status sft_recover_samples(const ss_lattice* lat, const void* samples, ss_pre
                               int32_t* freq_out, double* val_out, int64_t* n_out, void* stream);
 
 /* lattice_sample followed by sft_recover_samples (library-owned sample and
- * FFT buffers).  Synchronises `stream`. */
+ * FFT buffers).  In FP64 on a 7-smooth M up to 2^22 both transforms (the
+ * inverse one that samples g and the forward one that recovers it) run in the
+ * library's double-float FFT instead of cuFFT.  That FFT rounds at about
+ * 2^-46 relative.  The thresholding and output are as in sft_recover_samples.
+ * Synchronises `stream`. */
 ss_status sft_recover(const ss_lattice* lat, const ss_trig* g, ss_precision prec, const int32_t* cand,
                       int64_t n_cand, int64_t s_max, double tau, int32_t* freq_out, double* val_out,
                       int64_t* n_out, void* stream);
@@ -411,7 +419,12 @@ typedef struct {
  * the frequency set I of Theorem SFTRecovery), a_hat = SFT(a) and
  * f_hat = SFT(f) on it (sft_recover with threshold tau, precision sft_prec),
  * S^N[a_hat](supp f_hat) (stamp_build), f_hat scattered onto S and the solve
- * of L_{N,s} u = f_hat (solve with tol, max_iter, solve_prec).  The stages
+ * of L_{N,s} u = f_hat (solve with tol, max_iter, solve_prec).  Where
+ * sft_recover takes the double-float FFT (FP64, 7-smooth M up to 2^22), a and
+ * f share one complex transform each way: S_a / s_a + i S_f / s_f, with
+ * s_a and s_f powers of two near the two sums' l1 norms.  f_hat then agrees
+ * with two separate sft_recover calls to within the transform's rounding,
+ * not bit for bit.  The stages
  * run back to back on `stream` without returning to the caller in between;
  * each synchronises where its own entry point does.  Outputs: the lattice
  * (z_out host [d], M_out), the stamping set (*stamp_out, caller destroys it;
