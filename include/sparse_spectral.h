@@ -419,12 +419,14 @@ typedef struct {
  * the frequency set I of Theorem SFTRecovery), a_hat = SFT(a) and
  * f_hat = SFT(f) on it (sft_recover with threshold tau, precision sft_prec),
  * S^N[a_hat](supp f_hat) (stamp_build), f_hat scattered onto S and the solve
- * of L_{N,s} u = f_hat (solve with tol, max_iter, solve_prec).  Where
- * sft_recover takes the double-float FFT (FP64, 7-smooth M up to 2^22), a and
- * f share one complex transform each way: S_a / s_a + i S_f / s_f, with
- * s_a and s_f powers of two near the two sums' l1 norms.  f_hat then agrees
- * with two separate sft_recover calls to within the transform's rounding,
- * not bit for bit.  The stages
+ * of L_{N,s} u = f_hat (solve with tol, max_iter, solve_prec).  a and f
+ * share one complex transform in two cases: FP64 on a 7-smooth M up to 2^22,
+ * where sft_recover takes the double-float FFT and one transform runs each
+ * way; and FP32 on an M that is not 7-smooth, where cuFFT takes Bluestein's
+ * method and one forward C2C carries s_a / s_a' + i s_f / s_f'.  The scales
+ * s_a', s_f' (and their FP64 counterparts) are powers of two near the two
+ * sums' l1 norms.  In both cases f_hat agrees with two separate sft_recover
+ * calls to within the transform's rounding, not bit for bit.  The stages
  * run back to back on `stream` without returning to the caller in between;
  * each synchronises where its own entry point does.  Outputs: the lattice
  * (z_out host [d], M_out), the stamping set (*stamp_out, caller destroys it;

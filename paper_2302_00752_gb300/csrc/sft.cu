@@ -486,9 +486,18 @@ struct SftPlan {
   mutable std::mutex ifft_mu;
   mutable cufftHandle ifft = 0;
   mutable bool has_ifft = false;
+  // FP32 on sizes cuFFT transforms by Bluestein's method: a and f share one
+  // complex transform (made on first use: plan, f's samples, the packed
+  // vector, the two scales)
+  mutable cufftHandle c2c = 0;
+  mutable bool has_c2c = false;
+  mutable DevBuf<float> samples2;
+  mutable DevBuf<float2> z32;
+  mutable DevBuf<double> scale32;
   ~SftPlan() {
     if (has_fft) cufftDestroy(fft);
     if (has_ifft) cufftDestroy(ifft);
+    if (has_c2c) cufftDestroy(c2c);
   }
 };
 
@@ -598,6 +607,28 @@ bool use_fft_eval(const SftPlan& P, int64_t n) {
   return n >= (smooth7(P.M) ? kFftEvalTermsSmooth : kFftEvalTermsOther);
 }
 
+// FP32 recovery of two sums by one complex transform: on sizes that cuFFT
+// factors into small primes two real transforms cost no more than one complex
+// one; on the others (Bluestein) one complex transform costs about one real.
+bool use_pair32(const SftPlan& P) { return P.prec == SS_FP32 && !smooth7(P.M); }
+
+ss_status ensure_pair32(const SftPlan& P, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(P.ifft_mu);
+  if (P.has_c2c) return SS_OK;
+  SS_TRY(P.samples2.alloc(P.M, st));
+  SS_TRY(P.z32.alloc(P.M, st));
+  SS_TRY(P.scale32.alloc(2, st));
+  const cufftResult r = cufftPlan1d(&P.c2c, (int)P.M, CUFFT_C2C, 1);
+  if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cufftPlan1d(%lld, C2C) failed: %d", (long long)P.M, (int)r);
+  // the buffers belong to the cached plan and outlive this call
+  SS_CUDA(cudaStreamSynchronize(st));
+  P.samples2.settle();
+  P.z32.settle();
+  P.scale32.settle();
+  P.has_c2c = true;
+  return SS_OK;
+}
+
 ss_status ensure_ifft(const SftPlan& P) {
   std::lock_guard<std::mutex> lk(P.ifft_mu);
   if (P.has_ifft) return SS_OK;
@@ -647,13 +678,8 @@ __global__ void k_bin_terms(const int64_t* __restrict__ q, const double2* __rest
 // the two sums share one transform at comparable magnitudes, so each keeps its
 // own relative rounding error; powers of two scale exactly.
 constexpr int kScaleThreads = 512;
-__global__ void __launch_bounds__(kScaleThreads) k_pair_scale(const double2* __restrict__ ca,
-                                                              const int64_t* __restrict__ na_dev,
-                                                              const double2* __restrict__ cf,
-                                                              const int64_t* __restrict__ nf_dev, double* scale) {
+__device__ void pair_scale(const double2* const c[2], const int64_t n[2], double* scale) {
   __shared__ double s_part[kScaleThreads];
-  const double2* c[2] = {ca, cf};
-  const int64_t n[2] = {*na_dev, *nf_dev};
   for (int w = 0; w < 2; ++w) {
     double acc = 0.0;
     for (int64_t t = threadIdx.x; t < n[w]; t += kScaleThreads) acc += hypot(c[w][t].x, c[w][t].y);
@@ -666,6 +692,54 @@ __global__ void __launch_bounds__(kScaleThreads) k_pair_scale(const double2* __r
     if (threadIdx.x == 0) scale[w] = s_part[0] > 0.0 ? ldexp(1.0, ilogb(s_part[0])) : 1.0;
     __syncthreads();
   }
+}
+
+// term counts on the device (merged sums)
+__global__ void __launch_bounds__(kScaleThreads) k_pair_scale(const double2* __restrict__ ca,
+                                                              const int64_t* __restrict__ na_dev,
+                                                              const double2* __restrict__ cf,
+                                                              const int64_t* __restrict__ nf_dev, double* scale) {
+  const double2* c[2] = {ca, cf};
+  const int64_t n[2] = {*na_dev, *nf_dev};
+  pair_scale(c, n, scale);
+}
+
+// term counts from the host (the sums as given)
+__global__ void __launch_bounds__(kScaleThreads) k_pair_scale_n(const double2* __restrict__ ca, int64_t na,
+                                                                const double2* __restrict__ cf, int64_t nf,
+                                                                double* scale) {
+  const double2* c[2] = {ca, cf};
+  const int64_t n[2] = {na, nf};
+  pair_scale(c, n, scale);
+}
+
+// z[j] = s_a[j] / scale[0] + i s_f[j] / scale[1] (FP32, exact scaling)
+__global__ void k_pack_pair32(const float* __restrict__ sa, const float* __restrict__ sf,
+                              const double* __restrict__ scale, int64_t M, float2* __restrict__ z) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const float ia = (float)(1.0 / scale[0]), jf = (float)(1.0 / scale[1]);
+  z[j] = make_float2(sa[j] * ia, sf[j] * jf);
+}
+
+// Bins of a (WHICH = 0) and f (WHICH = 1) from the FP32 complex transform of
+// s_a / scale[0] + i s_f / scale[1], as in k_extract_pair.
+template <int WHICH>
+__global__ void k_extract_pair32(const int32_t* __restrict__ cand, int64_t n, LatticeDev L,
+                                 const float2* __restrict__ Zh, const double* __restrict__ scale, double2* val,
+                                 double* mag, unsigned long long* maxbits) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t b = residue_of(cand + i * L.d, L.d, L);
+  const int64_t nb = (L.M - b) % L.M;
+  const float2 x = Zh[b], y = Zh[nb];
+  const double sc = 0.5 / (double)L.M * scale[WHICH];
+  const double2 v = WHICH == 0 ? make_double2(((double)x.x + y.x) * sc, ((double)x.y - y.y) * sc)
+                               : make_double2(((double)x.y + y.y) * sc, ((double)y.x - x.x) * sc);
+  val[i] = v;
+  const double m = hypot(v.x, v.y);
+  mag[i] = m;
+  atomicMax(maxbits, (unsigned long long)__double_as_longlong(m));
 }
 
 // Two real sums a and f at once: Z = S_a + i S_f with S_a, S_f their
@@ -1293,7 +1367,37 @@ ss_status sft_recover_both(const ss_lattice* lat, const ss_trig* a, const ss_tri
       SS_LAUNCH_CHECK();
     }
   }
-  for (int k = 0; k < 2 && !P.has_dff; ++k) {
+  if (!P.has_dff && use_pair32(P)) {
+    SS_TRY(ensure_pair32(P, st));
+    SS_TRY(sample_into(P, L, a, P.samples.get(), st));
+    SS_TRY(sample_into(P, L, f, P.samples2.get(), st));
+    double* scale = P.scale32.get();
+    k_pair_scale_n<<<1, kScaleThreads, 0, st>>>(reinterpret_cast<const double2*>(a->coef), a->n_terms,
+                                                reinterpret_cast<const double2*>(f->coef), f->n_terms, scale);
+    float2* z = P.z32.get();
+    k_pack_pair32<<<nblk(P.M), 256, 0, st>>>(reinterpret_cast<const float*>(P.samples.get()), P.samples2.get(),
+                                             scale, P.M, z);
+    SS_LAUNCH_CHECK();
+    r = cufftSetStream(P.c2c, st);
+    if (r == CUFFT_SUCCESS)
+      r = cufftExecC2C(P.c2c, reinterpret_cast<cufftComplex*>(z), reinterpret_cast<cufftComplex*>(z), CUFFT_FORWARD);
+    if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cuFFT C2C exec failed: %d", (int)r);
+    for (int k = 0; k < 2; ++k) {
+      if (k == 0)
+        k_extract_pair32<0><<<nblk(n_cand), 256, 0, st>>>(cand, n_cand, L, z, scale, val.get(), mag.get(),
+                                                          maxbits.get());
+      else
+        k_extract_pair32<1><<<nblk(n_cand), 256, 0, st>>>(cand, n_cand, L, z, scale, val.get(), mag.get(),
+                                                          maxbits.get() + 1);
+      k_keep<<<nblk(n_cand), 256, 0, st>>>(mag.get(), n_cand, maxbits.get() + k, tau, flag.get());
+      SS_LAUNCH_CHECK();
+      SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), n_cand, total.get() + k, st));
+      k_compact<<<nblk(n_cand), 256, 0, st>>>(cand, val.get(), n_cand, L.d, flag.get(), pos.get(), fo[k],
+                                              reinterpret_cast<double2*>(vo[k]));
+      SS_LAUNCH_CHECK();
+    }
+  }
+  for (int k = 0; k < 2 && !P.has_dff && !use_pair32(P); ++k) {
     // the plan's sample and spectrum buffers serve both sums in stream order
     SS_TRY(sample_into(P, L, g[k], P.samples.get(), st));
     if (P.prec == SS_FP64)
