@@ -341,14 +341,17 @@ def apply_section(B, gp, flush, peaks, reps=10):
                 evs.append((a, b))
             torch.cuda.synchronize()
             ms = statistics.median([a.elapsed_time(b) for a, b in evs])
+            realc = bool(st.real_coefficients) if prec == "fp64" else False
             if prec == "fp32":
                 byts = 4 * st.nnz + st.size * (8 + 4 + 8)
             else:
-                byts = (4 + 16) * st.nnz + st.size * (16 + 8 + 16)
+                # index and coefficient per nonzero (8 B when the coefficients are real)
+                byts = (4 + (8 if realc else 16)) * st.nnz + st.size * (16 + 8 + 16)
             d = {"ms": ms, "nnz_per_s": st.nnz / (ms / 1e3), "algorithmic_bytes": byts,
                  "achieved_gbs": byts / (ms / 1e3) / 1e9, "hbm_frac": byts / (ms / 1e3) / 1e9 / hbm}
             if prec == "fp64":
-                d["fp64_gflops"] = 8.0 * st.nnz / (ms / 1e3) / 1e9
+                d["fp64_gflops"] = (4.0 if realc else 8.0) * st.nnz / (ms / 1e3) / 1e9
+                d["real_coefficients"] = realc
             res[prec] = d
         st.destroy()
         out[name] = res
@@ -787,17 +790,21 @@ def main():
     e2e_value = world * e2e_work / (sum(e2e_ms) / 1e3)
 
     # roofline of the dominant kernel: the persistent FP64 CG (FP64 ALU bound;
-    # algorithmic flops: 8 per processed nonzero and application, 30 per
-    # processed row and CG iteration - see the design doc).  With the Hermitian
+    # algorithmic flops: 8 per processed nonzero and application, 4 when the
+    # entry coefficients are real, 30 per processed row and CG iteration -
+    # see the design doc).  With the Hermitian
     # half system the CG processes the rows k >lex 0 and their nonzeros, half
     # of S and half of L's nonzeros (symmetric S; the zero row stores none).
     med = {k: statistics.median(v) for k, v in stage.items()}
     nnz, size, iters = r["nnz"], r["size"], r["iters"]
     applies = r["applies"]
     half = bool(r["stats"].get("half_system"))
+    realc = bool(r["stats"].get("real_coefficients"))
     nnz_p = nnz / 2 if half else nnz
     rows_p = (size - (1 if r["zero_index"] >= 0 else 0)) // 2 if half else size
-    solve_flops = 8.0 * nnz_p * applies + 30.0 * rows_p * iters
+    # real entry coefficients (a_hat real): 2 FP64 FMAs per nonzero, else 4
+    flops_nnz = 4.0 if realc else 8.0
+    solve_flops = flops_nnz * nnz_p * applies + 30.0 * rows_p * iters
     kms = med["solve_kernel"]
     clk = clocks.summary()
     sm_max = clk.get("sm_max_mhz") or 2070.0
@@ -807,6 +814,7 @@ def main():
                 "unit": "GFLOP/s (FP64)", "frac": achieved / peak64, "traffic": None,
                 "peak_source": "derived: 1 FP64 FMA/clk/SM (ncu FP64-pipe counters) x 152 SMs x 2 x sm_max_mhz",
                 "flops_per_launch": solve_flops, "kernel_ms": kms, "half_system": half,
+                "real_coefficients": realc, "flops_per_processed_nnz": flops_nnz,
                 "processed_nnz": nnz_p, "processed_rows": rows_p}
     launches_per_step = count_launches(lambda: step(prep))
     gpu_launches = launches_per_step * args.steps if launches_per_step is not None else None

@@ -85,6 +85,8 @@ typedef struct {
     double rel_residual;   /* ||f - L u||_2 / ||f||_2 in FP64 at exit */
     double kernel_ms;      /* duration of the persistent solver launch (CUDA events on the stream) */
     int32_t half_system;   /* 1 when the Hermitian half system was solved (see solve) */
+    int32_t real_coefficients;   /* 1 when a_hat was real and the operator's entry
+                                    coefficients real (two FP64 FMAs per nonzero; see stamp_build) */
 } ss_solve_stats;
 
 const char* ss_last_error(void);
@@ -233,6 +235,14 @@ ss_status stamp_build_adr(const ss_sparse* a_hat, const ss_sparse* b_hat, const 
 /* |S|, operator nonzeros #{(k,p): k in S\{0}, k-p in S\{0}}, the canonical
  * index of k = 0 (-1 if absent), and the number of levels (N + 1).  Host. */
 ss_status stamp_info(ss_stamp s, int64_t* size, int64_t* nnz, int64_t* zero_index, int32_t* n_levels);
+
+/* *real = 1 when the stamp's a_hat was taken as real: a even, every
+ * |Im a_hat_p| <= 1e-13 max |a_hat| (below an FP64 recovery's rounding), the
+ * imaginary parts dropped at build.  Every entry coefficient
+ * 2 pi^2 (|k|^2 + |l|^2 - |p|^2) a_hat_p is then real and the FP64 and
+ * double-float operators take two multiply-adds per nonzero instead of four.
+ * Never for an ADR stamp.  Host. */
+ss_status stamp_real_coefficients(ss_stamp s, int32_t* real);
 
 /* Frequencies (device int32 [|S|][d]) and levels (device int8 [|S|]) in
  * canonical order; either output may be NULL. */

@@ -49,12 +49,13 @@ class LatticeSpec(C.Structure):
 class SolveStats(C.Structure):
     _fields_ = [("status", C.c_int32), ("outer_iters", C.c_int32), ("inner_iters", C.c_int32),
                 ("applies", C.c_int32), ("rel_residual", C.c_double), ("kernel_ms", C.c_double),
-                ("half_system", C.c_int32)]
+                ("half_system", C.c_int32), ("real_coefficients", C.c_int32)]
 
     def as_dict(self):
         return {"status": STATUS.get(self.status, self.status), "outer_iters": self.outer_iters,
                 "inner_iters": self.inner_iters, "applies": self.applies, "rel_residual": self.rel_residual,
-                "kernel_ms": self.kernel_ms, "half_system": bool(self.half_system)}
+                "kernel_ms": self.kernel_ms, "half_system": bool(self.half_system),
+                "real_coefficients": bool(self.real_coefficients)}
 
 
 def _load():
@@ -80,6 +81,7 @@ def _load():
         "stamp_build": (i32, [P(Sparse), vp, i64, i32, P(vp), vp]),
         "stamp_build_adr": (i32, [P(Sparse), P(Sparse), P(Sparse), vp, i64, i32, P(vp), vp]),
         "stamp_info": (i32, [vp, P(i64), P(i64), P(i64), P(i32)]),
+        "stamp_real_coefficients": (i32, [vp, P(i32)]),
         "stamp_export": (i32, [vp, vp, vp, vp]),
         "stamp_lookup": (i32, [vp, vp, i64, vp, vp]),
         "stamp_scatter": (i32, [vp, P(Sparse), vp, P(i64), vp]),
@@ -304,6 +306,13 @@ class Stamp:
         lv = C.c_int32()
         _check(lib.stamp_info(self._h, C.byref(size), C.byref(nnz), C.byref(zero), C.byref(lv)))
         self.size, self.nnz, self.zero_index, self.n_levels = size.value, nnz.value, zero.value, lv.value
+
+    @property
+    def real_coefficients(self):
+        """a_hat taken as real (real entry coefficients, see stamp_real_coefficients)."""
+        r = C.c_int32()
+        _check(lib.stamp_real_coefficients(self.handle, C.byref(r)))
+        return bool(r.value)
 
     @property
     def handle(self):

@@ -127,6 +127,7 @@ OpView op_view(const ss_stamp_s* s) {
   op.ecoefdf = s->ecoefdf.get();
   op.colbits = colbits_of(s->jbits);
   op.colmask = colmask_of(s->jbits);
+  op.realc = s->a_real;
   return op;
 }
 

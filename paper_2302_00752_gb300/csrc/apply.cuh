@@ -36,6 +36,7 @@ struct OpView {
   uint32_t colmask;
   bool conj = false;       // half system: entry bit 31 set = the neighbour's value is conjugated
   uint32_t jmask = 0xffffffffu;   // step index = (entry >> colbits) & jmask
+  bool realc = false;      // every entry coefficient has imaginary part exactly 0 (real a_hat)
 };
 
 // Imaginary part of a gathered value, negated (the value conjugated) when the
@@ -52,11 +53,13 @@ __device__ __forceinline__ float conj_if(float y, bool conj, uint32_t ent) {
 }
 
 // Accumulate row `row` (lane of slice s) of L u in FP64 from the stored entry
-// coefficients (four FP64 FMAs per nonzero: GB300 issues one FP64 FMA per SM
-// clock, so the FP64 operator counts its FP64 instructions).
-template <bool CG = false>
-__device__ __forceinline__ double2 row_apply64(const OpView& op, int64_t s, int lane,
-                                               const double2* __restrict__ rec) {
+// coefficients: four FP64 FMAs per nonzero, two when the coefficients are real
+// (REAL: their imaginary parts are exactly 0, so the two dropped products add
+// exact zeros).  GB300 issues one FP64 FMA per SM clock, so the FP64 operator
+// counts its FP64 instructions.
+template <bool CG, bool REAL>
+__device__ __forceinline__ double2 row_apply64_t(const OpView& op, int64_t s, int lane,
+                                                 const double2* __restrict__ rec) {
   const int32_t w0 = __ldg(op.woff + s), w1 = __ldg(op.woff + s + 1);
   const int64_t base = (int64_t)w0 * kSlice + lane;
   const uint32_t* e = op.ent + base;
@@ -70,7 +73,8 @@ __device__ __forceinline__ double2 row_apply64(const OpView& op, int64_t s, int 
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       ee[q] = __ldg(e + (int64_t)(t + q) * kSlice);
-      c[q] = __ldg(cf + (int64_t)(t + q) * kSlice);
+      if constexpr (REAL) c[q].x = __ldg(&cf[(int64_t)(t + q) * kSlice].x);
+      else c[q] = __ldg(cf + (int64_t)(t + q) * kSlice);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -79,26 +83,44 @@ __device__ __forceinline__ double2 row_apply64(const OpView& op, int64_t s, int 
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      ar = fma(c[q].x, v[q].x, ar); ar = fma(-c[q].y, v[q].y, ar);
-      ai = fma(c[q].x, v[q].y, ai); ai = fma(c[q].y, v[q].x, ai);
+      if constexpr (REAL) {
+        ar = fma(c[q].x, v[q].x, ar);
+        ai = fma(c[q].x, v[q].y, ai);
+      } else {
+        ar = fma(c[q].x, v[q].x, ar); ar = fma(-c[q].y, v[q].y, ar);
+        ai = fma(c[q].x, v[q].y, ai); ai = fma(c[q].y, v[q].x, ai);
+      }
     }
   }
   for (; t < w; ++t) {
     const uint32_t ee = __ldg(e + (int64_t)t * kSlice);
-    const double2 c = __ldg(cf + (int64_t)t * kSlice);
     double2 v = ldv<CG>(rec + 2 * (int64_t)(ee & op.colmask));
     v.y = conj_if(v.y, op.conj, ee);
-    ar = fma(c.x, v.x, ar); ar = fma(-c.y, v.y, ar);
-    ai = fma(c.x, v.y, ai); ai = fma(c.y, v.x, ai);
+    if constexpr (REAL) {
+      const double c = __ldg(&cf[(int64_t)t * kSlice].x);
+      ar = fma(c, v.x, ar);
+      ai = fma(c, v.y, ai);
+    } else {
+      const double2 c = __ldg(cf + (int64_t)t * kSlice);
+      ar = fma(c.x, v.x, ar); ar = fma(-c.y, v.y, ar);
+      ai = fma(c.x, v.y, ai); ai = fma(c.y, v.x, ai);
+    }
   }
   return make_double2(ar, ai);
+}
+
+template <bool CG = false>
+__device__ __forceinline__ double2 row_apply64(const OpView& op, int64_t s, int lane,
+                                               const double2* __restrict__ rec) {
+  return op.realc ? row_apply64_t<CG, true>(op, s, lane, rec) : row_apply64_t<CG, false>(op, s, lane, rec);
 }
 
 // Same in double-float (DF64 mode): the FP64 entry coefficient and u_l as
 // unevaluated float pairs, four double-float multiply-adds per nonzero on the
 // FP32 pipe (about 2^-48 relative per operation).  rec: float4 per column.
-template <bool CG = false>
-__device__ __forceinline__ float4 row_applydf(const OpView& op, int64_t s, int lane, const float4* __restrict__ rec) {
+template <bool CG, bool REAL>
+__device__ __forceinline__ float4 row_applydf_t(const OpView& op, int64_t s, int lane,
+                                                const float4* __restrict__ rec) {
   const int32_t w0 = __ldg(op.woff + s), w1 = __ldg(op.woff + s + 1);
   const int64_t base = (int64_t)w0 * kSlice + lane;
   const uint32_t* e = op.ent + base;
@@ -112,7 +134,12 @@ __device__ __forceinline__ float4 row_applydf(const OpView& op, int64_t s, int l
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       ee[q] = __ldg(e + (int64_t)(t + q) * kSlice);
-      c[q] = __ldg(cf + (int64_t)(t + q) * kSlice);
+      if constexpr (REAL) {
+        const float2 h = __ldg(reinterpret_cast<const float2*>(cf + (int64_t)(t + q) * kSlice));
+        c[q] = make_float4(h.x, h.y, 0.f, 0.f);
+      } else {
+        c[q] = __ldg(cf + (int64_t)(t + q) * kSlice);
+      }
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -123,23 +150,38 @@ __device__ __forceinline__ float4 row_applydf(const OpView& op, int64_t s, int l
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       df_fma(ar, re_of(c[q]), re_of(v[q]));
-      df_fma(ar, df_neg(im_of(c[q])), im_of(v[q]));
       df_fma(ai, re_of(c[q]), im_of(v[q]));
-      df_fma(ai, im_of(c[q]), re_of(v[q]));
+      if constexpr (!REAL) {
+        df_fma(ar, df_neg(im_of(c[q])), im_of(v[q]));
+        df_fma(ai, im_of(c[q]), re_of(v[q]));
+      }
     }
   }
   for (; t < w; ++t) {
     const uint32_t ee = __ldg(e + (int64_t)t * kSlice);
-    const float4 c = __ldg(cf + (int64_t)t * kSlice);
     float4 v = ldv<CG>(rec + (ee & op.colmask));
     v.z = conj_if(v.z, op.conj, ee);
     v.w = conj_if(v.w, op.conj, ee);
+    float4 c;
+    if constexpr (REAL) {
+      const float2 h = __ldg(reinterpret_cast<const float2*>(cf + (int64_t)t * kSlice));
+      c = make_float4(h.x, h.y, 0.f, 0.f);
+    } else {
+      c = __ldg(cf + (int64_t)t * kSlice);
+    }
     df_fma(ar, re_of(c), re_of(v));
-    df_fma(ar, df_neg(im_of(c)), im_of(v));
     df_fma(ai, re_of(c), im_of(v));
-    df_fma(ai, im_of(c), re_of(v));
+    if constexpr (!REAL) {
+      df_fma(ar, df_neg(im_of(c)), im_of(v));
+      df_fma(ai, im_of(c), re_of(v));
+    }
   }
   return cdf(ar, ai);
+}
+
+template <bool CG = false>
+__device__ __forceinline__ float4 row_applydf(const OpView& op, int64_t s, int lane, const float4* __restrict__ rec) {
+  return op.realc ? row_applydf_t<CG, true>(op, s, lane, rec) : row_applydf_t<CG, false>(op, s, lane, rec);
 }
 
 // Same in FP32 (FP32 values, FP32 accumulation).  nk, the records' third

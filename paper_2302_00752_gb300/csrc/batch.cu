@@ -19,6 +19,7 @@ struct ss_batch_s {
   int64_t rows_total = 0, n_slices = 0, n_ent = 0;
   int jbits = 1;
   bool conj = false;                  // built from the instances' Hermitian half systems
+  bool realc = false;                 // every instance's a_hat real: real entry coefficients
   ss::DevBuf<int64_t> norm;
   ss::DevBuf<int32_t> woff, slice_inst, pn;
   ss::DevBuf<uint32_t> ent;
@@ -163,6 +164,7 @@ OpView batch_op(const ss_batch_s* b) {
   op.colmask = (uint32_t)((1ull << op.colbits) - 1);
   op.jmask = (1u << b->jbits) - 1u;
   op.conj = b->conj;
+  op.realc = b->realc;
   return op;
 }
 
@@ -260,9 +262,11 @@ static ss_status batch_create_impl(ss_batch_s* b, int32_t n, const ss_stamp* sta
   std::vector<SysIn> in(n);
   int64_t rows = 0, slices = 0, ent = 0, coefs = 0;
   int jb = 1;
+  b->realc = true;
   for (int i = 0; i < n; ++i) {
     const ss_stamp_s* s = stamps[i];
     if (!s) SS_FAIL(SS_ERR_INVALID, "batch_create: null stamp %d", i);
+    b->realc = b->realc && s->a_real;
     in[i] = half ? half_in(s) : full_in(s);
     rows += in[i].rows_pad;
     slices += in[i].n_slices;
@@ -460,7 +464,10 @@ ss_status run_half(ss_batch_s* b, const double* const* f, double* const* u, doub
   SS_TRY(read_stats(h->work, b->n_inst, stats, worst, st, h->work.ev[0], h->work.ev[1]));
   *used = *b->hflag_host == 0;
   if (*used && stats)
-    for (int i = 0; i < b->n_inst; ++i) stats[i].half_system = 1;
+    for (int i = 0; i < b->n_inst; ++i) {
+      stats[i].half_system = 1;
+      stats[i].real_coefficients = h->realc;
+    }
   return SS_OK;
 }
 
@@ -483,6 +490,8 @@ extern "C" ss_status batch_solve(ss_batch b, const double* const* f, double* con
   SS_TRY(set_pointers(b, f, u));
   SS_TRY(run_once(b, tol, max_iter, prec, use_graph != 0, st));
   SS_TRY(read_stats(b->work, b->n_inst, stats, &worst, st, b->work.ev[0], b->work.ev[1]));
+  if (stats)
+    for (int i = 0; i < b->n_inst; ++i) stats[i].real_coefficients = b->realc;
   return worst;
 }
 

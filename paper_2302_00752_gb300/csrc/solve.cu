@@ -1274,6 +1274,7 @@ ss_status read_stats(SolveWork& W, int n_inst, ss_solve_stats* stats, ss_status*
       stats[i].rel_residual = s.bb > 0 ? std::sqrt(s.rr / s.bb) : 0.0;
       stats[i].kernel_ms = kms;
       stats[i].half_system = 0;
+      stats[i].real_coefficients = 0;
     }
     if (*worst == SS_OK && s.status != SS_OK) {
       *worst = (ss_status)s.status;
@@ -1529,6 +1530,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
     hop.colmask = (1u << s->colbits_h) - 1u;
     hop.jmask = (1u << s->jbits) - 1u;
     hop.conj = true;
+    hop.realc = s->a_real;
     if (!H->work.ev[0]) {
       SS_CUDA(cudaEventCreate(&H->work.ev[0]));
       SS_CUDA(cudaEventCreate(&H->work.ev[1]));
@@ -1546,6 +1548,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
     C->hflag.settle();
     if (*C->hflag_host == 0) {
       one.half_system = 1;
+      one.real_coefficients = s->a_real;
       if (check_f0 && (C->f0_host->x != 0.0 || C->f0_host->y != 0.0)) {
         one.status = SS_ERR_INVALID;
         if (stats) *stats = one;
@@ -1566,6 +1569,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
   op.ecoefdf = s->ecoefdf.get();
   op.colbits = colbits_of(s->jbits);
   op.colmask = colmask_of(s->jbits);
+  op.realc = s->a_real;
   if (!C->work.ev[0]) {
     SS_CUDA(cudaEventCreate(&C->work.ev[0]));
     SS_CUDA(cudaEventCreate(&C->work.ev[1]));
@@ -1575,6 +1579,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
   ss_status worst;
   ss_solve_stats one{};
   SS_TRY(read_stats(C->work, 1, &one, &worst, st, C->work.ev[0], C->work.ev[1]));
+  one.real_coefficients = s->a_real;
   if (check_f0 && (C->f0_host->x != 0.0 || C->f0_host->y != 0.0)) {
     one.status = SS_ERR_INVALID;
     if (stats) *stats = one;
@@ -1741,6 +1746,7 @@ extern "C" ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_o
   P.op.ecoef = s->ecoef64.get();
   P.op.colbits = colbits_of(s->jbits);
   P.op.colmask = colmask_of(s->jbits);
+  P.op.realc = s->a_real;
   P.slice_inst = nullptr;
   P.norm = s->norm.get();
   P.ca64 = s->ca64.get();
@@ -1795,6 +1801,8 @@ extern "C" ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_o
     stats->applies = hs.applies;
     stats->rel_residual = rel;
     stats->kernel_ms = 0.0;
+    stats->half_system = 0;
+    stats->real_coefficients = s->a_real;
   }
   if (herr) SS_FAIL((ss_status)herr, "solve_noalloc: a device-side wait gave up (status %d)", herr);
   if (hs.status != SS_OK) SS_FAIL((ss_status)hs.status, "solve_noalloc: not converged (relative residual %.3e)", rel);

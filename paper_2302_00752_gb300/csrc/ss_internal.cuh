@@ -217,6 +217,7 @@ struct ss_stamp_s {
   // Hermitian half system (real data): compact rows k >lex 0 in canonical
   // order; a neighbour l < 0 is read as conj(u_{-l}) (entry bit 31).
   bool half_cand = false;             // F = -F and a_hat exactly Hermitian (set by the build)
+  bool a_real = false;                // every a_hat_p real: the entry coefficients are real
   bool half_ok = false;               // half system built for the current set
   int64_t n_plus = 0, rows_pad_h = 0, n_slices_h = 0;
   int colbits_h = 0;                  // half entries: col | j << colbits_h | conj << 31

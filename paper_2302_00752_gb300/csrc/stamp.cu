@@ -23,11 +23,24 @@
 namespace ss {
 namespace {
 
+// a_hat counts as real (a even) when no imaginary part exceeds this fraction
+// of max |a_hat|: below the rounding of an FP64 recovery (the FFT leaves
+// imaginary parts of order 1e-16 to 1e-14 of the largest coefficient on an
+// even a).  The imaginary parts are then dropped at build and every entry
+// coefficient is real.
+constexpr double kRealTol = 1e-13;
+
+__global__ void k_real_part(double2* av, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) av[j].y = 0.0;
+}
+
 struct PrepOut {
   int32_t maxabs_f, maxabs_a;
   int32_t dup_f, dup_a;
   int32_t bad_sym, zero_in_f, bad_herm, j0;
   int32_t f_sym, herm_exact;   // F = -F (F sorted); a_hat_{-p} == conj(a_hat_p) bit for bit
+  int32_t a_real;              // every |Im a_hat_p| <= kRealTol max |a_hat| (a even)
   double a0_re, a0_abs, off_l1, amax;
 };
 
@@ -79,11 +92,11 @@ constexpr int kPrepThreads = 512;
 __global__ void __launch_bounds__(kPrepThreads) k_prep(const int32_t* __restrict__ F, int64_t n_f,
                                                        const int32_t* __restrict__ A,
                                                        const double2* __restrict__ av, int s_a, int d, PrepOut* out) {
-  __shared__ int32_t s_maxf, s_maxa, s_zf, s_sym, s_herm, s_fasym, s_hinexact;
+  __shared__ int32_t s_maxf, s_maxa, s_zf, s_sym, s_herm, s_fasym, s_hinexact, s_aimag;
   __shared__ unsigned long long s_amax;
   __shared__ double s_hyp[4096];
   if (threadIdx.x == 0) {
-    s_maxf = 0; s_maxa = 0; s_zf = 0; s_sym = (s_a % 2 == 0); s_herm = 0; s_amax = 0; s_fasym = 0; s_hinexact = 0;
+    s_maxf = 0; s_maxa = 0; s_zf = 0; s_sym = (s_a % 2 == 0); s_herm = 0; s_amax = 0; s_fasym = 0; s_hinexact = 0; s_aimag = 0;
   }
   __syncthreads();
   int32_t mf = 0;
@@ -122,6 +135,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const int32_t* __restrict
     const int m = s_a - 1 - j;
     if (fabs(av[j].x - av[m].x) > 1e-12 * amax || fabs(av[j].y + av[m].y) > 1e-12 * amax) atomicExch(&s_herm, 1);
     if (!(av[j].x == av[m].x && av[j].y == -av[m].y)) atomicExch(&s_hinexact, 1);
+    if (fabs(av[j].y) > kRealTol * amax) atomicExch(&s_aimag, 1);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -141,6 +155,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const int32_t* __restrict
     out->amax = amax;
     out->f_sym = !s_fasym;
     out->herm_exact = !bad_sym && !s_hinexact;
+    out->a_real = !s_aimag;
   }
 }
 
@@ -915,6 +930,9 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   if (!(h.a0_re > 0)) SS_FAIL(SS_ERR_NOT_ELLIPTIC, "stamp_build: Re(a_hat_0) must be positive");
   S->a0 = h.a0_re;
   S->half_cand = !S->adr && h.f_sym && h.herm_exact;
+  // real a_hat: every entry coefficient 2 pi^2 (|k|^2 + |l|^2 - |p|^2) a_hat_p
+  // is real (the ADR entries carry the advection and reaction terms)
+  S->a_real = !S->adr && h.a_real;
   S->j0 = h.j0;
   S->maxabs_f = h.maxabs_f;
   S->maxabs_a = h.maxabs_a;
@@ -929,6 +947,11 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   int jb = 0;
   while ((1 << jb) < s_a) ++jb;
   S->jbits = std::max(jb, 1);
+
+  if (S->a_real) {
+    k_real_part<<<nblk(s_a), 256, 0, st>>>(avs.get(), s_a);
+    SS_LAUNCH_CHECK();
+  }
 
   // steps and coefficients in canonical order
   SS_TRY(S->afreq.alloc((size_t)s_a * d, st));
@@ -1173,6 +1196,12 @@ extern "C" void stamp_destroy(ss_stamp s) {
   cudaDeviceSynchronize();
   drop_solve_ctx(s);
   delete s;
+}
+
+extern "C" ss_status stamp_real_coefficients(ss_stamp s, int32_t* real) {
+  if (!s || !real) SS_FAIL(SS_ERR_INVALID, "stamp_real_coefficients: null argument");
+  *real = s->a_real ? 1 : 0;
+  return SS_OK;
 }
 
 extern "C" ss_status stamp_info(ss_stamp s, int64_t* size, int64_t* nnz, int64_t* zero_index, int32_t* n_levels) {
