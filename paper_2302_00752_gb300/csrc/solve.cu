@@ -240,6 +240,28 @@ __device__ void run_phase(const SolveParams& P, Smem& sm, unsigned qmask, Scal s
   }
 }
 
+// Row-wise phase of one instance (no neighbour reads, no partial sums): with
+// P.rows_slices > 0 the slices are split evenly over the blocks, so that the
+// work follows the rows rather than the entries the apply chunks are balanced
+// by; block 0 does the owner's bookkeeping.  Otherwise the chunks of run_phase.
+template <class Scal, class Row>
+__device__ void run_rows(const SolveParams& P, Smem& sm, Scal scal, Row row) {
+  if (P.rows_slices <= 0) {
+    run_phase(P, sm, 0u, scal, row);
+    return;
+  }
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t s0 = P.rows_slices * blockIdx.x / gridDim.x, s1 = P.rows_slices * (blockIdx.x + 1) / gridDim.x;
+  const Chunk ch{s0, s1, 0, 0};
+  if (warp == 0) scal(0, ch, 0, 0, blockIdx.x == 0, lane);
+  __syncthreads();
+  for (int64_t s = s0 + warp; s < s1; s += nw) {
+    double vals[kNQ] = {};
+    row(s * kSlice + lane, s, lane, 0, 0, vals);
+  }
+  __syncthreads();
+}
+
 // Power-of-two scale of an inner (FP32) solve: the residual handed to it has
 // RMS entry near 1, so that the FP32 inner products r.D^-1 r and p.Lp stay far
 // from FP32 underflow however small the outer residual and however large the
@@ -351,7 +373,7 @@ __device__ void solve_fp64(const SolveParams& P, Smem& sm) {
   if (!grid_sync(P)) return;
   for (int it = 0;; ++it) {
     const int cur = it & 1, nxt = cur ^ 1;
-    run_phase(P, sm, 0u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
+    run_rows(P, sm, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
       double t[kNQ];
       inst_sums(P, i, t);
       if (lane == 0) {
@@ -483,7 +505,7 @@ __device__ void solve_df64(const SolveParams& P, Smem& sm) {
   if (!grid_sync(P)) return;
   for (int it = 0;; ++it) {
     const int cur = it & 1, nxt = cur ^ 1;
-    run_phase(P, sm, 0u, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
+    run_rows(P, sm, [&](int, const Chunk&, int k, int i, bool owner, int lane) {
       double t[kNQ];
       inst_sums(P, i, t);
       if (lane == 0) {
@@ -1013,13 +1035,14 @@ inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t
 // ---------------------------------------------------------------- host side
 
 ss_status plan_chunks(SolvePlan& plan, const std::vector<int32_t>& woff, const std::vector<int32_t>& slice_inst,
-                      int target_chunks) {
+                      int target_chunks, double slice_overhead) {
   const int64_t n_slices = (int64_t)woff.size() - 1;
   const int n_inst = (int)plan.inst.size();
   plan.chunk.clear();
   if (n_slices <= 0) SS_FAIL(SS_ERR_INVALID, "solve: empty operator");
   // weight of a slice: its entries (gathers) plus the vector work of 32 rows
-  auto weight = [&](int64_t s) { return (double)(woff[s + 1] - woff[s]) + 6.0; };
+  // (small when the row-wise phases split the rows on their own)
+  auto weight = [&](int64_t s) { return (double)(woff[s + 1] - woff[s]) + slice_overhead; };
   double total = 0;
   for (int64_t s = 0; s < n_slices; ++s) total += weight(s);
   const double target = total / std::max(1, target_chunks);
@@ -1227,6 +1250,7 @@ ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, co
   P.max_inner = std::max(1, std::min(max_iter, 200));
   P.max_outer = std::max(1, max_iter);
   P.spin_limit = 2000000000ll;   // 2 s
+  P.rows_slices = plan.row_split && P.n_inst == 1 && !slice_inst ? plan.chunk.back().s1 : 0;
   SS_CUDA(cudaMemsetAsync(W.bar.get(), 0, 2 * sizeof(unsigned), st));
   SS_CUDA(cudaMemsetAsync(W.counters.get(), 0, 4 * sizeof(int), st));
   SS_CUDA(cudaMemsetAsync(W.err.get(), 0, sizeof(int), st));
@@ -1330,7 +1354,10 @@ static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream
   if (C.blocks_per_sm > 0) grid = std::min(grid, C.blocks_per_sm * sm_count());
   const int by_size = (int)std::max<int64_t>(1, s->n_slices / 8);   // at least 8 slices per chunk
   const int target = std::min<int64_t>((int64_t)grid * C.chunks_per_block, by_size);
-  SS_TRY(plan_chunks(C.plan, woff, {}, target));
+  // FP64 and DF64 CG: the vector updates run over an even split of the rows,
+  // the apply phases over chunks balanced by entries
+  C.plan.row_split = mode == 0 || mode == 3;
+  SS_TRY(plan_chunks(C.plan, woff, {}, target, C.plan.row_split ? 1.0 : 6.0));
   C.plan.grid = std::min<int>(grid, (int)C.plan.chunk.size());
   SS_TRY(work_alloc(C.work, s->rows_pad + 1, s->norm.get(), nullptr, s->wide, st));
   if (mode == 2) SS_TRY(work_alloc_bicgstab(C.work, st));
@@ -1361,7 +1388,8 @@ static ss_status stamp_plan_half(ss_stamp_s* s, ss_solve_ctx& H, int mode, cudaS
   if (H.blocks_per_sm > 0) grid = std::min(grid, H.blocks_per_sm * sm_count());
   const int by_size = (int)std::max<int64_t>(1, s->n_slices_h / 8);
   const int target = std::min<int64_t>((int64_t)grid * H.chunks_per_block, by_size);
-  SS_TRY(plan_chunks(H.plan, s->woff_h_host, {}, target));
+  H.plan.row_split = mode == 0 || mode == 3;
+  SS_TRY(plan_chunks(H.plan, s->woff_h_host, {}, target, H.plan.row_split ? 1.0 : 6.0));
   H.plan.grid = std::min<int>(grid, (int)H.plan.chunk.size());
   SS_TRY(work_alloc(H.work, s->rows_pad_h + 1, s->norm_h.get(), nullptr, s->wide, st));
   if (mode == 3) {

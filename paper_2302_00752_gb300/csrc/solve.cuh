@@ -72,6 +72,7 @@ struct SolveParams {
   double tol, inner_tol;
   int max_iter, max_inner, max_outer;
   long long spin_limit;
+  int64_t rows_slices;   // > 0: row-wise phases split slices [0, rows_slices) evenly over the blocks
 };
 
 // Host-side plan of the static work split.
@@ -80,6 +81,7 @@ struct SolvePlan {
   std::vector<Chunk> chunk;
   int64_t n_parts = 0;
   int grid = 0, block = 256;
+  bool row_split = false;   // single instance: the row-wise CG phases split the slices evenly over the blocks
 };
 
 // Device workspace of one solve context (single stamp or batch).
@@ -127,6 +129,6 @@ ss_status read_stats(SolveWork& W, int n_inst, ss_solve_stats* stats, ss_status*
                      cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 
 ss_status plan_chunks(SolvePlan& plan, const std::vector<int32_t>& woff_host, const std::vector<int32_t>& slice_inst_host,
-                      int target_chunks);
+                      int target_chunks, double slice_overhead = 6.0);
 
 }  // namespace ss
