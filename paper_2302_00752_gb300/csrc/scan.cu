@@ -66,6 +66,30 @@ __global__ void k_add_tile_offsets(int32_t* out, int64_t n, const int32_t* __res
   if (i < n) out[i] += tile_off[i / kTile];
 }
 
+// One block per tile t: adds the sum of the totals of tiles 0..t-1 (summed by
+// the block itself, O(t) reads) to the tile's outputs; the last tile also
+// writes the grand total.  Replaces a scan of the tile totals plus an offset
+// pass when the tiles are few.
+constexpr int64_t kPrefixTiles = 16384;
+__global__ void __launch_bounds__(kScanThreads) k_add_tile_prefix(int32_t* out, int64_t n,
+                                                                  const int32_t* __restrict__ tile_sum,
+                                                                  int64_t tiles, int64_t* d_total) {
+  __shared__ int32_t warp_sum[kScanThreads / 32];
+  const int64_t t = blockIdx.x;
+  int32_t acc = 0;
+  for (int64_t j = threadIdx.x; j < t; j += kScanThreads) acc += tile_sum[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  int32_t off = 0;
+#pragma unroll
+  for (int w = 0; w < kScanThreads / 32; ++w) off += warp_sum[w];
+  const int64_t base = t * kTile;
+  for (int i = threadIdx.x; i < kTile && base + i < n; i += kScanThreads) out[base + i] += off;
+  if (t == tiles - 1 && threadIdx.x == 0 && d_total) *d_total = (int64_t)off + tile_sum[t];
+}
+
 }  // namespace
 
 ss_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int64_t* d_total, cudaStream_t st) {
@@ -76,6 +100,14 @@ ss_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int64_t
   const int64_t tiles = (n + kTile - 1) / kTile;
   if (tiles == 1) {
     k_scan_tiles<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr, d_total);
+    SS_LAUNCH_CHECK();
+    return SS_OK;
+  }
+  if (tiles <= kPrefixTiles) {
+    DevBuf<int32_t> tsum;
+    SS_TRY(tsum.alloc_tmp(tiles, st));
+    k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, out, n, tsum.get(), nullptr);
+    k_add_tile_prefix<<<(unsigned)tiles, kScanThreads, 0, st>>>(out, n, tsum.get(), tiles, d_total);
     SS_LAUNCH_CHECK();
     return SS_OK;
   }
