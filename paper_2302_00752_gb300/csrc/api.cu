@@ -115,12 +115,55 @@ namespace {
 struct PinnedBlock {
   void* p = nullptr;
   size_t n = 0;
+  void* dev = nullptr;   // the block's device-side address (mapped)
   ~PinnedBlock() {
     if (p) cudaFreeHost(p);
   }
 };
 
 thread_local PinnedBlock g_pinned;
+
+constexpr int kGatherParts = 8;
+constexpr size_t kGatherBytes = 4096;
+
+struct GatherArgs {
+  const unsigned char* src[kGatherParts];
+  uint32_t bytes[kGatherParts];
+  uint32_t off[kGatherParts];
+  int n;
+};
+
+struct FillArgs {
+  unsigned char* dst[kGatherParts];
+  size_t bytes[kGatherParts];
+  unsigned char value[kGatherParts];
+  int n;
+};
+
+// Each region: 16-byte words over its 16-byte aligned body, bytes at the ends.
+__global__ void k_fill_small(FillArgs a) {
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (size_t)gridDim.x * blockDim.x;
+  for (int k = 0; k < a.n; ++k) {
+    unsigned char* p = a.dst[k];
+    const size_t nb = a.bytes[k];
+    const unsigned char v = a.value[k];
+    const size_t mis = (size_t)((16 - ((uintptr_t)p & 15)) & 15);
+    const size_t head = mis < nb ? mis : nb;
+    const size_t words = (nb - head) / 16;
+    const size_t tail0 = head + words * 16;
+    const uint32_t w = 0x01010101u * v;
+    const uint4 q = make_uint4(w, w, w, w);
+    for (size_t i = tid; i < head; i += nth) p[i] = v;
+    for (size_t i = tid; i < words; i += nth) reinterpret_cast<uint4*>(p + head)[i] = q;
+    for (size_t i = tail0 + tid; i < nb; i += nth) p[i] = v;
+  }
+}
+
+// Small read-backs: the items copied byte by byte into the mapped pinned block.
+__global__ void k_gather_small(GatherArgs a, unsigned char* dst) {
+  for (int k = 0; k < a.n; ++k)
+    for (uint32_t i = threadIdx.x; i < a.bytes[k]; i += blockDim.x) dst[a.off[k] + i] = a.src[k][i];
+}
 
 struct UploadBlock {
   void* p = nullptr;
@@ -173,16 +216,36 @@ ss_status read_back(cudaStream_t st, std::initializer_list<HostRead> parts) {
       cudaFreeHost(g_pinned.p);
       g_pinned.p = nullptr;
       g_pinned.n = 0;
+      g_pinned.dev = nullptr;
     }
     const size_t n = std::max<size_t>(total, 64 * 1024);
-    SS_CUDA(cudaMallocHost(&g_pinned.p, n));
+    SS_CUDA(cudaHostAlloc(&g_pinned.p, n, cudaHostAllocMapped));
     g_pinned.n = n;
+    if (cudaHostGetDevicePointer(&g_pinned.dev, g_pinned.p, 0) != cudaSuccess) {
+      cudaGetLastError();
+      g_pinned.dev = nullptr;
+    }
   }
   char* base = static_cast<char*>(g_pinned.p);
   size_t off = 0;
-  for (const HostRead& r : parts) {
-    if (r.bytes) SS_CUDA(cudaMemcpyAsync(base + off, r.src, r.bytes, cudaMemcpyDeviceToHost, st));
-    off += (r.bytes + 15) / 16 * 16;
+  if (parts.size() >= 2 && parts.size() <= (size_t)kGatherParts && total <= kGatherBytes && g_pinned.dev) {
+    // several small items: one kernel writes them into the mapped block
+    // instead of one copy call each
+    GatherArgs a{};
+    for (const HostRead& r : parts) {
+      a.src[a.n] = static_cast<const unsigned char*>(r.src);
+      a.bytes[a.n] = (uint32_t)r.bytes;
+      a.off[a.n] = (uint32_t)off;
+      ++a.n;
+      off += (r.bytes + 15) / 16 * 16;
+    }
+    k_gather_small<<<1, 256, 0, st>>>(a, static_cast<unsigned char*>(g_pinned.dev));
+    SS_LAUNCH_CHECK();
+  } else {
+    for (const HostRead& r : parts) {
+      if (r.bytes) SS_CUDA(cudaMemcpyAsync(base + off, r.src, r.bytes, cudaMemcpyDeviceToHost, st));
+      off += (r.bytes + 15) / 16 * 16;
+    }
   }
   SS_CUDA(cudaStreamSynchronize(st));
   off = 0;
@@ -190,6 +253,25 @@ ss_status read_back(cudaStream_t st, std::initializer_list<HostRead> parts) {
     if (r.bytes) std::memcpy(r.dst, base + off, r.bytes);
     off += (r.bytes + 15) / 16 * 16;
   }
+  return SS_OK;
+}
+
+ss_status fill_small(cudaStream_t st, std::initializer_list<FillPart> parts) {
+  if (parts.size() > (size_t)kGatherParts) SS_FAIL(SS_ERR_INVALID, "fill_small: more than %d regions", kGatherParts);
+  FillArgs a{};
+  size_t total = 0;
+  for (const FillPart& f : parts) {
+    if (!f.bytes) continue;
+    a.dst[a.n] = static_cast<unsigned char*>(f.dst);
+    a.bytes[a.n] = f.bytes;
+    a.value[a.n] = f.value;
+    ++a.n;
+    total += f.bytes;
+  }
+  if (!a.n) return SS_OK;
+  const size_t blocks = std::min<size_t>((total / 16 + 255) / 256 + 1, 4 * (size_t)sm_count());
+  k_fill_small<<<(unsigned)blocks, 256, 0, st>>>(a);
+  SS_LAUNCH_CHECK();
   return SS_OK;
 }
 

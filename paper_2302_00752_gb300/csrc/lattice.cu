@@ -341,8 +341,7 @@ ss_status residues(const int32_t* freq, int64_t n, const LatticeDev& L, int64_t*
 ss_status check_reconstructing_async(const int32_t* freq, int64_t n, const LatticeDev& L, const int64_t* res,
                                      bool need_symmetric, unsigned long long* table, uint64_t cap, int32_t* flags,
                                      cudaStream_t st) {
-  SS_CUDA(cudaMemsetAsync(table, 0, cap * sizeof(unsigned long long), st));
-  SS_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int32_t), st));
+  SS_TRY(fill_small(st, {{table, cap * sizeof(unsigned long long), 0}, {flags, 4 * sizeof(int32_t), 0}}));
   if (n == 0) return SS_OK;
   k_check_insert<<<nblk(n), 256, 0, st>>>(freq, res, n, L.d, table, cap - 1, flags);
   if (need_symmetric) k_check_symmetric<<<nblk(n), 256, 0, st>>>(freq, res, n, L.d, L.M, table, cap - 1, flags);
@@ -368,8 +367,7 @@ ss_status check_reconstructing(const int32_t* freq, int64_t n, const LatticeDev&
   DevBuf<int32_t> flags;
   SS_TRY(table.alloc_tmp(cap, st));
   SS_TRY(flags.alloc_tmp(4, st));
-  SS_CUDA(cudaMemsetAsync(table.get(), 0, cap * sizeof(unsigned long long), st));
-  SS_CUDA(cudaMemsetAsync(flags.get(), 0, 4 * sizeof(int32_t), st));
+  SS_TRY(fill_small(st, {{table.get(), cap * sizeof(unsigned long long), 0}, {flags.get(), 4 * sizeof(int32_t), 0}}));
   k_check_insert<<<nblk(n), 256, 0, st>>>(freq, res, n, L.d, table.get(), cap - 1, flags.get());
   if (need_symmetric) k_check_symmetric<<<nblk(n), 256, 0, st>>>(freq, res, n, L.d, L.M, table.get(), cap - 1, flags.get());
   SS_LAUNCH_CHECK();
@@ -532,8 +530,7 @@ extern "C" ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int6
       hc[(size_t)j * n_cand + c] = 1 + r % (M - 1);
     }
   SS_TRY(upload(st, {{cand.get(), hc.data(), hc.size() * sizeof(int64_t)}}));
-  SS_CUDA(cudaMemsetAsync(rho.get(), 0, n * sizeof(int64_t), st));
-  SS_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), st));
+  SS_TRY(fill_small(st, {{rho.get(), n * sizeof(int64_t), 0}, {err.get(), sizeof(int32_t), 0}}));
   // one cooperative launch for all coordinates when the per-block tables fit
   // in shared memory and every candidate's block can be resident at once
   const size_t all_smem = 2 * (size_t)n * sizeof(int64_t) + (size_t)hash_cap * sizeof(int32_t);
@@ -551,8 +548,7 @@ extern "C" ss_status lattice_cbc(const int32_t* freq, int64_t n, int32_t d, int6
     SS_TRY(fails.alloc_tmp((size_t)d * n_cand, st));
     SS_TRY(arrive.alloc_tmp(d, st));
     SS_TRY(err2.alloc_tmp(2, st));
-    SS_CUDA(cudaMemsetAsync(arrive.get(), 0, d * sizeof(unsigned), st));
-    SS_CUDA(cudaMemsetAsync(err2.get(), 0, 2 * sizeof(int32_t), st));
+    SS_TRY(fill_small(st, {{arrive.get(), d * sizeof(unsigned), 0}, {err2.get(), 2 * sizeof(int32_t), 0}}));
     const int32_t* fa = freq;
     int64_t na = n;
     int da = d;

@@ -1251,8 +1251,7 @@ ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, co
   P.max_outer = std::max(1, max_iter);
   P.spin_limit = 2000000000ll;   // 2 s
   P.rows_slices = plan.row_split && P.n_inst == 1 && !slice_inst ? plan.chunk.back().s1 : 0;
-  SS_CUDA(cudaMemsetAsync(W.bar.get(), 0, 2 * sizeof(unsigned), st));
-  SS_CUDA(cudaMemsetAsync(W.counters.get(), 0, 4 * sizeof(int), st));
+  SS_TRY(fill_small(st, {{W.bar.get(), 2 * sizeof(unsigned), 0}, {W.counters.get(), 4 * sizeof(int), 0}}));
   SS_CUDA(cudaMemsetAsync(W.err.get(), 0, sizeof(int), st));
   SS_CUDA(cudaMemsetAsync(W.state.get(), 0, plan.inst.size() * sizeof(InstState), st));
   // cooperative launch: all blocks co-resident (required by the grid barrier);

@@ -63,6 +63,15 @@ struct HostWrite {
 };
 ss_status upload(cudaStream_t st, std::initializer_list<HostWrite> parts);
 
+// Several device regions set to a byte value each by one kernel on `st`
+// (at most 8 regions; in place of one memset call per region).
+struct FillPart {
+  void* dst;
+  size_t bytes;
+  unsigned char value;
+};
+ss_status fill_small(cudaStream_t st, std::initializer_list<FillPart> parts);
+
 // ----------------------------------------------------------- device memory
 
 // Keeps freed device memory in the default stream-ordered pool (set once per

@@ -751,10 +751,10 @@ static ss_status build_half(ss_stamp_s* S, cudaStream_t st) {
   const int64_t cap_h = std::min<int64_t>(S->n_slices_h * (int64_t)max_w * kSlice, 2 * S->n_ent) + 1;
   SS_TRY(S->ent_h.alloc(cap_h, st));
   SS_TRY(S->ecoef_h.alloc(cap_h, st));
-  SS_CUDA(cudaMemsetAsync(S->norm_h.get(), 0, (S->rows_pad_h + 1) * sizeof(int64_t), st));
-  SS_CUDA(cudaMemsetAsync(S->plus_rows.get(), 0, S->rows_pad_h * sizeof(int32_t), st));
-  SS_CUDA(cudaMemsetAsync(slice_w.get(), 0, (S->n_slices_h + 1) * sizeof(int32_t), st));
-  SS_CUDA(cudaMemsetAsync(S->err_dev.get() + 3, 0, sizeof(int32_t), st));
+  SS_TRY(fill_small(st, {{S->norm_h.get(), (S->rows_pad_h + 1) * sizeof(int64_t), 0},
+                         {S->plus_rows.get(), S->rows_pad_h * sizeof(int32_t), 0},
+                         {slice_w.get(), (S->n_slices_h + 1) * sizeof(int32_t), 0},
+                         {S->err_dev.get() + 3, sizeof(int32_t), 0}}));
   SS_DISPATCH_WT(S->key.WT, (k_half_index<WT><<<nblk(S->size), 256, 0, st>>>(
                                 P, S->keys.get(), S->size, S->table.get(), (uint64_t)S->cap - 1, S->mirror.get(),
                                 plus.get(), S->err_dev.get() + 3)));
@@ -790,7 +790,6 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
     SS_FAIL(SS_ERR_KEY_RANGE, "stamp: |S| = %lld too large for %d-bit columns", (long long)S->size,
             colbits_of(S->jbits));
   SS_TRY(grow_keys(S, S->rows_pad + 1, st));   // norm padded to rows_pad + 1
-  SS_CUDA(cudaMemsetAsync(S->norm.get() + S->size, 0, (S->rows_pad + 1 - S->size) * sizeof(int64_t), st));
   DevBuf<int32_t> nbr, slice_w;
   DevBuf<unsigned long long> d_nnz;
   DevBuf<int64_t> d_total;
@@ -798,8 +797,9 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   SS_TRY(slice_w.alloc_tmp(S->n_slices + 1, st));
   SS_TRY(d_nnz.alloc_tmp(1, st));
   SS_TRY(d_total.alloc_tmp(1, st));
-  SS_CUDA(cudaMemsetAsync(d_nnz.get(), 0, sizeof(unsigned long long), st));
-  SS_CUDA(cudaMemsetAsync(slice_w.get(), 0, (S->n_slices + 1) * sizeof(int32_t), st));
+  SS_TRY(fill_small(st, {{S->norm.get() + S->size, (S->rows_pad + 1 - S->size) * sizeof(int64_t), 0},
+                         {d_nnz.get(), sizeof(unsigned long long), 0},
+                         {slice_w.get(), (S->n_slices + 1) * sizeof(int32_t), 0}}));
   SS_DISPATCH_WT(S->key.WT, (k_neighbors<WT><<<nblk(S->size * s_a), 256, 0, st>>>(
                                 P, S->keys.get(), S->size, s_a, S->stepkey.get(), S->table.get(),
                                 (uint64_t)S->cap - 1, S->zidx_dev.get(), S->adr, nbr.get())));
@@ -891,29 +891,28 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   S->N = N;
   S->s_a = s_a;
 
-  DevBuf<int32_t> Fs, As, rank;
+  DevBuf<int32_t> Fs, As, rank, rank_a;
   DevBuf<double2> avs;
   DevBuf<PrepOut> prep;
   SS_TRY(Fs.alloc_tmp(n_f * d, st));
   SS_TRY(As.alloc_tmp((size_t)s_a * d, st));
   SS_TRY(avs.alloc_tmp(s_a, st));
-  SS_TRY(rank.alloc_tmp(std::max<int64_t>(n_f, s_a), st));
+  SS_TRY(rank.alloc_tmp(n_f, st));
+  SS_TRY(rank_a.alloc_tmp(s_a, st));
   SS_TRY(prep.alloc_tmp(1, st));
   SS_TRY(S->err_dev.alloc(4, st));
   SS_TRY(S->zidx_dev.alloc(1, st));
   int32_t* err = S->err_dev.get();
-  SS_CUDA(cudaMemsetAsync(err, 0, 4 * sizeof(int32_t), st));
-  SS_CUDA(cudaMemsetAsync(S->zidx_dev.get(), 0xff, sizeof(int64_t), st));
+  SS_TRY(fill_small(st, {{err, 4 * sizeof(int32_t), 0}, {S->zidx_dev.get(), sizeof(int64_t), 0xff},
+                         {rank.get(), n_f * sizeof(int32_t), 0}, {rank_a.get(), s_a * sizeof(int32_t), 0}}));
 
   // signed lexicographic order of F and supp a_hat
   const int64_t ncf = (n_f + kRankChunk - 1) / kRankChunk, nca = (s_a + kRankChunk - 1) / kRankChunk;
-  SS_CUDA(cudaMemsetAsync(rank.get(), 0, std::max<int64_t>(n_f, s_a) * sizeof(int32_t), st));
   k_lex_rank<<<nblk(n_f * ncf), 256, 0, st>>>(f_freq, n_f, d, rank.get(), err + 1);
   k_scatter_rows<<<nblk(n_f), 256, 0, st>>>(f_freq, nullptr, n_f, d, rank.get(), Fs.get(), nullptr);
-  SS_CUDA(cudaMemsetAsync(rank.get(), 0, std::max<int64_t>(n_f, s_a) * sizeof(int32_t), st));
-  k_lex_rank<<<nblk(s_a * nca), 256, 0, st>>>(a_hat->freq, s_a, d, rank.get(), err + 2);
+  k_lex_rank<<<nblk(s_a * nca), 256, 0, st>>>(a_hat->freq, s_a, d, rank_a.get(), err + 2);
   k_scatter_rows<<<nblk(s_a), 256, 0, st>>>(a_hat->freq, reinterpret_cast<const double2*>(a_hat->val), s_a, d,
-                                            rank.get(), As.get(), avs.get());
+                                            rank_a.get(), As.get(), avs.get());
   k_prep<<<1, kPrepThreads, 0, st>>>(Fs.get(), n_f, As.get(), avs.get(), s_a, d, prep.get());
   SS_LAUNCH_CHECK();
   PrepOut h{};
