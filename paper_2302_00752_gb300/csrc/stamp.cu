@@ -52,19 +52,21 @@ __device__ int lexcmp(const int32_t* a, const int32_t* b, int d) {
 }
 
 // Stable lexicographic rank of every row (rank must start at zero); flags
-// duplicates.  Thread (i, c) compares row i with rows [64c, 64c + 64); the
-// threads of a warp share c, so the rows of the chunk are broadcast loads.
-constexpr int kRankChunk = 64;
+// duplicates.  Thread (i, c) compares row i with rows [chunk c, chunk (c + 1));
+// the threads of a warp share c, so the rows of the chunk are broadcast loads.
+// Short chunks for small sets (more threads, shorter dependent chains of
+// loads), long ones for large sets (fewer atomics).
+inline int rank_chunk(int64_t n) { return n <= 8192 ? 16 : 64; }
 
-__global__ void k_lex_rank(const int32_t* __restrict__ f, int64_t n, int d, int32_t* rank, int32_t* dup) {
-  const int64_t nc = (n + kRankChunk - 1) / kRankChunk;
+__global__ void k_lex_rank(const int32_t* __restrict__ f, int64_t n, int d, int32_t* rank, int32_t* dup, int chunk) {
+  const int64_t nc = (n + chunk - 1) / chunk;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * nc) return;
   const int64_t c = t / n, i = t - c * n;
-  const int64_t j1 = min(n, (c + 1) * kRankChunk);
+  const int64_t j1 = min(n, (c + 1) * chunk);
   int32_t r = 0;
   bool du = false;
-  for (int64_t j = c * kRankChunk; j < j1; ++j) {
+  for (int64_t j = c * chunk; j < j1; ++j) {
     const int cmp = lexcmp(f + j * d, f + i * d, d);
     if (cmp < 0 || (cmp == 0 && j < i)) ++r;
     if (cmp == 0 && j != i) du = true;
@@ -907,10 +909,11 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
                          {rank.get(), n_f * sizeof(int32_t), 0}, {rank_a.get(), s_a * sizeof(int32_t), 0}}));
 
   // signed lexicographic order of F and supp a_hat
-  const int64_t ncf = (n_f + kRankChunk - 1) / kRankChunk, nca = (s_a + kRankChunk - 1) / kRankChunk;
-  k_lex_rank<<<nblk(n_f * ncf), 256, 0, st>>>(f_freq, n_f, d, rank.get(), err + 1);
+  const int chf = rank_chunk(n_f), cha = rank_chunk(s_a);
+  const int64_t ncf = (n_f + chf - 1) / chf, nca = (s_a + cha - 1) / cha;
+  k_lex_rank<<<nblk(n_f * ncf), 256, 0, st>>>(f_freq, n_f, d, rank.get(), err + 1, chf);
   k_scatter_rows<<<nblk(n_f), 256, 0, st>>>(f_freq, nullptr, n_f, d, rank.get(), Fs.get(), nullptr);
-  k_lex_rank<<<nblk(s_a * nca), 256, 0, st>>>(a_hat->freq, s_a, d, rank_a.get(), err + 2);
+  k_lex_rank<<<nblk(s_a * nca), 256, 0, st>>>(a_hat->freq, s_a, d, rank_a.get(), err + 2, cha);
   k_scatter_rows<<<nblk(s_a), 256, 0, st>>>(a_hat->freq, reinterpret_cast<const double2*>(a_hat->val), s_a, d,
                                             rank_a.get(), As.get(), avs.get());
   k_prep<<<1, kPrepThreads, 0, st>>>(Fs.get(), n_f, As.get(), avs.get(), s_a, d, prep.get());
