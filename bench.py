@@ -227,8 +227,8 @@ def load_peaks():
 
 def fp64_peak_gflops(sm_mhz):
     """FP64 ALU peak: one FP64 FMA per SM clock (GB300; the per-SM rate comes
-    from the ncu FP64-pipe counters of k_sample<double>) x 152
-    SMs x 2 flops x clock."""
+    from the ncu FP64-pipe counters of a pure-FP64 sampling kernel,
+    k_sample<double>) x 152 SMs x 2 flops x clock."""
     return 152 * 2 * sm_mhz * 1e6 / 1e9
 
 
@@ -790,11 +790,12 @@ def main():
     e2e_value = world * e2e_work / (sum(e2e_ms) / 1e3)
 
     # roofline of the dominant kernel: the persistent FP64 CG (FP64 ALU bound;
-    # algorithmic flops: 8 per processed nonzero and application, 4 when the
-    # entry coefficients are real, 30 per processed row and CG iteration -
-    # see the design doc).  With the Hermitian
-    # half system the CG processes the rows k >lex 0 and their nonzeros, half
-    # of S and half of L's nonzeros (symmetric S; the zero row stores none).
+    # algorithmic flops: 8 per processed nonzero and application (4 FP64 FMAs
+    # of the complex product), 4 when the entry coefficients are real, and 30
+    # per processed row and CG iteration for the vector updates and the three
+    # inner products).  With the Hermitian half system the CG processes the
+    # rows k >lex 0 and their nonzeros, half of S and half of L's nonzeros
+    # (symmetric S; the zero row stores none).
     med = {k: statistics.median(v) for k, v in stage.items()}
     nnz, size, iters = r["nnz"], r["size"], r["iters"]
     applies = r["applies"]
