@@ -88,7 +88,8 @@ void retain_pool();
 // Requests above kScratchMaxTake go to the pool directly (the scratch saves
 // calls, which matters for many small temporaries, not for a few large ones)
 // and the block stays below kScratchMaxCap.
-// Not for memory that a captured graph or a persistent object keeps.
+// Not for memory that a captured graph or a persistent object keeps.  The
+// block stays with its thread (at most kScratchMaxCap) until the thread exits.
 constexpr size_t kScratchMaxTake = 16u << 20;
 constexpr size_t kScratchMaxCap = 96u << 20;
 void* scratch_take(size_t bytes, cudaStream_t st);   // nullptr: use the pool
