@@ -169,6 +169,23 @@ def test_recover_smooth_sizes_matches_oracle(B, M, d, span):
         assert np.abs(gv.cpu().numpy() - kv).max() <= 1e-12 * scale
 
 
+def test_recover_cfg2_full_size_closed_form(B):
+    # the d = 10 forcing (840 terms) on its CBC lattice, M >= 10^6 (7-smooth:
+    # the double-float transform), against the exact coefficients
+    from paper_2302_00752_gb300 import pipeline as gp
+    inst = W.make_cfg2()
+    p = gp.prepare(inst)
+    z, M = gp.choose_lattice(p.extra["lattice"], p.cand)
+    assert olat.is_smooth(M) and M <= 2 ** 22
+    ff, fc = p.f_freq.cpu().numpy(), p.f_coef.cpu().numpy()
+    gf, gv = B.sft_recover(z, M, ff, fc, p.cand, tau=1e-9)
+    want = osft.true_coefficients(ff, fc)
+    got = {tuple(k): v for k, v in zip(gf.cpu().numpy().tolist(), gv.cpu().numpy())}
+    scale = np.abs(fc).sum()
+    assert set(got) == {k for k, v in want.items() if abs(v) > 1e-9 * scale}
+    assert max(abs(v - want[k]) for k, v in got.items()) <= 1e-12 * scale
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 def test_recover_cfg1_matches_oracle(B, prec, tol):
     inst = W.make_cfg1()
