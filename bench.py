@@ -811,8 +811,13 @@ def main():
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak64 = fp64_peak_gflops(sm_max)
     achieved = solve_flops / (kms / 1e3) / 1e9
+    # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+    # the ncu capture in profiles/k_solve_fp64_half_system_cfg2.md, taken on
+    # this kernel for this workload (half system, real coefficients)
+    traffic = 41.355008e6 + 2.038272e6 if (half and realc) else None
     roofline = {"kernel": "k_solve<0> (persistent FP64 CG)", "bound": "alu", "achieved": achieved, "peak": peak64,
-                "unit": "GFLOP/s (FP64)", "frac": achieved / peak64, "traffic": None,
+                "unit": "GFLOP/s (FP64)", "frac": achieved / peak64, "traffic": traffic,
+                "traffic_unit": "DRAM bytes per launch (one ncu capture of this kernel on this workload)",
                 "peak_source": "derived: 1 FP64 FMA/clk/SM (ncu FP64-pipe counters) x 152 SMs x 2 x sm_max_mhz",
                 "flops_per_launch": solve_flops, "kernel_ms": kms, "half_system": half,
                 "real_coefficients": realc, "flops_per_processed_nnz": flops_nnz,
