@@ -90,6 +90,12 @@ def test_cfg3_multiscale(gp, prec):
     err = rel_l2(res.u.cpu().numpy(), ref.u)
     assert err < TOL, err
     assert res.stats["status"] == "SS_OK"
+    # independent of any CG: the FP64 residual with the oracle's explicit
+    # L_{N,s} (eq. GF assembled entry by entry) on the recovered data
+    from oracle.galerkin import galerkin_matrix
+    L, _ = galerkin_matrix(S, res.a_freq.cpu().numpy(), res.a_val.cpu().numpy())
+    f, u = res.f_on_S.cpu().numpy(), res.u.cpu().numpy()
+    assert np.linalg.norm(f - L @ u) <= 1e-11 * np.linalg.norm(f)
     res.stamp.destroy()
 
 
