@@ -15,8 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsparse_spectral.so")
+PEAKS_LIB = os.path.join(HERE, "libss_peaks.so")   # rate microbenchmarks (benchmark only)
 SOURCES = ["api.cu", "scan.cu", "stamp.cu", "apply.cu", "lattice.cu", "sft.cu", "solve.cu", "batch.cu", "proxy.cu",
-           "pipeline.cu", "fft_df.cu"]
+           "pipeline.cu", "fft_df.cu", "fft_pruned.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -48,9 +49,9 @@ def _compile(nv: str, src: str, obj: str, verbose: bool) -> None:
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PEAKS_LIB):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PEAKS_LIB))
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     deps.append(os.path.join(os.path.dirname(HERE), "include", "sparse_spectral.h"))
     return all(os.path.getmtime(p) <= t for p in deps)
@@ -62,8 +63,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nv = nvcc()
     os.makedirs(BUILD, exist_ok=True)
     objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
-    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
+    peaks_obj = os.path.join(BUILD, "peaks.o")
+    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES) + 1, os.cpu_count() or 4)) as ex:
         futs = [ex.submit(_compile, nv, os.path.join(CSRC, s), o, verbose) for s, o in zip(SOURCES, objs)]
+        futs.append(ex.submit(_compile, nv, os.path.join(CSRC, "peaks.cu"), peaks_obj, verbose))
         for f in futs:
             f.result()
     libdir = cuda_lib_dir(nv)
@@ -74,6 +77,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    tmp = PEAKS_LIB + ".tmp"
+    r = subprocess.run([nv, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, peaks_obj], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link of the peaks library failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PEAKS_LIB)
     return LIB
 
 

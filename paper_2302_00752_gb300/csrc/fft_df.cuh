@@ -22,6 +22,10 @@ struct DfFftPlan {
   DfRadices rad1, rad2;
 };
 
+// Radices of a self-sorting transform of length L (odd radices first, then
+// 8, 4, 2); n = -1 when L has a prime factor above 7.
+DfRadices df_radices(int L);
+
 // False when M has a prime factor above 7 or no factor pair fits.
 bool df_fft_plan(int64_t M, DfFftPlan* out);
 

@@ -27,22 +27,11 @@
 
 #include "df.cuh"
 #include "fft_df.cuh"
+#include "fft_pruned.cuh"
 #include "lattice.cuh"
 
 namespace ss {
 namespace {
-
-// (a b) mod M for a, b < M < 2^31 without a 64-bit division in the inner
-// loops: Barrett reduction with inv = floor((2^64 - 1) / M); the quotient
-// estimate __umul64hi(a b, inv) is at most two below floor(a b / M).
-__device__ __forceinline__ uint32_t mulmod(uint64_t a, uint64_t b, uint64_t M, uint64_t inv) {
-  const uint64_t x = a * b;
-  uint64_t r = x - __umul64hi(x, inv) * M;
-  r = r >= M ? r - M : r;
-  r = r >= M ? r - M : r;
-  return (uint32_t)r;
-}
-
 
 constexpr int kSampThreads = 256;
 constexpr int kSampPerThread = 8;
@@ -482,6 +471,13 @@ struct SftPlan {
   DfFftPlan dff;
   DevBuf<float4> dfz, dftmp;
   DevBuf<double> dfscale;   // the two sums' scales of the last round trip
+  // pruned double-float transforms (FP64 on a 7-smooth M above the full
+  // table's limit): two-level twiddle table, the complex sample vector
+  // s_a / sigma_a + i s_f / sigma_f and the two scales
+  bool has_pr = false;
+  TwoLevelTable prt;
+  DevBuf<float4> prz;
+  DevBuf<double> prscale;
   // inverse (Z2D) plan of the FFT evaluation path, made on first use
   mutable std::mutex ifft_mu;
   mutable cufftHandle ifft = 0;
@@ -572,6 +568,13 @@ ss_status get_plan(int64_t M, ss_precision prec, cudaStream_t st, std::shared_pt
       p->has_dff = true;
     }
   }
+  if (prec == SS_FP64 && M > kFullTableMax && !native_fp64_sampling() && pruned_supported(M)) {
+    SS_TRY(two_level_table(M, &p->prt, st));
+    SS_TRY(p->prz.alloc(M, st));
+    SS_TRY(p->prscale.alloc(2, st));
+    p->has_pr = true;
+  }
+  note_alloc();   // the plan allocates its work area
   const cufftResult r = cufftPlan1d(&p->fft, (int)M, prec == SS_FP64 ? CUFFT_D2Z : CUFFT_R2C, 1);
   if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cufftPlan1d(%lld) failed: %d", (long long)M, (int)r);
   p->has_fft = true;
@@ -579,6 +582,7 @@ ss_status get_plan(int64_t M, ss_precision prec, cudaStream_t st, std::shared_pt
   SS_CUDA(cudaStreamSynchronize(st));
   p->samples.settle(); p->spectrum.settle(); p->lo.settle(); p->hi.settle(); p->full.settle();
   p->dfz.settle(); p->dftmp.settle(); p->dfscale.settle();
+  p->prt.t0.settle(); p->prt.t1.settle(); p->prz.settle(); p->prscale.settle();
   for (auto& t : p->t3) t.settle();
   g_plans.push_front(p);
   while (g_plans.size() > kMaxPlans) g_plans.pop_back();
@@ -618,6 +622,7 @@ ss_status ensure_pair32(const SftPlan& P, cudaStream_t st) {
   SS_TRY(P.samples2.alloc(P.M, st));
   SS_TRY(P.z32.alloc(P.M, st));
   SS_TRY(P.scale32.alloc(2, st));
+  note_alloc();   // the plan allocates its work area
   const cufftResult r = cufftPlan1d(&P.c2c, (int)P.M, CUFFT_C2C, 1);
   if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cufftPlan1d(%lld, C2C) failed: %d", (long long)P.M, (int)r);
   // the buffers belong to the cached plan and outlive this call
@@ -632,6 +637,7 @@ ss_status ensure_pair32(const SftPlan& P, cudaStream_t st) {
 ss_status ensure_ifft(const SftPlan& P) {
   std::lock_guard<std::mutex> lk(P.ifft_mu);
   if (P.has_ifft) return SS_OK;
+  note_alloc();   // the plan allocates its work area
   const cufftResult r = cufftPlan1d(&P.ifft, (int)P.M, CUFFT_Z2D, 1);
   if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cufftPlan1d(%lld, Z2D) failed: %d", (long long)P.M, (int)r);
   P.has_ifft = true;
@@ -887,6 +893,9 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
   DevBuf<int64_t>& step = T.step;
   DevBuf<int64_t>& total = T.total;
   DevBuf<double2>& coef = T.coef;
+  if (P.has_pr)   // FP64 on a long 7-smooth lattice: sparse evaluation, real parts as FP64
+    return pruned_eval_pair(P.prt, q.get(), coef.get(), total.get(), n, nullptr, nullptr, nullptr, 0, nullptr, out,
+                            true, st);
   if (use_fft_eval(P, n)) {
     // the spectrum buffer holds the bins; its next reader (the forward
     // transform of recovery) follows in stream order
@@ -979,11 +988,69 @@ ss_status dff_round_trip(const SftPlan& P, const LatticeDev& L, const ss_trig* a
   return df_fft(P.dff, tab, Z, P.dftmp.get(), Z, -1, st);
 }
 
+// Pruned path (FP64 on a 7-smooth M above the full table): the two sums a and
+// f (f may be null) sampled at the M lattice nodes by the sparse evaluation
+// of their merged terms, as s_a / sigma_a + i s_f / sigma_f in P.prz.
+ss_status pr_sample_pair(const SftPlan& P, const LatticeDev& L, const ss_trig* a, const ss_trig* f, cudaStream_t st) {
+  const ss_trig none{L.d, 0, nullptr, nullptr};
+  if (!f) f = &none;
+  Terms ta, tf;
+  SS_TRY(prep_terms(L, a, &ta, st));
+  SS_TRY(prep_terms(L, f, &tf, st));
+  double* scale = P.prscale.get();
+  k_pair_scale<<<1, kScaleThreads, 0, st>>>(ta.coef.get(), ta.total.get(), tf.coef.get(), tf.total.get(), scale);
+  SS_LAUNCH_CHECK();
+  return pruned_eval_pair(P.prt, ta.q.get(), ta.coef.get(), ta.total.get(), a->n_terms, tf.q.get(), tf.coef.get(),
+                          tf.total.get(), f->n_terms, scale, P.prz.get(), false, st);
+}
+
+// Output bins of the pruned forward transform: for candidate i, its residue
+// b_i (output 2 i) and M - b_i (output 2 i + 1).
+__global__ void k_pr_bins(const int64_t* __restrict__ res, int64_t n, int64_t M, int64_t* __restrict__ bins) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  bins[2 * i] = res[i];
+  bins[2 * i + 1] = (M - res[i]) % M;
+}
+
+// k_extract_pair on the pruned transform's outputs (x = X[2 i], y = X[2 i + 1]);
+// scale null: one real sum given as samples (scale 1).
+template <int WHICH>
+__global__ void k_extract_pr(const int64_t* __restrict__ res, int64_t n, int64_t M, const float4* __restrict__ X,
+                             const double* __restrict__ scale, double2* val, double* mag,
+                             unsigned long long* maxbits) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 xs = X[2 * i], ys = X[2 * i + 1];
+  const double xr = (double)xs.x + (double)xs.y, xi = (double)xs.z + (double)xs.w;
+  const double yr = (double)ys.x + (double)ys.y, yi = (double)ys.z + (double)ys.w;
+  const double sc = 0.5 / (double)M * (scale ? scale[WHICH] : 1.0);
+  const double2 v = WHICH == 0 ? make_double2((xr + yr) * sc, (xi - yi) * sc)
+                               : make_double2((xi + yi) * sc, (yr - xr) * sc);
+  val[i] = v;
+  const double m = hypot(v.x, v.y);
+  mag[i] = m;
+  atomicMax(maxbits, (unsigned long long)__double_as_longlong(m));
+}
+
+// Pruned forward transform of s (P.prz, or the caller's real FP64 samples) at
+// the 2 n_cand bins of the candidates' residues; X: device [2 n_cand].
+ss_status pr_transform(const SftPlan& P, const void* s, bool real, const int64_t* res, int64_t n_cand, float4* X,
+                       cudaStream_t st) {
+  DevBuf<int64_t> bins;
+  SS_TRY(bins.alloc_tmp(2 * n_cand, st));
+  k_pr_bins<<<nblk(n_cand), 256, 0, st>>>(res, n_cand, P.M, bins.get());
+  SS_LAUNCH_CHECK();
+  return pruned_forward(P.prt, s, real, bins.get(), 2 * n_cand, X, st);
+}
+
 // zh non-null: the bins come from the double-float spectrum zh (real part
 // sum, as left by dff_round_trip) instead of a transform of samples.
+// pr != 0: the pruned forward transform of P.prz (pr = 1: complex samples of
+// one sum, scale P.prscale) or of the real FP64 samples (pr = 2).
 ss_status recover_from(const SftPlan& P, const LatticeDev& L, const void* samples, const int32_t* cand, int64_t n_cand,
                        int64_t s_max, double tau, int32_t* freq_out, double* val_out, int64_t* n_out, cudaStream_t st,
-                       const float4* zh = nullptr) {
+                       const float4* zh = nullptr, int pr = 0) {
   DevBuf<int64_t> res, total;
   DevBuf<unsigned long long> table, maxbits;
   DevBuf<int32_t> flags, flag, pos;
@@ -1002,7 +1069,11 @@ ss_status recover_from(const SftPlan& P, const LatticeDev& L, const void* sample
   SS_TRY(total.alloc_tmp(1, st));
   SS_TRY(residues(cand, n_cand, L, res.get(), st));
   SS_TRY(check_reconstructing_async(cand, n_cand, L, res.get(), true, table.get(), cap, flags.get(), st));
-  if (!zh) {
+  DevBuf<float4> X;
+  if (pr) {
+    SS_TRY(X.alloc_tmp(2 * n_cand, st));
+    SS_TRY(pr_transform(P, pr == 1 ? (const void*)P.prz.get() : samples, pr == 2, res.get(), n_cand, X.get(), st));
+  } else if (!zh) {
     cufftResult r = cufftSetStream(P.fft, st);
     if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cufftSetStream failed: %d", (int)r);
     if (P.prec == SS_FP64)
@@ -1014,7 +1085,10 @@ ss_status recover_from(const SftPlan& P, const LatticeDev& L, const void* sample
     if (r != CUFFT_SUCCESS) SS_FAIL(SS_ERR_CUDA, "cuFFT exec failed: %d", (int)r);
   }
   SS_CUDA(cudaMemsetAsync(maxbits.get(), 0, sizeof(unsigned long long), st));
-  if (zh)
+  if (pr)
+    k_extract_pr<0><<<nblk(n_cand), 256, 0, st>>>(res.get(), n_cand, L.M, X.get(), pr == 1 ? P.prscale.get() : nullptr,
+                                                  val.get(), mag.get(), maxbits.get());
+  else if (zh)
     k_extract_pair<0><<<nblk(n_cand), 256, 0, st>>>(cand, n_cand, L, zh, P.dfscale.get(), val.get(), mag.get(),
                                                     maxbits.get());
   else if (P.prec == SS_FP64)
@@ -1347,6 +1421,28 @@ ss_status sft_recover_both(const ss_lattice* lat, const ss_trig* a, const ss_tri
   const ss_trig* g[2] = {a, f};
   int32_t* fo[2] = {a_freq, f_freq};
   double* vo[2] = {a_val, f_val};
+  if (P.has_pr) {
+    // FP64 on a long 7-smooth lattice: both sums sampled by one sparse
+    // evaluation and recovered by one pruned forward transform
+    SS_TRY(pr_sample_pair(P, L, a, f, st));
+    DevBuf<float4> X;
+    SS_TRY(X.alloc_tmp(2 * n_cand, st));
+    SS_TRY(pr_transform(P, P.prz.get(), false, res.get(), n_cand, X.get(), st));
+    for (int k = 0; k < 2; ++k) {
+      if (k == 0)
+        k_extract_pr<0><<<nblk(n_cand), 256, 0, st>>>(res.get(), n_cand, L.M, X.get(), P.prscale.get(), val.get(),
+                                                      mag.get(), maxbits.get());
+      else
+        k_extract_pr<1><<<nblk(n_cand), 256, 0, st>>>(res.get(), n_cand, L.M, X.get(), P.prscale.get(), val.get(),
+                                                      mag.get(), maxbits.get() + 1);
+      k_keep<<<nblk(n_cand), 256, 0, st>>>(mag.get(), n_cand, maxbits.get() + k, tau, flag.get());
+      SS_LAUNCH_CHECK();
+      SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), n_cand, total.get() + k, st));
+      k_compact<<<nblk(n_cand), 256, 0, st>>>(cand, val.get(), n_cand, L.d, flag.get(), pos.get(), fo[k],
+                                              reinterpret_cast<double2*>(vo[k]));
+      SS_LAUNCH_CHECK();
+    }
+  }
   if (P.has_dff) {
     // FP64: both sums sampled by one inverse and recovered by one forward
     // double-float transform of length M
@@ -1367,7 +1463,7 @@ ss_status sft_recover_both(const ss_lattice* lat, const ss_trig* a, const ss_tri
       SS_LAUNCH_CHECK();
     }
   }
-  if (!P.has_dff && use_pair32(P)) {
+  if (!P.has_dff && !P.has_pr && use_pair32(P)) {
     SS_TRY(ensure_pair32(P, st));
     SS_TRY(sample_into(P, L, a, P.samples.get(), st));
     SS_TRY(sample_into(P, L, f, P.samples2.get(), st));
@@ -1397,7 +1493,7 @@ ss_status sft_recover_both(const ss_lattice* lat, const ss_trig* a, const ss_tri
       SS_LAUNCH_CHECK();
     }
   }
-  for (int k = 0; k < 2 && !P.has_dff && !use_pair32(P); ++k) {
+  for (int k = 0; k < 2 && !P.has_dff && !P.has_pr && !use_pair32(P); ++k) {
     // the plan's sample and spectrum buffers serve both sums in stream order
     SS_TRY(sample_into(P, L, g[k], P.samples.get(), st));
     if (P.prec == SS_FP64)
@@ -1460,6 +1556,8 @@ extern "C" ss_status sft_recover_samples(const ss_lattice* lat, const void* samp
   cudaStream_t st = as_stream(stream);
   std::shared_ptr<SftPlan> P;
   SS_TRY(get_plan(L.M, prec, st, &P));
+  if (P->has_pr)
+    return recover_from(*P, L, samples, cand, n_cand, s_max, tau, freq_out, val_out, n_out, st, nullptr, 2);
   return recover_from(*P, L, samples, cand, n_cand, s_max, tau, freq_out, val_out, n_out, st);
 }
 
@@ -1478,6 +1576,10 @@ extern "C" ss_status sft_recover(const ss_lattice* lat, const ss_trig* g, ss_pre
   if (P->has_dff) {
     SS_TRY(dff_round_trip(*P, L, g, nullptr, st));
     return recover_from(*P, L, nullptr, cand, n_cand, s_max, tau, freq_out, val_out, n_out, st, P->dfz.get());
+  }
+  if (P->has_pr) {
+    SS_TRY(pr_sample_pair(*P, L, g, nullptr, st));
+    return recover_from(*P, L, nullptr, cand, n_cand, s_max, tau, freq_out, val_out, n_out, st, nullptr, 1);
   }
   SS_TRY(sample_into(*P, L, g, P->samples.get(), st));
   return recover_from(*P, L, P->samples.get(), cand, n_cand, s_max, tau, freq_out, val_out, n_out, st);

@@ -78,6 +78,29 @@ ss_status fill_small(cudaStream_t st, std::initializer_list<FillPart> parts);
 // device) so that repeated builds do not go back to the driver.
 void retain_pool();
 
+// Counts one device or pinned-host allocation call made by the library
+// (reported by ss_alloc_count).
+void note_alloc();
+
+// Kernel timing (ss_profile): while it is on, a ProfScope brackets the
+// launches made inside its lifetime with a CUDA event pair on their stream
+// (not while the stream is being captured into a graph); the device time is
+// added to the named entry when the totals are read.
+bool prof_on();
+int64_t prof_begin(const char* name, cudaStream_t st);
+void prof_end(int64_t token);
+struct ProfScope {
+  int64_t tok = -1;
+  ProfScope(const char* name, cudaStream_t st) {
+    if (prof_on()) tok = prof_begin(name, st);
+  }
+  ~ProfScope() {
+    if (tok >= 0) prof_end(tok);
+  }
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+};
+
 // Scratch for call-local temporaries: one device block per host thread and
 // device, handed out in 256-byte units from the bottom up and given back in
 // any order (the top comes down once the blocks above are free).  A block is
@@ -148,6 +171,7 @@ struct DevBuf {
     release();
     retain_pool();
     if (count == 0) count = 1;
+    note_alloc();
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), stream);
     if (e != cudaSuccess) {
       p = nullptr;
@@ -309,6 +333,17 @@ __host__ __device__ __forceinline__ int32_t norm_word(int64_t n, bool wide) {
   std::memcpy(&w, &f, sizeof(w));
   return w;
 #endif
+}
+
+// (a b) mod M for a, b < M < 2^31 without a 64-bit division in the inner
+// loops: Barrett reduction with inv = floor((2^64 - 1) / M); the quotient
+// estimate __umul64hi(a b, inv) is at most two below floor(a b / M).
+__device__ __forceinline__ uint32_t mulmod(uint64_t a, uint64_t b, uint64_t M, uint64_t inv) {
+  const uint64_t x = a * b;
+  uint64_t r = x - __umul64hi(x, inv) * M;
+  r = r >= M ? r - M : r;
+  r = r >= M ? r - M : r;
+  return (uint32_t)r;
 }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
