@@ -92,6 +92,27 @@ typedef struct {
 const char* ss_last_error(void);
 const char* ss_version(void);
 
+/* Number of allocation calls the library has made in this process so far:
+ * device memory (stream-ordered pool, cuFFT plans) and pinned host staging
+ * blocks.  A diagnostic with no counterpart in the paper: a caller can check
+ * that a stretch of calls (e.g. solve_noalloc) allocated nothing.  Host. */
+int64_t ss_alloc_count(void);
+
+/* Kernel timing, a diagnostic with no counterpart in the paper.  With on != 0
+ * the library brackets its main kernels (recovery transforms, stamping,
+ * operator, solver) with CUDA events on the stream each is launched on -
+ * except while that stream is being captured into a graph - and accumulates
+ * launches and device time per kernel name; on = 0 stops.  Every call resets
+ * the totals.  Host. */
+ss_status ss_profile(int32_t on);
+
+/* Totals of entry i (0-based, in name order): the kernel name (NUL-terminated,
+ * truncated to name_cap bytes; name may be NULL), its launches and total
+ * milliseconds.  Waits for the events still pending.  *n_out (may be NULL)
+ * receives the number of entries; SS_ERR_INVALID when i is out of range. */
+ss_status ss_profile_entry(int32_t i, char* name, int32_t name_cap, int64_t* launches, double* total_ms,
+                           int32_t* n_out);
+
 /* ---------------------------------------------------------------- lattice */
 
 /* Lemma RandomRank1Lattice: smallest prime > max(K, n_I^2 / sigma) and
@@ -267,6 +288,15 @@ ss_status stamp_scatter(ss_stamp s, const ss_sparse* g, double* out, int64_t* n_
  * only be destroyed. */
 ss_status stamp_extend(ss_stamp s, int32_t levels, void* stream);
 
+/* Upper bound on the slots of the frequency hash table of every stamping set
+ * built or extended after this call (rounded down to a power of two, at least
+ * 16; 0 = no bound, the default).  A set whose frequencies do not fit makes
+ * stamp_build / stamp_extend return SS_ERR_HASH_FULL (every probe sequence is
+ * bounded by the table size, so an exhausted table ends the build with that
+ * status instead of waiting).  For capping the table's device memory, and for
+ * exercising the exhausted-table path.  Process-wide; host. */
+ss_status stamp_set_table_limit(int64_t max_slots);
+
 void stamp_destroy(ss_stamp s);
 
 /* -------------------------------------------------------------- operator */
@@ -336,6 +366,14 @@ ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, double tol, in
  * solves the full system (default 1). */
 ss_status solve_set_symmetry(ss_stamp s, int32_t use_half);
 
+/* Bound on every device-side wait of this stamp's persistent solver (the grid
+ * barrier between CG phases): a wait longer than ns nanoseconds ends the
+ * launch - every block returns - and solve reports SS_ERR_TIMEOUT, leaving
+ * the stamp usable for the next solve.  ns = 0 gives up at the first poll of
+ * a wait (always a timeout on a launch of more than one block).  Default
+ * 2 s.  Takes effect at the next solve. */
+ss_status solve_set_wait_limit(ss_stamp s, int64_t ns);
+
 /* Tile shape of this stamp's persistent solve: threads per block (128, 256,
  * 512 or 1024), resident blocks per SM (0 = as many as fit) and static work
  * chunks per block.  Takes effect at the next solve.  Default 1024, 1, 1. */
@@ -353,8 +391,13 @@ ss_status solve_set_config(ss_stamp s, int32_t block, int32_t blocks_per_sm, int
  * 32,768 padded rows (|S| <= 32,768, rounded up to whole 32-row slices);
  * larger sets return SS_ERR_INVALID.  It calls no allocating routine.
  * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Every call uses the whole array and leaves its contents
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life of
+ * the process; make that first call before any stream capture.  The kept
+ * address does not survive cudaDeviceReset (or any other teardown of the
+ * device's primary context): do not call solve_noalloc on a device after
+ * resetting it.  Unlike solve() it always solves the full system (never the
+ * Hermitian half system), with the work split solve() uses for the full
+ * system at its default tile shape.  Every call uses the whole array and leaves its contents
  * there (the next call re-initialises what must start at zero), so calls whose
  * GPU work overlaps - on different streams or threads - race and must be
  * serialised by the caller.  Synchronises `stream`; stats as solve() (without

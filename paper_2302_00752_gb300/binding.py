@@ -68,6 +68,11 @@ def _load():
     sigs = {
         "ss_last_error": (C.c_char_p, []),
         "ss_version": (C.c_char_p, []),
+        "ss_alloc_count": (C.c_int64, []),
+        "ss_profile": (i32, [i32]),
+        "ss_profile_entry": (i32, [i32, C.c_char_p, i32, P(i64), P(dbl), P(i32)]),
+        "solve_set_wait_limit": (i32, [vp, i64]),
+        "stamp_set_table_limit": (i32, [i64]),
         "lattice_size": (i32, [i64, i64, dbl, i64, P(i64)]),
         "lattice_check": (i32, [P(Lattice), vp, i64, vp]),
         "lattice_random": (i32, [vp, i64, i32, dbl, i64, P(i64), i32, P(i64), P(i64), P(i32), vp]),
@@ -353,6 +358,10 @@ class Stamp:
         self.size, self.nnz, self.zero_index, self.n_levels = size.value, nnz.value, zero.value, lv.value
         return self
 
+    def set_wait_limit(self, ns):
+        """Bound (ns) on each device-side wait of this stamp's solver (0: give up at once)."""
+        _check(lib.solve_set_wait_limit(self.handle, int(ns)))
+
     def set_symmetry(self, use_half):
         """Solve real data through the Hermitian half system (default True)."""
         _check(lib.solve_set_symmetry(self.handle, int(bool(use_half))))
@@ -456,9 +465,54 @@ def galerkin_apply(stamp, u, precision=None):
     return y
 
 
+def _check_solution_buffer(t, n, name):
+    if not (torch.is_tensor(t) and t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous complex128 CUDA tensor")
+    if t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} elements; the stamping set has {n}")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{torch.cuda.current_device()}")
+
+
+def set_table_limit(max_slots):
+    """Slot bound of the hash tables of stamps built from now on (0: none)."""
+    _check(lib.stamp_set_table_limit(int(max_slots)))
+
+
+def profile(on):
+    """Start (True) or stop kernel timing; resets the totals."""
+    _check(lib.ss_profile(1 if on else 0))
+
+
+def profile_totals():
+    """{kernel name: (launches, total ms)} accumulated since profile(True)."""
+    n = C.c_int32(0)
+    out = {}
+    i = 0
+    while True:
+        name = C.create_string_buffer(128)
+        cnt, ms = C.c_int64(), C.c_double()
+        if lib.ss_profile_entry(i, name, 128, C.byref(cnt), C.byref(ms), C.byref(n)) != 0:
+            break
+        out[name.value.decode()] = (cnt.value, ms.value)
+        i += 1
+    return out
+
+
+def alloc_count():
+    """Allocation calls the library has made in this process (diagnostic)."""
+    return int(lib.ss_alloc_count())
+
+
 def solve(stamp, f_on_S, tol=1e-12, max_iter=1000, precision="fp64", out=None, raise_on_error=True):
     f = _dev_c128(f_on_S)
-    u = torch.empty_like(f) if out is None else out
+    if f.numel() != stamp.size:
+        raise ValueError(f"f_on_S has {f.numel()} elements; the stamping set has {stamp.size}")
+    if out is None:
+        u = torch.empty_like(f)
+    else:
+        _check_solution_buffer(out, stamp.size, "out")
+        u = out
     st = SolveStats()
     status = lib.solve(stamp.handle, _ptr(f), _ptr(u), float(tol), int(max_iter), _prec(precision), C.byref(st),
                        _stream())
@@ -475,11 +529,8 @@ def solve_noalloc(stamp, f_on_S, out, tol=1e-12, max_iter=1000, precision="fp64"
     device tensors of length |S|; the workspace is a fixed library array for
     |S| <= 32768 (larger sets raise SSError).  Calls that overlap on the GPU
     share that array and race."""
-    if not (torch.is_tensor(f_on_S) and f_on_S.is_cuda and f_on_S.dtype == torch.complex128
-            and f_on_S.is_contiguous()):
-        raise TypeError("f_on_S must be a contiguous complex128 CUDA tensor")
-    if not (torch.is_tensor(out) and out.is_cuda and out.dtype == torch.complex128 and out.is_contiguous()):
-        raise TypeError("out must be a contiguous complex128 CUDA tensor")
+    _check_solution_buffer(f_on_S, stamp.size, "f_on_S")
+    _check_solution_buffer(out, stamp.size, "out")
     st = SolveStats()
     _check(lib.solve_noalloc(stamp.handle, _ptr(f_on_S), _ptr(out), float(tol), int(max_iter), _prec(precision),
                              C.byref(st), _stream()))

@@ -1,5 +1,9 @@
 // Library-wide helpers behind the C ABI: per-thread error text, version,
 // device properties.
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 #include <algorithm>
 #include <cstdarg>
@@ -71,6 +75,7 @@ void* scratch_take(size_t bytes, cudaStream_t st) {
     if (!A.base && A.want > 0) {
       retain_pool();
       const size_t cap = std::min(A.want + A.want / 4, kScratchMaxCap);
+      note_alloc();
       if (cudaMallocAsync(reinterpret_cast<void**>(&A.base), cap, st) != cudaSuccess) {
         cudaGetLastError();
         A.base = nullptr;
@@ -192,6 +197,7 @@ ss_status upload(cudaStream_t st, std::initializer_list<HostWrite> parts) {
       g_up.n = 0;
     }
     const size_t n = std::max<size_t>(total, 64 * 1024);
+    note_alloc();
     SS_CUDA(cudaMallocHost(&g_up.p, n));
     g_up.n = n;
   }
@@ -219,6 +225,7 @@ ss_status read_back(cudaStream_t st, std::initializer_list<HostRead> parts) {
       g_pinned.dev = nullptr;
     }
     const size_t n = std::max<size_t>(total, 64 * 1024);
+    note_alloc();
     SS_CUDA(cudaHostAlloc(&g_pinned.p, n, cudaHostAllocMapped));
     g_pinned.n = n;
     if (cudaHostGetDevicePointer(&g_pinned.dev, g_pinned.p, 0) != cudaSuccess) {
@@ -286,4 +293,141 @@ int sm_count() {
 
 extern "C" const char* ss_last_error(void) { return ss::g_err; }
 
+namespace ss {
+namespace {
+std::atomic<int64_t> g_alloc_count{0};
+}  // namespace
+void note_alloc() { g_alloc_count.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace ss
+
+extern "C" int64_t ss_alloc_count(void) { return ss::g_alloc_count.load(std::memory_order_relaxed); }
+
 extern "C" const char* ss_version(void) { return "sparse-spectral-gb300 0.1 (sm_103a)"; }
+
+// ------------------------------------------------------------ kernel timing
+
+namespace ss {
+namespace {
+
+struct ProfPending {
+  std::string name;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaStream_t st = nullptr;
+  bool ended = false;
+};
+
+struct ProfTotals {
+  int64_t launches = 0;
+  double ms = 0.0;
+};
+
+std::atomic<bool> g_prof_on{false};
+std::mutex g_prof_mu;
+std::map<int64_t, ProfPending> g_prof_pending;   // by token
+int64_t g_prof_next = 0;
+std::vector<cudaEvent_t> g_prof_free;
+std::map<std::string, ProfTotals> g_prof_totals;
+
+cudaEvent_t prof_event() {
+  if (!g_prof_free.empty()) {
+    cudaEvent_t e = g_prof_free.back();
+    g_prof_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Resolve every ended pair (waits for its end event); caller holds the lock.
+void prof_drain() {
+  for (auto it = g_prof_pending.begin(); it != g_prof_pending.end();) {
+    ProfPending& p = it->second;
+    if (!p.ended) {
+      ++it;
+      continue;
+    }
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.e1) == cudaSuccess && cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) {
+      ProfTotals& t = g_prof_totals[p.name];
+      t.launches += 1;
+      t.ms += ms;
+    } else {
+      cudaGetLastError();
+    }
+    g_prof_free.push_back(p.e0);
+    g_prof_free.push_back(p.e1);
+    it = g_prof_pending.erase(it);
+  }
+}
+
+}  // namespace
+
+bool prof_on() { return g_prof_on.load(std::memory_order_relaxed); }
+
+int64_t prof_begin(const char* name, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return -1;
+  }
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (g_prof_pending.size() > 4096) prof_drain();   // bound the events held
+  ProfPending p;
+  p.name = name;
+  p.st = st;
+  p.e0 = prof_event();
+  p.e1 = prof_event();
+  if (!p.e0 || !p.e1 || cudaEventRecord(p.e0, st) != cudaSuccess) {
+    cudaGetLastError();
+    if (p.e0) g_prof_free.push_back(p.e0);
+    if (p.e1) g_prof_free.push_back(p.e1);
+    return -1;
+  }
+  const int64_t tok = g_prof_next++;
+  g_prof_pending.emplace(tok, p);
+  return tok;
+}
+
+void prof_end(int64_t token) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  auto it = g_prof_pending.find(token);
+  if (it == g_prof_pending.end()) return;
+  ProfPending& p = it->second;
+  if (cudaEventRecord(p.e1, p.st) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  p.ended = true;
+}
+
+}  // namespace ss
+
+extern "C" ss_status ss_profile(int32_t on) {
+  std::lock_guard<std::mutex> lk(ss::g_prof_mu);
+  ss::prof_drain();
+  ss::g_prof_totals.clear();
+  ss::g_prof_on.store(on != 0, std::memory_order_relaxed);
+  return SS_OK;
+}
+
+extern "C" ss_status ss_profile_entry(int32_t i, char* name, int32_t name_cap, int64_t* launches, double* total_ms,
+                                      int32_t* n_out) {
+  std::lock_guard<std::mutex> lk(ss::g_prof_mu);
+  ss::prof_drain();
+  const int32_t n = (int32_t)ss::g_prof_totals.size();
+  if (n_out) *n_out = n;
+  if (i < 0 || i >= n) SS_FAIL(SS_ERR_INVALID, "ss_profile_entry: index %d of %d entries", (int)i, (int)n);
+  auto it = ss::g_prof_totals.begin();
+  std::advance(it, i);
+  if (name && name_cap > 0) {
+    std::strncpy(name, it->first.c_str(), (size_t)name_cap - 1);
+    name[name_cap - 1] = '\0';
+  }
+  if (launches) *launches = it->second.launches;
+  if (total_ms) *total_ms = it->second.ms;
+  return SS_OK;
+}

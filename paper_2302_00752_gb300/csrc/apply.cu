@@ -144,7 +144,10 @@ ss_status launch_pack64_prefix(const ss_stamp_s* s, const double2* u, int64_t n_
 }
 
 ss_status launch_apply64(const ss_stamp_s* s, double2* y, cudaStream_t st) {
-  k_apply64<<<nblk(s->rows_pad), 256, 0, st>>>(op_view(s), s->size, s->rows_pad, s->rec64.get(), identity_row(s), y);
+  {
+    ProfScope prof_("k_apply64", st);
+    k_apply64<<<nblk(s->rows_pad), 256, 0, st>>>(op_view(s), s->size, s->rows_pad, s->rec64.get(), identity_row(s), y);
+  }
   SS_LAUNCH_CHECK();
   return SS_OK;
 }
@@ -152,11 +155,17 @@ ss_status launch_apply64(const ss_stamp_s* s, double2* y, cudaStream_t st) {
 ss_status launch_apply32(const ss_stamp_s* s, const float2* u, float2* y, cudaStream_t st) {
   if (s->adr) SS_FAIL(SS_ERR_INVALID, "the FP32 operator is not available for ADR stamps (use SS_FP64)");
   if (s->wide)
-    k_apply32<true><<<nblk(s->rows_pad), 256, 0, st>>>(op_view(s), s->size, s->rows_pad, s->nw32.get(), u,
-                                                       s->ca32.get(), s->pn32.get(), s->zero_idx, y);
+    {
+      ProfScope prof_("k_apply32", st);
+      k_apply32<true><<<nblk(s->rows_pad), 256, 0, st>>>(op_view(s), s->size, s->rows_pad, s->nw32.get(), u,
+                                                         s->ca32.get(), s->pn32.get(), s->zero_idx, y);
+    }
   else
-    k_apply32<false><<<nblk(s->rows_pad), 256, 0, st>>>(op_view(s), s->size, s->rows_pad, s->nw32.get(), u,
-                                                        s->ca32.get(), s->pn32.get(), s->zero_idx, y);
+    {
+      ProfScope prof_("k_apply32", st);
+      k_apply32<false><<<nblk(s->rows_pad), 256, 0, st>>>(op_view(s), s->size, s->rows_pad, s->nw32.get(), u,
+                                                          s->ca32.get(), s->pn32.get(), s->zero_idx, y);
+    }
   SS_LAUNCH_CHECK();
   return SS_OK;
 }

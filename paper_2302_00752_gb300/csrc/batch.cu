@@ -382,7 +382,10 @@ static ss_status batch_create_half(ss_batch_s* b, int32_t n, const ss_stamp* sta
     h->plan.inst[i].u = b->uc.get() + row0_h;
     q0 += s->size;
   }
-  if (!b->hflag_host) SS_CUDA(cudaMallocHost(&b->hflag_host, sizeof(int32_t)));
+  if (!b->hflag_host) {
+    note_alloc();
+    SS_CUDA(cudaMallocHost(&b->hflag_host, sizeof(int32_t)));
+  }
   SS_CUDA(cudaStreamSynchronize(st));
   b->fc.settle(); b->uc.settle(); b->gsrc.settle(); b->gmir.settle(); b->srow_inst.settle();
   b->slocal.settle(); b->shpos.settle(); b->hflag.settle(); b->fptr.settle(); b->uptr.settle();

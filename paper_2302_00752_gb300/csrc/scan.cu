@@ -112,6 +112,7 @@ ss_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int64_t
     return SS_OK;
   }
   int32_t* sums = nullptr;
+  note_alloc();
   SS_CUDA(cudaMallocAsync(&sums, tiles * sizeof(int32_t), st));
   k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, out, n, sums, nullptr);
   ss_status s = SS_OK;

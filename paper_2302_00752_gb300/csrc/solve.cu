@@ -80,7 +80,7 @@ __device__ bool grid_sync(const SolveParams& P) {
     } else {
       const long long t0 = gtimer();
       for (unsigned it = 1; ld_acquire(gen) == g; ++it) {
-        if ((it & 255u) == 0) {
+        if (it == 1 || (it & 255u) == 0) {
           if (*(volatile int*)P.err) { ok = 0; break; }
           if (gtimer() - t0 > P.spin_limit) {
             atomicCAS(P.err, 0, (int)SS_ERR_TIMEOUT);
@@ -1249,7 +1249,7 @@ ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, co
   P.max_iter = max_iter;
   P.max_inner = std::max(1, std::min(max_iter, 200));
   P.max_outer = std::max(1, max_iter);
-  P.spin_limit = 2000000000ll;   // 2 s
+  P.spin_limit = plan.spin_limit;   // 2 s unless solve_set_wait_limit changed it
   P.rows_slices = plan.row_split && P.n_inst == 1 && !slice_inst ? plan.chunk.back().s1 : 0;
   SS_TRY(fill_small(st, {{W.bar.get(), 2 * sizeof(unsigned), 0}, {W.counters.get(), 4 * sizeof(int), 0}}));
   SS_CUDA(cudaMemsetAsync(W.err.get(), 0, sizeof(int), st));
@@ -1267,10 +1267,14 @@ ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, co
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (ev_begin) SS_CUDA(cudaEventRecord(ev_begin, st));
-  if (mode == 0) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<0>, P));
-  else if (mode == 1) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<1>, P));
-  else if (mode == 2) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<2>, P));
-  else SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<3>, P));
+  {
+    static const char* const names[4] = {"k_solve<0>", "k_solve<1>", "k_solve<2>", "k_solve<3>"};
+    ProfScope prof_(names[mode & 3], st);
+    if (mode == 0) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<0>, P));
+    else if (mode == 1) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<1>, P));
+    else if (mode == 2) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<2>, P));
+    else SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<3>, P));
+  }
   if (ev_end) SS_CUDA(cudaEventRecord(ev_end, st));
   return SS_OK;
 }
@@ -1317,6 +1321,7 @@ struct ss_solve_ctx {
   ss::SolvePlan plan;
   int planned_mode = -1;
   int block = 1024, blocks_per_sm = 1, chunks_per_block = 1;   // tile shape (solve_set_config)
+  long long wait_ns = 2000000000ll;   // grid-barrier wait bound (solve_set_wait_limit)
   double2* f0_host = nullptr;   // pinned copy of f_hat_0, checked after the solve's own synchronisation
   // Hermitian half system (FP64 CG): its own plan and workspace, the compact
   // right-hand side and solution, and the "f is not Hermitian" flag
@@ -1456,6 +1461,7 @@ static void reset_ctx(ss_solve_ctx* C) {
   C->blocks_per_sm = 1;
   C->chunks_per_block = 1;
   C->use_half = true;
+  C->wait_ns = 2000000000ll;
   if (C->half) reset_ctx(C->half);
 }
 
@@ -1501,6 +1507,12 @@ extern "C" ss_status solve_set_config(ss_stamp s, int32_t block, int32_t blocks_
   return SS_OK;
 }
 
+extern "C" ss_status solve_set_wait_limit(ss_stamp s, int64_t ns) {
+  if (!s || ns < 0) SS_FAIL(SS_ERR_INVALID, "solve_set_wait_limit: null stamp or negative limit");
+  solve_ctx(s)->wait_ns = ns == 0 ? -1 : (long long)ns;   // 0: give up at the first poll
+  return SS_OK;
+}
+
 extern "C" ss_status solve_set_symmetry(ss_stamp s, int32_t use_half) {
   if (!s) SS_FAIL(SS_ERR_INVALID, "solve_set_symmetry: null stamp");
   solve_ctx(s)->use_half = use_half != 0;
@@ -1518,7 +1530,10 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
   const bool check_f0 = !s->adr && s->zero_idx >= 0;
   if (check_f0) {
     // read back with the solve's statistics (one synchronisation for both)
-    if (!C->f0_host) SS_CUDA(cudaMallocHost(&C->f0_host, sizeof(double2)));
+    if (!C->f0_host) {
+      note_alloc();
+      SS_CUDA(cudaMallocHost(&C->f0_host, sizeof(double2)));
+    }
     SS_CUDA(cudaMemcpyAsync(C->f0_host, reinterpret_cast<const double2*>(f_on_S) + s->zero_idx, sizeof(double2),
                             cudaMemcpyDeviceToHost, st));
   }
@@ -1539,7 +1554,10 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
     SS_TRY(C->fh.ensure(s->rows_pad_h, st));
     SS_TRY(C->uh.ensure(s->rows_pad_h, st));
     SS_TRY(C->hflag.ensure(1, st));
-    if (!C->hflag_host) SS_CUDA(cudaMallocHost(&C->hflag_host, sizeof(int32_t)));
+    if (!C->hflag_host) {
+      note_alloc();
+      SS_CUDA(cudaMallocHost(&C->hflag_host, sizeof(int32_t)));
+    }
     SS_CUDA(cudaMemsetAsync(C->hflag.get(), 0, sizeof(int32_t), st));
     const unsigned gb = (unsigned)((s->n_plus + 255) / 256), sb = (unsigned)((s->size + 255) / 256);
     k_half_gather<<<gb, 256, 0, st>>>(reinterpret_cast<const double2*>(f_on_S), s->plus_rows.get(), s->mirror.get(),
@@ -1562,6 +1580,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
       SS_CUDA(cudaEventCreate(&H->work.ev[0]));
       SS_CUDA(cudaEventCreate(&H->work.ev[1]));
     }
+    H->plan.spin_limit = C->wait_ns;
     SS_TRY(launch_solve(H->work, H->plan, hop, nullptr, s->norm_h.get(), s->ca64.get(), s->ca32.get(), s->pn32.get(),
                         tol, max_iter, mode, st, H->work.ev[0], H->work.ev[1], nullptr));
     k_half_scatter<<<sb, 256, 0, st>>>(C->uh.get(), s->hpos.get(), s->size, reinterpret_cast<double2*>(u_on_S));
@@ -1601,6 +1620,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
     SS_CUDA(cudaEventCreate(&C->work.ev[0]));
     SS_CUDA(cudaEventCreate(&C->work.ev[1]));
   }
+  C->plan.spin_limit = C->wait_ns;
   SS_TRY(launch_solve(C->work, C->plan, op, nullptr, s->norm.get(), s->ca64.get(), s->ca32.get(), s->pn32.get(), tol,
                       max_iter, mode, st, C->work.ev[0], C->work.ev[1], s->adr ? s->diag64.get() : nullptr));
   ss_status worst;
@@ -1618,8 +1638,10 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
 
 // ------------------------------------------------------ allocation-free solve
 //
-// solve_noalloc runs the same persistent solver as solve() but takes all of
-// its workspace from one file-scope device array instead of allocating it.
+// solve_noalloc runs the same persistent solver as solve() (the full system,
+// never the Hermitian half system; the same work split as solve() with its
+// default tile shape) but takes all of its workspace from one file-scope
+// device array instead of allocating it.
 // It serves callers that may not allocate device memory once they run:
 // plug-ins inside a host application that owns all device memory, code that
 // must not stall on cudaMalloc (allocation synchronises the device), or code
@@ -1708,18 +1730,11 @@ extern "C" ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_o
   cudaStream_t st = as_stream(stream);
   unsigned char* base = nullptr;
   SS_TRY(noalloc_base(&base));
-  if (s->zero_idx >= 0) {
-    double2 f0;
-    SS_CUDA(cudaMemcpyAsync(&f0, reinterpret_cast<const double2*>(f_on_S) + s->zero_idx, sizeof(f0),
-                            cudaMemcpyDeviceToHost, st));
-    SS_CUDA(cudaStreamSynchronize(st));
-    if (f0.x != 0.0 || f0.y != 0.0) SS_FAIL(SS_ERR_INVALID, "solve_noalloc: f_hat_0 must be 0 (mean-zero forcing)");
-  }
-  // static work split, as solve() with its default tile shape (host memory only)
+  if ((int64_t)s->woff_host.size() != s->n_slices + 1) SS_FAIL(SS_ERR_INVALID, "solve_noalloc: stamp has no slice table");
+  // static work split, as solve() with its default tile shape, from the host
+  // copy of the slice table (host memory only)
   const int mode = prec == SS_FP64 ? 0 : 1;
-  std::vector<int32_t> woff(s->n_slices + 1);
-  SS_CUDA(cudaMemcpyAsync(woff.data(), s->slice_off.get(), woff.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
+  const std::vector<int32_t>& woff = s->woff_host;
   SolvePlan plan;
   plan.inst.assign(1, SolveInst{});
   SolveInst& in = plan.inst[0];
@@ -1737,7 +1752,9 @@ extern "C" ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_o
   SS_TRY(max_grid(mode, plan.block, &grid));
   grid = std::min(grid, sm_count());
   const int by_size = (int)std::max<int64_t>(1, s->n_slices / 8);
-  SS_TRY(plan_chunks(plan, woff, {}, std::min(grid, by_size)));
+  // FP64 CG: the vector updates over an even split of the rows (as solve())
+  plan.row_split = mode == 0;
+  SS_TRY(plan_chunks(plan, woff, {}, std::min(grid, by_size), plan.row_split ? 1.0 : 6.0));
   plan.grid = std::min<int>(grid, (int)plan.chunk.size());
   if ((int)plan.chunk.size() > kNoAllocChunks || plan.n_parts > kNoAllocParts)
     SS_FAIL(SS_ERR_INVALID, "solve_noalloc: work split exceeds the workspace tables");
@@ -1804,6 +1821,7 @@ extern "C" ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_o
   P.max_inner = std::max(1, std::min(max_iter, 200));
   P.max_outer = std::max(1, max_iter);
   P.spin_limit = 2000000000ll;
+  P.rows_slices = plan.row_split ? plan.chunk.back().s1 : 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(plan.grid);
   cfg.blockDim = dim3(plan.block);
@@ -1815,10 +1833,15 @@ extern "C" ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_o
   cfg.numAttrs = 1;
   if (mode == 0) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<0>, P));
   else SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<1>, P));
+  // statistics, error word and f_hat_0 read back with one synchronisation
   InstState hs;
   int herr = 0;
+  double2 f0 = make_double2(0.0, 0.0);
   SS_CUDA(cudaMemcpyAsync(&hs, d_state, sizeof(hs), cudaMemcpyDeviceToHost, st));
   SS_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (s->zero_idx >= 0)
+    SS_CUDA(cudaMemcpyAsync(&f0, reinterpret_cast<const double2*>(f_on_S) + s->zero_idx, sizeof(f0),
+                            cudaMemcpyDeviceToHost, st));
   SS_CUDA(cudaStreamSynchronize(st));
   const double rel = hs.bb > 0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
   if (stats) {
@@ -1830,6 +1853,10 @@ extern "C" ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_o
     stats->kernel_ms = 0.0;
     stats->half_system = 0;
     stats->real_coefficients = s->a_real;
+  }
+  if (f0.x != 0.0 || f0.y != 0.0) {
+    if (stats) stats->status = SS_ERR_INVALID;
+    SS_FAIL(SS_ERR_INVALID, "solve_noalloc: f_hat_0 must be 0 (mean-zero forcing)");
   }
   if (herr) SS_FAIL((ss_status)herr, "solve_noalloc: a device-side wait gave up (status %d)", herr);
   if (hs.status != SS_OK) SS_FAIL((ss_status)hs.status, "solve_noalloc: not converged (relative residual %.3e)", rel);

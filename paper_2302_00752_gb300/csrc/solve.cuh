@@ -82,6 +82,7 @@ struct SolvePlan {
   int64_t n_parts = 0;
   int grid = 0, block = 256;
   bool row_split = false;   // single instance: the row-wise CG phases split the slices evenly over the blocks
+  long long spin_limit = 2000000000ll;   // bound on each grid-barrier wait (ns); below 0: give up at the first poll
 };
 
 // Device workspace of one solve context (single stamp or batch).

@@ -14,6 +14,7 @@
 // the parent key and the step, so a claim is one 64-bit CAS.  Every slot word
 // also carries a 31-bit fingerprint of the key hash, so probes compare stored
 // keys (up to 12 words at d = 100) only when the fingerprints agree.
+#include <atomic>
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -492,8 +493,17 @@ uint64_t next_pow2(uint64_t x) {
 
 // ------------------------------------------------------------------ build
 
+// Slot bound of the hash tables built from now on (stamp_set_table_limit; 0: none).
+static std::atomic<int64_t> g_table_limit{0};
+
 static ss_status grow_table(ss_stamp_s* S, int64_t need, const KeyParams& P, cudaStream_t st, int32_t* d_err) {
-  const int64_t want = (int64_t)next_pow2((uint64_t)std::max<int64_t>(2 * need, 1024));
+  int64_t want = (int64_t)next_pow2((uint64_t)std::max<int64_t>(2 * need, 1024));
+  const int64_t lim = g_table_limit.load(std::memory_order_relaxed);
+  if (lim > 0) {
+    int64_t c = 16;
+    while (2 * c <= lim) c *= 2;   // largest power of two <= lim (at least 16)
+    want = std::min(want, c);
+  }
   if (want <= S->cap) return SS_OK;
   SS_TRY(S->table.alloc(want, st));
   S->cap = want;
@@ -590,10 +600,13 @@ static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st
     SS_TRY(grow_keys(S, S->size + n_par * (s_a - 1), st));
     SS_TRY(slot_of.ensure_tmp(ncand, st));
     SS_TRY(flag.ensure_tmp(ncand, st));
-    SS_DISPATCH_WT(S->key.WT, (k_insert<WT><<<nblk(ncand), 256, 0, st>>>(P, S->keys.get(), par0, n_par, s_a, S->j0,
-                                                                         S->stepkey.get(), S->table.get(),
-                                                                         (uint64_t)S->cap - 1, slot_of.get(),
-                                                                         S->err_dev.get())));
+    {
+      ProfScope prof_("k_insert", st);
+      SS_DISPATCH_WT(S->key.WT, (k_insert<WT><<<nblk(ncand), 256, 0, st>>>(P, S->keys.get(), par0, n_par, s_a, S->j0,
+                                                                           S->stepkey.get(), S->table.get(),
+                                                                           (uint64_t)S->cap - 1, slot_of.get(),
+                                                                           S->err_dev.get())));
+    }
     k_winner_flags<<<nblk(ncand), 256, 0, st>>>(slot_of.get(), S->table.get(), ncand, flag.get());
     SS_LAUNCH_CHECK();
     DevBuf<int32_t> pos;
@@ -603,11 +616,14 @@ static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st
     int32_t e = 0;
     SS_TRY(read_back(st, {{&added, d_total.get(), sizeof(int64_t)}, {&e, S->err_dev.get(), sizeof(int32_t)}}));
     if (e) SS_FAIL((ss_status)e, "stamp: hash table exhausted at level %d", n);
-    SS_DISPATCH_WT(S->key.WT, (k_finalize<WT><<<nblk(ncand), 256, 0, st>>>(P, S->keys.get(), par0, s_a,
-                                                                           S->stepkey.get(), slot_of.get(), flag.get(),
-                                                                           pos.get(), ncand, S->size, n,
-                                                                           S->level.get(), S->norm.get(),
-                                                                           S->table.get(), S->zidx_dev.get())));
+    {
+      ProfScope prof_("k_finalize", st);
+      SS_DISPATCH_WT(S->key.WT, (k_finalize<WT><<<nblk(ncand), 256, 0, st>>>(P, S->keys.get(), par0, s_a,
+                                                                             S->stepkey.get(), slot_of.get(), flag.get(),
+                                                                             pos.get(), ncand, S->size, n,
+                                                                             S->level.get(), S->norm.get(),
+                                                                             S->table.get(), S->zidx_dev.get())));
+    }
     SS_LAUNCH_CHECK();
     S->size += added;
     S->level_start.push_back(S->size);
@@ -770,10 +786,13 @@ static ss_status build_half(ss_stamp_s* S, cudaStream_t st) {
                                                      S->ent.get(), colmask, S->rows_pad, slice_w.get());
   SS_LAUNCH_CHECK();
   SS_TRY(exclusive_scan_i32(slice_w.get(), S->woff_h.get(), S->n_slices_h + 1, total.get(), st));
-  k_half_fill<<<nblk(S->rows_pad_h), 256, 0, st>>>(S->plus_rows.get(), n_plus, S->rows_pad_h, S->slice_off.get(),
-                                                   S->ent.get(), S->ecoef64.get(), colmask, colbits_of(S->jbits),
-                                                   S->rows_pad, S->colbits_h, S->j0, S->hpos.get(), S->woff_h.get(),
-                                                   S->ent_h.get(), S->ecoef_h.get());
+  {
+    ProfScope prof_("k_half_fill", st);
+    k_half_fill<<<nblk(S->rows_pad_h), 256, 0, st>>>(S->plus_rows.get(), n_plus, S->rows_pad_h, S->slice_off.get(),
+                                                     S->ent.get(), S->ecoef64.get(), colmask, colbits_of(S->jbits),
+                                                     S->rows_pad, S->colbits_h, S->j0, S->hpos.get(), S->woff_h.get(),
+                                                     S->ent_h.get(), S->ecoef_h.get());
+  }
   SS_LAUNCH_CHECK();
   S->woff_h_host.resize(S->n_slices_h + 1);
   S->half_ok = true;   // confirmed by the caller's read-back of the mirror flag
@@ -802,9 +821,12 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   SS_TRY(fill_small(st, {{S->norm.get() + S->size, (S->rows_pad + 1 - S->size) * sizeof(int64_t), 0},
                          {d_nnz.get(), sizeof(unsigned long long), 0},
                          {slice_w.get(), (S->n_slices + 1) * sizeof(int32_t), 0}}));
-  SS_DISPATCH_WT(S->key.WT, (k_neighbors<WT><<<nblk(S->size * s_a), 256, 0, st>>>(
-                                P, S->keys.get(), S->size, s_a, S->stepkey.get(), S->table.get(),
-                                (uint64_t)S->cap - 1, S->zidx_dev.get(), S->adr, nbr.get())));
+  {
+    ProfScope prof_("k_neighbors", st);
+    SS_DISPATCH_WT(S->key.WT, (k_neighbors<WT><<<nblk(S->size * s_a), 256, 0, st>>>(
+                                  P, S->keys.get(), S->size, s_a, S->stepkey.get(), S->table.get(),
+                                  (uint64_t)S->cap - 1, S->zidx_dev.get(), S->adr, nbr.get())));
+  }
   k_row_counts<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, slice_w.get(), d_nnz.get());
   SS_LAUNCH_CHECK();
   SS_TRY(S->slice_off.alloc(S->n_slices + 1, st));
@@ -829,9 +851,12 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
                                   colbits_of(S->jbits), S->norm.get(), S->pnorm.get(), S->ca64.get(), S->bval.get(),
                                   S->cval.get(), S->ent.get(), S->ecoef64.get(), S->diag64.get())));
   } else {
-    k_fill_slices<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, S->j0,
-                                                     S->slice_off.get(), colbits_of(S->jbits), S->norm.get(),
-                                                     S->pnorm.get(), S->ca64.get(), S->ent.get(), S->ecoef64.get());
+    {
+      ProfScope prof_("k_fill_slices", st);
+      k_fill_slices<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, S->j0,
+                                                       S->slice_off.get(), colbits_of(S->jbits), S->norm.get(),
+                                                       S->pnorm.get(), S->ca64.get(), S->ent.get(), S->ecoef64.get());
+    }
   }
   SS_LAUNCH_CHECK();
   SS_TRY(S->nw32.alloc(S->rows_pad + 1, st));
@@ -1191,6 +1216,12 @@ extern "C" ss_status stamp_extend(ss_stamp s, int32_t levels, void* stream) {
   const ss_status r = extend_impl(s, levels, st);
   if (r != SS_OK) cudaStreamSynchronize(st);
   return r;
+}
+
+extern "C" ss_status stamp_set_table_limit(int64_t max_slots) {
+  if (max_slots < 0) SS_FAIL(SS_ERR_INVALID, "stamp_set_table_limit: negative bound");
+  g_table_limit.store(max_slots, std::memory_order_relaxed);
+  return SS_OK;
 }
 
 extern "C" void stamp_destroy(ss_stamp s) {

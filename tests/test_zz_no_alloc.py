@@ -36,12 +36,15 @@ def test_noalloc_equals_solve_on_two_calls(B, prec):
         ref2, _ = B.solve(s2, f2, 1e-12, 500, prec)
         out = torch.empty_like(f_on)
         out2 = torch.empty_like(f2)
+        torch.cuda.synchronize()
         for _ in range(2):
+            n0 = B.alloc_count()
             u, st = B.solve_noalloc(s, f_on, out, 1e-12, 500, prec)
-            assert st["status"] == "SS_OK"
-            assert rel_l2(u.cpu().numpy(), ref.cpu().numpy()) <= TOL
             # a different, smaller set in between: the shared array is re-initialised
             u2, _ = B.solve_noalloc(s2, f2, out2, 1e-12, 500, prec)
+            assert B.alloc_count() == n0, "solve_noalloc called an allocating routine"
+            assert st["status"] == "SS_OK"
+            assert rel_l2(u.cpu().numpy(), ref.cpu().numpy()) <= TOL
             assert rel_l2(u2.cpu().numpy(), ref2.cpu().numpy()) <= TOL
 
 
@@ -53,3 +56,17 @@ def test_noalloc_rejects_sets_beyond_its_workspace(B):
         with pytest.raises(SSError) as e:
             B.solve_noalloc(s, f_on, torch.empty_like(f_on), 1e-12, 500, "fp64")
         assert e.value.name == "SS_ERR_INVALID"
+
+
+def test_noalloc_checks_buffer_sizes(B):
+    # buffers shorter than |S| (or on another device) are rejected before any
+    # kernel could write past them
+    inst, af, av, ff, fv = stamp_inputs("cfg1")
+    with B.stamp_build(af, av, ff, inst.N) as s:
+        f_on, _ = s.scatter(ff, fv)
+        with pytest.raises(ValueError):
+            B.solve_noalloc(s, f_on, torch.empty(s.size - 1, dtype=torch.complex128, device="cuda"))
+        with pytest.raises(ValueError):
+            B.solve_noalloc(s, f_on[:-1].contiguous(), torch.empty_like(f_on))
+        with pytest.raises(ValueError):
+            B.solve(s, f_on, out=torch.empty(s.size - 1, dtype=torch.complex128, device="cuda"))
