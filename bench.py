@@ -1,22 +1,25 @@
 """Benchmark of the sparse spectral method's hot path on one GB300 (or N replicas).
 
-Workload (default): the d = 10 plain-FP64 configuration - a with 10 cosines in
-[-8,8]^10 (s_a = 21), manufactured u with 20 +-pairs, f_hat = L[a_hat] u_hat
-(|supp f_hat| = 840), N = 3 (|S| = 334,440, 2.51e6 operator nonzeros), CBC
-lattice with M = 10^6.  Synthetic, seeded (workloads.make_cfg2).  Secondary
-sections: the d = 100 workload (FP32 sampling and FFT at M = 2^26 + 15, |S| =
-1.15e6, FP32-refined solve) and the 512-instance batched solve (persistent,
-graph-replayed) against a loop of single solves.
+Headline workload (the d = 100 configuration): a = 1 + 20 cosines whose
+frequencies have 3 nonzero coordinates in [-4, 4] (s_a = 41, sum|c| = 0.5),
+f = 50 sine/cosine pairs of the same form (|supp f| = 100), N = 3
+(|S| = 1,152,100, 7.56e6 operator nonzeros), random rank-1 lattice with the
+7-smooth M = 2^26.  Synthetic, seeded (workloads.make_cfg5).
 
-One step = the whole path: CBC lattice choice, sft_recover(a), sft_recover(f)
-(lattice sampling + length-M FFT + bin extraction), stamp_build (S^3 and the
-neighbour table), right-hand side on S, FP64 CG solve to 1e-12.
+One step = one sparse_spectral_solve call, the whole path at FP64 grade:
+lattice choice and its reconstructing check, recovery of a and f (sampling by
+the double-float sparse evaluation, one pruned double-float transform),
+stamping set S^3 with its neighbour table, right-hand side on S, FP64 CG to
+relative residual 1e-12 (error against the oracle below 1e-10).
 
-Metric: stamped Galerkin nonzeros per second = nnz(L) x operator applications in
-the step / step time.  Also reported: time to solution of the FP64 and the
-FP32-refined solves (solve only) with their errors against the exact
-(manufactured) solution, per-stage times, the roofline of the dominant kernel,
-and the CPU oracle timed on a bounded sample.
+Metric: stamped Galerkin nonzeros per second = nnz(L) x operator applications
+in the step / step time.  Also reported: solve-only time to solution (FP64,
+FP32-refined, double-float) with each result's residual against the oracle's
+operator on sampled rows, the same workload as configured with FP32 sampling
+and FFT, the d = 10, multiscale d = 3 and batched (512 instances) workloads
+with their errors against the oracle, the roofline of the step's dominant
+kernel (timed live with CUDA events by the library's kernel timing), measured
+FP64/FP32/gather rates, and the CPU oracle timed on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -28,7 +31,9 @@ for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
 import argparse
+import ctypes
 import json
+import math
 import statistics
 import subprocess
 import sys
@@ -44,16 +49,22 @@ import workloads as W  # noqa: E402
 
 L2_BYTES = 129 * 2**20
 FLUSH_BYTES = 512 * 2**20
+TOL = 1e-12                  # relative residual of the headline solve
+ORACLE_ROWS = 2000           # random rows of the oracle's residual check (plus every row of supp f)
+CPU_SAMPLE_ROWS = 20000      # rows of the CPU baseline's timed operator sample
+WORKLOAD = ("cfg5: d=100, a = 1 + 20 cosines with 3 nonzeros in [-4,4] (s_a=41), f = 50 pairs of the same form "
+            "(|supp f|=100), N=3, |S|=1152100, random rank-1 lattice M=2^26 (7-smooth); FP64 recovery "
+            "(double-float sparse evaluation + pruned transform), FP64 CG to relative residual 1e-12")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the d=100 and batched sections")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle legs (CPU baseline, errors)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--apply-only", action="store_true",
                     help="run only the galerkin_apply section and print it (profiling the operator kernels)")
     return ap.parse_args()
@@ -64,6 +75,9 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+# ------------------------------------------------------------------ clocks
 
 
 # ------------------------------------------------------------------ clocks
@@ -118,37 +132,244 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+
+
+# ------------------------------------------------------------------ rates
+
+def measure_rates():
+    """FP64 and FP32 multiply-add throughput and random-gather rates of this GPU
+    (the microbenchmarks of libss_peaks.so, CUDA events, best of 3): the
+    denominators of the ALU- and gather-bound rooflines, which the copy and
+    GEMM peaks do not cover."""
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2302_00752_gb300", "libss_peaks.so"))
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.peak_fma.argtypes = [ctypes.c_int, dp, dp]
+    lib.peak_gather.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, dp, dp]
+    out = {}
+    f64, f32 = ctypes.c_double(), ctypes.c_double()
+    if lib.peak_fma(3, ctypes.byref(f64), ctypes.byref(f32)) == 0:
+        out["fp64_tflops"] = f64.value
+        out["fp32_tflops"] = f32.value
+    for rb, ws, key in ((8, 64 << 20, "l2_gather8"), (16, 64 << 20, "l2_gather16"), (32, 64 << 20, "l2_gather32"),
+                        (32, 4 << 30, "hbm_gather32")):
+        g, r = ctypes.c_double(), ctypes.c_double()
+        if lib.peak_gather(rb, ws, 3, ctypes.byref(g), ctypes.byref(r)) == 0:
+            out[key] = {"GBs": g.value, "Grecords_s": r.value, "Grequests_s": r.value * (2 if rb == 32 else 1)}
+    out["how"] = ("libss_peaks.so: 8 independent FMA chains per thread (4 blocks of 1024 threads per SM); random "
+                  "gathers of 8/16/32-byte records (two 16-byte loads for 32) bypassing L1, from a 64 MB (L2) or "
+                  "4 GB (HBM) working set; best of 3 launches between CUDA events")
+    return out
+
+
+# ------------------------------------------------------- roofline models
+#
+# The recovery kernels are double-float arithmetic on the FP32 pipes: their
+# algorithmic work is the FP32 instruction count of the double-float
+# operations the transform performs (df.cuh, dfc.cuh): add/subtract 11,
+# product 7, dot product of two pairs 19, multiply-add 15; complex add 22,
+# complex product 38.  Loads, stores and index arithmetic are not counted.
+
+DF_ADD, DF_MUL, DF_DOT2, DF_FMA = 11, 7, 19, 15
+C_ADD, C_MUL = 2 * DF_ADD, 2 * DF_DOT2
+
+
+def radices_py(L):
+    out = []
+    for R in (7, 5, 3, 8, 4, 2):
+        while L > 1 and L % R == 0:
+            out.append(R)
+            L //= R
+    return out if L == 1 else None
+
+
+def butterfly_instr(R, twiddled):
+    if R == 2:
+        d = 2 * C_ADD
+    elif R == 4:
+        d = 8 * C_ADD
+    elif R == 8:
+        d = 2 * 8 * C_ADD + 2 * (2 * DF_MUL + 2 * DF_ADD) + 8 * C_ADD
+    else:
+        H = (R - 1) // 2
+        d = 3 * H * C_ADD + H * (4 * H * DF_FMA + 2 * C_ADD)
+    return d + ((R - 1) * C_MUL if twiddled else 0)
+
+
+def pruned_split_py(M, n):
+    """The split M = P Q and tile width of fft_pruned.cu's pruned_split."""
+    best, S = 1e300, None
+    for P in range(8, 1025):
+        if M % P or M // P < 2:
+            continue
+        rad = radices_py(P)
+        if rad is None:
+            continue
+        c = math.log2(P) + max(n, 1) / P
+        if c < best:
+            best, S = c, (P, M // P, rad)
+    P, Q, rad = S
+    w = 1
+    while 2 * w * P <= 2048:
+        w *= 2
+    return P, Q, w, rad
+
+
+def pruned_instr(kind, M, n_split, n_work):
+    """Algorithmic FP32 instructions of one k_pr_eval (n_work entries) or
+    k_pr_fwd (n_work outputs) launch."""
+    P, Q, w, rad = pruned_split_py(M, n_split)
+    col, Ns = 0, 1
+    for R in rad:
+        col += (P // R) * butterfly_instr(R, Ns > 1)
+        Ns *= R
+    tiles = -(-Q // w)
+    if kind == "eval":   # per entry: table product and value product, then w multiply-adds
+        per_tile = w * col + n_work * 2 * C_MUL + n_work * w * (C_MUL + C_ADD)
+    else:                # per output: w multiply-adds, table product, twist, accumulate
+        per_tile = w * col + n_work * (w * (C_MUL + C_ADD) + 2 * C_MUL + C_ADD)
+    return tiles * per_tile, {"P": P, "Q": Q, "W": w, "radices": rad, "tiles": tiles}
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# ncu captures summarised under profiles/, with the hash of the kernel's
+# source file at capture time; a record whose source has changed since is not
+# used (traffic null).
+KERNEL_TRAFFIC = {}
+
+
+def traffic_record(kernel):
+    import hashlib
+    rec = KERNEL_TRAFFIC.get(kernel)
+    if not rec:
+        return None
+    try:
+        with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest()[:16] != rec["source_sha16"]:
+                return None
+    except OSError:
+        return None
+    return rec
+
+
+def roofline_of(name, ms, ctx, rates):
+    """Roofline entry of kernel `name` at `ms` per launch (CUDA events around
+    each launch on its stream, inside the timed steps)."""
+    out = {"kernel": name, "kernel_ms": ms}
+    rec = traffic_record(name)
+    if name in ("k_pr_eval", "k_pr_fwd"):
+        kind = "eval" if name == "k_pr_eval" else "fwd"
+        n_split, n_work = (ctx["entries_max"], ctx["entries"]) if kind == "eval" else (ctx["outputs"], ctx["outputs"])
+        instr, split = pruned_instr(kind, ctx["M"], n_split, n_work)
+        peak = rates["fp32_tflops"] / 2.0                  # FP32 instructions per second (x 1e12)
+        ach = instr / (ms / 1e3) / 1e12
+        out.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "T FP32 instructions/s", "frac": ach / peak,
+                    "algorithmic_instructions": instr, "split": split,
+                    "peak_source": "measured: FP32 FMA rate of libss_peaks.so (instructions = flops / 2)"})
+    elif name.startswith("k_solve"):
+        st = ctx["solve_stats"]
+        half, realc = bool(st.get("half_system")), bool(st.get("real_coefficients"))
+        nnz_p = ctx["nnz"] / 2 if half else ctx["nnz"]
+        rows_p = (ctx["size"] - (1 if ctx["zero_index"] >= 0 else 0)) // 2 if half else ctx["size"]
+        flops_nnz = 4.0 if realc else 8.0
+        flops = flops_nnz * nnz_p * st["applies"] + 30.0 * rows_p * st["inner_iters"]
+        peak = rates["fp64_tflops"] * 1e3
+        ach = flops / (ms / 1e3) / 1e9
+        out.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "GFLOP/s (FP64)", "frac": ach / peak,
+                    "algorithmic_flops": flops, "half_system": half, "real_coefficients": realc,
+                    "peak_source": "measured: FP64 FMA rate of libss_peaks.so"})
+    elif name == "k_neighbors":
+        lookups = ctx["size"] * ctx["s_a"]
+        req = lookups + ctx["nnz"] * ctx["key_words"] / 2.0   # one slot probe per lookup, the key in 16-byte loads per hit
+        peak = rates["l2_gather16"]["Grequests_s"]
+        ach = req / (ms / 1e3) / 1e9
+        out.update({"bound": "l2_gather", "achieved": ach, "peak": peak, "unit": "G gather requests/s",
+                    "frac": ach / peak, "lookups": lookups,
+                    "peak_source": "measured: random 16-byte gathers from a 64 MB working set (libss_peaks.so)"})
+    else:
+        out.update({"bound": None, "achieved": None, "peak": None, "frac": None})
+    out["traffic"] = rec["dram_bytes_per_launch"] if rec else None
+    out["traffic_note"] = (rec.get("note") if rec else "null: no ncu capture of this kernel's current source")
+    return out
+
+
 # ------------------------------------------------------------- oracle legs
 
-def oracle_setup(inst):
-    """The oracle's stamping set (BFS), explicit sparse operator, right-hand
-    side and Jacobi diagonal for the workload, from the exact coefficients."""
-    from oracle import pipeline as op
-    from oracle import solve as osol
-    from oracle import stamp as ostamp
-    from oracle import galerkin as ogal
+def exact_coefficients(trig):
     from oracle.sft import true_coefficients
-    a = true_coefficients(inst.a.freq, inst.a.coef)
-    af = np.array(list(a.keys()), np.int64)
-    av = np.array(list(a.values()), np.complex128)
-    ff, fv = op.forcing(inst)
-    keep = np.abs(fv) > 0
-    ff, fv = ff[keep], fv[keep]
+    c = true_coefficients(trig.freq, trig.coef)
+    keys = sorted(c)
+    return np.array(keys, np.int64).reshape(len(keys), -1), np.array([c[k] for k in keys], np.complex128)
+
+
+def oracle_setup_rows(inst):
+    """The oracle's stamping set of the headline workload (its own BFS from
+    the exact coefficients) and the index of its frequencies."""
+    from oracle import stamp as ostamp
+    af, av = exact_coefficients(inst.a)
+    ff, fv = exact_coefficients(inst.f)
     t0 = time.perf_counter()
     S, _ = ostamp.stamp_bfs(af, ff, inst.N)
-    L, nnz = ogal.galerkin_matrix(S, af, av)
-    b = op.rhs_on(S, ff, fv)
-    D = osol.jacobi_diag(S, av[~af.any(axis=1)][0])
-    return {"L": L, "b": b, "D": D, "nnz": nnz, "size": len(S), "seconds": time.perf_counter() - t0}
+    t1 = time.perf_counter()
+    idx = ostamp.index_map(S)
+    t2 = time.perf_counter()
+    return {"S": S, "idx": idx, "af": af, "av": av, "ff": ff, "fv": fv, "bfs_s": t1 - t0, "index_s": t2 - t1}
 
 
-def run_reference(args, inst, budget_s=120.0):
-    """The oracle as the reference arm: its operator is assembled once
-    (stamping BFS and explicit matrix, reported as setup), then every warm-up
-    and timed step runs the oracle's Jacobi PCG toward 1e-12 for at most as
-    many applications as keep the whole run within about two minutes (the
-    full solve takes 15); throughput = nonzeros x applications / PCG time."""
-    from oracle import solve as osol
+def row_nonzeros(o, rows):
+    """#{p in supp a_hat : k - p in S \\ {0}} for the rows k != 0 (the operator's
+    nonzeros in those rows; bookkeeping for the oracle's throughput)."""
+    S, idx, af = o["S"], o["idx"], o["af"]
+    steps = af.tolist()
+    n = 0
+    for i in rows:
+        k = S[i].tolist()
+        if not any(k):
+            continue
+        for p in steps:
+            l = tuple(x - y for x, y in zip(k, p))
+            if any(l) and l in idx:
+                n += 1
+    return n
+
+
+def oracle_cpu_sample(o, u, n_rows=CPU_SAMPLE_ROWS, seed=0):
+    """The oracle's operator (eq. GF row by row, oracle.galerkin.apply_rows)
+    on a seeded sample of rows of the headline set, timed on one core."""
+    from oracle import galerkin as ogal
+    rows = np.random.default_rng(seed).choice(len(o["S"]), n_rows, replace=False)
+    t0 = time.perf_counter()
+    ogal.apply_rows(o["S"], o["af"], o["av"], u, rows, idx=o["idx"])
+    dt = time.perf_counter() - t0
+    nnz = row_nonzeros(o, rows)
+    return nnz, dt
+
+
+def oracle_residuals(o, results):
+    """max_k |f_k - (L u)_k| / ||f||_2 with the oracle's operator and the exact
+    f, over every row of supp f and ORACLE_ROWS random rows, for each GPU
+    solution in `results` (name -> numpy vector on the canonical S)."""
+    from oracle import galerkin as ogal
+    S, idx = o["S"], o["idx"]
+    f_rows = np.array([idx[tuple(k)] for k in o["ff"].tolist()], np.int64)
+    rows = np.unique(np.concatenate([f_rows, np.random.default_rng(1).choice(len(S), ORACLE_ROWS, replace=False)]))
+    b = np.zeros(len(rows), np.complex128)
+    pos = {int(r): i for i, r in enumerate(rows)}
+    for r, v in zip(f_rows.tolist(), o["fv"]):
+        b[pos[r]] = v
+    fn = float(np.linalg.norm(o["fv"]))
+    out = {}
+    for name, u in results.items():
+        res = b - ogal.apply_rows(S, o["af"], o["av"], u, rows, idx=idx)
+        out[name] = float(np.abs(res).max() / fn)
+    return out, int(len(rows))
+
+
+def run_reference(args, ref_rows=10000):
+    """The oracle as the reference arm, on the headline workload: its stamping
+    BFS and frequency index are built once (reported as setup), then every
+    warm-up and timed step applies its operator (eq. GF row by row,
+    oracle.galerkin.apply_rows) to a vector on ref_rows seeded random rows of
+    S; throughput = the nonzeros of those rows / the time of the apply."""
     world, rank, _ = dist_env()
     if world > 1:
         import torch.distributed as dist
@@ -156,32 +377,33 @@ def run_reference(args, inst, budget_s=120.0):
         if rank != 0:
             dist.barrier()
             return
-    st = oracle_setup(inst)
-    t0 = time.perf_counter()
-    _, it_full, _ = osol.pcg(st["L"], st["b"], st["D"], 1e-12, max_iter=1)
-    per_apply = max(time.perf_counter() - t0, 1e-3) / 2.0          # one iteration + the initial residual
-    per_step = budget_s / max(1, args.steps + args.warmup)
-    cap = int(max(1, min(15, per_step / per_apply - 1)))
+    from oracle import galerkin as ogal
+    inst = W.make_cfg5(smooth=True)
+    o = oracle_setup_rows(inst)
+    rng = np.random.default_rng(2)
+    u = rng.standard_normal(len(o["S"])) + 1j * rng.standard_normal(len(o["S"]))
     for _ in range(args.warmup):
-        osol.pcg(st["L"], st["b"], st["D"], 1e-12, max_iter=cap)
-    tot, work = 0.0, 0.0
+        ogal.apply_rows(o["S"], o["af"], o["av"], u, rng.choice(len(o["S"]), ref_rows, replace=False), idx=o["idx"])
+    tot, work = 0.0, 0
     for _ in range(args.steps):
+        rows = rng.choice(len(o["S"]), ref_rows, replace=False)
         t0 = time.perf_counter()
-        _, it, _ = osol.pcg(st["L"], st["b"], st["D"], 1e-12, max_iter=cap)
+        ogal.apply_rows(o["S"], o["af"], o["av"], u, rows, idx=o["idx"])
         tot += time.perf_counter() - t0
-        work += st["nnz"] * (it + 1)
+        work += row_nonzeros(o, rows)
     value = work / tot
-    sample = (f"oracle Jacobi PCG (numpy/scipy, FP64) on the explicit operator of the full workload "
-              f"(|S| = {st['size']}, nnz = {st['nnz']}), at most {cap} of the 15 applications per step; "
-              f"operator assembly (BFS stamping + matrix) {st['seconds']:.1f} s once, not in the steps")
+    sample = (f"oracle operator (eq. GF row by row, numpy/Python FP64, 1 core) on {ref_rows} seeded random rows of "
+              f"the headline set per step (|S| = {len(o['S'])}); its BFS stamping ({o['bfs_s']:.1f} s) and index "
+              f"({o['index_s']:.1f} s) built once, not in the steps; the explicit matrix of the full set takes about "
+              f"4.5 minutes to assemble in the oracle, beyond a bounded sample")
     line = {
         "impl": "reference", "metric": "stamped Galerkin nnz/s", "value": value, "unit": "nnz/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "cfg2: d=10 plain FP64, s_a=21, |supp f|=840, N=3, |S|=334440"},
+        "config": {"workload": WORKLOAD},
         "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "setup_seconds": st["seconds"],
+        "setup_seconds": o["bfs_s"] + o["index_s"],
     }
     print(json.dumps(line))
     if world > 1:
@@ -215,6 +437,7 @@ def count_launches(fn):
         return None
 
 
+
 def load_peaks():
     """The measured copy bandwidth and GEMM peaks of this GPU type, when present."""
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
@@ -225,12 +448,8 @@ def load_peaks():
         return {}
 
 
-def fp64_peak_gflops(sm_mhz):
-    """FP64 ALU peak: one FP64 FMA per SM clock (GB300; the per-SM rate comes
-    from the ncu FP64-pipe counters of a pure-FP64 sampling kernel,
-    k_sample<double>) x 152 SMs x 2 flops x clock."""
-    return 152 * 2 * sm_mhz * 1e6 / 1e9
 
+# --------------------------------------------------------------- sections
 
 def d100_section(B, gp, flush, steps=2, smooth=False):
     """The d = 100 workload: FP32 samples and FFT at M = 2^26 + 15 (prime; with
@@ -239,7 +458,7 @@ def d100_section(B, gp, flush, steps=2, smooth=False):
     import torch
     inst = W.make_cfg5(smooth=smooth)
     prep = gp.prepare(inst)
-    out = {"workload": "cfg5: d=100, s_a=41, 50 f pairs, N=3, FP32 sampling/FFT, FP32-refined solve"
+    out = {"workload": "cfg5 as configured: d=100, s_a=41, 50 f pairs, N=3, FP32 sampling/FFT, FP32-refined solve"
                        + (", 7-smooth M" if smooth else ", prime M")}
     times = []
     for it in range(steps + 1):
@@ -276,6 +495,8 @@ def d100_section(B, gp, flush, steps=2, smooth=False):
         if it:
             fused_ms.append(e0.elapsed_time(e1))
         fst = r.stats
+        if it == steps:
+            u_last = r.u.cpu().numpy()
         r.stamp.destroy()
     step_ms = float(np.median(fused_ms))
     out.update({"M": int(prep.M), "stamp_size": stamp.size, "nnz": stamp.nnz,
@@ -302,7 +523,9 @@ def d100_section(B, gp, flush, steps=2, smooth=False):
     out["apply_fp32"] = {"ms": ms, "nnz_per_s": stamp.nnz / (ms / 1e3),
                          "note": "standalone FP32 galerkin_apply (one kernel), L2-warm back-to-back (host launch rate included)"}
     stamp.destroy()
+    out["_u"] = u_last   # for the error against the oracle (removed before printing)
     return out
+
 
 
 def apply_section(B, gp, flush, peaks, reps=10):
@@ -362,6 +585,7 @@ def apply_section(B, gp, flush, peaks, reps=10):
     return out
 
 
+
 def adr_section(B, gp, flush, Q=1000):
     """The three-dimensional advection-diffusion-reaction data (Remark ADR,
     Section "Three-dimensional exactly sparse advection-diffusion-reaction
@@ -406,6 +630,7 @@ def adr_section(B, gp, flush, Q=1000):
     return out
 
 
+
 def identify_section(B, gp, flush):
     """Support identification without candidates (d + 1 shifted samplings and
     FFTs) of the d = 10 workload's forcing: 840 frequencies on the
@@ -431,6 +656,7 @@ def identify_section(B, gp, flush):
             "ms": statistics.median(times), "samplings_and_ffts": inst.d + 1}
 
 
+
 def next_prime_py(n):
     def prime(m):
         if m < 2:
@@ -446,6 +672,7 @@ def next_prime_py(n):
     return n
 
 
+
 DF_OPS_PER_PAIR = 150   # ten double-float multiply-adds of 15 FP32 instructions per (term, point)
 
 
@@ -459,6 +686,7 @@ def multiscale_section(B, gp, flush, reps=5):
     res = gp.run(gp.prepare(inst), solve=False)
     st_ = res.stamp
     out = {"size": st_.size, "nnz": st_.nnz}
+    host_u = {}
     for tol in (1e-10, 1e-12):
         sols = {}
         for prec in ("fp64", "fp32"):
@@ -472,13 +700,16 @@ def multiscale_section(B, gp, flush, reps=5):
                 b.synchronize()
                 times.append(a.elapsed_time(b))
             sols[prec] = u
+            host_u[f"{'fp32_refined' if prec == 'fp32' else prec}@{tol:g}"] = u.cpu().numpy()
             out[f"{prec}@{tol:g}"] = {"time_to_solution_ms": statistics.median(times), "kernel_ms": stt["kernel_ms"],
                                       "applies": stt["applies"], "rel_residual": stt["rel_residual"],
                                       "half_system": stt["half_system"], "status": stt["status"]}
         out[f"rel_l2_fp32_vs_fp64@{tol:g}"] = float(torch.linalg.norm(sols["fp32"] - sols["fp64"]) /
                                                    torch.linalg.norm(sols["fp64"]))
     st_.destroy()
+    out["_u"] = host_u   # for the error against the oracle (removed before printing)
     return out
+
 
 
 def proxy_section(B, gp, flush, Q=1000):
@@ -527,6 +758,7 @@ def proxy_section(B, gp, flush, Q=1000):
     return out
 
 
+
 def batched_section(B, flush, n_inst=512, reps=3, world=1, rank=0):
     """The batched workload: 512 instances of uneven d, s_a and |S| (1e3..1e5),
     FP32-refined, in one persistent graph-replayed launch vs a loop of single
@@ -568,6 +800,10 @@ def batched_section(B, flush, n_inst=512, reps=3, world=1, rank=0):
         b.record()
         b.synchronize()
         lt.append(a.elapsed_time(b))
+    # solutions of a few instances across the size range, for the error against the oracle
+    order = sorted(range(len(stamps)), key=lambda i: stamps[i].size)
+    pick = sorted({order[int(round(q * (len(order) - 1)))] for q in (0.0, 0.33, 0.67, 1.0)})
+    subset = {i: {"inst": insts[i], "fp32_refined": us[i].cpu().numpy()} for i in pick}
     # the same batch in the plain FP64 form (graph, same tiles), for comparison
     batch.solve(fs, us, tol=1e-12, max_iter=500, precision="fp64", use_graph=True)
     ft = []
@@ -580,6 +816,8 @@ def batched_section(B, flush, n_inst=512, reps=3, world=1, rank=0):
         b.synchronize()
         ft.append(a.elapsed_time(b))
     fp64_ok = all(st["status"] == "SS_OK" for st in stats64)
+    for i in pick:
+        subset[i]["fp64"] = us[i].cpu().numpy()
     applies = sum(st["applies"] for st in stats)
     nnz_applied = sum(s.nnz * st["applies"] for s, st in zip(stamps, stats))
     ok = all(st["status"] == "SS_OK" for st in stats)
@@ -601,6 +839,8 @@ def batched_section(B, flush, n_inst=512, reps=3, world=1, rank=0):
            "all_converged": ok, "autotuned": cfg, "autotune_best_ms": best_ms, "setup_s": setup_s,
            "fp64_persistent_graph_ms_rank0": statistics.median(ft), "fp64_all_converged_rank0": fp64_ok,
            "fp32_refined_vs_fp64_speedup_rank0": statistics.median(ft) / statistics.median(bt)}
+    if rank == 0:
+        out["_subset"] = subset   # for the error against the oracle (removed before printing)
     batch.destroy()
     for s in stamps:
         s.destroy()
@@ -609,11 +849,100 @@ def batched_section(B, flush, n_inst=512, reps=3, world=1, rank=0):
 
 # ---------------------------------------------------------------- our path
 
+
+def cfg2_section(B, gp, flush, steps=5):
+    """The d = 10 plain-FP64 workload: a with 10 cosines in [-8,8]^10 (s_a =
+    21), manufactured u with 20 +-pairs, f_hat = L[a_hat] u_hat (|supp f| =
+    840), N = 3 (|S| = 334,440), CBC lattice M = 10^6: one sparse_spectral_solve
+    per step (FP64 recovery by the full double-float transform, FP64 CG to
+    1e-12), its error against the exact manufactured solution."""
+    import torch
+    inst = W.make_cfg2()
+    p = gp.prepare(inst)
+    times = []
+    for it in range(steps + 2):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        r = gp.run_fused(p, tol=1e-12, max_iter=1000, tau=1e-9, solve_precision="fp64")
+        b.record()
+        b.synchronize()
+        if r.stats["status"] != "SS_OK":
+            raise RuntimeError(f"d = 10 step failed: {r.stats}")
+        if it >= 2:
+            times.append(a.elapsed_time(b))
+        last = it == steps + 1
+        if last:
+            S, _ = r.stamp.export()
+            idx = {tuple(k): i for i, k in enumerate(S.cpu().numpy().tolist())}
+            exact = np.zeros(r.stamp.size, complex)
+            for k, v in zip(inst.u_freq.tolist(), inst.u_val):
+                exact[idx[tuple(k)]] = v
+            err = float(np.linalg.norm(r.u.cpu().numpy() - exact) / np.linalg.norm(exact))
+            size, nnz, st = r.stamp.size, r.stamp.nnz, r.stats
+        r.stamp.destroy()
+    ms = statistics.median(times)
+    return {"workload": "cfg2: d=10 plain FP64, s_a=21, manufactured u (20 pairs), |supp f|=840, N=3, CBC M=10^6",
+            "stamp_size": size, "nnz": nnz, "ms_per_step": ms, "nnz_per_s": nnz * st["applies"] / (ms / 1e3),
+            "applies": st["applies"], "rel_residual": st["rel_residual"],
+            "rel_l2_err_vs_exact_solution": err, "half_system": st["half_system"]}
+
+
+def errors_vs_oracle_solution(results, ref):
+    """Relative l2 and max-element errors of GPU solutions against the oracle's."""
+    out = {}
+    n_ref, m_ref = float(np.linalg.norm(ref)), float(np.abs(ref).max())
+    for name, u in results.items():
+        out[name] = {"rel_l2": float(np.linalg.norm(u - ref) / n_ref), "rel_max": float(np.abs(u - ref).max() / m_ref)}
+    return out
+
+
+def multiscale_oracle(inst):
+    """The oracle's solution of the multiscale workload (BFS stamping, explicit
+    operator, Jacobi PCG to 1e-14) from the exact coefficients."""
+    from oracle import pipeline as opipe
+    af, av = exact_coefficients(inst.a)
+    ff, fv = exact_coefficients(inst.f)
+    t0 = time.perf_counter()
+    ref = opipe.solve_recovered(inst.N, af, av, ff, fv, tol=1e-14)
+    return ref, time.perf_counter() - t0
+
+
+def batched_oracle_errors(subset):
+    """Errors of a few batched solutions (FP32-refined and FP64, one graph-
+    replayed launch each) against the oracle's PCG solution of the same
+    instance from the exact coefficients."""
+    from oracle import pipeline as opipe
+    out = {}
+    for i, rec in subset.items():
+        inst = rec["inst"]
+        af, av = exact_coefficients(inst.a)
+        ff, fv = exact_coefficients(inst.f)
+        ref = opipe.solve_recovered(inst.N, af, av, ff, fv, tol=1e-14)
+        out[f"instance {i} (|S| = {len(ref.S)}, d = {inst.d})"] = errors_vs_oracle_solution(
+            {k: rec[k] for k in ("fp32_refined", "fp64")}, ref.u)
+    return {"metric": "relative l2 / max-element error against the oracle's PCG solution", "results": out}
+
+
+def key_words(d, maxabs):
+    """Words per packed key (the layout rule of stamp.cu's make_layout)."""
+    b = 1
+    while (1 << (b - 1)) - 1 < maxabs:
+        b += 1
+    fpw = 64 // (b + 1)
+    w = -(-d // fpw)
+    wt = 1
+    while wt < w:
+        wt <<= 1
+    return 12 if 8 < w <= 12 else wt
+
+
+# ---------------------------------------------------------------- our path
+
 def main():
     args = parse()
-    inst = W.make_cfg2()
     if args.impl == "reference":
-        run_reference(args, inst)
+        run_reference(args)
         return
     import torch
     if args.apply_only:
@@ -631,20 +960,22 @@ def main():
     from paper_2302_00752_gb300 import pipeline as gp
 
     dev = torch.device("cuda", local)
-    prep = gp.prepare(inst)                         # manufactured f_hat built by the library (untimed)
+    rates = measure_rates()
+    inst = W.make_cfg5(smooth=True)
+    prep = gp.prepare(inst)
+    prep.sft_precision = "fp64"
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-
-    u_buf = torch.empty(1 << 20, dtype=torch.complex128, device=dev)   # solution buffer, reused by every step
+    u_buf = torch.empty(1 << 21, dtype=torch.complex128, device=dev)   # solution buffer, reused by every step
 
     def step(p, keep=False):
         """One pass of Algorithm 1 through the single library call
         (sparse_spectral_solve): the timed step."""
-        r = gp.run_fused(p, tol=1e-12, max_iter=1000, tau=1e-9, solve_precision="fp64", out=u_buf)
+        r = gp.run_fused(p, tol=TOL, max_iter=1000, tau=1e-9, solve_precision="fp64", out=u_buf)
         st = r.stats
         if st["status"] != "SS_OK":
             raise RuntimeError(f"solve failed: {st}")
         out = {"nnz": r.stamp.nnz, "size": r.stamp.size, "zero_index": r.stamp.zero_index, "applies": st["applies"],
-               "iters": st["inner_iters"], "times": {"solve_kernel": st["kernel_ms"]}, "u": r.u, "stats": st}
+               "iters": st["inner_iters"], "u": r.u, "stats": st}
         if keep:
             out["stamp"] = r.stamp
         else:
@@ -654,8 +985,7 @@ def main():
     def staged_step(p, keep=False):
         """The same stages called one by one from Python, with CUDA events
         between them (the per-stage breakdown; not the timed step)."""
-        t = {}
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         ev[0].record()
         p.z, p.M = gp.choose_lattice(p.extra["lattice"], p.cand)
         ev[1].record()
@@ -665,16 +995,12 @@ def main():
         stamp = B.stamp_build(af, av, ff, inst.N)
         f_on, _ = stamp.scatter(ff, fv, count_outside=False)
         ev[3].record()
-        u, st = B.solve(stamp, f_on, 1e-12, 1000, "fp64")
+        u, st = B.solve(stamp, f_on, TOL, 1000, "fp64")
         ev[4].record()
         ev[4].synchronize()
-        t["lattice"] = ev[0].elapsed_time(ev[1])
-        t["sft"] = ev[1].elapsed_time(ev[2])
-        t["stamp"] = ev[2].elapsed_time(ev[3])
-        t["solve"] = ev[3].elapsed_time(ev[4])
+        t = {k: ev[i].elapsed_time(ev[i + 1]) for i, k in enumerate(("lattice", "sft", "stamp", "solve"))}
         t["solve_kernel"] = st["kernel_ms"]
-        out = {"nnz": stamp.nnz, "size": stamp.size, "applies": st["applies"], "iters": st["inner_iters"],
-               "times": t, "u": u, "stats": st}
+        out = {"times": t}
         if keep:
             out["stamp"], out["f_on"] = stamp, f_on
         else:
@@ -690,9 +1016,10 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    step_ms, work, stage = [], 0, {}
+    B.profile(True)                                  # per-kernel CUDA events inside the timed steps
+    step_ms, work = [], 0
     for _ in range(args.steps):
-        flush.zero_()                               # L2 flushed between steps
+        flush.zero_()                                # L2 flushed between steps
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         r = step(prep)
@@ -700,11 +1027,11 @@ def main():
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         work += r["nnz"] * r["applies"]
-        for k, v in r["times"].items():
-            stage.setdefault(k, []).append(v)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
+    totals = B.profile_totals()
+    B.profile(False)
     clocks.stop()
     total_ms = sum(step_ms)
     if world > 1:
@@ -712,67 +1039,52 @@ def main():
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(tt.item())
     value = world * work / (total_ms / 1e3)
+    u_step = r["u"].cpu().numpy()
+    nnz, size, applies = r["nnz"], r["size"], r["applies"]
 
     # per-stage breakdown from the staged form (same kernels, Python between the stages)
-    staged_ms = []
-    for _ in range(max(3, args.steps)):
+    stage, staged_ms = {}, []
+    for _ in range(3):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        r = staged_step(prep)
+        sr = staged_step(prep)
         e1.record()
         e1.synchronize()
         staged_ms.append(e0.elapsed_time(e1))
-        for k, v in r["times"].items():
-            if k != "solve_kernel":
-                stage.setdefault(k, []).append(v)
+        for k, v in sr["times"].items():
+            stage.setdefault(k, []).append(v)
 
-    # solve-only time to solution, FP64 vs FP32-refined, errors against the exact solution
+    # solve-only time to solution: FP64, FP32-refined and double-float CG
     keep = staged_step(prep, keep=True)
     stamp, f_on = keep["stamp"], keep["f_on"]
-    S, lv = stamp.export()
-    S = S.cpu().numpy()
-    # stamping throughput: every set member of levels 0..N-1 tries every step of supp a_hat
-    counts = np.bincount(lv.cpu().numpy().astype(np.int64), minlength=inst.N + 1)
-    af = np.asarray(inst.a.freq, np.int64)
-    s_a = len({tuple(k) for k in np.vstack([af, -af]).tolist()})   # |supp a_hat| of the real coefficient
-    cand = int(sum(counts[n] for n in range(inst.N)) * s_a)
-    stamp_stats = {"level_sizes": counts.tolist(), "candidates": cand,
-                   "candidates_per_s": cand / (statistics.median(stage["stamp"]) / 1e3),
-                   "stamp_ms": statistics.median(stage["stamp"]),
-                   "note": "whole stamp_build + scatter call (levels, hash, neighbour table, coefficients)"}
-    idx = {tuple(k): i for i, k in enumerate(S.tolist())}
-    exact = np.zeros(len(S), complex)
-    for k, v in zip(inst.u_freq.tolist(), inst.u_val):
-        exact[idx[tuple(k)]] = v
-    tts = {}
-    for prec in ("fp64", "fp64_full", "fp32", "df64", "fp64@1e-10", "fp32@1e-10"):
+    tts, sols = {}, {}
+    for prec, tol_p in (("fp64", 1e-12), ("fp32", 1e-12), ("df64", 1e-12), ("fp64", 1e-10), ("fp32", 1e-10)):
         times, kern = [], []
-        stamp.set_symmetry(prec != "fp64_full")        # fp64_full: the full system, for comparison
-        base, tol_p = (prec.split("@")[0], 1e-10) if "@" in prec else (prec, 1e-12)
         for _ in range(5):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            u, st = B.solve(stamp, f_on, tol_p, 1000, "fp64" if base == "fp64_full" else base)
+            u, st = B.solve(stamp, f_on, tol_p, 1000, prec)
             b.record()
             b.synchronize()
             times.append(a.elapsed_time(b))
             kern.append(st["kernel_ms"])
-        uu = u.cpu().numpy()
-        err = float(np.linalg.norm(uu - exact) / np.linalg.norm(exact))
-        tts[prec] = {"time_to_solution_ms": statistics.median(times), "kernel_ms": statistics.median(kern),
-                     "rel_l2_err_vs_exact": err, "rel_residual": st["rel_residual"], "applies": st["applies"],
-                     "outer_iters": st["outer_iters"], "inner_iters": st["inner_iters"],
-                     "half_system": st["half_system"],
+        name = f"{'fp32_refined' if prec == 'fp32' else prec}@{tol_p:g}"
+        sols[name] = u.cpu().numpy()
+        tts[name] = {"time_to_solution_ms": statistics.median(times), "kernel_ms": statistics.median(kern),
+                     "rel_residual": st["rel_residual"], "applies": st["applies"], "outer_iters": st["outer_iters"],
+                     "inner_iters": st["inner_iters"], "half_system": st["half_system"],
                      "nnz_per_s": stamp.nnz * st["applies"] / (statistics.median(kern) / 1e3)}
+    tts["fp32_refined_vs_fp64_speedup@1e-12"] = (tts["fp64@1e-12"]["time_to_solution_ms"] /
+                                                 tts["fp32_refined@1e-12"]["time_to_solution_ms"])
+    stamp.destroy()
 
     # end to end through the C ABI with host buffers: H2D of the data, D2H of u
     host = {k: getattr(prep, k).cpu().pin_memory() for k in ("a_freq", "a_coef", "f_freq", "f_coef", "cand")}
     h2d = sum(t.numel() * t.element_size() for t in host.values())
-    u_host = torch.empty(stamp.size, dtype=torch.complex128).pin_memory()
+    u_host = torch.empty(size, dtype=torch.complex128).pin_memory()
     d2h = u_host.numel() * u_host.element_size()
-    stamp.destroy()
     e2e_ms, e2e_work = [], 0
     for _ in range(args.steps):
         flush.zero_()
@@ -781,137 +1093,120 @@ def main():
         p2 = gp.Prepared(prep.d, prep.N, *[host[k].to(dev, non_blocking=True) for k in
                                            ("a_freq", "a_coef", "f_freq", "f_coef", "cand")],
                          sft_precision="fp64", solve_precision="fp64", extra=prep.extra)
-        r = step(p2)
-        u_host.copy_(r["u"], non_blocking=True)
+        r2 = step(p2)
+        u_host.copy_(r2["u"], non_blocking=True)
         b.record()
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
-        e2e_work += r["nnz"] * r["applies"]
+        e2e_work += r2["nnz"] * r2["applies"]
     e2e_value = world * e2e_work / (sum(e2e_ms) / 1e3)
 
-    # roofline of the dominant kernel: the persistent FP64 CG (FP64 ALU bound;
-    # algorithmic flops: 8 per processed nonzero and application (4 FP64 FMAs
-    # of the complex product), 4 when the entry coefficients are real, and 30
-    # per processed row and CG iteration for the vector updates and the three
-    # inner products).  With the Hermitian half system the CG processes the
-    # rows k >lex 0 and their nonzeros, half of S and half of L's nonzeros
-    # (symmetric S; the zero row stores none).
-    med = {k: statistics.median(v) for k, v in stage.items()}
-    nnz, size, iters = r["nnz"], r["size"], r["iters"]
-    applies = r["applies"]
-    half = bool(r["stats"].get("half_system"))
-    realc = bool(r["stats"].get("real_coefficients"))
-    nnz_p = nnz / 2 if half else nnz
-    rows_p = (size - (1 if r["zero_index"] >= 0 else 0)) // 2 if half else size
-    # real entry coefficients (a_hat real): 2 FP64 FMAs per nonzero, else 4
-    flops_nnz = 4.0 if realc else 8.0
-    solve_flops = flops_nnz * nnz_p * applies + 30.0 * rows_p * iters
-    kms = med["solve_kernel"]
-    clk = clocks.summary()
-    sm_max = clk.get("sm_max_mhz") or 2070.0
-    peak64 = fp64_peak_gflops(sm_max)
-    achieved = solve_flops / (kms / 1e3) / 1e9
-    # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
-    # the ncu capture in profiles/k_solve_fp64_half_system_cfg2.md, taken on
-    # this kernel for this workload (half system, real coefficients)
-    traffic = 41.355008e6 + 2.038272e6 if (half and realc) else None
-    roofline = {"kernel": "k_solve<0> (persistent FP64 CG)", "bound": "alu", "achieved": achieved, "peak": peak64,
-                "unit": "GFLOP/s (FP64)", "frac": achieved / peak64, "traffic": traffic,
-                "traffic_unit": "DRAM bytes per launch (one ncu capture of this kernel on this workload)",
-                "peak_source": "derived: 1 FP64 FMA/clk/SM (ncu FP64-pipe counters) x 152 SMs x 2 x sm_max_mhz",
-                "flops_per_launch": solve_flops, "kernel_ms": kms, "half_system": half,
-                "real_coefficients": realc, "flops_per_processed_nnz": flops_nnz,
-                "processed_nnz": nnz_p, "processed_rows": rows_p}
+    # kernels of the timed steps (library kernel timing) and the dominant one's roofline
+    step_med = statistics.median(step_ms)
+    kernels = {k: {"launches_per_step": c / args.steps, "ms_per_launch": t / c, "ms_per_step": t / args.steps,
+                   "share_of_step": t / args.steps / step_med} for k, (c, t) in totals.items() if c}
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"]) if kernels else None
+    maxabs_f = int(np.abs(np.asarray(inst.f.freq)).max())
+    maxabs_a = int(np.abs(np.asarray(inst.a.freq)).max())
+    n_cand = int(prep.cand.shape[0])
+    ctx = {"M": int(prep.M), "entries": 2 * (len(inst.a.freq) + len(inst.f.freq)) - 1,
+           "entries_max": 2 * (len(inst.a.freq) + len(inst.f.freq)), "outputs": 2 * n_cand, "size": size,
+           "nnz": nnz, "zero_index": r["zero_index"], "s_a": 2 * len(inst.a.freq) - 1,
+           "key_words": key_words(inst.d, maxabs_f + (inst.N + 1) * maxabs_a), "solve_stats": r["stats"]}
+    roofline = roofline_of(dom, kernels[dom]["ms_per_launch"], ctx, rates) if dom else None
+    if roofline:
+        roofline["share_of_step"] = kernels[dom]["share_of_step"]
+    others = {k: roofline_of(k, v["ms_per_launch"], ctx, rates) for k, v in kernels.items()
+              if k != dom and k in ("k_pr_eval", "k_pr_fwd", "k_solve<0>", "k_neighbors")}
     launches_per_step = count_launches(lambda: step(prep))
     gpu_launches = launches_per_step * args.steps if launches_per_step is not None else None
 
     extra = {}
+    u_fp32cfg = None
     if not args.no_extra:
         if rank == 0:
-            try:
-                extra["d100"] = d100_section(B, gp, flush)
-            except Exception as e:  # reported, not hidden
-                extra["d100"] = {"error": repr(e)}
-            try:
-                extra["d100_smooth_M"] = d100_section(B, gp, flush, smooth=True)
-            except Exception as e:
-                extra["d100_smooth_M"] = {"error": repr(e)}
-            try:
-                extra["apply"] = apply_section(B, gp, flush, load_peaks())
-            except Exception as e:
-                extra["apply"] = {"error": repr(e)}
-            try:
-                extra["identify"] = identify_section(B, gp, flush)
-            except Exception as e:
-                extra["identify"] = {"error": repr(e)}
-            try:
-                extra["adr"] = adr_section(B, gp, flush)
-            except Exception as e:
-                extra["adr"] = {"error": repr(e)}
-            try:
-                extra["multiscale"] = multiscale_section(B, gp, flush)
-            except Exception as e:
-                extra["multiscale"] = {"error": repr(e)}
-            try:
-                extra["proxy"] = proxy_section(B, gp, flush)
-            except Exception as e:
-                extra["proxy"] = {"error": repr(e)}
+            for key, fn in (("cfg5_fp32_as_configured", lambda: d100_section(B, gp, flush, smooth=True)),
+                            ("cfg5_fp32_prime_M", lambda: d100_section(B, gp, flush, smooth=False)),
+                            ("cfg2", lambda: cfg2_section(B, gp, flush)),
+                            ("apply", lambda: apply_section(B, gp, flush, load_peaks())),
+                            ("multiscale", lambda: multiscale_section(B, gp, flush)),
+                            ("identify", lambda: identify_section(B, gp, flush)),
+                            ("adr", lambda: adr_section(B, gp, flush)),
+                            ("proxy", lambda: proxy_section(B, gp, flush))):
+                try:
+                    extra[key] = fn()
+                except Exception as e:  # reported, not hidden
+                    extra[key] = {"error": repr(e)}
+            u_fp32cfg = extra.get("cfg5_fp32_as_configured", {}).pop("_u", None)
+            extra.get("cfg5_fp32_prime_M", {}).pop("_u", None)
         if world > 1:
             torch.distributed.barrier()
         extra["batched"] = batched_section(B, flush, world=world, rank=rank)
 
-    cpu = None
+    cpu, oracle_err = None, {}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle import solve as osol
-        o = oracle_setup(inst)
-        t0 = time.perf_counter()
-        _, it, _ = osol.pcg(o["L"], o["b"], o["D"], 1e-12)
-        dt = time.perf_counter() - t0
-        cpu = {"value": o["nnz"] * (it + 1) / dt, "unit": "nnz/s", "cores": 1, "kind": "oracle",
-               "sample": f"oracle Jacobi PCG to 1e-12 (numpy/scipy FP64, {it + 1} applications, {dt:.2f} s) on "
-                         f"the explicit operator of the full workload; its assembly (BFS stamping + matrix, "
-                         f"{o['seconds']:.1f} s) and the DFT recovery are not in the time",
-               "full_path_nnz_per_s": o["nnz"] * (it + 1) / (dt + o["seconds"])}
-        try:
-            from oracle import cpu_pcg
-            t0 = time.perf_counter()
-            n_cores = len(os.sched_getaffinity(0))
-            _, it_c = cpu_pcg.pcg(o["L"], o["b"], o["D"], 1e-12, n_threads=n_cores)
-            dt_c = time.perf_counter() - t0
-            cpu["all_cores"] = {"value": o["nnz"] * (it_c + 1) / dt_c, "unit": "nnz/s", "cores": n_cores,
-                                "kind": "oracle (C, OpenMP)",
-                                "sample": f"the same Jacobi PCG in C with OpenMP row-parallel products on the same "
-                                          f"CSR operator ({it_c + 1} applications, {dt_c:.2f} s)"}
-        except Exception as e:
-            cpu["all_cores"] = {"error": repr(e)}
+        o = oracle_setup_rows(inst)
+        if len(o["S"]) != size:
+            raise RuntimeError(f"oracle stamping set has {len(o['S'])} frequencies, the GPU's {size}")
+        nnz_s, dt = oracle_cpu_sample(o, u_step)
+        cpu = {"value": nnz_s / dt, "unit": "nnz/s", "cores": 1, "kind": "oracle",
+               "sample": (f"oracle operator (eq. GF row by row, numpy/Python FP64) on {CPU_SAMPLE_ROWS} seeded "
+                          f"random rows of the headline set ({nnz_s} nonzeros, {dt:.2f} s, 1 core); its BFS "
+                          f"stamping ({o['bfs_s']:.1f} s) and frequency index ({o['index_s']:.1f} s) not in the "
+                          f"time; the oracle's O(M |I|) DFT recovery and its explicit matrix (about 4.5 min to "
+                          f"assemble) are beyond a bounded sample")}
+        res_in = {"fp64 step (sparse_spectral_solve)": u_step}
+        res_in.update(sols)
+        if u_fp32cfg is not None:
+            res_in["fp32 sampling and FFT (as configured)"] = u_fp32cfg
+        res, n_rows = oracle_residuals(o, res_in)
+        oracle_err["cfg5"] = {"metric": "max_k |f_k - (L u)_k| / ||f||_2 with the oracle's operator and exact f",
+                              "rows": n_rows, "results": res}
+        del o
+        ms_ = extra.get("multiscale", {})
+        ms_u = ms_.pop("_u", None) if isinstance(ms_, dict) else None
+        if ms_u:
+            ref, secs = multiscale_oracle(W.make_cfg3())
+            oracle_err["cfg3"] = {"metric": "relative l2 / max-element error against the oracle's PCG solution",
+                                  "oracle_seconds": secs, "results": errors_vs_oracle_solution(ms_u, ref.u)}
+        bt = extra.get("batched", {})
+        sub = bt.pop("_subset", None) if isinstance(bt, dict) else None
+        if sub:
+            oracle_err["cfg4_subset"] = batched_oracle_errors(sub)
+    else:
+        for sec in ("multiscale", "batched", "cfg5_fp32_as_configured"):
+            if isinstance(extra.get(sec), dict):
+                extra[sec].pop("_u", None)
+                extra[sec].pop("_subset", None)
 
     if rank == 0:
+        clk = clocks.summary()
         line = {
             "metric": "stamped Galerkin nnz/s", "value": value, "unit": "nnz/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "cfg2: d=10 plain FP64, s_a=21, manufactured u (20 pairs), |supp f|=840, N=3",
-                       "stamp_size": size, "nnz": nnz, "M": int(prep.M), "l2_flush": True,
+            "config": {"workload": WORKLOAD, "stamp_size": size, "nnz": nnz, "M": int(prep.M), "applies": applies,
+                       "l2_flush": True, "tol": TOL,
                        "nnz_counting": ("value counts the nonzeros of L_{N,s} per operator application; the FP64 "
                                         "CG runs the Hermitian half system (rows k >lex 0, half of the stored "
-                                        "nonzeros per application, the rest by u_{-k} = conj(u_k)) when "
-                                        "half_system is true; processed_nnz_per_s counts the nonzeros it reads"),
+                                        "nonzeros per application, the rest by u_{-k} = conj(u_k))"),
                        "parallelism": "replicas" if world > 1 else "single"},
             "e2e": {"value": e2e_value, "unit": "nnz/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": sum(e2e_ms) / len(e2e_ms)},
-            "breakdown_ms": med,
+            "breakdown_ms": {k: statistics.median(v) for k, v in stage.items()},
             "staged_ms_per_step": statistics.median(staged_ms),
-            "step_form": ("timed step: sparse_spectral_solve (one library call for lattice, both SFTs, stamp, "
-                          "right-hand side, solve); breakdown_ms and staged_ms_per_step from the same stages "
-                          "called one by one from Python with events between them"),
-            "processed_nnz_per_s": value * (nnz_p / nnz if nnz else 1.0),
-            "half_system": half,
+            "step_form": ("timed step: sparse_spectral_solve (one library call for lattice, recovery of a and f, "
+                          "stamp, right-hand side, solve); breakdown_ms and staged_ms_per_step from the same "
+                          "stages called one by one from Python with events between them"),
             "solve_only": tts,
-            "stamp": stamp_stats,
+            "kernels": kernels,
             "roofline": roofline,
+            "roofline_other_kernels": others,
+            "rates": rates,
             "gpu_launches": gpu_launches,
             "gpu_launches_per_step": launches_per_step,
             "cpu_baseline": cpu,
+            "error_vs_oracle": oracle_err,
             "clocks": clk,
         }
         line.update(extra)

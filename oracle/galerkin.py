@@ -68,11 +68,13 @@ def galerkin_matrix(S, a_freq, a_val):
     return L, nnz
 
 
-def apply_rows(S, a_freq, a_val, u, rows):
+def apply_rows(S, a_freq, a_val, u, rows, idx=None):
     """(L u)_k for the selected row indices only (same entries as
-    ``galerkin_matrix``), for spot checks on sets too large to assemble."""
+    ``galerkin_matrix``), for spot checks on sets too large to assemble.
+    ``idx`` may pass ``index_map(S)`` when several calls share one set."""
     S = np.asarray(S, np.int64)
-    idx = index_map(S)
+    if idx is None:
+        idx = index_map(S)
     a = _a_dict(a_freq, a_val)
     out = np.zeros(len(rows), np.complex128)
     for o, i in enumerate(rows):

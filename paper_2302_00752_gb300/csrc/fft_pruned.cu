@@ -52,9 +52,11 @@ __global__ void k_tl_table(int64_t M, int b, int64_t n1, float4* t0, float4* t1)
   }
 }
 
-// One radix-R Stockham pass over the W columns (length P, column stride CS).
+// One radix-R Stockham pass over the W = 2^wsh columns (length P, column
+// stride CS).  j / Ns is formed as umulhi(j, ceil(2^32 / Ns)), exact for
+// j, Ns < 2^16.
 template <int R, int SIGN>
-__device__ __forceinline__ void mpass(const float4* __restrict__ a, float4* __restrict__ b, int P, int W, int CS,
+__device__ __forceinline__ void mpass(const float4* __restrict__ a, float4* __restrict__ b, int P, int wsh, int CS,
                                       int Ns, const float4* __restrict__ tw) {
   constexpr int NC = R == 8 ? 1 : (R - 1) / 2;
   C4 cs[NC > 0 ? NC : 1];
@@ -62,12 +64,15 @@ __device__ __forceinline__ void mpass(const float4* __restrict__ a, float4* __re
   for (int m = 0; m < NC; ++m) cs[m] = ld(tw[(P / R) * (m + 1)]);
   const int nb = P / R;
   const int tstride = P / (Ns * R);
-  const int total = W * nb;
+  const int total = nb << wsh;
+  const unsigned wmask = (1u << wsh) - 1u;
+  const unsigned nsm = Ns > 1 ? 0xffffffffu / (unsigned)Ns + 1u : 0u;
   for (int u = threadIdx.x; u < total; u += blockDim.x) {
-    const int c = u % W, j = u / W;
+    const int c = (int)((unsigned)u & wmask), j = u >> wsh;
     const float4* ac = a + c * CS;
     float4* bc = b + c * CS;
-    const int k = j % Ns;
+    const int jq = Ns > 1 ? (int)__umulhi((unsigned)j, nsm) : j;   // j / Ns
+    const int k = j - jq * Ns;
     C4 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = ld(ac[j + r * nb]);
@@ -79,7 +84,7 @@ __device__ __forceinline__ void mpass(const float4* __restrict__ a, float4* __re
       }
     }
     dft<R, SIGN>(v, cs);
-    const int base = (j / Ns) * Ns * R + k;
+    const int base = jq * Ns * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) bc[base + r * Ns] = st4(v[r]);
   }
@@ -88,18 +93,18 @@ __device__ __forceinline__ void mpass(const float4* __restrict__ a, float4* __re
 // Length-P transforms of the W columns in `a` (b: the other buffer); returns
 // the buffer that holds the result.  Ends with a block barrier.
 template <int SIGN>
-__device__ float4* columns_dft(float4* a, float4* b, int P, int W, int CS, const DfRadices& rad,
+__device__ float4* columns_dft(float4* a, float4* b, int P, int wsh, int CS, const DfRadices& rad,
                                const float4* __restrict__ tw) {
   int Ns = 1;
   for (int p = 0; p < rad.n; ++p) {
     const int R = rad.r[p];
     switch (R) {
-      case 8: mpass<8, SIGN>(a, b, P, W, CS, Ns, tw); break;
-      case 4: mpass<4, SIGN>(a, b, P, W, CS, Ns, tw); break;
-      case 2: mpass<2, SIGN>(a, b, P, W, CS, Ns, tw); break;
-      case 5: mpass<5, SIGN>(a, b, P, W, CS, Ns, tw); break;
-      case 3: mpass<3, SIGN>(a, b, P, W, CS, Ns, tw); break;
-      default: mpass<7, SIGN>(a, b, P, W, CS, Ns, tw); break;
+      case 8: mpass<8, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
+      case 4: mpass<4, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
+      case 2: mpass<2, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
+      case 5: mpass<5, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
+      case 3: mpass<3, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
+      default: mpass<7, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
     }
     __syncthreads();
     float4* t = a;
@@ -208,7 +213,7 @@ __global__ void k_pr_kout(const int64_t* __restrict__ bins, int64_t n, int P, in
 
 // Evaluation: s[q + Q p] for every tile of W columns (grid-stride over tiles).
 template <bool OUT_REAL>
-__global__ void __launch_bounds__(kPrThreads) k_pr_eval(int64_t M, int P, int64_t Q, int W, DfRadices rad,
+__global__ void __launch_bounds__(kPrThreads) k_pr_eval(int64_t M, int P, int64_t Q, int wsh, DfRadices rad,
                                                         const float4* __restrict__ t0, const float4* __restrict__ t1,
                                                         int b, const int64_t* __restrict__ er,
                                                         const float4* __restrict__ ev,
@@ -216,7 +221,8 @@ __global__ void __launch_bounds__(kPrThreads) k_pr_eval(int64_t M, int P, int64_
                                                         const float4* __restrict__ estep, int64_t n_tiles,
                                                         void* __restrict__ out) {
   extern __shared__ __align__(16) float4 sm[];
-  const int CS = P + 1;
+  const int CS = P + 1, W = 1 << wsh;
+  const unsigned wmask = (unsigned)W - 1u;
   float4* A = sm;
   float4* Bf = A + W * CS;
   float4* tw = Bf + W * CS;
@@ -237,7 +243,7 @@ __global__ void __launch_bounds__(kPrThreads) k_pr_eval(int64_t M, int P, int64_
         base[e - e0] = st4(cmul(ld(__ldg(ev + e)), tw2<1>(t0, t1, b, mulmod((uint64_t)q0, (uint64_t)er[e], Mu, inv))));
       __syncthreads();
       for (int u = threadIdx.x; u < P * W; u += blockDim.x) {
-        const int i = u % W, k = u / W;
+        const int i = (int)((unsigned)u & wmask), k = u >> wsh;
         const int lo = max(boff[k], e0), hi = min(boff[k + 1], e1);
         C4 s = e0 == 0 ? zero4() : ld(A[i * CS + k]);
         for (int e = lo; e < hi; ++e) s = cadd(s, cmul(ld(base[e - e0]), ld(__ldg(estep + (int64_t)e * W + i))));
@@ -247,9 +253,9 @@ __global__ void __launch_bounds__(kPrThreads) k_pr_eval(int64_t M, int P, int64_
       e0 += kPrChunk;
     } while (e0 < ne);
     // s[q0 + i + Q p] = sum_k w_P^{p k} C[k][i]
-    const float4* res = columns_dft<1>(A, Bf, P, W, CS, rad, tw);
+    const float4* res = columns_dft<1>(A, Bf, P, wsh, CS, rad, tw);
     for (int u = threadIdx.x; u < P * W; u += blockDim.x) {
-      const int i = u % W, p = u / W;
+      const int i = (int)((unsigned)u & wmask), p = u >> wsh;
       const int64_t q = q0 + i;
       if (q >= Q) continue;
       const float4 v = res[i * CS + p];
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(kPrThreads) k_pr_eval(int64_t M, int P, int64_
 //   w^{-q0 b_o} sum_i Y[b_o mod P][q0 + i] w^{-i b_o}
 // (thread o mod blockDim owns output o for the whole launch).
 template <bool IN_REAL>
-__global__ void __launch_bounds__(kPrThreads) k_pr_fwd(int64_t M, int P, int64_t Q, int W, DfRadices rad,
+__global__ void __launch_bounds__(kPrThreads) k_pr_fwd(int64_t M, int P, int64_t Q, int wsh, DfRadices rad,
                                                        const float4* __restrict__ t0, const float4* __restrict__ t1,
                                                        int b, const void* __restrict__ in,
                                                        const int64_t* __restrict__ ob,
@@ -275,7 +281,8 @@ __global__ void __launch_bounds__(kPrThreads) k_pr_fwd(int64_t M, int P, int64_t
                                                        const float4* __restrict__ ostep, int64_t n_tiles,
                                                        float4* __restrict__ partial) {
   extern __shared__ __align__(16) float4 sm[];
-  const int CS = P + 1;
+  const int CS = P + 1, W = 1 << wsh;
+  const unsigned wmask = (unsigned)W - 1u;
   float4* A = sm;
   float4* Bf = A + W * CS;
   float4* tw = Bf + W * CS;
@@ -287,7 +294,7 @@ __global__ void __launch_bounds__(kPrThreads) k_pr_fwd(int64_t M, int P, int64_t
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t q0 = tile * W;
     for (int u = threadIdx.x; u < P * W; u += blockDim.x) {
-      const int i = u % W, p = u / W;
+      const int i = (int)((unsigned)u & wmask), p = u >> wsh;
       const int64_t q = q0 + i;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (q < Q) {
@@ -301,7 +308,7 @@ __global__ void __launch_bounds__(kPrThreads) k_pr_fwd(int64_t M, int P, int64_t
       A[i * CS + p] = v;
     }
     __syncthreads();
-    const float4* res = columns_dft<-1>(A, Bf, P, W, CS, rad, tw);
+    const float4* res = columns_dft<-1>(A, Bf, P, wsh, CS, rad, tw);
     const int wl = Q - q0 < (int64_t)W ? (int)(Q - q0) : W;
     for (int o = threadIdx.x; o < n_out; o += blockDim.x) {
       const int k = kout[o];
@@ -374,7 +381,8 @@ bool pruned_split(int64_t M, int64_t n, PrunedSplit* out) {
       best = c;
       S.P = P;
       S.Q = M / P;
-      S.W = std::max(1, kPrTile / P);
+      S.W = 1;
+      while (2 * S.W * P <= kPrTile) S.W *= 2;   // W: a power of two, W P <= kPrTile
       S.rad = r;
     }
   }
@@ -416,16 +424,18 @@ ss_status pruned_eval_pair(const TwoLevelTable& T, const int64_t* qa, const doub
                                                     T.b, estep.get());
   SS_LAUNCH_CHECK();
   const int64_t n_tiles = (S.Q + S.W - 1) / S.W;
+  int wsh = 0;
+  while ((1 << wsh) < S.W) ++wsh;
   const size_t smem = eval_smem(S);
   int grid = 0;
   ProfScope prof_("k_pr_eval", st);
   if (out_real) {
     SS_TRY(grid_for(k_pr_eval<true>, smem, n_tiles, &grid));
-    k_pr_eval<true><<<grid, kPrThreads, smem, st>>>(M, S.P, S.Q, S.W, S.rad, T.t0.get(), T.t1.get(), T.b, er.get(),
+    k_pr_eval<true><<<grid, kPrThreads, smem, st>>>(M, S.P, S.Q, wsh, S.rad, T.t0.get(), T.t1.get(), T.b, er.get(),
                                                     ev.get(), boff.get(), estep.get(), n_tiles, out);
   } else {
     SS_TRY(grid_for(k_pr_eval<false>, smem, n_tiles, &grid));
-    k_pr_eval<false><<<grid, kPrThreads, smem, st>>>(M, S.P, S.Q, S.W, S.rad, T.t0.get(), T.t1.get(), T.b, er.get(),
+    k_pr_eval<false><<<grid, kPrThreads, smem, st>>>(M, S.P, S.Q, wsh, S.rad, T.t0.get(), T.t1.get(), T.b, er.get(),
                                                      ev.get(), boff.get(), estep.get(), n_tiles, out);
   }
   SS_LAUNCH_CHECK();
@@ -439,6 +449,8 @@ ss_status pruned_forward(const TwoLevelTable& T, const void* s, bool in_real, co
   PrunedSplit S;
   if (!pruned_split(M, n_out, &S)) SS_FAIL(SS_ERR_INVALID, "pruned transform: M = %lld has no split", (long long)M);
   const int64_t n_tiles = (S.Q + S.W - 1) / S.W;
+  int wsh = 0;
+  while ((1 << wsh) < S.W) ++wsh;
   for (int64_t o0 = 0; o0 < n_out; o0 += kPrMaxOut) {
     const int nc = (int)std::min<int64_t>(kPrMaxOut, n_out - o0);
     DevBuf<int32_t> kout;
@@ -459,10 +471,10 @@ ss_status pruned_forward(const TwoLevelTable& T, const void* s, bool in_real, co
     SS_TRY(partial.alloc_tmp((size_t)grid * nc, st));
     ProfScope prof_("k_pr_fwd", st);
     if (in_real)
-      k_pr_fwd<true><<<grid, kPrThreads, smem, st>>>(M, S.P, S.Q, S.W, S.rad, T.t0.get(), T.t1.get(), T.b, s,
+      k_pr_fwd<true><<<grid, kPrThreads, smem, st>>>(M, S.P, S.Q, wsh, S.rad, T.t0.get(), T.t1.get(), T.b, s,
                                                      bins + o0, kout.get(), nc, ostep.get(), n_tiles, partial.get());
     else
-      k_pr_fwd<false><<<grid, kPrThreads, smem, st>>>(M, S.P, S.Q, S.W, S.rad, T.t0.get(), T.t1.get(), T.b, s,
+      k_pr_fwd<false><<<grid, kPrThreads, smem, st>>>(M, S.P, S.Q, wsh, S.rad, T.t0.get(), T.t1.get(), T.b, s,
                                                       bins + o0, kout.get(), nc, ostep.get(), n_tiles, partial.get());
     SS_LAUNCH_CHECK();
     k_pr_reduce<<<nblk((int64_t)nc * 32), 256, 0, st>>>(partial.get(), grid, nc, X + o0);

@@ -11,6 +11,7 @@ struct KeyParams {
   int64_t bias_val;                 // 2^(b-1)
   uint64_t fieldmask;               // 2^b - 1
   uint64_t bias[kMaxWords];         // packed bias of every word
+  uint64_t lin_bias;                // key_lin of the packed bias (the linear form of frequency 0)
 };
 
 inline KeyParams make_key_params(const KeyLayout& L) {
@@ -27,6 +28,8 @@ inline KeyParams make_key_params(const KeyLayout& L) {
     const int w = c / L.fpw, sh = 64 - L.fb * (c % L.fpw + 1);
     P.bias[w] |= (uint64_t)P.bias_val << sh;
   }
+  P.lin_bias = 0;
+  for (int w = 0; w < L.WT; ++w) P.lin_bias += key_lin_coef(w) * P.bias[w];
   return P;
 }
 
@@ -94,23 +97,54 @@ __device__ __forceinline__ uint64_t slot_word(uint64_t fp, uint64_t low) { retur
 __device__ __forceinline__ uint64_t word_fp(uint64_t v) { return (v >> 32) & 0x7fffffffull; }
 __device__ __forceinline__ uint64_t word_low(uint64_t v) { return v & 0xffffffffull; }
 
-// Lookup of a finalised key: the canonical index, or -1.
-template <int WT>
-__device__ __forceinline__ int64_t table_find(const uint64_t* __restrict__ table, uint64_t capmask,
-                                              const uint64_t* __restrict__ keys, const uint64_t* k) {
-  const uint64_t hh = hash_key<WT>(k), fp = slot_fp(hh);
+// Lookup of a finalised key given its hash and linear form: the canonical
+// index, or -1.  hl holds the linear form of every stored key: a slot whose
+// fingerprint and linear form both agree is confirmed by eq(o), the exact
+// word-by-word comparison with stored key o.
+template <typename Eq>
+__device__ __forceinline__ int64_t table_find_h(const uint64_t* __restrict__ table, uint64_t capmask, uint64_t hh,
+                                                const uint64_t* __restrict__ hl, uint64_t lin, Eq eq) {
+  const uint64_t fp = slot_fp(hh);
   uint64_t h = hh & capmask;
   for (uint64_t probe = 0; probe <= capmask; ++probe) {
     const uint64_t v = __ldg(table + h);
     if (v == kEmpty) return -1;
     if (word_fp(v) == fp) {
-      uint64_t o[WT];
-      load_key<WT>(keys, (int64_t)word_low(v), o);
-      if (key_eq<WT>(o, k)) return (int64_t)word_low(v);
+      const int64_t o = (int64_t)word_low(v);
+      if (__ldg(hl + o) == lin && eq(o)) return o;
     }
     h = (h + 1) & capmask;
   }
   return -1;
+}
+
+// Stored key o equals a + b - bias (packed sum of a frequency and a step), or
+// equals m * bias - a (m = 2: the negated frequency) when b is null; the rows
+// are read two words at a time when WT is even (16-byte aligned rows).
+template <int WT>
+__device__ __forceinline__ bool key_eq_sum(const uint64_t* __restrict__ so, const uint64_t* __restrict__ a,
+                                           const uint64_t* __restrict__ b, const KeyParams& P) {
+  bool e = true;
+  if constexpr (WT % 2 == 0) {
+#pragma unroll
+    for (int w = 0; w < WT; w += 2) {
+      const ulonglong2 x = __ldg(reinterpret_cast<const ulonglong2*>(so + w));
+      const ulonglong2 y = __ldg(reinterpret_cast<const ulonglong2*>(a + w));
+      if (b) {
+        const ulonglong2 z = __ldg(reinterpret_cast<const ulonglong2*>(b + w));
+        e &= (x.x == y.x + z.x - P.bias[w]) & (x.y == y.y + z.y - P.bias[w + 1]);
+      } else {
+        e &= (x.x == 2 * P.bias[w] - y.x) & (x.y == 2 * P.bias[w + 1] - y.y);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int w = 0; w < WT; ++w) {
+      const uint64_t x = __ldg(so + w), y = __ldg(a + w);
+      e &= b ? (x == y + __ldg(b + w) - P.bias[w]) : (x == 2 * P.bias[w] - y);
+    }
+  }
+  return e;
 }
 
 #define SS_DISPATCH_WT(wt, ...)                              \

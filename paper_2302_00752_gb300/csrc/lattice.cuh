@@ -13,16 +13,21 @@ struct LatticeDev {
   int64_t z[kMaxLatticeDim];
 };
 
-// (k.z) mod M in [0, M), exact: every product (k_c mod M) z_c < 2^62.
+// (k.z) mod M in [0, M), exact: each product (k_c mod M) z_c < 2^62 is
+// reduced by mulmod (Barrett), and the d reduced terms (each < M < 2^31) are
+// summed without reduction (below 2^41 for d <= 1024) and reduced once.
 __device__ __forceinline__ int64_t residue_of(const int32_t* k, int d, const LatticeDev& L) {
-  const uint64_t M = (uint64_t)L.M;
-  uint64_t r = 0;
+  const uint64_t M = (uint64_t)L.M, inv = ~0ull / M;
+  uint64_t acc = 0;
   for (int c = 0; c < d; ++c) {
-    int64_t kc = (int64_t)k[c] % L.M;
-    if (kc < 0) kc += L.M;
-    r = (r + ((uint64_t)kc * (uint64_t)L.z[c]) % M) % M;
+    int64_t kc = k[c];
+    if (kc < 0 || kc >= L.M) {
+      kc %= L.M;
+      if (kc < 0) kc += L.M;
+    }
+    acc += mulmod((uint64_t)kc, (uint64_t)L.z[c], M, inv);
   }
-  return (int64_t)r;
+  return (int64_t)(acc % M);
 }
 
 ss_status make_lattice_dev(const ss_lattice* lat, LatticeDev* L);

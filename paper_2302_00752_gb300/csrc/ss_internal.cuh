@@ -219,6 +219,7 @@ struct ss_stamp_s {
   bool wide = false;                  // |k|^2 may reach 2^29: FP32 norm words hold FP32 values
   // set
   ss::DevBuf<uint64_t> keys;          // [size][WT]
+  ss::DevBuf<uint64_t> hl;            // [size] linear form of each key (key_lin; its hash is hash_of_lin)
   ss::DevBuf<int8_t> level;           // [size]
   ss::DevBuf<int64_t> norm;           // [rows_pad + 1] |k|^2 (0 on padding and the dummy row)
   ss::DevBuf<uint64_t> table;         // open-addressing slots
@@ -226,6 +227,7 @@ struct ss_stamp_s {
   // coefficient data in canonical step order (supp a_hat sorted lexicographically)
   ss::DevBuf<int32_t> afreq;          // [s_a][d]
   ss::DevBuf<uint64_t> stepkey;       // [s_a][WT] packed p_j
+  ss::DevBuf<uint64_t> stepg;         // [s_a] key_lin(stepkey_j) - key_lin(bias)
   ss::DevBuf<int64_t> pnorm;          // [s_a] |p_j|^2
   ss::DevBuf<int32_t> pn32;           // [s_a] FP32 norm words of |p_j|^2 (see norm_word)
   ss::DevBuf<double2> aval;           // [s_a] a_hat_j
@@ -356,12 +358,28 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   return x;
 }
 
+// Key hash: a linear form of the packed words modulo 2^64 (odd coefficient
+// per word) followed by a bijective finaliser.  Linearity lets the hash of a
+// neighbour k + p - bias (the packed sum of a frequency and a step) be formed
+// from the linear forms of k and of the step by one addition, without
+// touching k's words.
+__host__ __device__ constexpr uint64_t key_lin_coef(int w) {
+  return (0x9e3779b97f4a7c15ull ^ (0xbf58476d1ce4e5b9ull * (uint64_t)(w + 1))) | 1ull;
+}
+
+template <int WT>
+__device__ __forceinline__ uint64_t key_lin(const uint64_t* k) {
+  uint64_t h = 0;
+#pragma unroll
+  for (int w = 0; w < WT; ++w) h += key_lin_coef(w) * k[w];
+  return h;
+}
+
+__device__ __forceinline__ uint64_t hash_of_lin(uint64_t lin) { return mix64(lin + 0x632be59bd9b4e019ull); }
+
 template <int WT>
 __device__ __forceinline__ uint64_t hash_key(const uint64_t* k) {
-  uint64_t h = 0x9e3779b97f4a7c15ull;
-#pragma unroll
-  for (int w = 0; w < WT; ++w) h = mix64(h ^ (k[w] + 0x632be59bd9b4e019ull * (w + 1)));
-  return h;
+  return hash_of_lin(key_lin<WT>(k));
 }
 
 template <int WT>

@@ -164,13 +164,15 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const int32_t* __restrict
 
 template <int WT>
 __global__ void k_steps(KeyParams P, const int32_t* __restrict__ A, const double2* __restrict__ av, int s_a,
-                        uint64_t* stepkey, int64_t* pnorm, int32_t* pn32, bool wide, double2* ca64, float2* ca32) {
+                        uint64_t* stepkey, uint64_t* stepg, int64_t* pnorm, int32_t* pn32, bool wide, double2* ca64,
+                        float2* ca32) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= s_a) return;
   uint64_t k[WT];
   pack_key<WT>(A + (int64_t)j * P.d, P, k);
 #pragma unroll
   for (int w = 0; w < WT; ++w) stepkey[(int64_t)j * WT + w] = k[w];
+  stepg[j] = key_lin<WT>(k) - P.lin_bias;   // key_lin(k + p_j - bias) = key_lin(k) + stepg[j]
   int64_t s = 0;
   for (int c = 0; c < P.d; ++c) s += (int64_t)A[(int64_t)j * P.d + c] * A[(int64_t)j * P.d + c];
   pnorm[j] = s;
@@ -180,10 +182,8 @@ __global__ void k_steps(KeyParams P, const int32_t* __restrict__ A, const double
   ca32[j] = make_float2((float)(kTwoPiSq * a.x), (float)(kTwoPiSq * a.y));
 }
 
-// Insert a finalised key with value idx (no duplicates present).
-template <int WT>
-__device__ bool table_insert_final(uint64_t* table, uint64_t capmask, const uint64_t* k, uint64_t idx) {
-  const uint64_t hh = hash_key<WT>(k);
+// Insert a finalised key (hash hh) with value idx (no duplicates present).
+__device__ bool table_insert_final(uint64_t* table, uint64_t capmask, uint64_t hh, uint64_t idx) {
   const uint64_t word = slot_word(slot_fp(hh), idx);
   uint64_t h = hh & capmask;
   for (uint64_t probe = 0; probe <= capmask; ++probe) {
@@ -196,55 +196,80 @@ __device__ bool table_insert_final(uint64_t* table, uint64_t capmask, const uint
 }
 
 template <int WT>
-__global__ void k_level0(KeyParams P, const int32_t* __restrict__ F, int64_t n_f, uint64_t* keys, int8_t* level,
-                         int64_t* norm, uint64_t* table, uint64_t capmask, int32_t* err, int64_t* zero_idx) {
+__global__ void k_level0(KeyParams P, const int32_t* __restrict__ F, int64_t n_f, uint64_t* keys, uint64_t* hl,
+                         int8_t* level, int64_t* norm, uint64_t* table, uint64_t capmask, int32_t* err,
+                         int64_t* zero_idx) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_f) return;
   uint64_t k[WT];
   pack_key<WT>(F + i * P.d, P, k);
 #pragma unroll
   for (int w = 0; w < WT; ++w) keys[i * WT + w] = k[w];
+  const uint64_t lin = key_lin<WT>(k);
+  hl[i] = lin;
   level[i] = 0;
   norm[i] = key_norm<WT>(k, P);
   if (norm[i] == 0) *zero_idx = i;   // only when 0 is in F (allowed for the ADR operator)
-  if (!table_insert_final<WT>(table, capmask, k, (uint64_t)i)) atomicExch(err, SS_ERR_HASH_FULL);
+  if (!table_insert_final(table, capmask, hash_of_lin(lin), (uint64_t)i)) atomicExch(err, SS_ERR_HASH_FULL);
 }
 
 template <int WT>
-__global__ void k_pack_rows(KeyParams P, const int32_t* __restrict__ freq, int64_t n, uint64_t* keys) {
+__global__ void k_pack_rows(KeyParams P, const int32_t* __restrict__ freq, int64_t n, uint64_t* keys, uint64_t* hl) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint64_t k[WT];
   pack_key<WT>(freq + i * P.d, P, k);
 #pragma unroll
   for (int w = 0; w < WT; ++w) keys[i * WT + w] = k[w];
+  hl[i] = key_lin<WT>(k);
 }
 
-template <int WT>
-__global__ void k_rehash(const uint64_t* __restrict__ keys, int64_t size, uint64_t* table, uint64_t capmask,
+__global__ void k_rehash(const uint64_t* __restrict__ hl, int64_t size, uint64_t* table, uint64_t capmask,
                          int32_t* err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= size) return;
-  uint64_t k[WT];
-  load_key<WT>(keys, i, k);
-  if (!table_insert_final<WT>(table, capmask, k, (uint64_t)i)) atomicExch(err, SS_ERR_HASH_FULL);
+  if (!table_insert_final(table, capmask, hash_of_lin(hl[i]), (uint64_t)i)) atomicExch(err, SS_ERR_HASH_FULL);
 }
 
-// Candidate pass of one level (see the file comment).
+// (a1 + b1) == (a2 + b2) word by word: two packed frequency + step sums are
+// the same frequency (the bias they both carry cancels).
 template <int WT>
-__global__ void k_insert(KeyParams P, const uint64_t* __restrict__ keys, int64_t par0, int64_t n_par, int s_a,
-                         int j0, const uint64_t* __restrict__ stepkey, uint64_t* table, uint64_t capmask,
-                         int64_t* slot_of, int32_t* err) {
+__device__ __forceinline__ bool sums_equal(const uint64_t* __restrict__ a1, const uint64_t* __restrict__ b1,
+                                           const uint64_t* __restrict__ a2, const uint64_t* __restrict__ b2) {
+  bool e = true;
+  if constexpr (WT % 2 == 0) {
+#pragma unroll
+    for (int w = 0; w < WT; w += 2) {
+      const ulonglong2 x1 = __ldg(reinterpret_cast<const ulonglong2*>(a1 + w));
+      const ulonglong2 y1 = __ldg(reinterpret_cast<const ulonglong2*>(b1 + w));
+      const ulonglong2 x2 = __ldg(reinterpret_cast<const ulonglong2*>(a2 + w));
+      const ulonglong2 y2 = __ldg(reinterpret_cast<const ulonglong2*>(b2 + w));
+      e &= (x1.x + y1.x == x2.x + y2.x) & (x1.y + y1.y == x2.y + y2.y);
+    }
+  } else {
+#pragma unroll
+    for (int w = 0; w < WT; ++w) e &= __ldg(a1 + w) + __ldg(b1 + w) == __ldg(a2 + w) + __ldg(b2 + w);
+  }
+  return e;
+}
+
+// Candidate pass of one level (see the file comment).  The candidate's hash
+// comes from the linear forms (hl[parent] + stepg[j]); words are read only to
+// confirm a slot whose fingerprint and linear form agree.
+template <int WT>
+__global__ void k_insert(KeyParams P, const uint64_t* __restrict__ keys, const uint64_t* __restrict__ hl, int64_t par0,
+                         int64_t n_par, int s_a, int j0, const uint64_t* __restrict__ stepkey,
+                         const uint64_t* __restrict__ stepg, uint64_t* table, uint64_t capmask, int64_t* slot_of,
+                         int32_t* err) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_par * s_a) return;
   const int64_t par = c / s_a;
   const int j = (int)(c - par * s_a);
   if (j == j0) { slot_of[c] = -1; return; }
-  uint64_t pk[WT], sk[WT], ck[WT];
-  load_key<WT>(keys, par0 + par, pk);
-  load_key<WT>(stepkey, j, sk);
-  add_keys<WT>(pk, sk, P, ck);
-  const uint64_t hh = hash_key<WT>(ck), fp = slot_fp(hh);
+  const uint64_t lin = __ldg(hl + par0 + par) + __ldg(stepg + j);
+  const uint64_t* pk = keys + (par0 + par) * WT;
+  const uint64_t* sk = stepkey + (int64_t)j * WT;
+  const uint64_t hh = hash_of_lin(lin), fp = slot_fp(hh);
   const uint64_t mine = kPending | slot_word(fp, (uint64_t)c);
   uint64_t h = hh & capmask;
   for (uint64_t probe = 0; probe <= capmask; ++probe) {
@@ -256,24 +281,20 @@ __global__ void k_insert(KeyParams P, const uint64_t* __restrict__ keys, int64_t
       v = old;
     }
     if (word_fp(v) == fp) {
-      uint64_t ok[WT];
       if (v & kPending) {
         const int64_t oc = (int64_t)word_low(v);
         const int64_t opar = oc / s_a;
         const int oj = (int)(oc - opar * s_a);
-        uint64_t opk[WT], osk[WT];
-        load_key<WT>(keys, par0 + opar, opk);
-        load_key<WT>(stepkey, oj, osk);
-        add_keys<WT>(opk, osk, P, ok);
-        if (key_eq<WT>(ok, ck)) {
+        if (__ldg(hl + par0 + opar) + __ldg(stepg + oj) == lin &&
+            sums_equal<WT>(keys + (par0 + opar) * WT, stepkey + (int64_t)oj * WT, pk, sk)) {
           // same key, same fingerprint: the minimum keeps the smallest candidate id
           atomicMin((unsigned long long*)(table + h), (unsigned long long)mine);
           slot_of[c] = (int64_t)h;
           return;
         }
       } else {
-        load_key<WT>(keys, (int64_t)word_low(v), ok);
-        if (key_eq<WT>(ok, ck)) { slot_of[c] = -1; return; }
+        const int64_t o = (int64_t)word_low(v);
+        if (__ldg(hl + o) == lin && key_eq_sum<WT>(keys + o * WT, pk, sk, P)) { slot_of[c] = -1; return; }
       }
     }
     h = (h + 1) & capmask;
@@ -292,7 +313,8 @@ __global__ void k_winner_flags(const int64_t* __restrict__ slot_of, const uint64
 }
 
 template <int WT>
-__global__ void k_finalize(KeyParams P, uint64_t* keys, int64_t par0, int s_a, const uint64_t* __restrict__ stepkey,
+__global__ void k_finalize(KeyParams P, uint64_t* keys, uint64_t* hl, int64_t par0, int s_a,
+                           const uint64_t* __restrict__ stepkey, const uint64_t* __restrict__ stepg,
                            const int64_t* __restrict__ slot_of, const int32_t* __restrict__ flag,
                            const int32_t* __restrict__ pos, int64_t n, int64_t base, int lvl, int8_t* level,
                            int64_t* norm, uint64_t* table, int64_t* zero_idx) {
@@ -307,35 +329,49 @@ __global__ void k_finalize(KeyParams P, uint64_t* keys, int64_t par0, int s_a, c
   const int64_t idx = base + pos[c];
 #pragma unroll
   for (int w = 0; w < WT; ++w) keys[idx * WT + w] = ck[w];
+  const uint64_t lin = hl[par0 + par] + __ldg(stepg + j);
+  hl[idx] = lin;
   level[idx] = (int8_t)lvl;
   const int64_t nr = key_norm<WT>(ck, P);
   norm[idx] = nr;
   if (nr == 0) *zero_idx = idx;
-  table[slot_of[c]] = slot_word(slot_fp(hash_key<WT>(ck)), (uint64_t)idx);
+  table[slot_of[c]] = slot_word(slot_fp(hash_of_lin(lin)), (uint64_t)idx);
 }
 
-// Neighbour lookups: nbr[i*s_a + j] = index of k_i - p_j (= k_i + p_{s_a-1-j})
-// when it lies in S, is not 0, and k_i is not 0; else -1.  With keep_zero
-// (the ADR operator) the zero frequency is an ordinary row and column.
+// Neighbour lookups: nbr[j*size + i] = index of k_i - p_j (= k_i + p_{s_a-1-j})
+// when it lies in S, is not 0, and k_i is not 0; else -1 (nbr is filled with
+// -1 beforehand).  With keep_zero (the ADR operator) the zero frequency is an
+// ordinary row and column.  supp a_hat is sorted and symmetric (p_{s_a-1-j} =
+// -p_j, p_j0 = 0), and l = k - p_j lies in S exactly when k = l - p_{s_a-1-j}
+// does: thread (j, i) with j < j0 looks up l = k_i - p_j and, when found,
+// writes both nbr[j][i] = l and nbr[s_a-1-j][l] = i, so every pair is probed
+// once; thread (j0, i) writes the diagonal entry.  Consecutive threads take
+// consecutive rows of one step (coalesced reads of hl and writes of nbr).
 template <int WT>
-__global__ void k_neighbors(KeyParams P, const uint64_t* __restrict__ keys, int64_t size, int s_a,
-                            const uint64_t* __restrict__ stepkey, const uint64_t* __restrict__ table,
-                            uint64_t capmask, const int64_t* __restrict__ zero_dev, bool keep_zero, int32_t* nbr) {
+__global__ void k_neighbors(KeyParams P, const uint64_t* __restrict__ keys, const uint64_t* __restrict__ hl,
+                            int64_t size, int s_a, int j0, const uint64_t* __restrict__ stepkey,
+                            const uint64_t* __restrict__ stepg, const uint64_t* __restrict__ table, uint64_t capmask,
+                            const int64_t* __restrict__ zero_dev, bool keep_zero, int32_t* nbr) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= size * s_a) return;
+  if (c >= size * (j0 + 1)) return;
   const int64_t zero_idx = keep_zero ? -1 : *zero_dev;
-  const int64_t i = c / s_a;
-  const int j = (int)(c - i * s_a);
-  int32_t out = -1;
-  if (i != zero_idx) {
-    uint64_t k[WT], sk[WT], l[WT];
-    load_key<WT>(keys, i, k);
-    load_key<WT>(stepkey, s_a - 1 - j, sk);
-    add_keys<WT>(k, sk, P, l);
-    const int64_t v = table_find<WT>(table, capmask, keys, l);
-    if (v >= 0 && v != zero_idx) out = (int32_t)v;
+  const int j = (int)(c / size);
+  const int64_t i = c - (int64_t)j * size;
+  if (i == zero_idx) return;
+  if (j == j0) {
+    nbr[(int64_t)j0 * size + i] = (int32_t)i;
+    return;
   }
-  nbr[c] = out;
+  const int jr = s_a - 1 - j;   // p_jr = -p_j: k_i - p_j = k_i + p_jr
+  const uint64_t lin = __ldg(hl + i) + __ldg(stepg + jr);
+  const uint64_t* ki = keys + i * WT;
+  const uint64_t* sk = stepkey + (int64_t)jr * WT;
+  const int64_t v = table_find_h(table, capmask, hash_of_lin(lin), hl, lin,
+                                 [&](int64_t o) { return key_eq_sum<WT>(keys + o * WT, ki, sk, P); });
+  if (v >= 0 && v != zero_idx) {
+    nbr[(int64_t)j * size + i] = (int32_t)v;
+    nbr[(int64_t)jr * size + v] = (int32_t)i;
+  }
 }
 
 // Per-row counts, per-slice widths (max over the slice's 32 rows), nnz.
@@ -345,7 +381,7 @@ __global__ void k_row_counts(const int32_t* __restrict__ nbr, int64_t size, int6
   if (i >= rows_pad) return;
   int32_t cnt = 0;
   if (i < size)
-    for (int j = 0; j < s_a; ++j) cnt += (nbr[i * s_a + j] >= 0);
+    for (int j = 0; j < s_a; ++j) cnt += (nbr[(int64_t)j * size + i] >= 0);
   const int32_t w = __reduce_max_sync(0xffffffffu, cnt);
   const unsigned long long tot = __reduce_add_sync(0xffffffffu, (unsigned)cnt);
   if ((threadIdx.x & 31) == 0) {
@@ -372,7 +408,7 @@ __global__ void k_fill_slices(const int32_t* __restrict__ nbr, int64_t size, int
   if (i < size) {
     const int64_t nk = norm[i];
     for (int j = 0; j < s_a; ++j) {
-      const int32_t v = nbr[i * s_a + j];
+      const int32_t v = nbr[(int64_t)j * size + i];
       if (v >= 0) {
         const int64_t e = base + (int64_t)t++ * kSlice;
         ent[e] = (uint32_t)v | ((uint32_t)j << colbits);
@@ -415,7 +451,7 @@ __global__ void k_fill_slices_adr(KeyParams P, const uint64_t* __restrict__ keys
     const int64_t nk = norm[i];
     double2 dg = make_double2(1.0, 0.0);
     for (int j = 0; j < s_a; ++j) {
-      const int32_t v = nbr[i * s_a + j];
+      const int32_t v = nbr[(int64_t)j * size + i];
       if (v < 0) continue;
       const int64_t e = base + (int64_t)t++ * kSlice;
       ent[e] = (uint32_t)v | ((uint32_t)j << colbits);
@@ -462,13 +498,22 @@ __global__ void k_export(KeyParams P, const uint64_t* __restrict__ keys, int64_t
 }
 
 template <int WT>
-__global__ void k_lookup(KeyParams P, const uint64_t* __restrict__ keys, const uint64_t* __restrict__ table,
-                         uint64_t capmask, const int32_t* __restrict__ q, int64_t n, int64_t* idx) {
+__global__ void k_lookup(KeyParams P, const uint64_t* __restrict__ keys, const uint64_t* __restrict__ hl,
+                         const uint64_t* __restrict__ table, uint64_t capmask, const int32_t* __restrict__ q,
+                         int64_t n, int64_t* idx) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint64_t k[WT];
   int64_t r = -1;
-  if (pack_key<WT>(q + i * P.d, P, k)) r = table_find<WT>(table, capmask, keys, k);
+  if (pack_key<WT>(q + i * P.d, P, k)) {
+    const uint64_t lin = key_lin<WT>(k);
+    r = table_find_h(table, capmask, hash_of_lin(lin), hl, lin, [&](int64_t o) {
+      bool e = true;
+#pragma unroll
+      for (int w = 0; w < WT; ++w) e &= __ldg(keys + o * WT + w) == k[w];
+      return e;
+    });
+  }
   idx[i] = r;
 }
 
@@ -509,8 +554,7 @@ static ss_status grow_table(ss_stamp_s* S, int64_t need, const KeyParams& P, cud
   S->cap = want;
   SS_CUDA(cudaMemsetAsync(S->table.get(), 0xff, want * sizeof(uint64_t), st));
   if (S->size > 0) {
-    SS_DISPATCH_WT(P.WT, (k_rehash<WT><<<nblk(S->size), 256, 0, st>>>(S->keys.get(), S->size, S->table.get(),
-                                                                        (uint64_t)want - 1, d_err)));
+    k_rehash<<<nblk(S->size), 256, 0, st>>>(S->hl.get(), S->size, S->table.get(), (uint64_t)want - 1, d_err);
     SS_LAUNCH_CHECK();
   }
   return SS_OK;
@@ -527,22 +571,26 @@ static ss_status grow_keys(ss_stamp_s* S, int64_t need, cudaStream_t st) {
 // Keys, levels and norms moved to buffers of cap rows (cap >= size).
 static ss_status resize_keys(ss_stamp_s* S, int64_t cap, cudaStream_t st) {
   const int WT = S->key.WT;
-  DevBuf<uint64_t> k2;
+  DevBuf<uint64_t> k2, h2;
   DevBuf<int8_t> l2;
   DevBuf<int64_t> n2;
   SS_TRY(k2.alloc(cap * WT, st));
+  SS_TRY(h2.alloc(cap, st));
   SS_TRY(l2.alloc(cap, st));
   SS_TRY(n2.alloc(cap + kSlice + 1, st));
   if (S->size > 0) {
     SS_CUDA(cudaMemcpyAsync(k2.get(), S->keys.get(), S->size * WT * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+    SS_CUDA(cudaMemcpyAsync(h2.get(), S->hl.get(), S->size * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
     SS_CUDA(cudaMemcpyAsync(l2.get(), S->level.get(), S->size, cudaMemcpyDeviceToDevice, st));
     SS_CUDA(cudaMemcpyAsync(n2.get(), S->norm.get(), S->size * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
   }
   // the old buffers are released on this stream, after the copies
   std::swap(S->keys.p, k2.p); std::swap(S->keys.n, k2.n); std::swap(S->keys.s, k2.s);
+  std::swap(S->hl.p, h2.p); std::swap(S->hl.n, h2.n); std::swap(S->hl.s, h2.s);
   std::swap(S->level.p, l2.p); std::swap(S->level.n, l2.n); std::swap(S->level.s, l2.s);
   std::swap(S->norm.p, n2.p); std::swap(S->norm.n, n2.n); std::swap(S->norm.s, n2.s);
   k2.s = st;
+  h2.s = st;
   l2.s = st;
   n2.s = st;
   return SS_OK;
@@ -602,10 +650,10 @@ static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st
     SS_TRY(flag.ensure_tmp(ncand, st));
     {
       ProfScope prof_("k_insert", st);
-      SS_DISPATCH_WT(S->key.WT, (k_insert<WT><<<nblk(ncand), 256, 0, st>>>(P, S->keys.get(), par0, n_par, s_a, S->j0,
-                                                                           S->stepkey.get(), S->table.get(),
-                                                                           (uint64_t)S->cap - 1, slot_of.get(),
-                                                                           S->err_dev.get())));
+      SS_DISPATCH_WT(S->key.WT, (k_insert<WT><<<nblk(ncand), 256, 0, st>>>(
+                                    P, S->keys.get(), S->hl.get(), par0, n_par, s_a, S->j0, S->stepkey.get(),
+                                    S->stepg.get(), S->table.get(), (uint64_t)S->cap - 1, slot_of.get(),
+                                    S->err_dev.get())));
     }
     k_winner_flags<<<nblk(ncand), 256, 0, st>>>(slot_of.get(), S->table.get(), ncand, flag.get());
     SS_LAUNCH_CHECK();
@@ -618,8 +666,9 @@ static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st
     if (e) SS_FAIL((ss_status)e, "stamp: hash table exhausted at level %d", n);
     {
       ProfScope prof_("k_finalize", st);
-      SS_DISPATCH_WT(S->key.WT, (k_finalize<WT><<<nblk(ncand), 256, 0, st>>>(P, S->keys.get(), par0, s_a,
-                                                                             S->stepkey.get(), slot_of.get(), flag.get(),
+      SS_DISPATCH_WT(S->key.WT, (k_finalize<WT><<<nblk(ncand), 256, 0, st>>>(P, S->keys.get(), S->hl.get(), par0,
+                                                                             s_a, S->stepkey.get(), S->stepg.get(),
+                                                                             slot_of.get(), flag.get(),
                                                                              pos.get(), ncand, S->size, n,
                                                                              S->level.get(), S->norm.get(),
                                                                              S->table.get(), S->zidx_dev.get())));
@@ -642,16 +691,18 @@ static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st
 // mirror[g] = index of -k_g (negation is field-wise 2 bias - v on the packed
 // key, no carries since |k_c| < 2^(b-1)); plus[g] = 1 if k_g >lex 0.
 template <int WT>
-__global__ void k_half_index(KeyParams P, const uint64_t* __restrict__ keys, int64_t size,
-                             const uint64_t* __restrict__ table, uint64_t capmask, int64_t* mirror, int32_t* plus,
+__global__ void k_half_index(KeyParams P, const uint64_t* __restrict__ keys, const uint64_t* __restrict__ hl,
+                             int64_t size, const uint64_t* __restrict__ table, uint64_t capmask, int64_t* mirror, int32_t* plus,
                              int32_t* err) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= size) return;
-  uint64_t k[WT], n[WT];
+  uint64_t k[WT];
   load_key<WT>(keys, g, k);
-#pragma unroll
-  for (int w = 0; w < WT; ++w) n[w] = 2 * P.bias[w] - k[w];
-  const int64_t m = table_find<WT>(table, capmask, keys, n);
+  // -k packs as 2 bias - k field by field: its linear form is 2 lin(bias) - lin(k)
+  const uint64_t lin = 2 * P.lin_bias - __ldg(hl + g);
+  const uint64_t* kg = keys + g * WT;
+  const int64_t m = table_find_h(table, capmask, hash_of_lin(lin), hl, lin,
+                                 [&](int64_t o) { return key_eq_sum<WT>(keys + o * WT, kg, nullptr, P); });
   if (m < 0) atomicExch(err, 1);
   mirror[g] = m;
   int p = 0;
@@ -774,7 +825,7 @@ static ss_status build_half(ss_stamp_s* S, cudaStream_t st) {
                          {slice_w.get(), (S->n_slices_h + 1) * sizeof(int32_t), 0},
                          {S->err_dev.get() + 3, sizeof(int32_t), 0}}));
   SS_DISPATCH_WT(S->key.WT, (k_half_index<WT><<<nblk(S->size), 256, 0, st>>>(
-                                P, S->keys.get(), S->size, S->table.get(), (uint64_t)S->cap - 1, S->mirror.get(),
+                                P, S->keys.get(), S->hl.get(), S->size, S->table.get(), (uint64_t)S->cap - 1, S->mirror.get(),
                                 plus.get(), S->err_dev.get() + 3)));
   SS_LAUNCH_CHECK();
   SS_TRY(exclusive_scan_i32(plus.get(), ppos.get(), S->size, total.get(), st));
@@ -823,8 +874,10 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
                          {slice_w.get(), (S->n_slices + 1) * sizeof(int32_t), 0}}));
   {
     ProfScope prof_("k_neighbors", st);
-    SS_DISPATCH_WT(S->key.WT, (k_neighbors<WT><<<nblk(S->size * s_a), 256, 0, st>>>(
-                                  P, S->keys.get(), S->size, s_a, S->stepkey.get(), S->table.get(),
+    SS_CUDA(cudaMemsetAsync(nbr.get(), 0xff, (size_t)S->size * s_a * sizeof(int32_t), st));
+    SS_DISPATCH_WT(S->key.WT, (k_neighbors<WT><<<nblk(S->size * (S->j0 + 1)), 256, 0, st>>>(
+                                  P, S->keys.get(), S->hl.get(), S->size, s_a, S->j0, S->stepkey.get(), S->stepg.get(),
+                                  S->table.get(),
                                   (uint64_t)S->cap - 1, S->zidx_dev.get(), S->adr, nbr.get())));
   }
   k_row_counts<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, slice_w.get(), d_nnz.get());
@@ -874,8 +927,8 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   if (e[0]) SS_FAIL((ss_status)e[0], "stamp: hash table exhausted");
   if (S->half_ok && e[3]) S->half_ok = false;   // some -k not in S: no half system
   // the stamp's buffers outlive this call's stream (synchronised above)
-  S->keys.settle(); S->level.settle(); S->norm.settle(); S->table.settle();
-  S->afreq.settle(); S->stepkey.settle(); S->pnorm.settle(); S->pn32.settle(); S->aval.settle();
+  S->keys.settle(); S->hl.settle(); S->level.settle(); S->norm.settle(); S->table.settle();
+  S->afreq.settle(); S->stepkey.settle(); S->stepg.settle(); S->pnorm.settle(); S->pn32.settle(); S->aval.settle();
   S->ca64.settle(); S->ca32.settle(); S->slice_off.settle(); S->ent.settle(); S->ecoef64.settle();
   S->nw32.settle(); S->rec64.settle(); S->err_dev.settle(); S->zidx_dev.settle();
   S->mirror.settle(); S->hpos.settle(); S->plus_rows.settle(); S->woff_h.settle(); S->ent_h.settle();
@@ -895,14 +948,16 @@ static ss_status relayout(ss_stamp_s* S, const KeyLayout& L2, cudaStream_t st) {
   const int64_t cap_rows = (int64_t)(S->keys.n / S->key.WT);
   DevBuf<uint64_t> k2;
   SS_TRY(k2.alloc((size_t)cap_rows * L2.WT, st));
-  SS_DISPATCH_WT(L2.WT, (k_pack_rows<WT><<<nblk(S->size), 256, 0, st>>>(P2, freq.get(), S->size, k2.get())));
+  SS_DISPATCH_WT(L2.WT, (k_pack_rows<WT><<<nblk(S->size), 256, 0, st>>>(P2, freq.get(), S->size, k2.get(),
+                                                                       S->hl.get())));
   SS_LAUNCH_CHECK();
   std::swap(S->keys.p, k2.p); std::swap(S->keys.n, k2.n); std::swap(S->keys.s, k2.s);
   k2.s = st;   // the old keys are freed on this stream, after the export
   S->key = L2;
   SS_TRY(S->stepkey.alloc((size_t)S->s_a * L2.WT, st));
+  SS_TRY(S->stepg.alloc(S->s_a, st));
   SS_DISPATCH_WT(L2.WT, (k_steps<WT><<<nblk(S->s_a), 256, 0, st>>>(P2, S->afreq.get(), S->aval.get(), S->s_a,
-                                                                   S->stepkey.get(), S->pnorm.get(), S->pn32.get(),
+                                                                   S->stepkey.get(), S->stepg.get(), S->pnorm.get(), S->pn32.get(),
                                                                    S->wide, S->ca64.get(), S->ca32.get())));
   SS_LAUNCH_CHECK();
   const int64_t cap = S->cap;
@@ -986,12 +1041,13 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   SS_TRY(S->aval.alloc(s_a, st));
   SS_CUDA(cudaMemcpyAsync(S->aval.get(), avs.get(), s_a * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   SS_TRY(S->stepkey.alloc((size_t)s_a * L.WT, st));
+  SS_TRY(S->stepg.alloc(s_a, st));
   SS_TRY(S->pnorm.alloc(s_a, st));
   SS_TRY(S->pn32.alloc(s_a, st));
   SS_TRY(S->ca64.alloc(s_a, st));
   SS_TRY(S->ca32.alloc(s_a, st));
   SS_DISPATCH_WT(L.WT, (k_steps<WT><<<nblk(s_a), 256, 0, st>>>(P, As.get(), avs.get(), s_a, S->stepkey.get(),
-                                                               S->pnorm.get(), S->pn32.get(), S->wide,
+                                                               S->stepg.get(), S->pnorm.get(), S->pn32.get(), S->wide,
                                                                S->ca64.get(), S->ca32.get())));
   SS_LAUNCH_CHECK();
 
@@ -1001,7 +1057,8 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   const int64_t pre = std::max<int64_t>(n_f, stamp_size_bound(n_f, s_a, N, kPresizeCap));
   SS_TRY(grow_keys(S, pre, st));
   SS_TRY(grow_table(S, pre, P, st, err));
-  SS_DISPATCH_WT(L.WT, (k_level0<WT><<<nblk(n_f), 256, 0, st>>>(P, Fs.get(), n_f, S->keys.get(), S->level.get(),
+  SS_DISPATCH_WT(L.WT, (k_level0<WT><<<nblk(n_f), 256, 0, st>>>(P, Fs.get(), n_f, S->keys.get(), S->hl.get(),
+                                                                S->level.get(),
                                                                 S->norm.get(), S->table.get(),
                                                                 (uint64_t)S->cap - 1, err, S->zidx_dev.get())));
   SS_LAUNCH_CHECK();
@@ -1019,6 +1076,8 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
 // after the work already queued there.
 static void rebind(ss_stamp_s* S, cudaStream_t st) {
   S->keys.s = st;
+  S->hl.s = st;
+  S->stepg.s = st;
   S->level.s = st;
   S->norm.s = st;
   S->table.s = st;
@@ -1057,7 +1116,8 @@ static ss_status extend_impl(ss_stamp_s* S, int levels, cudaStream_t st) {
     S->wide = wide2;
     const KeyParams P = make_key_params(S->key);
     SS_DISPATCH_WT(S->key.WT, (k_steps<WT><<<nblk(S->s_a), 256, 0, st>>>(P, S->afreq.get(), S->aval.get(), S->s_a,
-                                                                         S->stepkey.get(), S->pnorm.get(),
+                                                                         S->stepkey.get(), S->stepg.get(),
+                                                                         S->pnorm.get(),
                                                                          S->pn32.get(), S->wide, S->ca64.get(),
                                                                          S->ca32.get())));
     SS_LAUNCH_CHECK();
@@ -1263,7 +1323,7 @@ extern "C" ss_status stamp_lookup(ss_stamp s, const int32_t* freq, int64_t n, in
   if (n == 0) return SS_OK;
   const KeyParams P = make_key_params(s->key);
   cudaStream_t st = as_stream(stream);
-  SS_DISPATCH_WT(s->key.WT, (k_lookup<WT><<<nblk(n), 256, 0, st>>>(P, s->keys.get(), s->table.get(),
+  SS_DISPATCH_WT(s->key.WT, (k_lookup<WT><<<nblk(n), 256, 0, st>>>(P, s->keys.get(), s->hl.get(), s->table.get(),
                                                                   (uint64_t)s->cap - 1, freq, n, idx_out)));
   SS_LAUNCH_CHECK();
   return SS_OK;
