@@ -195,8 +195,9 @@ def butterfly_instr(R, twiddled):
     return d + ((R - 1) * C_MUL if twiddled else 0)
 
 
-def pruned_split_py(M, n):
-    """The split M = P Q and tile width of fft_pruned.cu's pruned_split."""
+def pruned_split_py(M, n, tile=2048):
+    """The split M = P Q and tile width of fft_pruned.cu's pruned_split
+    (tile 1024 for the evaluation, 2048 for the forward transform)."""
     best, S = 1e300, None
     for P in range(8, 1025):
         if M % P or M // P < 2:
@@ -209,7 +210,7 @@ def pruned_split_py(M, n):
             best, S = c, (P, M // P, rad)
     P, Q, rad = S
     w = 1
-    while 2 * w * P <= 2048:
+    while 2 * w * P <= tile:
         w *= 2
     return P, Q, w, rad
 
@@ -217,7 +218,7 @@ def pruned_split_py(M, n):
 def pruned_instr(kind, M, n_split, n_work):
     """Algorithmic FP32 instructions of one k_pr_eval (n_work entries) or
     k_pr_fwd (n_work outputs) launch."""
-    P, Q, w, rad = pruned_split_py(M, n_split)
+    P, Q, w, rad = pruned_split_py(M, n_split, 2048)
     col, Ns = 0, 1
     for R in rad:
         col += (P // R) * butterfly_instr(R, Ns > 1)
@@ -225,8 +226,8 @@ def pruned_instr(kind, M, n_split, n_work):
     tiles = -(-Q // w)
     if kind == "eval":   # per entry: table product and value product, then w multiply-adds
         per_tile = w * col + n_work * 2 * C_MUL + n_work * w * (C_MUL + C_ADD)
-    else:                # per output: w multiply-adds, table product, twist, accumulate
-        per_tile = w * col + n_work * (w * (C_MUL + C_ADD) + 2 * C_MUL + C_ADD)
+    else:                # per output: w - 1 Horner steps, table product, twist, accumulate
+        per_tile = w * col + n_work * ((w - 1) * (C_MUL + C_ADD) + 2 * C_MUL + C_ADD)
     return tiles * per_tile, {"P": P, "Q": Q, "W": w, "radices": rad, "tiles": tiles}
 
 

@@ -88,10 +88,10 @@ __global__ void k_sum_partials(const double2* __restrict__ part, int n, double2*
   *out = s;
 }
 
-__global__ void k_ecoef_df(const double2* __restrict__ in, int64_t n, float4* __restrict__ out) {
+__global__ void k_ecoef_df(const double2* __restrict__ in, int64_t n, bool real, float4* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double2 c = in[i];
+  const double2 c = real ? make_double2(reinterpret_cast<const double*>(in)[i], 0.0) : in[i];
   out[i] = cdf(df_split(c.x), df_split(c.y));
 }
 
@@ -101,7 +101,7 @@ ss_status ensure_ecoefdf(ss_stamp_s* s, cudaStream_t st) {
   if (s->ecoefdf.get()) return SS_OK;
   const int64_t n = s->n_ent + 1;
   SS_TRY(s->ecoefdf.alloc(n, st));
-  k_ecoef_df<<<nblk(n), 256, 0, st>>>(s->ecoef64.get(), n, s->ecoefdf.get());
+  k_ecoef_df<<<nblk(n), 256, 0, st>>>(s->ecoef64.get(), n, s->a_real, s->ecoefdf.get());
   SS_LAUNCH_CHECK();
   SS_CUDA(cudaStreamSynchronize(st));
   s->ecoefdf.settle();
@@ -112,7 +112,7 @@ ss_status ensure_ecoefdf_half(ss_stamp_s* s, cudaStream_t st) {
   if (s->ecoefdf_h.get()) return SS_OK;
   const int64_t n = s->ecoef_h.n;
   SS_TRY(s->ecoefdf_h.alloc(n, st));
-  k_ecoef_df<<<nblk(n), 256, 0, st>>>(s->ecoef_h.get(), n, s->ecoefdf_h.get());
+  k_ecoef_df<<<nblk(n), 256, 0, st>>>(s->ecoef_h.get(), n, s->a_real, s->ecoefdf_h.get());
   SS_LAUNCH_CHECK();
   SS_CUDA(cudaStreamSynchronize(st));
   s->ecoefdf_h.settle();

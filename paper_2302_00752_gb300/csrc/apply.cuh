@@ -30,7 +30,7 @@ __device__ __forceinline__ T ldv(const T* p) {
 struct OpView {
   const int32_t* woff;     // slice offsets in units of 32 entries
   const uint32_t* ent;     // col | (j << colbits)
-  const double2* ecoef;    // FP64 coefficient of every entry
+  const double2* ecoef;    // FP64 coefficient of every entry (realc: one double per entry, same index)
   const float4* ecoefdf;   // the same as double-float (re.hi, re.lo, im.hi, im.lo), or null
   int colbits;
   uint32_t colmask;
@@ -64,6 +64,7 @@ __device__ __forceinline__ double2 row_apply64_t(const OpView& op, int64_t s, in
   const int64_t base = (int64_t)w0 * kSlice + lane;
   const uint32_t* e = op.ent + base;
   const double2* cf = op.ecoef + base;
+  const double* cfr = reinterpret_cast<const double*>(op.ecoef) + base;   // real coefficients
   double ar = 0.0, ai = 0.0;
   int t = 0;
   const int w = w1 - w0;
@@ -73,7 +74,7 @@ __device__ __forceinline__ double2 row_apply64_t(const OpView& op, int64_t s, in
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       ee[q] = __ldg(e + (int64_t)(t + q) * kSlice);
-      if constexpr (REAL) c[q].x = __ldg(&cf[(int64_t)(t + q) * kSlice].x);
+      if constexpr (REAL) c[q].x = __ldg(cfr + (int64_t)(t + q) * kSlice);
       else c[q] = __ldg(cf + (int64_t)(t + q) * kSlice);
     }
 #pragma unroll
@@ -97,7 +98,7 @@ __device__ __forceinline__ double2 row_apply64_t(const OpView& op, int64_t s, in
     double2 v = ldv<CG>(rec + 2 * (int64_t)(ee & op.colmask));
     v.y = conj_if(v.y, op.conj, ee);
     if constexpr (REAL) {
-      const double c = __ldg(&cf[(int64_t)t * kSlice].x);
+      const double c = __ldg(cfr + (int64_t)t * kSlice);
       ar = fma(c, v.x, ar);
       ai = fma(c, v.y, ai);
     } else {

@@ -127,6 +127,11 @@ __global__ void k_half_maps(const int32_t* __restrict__ plus_rows, const int64_t
   }
 }
 
+__global__ void k_widen_real(const double* __restrict__ in, int64_t n, double2* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_double2(in[i], 0.0);
+}
+
 __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
@@ -309,7 +314,16 @@ static ss_status batch_create_impl(ss_batch_s* b, int32_t n, const ss_stamp* sta
                                            (uint32_t)x.rows_pad, (uint32_t)row0, global_dummy, dst_colbits,
                                            b->ent.get() + e0);
     k_fill_i32<<<nblk(x.n_slices), 256, 0, st>>>(b->slice_inst.get() + s0, x.n_slices, i);
-    SS_CUDA(cudaMemcpyAsync(b->ecoef64.get() + e0, x.ecoef, x.n_ent * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    // entry coefficients: one double per entry when every stamp's are real
+    // (the batch keeps that layout), else double2 (a real stamp's widened)
+    if (b->realc)
+      SS_CUDA(cudaMemcpyAsync(reinterpret_cast<double*>(b->ecoef64.get()) + e0, x.ecoef, x.n_ent * sizeof(double),
+                              cudaMemcpyDeviceToDevice, st));
+    else if (s->a_real)
+      k_widen_real<<<nblk(x.n_ent), 256, 0, st>>>(reinterpret_cast<const double*>(x.ecoef), x.n_ent,
+                                                  b->ecoef64.get() + e0);
+    else
+      SS_CUDA(cudaMemcpyAsync(b->ecoef64.get() + e0, x.ecoef, x.n_ent * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     SS_LAUNCH_CHECK();
     SS_CUDA(cudaMemcpyAsync(b->ca64.get() + c0, s->ca64.get(), s->s_a * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     SS_CUDA(cudaMemcpyAsync(b->ca32.get() + c0, s->ca32.get(), s->s_a * sizeof(float2), cudaMemcpyDeviceToDevice, st));

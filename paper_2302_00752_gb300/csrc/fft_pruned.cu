@@ -1,13 +1,15 @@
-// Pruned double-float DFTs of a 7-smooth length M (the split, the index maps
-// and the cost are stated in fft_pruned.cuh).
+// Pruned DFTs of a 7-smooth length M (the split, the index maps and the cost
+// are stated in fft_pruned.cuh), in double-float arithmetic (the FP64
+// recovery) or in FP32 (the FP32 recovery).
 //
 // Inside a block a tile holds W columns of length P in shared memory, column c
-// at c (P + 1) (one float4 of padding: threads that share a row offset and
+// at c (P + 1) (one element of padding: threads that share a row offset and
 // differ in the column hit distinct banks).  The length-P transforms run as
 // self-sorting (Stockham) radix passes over all W columns at once, thread u
-// taking column u mod W, butterfly u / W, with the butterflies of dfc.cuh and
-// the P-th roots staged in shared memory.  All sums run in a fixed order, so
-// results are bit-reproducible.
+// taking column u mod W, butterfly u / W, with the P-th roots staged in
+// shared memory.  The arithmetic is a policy (ArDF: complex double-float
+// values as float4 and the butterflies of dfc.cuh; ArF32: float2).  All sums
+// run in a fixed order, so results are bit-reproducible.
 #include <algorithm>
 #include <cmath>
 
@@ -19,7 +21,9 @@ namespace {
 
 using namespace dfc;
 
-constexpr int kPrTile = 2048;      // complex values of one tile (W columns x P rows)
+constexpr int kPrTile = 2048;      // complex values of one tile (W columns x P rows), forward transform
+constexpr int kPrEvalTile = 2048;  // the same for the evaluation
+constexpr int kPrEvalStage = 1024; // step powers (entries x W) staged in shared memory up to this count
 constexpr int kPrThreads = 256;
 constexpr int kPrChunk = 256;      // entries staged in shared memory per round of the evaluation
 constexpr int kPrMaxOut = 1024;    // outputs per forward launch (accumulators in shared memory)
@@ -30,12 +34,153 @@ inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t
 __device__ __forceinline__ C4 conj4(const C4 a) { return C4{a.re, df_neg(a.im)}; }
 __device__ __forceinline__ C4 zero4() { return C4{DF{0.f, 0.f}, DF{0.f, 0.f}}; }
 
-// exp(sign 2 pi i r / M), r < M, from the two-level table
+// exp(sign 2 pi i r / M), r < M, from the two-level double-float table
 template <int SIGN>
 __device__ __forceinline__ C4 tw2(const float4* __restrict__ t0, const float4* __restrict__ t1, int b, uint64_t r) {
   const C4 w = cmul(ld(__ldg(t1 + (r >> b))), ld(__ldg(t0 + (r & ((1ull << b) - 1)))));
   return SIGN > 0 ? w : conj4(w);
 }
+
+// ------------------------------------------------------------ FP32 complex
+
+__device__ __forceinline__ float2 fadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 fsub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 fmul(float2 a, float2 w) {
+  return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+}
+__device__ __forceinline__ float2 fconj(float2 a) { return make_float2(a.x, -a.y); }
+template <int SIGN>
+__device__ __forceinline__ float2 fmul_si(float2 a) {   // a * (sign i)
+  return SIGN > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <int SIGN>
+__device__ __forceinline__ void fdft4(float2& v0, float2& v1, float2& v2, float2& v3) {
+  const float2 t0 = fadd(v0, v2), t1 = fsub(v0, v2), t2 = fadd(v1, v3), t3 = fmul_si<SIGN>(fsub(v1, v3));
+  v0 = fadd(t0, t2);
+  v2 = fsub(t0, t2);
+  v1 = fadd(t1, t3);
+  v3 = fsub(t1, t3);
+}
+
+// R-point DFT in place, the same forms as dfc.cuh's: cs[m - 1] =
+// exp(2 pi i m / R), m <= (R - 1) / 2; for R = 8, cs[0] = exp(2 pi i / 8).
+template <int R, int SIGN>
+__device__ __forceinline__ void fdft(float2 (&v)[R], const float2* cs) {
+  if constexpr (R == 2) {
+    const float2 a = v[0];
+    v[0] = fadd(a, v[1]);
+    v[1] = fsub(a, v[1]);
+  } else if constexpr (R == 4) {
+    fdft4<SIGN>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (R == 8) {
+    float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    fdft4<SIGN>(e0, e1, e2, e3);
+    fdft4<SIGN>(o0, o1, o2, o3);
+    const float c = cs[0].x;   // cos(pi / 4)
+    const float sg1 = SIGN > 0 ? o1.x : -o1.x, sh1 = SIGN > 0 ? o1.y : -o1.y;
+    o1 = make_float2(c * (o1.x - sh1), c * (o1.y + sg1));
+    o2 = fmul_si<SIGN>(o2);
+    const float sg3 = SIGN > 0 ? o3.x : -o3.x, sh3 = SIGN > 0 ? o3.y : -o3.y;
+    o3 = make_float2(-c * (o3.x + sh3), c * (sg3 - o3.y));
+    v[0] = fadd(e0, o0);
+    v[4] = fsub(e0, o0);
+    v[1] = fadd(e1, o1);
+    v[5] = fsub(e1, o1);
+    v[2] = fadd(e2, o2);
+    v[6] = fsub(e2, o2);
+    v[3] = fadd(e3, o3);
+    v[7] = fsub(e3, o3);
+  } else {
+    constexpr int H = (R - 1) / 2;
+    float2 a[H], b[H];
+#pragma unroll
+    for (int r = 1; r <= H; ++r) {
+      a[r - 1] = fadd(v[r], v[R - r]);
+      b[r - 1] = fsub(v[r], v[R - r]);
+    }
+    const float2 v0 = v[0];
+    float2 y0 = v0;
+#pragma unroll
+    for (int r = 0; r < H; ++r) y0 = fadd(y0, a[r]);
+#pragma unroll
+    for (int s = 1; s <= H; ++s) {
+      float2 A = v0, Bv = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int r = 1; r <= H; ++r) {
+        const int m = (r * s) % R;
+        const int mm = m <= H ? m : R - m;
+        const float cm = cs[mm - 1].x;
+        const float sm = m <= H ? cs[mm - 1].y : -cs[mm - 1].y;
+        A.x = fmaf(cm, a[r - 1].x, A.x);
+        A.y = fmaf(cm, a[r - 1].y, A.y);
+        Bv.x = fmaf(sm, b[r - 1].x, Bv.x);
+        Bv.y = fmaf(sm, b[r - 1].y, Bv.y);
+      }
+      const float2 iB = fmul_si<SIGN>(Bv);
+      v[s] = fadd(A, iB);
+      v[R - s] = fsub(A, iB);
+    }
+    v[0] = y0;
+  }
+}
+
+// ------------------------------------------------------- arithmetic policies
+
+// Double-float complex values stored as float4 (re.hi, re.lo, im.hi, im.lo).
+struct ArDF {
+  using V = float4;
+  using C = C4;
+  static __device__ __forceinline__ C ld(const V v) { return dfc::ld(v); }
+  static __device__ __forceinline__ V st(const C c) { return st4(c); }
+  static __device__ __forceinline__ C add(const C a, const C b) { return cadd(a, b); }
+  static __device__ __forceinline__ C mul(const C a, const C b) { return cmul(a, b); }
+  static __device__ __forceinline__ C conj(const C a) { return conj4(a); }
+  static __device__ __forceinline__ C zero() { return zero4(); }
+  // a double-float table or entry value
+  static __device__ __forceinline__ C from_df(const float4 v) { return dfc::ld(v); }
+  template <int SIGN>
+  static __device__ __forceinline__ C root(const float4* t0, const float4* t1, int b, uint64_t r) {
+    return tw2<SIGN>(t0, t1, b, r);
+  }
+  template <int R, int SIGN>
+  static __device__ __forceinline__ void dft(C (&v)[R], const C* cs) {
+    dfc::dft<R, SIGN>(v, cs);
+  }
+  static __device__ __forceinline__ double2 to_double2(const V v) {
+    return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+  }
+  using Real = double;   // real samples: FP64
+  static __device__ __forceinline__ C from_real(const double x) { return C4{df_split(x), DF{0.f, 0.f}}; }
+  static __device__ __forceinline__ double real_out(const V v) { return (double)v.x + (double)v.y; }
+};
+
+// FP32 complex values (the high words of the double-float tables and entries).
+struct ArF32 {
+  using V = float2;
+  using C = float2;
+  static __device__ __forceinline__ C ld(const V v) { return v; }
+  static __device__ __forceinline__ V st(const C c) { return c; }
+  static __device__ __forceinline__ C add(const C a, const C b) { return fadd(a, b); }
+  static __device__ __forceinline__ C mul(const C a, const C b) { return fmul(a, b); }
+  static __device__ __forceinline__ C conj(const C a) { return fconj(a); }
+  static __device__ __forceinline__ C zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ C from_df(const float4 v) { return make_float2(v.x, v.z); }
+  template <int SIGN>
+  static __device__ __forceinline__ C root(const float4* t0, const float4* t1, int b, uint64_t r) {
+    const float4 u = __ldg(t1 + (r >> b)), l = __ldg(t0 + (r & ((1ull << b) - 1)));
+    const float2 w = fmul(make_float2(u.x, u.z), make_float2(l.x, l.z));
+    return SIGN > 0 ? w : fconj(w);
+  }
+  template <int R, int SIGN>
+  static __device__ __forceinline__ void dft(C (&v)[R], const C* cs) {
+    fdft<R, SIGN>(v, cs);
+  }
+  static __device__ __forceinline__ double2 to_double2(const V v) { return make_double2(v.x, v.y); }
+  using Real = float;    // real samples: FP32
+  static __device__ __forceinline__ C from_real(const float x) { return make_float2(x, 0.f); }
+  static __device__ __forceinline__ float real_out(const V v) { return v.x; }
+};
 
 __global__ void k_tl_table(int64_t M, int b, int64_t n1, float4* t0, float4* t1) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -55,13 +200,14 @@ __global__ void k_tl_table(int64_t M, int b, int64_t n1, float4* t0, float4* t1)
 // One radix-R Stockham pass over the W = 2^wsh columns (length P, column
 // stride CS).  j / Ns is formed as umulhi(j, ceil(2^32 / Ns)), exact for
 // j, Ns < 2^16.
-template <int R, int SIGN>
-__device__ __forceinline__ void mpass(const float4* __restrict__ a, float4* __restrict__ b, int P, int wsh, int CS,
-                                      int Ns, const float4* __restrict__ tw) {
+template <class A, int R, int SIGN>
+__device__ __forceinline__ void mpass(const typename A::V* __restrict__ a, typename A::V* __restrict__ b, int P,
+                                      int wsh, int CS, int Ns, const typename A::V* __restrict__ tw) {
+  using C = typename A::C;
   constexpr int NC = R == 8 ? 1 : (R - 1) / 2;
-  C4 cs[NC > 0 ? NC : 1];
+  C cs[NC > 0 ? NC : 1];
 #pragma unroll
-  for (int m = 0; m < NC; ++m) cs[m] = ld(tw[(P / R) * (m + 1)]);
+  for (int m = 0; m < NC; ++m) cs[m] = A::ld(tw[(P / R) * (m + 1)]);
   const int nb = P / R;
   const int tstride = P / (Ns * R);
   const int total = nb << wsh;
@@ -69,45 +215,45 @@ __device__ __forceinline__ void mpass(const float4* __restrict__ a, float4* __re
   const unsigned nsm = Ns > 1 ? 0xffffffffu / (unsigned)Ns + 1u : 0u;
   for (int u = threadIdx.x; u < total; u += blockDim.x) {
     const int c = (int)((unsigned)u & wmask), j = u >> wsh;
-    const float4* ac = a + c * CS;
-    float4* bc = b + c * CS;
+    const typename A::V* ac = a + c * CS;
+    typename A::V* bc = b + c * CS;
     const int jq = Ns > 1 ? (int)__umulhi((unsigned)j, nsm) : j;   // j / Ns
     const int k = j - jq * Ns;
-    C4 v[R];
+    C v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = ld(ac[j + r * nb]);
+    for (int r = 0; r < R; ++r) v[r] = A::ld(ac[j + r * nb]);
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        const C4 w = ld(tw[tstride * (k * r)]);
-        v[r] = cmul(v[r], SIGN > 0 ? w : conj4(w));
+        const C w = A::ld(tw[tstride * (k * r)]);
+        v[r] = A::mul(v[r], SIGN > 0 ? w : A::conj(w));
       }
     }
-    dft<R, SIGN>(v, cs);
+    A::template dft<R, SIGN>(v, cs);
     const int base = jq * Ns * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) bc[base + r * Ns] = st4(v[r]);
+    for (int r = 0; r < R; ++r) bc[base + r * Ns] = A::st(v[r]);
   }
 }
 
 // Length-P transforms of the W columns in `a` (b: the other buffer); returns
 // the buffer that holds the result.  Ends with a block barrier.
-template <int SIGN>
-__device__ float4* columns_dft(float4* a, float4* b, int P, int wsh, int CS, const DfRadices& rad,
-                               const float4* __restrict__ tw) {
+template <class A, int SIGN>
+__device__ typename A::V* columns_dft(typename A::V* a, typename A::V* b, int P, int wsh, int CS,
+                                      const DfRadices& rad, const typename A::V* __restrict__ tw) {
   int Ns = 1;
   for (int p = 0; p < rad.n; ++p) {
     const int R = rad.r[p];
     switch (R) {
-      case 8: mpass<8, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
-      case 4: mpass<4, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
-      case 2: mpass<2, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
-      case 5: mpass<5, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
-      case 3: mpass<3, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
-      default: mpass<7, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
+      case 8: mpass<A, 8, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
+      case 4: mpass<A, 4, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
+      case 2: mpass<A, 2, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
+      case 5: mpass<A, 5, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
+      case 3: mpass<A, 3, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
+      default: mpass<A, 7, SIGN>(a, b, P, wsh, CS, Ns, tw); break;
     }
     __syncthreads();
-    float4* t = a;
+    typename A::V* t = a;
     a = b;
     b = t;
     Ns *= R;
@@ -212,27 +358,36 @@ __global__ void k_pr_kout(const int64_t* __restrict__ bins, int64_t n, int P, in
 }
 
 // Evaluation: s[q + Q p] for every tile of W columns (grid-stride over tiles).
-template <bool OUT_REAL>
+template <class A, bool OUT_REAL>
 __global__ void __launch_bounds__(kPrThreads) k_pr_eval(int64_t M, int P, int64_t Q, int wsh, DfRadices rad,
                                                         const float4* __restrict__ t0, const float4* __restrict__ t1,
                                                         int b, const int64_t* __restrict__ er,
                                                         const float4* __restrict__ ev,
                                                         const int32_t* __restrict__ boff_g,
-                                                        const float4* __restrict__ estep, int64_t n_tiles,
-                                                        void* __restrict__ out) {
-  extern __shared__ __align__(16) float4 sm[];
+                                                        const float4* __restrict__ estep, int n_stage,
+                                                        int64_t n_tiles, void* __restrict__ out) {
+  using V = typename A::V;
+  using C = typename A::C;
+  extern __shared__ __align__(16) float4 sm4[];
   const int CS = P + 1, W = 1 << wsh;
   const unsigned wmask = (unsigned)W - 1u;
-  float4* A = sm;
-  float4* Bf = A + W * CS;
-  float4* tw = Bf + W * CS;
-  float4* base = tw + P;
-  int32_t* boff = reinterpret_cast<int32_t*>(base + kPrChunk);
+  V* Av = reinterpret_cast<V*>(sm4);
+  V* Bf = Av + W * CS;
+  V* tw = Bf + W * CS;
+  V* base = tw + P;
+  V* es = base + kPrChunk;                          // staged step powers (n_stage > 0)
+  int32_t* boff = reinterpret_cast<int32_t*>(es + n_stage);
   const uint64_t Mu = (uint64_t)M, inv = ~0ull / Mu;
-  for (int m = threadIdx.x; m < P; m += blockDim.x) tw[m] = st4(tw2<1>(t0, t1, b, (uint64_t)m * (uint64_t)Q));
+  for (int m = threadIdx.x; m < P; m += blockDim.x)
+    tw[m] = A::st(A::template root<1>(t0, t1, b, (uint64_t)m * (uint64_t)Q));
   for (int k = threadIdx.x; k <= P; k += blockDim.x) boff[k] = boff_g[k];
   __syncthreads();
   const int ne = boff[P];
+  // the step powers exp(2 pi i i r_e / M) are the same for every tile
+  if (n_stage > 0) {
+    for (int x = threadIdx.x; x < ne * W; x += blockDim.x) es[x] = A::st(A::from_df(__ldg(estep + x)));
+    __syncthreads();
+  }
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t q0 = tile * W;
     // C[k][i] = sum_{e in bucket k} v_e w^{(q0 + i) r_e}, in chunks of entries
@@ -240,29 +395,35 @@ __global__ void __launch_bounds__(kPrThreads) k_pr_eval(int64_t M, int P, int64_
     do {
       const int e1 = min(ne, e0 + kPrChunk);
       for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x)
-        base[e - e0] = st4(cmul(ld(__ldg(ev + e)), tw2<1>(t0, t1, b, mulmod((uint64_t)q0, (uint64_t)er[e], Mu, inv))));
+        base[e - e0] = A::st(A::mul(A::from_df(__ldg(ev + e)),
+                                    A::template root<1>(t0, t1, b, mulmod((uint64_t)q0, (uint64_t)er[e], Mu, inv))));
       __syncthreads();
+#pragma unroll 4
       for (int u = threadIdx.x; u < P * W; u += blockDim.x) {
         const int i = (int)((unsigned)u & wmask), k = u >> wsh;
         const int lo = max(boff[k], e0), hi = min(boff[k + 1], e1);
-        C4 s = e0 == 0 ? zero4() : ld(A[i * CS + k]);
-        for (int e = lo; e < hi; ++e) s = cadd(s, cmul(ld(base[e - e0]), ld(__ldg(estep + (int64_t)e * W + i))));
-        A[i * CS + k] = st4(s);
+        C s = e0 == 0 ? A::zero() : A::ld(Av[i * CS + k]);
+        if (n_stage > 0) {
+          for (int e = lo; e < hi; ++e) s = A::add(s, A::mul(A::ld(base[e - e0]), A::ld(es[e * W + i])));
+        } else {
+          for (int e = lo; e < hi; ++e)
+            s = A::add(s, A::mul(A::ld(base[e - e0]), A::from_df(__ldg(estep + (int64_t)e * W + i))));
+        }
+        Av[i * CS + k] = A::st(s);
       }
       __syncthreads();
       e0 += kPrChunk;
     } while (e0 < ne);
     // s[q0 + i + Q p] = sum_k w_P^{p k} C[k][i]
-    const float4* res = columns_dft<1>(A, Bf, P, wsh, CS, rad, tw);
+    const V* res = columns_dft<A, 1>(Av, Bf, P, wsh, CS, rad, tw);
     for (int u = threadIdx.x; u < P * W; u += blockDim.x) {
       const int i = (int)((unsigned)u & wmask), p = u >> wsh;
       const int64_t q = q0 + i;
       if (q >= Q) continue;
-      const float4 v = res[i * CS + p];
       if (OUT_REAL)
-        static_cast<double*>(out)[q + Q * p] = (double)v.x + (double)v.y;
+        static_cast<typename A::Real*>(out)[q + Q * p] = A::real_out(res[i * CS + p]);
       else
-        static_cast<float4*>(out)[q + Q * p] = v;
+        static_cast<V*>(out)[q + Q * p] = res[i * CS + p];
     }
     __syncthreads();
   }
@@ -270,77 +431,92 @@ __global__ void __launch_bounds__(kPrThreads) k_pr_eval(int64_t M, int P, int64_
 
 // Pruned forward transform: per tile the length-P transforms of the W
 // columns, then every output o accumulates
-//   w^{-q0 b_o} sum_i Y[b_o mod P][q0 + i] w^{-i b_o}
-// (thread o mod blockDim owns output o for the whole launch).
-template <bool IN_REAL>
+//   w^{-q0 b_o} sum_i Y[b_o mod P][q0 + i] z_o^i,   z_o = w^{-b_o},
+// the sum over the tile's columns by Horner's scheme (thread o mod blockDim
+// owns output o for the whole launch).
+template <class A, bool IN_REAL>
 __global__ void __launch_bounds__(kPrThreads) k_pr_fwd(int64_t M, int P, int64_t Q, int wsh, DfRadices rad,
                                                        const float4* __restrict__ t0, const float4* __restrict__ t1,
                                                        int b, const void* __restrict__ in,
                                                        const int64_t* __restrict__ ob,
                                                        const int32_t* __restrict__ kout, int n_out,
-                                                       const float4* __restrict__ ostep, int64_t n_tiles,
-                                                       float4* __restrict__ partial) {
-  extern __shared__ __align__(16) float4 sm[];
+                                                       const float4* __restrict__ oz, int64_t n_tiles,
+                                                       typename A::V* __restrict__ partial) {
+  using V = typename A::V;
+  using C = typename A::C;
+  extern __shared__ __align__(16) float4 sm4[];
   const int CS = P + 1, W = 1 << wsh;
   const unsigned wmask = (unsigned)W - 1u;
-  float4* A = sm;
-  float4* Bf = A + W * CS;
-  float4* tw = Bf + W * CS;
-  float4* acc = tw + P;
+  V* Av = reinterpret_cast<V*>(sm4);
+  V* Bf = Av + W * CS;
+  V* tw = Bf + W * CS;
+  V* acc = tw + P;
   const uint64_t Mu = (uint64_t)M, inv = ~0ull / Mu;
-  for (int m = threadIdx.x; m < P; m += blockDim.x) tw[m] = st4(tw2<1>(t0, t1, b, (uint64_t)m * (uint64_t)Q));
-  for (int o = threadIdx.x; o < n_out; o += blockDim.x) acc[o] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int m = threadIdx.x; m < P; m += blockDim.x)
+    tw[m] = A::st(A::template root<1>(t0, t1, b, (uint64_t)m * (uint64_t)Q));
+  for (int o = threadIdx.x; o < n_out; o += blockDim.x) acc[o] = A::st(A::zero());
   __syncthreads();
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t q0 = tile * W;
     for (int u = threadIdx.x; u < P * W; u += blockDim.x) {
       const int i = (int)((unsigned)u & wmask), p = u >> wsh;
       const int64_t q = q0 + i;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      C v = A::zero();
       if (q < Q) {
-        if (IN_REAL) {
-          const DF x = df_split(__ldg(static_cast<const double*>(in) + q + Q * p));
-          v = make_float4(x.hi, x.lo, 0.f, 0.f);
-        } else {
-          v = __ldg(static_cast<const float4*>(in) + q + Q * p);
-        }
+        if (IN_REAL) v = A::from_real(__ldg(static_cast<const typename A::Real*>(in) + q + Q * p));
+        else v = A::ld(__ldg(static_cast<const V*>(in) + q + Q * p));
       }
-      A[i * CS + p] = v;
+      Av[i * CS + p] = A::st(v);
     }
     __syncthreads();
-    const float4* res = columns_dft<-1>(A, Bf, P, wsh, CS, rad, tw);
+    const V* res = columns_dft<A, -1>(Av, Bf, P, wsh, CS, rad, tw);
     const int wl = Q - q0 < (int64_t)W ? (int)(Q - q0) : W;
     for (int o = threadIdx.x; o < n_out; o += blockDim.x) {
       const int k = kout[o];
-      C4 s = zero4();
-      for (int i = 0; i < wl; ++i) s = cadd(s, cmul(ld(res[i * CS + k]), ld(__ldg(ostep + (int64_t)o * W + i))));
-      const C4 w = tw2<-1>(t0, t1, b, mulmod((uint64_t)q0, (uint64_t)ob[o], Mu, inv));
-      acc[o] = st4(cadd(ld(acc[o]), cmul(s, w)));
+      const C w = A::template root<-1>(t0, t1, b, mulmod((uint64_t)q0, (uint64_t)ob[o], Mu, inv));
+      const C z = A::from_df(__ldg(oz + 2 * o));   // oz: stride 2 (the step table of width 2, entry 1)
+      C s = A::ld(res[(wl - 1) * CS + k]);
+      for (int i = wl - 2; i >= 0; --i) s = A::add(A::mul(s, z), A::ld(res[i * CS + k]));
+      acc[o] = A::st(A::add(A::ld(acc[o]), A::mul(s, w)));
     }
     __syncthreads();
   }
   for (int o = threadIdx.x; o < n_out; o += blockDim.x) partial[(int64_t)blockIdx.x * n_out + o] = acc[o];
 }
 
-// X[o] = sum over blocks of partial[blk][o]: one warp per output, lanes in a
-// fixed stride, then a fixed butterfly.
-__global__ void k_pr_reduce(const float4* __restrict__ partial, int nb, int n_out, float4* __restrict__ X) {
+// X[o] = sum over blocks of partial[blk][o] in FP64: one warp per output,
+// lanes in a fixed stride, then a fixed butterfly; written as double-float.
+template <class A>
+__global__ void k_pr_reduce(const typename A::V* __restrict__ partial, int nb, int n_out, float4* __restrict__ X) {
   const int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (o >= n_out) return;   // warp-uniform
-  C4 s = zero4();
-  for (int blk = lane; blk < nb; blk += 32) s = cadd(s, ld(partial[(int64_t)blk * n_out + o]));
-  s.re = df_warp_sum(s.re);
-  s.im = df_warp_sum(s.im);
-  if (lane == 0) X[o] = st4(s);
+  double sr = 0.0, si = 0.0;
+  for (int blk = lane; blk < nb; blk += 32) {
+    const double2 v = A::to_double2(partial[(int64_t)blk * n_out + o]);
+    sr += v.x;
+    si += v.y;
+  }
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, m);
+    si += __shfl_xor_sync(0xffffffffu, si, m);
+  }
+  if (lane == 0) {
+    const DF r = df_split(sr), i = df_split(si);
+    X[o] = make_float4(r.hi, r.lo, i.hi, i.lo);
+  }
 }
 
-size_t eval_smem(const PrunedSplit& S) {
-  return (size_t)(2 * S.W * (S.P + 1) + S.P + kPrChunk) * sizeof(float4) + (size_t)(S.P + 1) * sizeof(int32_t);
+template <class A>
+size_t eval_smem(const PrunedSplit& S, int64_t n_stage) {
+  return (size_t)(2 * S.W * (S.P + 1) + S.P + kPrChunk + n_stage) * sizeof(typename A::V) +
+         (size_t)(S.P + 1) * sizeof(int32_t);
 }
 
+template <class A>
 size_t fwd_smem(const PrunedSplit& S, int n_out) {
-  return (size_t)(2 * S.W * (S.P + 1) + S.P + n_out) * sizeof(float4);
+  return (size_t)(2 * S.W * (S.P + 1) + S.P + n_out) * sizeof(typename A::V);
 }
 
 template <typename K>
@@ -350,6 +526,39 @@ ss_status grid_for(K kernel, size_t smem, int64_t n_tiles, int* grid) {
   SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPrThreads, smem));
   if (per_sm < 1) SS_FAIL(SS_ERR_CUDA, "pruned transform: a block of %zu bytes of shared memory does not fit", smem);
   *grid = (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, (int64_t)per_sm * sm_count()));
+  return SS_OK;
+}
+
+template <class A, bool OUT_REAL>
+ss_status launch_eval(const TwoLevelTable& T, const PrunedSplit& S, int wsh, const int64_t* er, const float4* ev,
+                      const int32_t* boff, const float4* estep, int64_t n_stage, void* out, cudaStream_t st) {
+  const int64_t n_tiles = (S.Q + S.W - 1) / S.W;
+  const size_t smem = eval_smem<A>(S, n_stage);
+  int grid = 0;
+  SS_TRY(grid_for(k_pr_eval<A, OUT_REAL>, smem, n_tiles, &grid));
+  k_pr_eval<A, OUT_REAL><<<grid, kPrThreads, smem, st>>>(T.M, S.P, S.Q, wsh, S.rad, T.t0.get(), T.t1.get(), T.b, er,
+                                                         ev, boff, estep, (int)n_stage, n_tiles, out);
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
+template <class A, bool IN_REAL>
+ss_status launch_fwd(const TwoLevelTable& T, const PrunedSplit& S, int wsh, const void* in, const int64_t* ob,
+                     const int32_t* kout, int nc, const float4* oz, float4* X, cudaStream_t st) {
+  const int64_t n_tiles = (S.Q + S.W - 1) / S.W;
+  const size_t smem = fwd_smem<A>(S, nc);
+  int grid = 0;
+  SS_TRY(grid_for(k_pr_fwd<A, IN_REAL>, smem, n_tiles, &grid));
+  DevBuf<typename A::V> partial;
+  SS_TRY(partial.alloc_tmp((size_t)grid * nc, st));
+  {
+    ProfScope prof_("k_pr_fwd", st);
+    k_pr_fwd<A, IN_REAL><<<grid, kPrThreads, smem, st>>>(T.M, S.P, S.Q, wsh, S.rad, T.t0.get(), T.t1.get(), T.b, in,
+                                                         ob, kout, nc, oz, n_tiles, partial.get());
+    SS_LAUNCH_CHECK();
+  }
+  k_pr_reduce<A><<<nblk((int64_t)nc * 32), 256, 0, st>>>(partial.get(), grid, nc, X);
+  SS_LAUNCH_CHECK();
   return SS_OK;
 }
 
@@ -368,7 +577,7 @@ ss_status two_level_table(int64_t M, TwoLevelTable* T, cudaStream_t st) {
   return SS_OK;
 }
 
-bool pruned_split(int64_t M, int64_t n, PrunedSplit* out) {
+bool pruned_split(int64_t M, int64_t n, PrunedSplit* out, int tile) {
   // cost per point ~ log2 P (the transform) + n / P (the sparse side)
   double best = 1e300;
   PrunedSplit S;
@@ -382,7 +591,7 @@ bool pruned_split(int64_t M, int64_t n, PrunedSplit* out) {
       S.P = P;
       S.Q = M / P;
       S.W = 1;
-      while (2 * S.W * P <= kPrTile) S.W *= 2;   // W: a power of two, W P <= kPrTile
+      while (2 * S.W * P <= tile) S.W *= 2;   // W: a power of two, W P <= tile
       S.rad = r;
     }
   }
@@ -401,13 +610,14 @@ bool pruned_supported(int64_t M) {
 
 ss_status pruned_eval_pair(const TwoLevelTable& T, const int64_t* qa, const double2* ca, const int64_t* na_dev,
                            int64_t na_max, const int64_t* qf, const double2* cf, const int64_t* nf_dev,
-                           int64_t nf_max, const double* scale, void* out, bool out_real, cudaStream_t st) {
+                           int64_t nf_max, const double* scale, void* out, PrunedFormat fmt, cudaStream_t st) {
   const int64_t M = T.M;
   if (!qf) nf_max = 0;
   const int64_t ne_max = std::max<int64_t>(1, 2 * (na_max + nf_max));
   if (ne_max > (1ll << 30)) SS_FAIL(SS_ERR_INVALID, "pruned evaluation: too many terms");
   PrunedSplit S;
-  if (!pruned_split(M, ne_max, &S)) SS_FAIL(SS_ERR_INVALID, "pruned evaluation: M = %lld has no split", (long long)M);
+  if (!pruned_split(M, ne_max, &S, kPrEvalTile))
+    SS_FAIL(SS_ERR_INVALID, "pruned evaluation: M = %lld has no split", (long long)M);
   DevBuf<int64_t> er;
   DevBuf<float4> ev, estep;
   DevBuf<int32_t> boff, kq;
@@ -416,69 +626,67 @@ ss_status pruned_eval_pair(const TwoLevelTable& T, const int64_t* qa, const doub
   SS_TRY(boff.alloc_tmp(S.P + 1, st));
   SS_TRY(kq.alloc_tmp(ne_max, st));
   SS_TRY(estep.alloc_tmp((size_t)ne_max * S.W, st));
-  const int eb = std::min(1024, (S.P + 31) / 32 * 32);
-  k_pr_entries<<<1, eb, (S.P + 1) * sizeof(int32_t), st>>>(qa, ca, na_dev, qf, cf, qf ? nf_dev : nullptr, scale, M,
-                                                           S.P, kq.get(), er.get(), ev.get(), boff.get());
-  SS_LAUNCH_CHECK();
-  k_pr_steps<1><<<nblk(ne_max * S.W), 256, 0, st>>>(er.get(), boff.get() + S.P, 0, S.W, M, T.t0.get(), T.t1.get(),
-                                                    T.b, estep.get());
-  SS_LAUNCH_CHECK();
-  const int64_t n_tiles = (S.Q + S.W - 1) / S.W;
+  {
+    ProfScope prof_setup("pr_setup", st);
+    const int eb = std::min(1024, (S.P + 31) / 32 * 32);
+    k_pr_entries<<<1, eb, (S.P + 1) * sizeof(int32_t), st>>>(qa, ca, na_dev, qf, cf, qf ? nf_dev : nullptr, scale, M,
+                                                             S.P, kq.get(), er.get(), ev.get(), boff.get());
+    SS_LAUNCH_CHECK();
+    k_pr_steps<1><<<nblk(ne_max * S.W), 256, 0, st>>>(er.get(), boff.get() + S.P, 0, S.W, M, T.t0.get(), T.t1.get(),
+                                                      T.b, estep.get());
+    SS_LAUNCH_CHECK();
+  }
   int wsh = 0;
   while ((1 << wsh) < S.W) ++wsh;
-  const size_t smem = eval_smem(S);
-  int grid = 0;
+  // the entries' step powers go to shared memory once per block when they fit
+  const int64_t n_stage = ne_max * S.W <= kPrEvalStage ? ne_max * S.W : 0;
   ProfScope prof_("k_pr_eval", st);
-  if (out_real) {
-    SS_TRY(grid_for(k_pr_eval<true>, smem, n_tiles, &grid));
-    k_pr_eval<true><<<grid, kPrThreads, smem, st>>>(M, S.P, S.Q, wsh, S.rad, T.t0.get(), T.t1.get(), T.b, er.get(),
-                                                    ev.get(), boff.get(), estep.get(), n_tiles, out);
-  } else {
-    SS_TRY(grid_for(k_pr_eval<false>, smem, n_tiles, &grid));
-    k_pr_eval<false><<<grid, kPrThreads, smem, st>>>(M, S.P, S.Q, wsh, S.rad, T.t0.get(), T.t1.get(), T.b, er.get(),
-                                                     ev.get(), boff.get(), estep.get(), n_tiles, out);
+  switch (fmt) {
+    case PrunedFormat::kDfComplex:
+      return launch_eval<ArDF, false>(T, S, wsh, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st);
+    case PrunedFormat::kF64Real:
+      return launch_eval<ArDF, true>(T, S, wsh, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st);
+    case PrunedFormat::kF32Complex:
+      return launch_eval<ArF32, false>(T, S, wsh, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st);
+    default:
+      return launch_eval<ArF32, true>(T, S, wsh, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st);
   }
-  SS_LAUNCH_CHECK();
-  return SS_OK;
 }
 
-ss_status pruned_forward(const TwoLevelTable& T, const void* s, bool in_real, const int64_t* bins, int64_t n_out,
+ss_status pruned_forward(const TwoLevelTable& T, const void* s, PrunedFormat fmt, const int64_t* bins, int64_t n_out,
                          float4* X, cudaStream_t st) {
   const int64_t M = T.M;
   if (n_out < 1) return SS_OK;
   PrunedSplit S;
   if (!pruned_split(M, n_out, &S)) SS_FAIL(SS_ERR_INVALID, "pruned transform: M = %lld has no split", (long long)M);
-  const int64_t n_tiles = (S.Q + S.W - 1) / S.W;
   int wsh = 0;
   while ((1 << wsh) < S.W) ++wsh;
   for (int64_t o0 = 0; o0 < n_out; o0 += kPrMaxOut) {
     const int nc = (int)std::min<int64_t>(kPrMaxOut, n_out - o0);
     DevBuf<int32_t> kout;
-    DevBuf<float4> ostep, partial;
+    DevBuf<float4> oz;
     SS_TRY(kout.alloc_tmp(nc, st));
-    SS_TRY(ostep.alloc_tmp((size_t)nc * S.W, st));
+    SS_TRY(oz.alloc_tmp((size_t)nc * 2, st));
     k_pr_kout<<<nblk(nc), 256, 0, st>>>(bins + o0, nc, S.P, kout.get());
-    k_pr_steps<-1><<<nblk((int64_t)nc * S.W), 256, 0, st>>>(bins + o0, nullptr, nc, S.W, M, T.t0.get(), T.t1.get(),
-                                                             T.b, ostep.get());
+    // oz[2 o + 1] = exp(-2 pi i b_o / M): the Horner root of output o
+    k_pr_steps<-1><<<nblk((int64_t)nc * 2), 256, 0, st>>>(bins + o0, nullptr, nc, 2, M, T.t0.get(), T.t1.get(), T.b,
+                                                          oz.get());
     SS_LAUNCH_CHECK();
-    const size_t smem = fwd_smem(S, nc);
-    int grid = 0;
-    if (in_real) {
-      SS_TRY(grid_for(k_pr_fwd<true>, smem, n_tiles, &grid));
-    } else {
-      SS_TRY(grid_for(k_pr_fwd<false>, smem, n_tiles, &grid));
+    const float4* z = oz.get() + 1;
+    switch (fmt) {
+      case PrunedFormat::kDfComplex:
+        SS_TRY((launch_fwd<ArDF, false>(T, S, wsh, s, bins + o0, kout.get(), nc, z, X + o0, st)));
+        break;
+      case PrunedFormat::kF64Real:
+        SS_TRY((launch_fwd<ArDF, true>(T, S, wsh, s, bins + o0, kout.get(), nc, z, X + o0, st)));
+        break;
+      case PrunedFormat::kF32Complex:
+        SS_TRY((launch_fwd<ArF32, false>(T, S, wsh, s, bins + o0, kout.get(), nc, z, X + o0, st)));
+        break;
+      default:
+        SS_TRY((launch_fwd<ArF32, true>(T, S, wsh, s, bins + o0, kout.get(), nc, z, X + o0, st)));
+        break;
     }
-    SS_TRY(partial.alloc_tmp((size_t)grid * nc, st));
-    ProfScope prof_("k_pr_fwd", st);
-    if (in_real)
-      k_pr_fwd<true><<<grid, kPrThreads, smem, st>>>(M, S.P, S.Q, wsh, S.rad, T.t0.get(), T.t1.get(), T.b, s,
-                                                     bins + o0, kout.get(), nc, ostep.get(), n_tiles, partial.get());
-    else
-      k_pr_fwd<false><<<grid, kPrThreads, smem, st>>>(M, S.P, S.Q, wsh, S.rad, T.t0.get(), T.t1.get(), T.b, s,
-                                                      bins + o0, kout.get(), nc, ostep.get(), n_tiles, partial.get());
-    SS_LAUNCH_CHECK();
-    k_pr_reduce<<<nblk((int64_t)nc * 32), 256, 0, st>>>(partial.get(), grid, nc, X + o0);
-    SS_LAUNCH_CHECK();
   }
   return SS_OK;
 }

@@ -1,5 +1,6 @@
-// Pruned double-float DFTs of a 7-smooth length M for the FP64 coefficient
-// recovery on lattices too long for the full transform of fft_df.cu
+// Pruned DFTs of a 7-smooth length M for the coefficient recovery on long
+// lattices (FP64: double-float arithmetic, beyond the full transform of
+// fft_df.cu; FP32: FP32 arithmetic)
 // (Section "Previous results on SFTs": one length-M 1D FFT of the lattice
 // samples; only the bins k.z mod M of the candidate set are read).
 //
@@ -33,34 +34,44 @@ struct TwoLevelTable {
 ss_status two_level_table(int64_t M, TwoLevelTable* T, cudaStream_t st);
 
 // Split M = P Q for a pruned transform that touches n sparse bins (entries
-// or outputs): P a divisor of M whose prime factors are 2, 3, 5, 7, between 64
-// and 512 where M allows, larger for more bins.  False when M has no such
-// divisor (then the pruned transforms do not apply).
+// or outputs): P the divisor of M (prime factors 2, 3, 5, 7; at most 1024)
+// that minimises log2 P + n / P, and W the largest power of two with
+// W P <= tile.  False when M has no such divisor (then the pruned transforms
+// do not apply).
 struct PrunedSplit {
   int P = 0;
   int64_t Q = 0;
   int W = 0;   // columns per tile
   DfRadices rad;
 };
-bool pruned_split(int64_t M, int64_t n, PrunedSplit* out);
+bool pruned_split(int64_t M, int64_t n, PrunedSplit* out, int tile = 2048);
 
 // True when M is 7-smooth and a split exists for a handful of bins.
 bool pruned_supported(int64_t M);
 
+// Layout of the sample vector s of the pruned transforms.
+enum class PrunedFormat {
+  kDfComplex,   // double-float complex (float4 per node): FP64 recovery of two sums
+  kF64Real,     // FP64 real (double per node)
+  kF32Complex,  // FP32 complex (float2 per node): FP32 recovery of two sums
+  kF32Real      // FP32 real (float per node)
+};
+
 // Samples of s_a / scale[0] + i s_f / scale[1] at the M lattice nodes, where
 // s_a(j) = sum_t Re(ca_t w^{j qa_t}) over na (device count, at most na_max)
-// merged terms and likewise s_f; out: M double-float complex values
-// (OUT_REAL = false) or the real parts as M doubles (OUT_REAL = true, f must
-// then be empty).  scale: device [2] (powers of two).  Asynchronous on st.
+// merged terms and likewise s_f, in the layout fmt (the real formats hold the
+// real parts; f must then be empty).  Double-float arithmetic for the FP64
+// formats, FP32 for the FP32 ones.  scale: device [2] (powers of two) or null
+// (1).  Asynchronous on st.
 ss_status pruned_eval_pair(const TwoLevelTable& T, const int64_t* qa, const double2* ca, const int64_t* na_dev,
                            int64_t na_max, const int64_t* qf, const double2* cf, const int64_t* nf_dev,
-                           int64_t nf_max, const double* scale, void* out, bool out_real, cudaStream_t st);
+                           int64_t nf_max, const double* scale, void* out, PrunedFormat fmt, cudaStream_t st);
 
 // X[o] = sum_{j < M} s[j] exp(-2 pi i j bins[o] / M) for o < n_out (host count),
-// s: M double-float complex values (in_real = false) or M doubles.  X: device
-// double-float complex [n_out].  Deterministic (fixed summation order).
-// Asynchronous on st.
-ss_status pruned_forward(const TwoLevelTable& T, const void* s, bool in_real, const int64_t* bins, int64_t n_out,
+// s in the layout fmt (double-float or FP32 arithmetic accordingly; the sum
+// over the blocks in FP64).  X: device double-float complex [n_out].
+// Deterministic (fixed summation order).  Asynchronous on st.
+ss_status pruned_forward(const TwoLevelTable& T, const void* s, PrunedFormat fmt, const int64_t* bins, int64_t n_out,
                          float4* X, cudaStream_t st);
 
 }  // namespace ss

@@ -332,6 +332,7 @@ ss_status make_lattice_dev(const ss_lattice* lat, LatticeDev* L) {
 }
 
 ss_status residues(const int32_t* freq, int64_t n, const LatticeDev& L, int64_t* res, cudaStream_t st) {
+  ProfScope prof_("k_residues", st);
   if (n == 0) return SS_OK;
   k_residues<<<nblk(n), 256, 0, st>>>(freq, n, L.d, L, res);
   SS_LAUNCH_CHECK();
@@ -341,6 +342,7 @@ ss_status residues(const int32_t* freq, int64_t n, const LatticeDev& L, int64_t*
 ss_status check_reconstructing_async(const int32_t* freq, int64_t n, const LatticeDev& L, const int64_t* res,
                                      bool need_symmetric, unsigned long long* table, uint64_t cap, int32_t* flags,
                                      cudaStream_t st) {
+  ProfScope prof_("lattice_check", st);
   SS_TRY(fill_small(st, {{table, cap * sizeof(unsigned long long), 0}, {flags, 4 * sizeof(int32_t), 0}}));
   if (n == 0) return SS_OK;
   k_check_insert<<<nblk(n), 256, 0, st>>>(freq, res, n, L.d, table, cap - 1, flags);

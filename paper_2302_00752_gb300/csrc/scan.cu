@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(kScanThreads) k_add_tile_prefix(int32_t* out, 
 }  // namespace
 
 ss_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int64_t* d_total, cudaStream_t st) {
+  ProfScope prof_("scan", st);
   if (n <= 0) {
     if (d_total) SS_CUDA(cudaMemsetAsync(d_total, 0, sizeof(int64_t), st));
     return SS_OK;

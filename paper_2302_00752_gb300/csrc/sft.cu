@@ -471,9 +471,10 @@ struct SftPlan {
   DfFftPlan dff;
   DevBuf<float4> dfz, dftmp;
   DevBuf<double> dfscale;   // the two sums' scales of the last round trip
-  // pruned double-float transforms (FP64 on a 7-smooth M above the full
-  // table's limit): two-level twiddle table, the complex sample vector
-  // s_a / sigma_a + i s_f / sigma_f and the two scales
+  // pruned transforms (on a 7-smooth M above the full table's limit;
+  // double-float arithmetic in FP64, FP32 in FP32): two-level twiddle table,
+  // the complex sample vector s_a / sigma_a + i s_f / sigma_f and the two
+  // scales
   bool has_pr = false;
   TwoLevelTable prt;
   DevBuf<float4> prz;
@@ -568,9 +569,9 @@ ss_status get_plan(int64_t M, ss_precision prec, cudaStream_t st, std::shared_pt
       p->has_dff = true;
     }
   }
-  if (prec == SS_FP64 && M > kFullTableMax && !native_fp64_sampling() && pruned_supported(M)) {
+  if (M > kFullTableMax && !(prec == SS_FP64 && native_fp64_sampling()) && pruned_supported(M)) {
     SS_TRY(two_level_table(M, &p->prt, st));
-    SS_TRY(p->prz.alloc(M, st));
+    SS_TRY(p->prz.alloc(prec == SS_FP64 ? M : (M + 1) / 2, st));   // float4 or float2 per node
     SS_TRY(p->prscale.alloc(2, st));
     p->has_pr = true;
   }
@@ -848,6 +849,7 @@ struct Terms {
 // Merge +-p terms (exact rewrite of the real sum) and compact them; no host
 // synchronisation (the merged count stays on the device).
 ss_status prep_terms(const LatticeDev& L, const ss_trig* g, Terms* T, cudaStream_t st) {
+  ProfScope prof_("prep_terms", st);
   const int64_t n = g->n_terms;
   SS_TRY(T->total.alloc_tmp(1, st));
   if (n == 0) {
@@ -893,9 +895,9 @@ ss_status sample_into(const SftPlan& P, const LatticeDev& L, const ss_trig* g, v
   DevBuf<int64_t>& step = T.step;
   DevBuf<int64_t>& total = T.total;
   DevBuf<double2>& coef = T.coef;
-  if (P.has_pr)   // FP64 on a long 7-smooth lattice: sparse evaluation, real parts as FP64
+  if (P.has_pr)   // long 7-smooth lattice: sparse evaluation, the real parts in the plan's precision
     return pruned_eval_pair(P.prt, q.get(), coef.get(), total.get(), n, nullptr, nullptr, nullptr, 0, nullptr, out,
-                            true, st);
+                            P.prec == SS_FP64 ? PrunedFormat::kF64Real : PrunedFormat::kF32Real, st);
   if (use_fft_eval(P, n)) {
     // the spectrum buffer holds the bins; its next reader (the forward
     // transform of recovery) follows in stream order
@@ -988,9 +990,10 @@ ss_status dff_round_trip(const SftPlan& P, const LatticeDev& L, const ss_trig* a
   return df_fft(P.dff, tab, Z, P.dftmp.get(), Z, -1, st);
 }
 
-// Pruned path (FP64 on a 7-smooth M above the full table): the two sums a and
-// f (f may be null) sampled at the M lattice nodes by the sparse evaluation
-// of their merged terms, as s_a / sigma_a + i s_f / sigma_f in P.prz.
+// Pruned path (a 7-smooth M above the full table): the two sums a and f (f
+// may be null) sampled at the M lattice nodes by the sparse evaluation of
+// their merged terms, as s_a / sigma_a + i s_f / sigma_f in P.prz (double-
+// float complex in FP64, FP32 complex in FP32).
 ss_status pr_sample_pair(const SftPlan& P, const LatticeDev& L, const ss_trig* a, const ss_trig* f, cudaStream_t st) {
   const ss_trig none{L.d, 0, nullptr, nullptr};
   if (!f) f = &none;
@@ -1001,7 +1004,8 @@ ss_status pr_sample_pair(const SftPlan& P, const LatticeDev& L, const ss_trig* a
   k_pair_scale<<<1, kScaleThreads, 0, st>>>(ta.coef.get(), ta.total.get(), tf.coef.get(), tf.total.get(), scale);
   SS_LAUNCH_CHECK();
   return pruned_eval_pair(P.prt, ta.q.get(), ta.coef.get(), ta.total.get(), a->n_terms, tf.q.get(), tf.coef.get(),
-                          tf.total.get(), f->n_terms, scale, P.prz.get(), false, st);
+                          tf.total.get(), f->n_terms, scale, P.prz.get(),
+                          P.prec == SS_FP64 ? PrunedFormat::kDfComplex : PrunedFormat::kF32Complex, st);
 }
 
 // Output bins of the pruned forward transform: for candidate i, its residue
@@ -1033,7 +1037,7 @@ __global__ void k_extract_pr(const int64_t* __restrict__ res, int64_t n, int64_t
   atomicMax(maxbits, (unsigned long long)__double_as_longlong(m));
 }
 
-// Pruned forward transform of s (P.prz, or the caller's real FP64 samples) at
+// Pruned forward transform of s (P.prz, or the caller's real samples) at
 // the 2 n_cand bins of the candidates' residues; X: device [2 n_cand].
 ss_status pr_transform(const SftPlan& P, const void* s, bool real, const int64_t* res, int64_t n_cand, float4* X,
                        cudaStream_t st) {
@@ -1041,7 +1045,9 @@ ss_status pr_transform(const SftPlan& P, const void* s, bool real, const int64_t
   SS_TRY(bins.alloc_tmp(2 * n_cand, st));
   k_pr_bins<<<nblk(n_cand), 256, 0, st>>>(res, n_cand, P.M, bins.get());
   SS_LAUNCH_CHECK();
-  return pruned_forward(P.prt, s, real, bins.get(), 2 * n_cand, X, st);
+  const PrunedFormat fmt = P.prec == SS_FP64 ? (real ? PrunedFormat::kF64Real : PrunedFormat::kDfComplex)
+                                             : (real ? PrunedFormat::kF32Real : PrunedFormat::kF32Complex);
+  return pruned_forward(P.prt, s, fmt, bins.get(), 2 * n_cand, X, st);
 }
 
 // zh non-null: the bins come from the double-float spectrum zh (real part
@@ -1422,8 +1428,8 @@ ss_status sft_recover_both(const ss_lattice* lat, const ss_trig* a, const ss_tri
   int32_t* fo[2] = {a_freq, f_freq};
   double* vo[2] = {a_val, f_val};
   if (P.has_pr) {
-    // FP64 on a long 7-smooth lattice: both sums sampled by one sparse
-    // evaluation and recovered by one pruned forward transform
+    // a long 7-smooth lattice: both sums sampled by one sparse evaluation
+    // and recovered by one pruned forward transform
     SS_TRY(pr_sample_pair(P, L, a, f, st));
     DevBuf<float4> X;
     SS_TRY(X.alloc_tmp(2 * n_cand, st));

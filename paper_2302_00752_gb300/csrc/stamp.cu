@@ -59,6 +59,52 @@ __device__ int lexcmp(const int32_t* a, const int32_t* b, int d) {
 // loads), long ones for large sets (fewer atomics).
 inline int rank_chunk(int64_t n) { return n <= 8192 ? 16 : 64; }
 
+// Wide rows (d > 16): one block per row i; its warps take the rows j in turn
+// and compare 32 coordinates per step (coalesced), the first differing
+// coordinate found by a ballot.  rank[i] is written once per block.
+constexpr int kLexWarps = 8;
+
+__global__ void __launch_bounds__(32 * kLexWarps) k_lex_rank_wide(const int32_t* __restrict__ f, int64_t n, int d,
+                                                                   int32_t* rank, int32_t* dup) {
+  __shared__ int32_t s_r[kLexWarps];
+  __shared__ int s_du[kLexWarps];
+  const int64_t i = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int32_t* fi = f + i * d;
+  int32_t r = 0;
+  bool du = false;
+  for (int64_t j = w; j < n; j += kLexWarps) {
+    const int32_t* fj = f + j * d;
+    int cmp = 0;
+    for (int c0 = 0; c0 < d && cmp == 0; c0 += 32) {
+      const int c = c0 + lane;
+      const int32_t a = c < d ? __ldg(fj + c) : 0, b = c < d ? __ldg(fi + c) : 0;
+      const unsigned m = __ballot_sync(0xffffffffu, a != b);
+      if (m) {
+        const int src = __ffs(m) - 1;
+        cmp = __shfl_sync(0xffffffffu, a, src) < __shfl_sync(0xffffffffu, b, src) ? -1 : 1;
+      }
+    }
+    r += (cmp < 0 || (cmp == 0 && j < i)) ? 1 : 0;
+    du |= (cmp == 0 && j != i);
+  }
+  if (lane == 0) {
+    s_r[w] = r;
+    s_du[w] = du;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t t = 0;
+    int any = 0;
+    for (int k = 0; k < kLexWarps; ++k) {
+      t += s_r[k];
+      any |= s_du[k];
+    }
+    rank[i] = t;
+    if (any) atomicExch(dup, 1);
+  }
+}
+
 __global__ void k_lex_rank(const int32_t* __restrict__ f, int64_t n, int d, int32_t* rank, int32_t* dup, int chunk) {
   const int64_t nc = (n + chunk - 1) / chunk;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -397,7 +443,8 @@ __global__ void k_row_counts(const int32_t* __restrict__ nbr, int64_t size, int6
 __global__ void k_fill_slices(const int32_t* __restrict__ nbr, int64_t size, int64_t rows_pad, int s_a, int j0,
                               const int32_t* __restrict__ woff, int colbits, const int64_t* __restrict__ norm,
                               const int64_t* __restrict__ pnorm, const double2* __restrict__ ca64, uint32_t* ent,
-                              double2* ecoef) {
+                              double2* ecoef, bool real) {
+  double* ecoef_re = reinterpret_cast<double*>(ecoef);   // real coefficients: one double per entry
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows_pad) return;
   const int64_t s = i / kSlice;
@@ -413,14 +460,16 @@ __global__ void k_fill_slices(const int32_t* __restrict__ nbr, int64_t size, int
         const int64_t e = base + (int64_t)t++ * kSlice;
         ent[e] = (uint32_t)v | ((uint32_t)j << colbits);
         const double sc = (double)(nk + norm[v] - pnorm[j]);
-        ecoef[e] = make_double2(sc * ca64[j].x, sc * ca64[j].y);
+        if (real) ecoef_re[e] = sc * ca64[j].x;
+        else ecoef[e] = make_double2(sc * ca64[j].x, sc * ca64[j].y);
       }
     }
   }
   const uint32_t pad = (uint32_t)rows_pad | ((uint32_t)j0 << colbits);
   for (; t < w; ++t) {
     ent[base + (int64_t)t * kSlice] = pad;
-    ecoef[base + (int64_t)t * kSlice] = make_double2(0.0, 0.0);
+    if (real) ecoef_re[base + (int64_t)t * kSlice] = 0.0;
+    else ecoef[base + (int64_t)t * kSlice] = make_double2(0.0, 0.0);
   }
 }
 
@@ -655,7 +704,10 @@ static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st
                                     S->stepg.get(), S->table.get(), (uint64_t)S->cap - 1, slot_of.get(),
                                     S->err_dev.get())));
     }
-    k_winner_flags<<<nblk(ncand), 256, 0, st>>>(slot_of.get(), S->table.get(), ncand, flag.get());
+    {
+      ProfScope prof_("k_winner_flags", st);
+      k_winner_flags<<<nblk(ncand), 256, 0, st>>>(slot_of.get(), S->table.get(), ncand, flag.get());
+    }
     SS_LAUNCH_CHECK();
     DevBuf<int32_t> pos;
     SS_TRY(pos.alloc_tmp(ncand, st));
@@ -757,7 +809,9 @@ __global__ void k_half_fill(const int32_t* __restrict__ plus_rows, int64_t n_plu
                             const int32_t* __restrict__ woff, const uint32_t* __restrict__ ent,
                             const double2* __restrict__ ecoef, uint32_t colmask, int colbits, int64_t pad_col,
                             int colbits_h, int j0, const int32_t* __restrict__ hpos,
-                            const int32_t* __restrict__ woff_h, uint32_t* ent_h, double2* ecoef_h) {
+                            const int32_t* __restrict__ woff_h, uint32_t* ent_h, double2* ecoef_h, bool real) {
+  const double* ecoef_re = reinterpret_cast<const double*>(ecoef);
+  double* ecoef_h_re = reinterpret_cast<double*>(ecoef_h);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows_pad_h) return;
   const int64_t sh = i / kSlice;
@@ -778,13 +832,15 @@ __global__ void k_half_fill(const int32_t* __restrict__ plus_rows, int64_t n_plu
       const uint32_t col = h >= 0 ? (uint32_t)h : (uint32_t)(-2 - h);
       const uint32_t j = ent[e] >> colbits;
       ent_h[base_h + (int64_t)t * kSlice] = col | (j << colbits_h) | (h < 0 ? 0x80000000u : 0u);
-      ecoef_h[base_h + (int64_t)t * kSlice] = ecoef[e];
+      if (real) ecoef_h_re[base_h + (int64_t)t * kSlice] = ecoef_re[e];
+      else ecoef_h[base_h + (int64_t)t * kSlice] = ecoef[e];
       ++t;
     }
   }
   for (; t < w_h; ++t) {
     ent_h[base_h + (int64_t)t * kSlice] = (uint32_t)rows_pad_h | ((uint32_t)j0 << colbits_h);
-    ecoef_h[base_h + (int64_t)t * kSlice] = make_double2(0.0, 0.0);
+    if (real) ecoef_h_re[base_h + (int64_t)t * kSlice] = 0.0;
+    else ecoef_h[base_h + (int64_t)t * kSlice] = make_double2(0.0, 0.0);
   }
 }
 
@@ -824,17 +880,26 @@ static ss_status build_half(ss_stamp_s* S, cudaStream_t st) {
                          {S->plus_rows.get(), S->rows_pad_h * sizeof(int32_t), 0},
                          {slice_w.get(), (S->n_slices_h + 1) * sizeof(int32_t), 0},
                          {S->err_dev.get() + 3, sizeof(int32_t), 0}}));
-  SS_DISPATCH_WT(S->key.WT, (k_half_index<WT><<<nblk(S->size), 256, 0, st>>>(
-                                P, S->keys.get(), S->hl.get(), S->size, S->table.get(), (uint64_t)S->cap - 1, S->mirror.get(),
-                                plus.get(), S->err_dev.get() + 3)));
+  {
+    ProfScope prof_("k_half_index", st);
+    SS_DISPATCH_WT(S->key.WT, (k_half_index<WT><<<nblk(S->size), 256, 0, st>>>(
+                                  P, S->keys.get(), S->hl.get(), S->size, S->table.get(), (uint64_t)S->cap - 1, S->mirror.get(),
+                                  plus.get(), S->err_dev.get() + 3)));
+  }
   SS_LAUNCH_CHECK();
   SS_TRY(exclusive_scan_i32(plus.get(), ppos.get(), S->size, total.get(), st));
-  k_half_rows<<<nblk(S->size), 256, 0, st>>>(plus.get(), ppos.get(), S->mirror.get(), S->norm.get(), S->size,
-                                             S->zero_idx, n_plus, S->hpos.get(), S->plus_rows.get(),
-                                             S->norm_h.get());
+  {
+    ProfScope prof_("k_half_rows", st);
+    k_half_rows<<<nblk(S->size), 256, 0, st>>>(plus.get(), ppos.get(), S->mirror.get(), S->norm.get(), S->size,
+                                               S->zero_idx, n_plus, S->hpos.get(), S->plus_rows.get(),
+                                               S->norm_h.get());
+  }
   const uint32_t colmask = colmask_of(S->jbits);
-  k_half_widths<<<nblk(S->rows_pad_h), 256, 0, st>>>(S->plus_rows.get(), n_plus, S->rows_pad_h, S->slice_off.get(),
-                                                     S->ent.get(), colmask, S->rows_pad, slice_w.get());
+  {
+    ProfScope prof_("k_half_widths", st);
+    k_half_widths<<<nblk(S->rows_pad_h), 256, 0, st>>>(S->plus_rows.get(), n_plus, S->rows_pad_h, S->slice_off.get(),
+                                                       S->ent.get(), colmask, S->rows_pad, slice_w.get());
+  }
   SS_LAUNCH_CHECK();
   SS_TRY(exclusive_scan_i32(slice_w.get(), S->woff_h.get(), S->n_slices_h + 1, total.get(), st));
   {
@@ -842,7 +907,7 @@ static ss_status build_half(ss_stamp_s* S, cudaStream_t st) {
     k_half_fill<<<nblk(S->rows_pad_h), 256, 0, st>>>(S->plus_rows.get(), n_plus, S->rows_pad_h, S->slice_off.get(),
                                                      S->ent.get(), S->ecoef64.get(), colmask, colbits_of(S->jbits),
                                                      S->rows_pad, S->colbits_h, S->j0, S->hpos.get(), S->woff_h.get(),
-                                                     S->ent_h.get(), S->ecoef_h.get());
+                                                     S->ent_h.get(), S->ecoef_h.get(), S->a_real);
   }
   SS_LAUNCH_CHECK();
   S->woff_h_host.resize(S->n_slices_h + 1);
@@ -880,7 +945,10 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
                                   S->table.get(),
                                   (uint64_t)S->cap - 1, S->zidx_dev.get(), S->adr, nbr.get())));
   }
-  k_row_counts<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, slice_w.get(), d_nnz.get());
+  {
+    ProfScope prof_("k_row_counts", st);
+    k_row_counts<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, slice_w.get(), d_nnz.get());
+  }
   SS_LAUNCH_CHECK();
   SS_TRY(S->slice_off.alloc(S->n_slices + 1, st));
   SS_TRY(exclusive_scan_i32(slice_w.get(), S->slice_off.get(), S->n_slices + 1, d_total.get(), st));
@@ -908,7 +976,8 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
       ProfScope prof_("k_fill_slices", st);
       k_fill_slices<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, S->j0,
                                                        S->slice_off.get(), colbits_of(S->jbits), S->norm.get(),
-                                                       S->pnorm.get(), S->ca64.get(), S->ent.get(), S->ecoef64.get());
+                                                       S->pnorm.get(), S->ca64.get(), S->ent.get(), S->ecoef64.get(),
+                                                       S->a_real);
     }
   }
   SS_LAUNCH_CHECK();
@@ -991,12 +1060,27 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   // signed lexicographic order of F and supp a_hat
   const int chf = rank_chunk(n_f), cha = rank_chunk(s_a);
   const int64_t ncf = (n_f + chf - 1) / chf, nca = (s_a + cha - 1) / cha;
-  k_lex_rank<<<nblk(n_f * ncf), 256, 0, st>>>(f_freq, n_f, d, rank.get(), err + 1, chf);
+  // ranks (rank and rank_a start at zero): per-thread chunks for short rows,
+  // one block per row for wide ones
+  auto lex_rank = [&](const int32_t* fr, int64_t n, int ch, int64_t nc, int32_t* rk, int32_t* du) {
+    if (d > 16) k_lex_rank_wide<<<(unsigned)n, 32 * kLexWarps, 0, st>>>(fr, n, d, rk, du);
+    else k_lex_rank<<<nblk(n * nc), 256, 0, st>>>(fr, n, d, rk, du, ch);
+  };
+  {
+    ProfScope prof_("k_lex_rank", st);
+    lex_rank(f_freq, n_f, chf, ncf, rank.get(), err + 1);
+  }
   k_scatter_rows<<<nblk(n_f), 256, 0, st>>>(f_freq, nullptr, n_f, d, rank.get(), Fs.get(), nullptr);
-  k_lex_rank<<<nblk(s_a * nca), 256, 0, st>>>(a_hat->freq, s_a, d, rank_a.get(), err + 2, cha);
+  {
+    ProfScope prof_("k_lex_rank", st);
+    lex_rank(a_hat->freq, s_a, cha, nca, rank_a.get(), err + 2);
+  }
   k_scatter_rows<<<nblk(s_a), 256, 0, st>>>(a_hat->freq, reinterpret_cast<const double2*>(a_hat->val), s_a, d,
                                             rank_a.get(), As.get(), avs.get());
-  k_prep<<<1, kPrepThreads, 0, st>>>(Fs.get(), n_f, As.get(), avs.get(), s_a, d, prep.get());
+  {
+    ProfScope prof_("k_prep", st);
+    k_prep<<<1, kPrepThreads, 0, st>>>(Fs.get(), n_f, As.get(), avs.get(), s_a, d, prep.get());
+  }
   SS_LAUNCH_CHECK();
   PrepOut h{};
   int32_t herr[4];
@@ -1057,10 +1141,13 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   const int64_t pre = std::max<int64_t>(n_f, stamp_size_bound(n_f, s_a, N, kPresizeCap));
   SS_TRY(grow_keys(S, pre, st));
   SS_TRY(grow_table(S, pre, P, st, err));
-  SS_DISPATCH_WT(L.WT, (k_level0<WT><<<nblk(n_f), 256, 0, st>>>(P, Fs.get(), n_f, S->keys.get(), S->hl.get(),
-                                                                S->level.get(),
-                                                                S->norm.get(), S->table.get(),
-                                                                (uint64_t)S->cap - 1, err, S->zidx_dev.get())));
+  {
+    ProfScope prof_("k_level0", st);
+    SS_DISPATCH_WT(L.WT, (k_level0<WT><<<nblk(n_f), 256, 0, st>>>(P, Fs.get(), n_f, S->keys.get(), S->hl.get(),
+                                                                  S->level.get(),
+                                                                  S->norm.get(), S->table.get(),
+                                                                  (uint64_t)S->cap - 1, err, S->zidx_dev.get())));
+  }
   SS_LAUNCH_CHECK();
   S->size = n_f;
   S->level_start.push_back(n_f);

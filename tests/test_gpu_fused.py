@@ -22,10 +22,13 @@ def mods():
 
 def paired(p, M):
     """Whether the one-call form recovers a and f with one complex transform:
+    on a 7-smooth M above 2^22 in either precision (the pruned transforms),
     FP64 on a 7-smooth M <= 2^22 (double-float FFT), FP32 on an M that is not
     7-smooth (cuFFT's Bluestein C2C costs about one real transform)."""
+    if olat.is_smooth(M) and M > 2 ** 22:
+        return True
     if p.sft_precision == "fp64":
-        return olat.is_smooth(M) and M <= 2 ** 22
+        return olat.is_smooth(M)
     return not olat.is_smooth(M)
 
 

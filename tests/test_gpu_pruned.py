@@ -52,36 +52,46 @@ def _instance(M, n_terms, seed, d=3, span=40):
     return freq, coef, I, z
 
 
-def _check_coefficients(gf, gv, freq, coef, tol=1e-12):
+def _check_coefficients(gf, gv, freq, coef, tol=1e-12, tau=1e-9):
+    # kept: |g_k| > tau max |g| (coefficients within rounding of the cut may go
+    # either way), values within tol sum|c| of the closed form
     want = osft.true_coefficients(freq, coef)
     got = {tuple(k): v for k, v in zip(gf.cpu().numpy().tolist(), gv.cpu().numpy())}
     scale = np.abs(coef).sum()
-    assert set(got) == {k for k, v in want.items() if abs(v) > 1e-9 * scale}
+    vmax = max(abs(v) for v in want.values())
+    assert {k for k, v in want.items() if abs(v) > 2 * tau * vmax} <= set(got)
+    assert set(got) <= {k for k, v in want.items() if abs(v) > 0.5 * tau * vmax}
     err = max(abs(v - want[k]) for k, v in got.items())
     assert err <= tol * scale, err
 
 
+# tolerances per precision: samples, coefficients (of sum|c|), threshold
+TOLS = {"fp64": (1e-13, 1e-12, 1e-9), "fp32": (2e-6, 1e-5, 1e-4)}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("M", SIZES)
-def test_sampling_and_recovery(B, M):
+def test_sampling_and_recovery(B, M, prec):
+    tol_s, tol_c, tau = TOLS[prec]
     freq, coef, I, z = _instance(M, 40, 0)
     scale = np.abs(coef).sum()
-    # FP64 samples by the sparse evaluation, against the direct sum at chosen
-    # and random indices (tile and column boundaries included)
-    s = B.lattice_sample(z, M, freq, coef, "fp64")
-    assert s.dtype == torch.float64 and s.numel() == M
+    # samples by the sparse evaluation, against the direct sum at chosen and
+    # random indices (tile and column boundaries included)
+    s = B.lattice_sample(z, M, freq, coef, prec)
+    assert s.dtype == (torch.float64 if prec == "fp64" else torch.float32) and s.numel() == M
     rng = np.random.default_rng(1)
     js = np.unique(np.concatenate([[0, 1, 2, M - 1, M - 2, M // 2, M // 3, M // 7],
                                    [M // q * t for q in (8, 27, 125, 343) for t in (1, 2)],
                                    rng.integers(0, M, 3000)]))
     ref = osft.sample(freq, coef, z, M, js)
-    got = s.cpu().numpy()[js]
-    assert np.abs(got - ref).max() <= 1e-13 * scale
+    got = s.double().cpu().numpy()[js]
+    assert np.abs(got - ref).max() <= tol_s * scale
     # recovery through the library (sampling + pruned transform) and from the
-    # samples above (pruned transform of real FP64 input)
-    gf, gv = B.sft_recover(z, M, freq, coef, I, tau=1e-9)
-    _check_coefficients(gf, gv, freq, coef)
-    gf2, gv2 = B.sft_recover_samples(z, M, s, I, tau=1e-9)
-    _check_coefficients(gf2, gv2, freq, coef)
+    # samples above (pruned transform of real input)
+    gf, gv = B.sft_recover(z, M, freq, coef, I, tau=tau, precision=prec)
+    _check_coefficients(gf, gv, freq, coef, tol_c, tau)
+    gf2, gv2 = B.sft_recover_samples(z, M, s, I, tau=tau, precision=prec)
+    _check_coefficients(gf2, gv2, freq, coef, tol_c, tau)
 
 
 def test_many_terms_and_buckets(B):
@@ -161,5 +171,32 @@ def test_cfg5_fp64_recovery_closed_form(B):
     S2, _ = staged.stamp.export()
     assert torch.equal(S1, S2)
     assert rel_l2(r.u.cpu().numpy(), staged.u.cpu().numpy()) <= 1e-11
+    r.stamp.destroy()
+    staged.stamp.destroy()
+
+
+def test_cfg5_fp32_pair_recovery(B):
+    # the d = 100 data as configured (FP32 samples and FFT) on M = 2^26: a and
+    # f share one FP32 evaluation and one pruned FP32 transform in the one-call
+    # path; each sum recovered alone against the closed form, and the one-call
+    # solution against the staged one (same S, u within the FP32 recovery's
+    # rounding)
+    from paper_2302_00752_gb300 import pipeline as gp
+    inst = W.make_cfg5(smooth=True)
+    cand = opipe.candidates(inst, inst.f.freq)
+    L = inst.lattice
+    z, M, _ = B.lattice_random(cand, L["raw"], L["sigma"], L["M_min"], smooth=True)
+    assert M == 2 ** 26
+    for trig in (inst.a, inst.f):
+        gf, gv = B.sft_recover(z, M, trig.freq, trig.coef, cand, tau=1e-4, precision="fp32")
+        _check_coefficients(gf, gv, trig.freq, trig.coef, 1e-5, 1e-4)
+    p = gp.prepare(inst)
+    r = gp.run_fused(p, tol=1e-12, max_iter=1000, solve_precision="fp32_refined")
+    assert r.stats["status"] == "SS_OK" and p.M == 2 ** 26
+    staged = gp.run(p, tol=1e-12, solve_precision="fp32_refined", lattice=False)
+    S1, _ = r.stamp.export()
+    S2, _ = staged.stamp.export()
+    assert torch.equal(S1, S2)
+    assert rel_l2(r.u.cpu().numpy(), staged.u.cpu().numpy()) <= 1e-5
     r.stamp.destroy()
     staged.stamp.destroy()
