@@ -98,9 +98,9 @@ __device__ __forceinline__ uint64_t word_fp(uint64_t v) { return (v >> 32) & 0x7
 __device__ __forceinline__ uint64_t word_low(uint64_t v) { return v & 0xffffffffull; }
 
 // Lookup of a finalised key given its hash and linear form: the canonical
-// index, or -1.  hl holds the linear form of every stored key: a slot whose
-// fingerprint and linear form both agree is confirmed by eq(o), the exact
-// word-by-word comparison with stored key o.
+// index, or -1.  A slot whose fingerprint agrees is confirmed by eq(o), the
+// exact word-by-word comparison with stored key o; when hl (the linear form of
+// every stored key) is given, the linear forms are compared first.
 template <typename Eq>
 __device__ __forceinline__ int64_t table_find_h(const uint64_t* __restrict__ table, uint64_t capmask, uint64_t hh,
                                                 const uint64_t* __restrict__ hl, uint64_t lin, Eq eq) {
@@ -111,7 +111,7 @@ __device__ __forceinline__ int64_t table_find_h(const uint64_t* __restrict__ tab
     if (v == kEmpty) return -1;
     if (word_fp(v) == fp) {
       const int64_t o = (int64_t)word_low(v);
-      if (__ldg(hl + o) == lin && eq(o)) return o;
+      if ((!hl || __ldg(hl + o) == lin) && eq(o)) return o;
     }
     h = (h + 1) & capmask;
   }

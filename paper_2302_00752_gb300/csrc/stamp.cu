@@ -358,76 +358,184 @@ __global__ void k_winner_flags(const int64_t* __restrict__ slot_of, const uint64
   flag[c] = (s >= 0 && (v & kPending) && word_low(v) == (uint64_t)c) ? 1 : 0;
 }
 
+// The winning candidates in canonical order: cand[pos[c]] = c.
+__global__ void k_compact_winners(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t n,
+                                  int64_t* cand) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n && flag[c]) cand[pos[c]] = c;
+}
+
+// k . p over the fields where the step p is nonzero (k, p packed; a step
+// usually touches few coordinates).  The highest set bit of p ^ bias lies in
+// the value bits of the first differing field of the word (the guard bit
+// above each field is zero in both).
+template <int WT>
+__device__ __forceinline__ int64_t dot_step(const uint64_t* k, const uint64_t* p, const KeyParams& P) {
+  int64_t s = 0;
+#pragma unroll
+  for (int w = 0; w < WT; ++w) {
+    uint64_t x = p[w] ^ P.bias[w];
+    while (x) {
+      const int f = __clzll(x) / P.fb;
+      const int sh = 64 - P.fb * (f + 1);
+      const int64_t kv = (int64_t)((k[w] >> sh) & P.fieldmask) - P.bias_val;
+      const int64_t pv = (int64_t)((p[w] >> sh) & P.fieldmask) - P.bias_val;
+      s += kv * pv;
+      x = sh ? (x & ((1ull << sh) - 1)) : 0;
+    }
+  }
+  return s;
+}
+
+// One thread per new element t (canonical index base + t), so the key
+// arithmetic and the stores run in full warps.  |k + p|^2 = |k|^2 + |p|^2 +
+// 2 k.p from the parent's norm.
 template <int WT>
 __global__ void k_finalize(KeyParams P, uint64_t* keys, uint64_t* hl, int64_t par0, int s_a,
                            const uint64_t* __restrict__ stepkey, const uint64_t* __restrict__ stepg,
-                           const int64_t* __restrict__ slot_of, const int32_t* __restrict__ flag,
-                           const int32_t* __restrict__ pos, int64_t n, int64_t base, int lvl, int8_t* level,
+                           const int64_t* __restrict__ pnorm, const int64_t* __restrict__ slot_of,
+                           const int64_t* __restrict__ cand, int64_t added, int64_t base, int lvl, int8_t* level,
                            int64_t* norm, uint64_t* table, int64_t* zero_idx) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n || !flag[c]) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= added) return;
+  const int64_t c = cand[t];
   const int64_t par = c / s_a;
   const int j = (int)(c - par * s_a);
   uint64_t pk[WT], sk[WT], ck[WT];
   load_key<WT>(keys, par0 + par, pk);
   load_key<WT>(stepkey, j, sk);
   add_keys<WT>(pk, sk, P, ck);
-  const int64_t idx = base + pos[c];
+  const int64_t idx = base + t;
 #pragma unroll
   for (int w = 0; w < WT; ++w) keys[idx * WT + w] = ck[w];
   const uint64_t lin = hl[par0 + par] + __ldg(stepg + j);
   hl[idx] = lin;
   level[idx] = (int8_t)lvl;
-  const int64_t nr = key_norm<WT>(ck, P);
+  const int64_t nr = norm[par0 + par] + __ldg(pnorm + j) + 2 * dot_step<WT>(pk, sk, P);
   norm[idx] = nr;
   if (nr == 0) *zero_idx = idx;
   table[slot_of[c]] = slot_word(slot_fp(hash_of_lin(lin)), (uint64_t)idx);
 }
 
-// Neighbour lookups: nbr[j*size + i] = index of k_i - p_j (= k_i + p_{s_a-1-j})
-// when it lies in S, is not 0, and k_i is not 0; else -1 (nbr is filled with
-// -1 beforehand).  With keep_zero (the ADR operator) the zero frequency is an
-// ordinary row and column.  supp a_hat is sorted and symmetric (p_{s_a-1-j} =
-// -p_j, p_j0 = 0), and l = k - p_j lies in S exactly when k = l - p_{s_a-1-j}
-// does: thread (j, i) with j < j0 looks up l = k_i - p_j and, when found,
-// writes both nbr[j][i] = l and nbr[s_a-1-j][l] = i, so every pair is probed
-// once; thread (j0, i) writes the diagonal entry.  Consecutive threads take
-// consecutive rows of one step (coalesced reads of hl and writes of nbr).
+// Neighbour words: for row i and step j, the index of k_i - p_j when it lies
+// in S, is not 0, and k_i is not 0; else -1.  Steps j <= j0 are in
+// lo[i Ls + j] (L = j0 + 1 of them), steps j > j0 in hi[i Hs + j - L] (H =
+// s_a - L); row-major with the row strides Ls, Hs rounded up to multiples of 4
+// (16-byte rows, padding -1), so one row moves as a few int4 words.  A row
+// is scanned as the virtual slots u < Ls + Hs: lo then hi.
+struct NbrView {
+  int32_t* lo;
+  int32_t* hi;
+  int L, H, Ls, Hs;
+};
+
+__device__ __forceinline__ const int32_t* nbr_addr(const NbrView& nb, int64_t i, int j) {
+  return j < nb.L ? nb.lo + i * nb.Ls + j : nb.hi + i * nb.Hs + (j - nb.L);
+}
+
+// Words u .. u + 3 of row i (u a multiple of 4 below Ls + Hs).
+__device__ __forceinline__ int4 nbr_chunk(const NbrView& nb, int64_t i, int u) {
+  const int32_t* p = u < nb.Ls ? nb.lo + i * nb.Ls + u : nb.hi + i * nb.Hs + (u - nb.Ls);
+  return __ldg(reinterpret_cast<const int4*>(p));
+}
+
+// Step of virtual slot u, or -1 for padding.
+__device__ __forceinline__ int nbr_step(const NbrView& nb, int u) {
+  if (u < nb.Ls) return u < nb.L ? u : -1;
+  const int h = u - nb.Ls;
+  return h < nb.H ? nb.L + h : -1;
+}
+
+__device__ __forceinline__ int32_t int4_at(const int4& x, int q) {
+  return q == 0 ? x.x : q == 1 ? x.y : q == 2 ? x.z : x.w;
+}
+
+// Steps whose lookups (or neighbour words) one thread issues before using
+// them: a multiple of 4.
+constexpr int kNbrBatch = 8;
+
+// Neighbour lookups.  With keep_zero (the ADR operator) the zero frequency is
+// an ordinary row and column.  supp a_hat is sorted and symmetric (p_{s_a-1-j}
+// = -p_j, p_j0 = 0), and l = k - p_j lies in S exactly when k = l - p_{s_a-1-j}
+// does: for j < j0 the thread of row i looks up l = k_i - p_j and writes
+// lo[i][j] (l or -1) and, when found, hi[l][s_a-1-j] = i, so every pair is
+// probed once (hi is filled with -1 beforehand).  One thread per row: the
+// first table words of kNbrBatch steps are loaded before any is resolved, and
+// the row's lo words are stored as int4.  A slot whose 31-bit fingerprint
+// agrees is confirmed by the exact word-by-word comparison.
 template <int WT>
-__global__ void k_neighbors(KeyParams P, const uint64_t* __restrict__ keys, const uint64_t* __restrict__ hl,
-                            int64_t size, int s_a, int j0, const uint64_t* __restrict__ stepkey,
-                            const uint64_t* __restrict__ stepg, const uint64_t* __restrict__ table, uint64_t capmask,
-                            const int64_t* __restrict__ zero_dev, bool keep_zero, int32_t* nbr) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= size * (j0 + 1)) return;
+__global__ void __launch_bounds__(256) k_neighbors(KeyParams P, const uint64_t* __restrict__ keys,
+                                                   const uint64_t* __restrict__ hl, int64_t size, int s_a, int j0,
+                                                   const uint64_t* __restrict__ stepkey,
+                                                   const uint64_t* __restrict__ stepg,
+                                                   const uint64_t* __restrict__ table, uint64_t capmask,
+                                                   const int64_t* __restrict__ zero_dev, bool keep_zero, NbrView nb) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= size) return;
   const int64_t zero_idx = keep_zero ? -1 : *zero_dev;
-  const int j = (int)(c / size);
-  const int64_t i = c - (int64_t)j * size;
-  if (i == zero_idx) return;
-  if (j == j0) {
-    nbr[(int64_t)j0 * size + i] = (int32_t)i;
+  int4* out = reinterpret_cast<int4*>(nb.lo + i * nb.Ls);
+  if (i == zero_idx) {
+    for (int u = 0; u < nb.Ls; u += 4) out[u / 4] = make_int4(-1, -1, -1, -1);
     return;
   }
-  const int jr = s_a - 1 - j;   // p_jr = -p_j: k_i - p_j = k_i + p_jr
-  const uint64_t lin = __ldg(hl + i) + __ldg(stepg + jr);
+  const uint64_t hli = __ldg(hl + i);
   const uint64_t* ki = keys + i * WT;
-  const uint64_t* sk = stepkey + (int64_t)jr * WT;
-  const int64_t v = table_find_h(table, capmask, hash_of_lin(lin), hl, lin,
-                                 [&](int64_t o) { return key_eq_sum<WT>(keys + o * WT, ki, sk, P); });
-  if (v >= 0 && v != zero_idx) {
-    nbr[(int64_t)j * size + i] = (int32_t)v;
-    nbr[(int64_t)jr * size + v] = (int32_t)i;
+  for (int jb = 0; jb < nb.Ls; jb += kNbrBatch) {
+    uint64_t hh[kNbrBatch], w[kNbrBatch];
+#pragma unroll
+    for (int q = 0; q < kNbrBatch; ++q) {
+      const int j = jb + q;
+      if (j < j0) {
+        hh[q] = hash_of_lin(hli + __ldg(stepg + (s_a - 1 - j)));
+        w[q] = __ldg(table + (hh[q] & capmask));
+      }
+    }
+    int32_t r[kNbrBatch];
+#pragma unroll
+    for (int q = 0; q < kNbrBatch; ++q) {
+      const int j = jb + q;
+      r[q] = j == j0 ? (int32_t)i : -1;
+      if (j >= j0) continue;
+      const int jr = s_a - 1 - j;   // p_jr = -p_j: k_i - p_j = k_i + p_jr
+      const uint64_t* sk = stepkey + (int64_t)jr * WT;
+      const uint64_t fp = slot_fp(hh[q]);
+      uint64_t h = hh[q] & capmask, v = w[q];
+      int64_t found = -1;
+      for (uint64_t probe = 0; probe <= capmask; ++probe) {
+        if (v == kEmpty) break;
+        if (word_fp(v) == fp) {
+          const int64_t o = (int64_t)word_low(v);
+          if (key_eq_sum<WT>(keys + o * WT, ki, sk, P)) { found = o; break; }
+        }
+        h = (h + 1) & capmask;
+        v = __ldg(table + h);
+      }
+      if (found >= 0 && found != zero_idx) {
+        r[q] = (int32_t)found;
+        nb.hi[found * nb.Hs + (jr - nb.L)] = (int32_t)i;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kNbrBatch; q += 4)
+      if (jb + q < nb.Ls) out[(jb + q) / 4] = make_int4(r[q], r[q + 1], r[q + 2], r[q + 3]);
   }
 }
 
 // Per-row counts, per-slice widths (max over the slice's 32 rows), nnz.
-__global__ void k_row_counts(const int32_t* __restrict__ nbr, int64_t size, int64_t rows_pad, int s_a,
-                             int32_t* slice_w, unsigned long long* nnz) {
+__global__ void k_row_counts(NbrView nb, int64_t size, int64_t rows_pad, int32_t* slice_w,
+                             unsigned long long* nnz) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows_pad) return;
   int32_t cnt = 0;
   if (i < size)
-    for (int j = 0; j < s_a; ++j) cnt += (nbr[(int64_t)j * size + i] >= 0);
+    for (int ub = 0; ub < nb.Ls + nb.Hs; ub += kNbrBatch) {
+      int4 x[kNbrBatch / 4];   // loads issued before use (latency-bound otherwise)
+#pragma unroll
+      for (int q = 0; q < kNbrBatch / 4; ++q)
+        x[q] = ub + 4 * q < nb.Ls + nb.Hs ? nbr_chunk(nb, i, ub + 4 * q) : make_int4(-1, -1, -1, -1);
+#pragma unroll
+      for (int q = 0; q < kNbrBatch / 4; ++q) cnt += (x[q].x >= 0) + (x[q].y >= 0) + (x[q].z >= 0) + (x[q].w >= 0);
+    }
   const int32_t w = __reduce_max_sync(0xffffffffu, cnt);
   const unsigned long long tot = __reduce_add_sync(0xffffffffu, (unsigned)cnt);
   if ((threadIdx.x & 31) == 0) {
@@ -440,7 +548,7 @@ __global__ void k_row_counts(const int32_t* __restrict__ nbr, int64_t size, int6
 // coefficient).  Also stores the FP64 coefficient of every entry,
 // (|k|^2 + |l|^2 - |p_j|^2) * 2 pi^2 a_hat_j = 4 pi^2 (k.l) a_hat_j (eq. GF), so
 // that the FP64 operator spends four FP64 FMAs per nonzero.
-__global__ void k_fill_slices(const int32_t* __restrict__ nbr, int64_t size, int64_t rows_pad, int s_a, int j0,
+__global__ void k_fill_slices(NbrView nb, int64_t size, int64_t rows_pad, int s_a, int j0,
                               const int32_t* __restrict__ woff, int colbits, const int64_t* __restrict__ norm,
                               const int64_t* __restrict__ pnorm, const double2* __restrict__ ca64, uint32_t* ent,
                               double2* ecoef, bool real) {
@@ -454,12 +562,24 @@ __global__ void k_fill_slices(const int32_t* __restrict__ nbr, int64_t size, int
   int t = 0;
   if (i < size) {
     const int64_t nk = norm[i];
-    for (int j = 0; j < s_a; ++j) {
-      const int32_t v = nbr[(int64_t)j * size + i];
-      if (v >= 0) {
+    for (int ub = 0; ub < nb.Ls + nb.Hs; ub += kNbrBatch) {
+      int4 x[kNbrBatch / 4];
+#pragma unroll
+      for (int q = 0; q < kNbrBatch / 4; ++q)
+        x[q] = ub + 4 * q < nb.Ls + nb.Hs ? nbr_chunk(nb, i, ub + 4 * q) : make_int4(-1, -1, -1, -1);
+      int32_t v[kNbrBatch];
+      int64_t nv[kNbrBatch];
+#pragma unroll
+      for (int q = 0; q < kNbrBatch; ++q) v[q] = int4_at(x[q / 4], q % 4);
+#pragma unroll
+      for (int q = 0; q < kNbrBatch; ++q) nv[q] = v[q] >= 0 ? __ldg(norm + v[q]) : 0;
+#pragma unroll
+      for (int q = 0; q < kNbrBatch; ++q) {
+        if (v[q] < 0) continue;
+        const int j = nbr_step(nb, ub + q);
         const int64_t e = base + (int64_t)t++ * kSlice;
-        ent[e] = (uint32_t)v | ((uint32_t)j << colbits);
-        const double sc = (double)(nk + norm[v] - pnorm[j]);
+        ent[e] = (uint32_t)v[q] | ((uint32_t)j << colbits);
+        const double sc = (double)(nk + nv[q] - pnorm[j]);
         if (real) ecoef_re[e] = sc * ca64[j].x;
         else ecoef[e] = make_double2(sc * ca64[j].x, sc * ca64[j].y);
       }
@@ -480,7 +600,7 @@ __global__ void k_fill_slices(const int32_t* __restrict__ nbr, int64_t size, int
 // coordinates of l unpacked from its key.  The entry with l = k (p_j = 0) is
 // also the row's Jacobi diagonal.
 template <int WT>
-__global__ void k_fill_slices_adr(KeyParams P, const uint64_t* __restrict__ keys, const int32_t* __restrict__ nbr,
+__global__ void k_fill_slices_adr(KeyParams P, const uint64_t* __restrict__ keys, NbrView nb,
                                   int64_t size, int64_t rows_pad, int s_a, int j0, const int32_t* __restrict__ woff,
                                   int colbits, const int64_t* __restrict__ norm, const int64_t* __restrict__ pnorm,
                                   const double2* __restrict__ ca64, const double2* __restrict__ bval,
@@ -500,7 +620,7 @@ __global__ void k_fill_slices_adr(KeyParams P, const uint64_t* __restrict__ keys
     const int64_t nk = norm[i];
     double2 dg = make_double2(1.0, 0.0);
     for (int j = 0; j < s_a; ++j) {
-      const int32_t v = nbr[(int64_t)j * size + i];
+      const int32_t v = *nbr_addr(nb, i, j);
       if (v < 0) continue;
       const int64_t e = base + (int64_t)t++ * kSlice;
       ent[e] = (uint32_t)v | ((uint32_t)j << colbits);
@@ -609,6 +729,21 @@ static ss_status grow_table(ss_stamp_s* S, int64_t need, const KeyParams& P, cud
   return SS_OK;
 }
 
+// The table is sized for the candidates of the last level and is mostly
+// empty once the set is complete; the lookups that follow probe one of about
+// 2 |S| slots instead (fewer sectors per probe, more of it resident in L2).
+static ss_status compact_table(ss_stamp_s* S, cudaStream_t st) {
+  int64_t want = (int64_t)next_pow2((uint64_t)std::max<int64_t>(2 * S->size, 1024));
+  if (want >= S->cap || S->size == 0) return SS_OK;
+  SS_TRY(S->table.alloc(want, st));
+  S->cap = want;
+  SS_CUDA(cudaMemsetAsync(S->table.get(), 0xff, want * sizeof(uint64_t), st));
+  k_rehash<<<nblk(S->size), 256, 0, st>>>(S->hl.get(), S->size, S->table.get(), (uint64_t)want - 1,
+                                          S->err_dev.get());
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
 static ss_status resize_keys(ss_stamp_s* S, int64_t cap, cudaStream_t st);
 
 static ss_status grow_keys(ss_stamp_s* S, int64_t need, cudaStream_t st) {
@@ -685,7 +820,7 @@ static ss_status make_layout(int d, int64_t maxabs, KeyLayout* out) {
 static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st) {
   const KeyParams P = make_key_params(S->key);
   const int s_a = S->s_a;
-  DevBuf<int64_t> slot_of, d_total;
+  DevBuf<int64_t> slot_of, d_total, cand;
   DevBuf<int32_t> flag;
   SS_TRY(d_total.alloc_tmp(1, st));
   for (int n = n_from; n <= n_to; ++n) {
@@ -716,14 +851,17 @@ static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st
     int32_t e = 0;
     SS_TRY(read_back(st, {{&added, d_total.get(), sizeof(int64_t)}, {&e, S->err_dev.get(), sizeof(int32_t)}}));
     if (e) SS_FAIL((ss_status)e, "stamp: hash table exhausted at level %d", n);
-    {
+    if (added > 0) {
       ProfScope prof_("k_finalize", st);
-      SS_DISPATCH_WT(S->key.WT, (k_finalize<WT><<<nblk(ncand), 256, 0, st>>>(P, S->keys.get(), S->hl.get(), par0,
+      SS_TRY(cand.ensure_tmp(added, st));
+      k_compact_winners<<<nblk(ncand), 256, 0, st>>>(flag.get(), pos.get(), ncand, cand.get());
+      SS_DISPATCH_WT(S->key.WT, (k_finalize<WT><<<nblk(added), 256, 0, st>>>(P, S->keys.get(), S->hl.get(), par0,
                                                                              s_a, S->stepkey.get(), S->stepg.get(),
-                                                                             slot_of.get(), flag.get(),
-                                                                             pos.get(), ncand, S->size, n,
-                                                                             S->level.get(), S->norm.get(),
-                                                                             S->table.get(), S->zidx_dev.get())));
+                                                                             S->pnorm.get(), slot_of.get(), cand.get(),
+                                                                             added,
+                                                                             S->size, n, S->level.get(),
+                                                                             S->norm.get(), S->table.get(),
+                                                                             S->zidx_dev.get())));
     }
     SS_LAUNCH_CHECK();
     S->size += added;
@@ -753,15 +891,17 @@ __global__ void k_half_index(KeyParams P, const uint64_t* __restrict__ keys, con
   // -k packs as 2 bias - k field by field: its linear form is 2 lin(bias) - lin(k)
   const uint64_t lin = 2 * P.lin_bias - __ldg(hl + g);
   const uint64_t* kg = keys + g * WT;
-  const int64_t m = table_find_h(table, capmask, hash_of_lin(lin), hl, lin,
+  const int64_t m = table_find_h(table, capmask, hash_of_lin(lin), nullptr, lin,
                                  [&](int64_t o) { return key_eq_sum<WT>(keys + o * WT, kg, nullptr, P); });
   if (m < 0) atomicExch(err, 1);
   mirror[g] = m;
+  // Fields are packed first coordinate first from the top bit down, biased
+  // and without carries, so the words compare like the coordinates: k >lex 0
+  // iff the word sequence of k exceeds that of the packed zero.
   int p = 0;
-  for (int c = 0; c < P.d; ++c) {
-    const int32_t x = unpack_coord(k, P, c);
-    if (x != 0) { p = x > 0; break; }
-  }
+#pragma unroll
+  for (int w = WT - 1; w >= 0; --w)
+    if (k[w] != P.bias[w]) p = k[w] > P.bias[w];
   plus[g] = p;
 }
 
@@ -823,18 +963,30 @@ __global__ void k_half_fill(const int32_t* __restrict__ plus_rows, int64_t n_plu
     const int64_t s = g / kSlice;
     const int64_t base = (int64_t)woff[s] * kSlice + (g % kSlice);
     const int w = woff[s + 1] - woff[s];
-    for (int tf = 0; tf < w; ++tf) {
-      const int64_t e = base + (int64_t)tf * kSlice;
-      const int64_t c = ent[e] & colmask;
-      if (c == pad_col) continue;
-      const int32_t h = hpos[c];
-      if (h == -1) continue;   // the zero column is never stored; kept for safety
-      const uint32_t col = h >= 0 ? (uint32_t)h : (uint32_t)(-2 - h);
-      const uint32_t j = ent[e] >> colbits;
-      ent_h[base_h + (int64_t)t * kSlice] = col | (j << colbits_h) | (h < 0 ? 0x80000000u : 0u);
-      if (real) ecoef_h_re[base_h + (int64_t)t * kSlice] = ecoef_re[e];
-      else ecoef_h[base_h + (int64_t)t * kSlice] = ecoef[e];
-      ++t;
+    for (int tf0 = 0; tf0 < w; tf0 += kNbrBatch) {
+      // entry words, then the gathered positions, loaded before use
+      uint32_t ev[kNbrBatch];
+      int32_t hv[kNbrBatch];
+#pragma unroll
+      for (int q = 0; q < kNbrBatch; ++q)
+        ev[q] = tf0 + q < w ? __ldg(ent + base + (int64_t)(tf0 + q) * kSlice) : (uint32_t)pad_col;
+#pragma unroll
+      for (int q = 0; q < kNbrBatch; ++q) {
+        const int64_t c = ev[q] & colmask;
+        hv[q] = c == pad_col ? -1 : __ldg(hpos + c);
+      }
+#pragma unroll
+      for (int q = 0; q < kNbrBatch; ++q) {
+        const int32_t h = hv[q];
+        if (h == -1) continue;   // padding (the zero column is never stored)
+        const int64_t e = base + (int64_t)(tf0 + q) * kSlice;
+        const uint32_t col = h >= 0 ? (uint32_t)h : (uint32_t)(-2 - h);
+        const uint32_t j = ev[q] >> colbits;
+        ent_h[base_h + (int64_t)t * kSlice] = col | (j << colbits_h) | (h < 0 ? 0x80000000u : 0u);
+        if (real) ecoef_h_re[base_h + (int64_t)t * kSlice] = ecoef_re[e];
+        else ecoef_h[base_h + (int64_t)t * kSlice] = ecoef[e];
+        ++t;
+      }
     }
   }
   for (; t < w_h; ++t) {
@@ -927,10 +1079,22 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
     SS_FAIL(SS_ERR_KEY_RANGE, "stamp: |S| = %lld too large for %d-bit columns", (long long)S->size,
             colbits_of(S->jbits));
   SS_TRY(grow_keys(S, S->rows_pad + 1, st));   // norm padded to rows_pad + 1
-  DevBuf<int32_t> nbr, slice_w;
+  {
+    ProfScope prof_("compact_table", st);
+    SS_TRY(compact_table(S, st));
+  }
+  DevBuf<int32_t> nbr_lo, nbr_hi, slice_w;
   DevBuf<unsigned long long> d_nnz;
   DevBuf<int64_t> d_total;
-  SS_TRY(nbr.alloc_tmp((size_t)S->size * s_a, st));
+  NbrView nb;
+  nb.L = S->j0 + 1;
+  nb.H = s_a - nb.L;
+  nb.Ls = (nb.L + 3) / 4 * 4;
+  nb.Hs = (nb.H + 3) / 4 * 4;
+  SS_TRY(nbr_lo.alloc_tmp((size_t)S->size * nb.Ls, st));
+  SS_TRY(nbr_hi.alloc_tmp((size_t)std::max(S->size * nb.Hs, (int64_t)4), st));
+  nb.lo = nbr_lo.get();
+  nb.hi = nbr_hi.get();
   SS_TRY(slice_w.alloc_tmp(S->n_slices + 1, st));
   SS_TRY(d_nnz.alloc_tmp(1, st));
   SS_TRY(d_total.alloc_tmp(1, st));
@@ -939,15 +1103,15 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
                          {slice_w.get(), (S->n_slices + 1) * sizeof(int32_t), 0}}));
   {
     ProfScope prof_("k_neighbors", st);
-    SS_CUDA(cudaMemsetAsync(nbr.get(), 0xff, (size_t)S->size * s_a * sizeof(int32_t), st));
-    SS_DISPATCH_WT(S->key.WT, (k_neighbors<WT><<<nblk(S->size * (S->j0 + 1)), 256, 0, st>>>(
+    if (nb.Hs > 0) SS_CUDA(cudaMemsetAsync(nb.hi, 0xff, (size_t)S->size * nb.Hs * sizeof(int32_t), st));
+    SS_DISPATCH_WT(S->key.WT, (k_neighbors<WT><<<nblk(S->size), 256, 0, st>>>(
                                   P, S->keys.get(), S->hl.get(), S->size, s_a, S->j0, S->stepkey.get(), S->stepg.get(),
                                   S->table.get(),
-                                  (uint64_t)S->cap - 1, S->zidx_dev.get(), S->adr, nbr.get())));
+                                  (uint64_t)S->cap - 1, S->zidx_dev.get(), S->adr, nb)));
   }
   {
     ProfScope prof_("k_row_counts", st);
-    k_row_counts<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, slice_w.get(), d_nnz.get());
+    k_row_counts<<<nblk(S->rows_pad), 256, 0, st>>>(nb, S->size, S->rows_pad, slice_w.get(), d_nnz.get());
   }
   SS_LAUNCH_CHECK();
   SS_TRY(S->slice_off.alloc(S->n_slices + 1, st));
@@ -968,13 +1132,13 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   if (S->adr) {
     SS_TRY(S->diag64.alloc(S->rows_pad + 1, st));
     SS_DISPATCH_WT(S->key.WT, (k_fill_slices_adr<WT><<<nblk(S->rows_pad + 1), 256, 0, st>>>(
-                                  P, S->keys.get(), nbr.get(), S->size, S->rows_pad, s_a, S->j0, S->slice_off.get(),
+                                  P, S->keys.get(), nb, S->size, S->rows_pad, s_a, S->j0, S->slice_off.get(),
                                   colbits_of(S->jbits), S->norm.get(), S->pnorm.get(), S->ca64.get(), S->bval.get(),
                                   S->cval.get(), S->ent.get(), S->ecoef64.get(), S->diag64.get())));
   } else {
     {
       ProfScope prof_("k_fill_slices", st);
-      k_fill_slices<<<nblk(S->rows_pad), 256, 0, st>>>(nbr.get(), S->size, S->rows_pad, s_a, S->j0,
+      k_fill_slices<<<nblk(S->rows_pad), 256, 0, st>>>(nb, S->size, S->rows_pad, s_a, S->j0,
                                                        S->slice_off.get(), colbits_of(S->jbits), S->norm.get(),
                                                        S->pnorm.get(), S->ca64.get(), S->ent.get(), S->ecoef64.get(),
                                                        S->a_real);
