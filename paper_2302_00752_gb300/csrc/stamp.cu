@@ -20,6 +20,7 @@
 #include <map>
 
 #include "keys.cuh"
+#include "scan.cuh"
 
 namespace ss {
 namespace {
@@ -309,7 +310,7 @@ __global__ void k_insert(KeyParams P, const uint64_t* __restrict__ keys, const u
                          int32_t* err) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_par * s_a) return;
-  const int64_t par = c / s_a;
+  const int64_t par = (uint32_t)c / (uint32_t)s_a;   // candidate ids stay below 2^32
   const int j = (int)(c - par * s_a);
   if (j == j0) { slot_of[c] = -1; return; }
   const uint64_t lin = __ldg(hl + par0 + par) + __ldg(stepg + j);
@@ -329,7 +330,7 @@ __global__ void k_insert(KeyParams P, const uint64_t* __restrict__ keys, const u
     if (word_fp(v) == fp) {
       if (v & kPending) {
         const int64_t oc = (int64_t)word_low(v);
-        const int64_t opar = oc / s_a;
+        const int64_t opar = (uint32_t)oc / (uint32_t)s_a;
         const int oj = (int)(oc - opar * s_a);
         if (__ldg(hl + par0 + opar) + __ldg(stepg + oj) == lin &&
             sums_equal<WT>(keys + (par0 + opar) * WT, stepkey + (int64_t)oj * WT, pk, sk)) {
@@ -349,21 +350,26 @@ __global__ void k_insert(KeyParams P, const uint64_t* __restrict__ keys, const u
   slot_of[c] = -1;
 }
 
-__global__ void k_winner_flags(const int64_t* __restrict__ slot_of, const uint64_t* __restrict__ table,
-                               int64_t n, int32_t* flag) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
-  const int64_t s = slot_of[c];
-  const uint64_t v = s >= 0 ? __ldg(table + s) : kEmpty;
-  flag[c] = (s >= 0 && (v & kPending) && word_low(v) == (uint64_t)c) ? 1 : 0;
-}
+// A candidate wins when its slot still holds its own (pending) id: the
+// smallest id among the candidates of one new key.
+struct WinnerFlag {
+  const int64_t* slot_of;
+  const uint64_t* table;
+  __device__ int32_t operator()(int64_t c) const {
+    const int64_t s = slot_of[c];
+    if (s < 0) return 0;
+    const uint64_t v = __ldg(table + s);
+    return ((v & kPending) && word_low(v) == (uint64_t)c) ? 1 : 0;
+  }
+};
 
-// The winning candidates in canonical order: cand[pos[c]] = c.
-__global__ void k_compact_winners(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t n,
-                                  int64_t* cand) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < n && flag[c]) cand[pos[c]] = c;
-}
+// The winners in canonical order: cand[prefix] = c.
+struct WinnerPut {
+  int64_t* cand;
+  __device__ void operator()(int64_t c, int32_t win, int64_t prefix) const {
+    if (win) cand[prefix] = c;
+  }
+};
 
 // k . p over the fields where the step p is nonzero (k, p packed; a step
 // usually touches few coordinates).  The highest set bit of p ^ bias lies in
@@ -388,33 +394,46 @@ __device__ __forceinline__ int64_t dot_step(const uint64_t* k, const uint64_t* p
 }
 
 // One thread per new element t (canonical index base + t), so the key
-// arithmetic and the stores run in full warps.  |k + p|^2 = |k|^2 + |p|^2 +
-// 2 k.p from the parent's norm.
+// arithmetic runs in full warps; the block's new keys are staged in shared
+// memory and stored as one contiguous run (coalesced).  |k + p|^2 = |k|^2 +
+// |p|^2 + 2 k.p from the parent's norm.
+constexpr int kFinThreads = 256;
+
 template <int WT>
-__global__ void k_finalize(KeyParams P, uint64_t* keys, uint64_t* hl, int64_t par0, int s_a,
-                           const uint64_t* __restrict__ stepkey, const uint64_t* __restrict__ stepg,
-                           const int64_t* __restrict__ pnorm, const int64_t* __restrict__ slot_of,
-                           const int64_t* __restrict__ cand, int64_t added, int64_t base, int lvl, int8_t* level,
-                           int64_t* norm, uint64_t* table, int64_t* zero_idx) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= added) return;
-  const int64_t c = cand[t];
-  const int64_t par = c / s_a;
-  const int j = (int)(c - par * s_a);
-  uint64_t pk[WT], sk[WT], ck[WT];
-  load_key<WT>(keys, par0 + par, pk);
-  load_key<WT>(stepkey, j, sk);
-  add_keys<WT>(pk, sk, P, ck);
-  const int64_t idx = base + t;
+__global__ void __launch_bounds__(kFinThreads) k_finalize(KeyParams P, uint64_t* keys, uint64_t* hl, int64_t par0,
+                                                          int s_a, const uint64_t* __restrict__ stepkey,
+                                                          const uint64_t* __restrict__ stepg,
+                                                          const int64_t* __restrict__ pnorm,
+                                                          const int64_t* __restrict__ slot_of,
+                                                          const int64_t* __restrict__ cand, int64_t added,
+                                                          int64_t base, int lvl, int8_t* level, int64_t* norm,
+                                                          uint64_t* table, int64_t* zero_idx) {
+  __shared__ uint64_t stage[kFinThreads * WT];
+  const int64_t t0 = (int64_t)blockIdx.x * kFinThreads;
+  const int64_t t = t0 + threadIdx.x;
+  if (t < added) {
+    const int64_t c = cand[t];
+    const int64_t par = (uint32_t)c / (uint32_t)s_a;   // candidate ids stay below 2^32
+    const int j = (int)(c - par * s_a);
+    uint64_t pk[WT], sk[WT], ck[WT];
+    load_key<WT>(keys, par0 + par, pk);
+    load_key<WT>(stepkey, j, sk);
+    add_keys<WT>(pk, sk, P, ck);
 #pragma unroll
-  for (int w = 0; w < WT; ++w) keys[idx * WT + w] = ck[w];
-  const uint64_t lin = hl[par0 + par] + __ldg(stepg + j);
-  hl[idx] = lin;
-  level[idx] = (int8_t)lvl;
-  const int64_t nr = norm[par0 + par] + __ldg(pnorm + j) + 2 * dot_step<WT>(pk, sk, P);
-  norm[idx] = nr;
-  if (nr == 0) *zero_idx = idx;
-  table[slot_of[c]] = slot_word(slot_fp(hash_of_lin(lin)), (uint64_t)idx);
+    for (int w = 0; w < WT; ++w) stage[threadIdx.x * WT + w] = ck[w];
+    const int64_t idx = base + t;
+    const uint64_t lin = hl[par0 + par] + __ldg(stepg + j);
+    hl[idx] = lin;
+    level[idx] = (int8_t)lvl;
+    const int64_t nr = norm[par0 + par] + __ldg(pnorm + j) + 2 * dot_step<WT>(pk, sk, P);
+    norm[idx] = nr;
+    if (nr == 0) *zero_idx = idx;
+    table[slot_of[c]] = slot_word(slot_fp(hash_of_lin(lin)), (uint64_t)idx);
+  }
+  __syncthreads();
+  const int64_t rows = added - t0 < kFinThreads ? added - t0 : kFinThreads;
+  uint64_t* dst = keys + (base + t0) * WT;
+  for (int64_t q = threadIdx.x; q < rows * WT; q += kFinThreads) dst[q] = stage[q];
 }
 
 // Neighbour words: for row i and step j, the index of k_i - p_j when it lies
@@ -821,7 +840,6 @@ static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st
   const KeyParams P = make_key_params(S->key);
   const int s_a = S->s_a;
   DevBuf<int64_t> slot_of, d_total, cand;
-  DevBuf<int32_t> flag;
   SS_TRY(d_total.alloc_tmp(1, st));
   for (int n = n_from; n <= n_to; ++n) {
     const int64_t par0 = S->level_start[n - 1], n_par = S->level_start[n] - par0;
@@ -831,7 +849,7 @@ static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st
     SS_TRY(grow_table(S, S->size + n_par * (s_a - 1), P, st, S->err_dev.get()));
     SS_TRY(grow_keys(S, S->size + n_par * (s_a - 1), st));
     SS_TRY(slot_of.ensure_tmp(ncand, st));
-    SS_TRY(flag.ensure_tmp(ncand, st));
+    SS_TRY(cand.ensure_tmp(ncand, st));
     {
       ProfScope prof_("k_insert", st);
       SS_DISPATCH_WT(S->key.WT, (k_insert<WT><<<nblk(ncand), 256, 0, st>>>(
@@ -839,23 +857,23 @@ static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st
                                     S->stepg.get(), S->table.get(), (uint64_t)S->cap - 1, slot_of.get(),
                                     S->err_dev.get())));
     }
-    {
-      ProfScope prof_("k_winner_flags", st);
-      k_winner_flags<<<nblk(ncand), 256, 0, st>>>(slot_of.get(), S->table.get(), ncand, flag.get());
-    }
     SS_LAUNCH_CHECK();
-    DevBuf<int32_t> pos;
-    SS_TRY(pos.alloc_tmp(ncand, st));
-    SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), ncand, d_total.get(), st));
+    {
+      // winners (the candidate that holds its slot) in candidate order: one
+      // pass computes the flags, their prefix sums and the compaction
+      ProfScope prof_("winners", st);
+      SS_TRY(scan_lookback(WinnerFlag{slot_of.get(), S->table.get()}, WinnerPut{cand.get()}, ncand, d_total.get(),
+                           S->err_dev.get(), st));
+    }
     int64_t added = 0;
     int32_t e = 0;
     SS_TRY(read_back(st, {{&added, d_total.get(), sizeof(int64_t)}, {&e, S->err_dev.get(), sizeof(int32_t)}}));
+    if (e == SS_ERR_TIMEOUT) SS_FAIL(SS_ERR_TIMEOUT, "stamp: a bounded device wait gave up at level %d", n);
     if (e) SS_FAIL((ss_status)e, "stamp: hash table exhausted at level %d", n);
     if (added > 0) {
       ProfScope prof_("k_finalize", st);
-      SS_TRY(cand.ensure_tmp(added, st));
-      k_compact_winners<<<nblk(ncand), 256, 0, st>>>(flag.get(), pos.get(), ncand, cand.get());
-      SS_DISPATCH_WT(S->key.WT, (k_finalize<WT><<<nblk(added), 256, 0, st>>>(P, S->keys.get(), S->hl.get(), par0,
+      SS_DISPATCH_WT(S->key.WT, (k_finalize<WT><<<nblk(added, kFinThreads), kFinThreads, 0, st>>>(
+                                    P, S->keys.get(), S->hl.get(), par0,
                                                                              s_a, S->stepkey.get(), S->stepg.get(),
                                                                              S->pnorm.get(), slot_of.get(), cand.get(),
                                                                              added,
@@ -1039,7 +1057,7 @@ static ss_status build_half(ss_stamp_s* S, cudaStream_t st) {
                                   plus.get(), S->err_dev.get() + 3)));
   }
   SS_LAUNCH_CHECK();
-  SS_TRY(exclusive_scan_i32(plus.get(), ppos.get(), S->size, total.get(), st));
+  SS_TRY(scan_lookback(LbRead{plus.get()}, LbWrite{ppos.get()}, S->size, total.get(), S->err_dev.get(), st));
   {
     ProfScope prof_("k_half_rows", st);
     k_half_rows<<<nblk(S->size), 256, 0, st>>>(plus.get(), ppos.get(), S->mirror.get(), S->norm.get(), S->size,
@@ -1053,7 +1071,8 @@ static ss_status build_half(ss_stamp_s* S, cudaStream_t st) {
                                                        S->ent.get(), colmask, S->rows_pad, slice_w.get());
   }
   SS_LAUNCH_CHECK();
-  SS_TRY(exclusive_scan_i32(slice_w.get(), S->woff_h.get(), S->n_slices_h + 1, total.get(), st));
+  SS_TRY(scan_lookback(LbRead{slice_w.get()}, LbWrite{S->woff_h.get()}, S->n_slices_h + 1, total.get(),
+                       S->err_dev.get(), st));
   {
     ProfScope prof_("k_half_fill", st);
     k_half_fill<<<nblk(S->rows_pad_h), 256, 0, st>>>(S->plus_rows.get(), n_plus, S->rows_pad_h, S->slice_off.get(),
@@ -1115,7 +1134,8 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   }
   SS_LAUNCH_CHECK();
   SS_TRY(S->slice_off.alloc(S->n_slices + 1, st));
-  SS_TRY(exclusive_scan_i32(slice_w.get(), S->slice_off.get(), S->n_slices + 1, d_total.get(), st));
+  SS_TRY(scan_lookback(LbRead{slice_w.get()}, LbWrite{S->slice_off.get()}, S->n_slices + 1, d_total.get(),
+                       S->err_dev.get(), st));
   int64_t total_w = 0;
   unsigned long long hnnz = 0;
   S->woff_host.resize(S->n_slices + 1);
@@ -1157,6 +1177,7 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
                           {S->woff_h_host.data(), S->woff_h.get(), (S->n_slices_h + 1) * sizeof(int32_t)}}));
   else
     SS_TRY(read_back(st, {{e, S->err_dev.get(), sizeof(e)}}));
+  if (e[0] == SS_ERR_TIMEOUT) SS_FAIL(SS_ERR_TIMEOUT, "stamp: a bounded device wait gave up");
   if (e[0]) SS_FAIL((ss_status)e[0], "stamp: hash table exhausted");
   if (S->half_ok && e[3]) S->half_ok = false;   // some -k not in S: no half system
   // the stamp's buffers outlive this call's stream (synchronised above)
