@@ -44,7 +44,23 @@ __device__ __forceinline__ DF df_add(const DF a, const DF b) {
   return DF{hi, __fsub_rn(lo, __fsub_rn(hi, s))};
 }
 
+// a + b without the final renormalisation: the high part is the rounded sum
+// of the high parts, the low part their exact rounding error plus the low
+// parts, so hi + lo carries the same ~48-bit accuracy while |lo| may exceed
+// half an ulp of hi by a few ulps.  Such a pair is a valid input to df_add,
+// df_mul, df_dot2 and df_fma (their TwoSum and TwoProd act on the high parts
+// exactly; the low parts enter as FP32 corrections), which renormalise.  Used
+// for the inner levels of the small DFT kernels.
+__device__ __forceinline__ DF df_add_nr(const DF a, const DF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return DF{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+}
+
 __device__ __forceinline__ DF df_neg(const DF a) { return DF{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ DF df_sub_nr(const DF a, const DF b) { return df_add_nr(a, DF{-b.hi, -b.lo}); }
 
 __device__ __forceinline__ DF df_sub(const DF a, const DF b) { return df_add(a, df_neg(b)); }
 

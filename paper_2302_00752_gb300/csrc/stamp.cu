@@ -334,8 +334,9 @@ __global__ void k_insert(KeyParams P, const uint64_t* __restrict__ keys, const u
         const int oj = (int)(oc - opar * s_a);
         if (__ldg(hl + par0 + opar) + __ldg(stepg + oj) == lin &&
             sums_equal<WT>(keys + (par0 + opar) * WT, stepkey + (int64_t)oj * WT, pk, sk)) {
-          // same key, same fingerprint: the minimum keeps the smallest candidate id
-          atomicMin((unsigned long long*)(table + h), (unsigned long long)mine);
+          // same key, same fingerprint: the minimum keeps the smallest candidate
+          // id (the slot's id only decreases, so a smaller one seen here stays)
+          if (oc > c) atomicMin((unsigned long long*)(table + h), (unsigned long long)mine);
           slot_of[c] = (int64_t)h;
           return;
         }
@@ -476,90 +477,133 @@ constexpr int kNbrBatch = 8;
 // Neighbour lookups.  With keep_zero (the ADR operator) the zero frequency is
 // an ordinary row and column.  supp a_hat is sorted and symmetric (p_{s_a-1-j}
 // = -p_j, p_j0 = 0), and l = k - p_j lies in S exactly when k = l - p_{s_a-1-j}
-// does: for j < j0 the thread of row i looks up l = k_i - p_j and writes
-// lo[i][j] (l or -1) and, when found, hi[l][s_a-1-j] = i, so every pair is
-// probed once (hi is filled with -1 beforehand).  One thread per row: the
-// first table words of kNbrBatch steps are loaded before any is resolved, and
-// the row's lo words are stored as int4.  A slot whose 31-bit fingerprint
-// agrees is confirmed by the exact word-by-word comparison.
+// does: for j < j0 the lookup of row i finds l = k_i - p_j and writes
+// lo[i][j] = l and hi[l][s_a-1-j] = i, so every pair is probed once (lo is
+// written -1 first, hi is filled with -1 beforehand).  One thread per row
+// probes kNbrBatch steps at a time (their first table words loaded before any
+// is resolved) up to the first slot whose 31-bit fingerprint agrees; the
+// warp queues those candidates in shared memory and confirms them with all
+// its lanes (the exact word-by-word key comparison), so the comparisons do
+// not run divergent once per step.  A candidate that fails (a fingerprint
+// collision) resumes its probe sequence.  cnt (zero beforehand) receives
+// every row's number of neighbours.
+constexpr int kNbrThreads = 256;
+
 template <int WT>
-__global__ void __launch_bounds__(256) k_neighbors(KeyParams P, const uint64_t* __restrict__ keys,
-                                                   const uint64_t* __restrict__ hl, int64_t size, int s_a, int j0,
-                                                   const uint64_t* __restrict__ stepkey,
-                                                   const uint64_t* __restrict__ stepg,
-                                                   const uint64_t* __restrict__ table, uint64_t capmask,
-                                                   const int64_t* __restrict__ zero_dev, bool keep_zero, NbrView nb) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= size) return;
+__global__ void __launch_bounds__(kNbrThreads) k_neighbors(KeyParams P, const uint64_t* __restrict__ keys,
+                                                           const uint64_t* __restrict__ hl, int64_t size, int s_a,
+                                                           int j0, const uint64_t* __restrict__ stepkey,
+                                                           const uint64_t* __restrict__ stepg,
+                                                           const uint64_t* __restrict__ table, uint64_t capmask,
+                                                           const int64_t* __restrict__ zero_dev, bool keep_zero,
+                                                           NbrView nb, int32_t* cnt) {
+  constexpr int kWarps = kNbrThreads / 32, kQueue = 32 * kNbrBatch;
+  __shared__ uint32_t q_tag[kWarps][kQueue];   // lane << 8 | step offset in the batch
+  __shared__ uint32_t q_slot[kWarps][kQueue];  // table slot of the candidate
+  __shared__ int32_t s_cnt[kNbrThreads];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int64_t row0 = (int64_t)blockIdx.x * kNbrThreads + (int64_t)wp * 32;
+  const int64_t i = row0 + lane;
   const int64_t zero_idx = keep_zero ? -1 : *zero_dev;
+  const bool active = i < size && i != zero_idx;
+  s_cnt[threadIdx.x] = active ? 1 : 0;   // the diagonal
+  const uint64_t hli = active ? __ldg(hl + i) : 0;
   int4* out = reinterpret_cast<int4*>(nb.lo + i * nb.Ls);
-  if (i == zero_idx) {
-    for (int u = 0; u < nb.Ls; u += 4) out[u / 4] = make_int4(-1, -1, -1, -1);
-    return;
-  }
-  const uint64_t hli = __ldg(hl + i);
-  const uint64_t* ki = keys + i * WT;
+  const unsigned lt = (1u << lane) - 1u;
   for (int jb = 0; jb < nb.Ls; jb += kNbrBatch) {
     uint64_t hh[kNbrBatch], w[kNbrBatch];
 #pragma unroll
     for (int q = 0; q < kNbrBatch; ++q) {
-      const int j = jb + q;
-      if (j < j0) {
-        hh[q] = hash_of_lin(hli + __ldg(stepg + (s_a - 1 - j)));
+      hh[q] = 0;
+      w[q] = kEmpty;
+      if (active && jb + q < j0) {
+        hh[q] = hash_of_lin(hli + __ldg(stepg + (s_a - 1 - (jb + q))));
         w[q] = __ldg(table + (hh[q] & capmask));
       }
     }
-    int32_t r[kNbrBatch];
+    if (i < size) {
+#pragma unroll
+      for (int q = 0; q < kNbrBatch; q += 4)
+        if (jb + q < nb.Ls) {
+          int32_t r[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) r[e] = (active && jb + q + e == j0) ? (int32_t)i : -1;
+          out[(jb + q) / 4] = make_int4(r[0], r[1], r[2], r[3]);
+        }
+    }
+    int n = 0;
 #pragma unroll
     for (int q = 0; q < kNbrBatch; ++q) {
-      const int j = jb + q;
-      r[q] = j == j0 ? (int32_t)i : -1;
-      if (j >= j0) continue;
-      const int jr = s_a - 1 - j;   // p_jr = -p_j: k_i - p_j = k_i + p_jr
-      const uint64_t* sk = stepkey + (int64_t)jr * WT;
+      // first slot with a matching fingerprint, or none
       const uint64_t fp = slot_fp(hh[q]);
       uint64_t h = hh[q] & capmask, v = w[q];
-      int64_t found = -1;
-      for (uint64_t probe = 0; probe <= capmask; ++probe) {
-        if (v == kEmpty) break;
-        if (word_fp(v) == fp) {
-          const int64_t o = (int64_t)word_low(v);
-          if (key_eq_sum<WT>(keys + o * WT, ki, sk, P)) { found = o; break; }
-        }
+      bool cand = false;
+      for (uint64_t probe = 0; probe <= capmask && v != kEmpty; ++probe) {
+        if (word_fp(v) == fp) { cand = true; break; }
         h = (h + 1) & capmask;
         v = __ldg(table + h);
       }
-      if (found >= 0 && found != zero_idx) {
-        r[q] = (int32_t)found;
-        nb.hi[found * nb.Hs + (jr - nb.L)] = (int32_t)i;
+      const unsigned m = __ballot_sync(0xffffffffu, cand);
+      if (cand) {
+        const int pos = n + __popc(m & lt);
+        q_tag[wp][pos] = ((uint32_t)lane << 8) | (uint32_t)q;
+        q_slot[wp][pos] = (uint32_t)h;
+      }
+      n += __popc(m);
+    }
+    __syncwarp();
+    for (int e = lane; e < n; e += 32) {
+      const int src = (int)(q_tag[wp][e] >> 8), j = jb + (int)(q_tag[wp][e] & 255u);
+      const int64_t is = row0 + src;
+      const int jr = s_a - 1 - j;   // p_jr = -p_j: k_i - p_j = k_i + p_jr
+      const uint64_t* ki = keys + is * WT;
+      const uint64_t* sk = stepkey + (int64_t)jr * WT;
+      uint64_t h = q_slot[wp][e];
+      int64_t o = (int64_t)word_low(__ldg(table + h));
+      if (!key_eq_sum<WT>(keys + o * WT, ki, sk, P)) {
+        // a fingerprint collision: resume the probe sequence after it
+        const uint64_t lin = __ldg(hl + is) + __ldg(stepg + jr);
+        const uint64_t hh2 = hash_of_lin(lin), fp = slot_fp(hh2);
+        o = -1;
+        for (uint64_t probe = 0; probe < capmask; ++probe) {
+          h = (h + 1) & capmask;
+          const uint64_t v = __ldg(table + h);
+          if (v == kEmpty) break;
+          if (word_fp(v) == fp && key_eq_sum<WT>(keys + (int64_t)word_low(v) * WT, ki, sk, P)) {
+            o = (int64_t)word_low(v);
+            break;
+          }
+        }
+      }
+      if (o >= 0 && o != zero_idx) {
+        nb.lo[is * nb.Ls + j] = (int32_t)o;
+        nb.hi[o * nb.Hs + (jr - nb.L)] = (int32_t)is;
+        atomicAdd(&s_cnt[wp * 32 + src], 1);
+        atomicAdd(cnt + o, 1);
       }
     }
-#pragma unroll
-    for (int q = 0; q < kNbrBatch; q += 4)
-      if (jb + q < nb.Ls) out[(jb + q) / 4] = make_int4(r[q], r[q + 1], r[q + 2], r[q + 3]);
+    __syncwarp();
   }
+  if (i < size) atomicAdd(cnt + i, s_cnt[threadIdx.x]);
 }
 
-// Per-row counts, per-slice widths (max over the slice's 32 rows), nnz.
-__global__ void k_row_counts(NbrView nb, int64_t size, int64_t rows_pad, int32_t* slice_w,
-                             unsigned long long* nnz) {
+// Per-slice widths (max over the slice's 32 rows) and nnz from the row counts.
+__global__ void k_slice_widths(const int32_t* __restrict__ cnt, int64_t size, int64_t rows_pad, int32_t* slice_w,
+                               unsigned long long* nnz) {
+  __shared__ unsigned s_tot[8];   // launched with 256 threads
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= rows_pad) return;
-  int32_t cnt = 0;
-  if (i < size)
-    for (int ub = 0; ub < nb.Ls + nb.Hs; ub += kNbrBatch) {
-      int4 x[kNbrBatch / 4];   // loads issued before use (latency-bound otherwise)
-#pragma unroll
-      for (int q = 0; q < kNbrBatch / 4; ++q)
-        x[q] = ub + 4 * q < nb.Ls + nb.Hs ? nbr_chunk(nb, i, ub + 4 * q) : make_int4(-1, -1, -1, -1);
-#pragma unroll
-      for (int q = 0; q < kNbrBatch / 4; ++q) cnt += (x[q].x >= 0) + (x[q].y >= 0) + (x[q].z >= 0) + (x[q].w >= 0);
-    }
-  const int32_t w = __reduce_max_sync(0xffffffffu, cnt);
-  const unsigned long long tot = __reduce_add_sync(0xffffffffu, (unsigned)cnt);
+  const int32_t c = i < size ? cnt[i] : 0;
+  const int32_t w = __reduce_max_sync(0xffffffffu, c);
+  const unsigned tot = __reduce_add_sync(0xffffffffu, (unsigned)c);
   if ((threadIdx.x & 31) == 0) {
-    slice_w[i / kSlice] = w;
-    atomicAdd(nnz, tot);
+    if (i < rows_pad) slice_w[i / kSlice] = w;   // rows_pad is a multiple of the warp
+    s_tot[threadIdx.x >> 5] = tot;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {   // one atomic per block
+    unsigned long long b = 0;
+    for (int q = 0; q < 8; ++q) b += s_tot[q];
+    atomicAdd(nnz, b);
   }
 }
 
@@ -748,11 +792,12 @@ static ss_status grow_table(ss_stamp_s* S, int64_t need, const KeyParams& P, cud
   return SS_OK;
 }
 
-// The table is sized for the candidates of the last level and is mostly
-// empty once the set is complete; the lookups that follow probe one of about
-// 2 |S| slots instead (fewer sectors per probe, more of it resident in L2).
+// The table is sized for the candidates of the last level; when that leaves
+// it more than about 8 times larger than S, the lookups that follow probe a
+// table of about 4 |S| slots instead (a table that size keeps short probe
+// sequences and most of it resident in L2).
 static ss_status compact_table(ss_stamp_s* S, cudaStream_t st) {
-  int64_t want = (int64_t)next_pow2((uint64_t)std::max<int64_t>(2 * S->size, 1024));
+  int64_t want = (int64_t)next_pow2((uint64_t)std::max<int64_t>(4 * S->size, 1024));
   if (want >= S->cap || S->size == 0) return SS_OK;
   SS_TRY(S->table.alloc(want, st));
   S->cap = want;
@@ -1102,7 +1147,8 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
     ProfScope prof_("compact_table", st);
     SS_TRY(compact_table(S, st));
   }
-  DevBuf<int32_t> nbr_lo, nbr_hi, slice_w;
+  if (S->cap > ((int64_t)1 << 32)) SS_FAIL(SS_ERR_KEY_RANGE, "stamp: hash table of %lld slots", (long long)S->cap);
+  DevBuf<int32_t> nbr_lo, nbr_hi, cnt, slice_w;
   DevBuf<unsigned long long> d_nnz;
   DevBuf<int64_t> d_total;
   NbrView nb;
@@ -1114,6 +1160,7 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   SS_TRY(nbr_hi.alloc_tmp((size_t)std::max(S->size * nb.Hs, (int64_t)4), st));
   nb.lo = nbr_lo.get();
   nb.hi = nbr_hi.get();
+  SS_TRY(cnt.alloc_tmp(S->size, st));
   SS_TRY(slice_w.alloc_tmp(S->n_slices + 1, st));
   SS_TRY(d_nnz.alloc_tmp(1, st));
   SS_TRY(d_total.alloc_tmp(1, st));
@@ -1123,14 +1170,15 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   {
     ProfScope prof_("k_neighbors", st);
     if (nb.Hs > 0) SS_CUDA(cudaMemsetAsync(nb.hi, 0xff, (size_t)S->size * nb.Hs * sizeof(int32_t), st));
-    SS_DISPATCH_WT(S->key.WT, (k_neighbors<WT><<<nblk(S->size), 256, 0, st>>>(
+    SS_CUDA(cudaMemsetAsync(cnt.get(), 0, (size_t)S->size * sizeof(int32_t), st));
+    SS_DISPATCH_WT(S->key.WT, (k_neighbors<WT><<<nblk(S->size, kNbrThreads), kNbrThreads, 0, st>>>(
                                   P, S->keys.get(), S->hl.get(), S->size, s_a, S->j0, S->stepkey.get(), S->stepg.get(),
                                   S->table.get(),
-                                  (uint64_t)S->cap - 1, S->zidx_dev.get(), S->adr, nb)));
+                                  (uint64_t)S->cap - 1, S->zidx_dev.get(), S->adr, nb, cnt.get())));
   }
   {
-    ProfScope prof_("k_row_counts", st);
-    k_row_counts<<<nblk(S->rows_pad), 256, 0, st>>>(nb, S->size, S->rows_pad, slice_w.get(), d_nnz.get());
+    ProfScope prof_("k_slice_widths", st);
+    k_slice_widths<<<nblk(S->rows_pad), 256, 0, st>>>(cnt.get(), S->size, S->rows_pad, slice_w.get(), d_nnz.get());
   }
   SS_LAUNCH_CHECK();
   SS_TRY(S->slice_off.alloc(S->n_slices + 1, st));
@@ -1336,11 +1384,15 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   SS_LAUNCH_CHECK();
   S->size = n_f;
   S->level_start.push_back(n_f);
-  SS_TRY(run_levels(S, 1, N, st));
+  {
+    ProfScope prof_("stamp_levels", st);
+    SS_TRY(run_levels(S, 1, N, st));
+  }
   // give back a large over-reservation of the size bound (the keys stay for
   // lookups, extension and export; the norms are read up to rows_pad + 1)
   const int64_t rows = (int64_t)(S->keys.n / L.WT), keep = S->size + kSlice + 1;
   if (rows > 4 * keep && (double)rows * (8.0 * L.WT + 9.0) > 64e6) SS_TRY(resize_keys(S, keep, st));
+  ProfScope prof_("stamp_operator", st);
   return build_operator(S, st);
 }
 
@@ -1411,7 +1463,11 @@ extern "C" ss_status stamp_build(const ss_sparse* a_hat, const int32_t* f_freq, 
   if (a_hat->n > 4096) SS_FAIL(SS_ERR_INVALID, "stamp_build: |supp a_hat| > 4096");
   *out = nullptr;
   ss_stamp_s* S = new ss_stamp_s();
-  ss_status s = build_impl(S, a_hat, f_freq, n_f, N, as_stream(stream));
+  ss_status s;
+  {
+    ProfScope prof_("stamp_build", as_stream(stream));
+    s = build_impl(S, a_hat, f_freq, n_f, N, as_stream(stream));
+  }
   if (s != SS_OK) {
     cudaStreamSynchronize(as_stream(stream));
     delete S;
