@@ -67,6 +67,10 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--apply-only", action="store_true",
                     help="run only the galerkin_apply section and print it (profiling the operator kernels)")
+    ap.add_argument("--case", choices=["step", "pruned_small"],
+                    help="profiling cases: three headline steps (step), or three steps of the same data on a "
+                         "lattice of M = 2^23 (pruned_small: the pruned transforms at 1/8 of the points); "
+                         "prints a status line only")
     return ap.parse_args()
 
 
@@ -235,7 +239,24 @@ def pruned_instr(kind, M, n_split, n_work):
 # ncu captures summarised under profiles/, with the hash of the kernel's
 # source file at capture time; a record whose source has changed since is not
 # used (traffic null).
-KERNEL_TRAFFIC = {}
+_PR_SOURCES = ["paper_2302_00752_gb300/csrc/fft_pruned.cu", "paper_2302_00752_gb300/csrc/dfc.cuh",
+               "paper_2302_00752_gb300/csrc/df.cuh"]
+KERNEL_TRAFFIC = {
+    "k_pr_eval": {"sources": _PR_SOURCES, "source_sha16": "3bd76de49a76a96d", "dram_bytes_per_launch": 648.81e6,
+                  "note": "ncu capture at M = 2^23 (81.10 MB) scaled by the tiles to M = 2^26 (x8); the capture "
+                          "misses the output lines still dirty in L2 when the kernel ends (algorithmic write "
+                          "1.07 GB at 2^26); profiles/k_pr_eval_fwd_cfg5_M2e23.md"},
+    "k_pr_fwd": {"sources": _PR_SOURCES, "source_sha16": "3bd76de49a76a96d", "dram_bytes_per_launch": 1157.3e6,
+                 "note": "ncu capture at M = 2^23 (144.66 MB) scaled by the tiles to M = 2^26 (x8); "
+                         "profiles/k_pr_eval_fwd_cfg5_M2e23.md"},
+    "k_neighbors": {"sources": ["paper_2302_00752_gb300/csrc/stamp.cu", "paper_2302_00752_gb300/csrc/keys.cuh"],
+                    "source_sha16": "e28d2e437c112942", "dram_bytes_per_launch": 958.17e6,
+                    "note": "ncu capture of the d = 100 stamp (full size); profiles/k_neighbors_insert_finalize_cfg5.md"},
+    "k_solve<0>": {"sources": ["paper_2302_00752_gb300/csrc/solve.cu", "paper_2302_00752_gb300/csrc/apply.cuh"],
+                   "source_sha16": "c1c7f4e22d20e9b1", "dram_bytes_per_launch": 1853.91e6,
+                   "note": "ncu capture of the d = 100 FP64 half-system solve (full size); "
+                           "profiles/k_solve_fp64_half_cfg5.md"},
+}
 
 
 def traffic_record(kernel):
@@ -243,13 +264,14 @@ def traffic_record(kernel):
     rec = KERNEL_TRAFFIC.get(kernel)
     if not rec:
         return None
+    h = hashlib.sha256()
     try:
-        with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
-            if hashlib.sha256(fh.read()).hexdigest()[:16] != rec["source_sha16"]:
-                return None
+        for f in rec["sources"]:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
     except OSError:
         return None
-    return rec
+    return rec if h.hexdigest()[:16] == rec["source_sha16"] else None
 
 
 def roofline_of(name, ms, ctx, rates):
@@ -279,12 +301,15 @@ def roofline_of(name, ms, ctx, rates):
                     "algorithmic_flops": flops, "half_system": half, "real_coefficients": realc,
                     "peak_source": "measured: FP64 FMA rate of libss_peaks.so"})
     elif name == "k_neighbors":
-        lookups = ctx["size"] * ctx["s_a"]
-        req = lookups + ctx["nnz"] * ctx["key_words"] / 2.0   # one slot probe per lookup, the key in 16-byte loads per hit
+        # pair-symmetric lookups: j0 = (s_a - 1) / 2 per row, one slot probe
+        # each; every found pair reads the stored key once (16-byte loads)
+        lookups = ctx["size"] * ((ctx["s_a"] - 1) // 2)
+        pairs = (ctx["nnz"] - ctx["size"]) / 2.0
+        req = lookups + pairs * ctx["key_words"] / 2.0
         peak = rates["l2_gather16"]["Grequests_s"]
         ach = req / (ms / 1e3) / 1e9
         out.update({"bound": "l2_gather", "achieved": ach, "peak": peak, "unit": "G gather requests/s",
-                    "frac": ach / peak, "lookups": lookups,
+                    "frac": ach / peak, "lookups": lookups, "found_pairs": pairs,
                     "peak_source": "measured: random 16-byte gathers from a 64 MB working set (libss_peaks.so)"})
     else:
         out.update({"bound": None, "achieved": None, "peak": None, "frac": None})
@@ -940,6 +965,36 @@ def key_words(d, maxabs):
 
 # ---------------------------------------------------------------- our path
 
+def run_case(case, reps=3):
+    """Small fixed runs for ncu captures (launch lists and kernel sections)."""
+    from paper_2302_00752_gb300 import binding as B
+    from paper_2302_00752_gb300 import pipeline as gp
+    inst = W.make_cfg5(smooth=True)
+    p = gp.prepare(inst)
+    p.sft_precision = "fp64"
+    if case == "pruned_small":
+        # a reconstructing lattice of M = 2^23 for the same candidates (checked by the library)
+        M, rng = 2 ** 23, np.random.default_rng(3)
+        for _ in range(100):
+            z = rng.integers(1, M, size=inst.d)
+            try:
+                B.lattice_check(z, M, p.cand)
+                break
+            except Exception:
+                continue
+        else:
+            raise RuntimeError("no reconstructing lattice of size 2^23 found")
+        p.extra["lattice"] = {"kind": "box", "z": z, "M": M}
+    for _ in range(reps):
+        r = gp.run_fused(p, tol=TOL, max_iter=1000, tau=1e-9, solve_precision="fp64")
+        if r.stats["status"] != "SS_OK":
+            raise RuntimeError(f"{case}: {r.stats}")
+        r.stamp.destroy()
+    import torch
+    torch.cuda.synchronize()
+    print(json.dumps({"case": case, "status": "ok", "M": int(p.M) if p.M else None}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -951,6 +1006,9 @@ def main():
         from paper_2302_00752_gb300 import pipeline as gp
         flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
         print(json.dumps({"apply": apply_section(B, gp, flush, load_peaks())}))
+        return
+    if args.case:
+        run_case(args.case)
         return
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -1023,9 +1081,10 @@ def main():
         flush.zero_()                                # L2 flushed between steps
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        r = step(prep)
+        r = step(prep, keep=True)
         e1.record()
         e1.synchronize()
+        r["stamp"].destroy()                         # the stamp's memory is given back after the step's end
         step_ms.append(e0.elapsed_time(e1))
         work += r["nnz"] * r["applies"]
     torch.cuda.synchronize()
@@ -1094,18 +1153,24 @@ def main():
         p2 = gp.Prepared(prep.d, prep.N, *[host[k].to(dev, non_blocking=True) for k in
                                            ("a_freq", "a_coef", "f_freq", "f_coef", "cand")],
                          sft_precision="fp64", solve_precision="fp64", extra=prep.extra)
-        r2 = step(p2)
+        r2 = step(p2, keep=True)
         u_host.copy_(r2["u"], non_blocking=True)
         b.record()
         b.synchronize()
+        r2["stamp"].destroy()
         e2e_ms.append(a.elapsed_time(b))
         e2e_work += r2["nnz"] * r2["applies"]
     e2e_value = world * e2e_work / (sum(e2e_ms) / 1e3)
 
     # kernels of the timed steps (library kernel timing) and the dominant one's roofline
     step_med = statistics.median(step_ms)
-    kernels = {k: {"launches_per_step": c / args.steps, "ms_per_launch": t / c, "ms_per_step": t / args.steps,
-                   "share_of_step": t / args.steps / step_med} for k, (c, t) in totals.items() if c}
+    # entries named k_* bracket one kernel each (k_neighbors also its two
+    # memsets); the others bracket stages of several launches
+    timed = {k: {"launches_per_step": c / args.steps, "ms_per_launch": t / c, "ms_per_step": t / args.steps,
+                 "share_of_step": t / args.steps / step_med} for k, (c, t) in totals.items() if c}
+    kernels = {k: v for k, v in timed.items() if k.startswith("k_")}
+    stages = {k: {"ms_per_step": v["ms_per_step"], "share_of_step": v["share_of_step"]}
+              for k, v in timed.items() if not k.startswith("k_")}
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"]) if kernels else None
     maxabs_f = int(np.abs(np.asarray(inst.f.freq)).max())
     maxabs_a = int(np.abs(np.asarray(inst.a.freq)).max())
@@ -1201,6 +1266,7 @@ def main():
                           "stages called one by one from Python with events between them"),
             "solve_only": tts,
             "kernels": kernels,
+            "stages": stages,
             "roofline": roofline,
             "roofline_other_kernels": others,
             "rates": rates,
