@@ -98,12 +98,14 @@ const char* ss_version(void);
  * that a stretch of calls (e.g. solve_noalloc) allocated nothing.  Host. */
 int64_t ss_alloc_count(void);
 
-/* Kernel timing, a diagnostic with no counterpart in the paper.  With on != 0
- * the library brackets its main kernels (recovery transforms, stamping,
- * operator, solver) with CUDA events on the stream each is launched on -
- * except while that stream is being captured into a graph - and accumulates
- * launches and device time per kernel name; on = 0 stops.  Every call resets
- * the totals.  Host. */
+/* Kernel timing, a diagnostic with no counterpart in the paper.  With on = 1
+ * the library brackets its main kernels (the recovery transforms, the
+ * neighbour lookups, the operator and the solver) with CUDA events on the
+ * stream each is launched on - except while that stream is being captured
+ * into a graph - and accumulates launches and device time per kernel name;
+ * on = 2 brackets every kernel and stage that has a bracket (more event
+ * records on the host); on = 0 stops.  Every call resets the totals and the
+ * trace.  Host. */
 ss_status ss_profile(int32_t on);
 
 /* Totals of entry i (0-based, in name order): the kernel name (NUL-terminated,
@@ -112,6 +114,13 @@ ss_status ss_profile(int32_t on);
  * receives the number of entries; SS_ERR_INVALID when i is out of range. */
 ss_status ss_profile_entry(int32_t i, char* name, int32_t name_cap, int64_t* launches, double* total_ms,
                            int32_t* n_out);
+
+/* Trace entry i of the current profiling session: the bracket's name and its
+ * start and end in ms relative to the session's first bracket start (device
+ * time, in the order the brackets were resolved, at most 65536 entries).
+ * n_out (nullable) receives the entry count.  Waits for the brackets queued
+ * so far.  SS_ERR_INVALID for an index out of range. */
+ss_status ss_profile_trace(int32_t i, char* name, int32_t name_cap, double* t0_ms, double* t1_ms, int32_t* n_out);
 
 /* ---------------------------------------------------------------- lattice */
 

@@ -71,6 +71,7 @@ def _load():
         "ss_alloc_count": (C.c_int64, []),
         "ss_profile": (i32, [i32]),
         "ss_profile_entry": (i32, [i32, C.c_char_p, i32, P(i64), P(dbl), P(i32)]),
+        "ss_profile_trace": (i32, [i32, C.c_char_p, i32, P(dbl), P(dbl), P(i32)]),
         "solve_set_wait_limit": (i32, [vp, i64]),
         "stamp_set_table_limit": (i32, [i64]),
         "lattice_size": (i32, [i64, i64, dbl, i64, P(i64)]),
@@ -479,9 +480,10 @@ def set_table_limit(max_slots):
     _check(lib.stamp_set_table_limit(int(max_slots)))
 
 
-def profile(on):
-    """Start (True) or stop kernel timing; resets the totals."""
-    _check(lib.ss_profile(1 if on else 0))
+def profile(on, level=2):
+    """Start (True) or stop kernel timing; resets the totals.  level 1: the
+    main kernels only (little host work per step), 2: every bracket."""
+    _check(lib.ss_profile(int(level) if on else 0))
 
 
 def profile_totals():
@@ -498,6 +500,20 @@ def profile_totals():
         i += 1
     return out
 
+
+
+def profile_trace():
+    """[(name, start ms, end ms)] of the brackets since profile(True), device
+    time relative to the first bracket's start."""
+    out = []
+    n = C.c_int32(0)
+    lib.ss_profile_trace(0, None, 0, None, None, C.byref(n))
+    name = C.create_string_buffer(128)
+    a, b = C.c_double(), C.c_double()
+    for i in range(n.value):
+        _check(lib.ss_profile_trace(i, name, 128, C.byref(a), C.byref(b), None))
+        out.append((name.value.decode(), a.value, b.value))
+    return out
 
 def alloc_count():
     """Allocation calls the library has made in this process (diagnostic)."""

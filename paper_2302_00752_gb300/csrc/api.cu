@@ -321,12 +321,22 @@ struct ProfTotals {
   double ms = 0.0;
 };
 
-std::atomic<bool> g_prof_on{false};
+std::atomic<int> g_prof_level{0};
 std::mutex g_prof_mu;
 std::map<int64_t, ProfPending> g_prof_pending;   // by token
 int64_t g_prof_next = 0;
 std::vector<cudaEvent_t> g_prof_free;
 std::map<std::string, ProfTotals> g_prof_totals;
+
+// Trace: every bracket's start and end relative to the first bracket of the
+// session (its start event), at most kProfTraceMax entries.
+struct ProfTraceEntry {
+  std::string name;
+  double t0, t1;
+};
+constexpr size_t kProfTraceMax = 1 << 16;
+cudaEvent_t g_prof_origin = nullptr;
+std::vector<ProfTraceEntry> g_prof_trace;
 
 cudaEvent_t prof_event() {
   if (!g_prof_free.empty()) {
@@ -355,6 +365,12 @@ void prof_drain() {
       ProfTotals& t = g_prof_totals[p.name];
       t.launches += 1;
       t.ms += ms;
+      float a = 0.f, b = 0.f;
+      if (g_prof_origin && g_prof_trace.size() < kProfTraceMax &&
+          cudaEventElapsedTime(&a, g_prof_origin, p.e0) == cudaSuccess &&
+          cudaEventElapsedTime(&b, g_prof_origin, p.e1) == cudaSuccess)
+        g_prof_trace.push_back(ProfTraceEntry{p.name, (double)a, (double)b});
+      cudaGetLastError();
     } else {
       cudaGetLastError();
     }
@@ -366,7 +382,7 @@ void prof_drain() {
 
 }  // namespace
 
-bool prof_on() { return g_prof_on.load(std::memory_order_relaxed); }
+int prof_level() { return g_prof_level.load(std::memory_order_relaxed); }
 
 int64_t prof_begin(const char* name, cudaStream_t st) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -376,6 +392,12 @@ int64_t prof_begin(const char* name, cudaStream_t st) {
   }
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (g_prof_pending.size() > 4096) prof_drain();   // bound the events held
+  if (!g_prof_origin) {   // the session's time origin, just before its first bracket
+    if (cudaEventCreate(&g_prof_origin) != cudaSuccess || cudaEventRecord(g_prof_origin, st) != cudaSuccess) {
+      cudaGetLastError();
+      g_prof_origin = nullptr;
+    }
+  }
   ProfPending p;
   p.name = name;
   p.st = st;
@@ -410,7 +432,12 @@ extern "C" ss_status ss_profile(int32_t on) {
   std::lock_guard<std::mutex> lk(ss::g_prof_mu);
   ss::prof_drain();
   ss::g_prof_totals.clear();
-  ss::g_prof_on.store(on != 0, std::memory_order_relaxed);
+  ss::g_prof_trace.clear();
+  if (ss::g_prof_origin) {
+    cudaEventDestroy(ss::g_prof_origin);
+    ss::g_prof_origin = nullptr;
+  }
+  ss::g_prof_level.store(on < 0 ? 0 : (on > 2 ? 2 : on), std::memory_order_relaxed);
   return SS_OK;
 }
 
@@ -429,5 +456,22 @@ extern "C" ss_status ss_profile_entry(int32_t i, char* name, int32_t name_cap, i
   }
   if (launches) *launches = it->second.launches;
   if (total_ms) *total_ms = it->second.ms;
+  return SS_OK;
+}
+
+extern "C" ss_status ss_profile_trace(int32_t i, char* name, int32_t name_cap, double* t0_ms, double* t1_ms,
+                                      int32_t* n_out) {
+  std::lock_guard<std::mutex> lk(ss::g_prof_mu);
+  ss::prof_drain();
+  const int32_t n = (int32_t)ss::g_prof_trace.size();
+  if (n_out) *n_out = n;
+  if (i < 0 || i >= n) SS_FAIL(SS_ERR_INVALID, "ss_profile_trace: index %d of %d entries", (int)i, (int)n);
+  const ss::ProfTraceEntry& e = ss::g_prof_trace[(size_t)i];
+  if (name && name_cap > 0) {
+    std::strncpy(name, e.name.c_str(), (size_t)name_cap - 1);
+    name[name_cap - 1] = '\0';
+  }
+  if (t0_ms) *t0_ms = e.t0;
+  if (t1_ms) *t1_ms = e.t1;
   return SS_OK;
 }

@@ -145,7 +145,7 @@ ss_status launch_pack64_prefix(const ss_stamp_s* s, const double2* u, int64_t n_
 
 ss_status launch_apply64(const ss_stamp_s* s, double2* y, cudaStream_t st) {
   {
-    ProfScope prof_("k_apply64", st);
+    ProfScope prof_("k_apply64", st, true);
     k_apply64<<<nblk(s->rows_pad), 256, 0, st>>>(op_view(s), s->size, s->rows_pad, s->rec64.get(), identity_row(s), y);
   }
   SS_LAUNCH_CHECK();
@@ -156,13 +156,13 @@ ss_status launch_apply32(const ss_stamp_s* s, const float2* u, float2* y, cudaSt
   if (s->adr) SS_FAIL(SS_ERR_INVALID, "the FP32 operator is not available for ADR stamps (use SS_FP64)");
   if (s->wide)
     {
-      ProfScope prof_("k_apply32", st);
+      ProfScope prof_("k_apply32", st, true);
       k_apply32<true><<<nblk(s->rows_pad), 256, 0, st>>>(op_view(s), s->size, s->rows_pad, s->nw32.get(), u,
                                                          s->ca32.get(), s->pn32.get(), s->zero_idx, y);
     }
   else
     {
-      ProfScope prof_("k_apply32", st);
+      ProfScope prof_("k_apply32", st, true);
       k_apply32<false><<<nblk(s->rows_pad), 256, 0, st>>>(op_view(s), s->size, s->rows_pad, s->nw32.get(), u,
                                                           s->ca32.get(), s->pn32.get(), s->zero_idx, y);
     }

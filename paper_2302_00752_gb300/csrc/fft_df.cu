@@ -115,7 +115,7 @@ ss_status launch(const DfFftPlan& F, const float4* tab, const float4* in, float4
   threads = threads < 64 ? 64 : (threads > 512 ? 512 : threads);
   if (sm > 48 * 1024)
     SS_CUDA(cudaFuncSetAttribute(k_fft_df<SIGN, SECOND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  ProfScope prof_("k_fft_df", st);
+  ProfScope prof_("k_fft_df", st, true);
   k_fft_df<SIGN, SECOND><<<SECOND ? F.L1 : F.L2, threads, sm, st>>>(in, out, tab, F.M, F.L1, F.L2, rad);
   SS_LAUNCH_CHECK();
   return SS_OK;

@@ -552,7 +552,7 @@ ss_status launch_fwd(const TwoLevelTable& T, const PrunedSplit& S, int wsh, cons
   DevBuf<typename A::V> partial;
   SS_TRY(partial.alloc_tmp((size_t)grid * nc, st));
   {
-    ProfScope prof_("k_pr_fwd", st);
+    ProfScope prof_("k_pr_fwd", st, true);
     k_pr_fwd<A, IN_REAL><<<grid, kPrThreads, smem, st>>>(T.M, S.P, S.Q, wsh, S.rad, T.t0.get(), T.t1.get(), T.b, in,
                                                          ob, kout, nc, oz, n_tiles, partial.get());
     SS_LAUNCH_CHECK();
@@ -640,7 +640,7 @@ ss_status pruned_eval_pair(const TwoLevelTable& T, const int64_t* qa, const doub
   while ((1 << wsh) < S.W) ++wsh;
   // the entries' step powers go to shared memory once per block when they fit
   const int64_t n_stage = ne_max * S.W <= kPrEvalStage ? ne_max * S.W : 0;
-  ProfScope prof_("k_pr_eval", st);
+  ProfScope prof_("k_pr_eval", st, true);
   switch (fmt) {
     case PrunedFormat::kDfComplex:
       return launch_eval<ArDF, false>(T, S, wsh, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st);

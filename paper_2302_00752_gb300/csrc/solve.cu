@@ -1269,7 +1269,7 @@ ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, co
   if (ev_begin) SS_CUDA(cudaEventRecord(ev_begin, st));
   {
     static const char* const names[4] = {"k_solve<0>", "k_solve<1>", "k_solve<2>", "k_solve<3>"};
-    ProfScope prof_(names[mode & 3], st);
+    ProfScope prof_(names[mode & 3], st, true);
     if (mode == 0) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<0>, P));
     else if (mode == 1) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<1>, P));
     else if (mode == 2) SS_CUDA(cudaLaunchKernelEx(&cfg, k_solve<2>, P));

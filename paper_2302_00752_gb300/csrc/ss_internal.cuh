@@ -85,14 +85,17 @@ void note_alloc();
 // Kernel timing (ss_profile): while it is on, a ProfScope brackets the
 // launches made inside its lifetime with a CUDA event pair on their stream
 // (not while the stream is being captured into a graph); the device time is
-// added to the named entry when the totals are read.
-bool prof_on();
+// added to the named entry when the totals are read.  Level 1 brackets the
+// main kernels only (a few per pipeline step, so the host spends little on
+// event records), level 2 every bracket.
+int prof_level();
+inline bool prof_on() { return prof_level() > 0; }
 int64_t prof_begin(const char* name, cudaStream_t st);
 void prof_end(int64_t token);
 struct ProfScope {
   int64_t tok = -1;
-  ProfScope(const char* name, cudaStream_t st) {
-    if (prof_on()) tok = prof_begin(name, st);
+  ProfScope(const char* name, cudaStream_t st, bool main = false) {
+    if (prof_level() >= (main ? 1 : 2)) tok = prof_begin(name, st);
   }
   ~ProfScope() {
     if (tok >= 0) prof_end(tok);

@@ -1168,7 +1168,7 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
                          {d_nnz.get(), sizeof(unsigned long long), 0},
                          {slice_w.get(), (S->n_slices + 1) * sizeof(int32_t), 0}}));
   {
-    ProfScope prof_("k_neighbors", st);
+    ProfScope prof_("k_neighbors", st, true);
     if (nb.Hs > 0) SS_CUDA(cudaMemsetAsync(nb.hi, 0xff, (size_t)S->size * nb.Hs * sizeof(int32_t), st));
     SS_CUDA(cudaMemsetAsync(cnt.get(), 0, (size_t)S->size * sizeof(int32_t), st));
     SS_DISPATCH_WT(S->key.WT, (k_neighbors<WT><<<nblk(S->size, kNbrThreads), kNbrThreads, 0, st>>>(
