@@ -270,22 +270,22 @@ __device__ typename A::V* columns_dft(typename A::V* a, typename A::V* b, int P,
 __global__ void k_pr_entries(const int64_t* __restrict__ qa, const double2* __restrict__ ca,
                              const int64_t* __restrict__ na_dev, const int64_t* __restrict__ qf,
                              const double2* __restrict__ cf, const int64_t* __restrict__ nf_dev,
-                             const double* __restrict__ scale, int64_t M, int P, int32_t* kq, int64_t* er,
-                             float4* ev, int32_t* boff) {
-  extern __shared__ int32_t cnt[];   // P + 1
+                             const double* __restrict__ scale, int64_t M, int P, int32_t* kq_g, int64_t* er,
+                             float4* ev, int32_t* boff, int kq_smem) {
+  extern __shared__ int32_t cnt[];   // P + 1, then the buckets of the entries when 2 n <= kq_smem
   const int64_t na = *na_dev, nf = nf_dev ? *nf_dev : 0, n = na + nf;
+  int32_t* kq = 2 * n <= kq_smem ? cnt + P + 1 : kq_g;
   auto res = [&](int64_t u) { return u < na ? qa[u] : qf[u - na]; };
+  for (int k = threadIdx.x; k <= P; k += blockDim.x) cnt[k] = 0;
+  __syncthreads();
   for (int64_t u = threadIdx.x; u < n; u += blockDim.x) {
     const int64_t r = res(u);
     const bool one = r == 0 || 2 * r == M;
-    kq[2 * u] = (int32_t)(r % P);
-    kq[2 * u + 1] = one ? -1 : (int32_t)((M - r) % P);
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < P; k += blockDim.x) {
-    int c = 0;
-    for (int64_t v = 0; v < 2 * n; ++v) c += kq[v] == k;
-    cnt[k] = c;
+    const int32_t k0 = (int32_t)(r % P), k1 = one ? -1 : (int32_t)((M - r) % P);
+    kq[2 * u] = k0;
+    kq[2 * u + 1] = k1;
+    atomicAdd(cnt + k0, 1);
+    if (k1 >= 0) atomicAdd(cnt + k1, 1);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -300,39 +300,39 @@ __global__ void k_pr_entries(const int64_t* __restrict__ qa, const double2* __re
   __syncthreads();
   for (int k = threadIdx.x; k <= P; k += blockDim.x) boff[k] = cnt[k];
   const double ia = scale ? 1.0 / scale[0] : 1.0, jf = scale ? 1.0 / scale[1] : 1.0;   // exact: powers of two
-  for (int k = threadIdx.x; k < P; k += blockDim.x) {
+  // stable placement: entry v goes after the earlier entries of its bucket
+  for (int64_t v = threadIdx.x; v < 2 * n; v += blockDim.x) {
+    const int32_t k = kq[v];
+    if (k < 0) continue;
     int pos = cnt[k];
-    for (int64_t v = 0; v < 2 * n; ++v) {
-      if (kq[v] != k) continue;
-      const int64_t u = v >> 1;
-      const bool neg = v & 1;
-      const int64_t r = res(u);
-      const bool one = r == 0 || 2 * r == M;
-      double x, y;
-      if (u < na) {
-        const double2 c = ca[u];
-        if (one) {
-          x = c.x * ia;
-          y = 0.0;
-        } else {
-          x = 0.5 * c.x * ia;
-          y = (neg ? -0.5 : 0.5) * c.y * ia;
-        }
+    for (int64_t w = 0; w < v; ++w) pos += kq[w] == k;
+    const int64_t u = v >> 1;
+    const bool neg = v & 1;
+    const int64_t r = res(u);
+    const bool one = r == 0 || 2 * r == M;
+    double x, y;
+    if (u < na) {
+      const double2 c = ca[u];
+      if (one) {
+        x = c.x * ia;
+        y = 0.0;
       } else {
-        const double2 c = cf[u - na];
-        if (one) {
-          x = 0.0;
-          y = c.x * jf;
-        } else {
-          x = (neg ? 0.5 : -0.5) * c.y * jf;
-          y = 0.5 * c.x * jf;
-        }
+        x = 0.5 * c.x * ia;
+        y = (neg ? -0.5 : 0.5) * c.y * ia;
       }
-      const DF dx = df_split(x), dy = df_split(y);
-      er[pos] = neg ? M - r : r;
-      ev[pos] = make_float4(dx.hi, dx.lo, dy.hi, dy.lo);
-      ++pos;
+    } else {
+      const double2 c = cf[u - na];
+      if (one) {
+        x = 0.0;
+        y = c.x * jf;
+      } else {
+        x = (neg ? 0.5 : -0.5) * c.y * jf;
+        y = 0.5 * c.x * jf;
+      }
     }
+    const DF dx = df_split(x), dy = df_split(y);
+    er[pos] = neg ? M - r : r;
+    ev[pos] = make_float4(dx.hi, dx.lo, dy.hi, dy.lo);
   }
 }
 
@@ -629,8 +629,12 @@ ss_status pruned_eval_pair(const TwoLevelTable& T, const int64_t* qa, const doub
   {
     ProfScope prof_setup("pr_setup", st);
     const int eb = std::min(1024, (S.P + 31) / 32 * 32);
-    k_pr_entries<<<1, eb, (S.P + 1) * sizeof(int32_t), st>>>(qa, ca, na_dev, qf, cf, qf ? nf_dev : nullptr, scale, M,
-                                                             S.P, kq.get(), er.get(), ev.get(), boff.get());
+    // the entries' buckets in shared memory when they fit (48 KB with the counts)
+    const int kq_smem = (int)std::min<int64_t>(ne_max, 12288 - (S.P + 1));
+    k_pr_entries<<<1, eb, (S.P + 1 + kq_smem) * sizeof(int32_t), st>>>(qa, ca, na_dev, qf, cf, qf ? nf_dev : nullptr,
+                                                                        scale, M,
+                                                                        S.P, kq.get(), er.get(), ev.get(),
+                                                                        boff.get(), kq_smem);
     SS_LAUNCH_CHECK();
     k_pr_steps<1><<<nblk(ne_max * S.W), 256, 0, st>>>(er.get(), boff.get() + S.P, 0, S.W, M, T.t0.get(), T.t1.get(),
                                                       T.b, estep.get());

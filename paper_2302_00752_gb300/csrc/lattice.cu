@@ -36,10 +36,12 @@ int64_t next_smooth_host(int64_t n) {
 
 // ---------------------------------------------------------------- kernels
 
+// One warp per row.
 __global__ void k_residues(const int32_t* __restrict__ f, int64_t n, int d, LatticeDev L, int64_t* res) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  res[i] = residue_of(f + i * d, d, L);
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= n) return;   // warp-uniform
+  const int64_t r = residue_warp(f + i * d, d, L);
+  if ((threadIdx.x & 31) == 0) res[i] = r;
 }
 
 namespace {
@@ -47,12 +49,6 @@ namespace {
 __device__ bool rows_equal(const int32_t* a, const int32_t* b, int d) {
   for (int c = 0; c < d; ++c)
     if (a[c] != b[c]) return false;
-  return true;
-}
-
-__device__ bool rows_negated(const int32_t* a, const int32_t* b, int d) {
-  for (int c = 0; c < d; ++c)
-    if (a[c] != -b[c]) return false;
   return true;
 }
 
@@ -85,24 +81,36 @@ __global__ void k_check_insert(const int32_t* __restrict__ f, const int64_t* __r
 }
 
 // For every row k, is -k present?  (residue of -k is (M - r) mod M)
+// One warp per row: the row owning residue M - res[i] is found by probing
+// (lane 0's loads, broadcast), then compared with -f_i 32 coordinates at a time.
 __global__ void k_check_symmetric(const int32_t* __restrict__ f, const int64_t* __restrict__ res, int64_t n, int d,
                                   int64_t M, const unsigned long long* __restrict__ table, uint64_t capmask,
                                   int32_t* flags) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;   // warp-uniform
   const uint64_t r = (uint64_t)((M - res[i]) % M);
   uint64_t h = rhash(r) & capmask;
+  int64_t o = -1;
   for (uint64_t probe = 0; probe <= capmask; ++probe) {
     const unsigned long long v = table[h];
     if (v == 0ull) break;
-    const int64_t o = (int64_t)v - 1;
-    if ((uint64_t)res[o] == r) {
-      if (rows_negated(f + o * d, f + i * d, d)) return;
+    const int64_t oc = (int64_t)v - 1;
+    if ((uint64_t)res[oc] == r) {
+      o = oc;
       break;
     }
     h = (h + 1) & capmask;
   }
-  atomicOr(flags + 3, 1);
+  bool neg = o >= 0;
+  if (neg) {
+    const int32_t* a = f + o * d;
+    const int32_t* b = f + i * d;
+    bool bad = false;
+    for (int c = lane; c < d; c += 32) bad |= a[c] != -b[c];
+    neg = !__any_sync(0xffffffffu, bad);
+  }
+  if (!neg && lane == 0) atomicOr(flags + 3, 1);
 }
 
 __global__ void k_minmax(const int32_t* __restrict__ f, int64_t n, int d, int32_t* mn, int32_t* mx) {
@@ -334,7 +342,7 @@ ss_status make_lattice_dev(const ss_lattice* lat, LatticeDev* L) {
 ss_status residues(const int32_t* freq, int64_t n, const LatticeDev& L, int64_t* res, cudaStream_t st) {
   ProfScope prof_("k_residues", st);
   if (n == 0) return SS_OK;
-  k_residues<<<nblk(n), 256, 0, st>>>(freq, n, L.d, L, res);
+  k_residues<<<nblk(n * 32), 256, 0, st>>>(freq, n, L.d, L, res);
   SS_LAUNCH_CHECK();
   return SS_OK;
 }
@@ -346,7 +354,7 @@ ss_status check_reconstructing_async(const int32_t* freq, int64_t n, const Latti
   SS_TRY(fill_small(st, {{table, cap * sizeof(unsigned long long), 0}, {flags, 4 * sizeof(int32_t), 0}}));
   if (n == 0) return SS_OK;
   k_check_insert<<<nblk(n), 256, 0, st>>>(freq, res, n, L.d, table, cap - 1, flags);
-  if (need_symmetric) k_check_symmetric<<<nblk(n), 256, 0, st>>>(freq, res, n, L.d, L.M, table, cap - 1, flags);
+  if (need_symmetric) k_check_symmetric<<<nblk(n * 32), 256, 0, st>>>(freq, res, n, L.d, L.M, table, cap - 1, flags);
   SS_LAUNCH_CHECK();
   return SS_OK;
 }
@@ -371,7 +379,8 @@ ss_status check_reconstructing(const int32_t* freq, int64_t n, const LatticeDev&
   SS_TRY(flags.alloc_tmp(4, st));
   SS_TRY(fill_small(st, {{table.get(), cap * sizeof(unsigned long long), 0}, {flags.get(), 4 * sizeof(int32_t), 0}}));
   k_check_insert<<<nblk(n), 256, 0, st>>>(freq, res, n, L.d, table.get(), cap - 1, flags.get());
-  if (need_symmetric) k_check_symmetric<<<nblk(n), 256, 0, st>>>(freq, res, n, L.d, L.M, table.get(), cap - 1, flags.get());
+  if (need_symmetric)
+    k_check_symmetric<<<nblk(n * 32), 256, 0, st>>>(freq, res, n, L.d, L.M, table.get(), cap - 1, flags.get());
   SS_LAUNCH_CHECK();
   int32_t h[4];
   SS_TRY(read_back(st, {{h, flags.get(), sizeof(h)}}));

@@ -30,6 +30,30 @@ __device__ __forceinline__ int64_t residue_of(const int32_t* k, int d, const Lat
   return (int64_t)(acc % M);
 }
 
+// The same residue by one warp (every lane gets it): lane l takes the
+// coordinates c = l, l + 32, ... (coalesced reads of k and z), the partial
+// sums are reduced mod M as they grow and combined in a fixed butterfly.
+// Call with the whole warp.
+__device__ __forceinline__ int64_t residue_warp(const int32_t* k, int d, const LatticeDev& L) {
+  const uint64_t M = (uint64_t)L.M, inv = ~0ull / M;
+  uint64_t acc = 0;
+  for (int c = (int)(threadIdx.x & 31); c < d; c += 32) {
+    int64_t kc = k[c];
+    if (kc < 0 || kc >= L.M) {
+      kc %= L.M;
+      if (kc < 0) kc += L.M;
+    }
+    acc += mulmod((uint64_t)kc, (uint64_t)L.z[c], M, inv);
+    if (acc >= M) acc -= M;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (acc >= M) acc -= M;
+  }
+  return (int64_t)acc;
+}
+
 ss_status make_lattice_dev(const ss_lattice* lat, LatticeDev* L);
 ss_status residues(const int32_t* freq, int64_t n, const LatticeDev& L, int64_t* res, cudaStream_t st);
 ss_status check_reconstructing(const int32_t* freq, int64_t n, const LatticeDev& L, const int64_t* res,

@@ -258,39 +258,57 @@ __global__ void k_twiddles_full(int64_t M, double2* tab) {
 // nonzero coordinate positive) with c or conj(c); equal representatives are
 // merged by their first occurrence ("leader"), which sums its group in index
 // order (deterministic).  The zero frequency keeps Re(c).
-__device__ __forceinline__ int rep_sign(const int32_t* p, int d) {
-  for (int c = 0; c < d; ++c)
-    if (p[c] != 0) return p[c] > 0 ? 1 : -1;
-  return 0;
+
+// One warp per term: sgn[t] = sign of the first nonzero coordinate of p_t
+// (0 for p_t = 0), 32 coordinates per step.
+__global__ void k_term_signs(const int32_t* __restrict__ freq, int64_t n, int d, int32_t* sgn) {
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= n) return;   // warp-uniform
+  int s = 0;
+  for (int c0 = 0; c0 < d && s == 0; c0 += 32) {
+    const int32_t v = c0 + lane < d ? freq[t * d + c0 + lane] : 0;
+    const unsigned m = __ballot_sync(0xffffffffu, v != 0);
+    if (m) s = __shfl_sync(0xffffffffu, v, __ffs(m) - 1) > 0 ? 1 : -1;
+  }
+  if (lane == 0) sgn[t] = s;
 }
 
-__device__ __forceinline__ bool same_rep(const int32_t* a, int sa, const int32_t* b, int sb, int d) {
-  const int xa = sa < 0 ? -1 : 1, xb = sb < 0 ? -1 : 1;
-  for (int c = 0; c < d; ++c)
-    if (xa * a[c] != xb * b[c]) return false;
-  return true;
-}
+// first[t] = smallest u < t with the same representative sgn p (n if none):
+// one block per term t, its warps taking u = w, w + 8, ... in increasing
+// order and comparing 32 coordinates per step.
+constexpr int kMergeWarps = 8;
 
-__global__ void k_fill_first(int32_t* first, int64_t n) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) first[t] = (int32_t)n;
-}
-
-// first[t] = smallest u < t with the same representative (n if none), one
-// thread per pair (t, u).
-__global__ void k_merge_first(const int32_t* __restrict__ freq, int64_t n, int d, int32_t* first) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n * n) return;
-  const int64_t t = p / n, u = p - t * n;
-  if (u >= t) return;
+__global__ void __launch_bounds__(32 * kMergeWarps) k_merge_first(const int32_t* __restrict__ freq, int64_t n, int d,
+                                                                   const int32_t* __restrict__ sgn, int32_t* first) {
+  __shared__ int32_t s_min[kMergeWarps];
+  const int64_t t = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int xt = sgn[t] < 0 ? -1 : 1;
   const int32_t* pt = freq + t * d;
-  const int32_t* pu = freq + u * d;
-  if (same_rep(pu, rep_sign(pu, d), pt, rep_sign(pt, d), d)) atomicMin(first + t, (int32_t)u);
+  int32_t best = (int32_t)n;
+  for (int64_t u = w; u < t; u += kMergeWarps) {
+    const int xu = sgn[u] < 0 ? -1 : 1;
+    const int32_t* pu = freq + u * d;
+    bool diff = false;
+    for (int c = lane; c < d; c += 32) diff |= xu * pu[c] != xt * pt[c];
+    if (!__any_sync(0xffffffffu, diff)) {
+      best = (int32_t)u;
+      break;
+    }
+  }
+  if (lane == 0) s_min[w] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t m = (int32_t)n;
+    for (int q = 0; q < kMergeWarps; ++q) m = min(m, s_min[q]);
+    first[t] = m;
+  }
 }
 
 // Leaders sum their group: one warp per term, lanes take the members in a
 // fixed stride, then a fixed butterfly (deterministic).
-__global__ void k_merge_sum(const int32_t* __restrict__ freq, const double2* __restrict__ coef, int64_t n, int d,
+__global__ void k_merge_sum(const int32_t* __restrict__ sgn, const double2* __restrict__ coef, int64_t n,
                             const int32_t* __restrict__ first, int32_t* leader_flag, double2* merged,
                             int32_t* imag_nonzero) {
   const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -299,11 +317,11 @@ __global__ void k_merge_sum(const int32_t* __restrict__ freq, const double2* __r
   const bool leader = first[t] == (int32_t)n;
   if (lane == 0) leader_flag[t] = leader ? 1 : 0;
   if (!leader) return;
-  const int st = rep_sign(freq + t * d, d);
+  const int st = sgn[t];
   double re = 0.0, im = 0.0;
   for (int64_t u = t + lane; u < n; u += 32) {
     if (u != t && first[u] != (int32_t)t) continue;
-    const int su = rep_sign(freq + u * d, d);
+    const int su = sgn[u];
     const double2 c = coef[u];
     re += c.x;
     im += (su == st) ? c.y : -c.y;
@@ -320,14 +338,16 @@ __global__ void k_merge_sum(const int32_t* __restrict__ freq, const double2* __r
 }
 
 // Compact the leaders: residue of the leader's frequency, step and coefficient.
+// One warp per term.
 __global__ void k_compact_terms(const int32_t* __restrict__ freq, int64_t n, LatticeDev L,
                                 const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
                                 const double2* __restrict__ merged, int64_t* q, int64_t* step, double2* coef_out) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n || !flag[t]) return;
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (t >= n || !flag[t]) return;   // warp-uniform
   const int64_t k = pos[t];
   // the merged coefficient is expressed in the leader's own orientation p_t
-  const int64_t r = residue_of(freq + t * L.d, L.d, L);
+  const int64_t r = residue_warp(freq + t * L.d, L.d, L);
+  if ((threadIdx.x & 31) != 0) return;
   q[k] = r;
   step[k] = (int64_t)(((uint64_t)r * (uint64_t)kSampThreads) % (uint64_t)L.M);
   coef_out[k] = merged[t];
@@ -857,7 +877,7 @@ ss_status prep_terms(const LatticeDev& L, const ss_trig* g, Terms* T, cudaStream
     return SS_OK;
   }
   if (n > 46340) SS_FAIL(SS_ERR_INVALID, "lattice_sample: more than 46340 terms");
-  DevBuf<int32_t> flag, pos, imag, first;
+  DevBuf<int32_t> flag, pos, imag, first, sgn;
   DevBuf<double2> merged;
   SS_TRY(T->q.alloc_tmp(n, st));
   SS_TRY(T->step.alloc_tmp(n, st));
@@ -867,15 +887,164 @@ ss_status prep_terms(const LatticeDev& L, const ss_trig* g, Terms* T, cudaStream
   SS_TRY(first.alloc_tmp(n, st));
   SS_TRY(merged.alloc_tmp(n, st));
   SS_TRY(T->coef.alloc_tmp(n, st));
+  SS_TRY(sgn.alloc_tmp(n, st));
   SS_CUDA(cudaMemsetAsync(imag.get(), 0, sizeof(int32_t), st));
-  k_fill_first<<<nblk(n), 256, 0, st>>>(first.get(), n);
-  k_merge_first<<<nblk(n * n), 256, 0, st>>>(g->freq, n, L.d, first.get());
-  k_merge_sum<<<nblk(n * 32), 256, 0, st>>>(g->freq, reinterpret_cast<const double2*>(g->coef), n, L.d,
-                                            first.get(), flag.get(), merged.get(), imag.get());
+  k_term_signs<<<nblk(n * 32), 256, 0, st>>>(g->freq, n, L.d, sgn.get());
+  k_merge_first<<<(unsigned)n, 32 * kMergeWarps, 0, st>>>(g->freq, n, L.d, sgn.get(), first.get());
+  k_merge_sum<<<nblk(n * 32), 256, 0, st>>>(sgn.get(), reinterpret_cast<const double2*>(g->coef), n, first.get(),
+                                            flag.get(), merged.get(), imag.get());
   SS_LAUNCH_CHECK();
   SS_TRY(exclusive_scan_i32(flag.get(), pos.get(), n, T->total.get(), st));
-  k_compact_terms<<<nblk(n), 256, 0, st>>>(g->freq, n, L, flag.get(), pos.get(), merged.get(), T->q.get(),
-                                           T->step.get(), T->coef.get());
+  k_compact_terms<<<nblk(n * 32), 256, 0, st>>>(g->freq, n, L, flag.get(), pos.get(), merged.get(), T->q.get(),
+                                                T->step.get(), T->coef.get());
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
+// Both sums of a pair with at most kPrepSmall terms each: one launch, one
+// block per sum doing every step of prep_terms (signs, first occurrences,
+// leader sums in the same order, prefix sum, compaction) in shared memory.
+constexpr int kPrepSmall = 1024;
+
+struct PrepArgs {
+  const int32_t* freq;
+  const double2* coef;
+  int64_t n;
+  int64_t* q;
+  int64_t* step;
+  double2* coef_out;
+  int64_t* total;
+};
+
+__global__ void __launch_bounds__(1024) k_prep_terms_small(PrepArgs A0, PrepArgs A1, LatticeDev L) {
+  __shared__ int32_t s_sgn[kPrepSmall], s_first[kPrepSmall], s_pos[kPrepSmall];
+  __shared__ double2 s_merged[kPrepSmall];
+  __shared__ uint64_t s_hash[kPrepSmall];
+  __shared__ int32_t s_wsum[32];
+  const PrepArgs& A = blockIdx.x == 0 ? A0 : A1;
+  const int n = (int)A.n, d = L.d;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // signs of the first nonzero coordinates
+  for (int t = w; t < n; t += nw) {
+    int sg = 0;
+    for (int c0 = 0; c0 < d && sg == 0; c0 += 32) {
+      const int32_t v = c0 + lane < d ? A.freq[(int64_t)t * d + c0 + lane] : 0;
+      const unsigned m = __ballot_sync(0xffffffffu, v != 0);
+      if (m) sg = __shfl_sync(0xffffffffu, v, __ffs(m) - 1) > 0 ? 1 : -1;
+    }
+    // a hash of the representative sgn p: equal representatives, equal hashes
+    const int x = sg < 0 ? -1 : 1;
+    uint64_t h = 0;
+    for (int c = lane; c < d; c += 32)
+      h += (uint64_t)(int64_t)(x * A.freq[(int64_t)t * d + c]) * (0x9e3779b97f4a7c15ull ^ ((uint64_t)c << 32 | 1u));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+    if (lane == 0) {
+      s_sgn[t] = sg;
+      s_hash[t] = h;
+    }
+  }
+  __syncthreads();
+  // first occurrence of every representative: hashes compared 32 at a time,
+  // the coordinates only where they agree
+  for (int t = w; t < n; t += nw) {
+    const int xt = s_sgn[t] < 0 ? -1 : 1;
+    const int32_t* pt = A.freq + (int64_t)t * d;
+    const uint64_t ht = s_hash[t];
+    int fu = n;
+    for (int u0 = 0; u0 < t && fu == n; u0 += 32) {
+      unsigned m = __ballot_sync(0xffffffffu, u0 + lane < t && s_hash[u0 + lane] == ht);
+      while (m) {
+        const int u = u0 + __ffs(m) - 1;
+        m &= m - 1;
+        const int xu = s_sgn[u] < 0 ? -1 : 1;
+        const int32_t* pu = A.freq + (int64_t)u * d;
+        bool diff = false;
+        for (int c = lane; c < d; c += 32) diff |= xu * pu[c] != xt * pt[c];
+        if (!__any_sync(0xffffffffu, diff)) {
+          fu = u;
+          break;
+        }
+      }
+    }
+    if (lane == 0) s_first[t] = fu;
+  }
+  __syncthreads();
+  // leaders sum their groups (lanes in a fixed stride, then a fixed butterfly)
+  for (int t = w; t < n; t += nw) {
+    const bool leader = s_first[t] == n;
+    if (lane == 0) s_pos[t] = leader ? 1 : 0;
+    if (!leader) continue;
+    const int st = s_sgn[t];
+    double re = 0.0, im = 0.0;
+    for (int u = t + lane; u < n; u += 32) {
+      if (u != t && s_first[u] != t) continue;
+      const double2 c = A.coef[u];
+      re += c.x;
+      im += (s_sgn[u] == st) ? c.y : -c.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) s_merged[t] = make_double2(re, st == 0 ? 0.0 : im);
+  }
+  __syncthreads();
+  // exclusive prefix sum of the leader flags (n <= blockDim)
+  const int t = threadIdx.x;
+  const int f = t < n ? s_pos[t] : 0;
+  int x = f;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_wsum[w] = x;
+  __syncthreads();
+  int before = 0, total = 0;
+  for (int q = 0; q < nw; ++q) {
+    if (q < w) before += s_wsum[q];
+    total += s_wsum[q];
+  }
+  __syncthreads();
+  if (t < n) s_pos[t] = f ? before + x - f : -1;
+  if (t == 0) *A.total = total;
+  __syncthreads();
+  // compaction: the residue of every leader by its warp
+  for (int u = w; u < n; u += nw) {
+    const int k = s_pos[u];
+    if (k < 0) continue;
+    const int64_t r = residue_warp(A.freq + (int64_t)u * d, d, L);
+    if (lane == 0) {
+      A.q[k] = r;
+      A.step[k] = (int64_t)(((uint64_t)r * (uint64_t)kSampThreads) % (uint64_t)L.M);
+      A.coef_out[k] = s_merged[u];
+    }
+  }
+}
+
+// prep_terms of the two sums of a pair (f may have no terms).
+ss_status prep_terms_pair(const LatticeDev& L, const ss_trig* a, const ss_trig* f, Terms* Ta, Terms* Tf,
+                          cudaStream_t st) {
+  if (a->n_terms > kPrepSmall || f->n_terms > kPrepSmall) {
+    SS_TRY(prep_terms(L, a, Ta, st));
+    return prep_terms(L, f, Tf, st);
+  }
+  ProfScope prof_("prep_terms", st);
+  PrepArgs A[2];
+  Terms* T[2] = {Ta, Tf};
+  const ss_trig* g[2] = {a, f};
+  for (int i = 0; i < 2; ++i) {
+    const int64_t n = g[i]->n_terms;
+    SS_TRY(T[i]->total.alloc_tmp(1, st));
+    SS_TRY(T[i]->q.alloc_tmp(std::max<int64_t>(n, 1), st));
+    SS_TRY(T[i]->step.alloc_tmp(std::max<int64_t>(n, 1), st));
+    SS_TRY(T[i]->coef.alloc_tmp(std::max<int64_t>(n, 1), st));
+    A[i] = PrepArgs{g[i]->freq, reinterpret_cast<const double2*>(g[i]->coef), n, T[i]->q.get(), T[i]->step.get(),
+                    T[i]->coef.get(), T[i]->total.get()};
+  }
+  k_prep_terms_small<<<2, 1024, 0, st>>>(A[0], A[1], L);
   SS_LAUNCH_CHECK();
   return SS_OK;
 }
@@ -973,8 +1142,7 @@ ss_status dff_round_trip(const SftPlan& P, const LatticeDev& L, const ss_trig* a
   const ss_trig none{L.d, 0, nullptr, nullptr};
   if (!f) f = &none;
   Terms ta, tf;
-  SS_TRY(prep_terms(L, a, &ta, st));
-  SS_TRY(prep_terms(L, f, &tf, st));
+  SS_TRY(prep_terms_pair(L, a, f, &ta, &tf, st));
   float4* Z = P.dfz.get();
   const float4* tab = reinterpret_cast<const float4*>(P.full.get());
   SS_CUDA(cudaMemsetAsync(Z, 0, P.M * sizeof(float4), st));
@@ -998,8 +1166,7 @@ ss_status pr_sample_pair(const SftPlan& P, const LatticeDev& L, const ss_trig* a
   const ss_trig none{L.d, 0, nullptr, nullptr};
   if (!f) f = &none;
   Terms ta, tf;
-  SS_TRY(prep_terms(L, a, &ta, st));
-  SS_TRY(prep_terms(L, f, &tf, st));
+  SS_TRY(prep_terms_pair(L, a, f, &ta, &tf, st));
   double* scale = P.prscale.get();
   k_pair_scale<<<1, kScaleThreads, 0, st>>>(ta.coef.get(), ta.total.get(), tf.coef.get(), tf.total.get(), scale);
   SS_LAUNCH_CHECK();
@@ -1035,6 +1202,67 @@ __global__ void k_extract_pr(const int64_t* __restrict__ res, int64_t n, int64_t
   const double m = hypot(v.x, v.y);
   mag[i] = m;
   atomicMax(maxbits, (unsigned long long)__double_as_longlong(m));
+}
+
+// Extraction, threshold and compaction of both sums in one launch (block k:
+// sum k) for at most kExtractSmall candidates: the same values, the same
+// threshold tau max|c| and the same candidate order as k_extract_pr, k_keep,
+// the prefix sum and k_compact.
+constexpr int kExtractSmall = 1024;
+
+__global__ void __launch_bounds__(1024) k_extract_keep_pr(const int64_t* __restrict__ res, int64_t n, int64_t M,
+                                                          const float4* __restrict__ X,
+                                                          const double* __restrict__ scale, double tau,
+                                                          const int32_t* __restrict__ cand, int d, int32_t* fo0,
+                                                          double2* vo0, int32_t* fo1, double2* vo1, int64_t* total) {
+  __shared__ double s_max[32];
+  __shared__ int32_t s_wsum[32];
+  __shared__ int32_t s_pos[kExtractSmall];
+  const int k = blockIdx.x;
+  const int i = threadIdx.x, lane = i & 31, w = i >> 5, nw = blockDim.x >> 5;
+  double2 v = make_double2(0.0, 0.0);
+  double m = 0.0;
+  if (i < n) {
+    const float4 xs = X[2 * i], ys = X[2 * i + 1];
+    const double xr = (double)xs.x + (double)xs.y, xi = (double)xs.z + (double)xs.w;
+    const double yr = (double)ys.x + (double)ys.y, yi = (double)ys.z + (double)ys.w;
+    const double sc = 0.5 / (double)M * scale[k];
+    v = k == 0 ? make_double2((xr + yr) * sc, (xi - yi) * sc) : make_double2((xi + yi) * sc, (yr - xr) * sc);
+    m = hypot(v.x, v.y);
+  }
+  double mx = m;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) s_max[w] = mx;
+  __syncthreads();
+  mx = 0.0;
+  for (int q = 0; q < nw; ++q) mx = fmax(mx, s_max[q]);
+  const int keep = (i < n && m > tau * mx) ? 1 : 0;
+  int x = keep;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_wsum[w] = x;
+  __syncthreads();
+  int before = 0, tot = 0;
+  for (int q = 0; q < nw; ++q) {
+    if (q < w) before += s_wsum[q];
+    tot += s_wsum[q];
+  }
+  if (i == 0) total[k] = tot;
+  int32_t* fo = k == 0 ? fo0 : fo1;
+  double2* vo = k == 0 ? vo0 : vo1;
+  if (i < n) s_pos[i] = keep ? before + x - 1 : -1;
+  if (keep) vo[before + x - 1] = v;
+  __syncthreads();
+  // the kept frequencies, one warp per row (coalesced coordinates)
+  for (int u = w; u < n; u += nw) {
+    const int p = s_pos[u];
+    if (p < 0) continue;
+    for (int c = lane; c < d; c += 32) fo[(int64_t)p * d + c] = cand[(int64_t)u * d + c];
+  }
 }
 
 // Pruned forward transform of s (P.prz, or the caller's real samples) at
@@ -1434,7 +1662,14 @@ ss_status sft_recover_both(const ss_lattice* lat, const ss_trig* a, const ss_tri
     DevBuf<float4> X;
     SS_TRY(X.alloc_tmp(2 * n_cand, st));
     SS_TRY(pr_transform(P, P.prz.get(), false, res.get(), n_cand, X.get(), st));
-    for (int k = 0; k < 2; ++k) {
+    if (n_cand <= kExtractSmall) {
+      ProfScope prof_("extract", st);
+      k_extract_keep_pr<<<2, 1024, 0, st>>>(res.get(), n_cand, L.M, X.get(), P.prscale.get(), tau, cand, L.d,
+                                           fo[0], reinterpret_cast<double2*>(vo[0]), fo[1],
+                                           reinterpret_cast<double2*>(vo[1]), total.get());
+      SS_LAUNCH_CHECK();
+    }
+    for (int k = 0; k < 2 && n_cand > kExtractSmall; ++k) {
       if (k == 0)
         k_extract_pr<0><<<nblk(n_cand), 256, 0, st>>>(res.get(), n_cand, L.M, X.get(), P.prscale.get(), val.get(),
                                                       mag.get(), maxbits.get());

@@ -1043,21 +1043,43 @@ ss_status plan_chunks(SolvePlan& plan, const std::vector<int32_t>& woff, const s
   // weight of a slice: its entries (gathers) plus the vector work of 32 rows
   // (small when the row-wise phases split the rows on their own)
   auto weight = [&](int64_t s) { return (double)(woff[s + 1] - woff[s]) + slice_overhead; };
-  double total = 0;
-  for (int64_t s = 0; s < n_slices; ++s) total += weight(s);
-  const double target = total / std::max(1, target_chunks);
   auto inst_of = [&](int64_t s) { return slice_inst.empty() ? 0 : slice_inst[s]; };
-  int64_t s0 = 0;
-  double acc = 0;
-  for (int64_t s = 0; s < n_slices; ++s) {
-    acc += weight(s);
-    const bool last = s + 1 == n_slices;
-    bool cut = last || acc >= target;
-    if (!last && inst_of(s + 1) - inst_of(s0) + 1 > kMaxInstPerChunk) cut = true;
-    if (cut) {
-      plan.chunk.push_back(Chunk{s0, s + 1, inst_of(s0), inst_of(s)});
-      s0 = s + 1;
-      acc = 0;
+  if (slice_inst.empty() && slice_overhead == std::floor(slice_overhead)) {
+    // one instance, integer weights: woff is the prefix sum of the widths, so
+    // the weight of slices [s0, s] is woff[s + 1] - woff[s0] + (s + 1 - s0) x
+    // overhead, exact in double; each cut (the first s where it reaches the
+    // target) by binary search, the same cuts as the running sum below
+    auto wsum = [&](int64_t s0, int64_t s1) {   // slices [s0, s1)
+      return (double)(woff[s1] - woff[s0]) + (double)(s1 - s0) * slice_overhead;
+    };
+    const double target = wsum(0, n_slices) / std::max(1, target_chunks);
+    int64_t s0 = 0;
+    while (s0 < n_slices) {
+      int64_t lo = s0, hi = n_slices - 1;   // smallest s in [s0, n) with wsum(s0, s + 1) >= target
+      while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (wsum(s0, mid + 1) >= target) hi = mid;
+        else lo = mid + 1;
+      }
+      plan.chunk.push_back(Chunk{s0, lo + 1, 0, 0});
+      s0 = lo + 1;
+    }
+  } else {
+    double total = 0;
+    for (int64_t s = 0; s < n_slices; ++s) total += weight(s);
+    const double target = total / std::max(1, target_chunks);
+    int64_t s0 = 0;
+    double acc = 0;
+    for (int64_t s = 0; s < n_slices; ++s) {
+      acc += weight(s);
+      const bool last = s + 1 == n_slices;
+      bool cut = last || acc >= target;
+      if (!last && inst_of(s + 1) - inst_of(s0) + 1 > kMaxInstPerChunk) cut = true;
+      if (cut) {
+        plan.chunk.push_back(Chunk{s0, s + 1, inst_of(s0), inst_of(s)});
+        s0 = s + 1;
+        acc = 0;
+      }
     }
   }
   for (auto& in : plan.inst) { in.c_first = INT32_MAX; in.c_last = -1; }

@@ -749,6 +749,55 @@ __global__ void k_lookup(KeyParams P, const uint64_t* __restrict__ keys, const u
   idx[i] = r;
 }
 
+// The same lookup by one warp per query: the lanes pack the coordinates
+// c = lane, lane + 32, ... into the key words (shared-memory OR: the fields do
+// not overlap), lane 0 probes, the lanes compare the words of a candidate.
+constexpr int kLookupWarps = 8;
+
+template <int WT>
+__global__ void __launch_bounds__(32 * kLookupWarps) k_lookup_warp(KeyParams P, const uint64_t* __restrict__ keys,
+                                                                   const uint64_t* __restrict__ table, uint64_t capmask,
+                                                                   const int32_t* __restrict__ q, int64_t n,
+                                                                   int64_t* idx) {
+  __shared__ unsigned long long s_key[kLookupWarps][WT];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * kLookupWarps + w;
+  if (i >= n) return;   // warp-uniform
+  if (lane < WT) s_key[w][lane] = 0ull;
+  __syncwarp();
+  bool ok = true;
+  for (int c = lane; c < P.d; c += 32) {
+    const int64_t v = (int64_t)q[i * P.d + c] + P.bias_val;
+    ok &= (v >= 0) && (v <= (int64_t)P.fieldmask);
+    const int wd = c / P.fpw, sh = 64 - P.fb * (c % P.fpw + 1);
+    atomicOr(&s_key[w][wd], (unsigned long long)(((uint64_t)v & P.fieldmask) << sh));
+  }
+  __syncwarp();
+  int64_t r = -1;
+  if (__all_sync(0xffffffffu, ok)) {
+    const uint64_t kw = lane < WT ? (uint64_t)s_key[w][lane] : 0ull;
+    uint64_t lin = lane < WT ? key_lin_coef(lane) * kw : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lin += __shfl_xor_sync(0xffffffffu, lin, o);
+    const uint64_t hh = hash_of_lin(lin), fp = slot_fp(hh);
+    uint64_t h = hh & capmask;
+    for (uint64_t probe = 0; probe <= capmask; ++probe) {
+      const uint64_t v = __ldg(table + h);   // every lane loads the same word
+      if (v == kEmpty) break;
+      if (word_fp(v) == fp) {
+        const int64_t o = (int64_t)word_low(v);
+        const bool eq = lane >= WT || __ldg(keys + o * WT + lane) == kw;
+        if (__all_sync(0xffffffffu, eq)) {
+          r = o;
+          break;
+        }
+      }
+      h = (h + 1) & capmask;
+    }
+  }
+  if (lane == 0) idx[i] = r;
+}
+
 __global__ void k_scatter_vals(const int64_t* __restrict__ idx, const double2* __restrict__ v, int64_t n,
                                double2* out, unsigned long long* outside) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1651,8 +1700,15 @@ extern "C" ss_status stamp_lookup(ss_stamp s, const int32_t* freq, int64_t n, in
   if (n == 0) return SS_OK;
   const KeyParams P = make_key_params(s->key);
   cudaStream_t st = as_stream(stream);
-  SS_DISPATCH_WT(s->key.WT, (k_lookup<WT><<<nblk(n), 256, 0, st>>>(P, s->keys.get(), s->hl.get(), s->table.get(),
-                                                                  (uint64_t)s->cap - 1, freq, n, idx_out)));
+  if (P.d > 16) {   // wide keys: one warp per query
+    SS_DISPATCH_WT(s->key.WT, (k_lookup_warp<WT><<<(unsigned)((n + kLookupWarps - 1) / kLookupWarps),
+                                                   32 * kLookupWarps, 0, st>>>(P, s->keys.get(), s->table.get(),
+                                                                               (uint64_t)s->cap - 1, freq, n,
+                                                                               idx_out)));
+  } else {
+    SS_DISPATCH_WT(s->key.WT, (k_lookup<WT><<<nblk(n), 256, 0, st>>>(P, s->keys.get(), s->hl.get(), s->table.get(),
+                                                                    (uint64_t)s->cap - 1, freq, n, idx_out)));
+  }
   SS_LAUNCH_CHECK();
   return SS_OK;
 }
