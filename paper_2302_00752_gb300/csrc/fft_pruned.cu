@@ -484,6 +484,231 @@ __global__ void __launch_bounds__(kPrThreads) k_pr_fwd(int64_t M, int P, int64_t
   for (int o = threadIdx.x; o < n_out; o += blockDim.x) partial[(int64_t)blockIdx.x * n_out + o] = acc[o];
 }
 
+// ------------------------------------------- 4096-value tiles, radix 16
+//
+// Double-float transforms with P = 128 or 256: tiles of W = 4096 / P columns,
+// the column transforms as two in-place Stockham passes, a radix-16 one and
+// one of radix P / 16.  Every thread holds one radix-16 butterfly (or two
+// radix-8 ones) in registers between a read phase and a write phase, so one
+// shared buffer serves both passes (two barriers per pass).  The forward
+// kernel's first pass reads the samples straight from global memory and the
+// evaluation's second pass writes them straight there.
+constexpr int kPr16Tile = 4096;
+constexpr int kPr16Threads = 256;   // butterflies of a radix-16 pass over a tile
+
+__host__ __device__ constexpr bool pr16_supported(int P) { return P == 128 || P == 256; }
+
+// 16-point DFT in place (SIGN: exponent sign), natural input order; the
+// output X[k1 + 4 k2] ends at v[4 k1 + k2].  w1, w2, w3 = exp(2 pi i j / 16).
+// Four 4-point transforms (stride 4), the twiddles w16^(n2 k1), four more.
+template <int SIGN>
+__device__ __forceinline__ void dft16(C4 (&v)[16], const C4 w1, const C4 w2, const C4 w3) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<SIGN>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+  auto tw = [](const C4 a, const C4 w) { return cmul(a, SIGN > 0 ? w : conj4(w)); };
+  v[5] = tw(v[5], w1);
+  v[9] = tw(v[9], w2);
+  v[13] = tw(v[13], w3);
+  v[6] = tw(v[6], w2);
+  v[10] = mul_si<SIGN>(v[10]);
+  v[14] = mul_si<SIGN>(tw(v[14], w2));   // w16^6 = i w16^2
+  v[7] = tw(v[7], w3);
+  v[11] = mul_si<SIGN>(tw(v[11], w2));
+  {
+    const C4 t = tw(v[15], w1);   // w16^9 = -w16^1
+    v[15] = C4{df_neg(t.re), df_neg(t.im)};
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<SIGN>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+}
+
+// Second pass (Ns = 16) of one column in place: butterflies k (and k + 8 when
+// the radix is 8) read k + 16 r, take the twiddles w_P^(SIGN k r) and write
+// output r at k + 16 r.  OUT(p, value) receives the outputs (position p in the
+// column); with IN_PLACE the block synchronises between reads and writes.
+template <int P, int SIGN, bool IN_PLACE, class Out>
+__device__ __forceinline__ void pr16_pass2(float4* col, int k, const float4* tw, const C4 w1, const C4 w2,
+                                           const C4 w3, Out out) {
+  if constexpr (P == 256) {
+    C4 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = ld(col[k + 16 * r]);
+    if (IN_PLACE) __syncthreads();
+#pragma unroll
+    for (int r = 1; r < 16; ++r) {
+      const C4 w = ld(tw[k * r]);
+      v[r] = cmul(v[r], SIGN > 0 ? w : conj4(w));
+    }
+    dft16<SIGN>(v, w1, w2, w3);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) out(k + 16 * (k1 + 4 * k2), v[4 * k1 + k2]);
+  } else {   // P = 128: radix 8, butterflies k and k + 8
+    C4 v[2][8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[h][r] = ld(col[k + 8 * h + 16 * r]);
+    if (IN_PLACE) __syncthreads();
+    const C4 cs[1] = {w2};   // exp(2 pi i / 8)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int kk = k + 8 * h;
+#pragma unroll
+      for (int r = 1; r < 8; ++r) {
+        const C4 w = ld(tw[kk * r]);
+        v[h][r] = cmul(v[h][r], SIGN > 0 ? w : conj4(w));
+      }
+      dft<8, SIGN>(v[h], cs);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) out(kk + 16 * r, v[h][r]);
+    }
+  }
+}
+
+// Evaluation with 4096-value tiles (see above); the bucket phase as k_pr_eval.
+template <int P, bool OUT_REAL>
+__global__ void __launch_bounds__(kPr16Threads, 2) k_pr_eval16(int64_t M, int64_t Q, const float4* __restrict__ t0,
+                                                               const float4* __restrict__ t1, int b,
+                                                               const int64_t* __restrict__ er,
+                                                               const float4* __restrict__ ev,
+                                                               const int32_t* __restrict__ boff_g,
+                                                               const float4* __restrict__ estep, int n_stage,
+                                                               int64_t n_tiles, void* __restrict__ out) {
+  constexpr int W = kPr16Tile / P, CS = P + 1, R2 = P / 16;
+  extern __shared__ __align__(16) float4 sm4[];
+  float4* tl = sm4;
+  float4* tw = tl + W * CS;
+  float4* base = tw + P;
+  float4* es = base + kPrChunk;
+  int32_t* boff = reinterpret_cast<int32_t*>(es + n_stage);
+  const uint64_t Mu = (uint64_t)M, inv = ~0ull / Mu;
+  for (int m = threadIdx.x; m < P; m += blockDim.x) tw[m] = st4(tw2<1>(t0, t1, b, (uint64_t)m * (uint64_t)Q));
+  for (int k = threadIdx.x; k <= P; k += blockDim.x) boff[k] = boff_g[k];
+  __syncthreads();
+  const int ne = boff[P];
+  if (n_stage > 0) {
+    for (int x = threadIdx.x; x < ne * W; x += blockDim.x) es[x] = __ldg(estep + x);
+    __syncthreads();
+  }
+  const C4 w1 = ld(tw[P / 16]), w2 = ld(tw[2 * P / 16]), w3 = ld(tw[3 * P / 16]);
+  const int u = threadIdx.x;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t q0 = tile * W;
+    // C[k][i] = sum_{e in bucket k} v_e w^{(q0 + i) r_e}, in chunks of entries
+    int e0 = 0;
+    do {
+      const int e1 = min(ne, e0 + kPrChunk);
+      for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x)
+        base[e - e0] = st4(cmul(ld(__ldg(ev + e)), tw2<1>(t0, t1, b, mulmod((uint64_t)q0, (uint64_t)er[e], Mu, inv))));
+      __syncthreads();
+      for (int x = threadIdx.x; x < P * W; x += blockDim.x) {
+        const int i = x % W, k = x / W;
+        const int lo = max(boff[k], e0), hi = min(boff[k + 1], e1);
+        C4 sum = e0 == 0 ? zero4() : ld(tl[i * CS + k]);
+        for (int e = lo; e < hi; ++e)
+          sum = cadd(sum, cmul(ld(base[e - e0]), ld(n_stage > 0 ? es[e * W + i] : __ldg(estep + (int64_t)e * W + i))));
+        tl[i * CS + k] = st4(sum);
+      }
+      __syncthreads();
+      e0 += kPrChunk;
+    } while (e0 < ne);
+    // pass 1 (radix 16, Ns = 1): butterfly j of column c reads j + R2 r, writes 16 j + r
+    {
+      const int c = u % W, j = u / W;
+      float4* col = tl + c * CS;
+      C4 v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = ld(col[j + R2 * r]);
+      __syncthreads();
+      dft16<1>(v, w1, w2, w3);
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) col[16 * j + k1 + 4 * k2] = st4(v[4 * k1 + k2]);
+    }
+    __syncthreads();
+    // pass 2 straight to the samples s[q0 + c + Q p]
+    {
+      const int c = u % W, k = u / W;
+      const int64_t q = q0 + c;
+      pr16_pass2<P, 1, false>(tl + c * CS, k, tw, w1, w2, w3, [&](int p, const C4 val) {
+        if (q >= Q) return;
+        if (OUT_REAL)
+          static_cast<double*>(out)[q + Q * p] = (double)val.re.hi + (double)val.re.lo;
+        else
+          static_cast<float4*>(out)[q + Q * p] = st4(val);
+      });
+    }
+    __syncthreads();
+  }
+}
+
+// Pruned forward transform with 4096-value tiles (see above); the Horner
+// phase as k_pr_fwd.
+template <int P, bool IN_REAL>
+__global__ void __launch_bounds__(kPr16Threads, 2) k_pr_fwd16(int64_t M, int64_t Q, const float4* __restrict__ t0,
+                                                              const float4* __restrict__ t1, int b,
+                                                              const void* __restrict__ in,
+                                                              const int64_t* __restrict__ ob,
+                                                              const int32_t* __restrict__ kout, int n_out,
+                                                              const float4* __restrict__ oz, int64_t n_tiles,
+                                                              float4* __restrict__ partial) {
+  constexpr int W = kPr16Tile / P, CS = P + 1, R2 = P / 16;
+  extern __shared__ __align__(16) float4 sm4[];
+  float4* tl = sm4;
+  float4* tw = tl + W * CS;
+  float4* acc = tw + P;
+  const uint64_t Mu = (uint64_t)M, inv = ~0ull / Mu;
+  for (int m = threadIdx.x; m < P; m += blockDim.x) tw[m] = st4(tw2<1>(t0, t1, b, (uint64_t)m * (uint64_t)Q));
+  for (int o = threadIdx.x; o < n_out; o += blockDim.x) acc[o] = st4(zero4());
+  __syncthreads();
+  const C4 w1 = ld(tw[P / 16]), w2 = ld(tw[2 * P / 16]), w3 = ld(tw[3 * P / 16]);
+  const int u = threadIdx.x;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t q0 = tile * W;
+    // pass 1 (radix 16, Ns = 1) from the samples: butterfly j of column c
+    // reads p = j + R2 r, writes 16 j + r
+    {
+      const int c = u % W, j = u / W;
+      const int64_t q = q0 + c;
+      C4 v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int64_t p = j + R2 * r;
+        if (q >= Q) v[r] = zero4();
+        else if (IN_REAL) v[r] = C4{df_split(__ldg(static_cast<const double*>(in) + q + Q * p)), DF{0.f, 0.f}};
+        else v[r] = ld(__ldg(static_cast<const float4*>(in) + q + Q * p));
+      }
+      dft16<-1>(v, w1, w2, w3);
+      float4* col = tl + c * CS;
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) col[16 * j + k1 + 4 * k2] = st4(v[4 * k1 + k2]);
+    }
+    __syncthreads();
+    {
+      const int c = u % W, k = u / W;
+      float4* col = tl + c * CS;
+      pr16_pass2<P, -1, true>(col, k, tw, w1, w2, w3, [&](int p, const C4 val) { col[p] = st4(val); });
+    }
+    __syncthreads();
+    const int wl = Q - q0 < (int64_t)W ? (int)(Q - q0) : W;
+    for (int o = threadIdx.x; o < n_out; o += blockDim.x) {
+      const int k = kout[o];
+      const C4 w = tw2<-1>(t0, t1, b, mulmod((uint64_t)q0, (uint64_t)ob[o], Mu, inv));
+      const C4 z = ld(__ldg(oz + 2 * o));
+      C4 sum = ld(tl[(wl - 1) * CS + k]);
+      for (int i = wl - 2; i >= 0; --i) sum = cadd(cmul(sum, z), ld(tl[i * CS + k]));
+      acc[o] = st4(cadd(ld(acc[o]), cmul(sum, w)));
+    }
+    __syncthreads();
+  }
+  for (int o = threadIdx.x; o < n_out; o += blockDim.x) partial[(int64_t)blockIdx.x * n_out + o] = acc[o];
+}
+
 // X[o] = sum over blocks of partial[blk][o] in FP64: one warp per output,
 // lanes in a fixed stride, then a fixed butterfly; written as double-float.
 template <class A>
@@ -538,6 +763,46 @@ ss_status launch_eval(const TwoLevelTable& T, const PrunedSplit& S, int wsh, con
   SS_TRY(grid_for(k_pr_eval<A, OUT_REAL>, smem, n_tiles, &grid));
   k_pr_eval<A, OUT_REAL><<<grid, kPrThreads, smem, st>>>(T.M, S.P, S.Q, wsh, S.rad, T.t0.get(), T.t1.get(), T.b, er,
                                                          ev, boff, estep, (int)n_stage, n_tiles, out);
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
+template <int P, bool OUT_REAL>
+ss_status launch_eval16(const TwoLevelTable& T, const PrunedSplit& S, const int64_t* er, const float4* ev,
+                        const int32_t* boff, const float4* estep, int64_t n_stage, void* out, cudaStream_t st) {
+  constexpr int W = kPr16Tile / P;
+  const int64_t n_tiles = (S.Q + W - 1) / W;
+  const size_t smem = (size_t)(W * (P + 1) + P + kPrChunk + n_stage) * sizeof(float4) + (P + 1) * sizeof(int32_t);
+  int grid = 0;
+  SS_TRY(grid_for(k_pr_eval16<P, OUT_REAL>, smem, n_tiles, &grid));
+  k_pr_eval16<P, OUT_REAL><<<grid, kPr16Threads, smem, st>>>(T.M, S.Q, T.t0.get(), T.t1.get(), T.b, er, ev, boff,
+                                                              estep, (int)n_stage, n_tiles, out);
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
+template <bool IN_REAL>
+ss_status launch_fwd16(const TwoLevelTable& T, const PrunedSplit& S, const void* in, const int64_t* ob,
+                       const int32_t* kout, int nc, const float4* oz, float4* X, cudaStream_t st) {
+  const int W = kPr16Tile / S.P;
+  const int64_t n_tiles = (S.Q + W - 1) / W;
+  const size_t smem = (size_t)(W * (S.P + 1) + S.P + nc) * sizeof(float4);
+  int grid = 0;
+  if (S.P == 256) SS_TRY(grid_for(k_pr_fwd16<256, IN_REAL>, smem, n_tiles, &grid));
+  else SS_TRY(grid_for(k_pr_fwd16<128, IN_REAL>, smem, n_tiles, &grid));
+  DevBuf<float4> partial;
+  SS_TRY(partial.alloc_tmp((size_t)grid * nc, st));
+  {
+    ProfScope prof_("k_pr_fwd", st, true);
+    if (S.P == 256)
+      k_pr_fwd16<256, IN_REAL><<<grid, kPr16Threads, smem, st>>>(T.M, S.Q, T.t0.get(), T.t1.get(), T.b, in, ob, kout,
+                                                                  nc, oz, n_tiles, partial.get());
+    else
+      k_pr_fwd16<128, IN_REAL><<<grid, kPr16Threads, smem, st>>>(T.M, S.Q, T.t0.get(), T.t1.get(), T.b, in, ob, kout,
+                                                                  nc, oz, n_tiles, partial.get());
+    SS_LAUNCH_CHECK();
+  }
+  k_pr_reduce<ArDF><<<nblk((int64_t)nc * 32), 256, 0, st>>>(partial.get(), grid, nc, X);
   SS_LAUNCH_CHECK();
   return SS_OK;
 }
@@ -618,6 +883,10 @@ ss_status pruned_eval_pair(const TwoLevelTable& T, const int64_t* qa, const doub
   PrunedSplit S;
   if (!pruned_split(M, ne_max, &S, kPrEvalTile))
     SS_FAIL(SS_ERR_INVALID, "pruned evaluation: M = %lld has no split", (long long)M);
+  // double-float sums with P = 128 or 256: 4096-value tiles (k_pr_eval16)
+  const bool df = fmt == PrunedFormat::kDfComplex || fmt == PrunedFormat::kF64Real;
+  const bool t16 = df && pr16_supported(S.P);
+  const int Wt = t16 ? kPr16Tile / S.P : S.W;
   DevBuf<int64_t> er;
   DevBuf<float4> ev, estep;
   DevBuf<int32_t> boff, kq;
@@ -625,7 +894,7 @@ ss_status pruned_eval_pair(const TwoLevelTable& T, const int64_t* qa, const doub
   SS_TRY(ev.alloc_tmp(ne_max, st));
   SS_TRY(boff.alloc_tmp(S.P + 1, st));
   SS_TRY(kq.alloc_tmp(ne_max, st));
-  SS_TRY(estep.alloc_tmp((size_t)ne_max * S.W, st));
+  SS_TRY(estep.alloc_tmp((size_t)ne_max * Wt, st));
   {
     ProfScope prof_setup("pr_setup", st);
     const int eb = std::min(1024, (S.P + 31) / 32 * 32);
@@ -636,15 +905,23 @@ ss_status pruned_eval_pair(const TwoLevelTable& T, const int64_t* qa, const doub
                                                                         S.P, kq.get(), er.get(), ev.get(),
                                                                         boff.get(), kq_smem);
     SS_LAUNCH_CHECK();
-    k_pr_steps<1><<<nblk(ne_max * S.W), 256, 0, st>>>(er.get(), boff.get() + S.P, 0, S.W, M, T.t0.get(), T.t1.get(),
-                                                      T.b, estep.get());
+    k_pr_steps<1><<<nblk(ne_max * Wt), 256, 0, st>>>(er.get(), boff.get() + S.P, 0, Wt, M, T.t0.get(), T.t1.get(),
+                                                     T.b, estep.get());
     SS_LAUNCH_CHECK();
   }
   int wsh = 0;
   while ((1 << wsh) < S.W) ++wsh;
   // the entries' step powers go to shared memory once per block when they fit
-  const int64_t n_stage = ne_max * S.W <= kPrEvalStage ? ne_max * S.W : 0;
+  const int64_t n_stage = ne_max * Wt <= kPrEvalStage ? ne_max * Wt : 0;
   ProfScope prof_("k_pr_eval", st, true);
+  if (t16) {
+    const bool real = fmt == PrunedFormat::kF64Real;
+    if (S.P == 256)
+      return real ? launch_eval16<256, true>(T, S, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st)
+                  : launch_eval16<256, false>(T, S, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st);
+    return real ? launch_eval16<128, true>(T, S, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st)
+                : launch_eval16<128, false>(T, S, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st);
+  }
   switch (fmt) {
     case PrunedFormat::kDfComplex:
       return launch_eval<ArDF, false>(T, S, wsh, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st);
@@ -677,12 +954,15 @@ ss_status pruned_forward(const TwoLevelTable& T, const void* s, PrunedFormat fmt
                                                           oz.get());
     SS_LAUNCH_CHECK();
     const float4* z = oz.get() + 1;
+    const bool t16 = pr16_supported(S.P);   // double-float formats: 4096-value tiles
     switch (fmt) {
       case PrunedFormat::kDfComplex:
-        SS_TRY((launch_fwd<ArDF, false>(T, S, wsh, s, bins + o0, kout.get(), nc, z, X + o0, st)));
+        if (t16) SS_TRY((launch_fwd16<false>(T, S, s, bins + o0, kout.get(), nc, z, X + o0, st)));
+        else SS_TRY((launch_fwd<ArDF, false>(T, S, wsh, s, bins + o0, kout.get(), nc, z, X + o0, st)));
         break;
       case PrunedFormat::kF64Real:
-        SS_TRY((launch_fwd<ArDF, true>(T, S, wsh, s, bins + o0, kout.get(), nc, z, X + o0, st)));
+        if (t16) SS_TRY((launch_fwd16<true>(T, S, s, bins + o0, kout.get(), nc, z, X + o0, st)));
+        else SS_TRY((launch_fwd<ArDF, true>(T, S, wsh, s, bins + o0, kout.get(), nc, z, X + o0, st)));
         break;
       case PrunedFormat::kF32Complex:
         SS_TRY((launch_fwd<ArF32, false>(T, S, wsh, s, bins + o0, kout.get(), nc, z, X + o0, st)));
