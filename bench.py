@@ -193,6 +193,8 @@ def butterfly_instr(R, twiddled):
         d = 8 * C_ADD
     elif R == 8:
         d = 2 * 8 * C_ADD + 2 * (2 * DF_MUL + 2 * DF_ADD) + 8 * C_ADD
+    elif R == 16:   # 4 x 4: eight 4-point transforms, eight products by w16 powers (w16^4 = i is free)
+        d = 8 * 8 * C_ADD + 8 * C_MUL
     else:
         H = (R - 1) // 2
         d = 3 * H * C_ADD + H * (4 * H * DF_FMA + 2 * C_ADD)
@@ -223,6 +225,8 @@ def pruned_instr(kind, M, n_split, n_work):
     """Algorithmic FP32 instructions of one k_pr_eval (n_work entries) or
     k_pr_fwd (n_work outputs) launch."""
     P, Q, w, rad = pruned_split_py(M, n_split, 2048)
+    if P in (128, 256):   # double-float kernels with 4096-value tiles: a radix-16 pass, then one of radix P / 16
+        w, rad = 4096 // P, [16, P // 16]
     col, Ns = 0, 1
     for R in rad:
         col += (P // R) * butterfly_instr(R, Ns > 1)

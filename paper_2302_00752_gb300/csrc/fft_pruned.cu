@@ -125,12 +125,60 @@ __device__ __forceinline__ void fdft(float2 (&v)[R], const float2* cs) {
   }
 }
 
+// 16-point DFT as dft16 below, on FP32 complex values; output X[k1 + 4 k2]
+// at v[4 k1 + k2].
+template <int SIGN>
+__device__ __forceinline__ void fdft16(float2 (&v)[16], const float2 w1, const float2 w2, const float2 w3) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) fdft4<SIGN>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+  auto tw = [](const float2 a, const float2 w) { return fmul(a, SIGN > 0 ? w : fconj(w)); };
+  v[5] = tw(v[5], w1);
+  v[9] = tw(v[9], w2);
+  v[13] = tw(v[13], w3);
+  v[6] = tw(v[6], w2);
+  v[10] = fmul_si<SIGN>(v[10]);
+  v[14] = fmul_si<SIGN>(tw(v[14], w2));
+  v[7] = tw(v[7], w3);
+  v[11] = fmul_si<SIGN>(tw(v[11], w2));
+  {
+    const float2 t = tw(v[15], w1);
+    v[15] = make_float2(-t.x, -t.y);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) fdft4<SIGN>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+}
+
+// 16-point DFT in place (SIGN: exponent sign), natural input order; the
+// output X[k1 + 4 k2] ends at v[4 k1 + k2].  w1, w2, w3 = exp(2 pi i j / 16).
+// Four 4-point transforms (stride 4), the twiddles w16^(n2 k1), four more.
+template <int SIGN>
+__device__ __forceinline__ void dft16(C4 (&v)[16], const C4 w1, const C4 w2, const C4 w3) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<SIGN>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+  auto tw = [](const C4 a, const C4 w) { return cmul(a, SIGN > 0 ? w : conj4(w)); };
+  v[5] = tw(v[5], w1);
+  v[9] = tw(v[9], w2);
+  v[13] = tw(v[13], w3);
+  v[6] = tw(v[6], w2);
+  v[10] = mul_si<SIGN>(v[10]);
+  v[14] = mul_si<SIGN>(tw(v[14], w2));   // w16^6 = i w16^2
+  v[7] = tw(v[7], w3);
+  v[11] = mul_si<SIGN>(tw(v[11], w2));
+  {
+    const C4 t = tw(v[15], w1);   // w16^9 = -w16^1
+    v[15] = C4{df_neg(t.re), df_neg(t.im)};
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<SIGN>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+}
+
 // ------------------------------------------------------- arithmetic policies
 
 // Double-float complex values stored as float4 (re.hi, re.lo, im.hi, im.lo).
 struct ArDF {
   using V = float4;
   using C = C4;
+  static constexpr int kMinBlocks16 = 2;   // resident blocks per SM of the 4096-value-tile kernels
   static __device__ __forceinline__ C ld(const V v) { return dfc::ld(v); }
   static __device__ __forceinline__ V st(const C c) { return st4(c); }
   static __device__ __forceinline__ C add(const C a, const C b) { return cadd(a, b); }
@@ -147,6 +195,10 @@ struct ArDF {
   static __device__ __forceinline__ void dft(C (&v)[R], const C* cs) {
     dfc::dft<R, SIGN>(v, cs);
   }
+  template <int SIGN>
+  static __device__ __forceinline__ void dft16(C (&v)[16], const C w1, const C w2, const C w3) {
+    ss::dft16<SIGN>(v, w1, w2, w3);
+  }
   static __device__ __forceinline__ double2 to_double2(const V v) {
     return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
   }
@@ -159,6 +211,7 @@ struct ArDF {
 struct ArF32 {
   using V = float2;
   using C = float2;
+  static constexpr int kMinBlocks16 = 3;
   static __device__ __forceinline__ C ld(const V v) { return v; }
   static __device__ __forceinline__ V st(const C c) { return c; }
   static __device__ __forceinline__ C add(const C a, const C b) { return fadd(a, b); }
@@ -175,6 +228,10 @@ struct ArF32 {
   template <int R, int SIGN>
   static __device__ __forceinline__ void dft(C (&v)[R], const C* cs) {
     fdft<R, SIGN>(v, cs);
+  }
+  template <int SIGN>
+  static __device__ __forceinline__ void dft16(C (&v)[16], const C w1, const C w2, const C w3) {
+    fdft16<SIGN>(v, w1, w2, w3);
   }
   static __device__ __forceinline__ double2 to_double2(const V v) { return make_double2(v.x, v.y); }
   using Real = float;    // real samples: FP32
@@ -498,69 +555,47 @@ constexpr int kPr16Threads = 256;   // butterflies of a radix-16 pass over a til
 
 __host__ __device__ constexpr bool pr16_supported(int P) { return P == 128 || P == 256; }
 
-// 16-point DFT in place (SIGN: exponent sign), natural input order; the
-// output X[k1 + 4 k2] ends at v[4 k1 + k2].  w1, w2, w3 = exp(2 pi i j / 16).
-// Four 4-point transforms (stride 4), the twiddles w16^(n2 k1), four more.
-template <int SIGN>
-__device__ __forceinline__ void dft16(C4 (&v)[16], const C4 w1, const C4 w2, const C4 w3) {
-#pragma unroll
-  for (int n2 = 0; n2 < 4; ++n2) dft4<SIGN>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
-  auto tw = [](const C4 a, const C4 w) { return cmul(a, SIGN > 0 ? w : conj4(w)); };
-  v[5] = tw(v[5], w1);
-  v[9] = tw(v[9], w2);
-  v[13] = tw(v[13], w3);
-  v[6] = tw(v[6], w2);
-  v[10] = mul_si<SIGN>(v[10]);
-  v[14] = mul_si<SIGN>(tw(v[14], w2));   // w16^6 = i w16^2
-  v[7] = tw(v[7], w3);
-  v[11] = mul_si<SIGN>(tw(v[11], w2));
-  {
-    const C4 t = tw(v[15], w1);   // w16^9 = -w16^1
-    v[15] = C4{df_neg(t.re), df_neg(t.im)};
-  }
-#pragma unroll
-  for (int k1 = 0; k1 < 4; ++k1) dft4<SIGN>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
-}
-
 // Second pass (Ns = 16) of one column in place: butterflies k (and k + 8 when
 // the radix is 8) read k + 16 r, take the twiddles w_P^(SIGN k r) and write
-// output r at k + 16 r.  OUT(p, value) receives the outputs (position p in the
+// output r at k + 16 r.  out(p, value) receives the outputs (position p in the
 // column); with IN_PLACE the block synchronises between reads and writes.
-template <int P, int SIGN, bool IN_PLACE, class Out>
-__device__ __forceinline__ void pr16_pass2(float4* col, int k, const float4* tw, const C4 w1, const C4 w2,
-                                           const C4 w3, Out out) {
+template <class A, int P, int SIGN, bool IN_PLACE, class Out>
+__device__ __forceinline__ void pr16_pass2(const typename A::V* col, int k, const typename A::V* tw,
+                                           const typename A::C w1, const typename A::C w2, const typename A::C w3,
+                                           Out out) {
+  using C = typename A::C;
   if constexpr (P == 256) {
-    C4 v[16];
+    C v[16];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = ld(col[k + 16 * r]);
+    for (int r = 0; r < 16; ++r) v[r] = A::ld(col[k + 16 * r]);
     if (IN_PLACE) __syncthreads();
 #pragma unroll
     for (int r = 1; r < 16; ++r) {
-      const C4 w = ld(tw[k * r]);
-      v[r] = cmul(v[r], SIGN > 0 ? w : conj4(w));
+      const C w = A::ld(tw[k * r]);
+      v[r] = A::mul(v[r], SIGN > 0 ? w : A::conj(w));
     }
-    dft16<SIGN>(v, w1, w2, w3);
+    A::template dft16<SIGN>(v, w1, w2, w3);
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1)
 #pragma unroll
       for (int k2 = 0; k2 < 4; ++k2) out(k + 16 * (k1 + 4 * k2), v[4 * k1 + k2]);
   } else {   // P = 128: radix 8, butterflies k and k + 8
-    C4 v[2][8];
+    C v[2][8];
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int r = 0; r < 8; ++r) v[h][r] = ld(col[k + 8 * h + 16 * r]);
+      for (int r = 0; r < 8; ++r) v[h][r] = A::ld(col[k + 8 * h + 16 * r]);
     if (IN_PLACE) __syncthreads();
-    const C4 cs[1] = {w2};   // exp(2 pi i / 8)
+    const C cs[1] = {w2};   // exp(2 pi i / 8)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int kk = k + 8 * h;
 #pragma unroll
       for (int r = 1; r < 8; ++r) {
-        const C4 w = ld(tw[kk * r]);
-        v[h][r] = cmul(v[h][r], SIGN > 0 ? w : conj4(w));
+        const C w = A::ld(tw[kk * r]);
+        v[h][r] = A::mul(v[h][r], SIGN > 0 ? w : A::conj(w));
       }
-      dft<8, SIGN>(v[h], cs);
+      A::template dft<8, SIGN>(v[h], cs);
 #pragma unroll
       for (int r = 0; r < 8; ++r) out(kk + 16 * r, v[h][r]);
     }
@@ -568,31 +603,34 @@ __device__ __forceinline__ void pr16_pass2(float4* col, int k, const float4* tw,
 }
 
 // Evaluation with 4096-value tiles (see above); the bucket phase as k_pr_eval.
-template <int P, bool OUT_REAL>
-__global__ void __launch_bounds__(kPr16Threads, 2) k_pr_eval16(int64_t M, int64_t Q, const float4* __restrict__ t0,
+template <class A, int P, bool OUT_REAL>
+__global__ void __launch_bounds__(kPr16Threads, A::kMinBlocks16) k_pr_eval16(int64_t M, int64_t Q, const float4* __restrict__ t0,
                                                                const float4* __restrict__ t1, int b,
                                                                const int64_t* __restrict__ er,
                                                                const float4* __restrict__ ev,
                                                                const int32_t* __restrict__ boff_g,
                                                                const float4* __restrict__ estep, int n_stage,
                                                                int64_t n_tiles, void* __restrict__ out) {
+  using V = typename A::V;
+  using C = typename A::C;
   constexpr int W = kPr16Tile / P, CS = P + 1, R2 = P / 16;
   extern __shared__ __align__(16) float4 sm4[];
-  float4* tl = sm4;
-  float4* tw = tl + W * CS;
-  float4* base = tw + P;
-  float4* es = base + kPrChunk;
+  V* tl = reinterpret_cast<V*>(sm4);
+  V* tw = tl + W * CS;
+  V* base = tw + P;
+  V* es = base + kPrChunk;
   int32_t* boff = reinterpret_cast<int32_t*>(es + n_stage);
   const uint64_t Mu = (uint64_t)M, inv = ~0ull / Mu;
-  for (int m = threadIdx.x; m < P; m += blockDim.x) tw[m] = st4(tw2<1>(t0, t1, b, (uint64_t)m * (uint64_t)Q));
+  for (int m = threadIdx.x; m < P; m += blockDim.x)
+    tw[m] = A::st(A::template root<1>(t0, t1, b, (uint64_t)m * (uint64_t)Q));
   for (int k = threadIdx.x; k <= P; k += blockDim.x) boff[k] = boff_g[k];
   __syncthreads();
   const int ne = boff[P];
   if (n_stage > 0) {
-    for (int x = threadIdx.x; x < ne * W; x += blockDim.x) es[x] = __ldg(estep + x);
+    for (int x = threadIdx.x; x < ne * W; x += blockDim.x) es[x] = A::st(A::from_df(__ldg(estep + x)));
     __syncthreads();
   }
-  const C4 w1 = ld(tw[P / 16]), w2 = ld(tw[2 * P / 16]), w3 = ld(tw[3 * P / 16]);
+  const C w1 = A::ld(tw[P / 16]), w2 = A::ld(tw[2 * P / 16]), w3 = A::ld(tw[3 * P / 16]);
   const int u = threadIdx.x;
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t q0 = tile * W;
@@ -601,15 +639,18 @@ __global__ void __launch_bounds__(kPr16Threads, 2) k_pr_eval16(int64_t M, int64_
     do {
       const int e1 = min(ne, e0 + kPrChunk);
       for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x)
-        base[e - e0] = st4(cmul(ld(__ldg(ev + e)), tw2<1>(t0, t1, b, mulmod((uint64_t)q0, (uint64_t)er[e], Mu, inv))));
+        base[e - e0] = A::st(A::mul(A::from_df(__ldg(ev + e)),
+                                    A::template root<1>(t0, t1, b, mulmod((uint64_t)q0, (uint64_t)er[e], Mu, inv))));
       __syncthreads();
       for (int x = threadIdx.x; x < P * W; x += blockDim.x) {
         const int i = x % W, k = x / W;
         const int lo = max(boff[k], e0), hi = min(boff[k + 1], e1);
-        C4 sum = e0 == 0 ? zero4() : ld(tl[i * CS + k]);
-        for (int e = lo; e < hi; ++e)
-          sum = cadd(sum, cmul(ld(base[e - e0]), ld(n_stage > 0 ? es[e * W + i] : __ldg(estep + (int64_t)e * W + i))));
-        tl[i * CS + k] = st4(sum);
+        C sum = e0 == 0 ? A::zero() : A::ld(tl[i * CS + k]);
+        for (int e = lo; e < hi; ++e) {
+          const C st = n_stage > 0 ? A::ld(es[e * W + i]) : A::from_df(__ldg(estep + (int64_t)e * W + i));
+          sum = A::add(sum, A::mul(A::ld(base[e - e0]), st));
+        }
+        tl[i * CS + k] = A::st(sum);
       }
       __syncthreads();
       e0 += kPrChunk;
@@ -617,28 +658,28 @@ __global__ void __launch_bounds__(kPr16Threads, 2) k_pr_eval16(int64_t M, int64_
     // pass 1 (radix 16, Ns = 1): butterfly j of column c reads j + R2 r, writes 16 j + r
     {
       const int c = u % W, j = u / W;
-      float4* col = tl + c * CS;
-      C4 v[16];
+      V* col = tl + c * CS;
+      C v[16];
 #pragma unroll
-      for (int r = 0; r < 16; ++r) v[r] = ld(col[j + R2 * r]);
+      for (int r = 0; r < 16; ++r) v[r] = A::ld(col[j + R2 * r]);
       __syncthreads();
-      dft16<1>(v, w1, w2, w3);
+      A::template dft16<1>(v, w1, w2, w3);
 #pragma unroll
       for (int k1 = 0; k1 < 4; ++k1)
 #pragma unroll
-        for (int k2 = 0; k2 < 4; ++k2) col[16 * j + k1 + 4 * k2] = st4(v[4 * k1 + k2]);
+        for (int k2 = 0; k2 < 4; ++k2) col[16 * j + k1 + 4 * k2] = A::st(v[4 * k1 + k2]);
     }
     __syncthreads();
     // pass 2 straight to the samples s[q0 + c + Q p]
     {
       const int c = u % W, k = u / W;
       const int64_t q = q0 + c;
-      pr16_pass2<P, 1, false>(tl + c * CS, k, tw, w1, w2, w3, [&](int p, const C4 val) {
+      pr16_pass2<A, P, 1, false>(tl + c * CS, k, tw, w1, w2, w3, [&](int p, const C val) {
         if (q >= Q) return;
         if (OUT_REAL)
-          static_cast<double*>(out)[q + Q * p] = (double)val.re.hi + (double)val.re.lo;
+          static_cast<typename A::Real*>(out)[q + Q * p] = A::real_out(A::st(val));
         else
-          static_cast<float4*>(out)[q + Q * p] = st4(val);
+          static_cast<V*>(out)[q + Q * p] = A::st(val);
       });
     }
     __syncthreads();
@@ -647,24 +688,27 @@ __global__ void __launch_bounds__(kPr16Threads, 2) k_pr_eval16(int64_t M, int64_
 
 // Pruned forward transform with 4096-value tiles (see above); the Horner
 // phase as k_pr_fwd.
-template <int P, bool IN_REAL>
-__global__ void __launch_bounds__(kPr16Threads, 2) k_pr_fwd16(int64_t M, int64_t Q, const float4* __restrict__ t0,
+template <class A, int P, bool IN_REAL>
+__global__ void __launch_bounds__(kPr16Threads, A::kMinBlocks16) k_pr_fwd16(int64_t M, int64_t Q, const float4* __restrict__ t0,
                                                               const float4* __restrict__ t1, int b,
                                                               const void* __restrict__ in,
                                                               const int64_t* __restrict__ ob,
                                                               const int32_t* __restrict__ kout, int n_out,
                                                               const float4* __restrict__ oz, int64_t n_tiles,
-                                                              float4* __restrict__ partial) {
+                                                              typename A::V* __restrict__ partial) {
+  using V = typename A::V;
+  using C = typename A::C;
   constexpr int W = kPr16Tile / P, CS = P + 1, R2 = P / 16;
   extern __shared__ __align__(16) float4 sm4[];
-  float4* tl = sm4;
-  float4* tw = tl + W * CS;
-  float4* acc = tw + P;
+  V* tl = reinterpret_cast<V*>(sm4);
+  V* tw = tl + W * CS;
+  V* acc = tw + P;
   const uint64_t Mu = (uint64_t)M, inv = ~0ull / Mu;
-  for (int m = threadIdx.x; m < P; m += blockDim.x) tw[m] = st4(tw2<1>(t0, t1, b, (uint64_t)m * (uint64_t)Q));
-  for (int o = threadIdx.x; o < n_out; o += blockDim.x) acc[o] = st4(zero4());
+  for (int m = threadIdx.x; m < P; m += blockDim.x)
+    tw[m] = A::st(A::template root<1>(t0, t1, b, (uint64_t)m * (uint64_t)Q));
+  for (int o = threadIdx.x; o < n_out; o += blockDim.x) acc[o] = A::st(A::zero());
   __syncthreads();
-  const C4 w1 = ld(tw[P / 16]), w2 = ld(tw[2 * P / 16]), w3 = ld(tw[3 * P / 16]);
+  const C w1 = A::ld(tw[P / 16]), w2 = A::ld(tw[2 * P / 16]), w3 = A::ld(tw[3 * P / 16]);
   const int u = threadIdx.x;
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t q0 = tile * W;
@@ -673,36 +717,36 @@ __global__ void __launch_bounds__(kPr16Threads, 2) k_pr_fwd16(int64_t M, int64_t
     {
       const int c = u % W, j = u / W;
       const int64_t q = q0 + c;
-      C4 v[16];
+      C v[16];
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
         const int64_t p = j + R2 * r;
-        if (q >= Q) v[r] = zero4();
-        else if (IN_REAL) v[r] = C4{df_split(__ldg(static_cast<const double*>(in) + q + Q * p)), DF{0.f, 0.f}};
-        else v[r] = ld(__ldg(static_cast<const float4*>(in) + q + Q * p));
+        if (q >= Q) v[r] = A::zero();
+        else if (IN_REAL) v[r] = A::from_real(__ldg(static_cast<const typename A::Real*>(in) + q + Q * p));
+        else v[r] = A::ld(__ldg(static_cast<const V*>(in) + q + Q * p));
       }
-      dft16<-1>(v, w1, w2, w3);
-      float4* col = tl + c * CS;
+      A::template dft16<-1>(v, w1, w2, w3);
+      V* col = tl + c * CS;
 #pragma unroll
       for (int k1 = 0; k1 < 4; ++k1)
 #pragma unroll
-        for (int k2 = 0; k2 < 4; ++k2) col[16 * j + k1 + 4 * k2] = st4(v[4 * k1 + k2]);
+        for (int k2 = 0; k2 < 4; ++k2) col[16 * j + k1 + 4 * k2] = A::st(v[4 * k1 + k2]);
     }
     __syncthreads();
     {
       const int c = u % W, k = u / W;
-      float4* col = tl + c * CS;
-      pr16_pass2<P, -1, true>(col, k, tw, w1, w2, w3, [&](int p, const C4 val) { col[p] = st4(val); });
+      V* col = tl + c * CS;
+      pr16_pass2<A, P, -1, true>(col, k, tw, w1, w2, w3, [&](int p, const C val) { col[p] = A::st(val); });
     }
     __syncthreads();
     const int wl = Q - q0 < (int64_t)W ? (int)(Q - q0) : W;
     for (int o = threadIdx.x; o < n_out; o += blockDim.x) {
       const int k = kout[o];
-      const C4 w = tw2<-1>(t0, t1, b, mulmod((uint64_t)q0, (uint64_t)ob[o], Mu, inv));
-      const C4 z = ld(__ldg(oz + 2 * o));
-      C4 sum = ld(tl[(wl - 1) * CS + k]);
-      for (int i = wl - 2; i >= 0; --i) sum = cadd(cmul(sum, z), ld(tl[i * CS + k]));
-      acc[o] = st4(cadd(ld(acc[o]), cmul(sum, w)));
+      const C w = A::template root<-1>(t0, t1, b, mulmod((uint64_t)q0, (uint64_t)ob[o], Mu, inv));
+      const C z = A::from_df(__ldg(oz + 2 * o));
+      C sum = A::ld(tl[(wl - 1) * CS + k]);
+      for (int i = wl - 2; i >= 0; --i) sum = A::add(A::mul(sum, z), A::ld(tl[i * CS + k]));
+      acc[o] = A::st(A::add(A::ld(acc[o]), A::mul(sum, w)));
     }
     __syncthreads();
   }
@@ -767,44 +811,54 @@ ss_status launch_eval(const TwoLevelTable& T, const PrunedSplit& S, int wsh, con
   return SS_OK;
 }
 
-template <int P, bool OUT_REAL>
+template <class A, int P, bool OUT_REAL>
 ss_status launch_eval16(const TwoLevelTable& T, const PrunedSplit& S, const int64_t* er, const float4* ev,
                         const int32_t* boff, const float4* estep, int64_t n_stage, void* out, cudaStream_t st) {
   constexpr int W = kPr16Tile / P;
   const int64_t n_tiles = (S.Q + W - 1) / W;
-  const size_t smem = (size_t)(W * (P + 1) + P + kPrChunk + n_stage) * sizeof(float4) + (P + 1) * sizeof(int32_t);
+  const size_t smem =
+      (size_t)(W * (P + 1) + P + kPrChunk + n_stage) * sizeof(typename A::V) + (P + 1) * sizeof(int32_t);
   int grid = 0;
-  SS_TRY(grid_for(k_pr_eval16<P, OUT_REAL>, smem, n_tiles, &grid));
-  k_pr_eval16<P, OUT_REAL><<<grid, kPr16Threads, smem, st>>>(T.M, S.Q, T.t0.get(), T.t1.get(), T.b, er, ev, boff,
-                                                              estep, (int)n_stage, n_tiles, out);
+  SS_TRY(grid_for(k_pr_eval16<A, P, OUT_REAL>, smem, n_tiles, &grid));
+  k_pr_eval16<A, P, OUT_REAL><<<grid, kPr16Threads, smem, st>>>(T.M, S.Q, T.t0.get(), T.t1.get(), T.b, er, ev, boff,
+                                                                 estep, (int)n_stage, n_tiles, out);
   SS_LAUNCH_CHECK();
   return SS_OK;
 }
 
-template <bool IN_REAL>
+template <class A, bool OUT_REAL>
+ss_status launch_eval16_p(const TwoLevelTable& T, const PrunedSplit& S, const int64_t* er, const float4* ev,
+                          const int32_t* boff, const float4* estep, int64_t n_stage, void* out, cudaStream_t st) {
+  if (S.P == 256) return launch_eval16<A, 256, OUT_REAL>(T, S, er, ev, boff, estep, n_stage, out, st);
+  return launch_eval16<A, 128, OUT_REAL>(T, S, er, ev, boff, estep, n_stage, out, st);
+}
+
+template <class A, int P, bool IN_REAL>
 ss_status launch_fwd16(const TwoLevelTable& T, const PrunedSplit& S, const void* in, const int64_t* ob,
                        const int32_t* kout, int nc, const float4* oz, float4* X, cudaStream_t st) {
-  const int W = kPr16Tile / S.P;
+  constexpr int W = kPr16Tile / P;
   const int64_t n_tiles = (S.Q + W - 1) / W;
-  const size_t smem = (size_t)(W * (S.P + 1) + S.P + nc) * sizeof(float4);
+  const size_t smem = (size_t)(W * (P + 1) + P + nc) * sizeof(typename A::V);
   int grid = 0;
-  if (S.P == 256) SS_TRY(grid_for(k_pr_fwd16<256, IN_REAL>, smem, n_tiles, &grid));
-  else SS_TRY(grid_for(k_pr_fwd16<128, IN_REAL>, smem, n_tiles, &grid));
-  DevBuf<float4> partial;
+  SS_TRY(grid_for(k_pr_fwd16<A, P, IN_REAL>, smem, n_tiles, &grid));
+  DevBuf<typename A::V> partial;
   SS_TRY(partial.alloc_tmp((size_t)grid * nc, st));
   {
     ProfScope prof_("k_pr_fwd", st, true);
-    if (S.P == 256)
-      k_pr_fwd16<256, IN_REAL><<<grid, kPr16Threads, smem, st>>>(T.M, S.Q, T.t0.get(), T.t1.get(), T.b, in, ob, kout,
-                                                                  nc, oz, n_tiles, partial.get());
-    else
-      k_pr_fwd16<128, IN_REAL><<<grid, kPr16Threads, smem, st>>>(T.M, S.Q, T.t0.get(), T.t1.get(), T.b, in, ob, kout,
-                                                                  nc, oz, n_tiles, partial.get());
+    k_pr_fwd16<A, P, IN_REAL><<<grid, kPr16Threads, smem, st>>>(T.M, S.Q, T.t0.get(), T.t1.get(), T.b, in, ob, kout,
+                                                                 nc, oz, n_tiles, partial.get());
     SS_LAUNCH_CHECK();
   }
-  k_pr_reduce<ArDF><<<nblk((int64_t)nc * 32), 256, 0, st>>>(partial.get(), grid, nc, X);
+  k_pr_reduce<A><<<nblk((int64_t)nc * 32), 256, 0, st>>>(partial.get(), grid, nc, X);
   SS_LAUNCH_CHECK();
   return SS_OK;
+}
+
+template <class A, bool IN_REAL>
+ss_status launch_fwd16_p(const TwoLevelTable& T, const PrunedSplit& S, const void* in, const int64_t* ob,
+                         const int32_t* kout, int nc, const float4* oz, float4* X, cudaStream_t st) {
+  if (S.P == 256) return launch_fwd16<A, 256, IN_REAL>(T, S, in, ob, kout, nc, oz, X, st);
+  return launch_fwd16<A, 128, IN_REAL>(T, S, in, ob, kout, nc, oz, X, st);
 }
 
 template <class A, bool IN_REAL>
@@ -883,9 +937,8 @@ ss_status pruned_eval_pair(const TwoLevelTable& T, const int64_t* qa, const doub
   PrunedSplit S;
   if (!pruned_split(M, ne_max, &S, kPrEvalTile))
     SS_FAIL(SS_ERR_INVALID, "pruned evaluation: M = %lld has no split", (long long)M);
-  // double-float sums with P = 128 or 256: 4096-value tiles (k_pr_eval16)
-  const bool df = fmt == PrunedFormat::kDfComplex || fmt == PrunedFormat::kF64Real;
-  const bool t16 = df && pr16_supported(S.P);
+  // P = 128 or 256: 4096-value tiles (k_pr_eval16)
+  const bool t16 = pr16_supported(S.P);
   const int Wt = t16 ? kPr16Tile / S.P : S.W;
   DevBuf<int64_t> er;
   DevBuf<float4> ev, estep;
@@ -915,12 +968,16 @@ ss_status pruned_eval_pair(const TwoLevelTable& T, const int64_t* qa, const doub
   const int64_t n_stage = ne_max * Wt <= kPrEvalStage ? ne_max * Wt : 0;
   ProfScope prof_("k_pr_eval", st, true);
   if (t16) {
-    const bool real = fmt == PrunedFormat::kF64Real;
-    if (S.P == 256)
-      return real ? launch_eval16<256, true>(T, S, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st)
-                  : launch_eval16<256, false>(T, S, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st);
-    return real ? launch_eval16<128, true>(T, S, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st)
-                : launch_eval16<128, false>(T, S, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st);
+    switch (fmt) {
+      case PrunedFormat::kDfComplex:
+        return launch_eval16_p<ArDF, false>(T, S, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st);
+      case PrunedFormat::kF64Real:
+        return launch_eval16_p<ArDF, true>(T, S, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st);
+      case PrunedFormat::kF32Complex:
+        return launch_eval16_p<ArF32, false>(T, S, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st);
+      default:
+        return launch_eval16_p<ArF32, true>(T, S, er.get(), ev.get(), boff.get(), estep.get(), n_stage, out, st);
+    }
   }
   switch (fmt) {
     case PrunedFormat::kDfComplex:
@@ -954,21 +1011,23 @@ ss_status pruned_forward(const TwoLevelTable& T, const void* s, PrunedFormat fmt
                                                           oz.get());
     SS_LAUNCH_CHECK();
     const float4* z = oz.get() + 1;
-    const bool t16 = pr16_supported(S.P);   // double-float formats: 4096-value tiles
+    const bool t16 = pr16_supported(S.P);   // 4096-value tiles
     switch (fmt) {
       case PrunedFormat::kDfComplex:
-        if (t16) SS_TRY((launch_fwd16<false>(T, S, s, bins + o0, kout.get(), nc, z, X + o0, st)));
+        if (t16) SS_TRY((launch_fwd16_p<ArDF, false>(T, S, s, bins + o0, kout.get(), nc, z, X + o0, st)));
         else SS_TRY((launch_fwd<ArDF, false>(T, S, wsh, s, bins + o0, kout.get(), nc, z, X + o0, st)));
         break;
       case PrunedFormat::kF64Real:
-        if (t16) SS_TRY((launch_fwd16<true>(T, S, s, bins + o0, kout.get(), nc, z, X + o0, st)));
+        if (t16) SS_TRY((launch_fwd16_p<ArDF, true>(T, S, s, bins + o0, kout.get(), nc, z, X + o0, st)));
         else SS_TRY((launch_fwd<ArDF, true>(T, S, wsh, s, bins + o0, kout.get(), nc, z, X + o0, st)));
         break;
       case PrunedFormat::kF32Complex:
-        SS_TRY((launch_fwd<ArF32, false>(T, S, wsh, s, bins + o0, kout.get(), nc, z, X + o0, st)));
+        if (t16) SS_TRY((launch_fwd16_p<ArF32, false>(T, S, s, bins + o0, kout.get(), nc, z, X + o0, st)));
+        else SS_TRY((launch_fwd<ArF32, false>(T, S, wsh, s, bins + o0, kout.get(), nc, z, X + o0, st)));
         break;
       default:
-        SS_TRY((launch_fwd<ArF32, true>(T, S, wsh, s, bins + o0, kout.get(), nc, z, X + o0, st)));
+        if (t16) SS_TRY((launch_fwd16_p<ArF32, true>(T, S, s, bins + o0, kout.get(), nc, z, X + o0, st)));
+        else SS_TRY((launch_fwd<ArF32, true>(T, S, wsh, s, bins + o0, kout.get(), nc, z, X + o0, st)));
         break;
     }
   }
