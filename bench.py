@@ -246,12 +246,12 @@ def pruned_instr(kind, M, n_split, n_work):
 _PR_SOURCES = ["paper_2302_00752_gb300/csrc/fft_pruned.cu", "paper_2302_00752_gb300/csrc/dfc.cuh",
                "paper_2302_00752_gb300/csrc/df.cuh"]
 KERNEL_TRAFFIC = {
-    "k_pr_eval": {"sources": _PR_SOURCES, "source_sha16": "3bd76de49a76a96d", "dram_bytes_per_launch": 648.81e6,
-                  "note": "ncu capture at M = 2^23 (81.10 MB) scaled by the tiles to M = 2^26 (x8); the capture "
+    "k_pr_eval": {"sources": _PR_SOURCES, "source_sha16": "9dba2b952b8e144a", "dram_bytes_per_launch": 583.52e6,
+                  "note": "ncu capture at M = 2^23 (72.94 MB) scaled by the tiles to M = 2^26 (x8); the capture "
                           "misses the output lines still dirty in L2 when the kernel ends (algorithmic write "
                           "1.07 GB at 2^26); profiles/k_pr_eval_fwd_cfg5_M2e23.md"},
-    "k_pr_fwd": {"sources": _PR_SOURCES, "source_sha16": "3bd76de49a76a96d", "dram_bytes_per_launch": 1157.3e6,
-                 "note": "ncu capture at M = 2^23 (144.66 MB) scaled by the tiles to M = 2^26 (x8); "
+    "k_pr_fwd": {"sources": _PR_SOURCES, "source_sha16": "9dba2b952b8e144a", "dram_bytes_per_launch": 1099.48e6,
+                 "note": "ncu capture at M = 2^23 (137.43 MB) scaled by the tiles to M = 2^26 (x8); "
                          "profiles/k_pr_eval_fwd_cfg5_M2e23.md"},
     "k_neighbors": {"sources": ["paper_2302_00752_gb300/csrc/stamp.cu", "paper_2302_00752_gb300/csrc/keys.cuh"],
                     "source_sha16": "e28d2e437c112942", "dram_bytes_per_launch": 958.17e6,
