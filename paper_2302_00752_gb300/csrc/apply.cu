@@ -13,7 +13,7 @@ namespace {
 
 __global__ void k_pack64(const double2* __restrict__ u, int64_t size, double2* rec) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < size) rec[2 * i] = u[i];
+  if (i < size) rec[i] = u[i];
 }
 
 __global__ void __launch_bounds__(256) k_apply64(OpView op, int64_t size, int64_t rows_pad,
@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(256) k_apply64(OpView op, int64_t size, int64_
   const int64_t s = row / kSlice;
   const int lane = (int)(row % kSlice);
   double2 acc = row_apply64(op, s, lane, rec);
-  if (row == zero_idx) acc = rec[2 * row];
+  if (row == zero_idx) acc = rec[row];
   if (row < size) y[row] = acc;
 }
 
@@ -48,7 +48,7 @@ inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t
 // u on the first n_u rows (a solution on S^N is the prefix of S^{N+L}), zero after.
 __global__ void k_pack64_prefix(const double2* __restrict__ u, int64_t n_u, int64_t size, double2* rec) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < size) rec[2 * i] = i < n_u ? u[i] : make_double2(0.0, 0.0);
+  if (i < size) rec[i] = i < n_u ? u[i] : make_double2(0.0, 0.0);
 }
 
 constexpr int kNormThreads = 256;

@@ -79,7 +79,7 @@ __device__ __forceinline__ double2 row_apply64_t(const OpView& op, int64_t s, in
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      v[q] = ldv<CG>(rec + 2 * (int64_t)(ee[q] & op.colmask));
+      v[q] = ldv<CG>(rec + (ee[q] & op.colmask));
       v[q].y = conj_if(v[q].y, op.conj, ee[q]);
     }
 #pragma unroll
@@ -95,7 +95,7 @@ __device__ __forceinline__ double2 row_apply64_t(const OpView& op, int64_t s, in
   }
   for (; t < w; ++t) {
     const uint32_t ee = __ldg(e + (int64_t)t * kSlice);
-    double2 v = ldv<CG>(rec + 2 * (int64_t)(ee & op.colmask));
+    double2 v = ldv<CG>(rec + (ee & op.colmask));
     v.y = conj_if(v.y, op.conj, ee);
     if constexpr (REAL) {
       const double c = __ldg(cfr + (int64_t)t * kSlice);

@@ -288,7 +288,7 @@ __device__ __forceinline__ double2 f_at(const SolveInst& in, int64_t g) {
 
 __device__ __forceinline__ double2 apply64_row(const SolveParams& P, const SolveInst& in, int64_t s, int lane,
                                                int64_t g, const double2* rec) {
-  if (g == in.zero_row) return __ldcg(rec + 2 * g);
+  if (g == in.zero_row) return __ldcg(rec + g);
   return row_apply64<true>(P.op, s, lane, rec);
 }
 
@@ -348,8 +348,8 @@ __device__ void solve_fp64(const SolveParams& P, Smem& sm) {
     const double rD = 1.0 / jacobi(P, in, g);
     P.rdiag[g] = rD;
     P.r[g] = f;
-    P.xrec[2 * g] = make_double2(0.0, 0.0);
-    P.urec64[2 * g] = make_double2(f.x * rD, f.y * rD);
+    P.xrec[g] = make_double2(0.0, 0.0);
+    P.urec64[g] = make_double2(f.x * rD, f.y * rD);
     P.pd[g] = make_double2(0.0, 0.0);
     P.sd[g] = make_double2(0.0, 0.0);
     v[3] = f.x * f.x + f.y * f.y;
@@ -362,7 +362,7 @@ __device__ void solve_fp64(const SolveParams& P, Smem& sm) {
       if (!sm.flag[k]) return;
       const SolveInst& in = P.inst[i];
       const double2 w = apply64_row(P, in, s, lane, g, P.urec64);
-      const double2 u = P.urec64[2 * g], r = P.r[g];
+      const double2 u = P.urec64[g], r = P.r[g];
       P.w64[g] = w;
       v[0] = r.x * u.x + r.y * u.y;
       v[1] = w.x * u.x + w.y * u.y;
@@ -410,8 +410,8 @@ __device__ void solve_fp64(const SolveParams& P, Smem& sm) {
       if (!sm.flag[k]) return;
       const SolveInst& in = P.inst[i];
       const double a = sm.ca[k], b = sm.cb[k];
-      const double2 u = P.urec64[2 * g], w = P.w64[g];
-      double2 p = P.pd[g], sv = P.sd[g], x = P.xrec[2 * g], r = P.r[g];
+      const double2 u = P.urec64[g], w = P.w64[g];
+      double2 p = P.pd[g], sv = P.sd[g], x = P.xrec[g], r = P.r[g];
       p.x = u.x + b * p.x; p.y = u.y + b * p.y;
       sv.x = w.x + b * sv.x; sv.y = w.y + b * sv.y;
       x.x += a * p.x; x.y += a * p.y;
@@ -419,9 +419,9 @@ __device__ void solve_fp64(const SolveParams& P, Smem& sm) {
       const double rD = P.rdiag[g];
       P.pd[g] = p;
       P.sd[g] = sv;
-      P.xrec[2 * g] = x;
+      P.xrec[g] = x;
       P.r[g] = r;
-      P.urec64[2 * g] = make_double2(r.x * rD, r.y * rD);
+      P.urec64[g] = make_double2(r.x * rD, r.y * rD);
     });
     if (!grid_sync(P)) return;
     if (block_counter(P, 0) >= P.n_inst) break;
@@ -436,7 +436,7 @@ __device__ void solve_fp64(const SolveParams& P, Smem& sm) {
     const double2 r = make_double2(f.x - y.x, f.y - y.y);
     v[2] = r.x * r.x + r.y * r.y;
     const int64_t l = g - in.row0;
-    if (l < in.rows) in.u[l] = P.xrec[2 * g];
+    if (l < in.rows) in.u[l] = P.xrec[g];
   });
   if (!grid_sync(P)) return;
   run_phase(P, sm, 0u, [&](int, const Chunk&, int, int i, bool owner, int lane) {
@@ -601,7 +601,7 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
   // x = 0; |f|^2
   run_phase(P, sm, 0b1000u, noscal, [&](int64_t g, int64_t, int, int i, int, double* v) {
     const double2 f = f_at(P.inst[i], g);
-    P.xrec[2 * g] = make_double2(0.0, 0.0);
+    P.xrec[g] = make_double2(0.0, 0.0);
     v[3] = f.x * f.x + f.y * f.y;
   });
   if (!grid_sync(P)) return;
@@ -760,19 +760,19 @@ __device__ void solve_refined(const SolveParams& P, Smem& sm) {
       }
     }, [&](int64_t g, int64_t, int, int, int k, double*) {
       if (!sm.flag[k]) return;
-      double2 x = P.xrec[2 * g];
+      double2 x = P.xrec[g];
       const float2 dl = P.d32[g];
       const double us = sm.ca[k];
       x.x += (double)dl.x * us;
       x.y += (double)dl.y * us;
-      P.xrec[2 * g] = x;
+      P.xrec[g] = x;
     });
     if (!grid_sync(P)) return;
   }
   run_phase(P, sm, 0u, noscal, [&](int64_t g, int64_t, int, int i, int, double*) {
     const SolveInst& in = P.inst[i];
     const int64_t l = g - in.row0;
-    if (l < in.rows) in.u[l] = P.xrec[2 * g];
+    if (l < in.rows) in.u[l] = P.xrec[g];
   });
 }
 
@@ -817,7 +817,7 @@ __device__ void solve_bicgstab(const SolveParams& P, Smem& sm) {
   // and a slot left out would hold whatever an earlier phase or solve left there.
   run_phase(P, sm, 0b1111u, noscal, [&](int64_t g, int64_t, int, int i, int, double* v) {
     const double2 f = f_at(P.inst[i], g);
-    P.xrec[2 * g] = make_double2(0.0, 0.0);
+    P.xrec[g] = make_double2(0.0, 0.0);
     P.r[g] = f;
     P.rhat[g] = f;
     P.pd[g] = make_double2(0.0, 0.0);
@@ -877,7 +877,7 @@ __device__ void solve_bicgstab(const SolveParams& P, Smem& sm) {
       const double2 q = make_double2(p.x - (om.x * v.x - om.y * v.y), p.y - (om.x * v.y + om.y * v.x));
       p = make_double2(r.x + (beta.x * q.x - beta.y * q.y), r.y + (beta.x * q.y + beta.y * q.x));
       P.pd[g] = p;
-      P.urec64[2 * g] = cmul(P.dlt[g], p);
+      P.urec64[g] = cmul(P.dlt[g], p);
     });
     if (!grid_sync(P)) return;
     if (block_counter(P, 0) >= P.n_inst) break;
@@ -911,15 +911,15 @@ __device__ void solve_bicgstab(const SolveParams& P, Smem& sm) {
     }, [&](int64_t g, int64_t, int, int, int k, double* vq) {
       if (!sm.flag[k]) return;
       const double2 alpha = make_double2(sm.ca[k], sm.cb[k]);
-      const double2 r = P.r[g], v = P.w64[g], y = P.urec64[2 * g];
+      const double2 r = P.r[g], v = P.w64[g], y = P.urec64[g];
       const double2 av = cmul(alpha, v), ay = cmul(alpha, y);
       const double2 s = make_double2(r.x - av.x, r.y - av.y);
-      double2 x = P.xrec[2 * g];
+      double2 x = P.xrec[g];
       x.x += ay.x;
       x.y += ay.y;
-      P.xrec[2 * g] = x;
+      P.xrec[g] = x;
       P.sd[g] = s;
-      P.zrec[2 * g] = cmul(P.dlt[g], s);
+      P.zrec[g] = cmul(P.dlt[g], s);
       vq[2] = s.x * s.x + s.y * s.y;
     });
     if (!grid_sync(P)) return;
@@ -969,12 +969,12 @@ __device__ void solve_bicgstab(const SolveParams& P, Smem& sm) {
     }, [&](int64_t g, int64_t, int, int, int k, double* v) {
       if (!sm.flag[k]) return;
       const double2 om = make_double2(sm.ca[k], sm.cb[k]);
-      const double2 s = P.sd[g], t = P.tv[g], z = P.zrec[2 * g];
+      const double2 s = P.sd[g], t = P.tv[g], z = P.zrec[g];
       const double2 oz = cmul(om, z), ot = cmul(om, t);
-      double2 x = P.xrec[2 * g];
+      double2 x = P.xrec[g];
       x.x += oz.x;
       x.y += oz.y;
-      P.xrec[2 * g] = x;
+      P.xrec[g] = x;
       const double2 r = make_double2(s.x - ot.x, s.y - ot.y);
       P.r[g] = r;
       const double2 q = cdot(P.rhat[g], r);
@@ -992,7 +992,7 @@ __device__ void solve_bicgstab(const SolveParams& P, Smem& sm) {
     const double2 r = make_double2(f.x - y.x, f.y - y.y);
     v[2] = r.x * r.x + r.y * r.y;
     const int64_t l = g - in.row0;
-    if (l < in.rows) in.u[l] = P.xrec[2 * g];
+    if (l < in.rows) in.u[l] = P.xrec[g];
   });
   if (!grid_sync(P)) return;
   run_phase(P, sm, 0u, [&](int, const Chunk&, int, int i, bool owner, int lane) {
@@ -1020,11 +1020,8 @@ __global__ void k_init_solve_records(const int64_t* __restrict__ norm, int64_t n
   if (g >= n) return;
   const int64_t nr = norm[g];
   const bool wd = wide_rows ? wide_rows[g] != 0 : wide;
-  const double2 nb = make_double2(__longlong_as_double((long long)nr), 0.0);
-  xrec[2 * g] = make_double2(0.0, 0.0);
-  xrec[2 * g + 1] = nb;
-  prec64[2 * g] = make_double2(0.0, 0.0);
-  prec64[2 * g + 1] = nb;
+  xrec[g] = make_double2(0.0, 0.0);
+  prec64[g] = make_double2(0.0, 0.0);
   prec32[g] = make_float4(0.f, 0.f, __int_as_float(norm_word(nr, wd)), 0.f);
 }
 
@@ -1112,8 +1109,8 @@ ss_status work_alloc(SolveWork& W, int64_t rows_total, const int64_t* norm, cons
   W.rows_total = rows_total;
   W.cap_rows = rows_total;
   W.df_rows = W.bi_rows = -1;
-  SS_TRY(W.xrec.alloc(2 * rows_total, st));
-  SS_TRY(W.urec64.alloc(2 * rows_total, st));
+  SS_TRY(W.xrec.alloc(rows_total, st));
+  SS_TRY(W.urec64.alloc(rows_total, st));
   SS_TRY(W.urec32.alloc(rows_total, st));
   SS_TRY(W.r.alloc(rows_total, st));
   SS_TRY(W.w64.alloc(rows_total, st));
@@ -1144,18 +1141,17 @@ ss_status work_alloc(SolveWork& W, int64_t rows_total, const int64_t* norm, cons
 }
 
 ss_status work_alloc_bicgstab(SolveWork& W, cudaStream_t st) {
-  if (W.zrec.n >= (size_t)(2 * W.rows_total) && W.tv.n >= (size_t)W.rows_total) {
-    if (W.bi_rows != W.rows_total) {   // the dummy record of this row count must read as zero
-      SS_CUDA(cudaMemsetAsync(W.zrec.get() + 2 * (W.rows_total - 1), 0, 2 * sizeof(double2), st));
+  if (W.zrec.n >= (size_t)W.rows_total && W.tv.n >= (size_t)W.rows_total) {
+    if (W.bi_rows != W.rows_total) {   // the dummy row of this row count must read as zero
+      SS_CUDA(cudaMemsetAsync(W.zrec.get() + (W.rows_total - 1), 0, sizeof(double2), st));
       W.bi_rows = W.rows_total;
     }
     return SS_OK;
   }
   W.bi_rows = W.rows_total;
-  SS_TRY(W.zrec.alloc(2 * W.rows_total, st));
+  SS_TRY(W.zrec.alloc(W.rows_total, st));
   SS_TRY(W.tv.alloc(W.rows_total, st));
-  // the odd halves of the z records are never read by the FP64 operator
-  SS_CUDA(cudaMemsetAsync(W.zrec.get(), 0, 2 * W.rows_total * sizeof(double2), st));
+  SS_CUDA(cudaMemsetAsync(W.zrec.get(), 0, W.rows_total * sizeof(double2), st));
   SS_CUDA(cudaStreamSynchronize(st));
   W.zrec.settle();
   W.tv.settle();

@@ -45,8 +45,8 @@ struct SolveParams {
   const double2* ca64;
   const float2* ca32;
   const int32_t* pn;           // FP32 norm words of |p_j|^2
-  double2* xrec;               // FP64 records (value, norm) of x: gathered for f - L x
-  double2* urec64;             // FP64 records of u = D^-1 r: gathered by the FP64 operator
+  double2* xrec;               // FP64 values of x: gathered for f - L x
+  double2* urec64;             // FP64 values of u = D^-1 r: gathered by the FP64 operator
   float4* urec32;              // FP32 records of u: gathered by the FP32 operator
   double2* r;
   double2* w64;                // L u (FP64 mode)

@@ -244,7 +244,7 @@ struct ss_stamp_s {
   ss::DevBuf<float4> ecoefdf;         // [n_ent + 1] the same as double-float, built on first DF64 solve
   ss::DevBuf<int32_t> nw32;           // [rows_pad + 1] FP32 norm words of |k|^2 (norm_word; 0 on padding)
   // scratch for galerkin_apply (FP64)
-  ss::DevBuf<double2> rec64;          // [2 * (rows_pad + 1)] (value, norm|pad) pairs
+  ss::DevBuf<double2> rec64;          // [rows_pad + 1] FP64 values gathered by the FP64 operator
   // build state kept for stamp_extend
   int maxabs_f = 0, maxabs_a = 0;     // largest |coordinate| of F and of supp a_hat
   // operator of Remark ADR (advection b.grad u and reaction c u added; not

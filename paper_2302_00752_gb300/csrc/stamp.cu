@@ -718,8 +718,7 @@ __global__ void k_init_records(const int64_t* __restrict__ norm, int64_t n, bool
   if (i >= n) return;
   const int64_t nr = norm[i];
   nw32[i] = norm_word(nr, wide);
-  rec64[2 * i] = make_double2(0.0, 0.0);
-  rec64[2 * i + 1] = make_double2(__longlong_as_double((long long)nr), 0.0);
+  rec64[i] = make_double2(0.0, 0.0);
 }
 
 template <int WT>
@@ -1263,7 +1262,7 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   }
   SS_LAUNCH_CHECK();
   SS_TRY(S->nw32.alloc(S->rows_pad + 1, st));
-  SS_TRY(S->rec64.alloc(2 * (S->rows_pad + 1), st));
+  SS_TRY(S->rec64.alloc(S->rows_pad + 1, st));
   k_init_records<<<nblk(S->rows_pad + 1), 256, 0, st>>>(S->norm.get(), S->rows_pad + 1, S->wide, S->nw32.get(),
                                                         S->rec64.get());
   SS_LAUNCH_CHECK();
