@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <mutex>
 #include <cmath>
+#include <type_traits>
 
 #include "solve.cuh"
 
@@ -1109,24 +1110,28 @@ ss_status work_alloc(SolveWork& W, int64_t rows_total, const int64_t* norm, cons
   W.rows_total = rows_total;
   W.cap_rows = rows_total;
   W.df_rows = W.bi_rows = -1;
-  SS_TRY(W.xrec.alloc(rows_total, st));
-  SS_TRY(W.urec64.alloc(rows_total, st));
-  SS_TRY(W.urec32.alloc(rows_total, st));
-  SS_TRY(W.r.alloc(rows_total, st));
-  SS_TRY(W.w64.alloc(rows_total, st));
-  SS_TRY(W.w32.alloc(rows_total, st));
-  SS_TRY(W.pd.alloc(rows_total, st));
-  SS_TRY(W.sd.alloc(rows_total, st));
-  SS_TRY(W.rhat.alloc(rows_total, st));
-  SS_TRY(W.dlt.alloc(rows_total, st));
-  SS_TRY(W.r32.alloc(rows_total, st));
-  SS_TRY(W.p32.alloc(rows_total, st));
-  SS_TRY(W.s32.alloc(rows_total, st));
-  SS_TRY(W.d32.alloc(rows_total, st));
-  SS_TRY(W.rdiag.alloc(rows_total, st));
-  SS_TRY(W.bar.alloc(2, st));
-  SS_TRY(W.counters.alloc(4, st));
-  SS_TRY(W.err.alloc(1, st));
+  {
+    // one allocation, carved in 256-byte aligned pieces
+    size_t off = 0;
+    auto take = [&](auto& view, size_t count) {
+      using T = typename std::remove_pointer<decltype(view.p)>::type;
+      view.p = reinterpret_cast<T*>(off);   // offset for now, rebased below
+      off += (count * sizeof(T) + 255) / 256 * 256;
+    };
+    const size_t n = (size_t)rows_total;
+    take(W.xrec, n); take(W.urec64, n); take(W.urec32, n); take(W.r, n); take(W.w64, n); take(W.w32, n);
+    take(W.pd, n); take(W.sd, n); take(W.rhat, n); take(W.dlt, n); take(W.r32, n); take(W.p32, n);
+    take(W.s32, n); take(W.d32, n); take(W.rdiag, n); take(W.bar, 2); take(W.counters, 4); take(W.err, 1);
+    SS_TRY(W.arena.alloc(off, st));
+    const uintptr_t b = reinterpret_cast<uintptr_t>(W.arena.get());
+    auto rebase = [&](auto& view) {
+      using T = typename std::remove_pointer<decltype(view.p)>::type;
+      view.p = reinterpret_cast<T*>(b + reinterpret_cast<uintptr_t>(view.p));
+    };
+    rebase(W.xrec); rebase(W.urec64); rebase(W.urec32); rebase(W.r); rebase(W.w64); rebase(W.w32);
+    rebase(W.pd); rebase(W.sd); rebase(W.rhat); rebase(W.dlt); rebase(W.r32); rebase(W.p32);
+    rebase(W.s32); rebase(W.d32); rebase(W.rdiag); rebase(W.bar); rebase(W.counters); rebase(W.err);
+  }
   k_init_solve_records<<<nblk(rows_total), 256, 0, st>>>(norm, rows_total, wide_rows, wide, W.xrec.get(),
                                                          W.urec64.get(), W.urec32.get());
   SS_LAUNCH_CHECK();
@@ -1134,9 +1139,7 @@ ss_status work_alloc(SolveWork& W, int64_t rows_total, const int64_t* norm, cons
   // callers synchronise `st` before they return (solve when it reads the
   // statistics, batch_create right after this), which orders those calls
   // after these allocations.
-  W.xrec.settle(); W.urec64.settle(); W.urec32.settle(); W.r.settle(); W.w64.settle(); W.w32.settle();
-  W.pd.settle(); W.sd.settle(); W.rhat.settle(); W.dlt.settle(); W.bar.settle(); W.counters.settle();
-  W.err.settle(); W.r32.settle(); W.p32.settle(); W.s32.settle(); W.d32.settle(); W.rdiag.settle();
+  W.arena.settle();
   return SS_OK;
 }
 

@@ -95,15 +95,24 @@ struct SolveWork {
     if (ev[0]) cudaEventDestroy(ev[0]);
     if (ev[1]) cudaEventDestroy(ev[1]);
   }
-  DevBuf<double2> xrec, urec64, r, w64, pd, sd, rhat, dlt;
+  // the per-row vectors and the barrier / counter / error words: views of
+  // one arena (one allocation per workspace)
+  template <typename T>
+  struct View {
+    T* p = nullptr;
+    T* get() const { return p; }
+    void settle() {}
+  };
+  DevBuf<unsigned char> arena;
+  View<double2> xrec, urec64, r, w64, pd, sd, rhat, dlt;
   DevBuf<double2> zrec, tv;                // BiCGStab only (allocated on first use)
   DevBuf<float4> xdf, udf;                 // DF64 CG only (allocated on first use)
-  DevBuf<float4> urec32;
-  DevBuf<float2> w32, r32, p32, s32, d32;
-  DevBuf<double> rdiag;
+  View<float4> urec32;
+  View<float2> w32, r32, p32, s32, d32;
+  View<double> rdiag;
   DevBuf<double> part;
-  DevBuf<unsigned> bar;
-  DevBuf<int> counters, err;
+  View<unsigned> bar;
+  View<int> counters, err;
   DevBuf<InstState> state;
   DevBuf<SolveInst> inst;
   DevBuf<Chunk> chunk;

@@ -229,6 +229,70 @@ __global__ void k_steps(KeyParams P, const int32_t* __restrict__ A, const double
   ca32[j] = make_float2((float)(kTwoPiSq * a.x), (float)(kTwoPiSq * a.y));
 }
 
+// Warp-cooperative packing for wide rows (d > 16): lane l takes coordinates
+// c = l, l + 32, ... and ORs its fields into the warp's words in shared memory
+// (the fields do not overlap); returns whether every coordinate fits, and the
+// row's |k|^2 (both to every lane).  Lanes w < WT then read word w.
+constexpr int kPackWarps = 8;
+
+template <int WT>
+__device__ __forceinline__ bool warp_pack(const int32_t* __restrict__ k, const KeyParams& P, unsigned long long* words,
+                                          int64_t* norm2) {
+  const int lane = threadIdx.x & 31;
+  if (lane < WT) words[lane] = 0ull;
+  __syncwarp();
+  bool ok = true;
+  int64_t n2 = 0;
+  for (int c = lane; c < P.d; c += 32) {
+    const int64_t kc = k[c];
+    n2 += kc * kc;
+    const int64_t v = kc + P.bias_val;
+    ok &= (v >= 0) && (v <= (int64_t)P.fieldmask);
+    const int wd = c / P.fpw, sh = 64 - P.fb * (c % P.fpw + 1);
+    atomicOr(words + wd, (unsigned long long)(((uint64_t)v & P.fieldmask) << sh));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+  __syncwarp();
+  *norm2 = n2;
+  return __all_sync(0xffffffffu, ok);
+}
+
+// The linear form of the packed words held by lanes w < WT (sum mod 2^64).
+template <int WT>
+__device__ __forceinline__ uint64_t warp_lin(uint64_t word) {
+  const int lane = threadIdx.x & 31;
+  uint64_t lin = lane < WT ? key_lin_coef(lane) * word : 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lin += __shfl_xor_sync(0xffffffffu, lin, o);
+  return lin;
+}
+
+// k_steps with one warp per step (d > 16).
+template <int WT>
+__global__ void __launch_bounds__(32 * kPackWarps) k_steps_warp(KeyParams P, const int32_t* __restrict__ A,
+                                                                const double2* __restrict__ av, int s_a,
+                                                                uint64_t* stepkey, uint64_t* stepg, int64_t* pnorm,
+                                                                int32_t* pn32, bool wide, double2* ca64,
+                                                                float2* ca32) {
+  __shared__ unsigned long long s_w[kPackWarps][WT];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j = blockIdx.x * kPackWarps + w;
+  if (j >= s_a) return;   // warp-uniform
+  int64_t n2 = 0;
+  warp_pack<WT>(A + (int64_t)j * P.d, P, s_w[w], &n2);
+  const uint64_t kw = lane < WT ? (uint64_t)s_w[w][lane] : 0ull;
+  if (lane < WT) stepkey[(int64_t)j * WT + lane] = kw;
+  const uint64_t lin = warp_lin<WT>(kw);
+  if (lane != 0) return;
+  stepg[j] = lin - P.lin_bias;   // key_lin(k + p_j - bias) = key_lin(k) + stepg[j]
+  pnorm[j] = n2;
+  pn32[j] = norm_word(n2, wide);
+  const double2 a = av[j];
+  ca64[j] = make_double2(kTwoPiSq * a.x, kTwoPiSq * a.y);
+  ca32[j] = make_float2((float)(kTwoPiSq * a.x), (float)(kTwoPiSq * a.y));
+}
+
 // Insert a finalised key (hash hh) with value idx (no duplicates present).
 __device__ bool table_insert_final(uint64_t* table, uint64_t capmask, uint64_t hh, uint64_t idx) {
   const uint64_t word = slot_word(slot_fp(hh), idx);
@@ -257,6 +321,29 @@ __global__ void k_level0(KeyParams P, const int32_t* __restrict__ F, int64_t n_f
   level[i] = 0;
   norm[i] = key_norm<WT>(k, P);
   if (norm[i] == 0) *zero_idx = i;   // only when 0 is in F (allowed for the ADR operator)
+  if (!table_insert_final(table, capmask, hash_of_lin(lin), (uint64_t)i)) atomicExch(err, SS_ERR_HASH_FULL);
+}
+
+// k_level0 with one warp per row (d > 16).
+template <int WT>
+__global__ void __launch_bounds__(32 * kPackWarps) k_level0_warp(KeyParams P, const int32_t* __restrict__ F,
+                                                                 int64_t n_f, uint64_t* keys, uint64_t* hl,
+                                                                 int8_t* level, int64_t* norm, uint64_t* table,
+                                                                 uint64_t capmask, int32_t* err, int64_t* zero_idx) {
+  __shared__ unsigned long long s_w[kPackWarps][WT];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * kPackWarps + w;
+  if (i >= n_f) return;   // warp-uniform
+  int64_t n2 = 0;
+  warp_pack<WT>(F + i * P.d, P, s_w[w], &n2);
+  const uint64_t kw = lane < WT ? (uint64_t)s_w[w][lane] : 0ull;
+  if (lane < WT) keys[i * WT + lane] = kw;
+  const uint64_t lin = warp_lin<WT>(kw);
+  if (lane != 0) return;
+  hl[i] = lin;
+  level[i] = 0;
+  norm[i] = n2;
+  if (n2 == 0) *zero_idx = i;   // only when 0 is in F (allowed for the ADR operator)
   if (!table_insert_final(table, capmask, hash_of_lin(lin), (uint64_t)i)) atomicExch(err, SS_ERR_HASH_FULL);
 }
 
@@ -821,6 +908,21 @@ uint64_t next_pow2(uint64_t x) {
 // Slot bound of the hash tables built from now on (stamp_set_table_limit; 0: none).
 static std::atomic<int64_t> g_table_limit{0};
 
+// Step keys, their linear forms and norms, and the entry scale factors.
+static ss_status launch_steps(const KeyParams& P, const int32_t* A, const double2* av, int s_a, uint64_t* stepkey,
+                              uint64_t* stepg, int64_t* pnorm, int32_t* pn32, bool wide, double2* ca64, float2* ca32,
+                              cudaStream_t st) {
+  if (P.d > 16) {
+    SS_DISPATCH_WT(P.WT, (k_steps_warp<WT><<<(unsigned)((s_a + kPackWarps - 1) / kPackWarps), 32 * kPackWarps, 0,
+                                              st>>>(P, A, av, s_a, stepkey, stepg, pnorm, pn32, wide, ca64, ca32)));
+  } else {
+    SS_DISPATCH_WT(P.WT, (k_steps<WT><<<nblk(s_a), 256, 0, st>>>(P, A, av, s_a, stepkey, stepg, pnorm, pn32, wide,
+                                                                   ca64, ca32)));
+  }
+  SS_LAUNCH_CHECK();
+  return SS_OK;
+}
+
 static ss_status grow_table(ss_stamp_s* S, int64_t need, const KeyParams& P, cudaStream_t st, int32_t* d_err) {
   int64_t want = (int64_t)next_pow2((uint64_t)std::max<int64_t>(2 * need, 1024));
   const int64_t lim = g_table_limit.load(std::memory_order_relaxed);
@@ -1306,9 +1408,8 @@ static ss_status relayout(ss_stamp_s* S, const KeyLayout& L2, cudaStream_t st) {
   S->key = L2;
   SS_TRY(S->stepkey.alloc((size_t)S->s_a * L2.WT, st));
   SS_TRY(S->stepg.alloc(S->s_a, st));
-  SS_DISPATCH_WT(L2.WT, (k_steps<WT><<<nblk(S->s_a), 256, 0, st>>>(P2, S->afreq.get(), S->aval.get(), S->s_a,
-                                                                   S->stepkey.get(), S->stepg.get(), S->pnorm.get(), S->pn32.get(),
-                                                                   S->wide, S->ca64.get(), S->ca32.get())));
+  SS_TRY(launch_steps(P2, S->afreq.get(), S->aval.get(), S->s_a, S->stepkey.get(), S->stepg.get(), S->pnorm.get(),
+                      S->pn32.get(), S->wide, S->ca64.get(), S->ca32.get(), st));
   SS_LAUNCH_CHECK();
   const int64_t cap = S->cap;
   S->cap = 0;
@@ -1411,9 +1512,8 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   SS_TRY(S->pn32.alloc(s_a, st));
   SS_TRY(S->ca64.alloc(s_a, st));
   SS_TRY(S->ca32.alloc(s_a, st));
-  SS_DISPATCH_WT(L.WT, (k_steps<WT><<<nblk(s_a), 256, 0, st>>>(P, As.get(), avs.get(), s_a, S->stepkey.get(),
-                                                               S->stepg.get(), S->pnorm.get(), S->pn32.get(), S->wide,
-                                                               S->ca64.get(), S->ca32.get())));
+  SS_TRY(launch_steps(P, As.get(), avs.get(), s_a, S->stepkey.get(), S->stepg.get(), S->pnorm.get(), S->pn32.get(),
+                      S->wide, S->ca64.get(), S->ca32.get(), st));
   SS_LAUNCH_CHECK();
 
   // level 0; keys and table sized at once for the whole construction when
@@ -1424,10 +1524,16 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   SS_TRY(grow_table(S, pre, P, st, err));
   {
     ProfScope prof_("k_level0", st);
-    SS_DISPATCH_WT(L.WT, (k_level0<WT><<<nblk(n_f), 256, 0, st>>>(P, Fs.get(), n_f, S->keys.get(), S->hl.get(),
-                                                                  S->level.get(),
-                                                                  S->norm.get(), S->table.get(),
-                                                                  (uint64_t)S->cap - 1, err, S->zidx_dev.get())));
+    if (d > 16) {
+      SS_DISPATCH_WT(L.WT, (k_level0_warp<WT><<<(unsigned)((n_f + kPackWarps - 1) / kPackWarps), 32 * kPackWarps, 0,
+                                                 st>>>(P, Fs.get(), n_f, S->keys.get(), S->hl.get(), S->level.get(),
+                                                       S->norm.get(), S->table.get(), (uint64_t)S->cap - 1, err,
+                                                       S->zidx_dev.get())));
+    } else {
+      SS_DISPATCH_WT(L.WT, (k_level0<WT><<<nblk(n_f), 256, 0, st>>>(P, Fs.get(), n_f, S->keys.get(), S->hl.get(),
+                                                                    S->level.get(), S->norm.get(), S->table.get(),
+                                                                    (uint64_t)S->cap - 1, err, S->zidx_dev.get())));
+    }
   }
   SS_LAUNCH_CHECK();
   S->size = n_f;
@@ -1487,11 +1593,8 @@ static ss_status extend_impl(ss_stamp_s* S, int levels, cudaStream_t st) {
     // rewritten by build_operator)
     S->wide = wide2;
     const KeyParams P = make_key_params(S->key);
-    SS_DISPATCH_WT(S->key.WT, (k_steps<WT><<<nblk(S->s_a), 256, 0, st>>>(P, S->afreq.get(), S->aval.get(), S->s_a,
-                                                                         S->stepkey.get(), S->stepg.get(),
-                                                                         S->pnorm.get(),
-                                                                         S->pn32.get(), S->wide, S->ca64.get(),
-                                                                         S->ca32.get())));
+    SS_TRY(launch_steps(P, S->afreq.get(), S->aval.get(), S->s_a, S->stepkey.get(), S->stepg.get(), S->pnorm.get(),
+                        S->pn32.get(), S->wide, S->ca64.get(), S->ca32.get(), st));
     SS_LAUNCH_CHECK();
   }
   SS_TRY(run_levels(S, S->N + 1, N2, st));
