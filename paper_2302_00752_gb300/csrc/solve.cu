@@ -177,8 +177,13 @@ __device__ __forceinline__ double acc_fold(DF v) { return df_to_double(df_warp_s
 // of one instance (fixed butterfly), the block adds its warps in order.
 //   scal(c, ch, k, i, owner): per instance of the chunk (one warp each), fills
 //                             sm.ca/cb/flag[k] and does the owner's bookkeeping;
-//   row(g, s, lane, i, k, vals): per row, adds to vals[q] for q in qmask.
-template <class Acc = double, class Scal, class Row>
+//   row(g, s, lane, i, k, vals): per row, sets vals[q] for q in qmask; with
+//                             INTO the row adds to the lane's running sums
+//                             itself (vals is then the running sums: the FP64
+//                             CG accumulates its inner products by FMA, two
+//                             FP64 operations per complex product instead of
+//                             three).
+template <class Acc = double, bool INTO = false, class Scal, class Row>
 __device__ void run_phase(const SolveParams& P, Smem& sm, unsigned qmask, Scal scal, Row row) {
   const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int c = blockIdx.x; c < P.n_chunks; c += gridDim.x) {
@@ -198,6 +203,21 @@ __device__ void run_phase(const SolveParams& P, Smem& sm, unsigned qmask, Scal s
       const int i = P.slice_inst ? __ldg(P.slice_inst + s) : 0;
       const int k = i - ch.inst0;
       const int64_t g = s * kSlice + lane;
+      if constexpr (INTO) {
+        if (qmask && k != cur_k) {
+          if (cur_k >= 0) {
+#pragma unroll
+            for (int q = 0; q < kNQ; ++q) {
+              const double t = (qmask & (1u << q)) ? acc_fold(run[q]) : 0.0;
+              if (lane == 0) sm.acc[warp][cur_k][q] += t;
+            }
+          }
+          for (int q = 0; q < kNQ; ++q) run[q] = Acc{};
+          cur_k = k;
+        }
+        row(g, s, lane, i, k, run);
+        continue;
+      }
       Acc vals[kNQ] = {};
       row(g, s, lane, i, k, vals);
       if (qmask) {
@@ -357,7 +377,7 @@ __device__ void solve_fp64(const SolveParams& P, Smem& sm) {
   });
   if (!grid_sync(P)) return;
   auto phase_y = [&](unsigned par) {
-    run_phase(P, sm, 0b0111u, [&](int, const Chunk&, int k, int i, bool, int lane) {
+    run_phase<double, true>(P, sm, 0b0111u, [&](int, const Chunk&, int k, int i, bool, int lane) {
       if (lane == 0) sm.flag[k] = par > 1 ? 1 : __ldcg(&P.state[i].act[par]);
     }, [&](int64_t g, int64_t s, int lane, int i, int k, double* v) {
       if (!sm.flag[k]) return;
@@ -365,9 +385,9 @@ __device__ void solve_fp64(const SolveParams& P, Smem& sm) {
       const double2 w = apply64_row(P, in, s, lane, g, P.urec64);
       const double2 u = P.urec64[g], r = P.r[g];
       P.w64[g] = w;
-      v[0] = r.x * u.x + r.y * u.y;
-      v[1] = w.x * u.x + w.y * u.y;
-      v[2] = r.x * r.x + r.y * r.y;
+      v[0] = fma(r.y, u.y, fma(r.x, u.x, v[0]));
+      v[1] = fma(w.y, u.y, fma(w.x, u.x, v[1]));
+      v[2] = fma(r.y, r.y, fma(r.x, r.x, v[2]));
     });
   };
   phase_y(2);   // every instance
@@ -1042,25 +1062,59 @@ ss_status plan_chunks(SolvePlan& plan, const std::vector<int32_t>& woff, const s
   // (small when the row-wise phases split the rows on their own)
   auto weight = [&](int64_t s) { return (double)(woff[s + 1] - woff[s]) + slice_overhead; };
   auto inst_of = [&](int64_t s) { return slice_inst.empty() ? 0 : slice_inst[s]; };
-  if (slice_inst.empty() && slice_overhead == std::floor(slice_overhead)) {
-    // one instance, integer weights: woff is the prefix sum of the widths, so
-    // the weight of slices [s0, s] is woff[s + 1] - woff[s0] + (s + 1 - s0) x
-    // overhead, exact in double; each cut (the first s where it reaches the
-    // target) by binary search, the same cuts as the running sum below
-    auto wsum = [&](int64_t s0, int64_t s1) {   // slices [s0, s1)
-      return (double)(woff[s1] - woff[s0]) + (double)(s1 - s0) * slice_overhead;
-    };
-    const double target = wsum(0, n_slices) / std::max(1, target_chunks);
-    int64_t s0 = 0;
-    while (s0 < n_slices) {
-      int64_t lo = s0, hi = n_slices - 1;   // smallest s in [s0, n) with wsum(s0, s + 1) >= target
-      while (lo < hi) {
-        const int64_t mid = lo + (hi - lo) / 2;
-        if (wsum(s0, mid + 1) >= target) hi = mid;
-        else lo = mid + 1;
+  if (slice_inst.empty()) {
+    // one instance: weights in quarter units (4 per entry row, 4 x overhead
+    // per slice, rounded), exact in int64; woff is the prefix sum of the
+    // widths, so the weight of slices [s0, s1) is a difference of two prefix
+    // weights (pw < 2^39 and K < 2^24: the products below fit in int64).
+    const int64_t ov4 = std::llround(4.0 * slice_overhead);
+    auto pw = [&](int64_t s) { return 4 * (int64_t)woff[s] + ov4 * s; };   // weight of slices [0, s)
+    // K chunks over slices [a, b): cut c sits at the slice boundary whose
+    // prefix weight is nearest c/K of the range's weight, so every block gets
+    // one chunk within half a slice of the mean and no remainder chunk is left
+    // over (a running cut that closes a chunk once it reaches the mean makes
+    // K - 1 chunks and leaves one SM idle).
+    auto cut_range = [&](int64_t a, int64_t b, int64_t K) {
+      K = std::max<int64_t>(1, std::min<int64_t>(K, b - a));
+      const int64_t base = pw(a), total = pw(b) - base;
+      int64_t s0 = a;
+      for (int64_t c = 1; c <= K && s0 < b; ++c) {
+        int64_t cut = b;
+        if (c < K) {
+          const int64_t tgt = total * c;   // smallest s in (s0, b] with K (pw(s) - base) >= tgt, or s - 1 if nearer
+          int64_t lo = s0 + 1, hi = b;
+          while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if ((pw(mid) - base) * K >= tgt) hi = mid;
+            else lo = mid + 1;
+          }
+          if (lo - 1 > s0 && tgt - (pw(lo - 1) - base) * K < (pw(lo) - base) * K - tgt) --lo;
+          cut = lo;
+        }
+        plan.chunk.push_back(Chunk{s0, cut, 0, 0});
+        s0 = cut;
       }
-      plan.chunk.push_back(Chunk{s0, lo + 1, 0, 0});
-      s0 = lo + 1;
+    };
+    // Stamping operators order their rows by level: interior rows (every step
+    // of supp a_hat, width s_a) first, then the last level's rows with a few
+    // entries each.  A chunk that holds the transition gives its first warps
+    // an interior slice and boundary slices in the later rounds of the warp
+    // loop, so the transition gets a cut of its own: the first slice t whose
+    // width is below half the maximum, when no slice after it is wider than
+    // that, and the chunks are shared between [0, t) and [t, n) by weight.
+    int32_t wmax = 0;
+    for (int64_t s = 0; s < n_slices; ++s) wmax = std::max(wmax, woff[s + 1] - woff[s]);
+    int64_t t = 0;
+    while (t < n_slices && 2 * (woff[t + 1] - woff[t]) >= wmax) ++t;
+    bool split = t > 0 && t < n_slices;
+    for (int64_t s = t; split && s < n_slices; ++s) split = 2 * (woff[s + 1] - woff[s]) < wmax;
+    const int64_t K = std::max<int64_t>(1, std::min<int64_t>(target_chunks, n_slices));
+    if (split && K >= 2) {
+      const int64_t k1 = std::min<int64_t>(K - 1, std::max<int64_t>(1, (2 * pw(t) * K + pw(n_slices)) / (2 * pw(n_slices))));
+      cut_range(0, t, k1);
+      cut_range(t, n_slices, K - k1);
+    } else {
+      cut_range(0, n_slices, K);
     }
   } else {
     double total = 0;
@@ -1360,6 +1414,24 @@ struct ss_solve_ctx {
 
 namespace ss {
 
+// Weight of a slice in the chunk cuts beyond its entries, in entry rows (one
+// unit = one entry per row of the slice).  Fitted to per-block clock counts
+// of the apply phases on the d = 100 operator (interior slices of width 41,
+// boundary slices of width 4): an interior slice took 5.8 times a boundary
+// slice in the FP64 CG, (41 + 3.75) / (4 + 3.75), whose boundary rows carry
+// three FP64 inner products and the record loads and stores besides their
+// entries; 7.6 times in the double-float CG, whose row work runs on the FP32
+// pipes.  The FP32-refined and BiCGStab solves do their vector updates in the
+// chunks too (no even row split of those phases).
+static double slice_overhead(int mode) {
+  switch (mode) {
+    case 0: return 3.75;   // FP64 CG
+    case 3: return 1.5;    // DF64 CG
+    case 1: return 2.0;    // FP32-refined
+    default: return 6.0;   // BiCGStab
+  }
+}
+
 static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream_t st) {
   if (C.planned_mode == mode) return SS_OK;
   if ((int64_t)s->woff_host.size() != s->n_slices + 1) SS_FAIL(SS_ERR_INVALID, "solve: stamp has no slice table");
@@ -1382,7 +1454,7 @@ static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream
   // FP64 and DF64 CG: the vector updates run over an even split of the rows,
   // the apply phases over chunks balanced by entries
   C.plan.row_split = mode == 0 || mode == 3;
-  SS_TRY(plan_chunks(C.plan, woff, {}, target, C.plan.row_split ? 1.0 : 6.0));
+  SS_TRY(plan_chunks(C.plan, woff, {}, target, slice_overhead(mode)));
   C.plan.grid = std::min<int>(grid, (int)C.plan.chunk.size());
   SS_TRY(work_alloc(C.work, s->rows_pad + 1, s->norm.get(), nullptr, s->wide, st));
   if (mode == 2) SS_TRY(work_alloc_bicgstab(C.work, st));
@@ -1414,7 +1486,7 @@ static ss_status stamp_plan_half(ss_stamp_s* s, ss_solve_ctx& H, int mode, cudaS
   const int by_size = (int)std::max<int64_t>(1, s->n_slices_h / 8);
   const int target = std::min<int64_t>((int64_t)grid * H.chunks_per_block, by_size);
   H.plan.row_split = mode == 0 || mode == 3;
-  SS_TRY(plan_chunks(H.plan, s->woff_h_host, {}, target, H.plan.row_split ? 1.0 : 6.0));
+  SS_TRY(plan_chunks(H.plan, s->woff_h_host, {}, target, slice_overhead(mode)));
   H.plan.grid = std::min<int>(grid, (int)H.plan.chunk.size());
   SS_TRY(work_alloc(H.work, s->rows_pad_h + 1, s->norm_h.get(), nullptr, s->wide, st));
   if (mode == 3) {
@@ -1775,7 +1847,7 @@ extern "C" ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_o
   const int by_size = (int)std::max<int64_t>(1, s->n_slices / 8);
   // FP64 CG: the vector updates over an even split of the rows (as solve())
   plan.row_split = mode == 0;
-  SS_TRY(plan_chunks(plan, woff, {}, std::min(grid, by_size), plan.row_split ? 1.0 : 6.0));
+  SS_TRY(plan_chunks(plan, woff, {}, std::min(grid, by_size), slice_overhead(mode)));
   plan.grid = std::min<int>(grid, (int)plan.chunk.size());
   if ((int)plan.chunk.size() > kNoAllocChunks || plan.n_parts > kNoAllocParts)
     SS_FAIL(SS_ERR_INVALID, "solve_noalloc: work split exceeds the workspace tables");
