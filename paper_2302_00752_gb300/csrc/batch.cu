@@ -408,13 +408,16 @@ static ss_status batch_create_half(ss_batch_s* b, int32_t n, const ss_stamp* sta
 
 extern "C" ss_status batch_create(int32_t n_inst, const ss_stamp* stamps, ss_batch* out, void* stream) {
   if (!out || !stamps || n_inst < 1) SS_FAIL(SS_ERR_INVALID, "batch_create: bad argument");
+  cudaStream_t st = as_stream(stream);
+  // host copies of the slice offsets: the batch's tables are laid out on the host
+  for (int i = 0; i < n_inst; ++i)
+    if (stamps[i]) SS_TRY(stamp_host_tables(stamps[i], st));
   bool all_half = true;
   for (int i = 0; i < n_inst; ++i) {
     if (stamps[i] && stamps[i]->adr) SS_FAIL(SS_ERR_INVALID, "batch_create: ADR stamps are solved one at a time");
     all_half = all_half && stamps[i] && stamps[i]->half_ok;
   }
   *out = nullptr;
-  cudaStream_t st = as_stream(stream);
   ss_batch_s* b = new ss_batch_s();
   ss_status s = batch_create_impl(b, n_inst, stamps, false, st);
   // real data throughout: the half batch as well (one that does not fit its

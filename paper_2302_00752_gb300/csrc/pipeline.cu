@@ -58,7 +58,9 @@ ss_status run(const ss_lattice_spec* ls, const ss_trig* a, const ss_trig* f, con
     SS_FAIL(SS_ERR_INVALID, "sparse_spectral_solve: %s has no coefficient above the threshold", n_a < 1 ? "a" : "f");
   const ss_sparse a_hat{d, n_a, af.get(), reinterpret_cast<const double*>(av.get())};
   ss_stamp s = nullptr;
-  SS_TRY(stamp_build(&a_hat, ff.get(), n_f, N, &s, st));
+  // the build's final error words are read with the solve's statistics (one
+  // synchronisation fewer between the stamp and the solve)
+  SS_TRY(stamp_build_pending(&a_hat, ff.get(), n_f, N, &s, st));
   ss_status r = SS_OK;
   do {
     r = s->sol.alloc(std::max<int64_t>(s->size, 1), st);
@@ -83,6 +85,10 @@ ss_status run(const ss_lattice_spec* ls, const ss_trig* a, const ss_trig* f, con
     s->sol.settle();
     s->rhs.settle();
   } while (false);
+  if (s->check_pending) {   // the solve stopped before it read the build's error words
+    const ss_status rc = stamp_host_tables(s, st);
+    if (rc != SS_OK) r = rc;
+  }
   if (r != SS_OK && r != SS_ERR_NOT_CONVERGED) {
     const std::string msg = ss_last_error();
     stamp_destroy(s);

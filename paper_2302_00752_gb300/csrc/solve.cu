@@ -1048,9 +1048,222 @@ __global__ void k_init_solve_records(const int64_t* __restrict__ norm, int64_t n
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// Chunk cuts of one instance, computed where the slice table lives (one
+// block of kPlanThreads threads; no host copy of the widths and no host
+// synchronisation).  Slice s weighs 4 (woff[s+1] - woff[s]) + ov4 (quarter
+// units, exact in int64); pw(s) = 4 woff[s] + ov4 s is the weight of slices
+// [0, s).  Stamping operators order their rows by level: interior rows
+// (every step of supp a_hat) first, then the last level's rows with a few
+// entries each.  When the first slice t narrower than half the widest one has
+// no wider slice after it, [0, t) and [t, n) get their own chunks, shared by
+// weight (a chunk holding the transition gives its first warps an interior
+// slice plus boundary slices in the later rounds of the warp loop).  Within a
+// range of K' chunks, cut c sits at the slice boundary whose prefix weight is
+// nearest c/K' of the range's weight, so every block gets one chunk within
+// half a slice of the mean.  A sequential pass then makes the cuts strictly
+// increasing (K <= n).  If the stamp's build reported an error (err[0]; its
+// check may still be pending) every chunk is empty and the solve reads no
+// entry.  The slice table is staged in shared memory when it fits.
+constexpr int kPlanThreads = 1024;
+constexpr int kPlanMaxK = 8192;            // chunks of one instance
+constexpr int kPlanSmemWoff = 40960;       // slice offsets staged in shared memory up to this count
+
+__device__ void plan_cuts_block(const int32_t* __restrict__ woff_g, int64_t n, int K, int64_t ov4,
+                                const int32_t* __restrict__ stamp_err, Chunk* out) {
+  extern __shared__ int32_t sm_plan[];
+  __shared__ int32_t s_wmax;
+  __shared__ unsigned long long s_t;
+  __shared__ int s_bad, s_fix;
+  const int tid = threadIdx.x;
+  const bool staged = n + 1 <= kPlanSmemWoff;
+  int32_t* cut = sm_plan + (staged ? kPlanSmemWoff : 0);   // [K + 1]
+  if (tid == 0) {
+    s_wmax = 0;
+    s_t = (unsigned long long)n;
+    s_bad = 0;
+    s_fix = 0;
+  }
+  if (staged) {
+    // kStage loads in flight per thread before the first store (the table
+    // holds at most kPlanSmemWoff words: ceil(40960 / 1024) = 40 per thread)
+    constexpr int kStage = 8;
+    for (int64_t s0 = tid; s0 <= n; s0 += (int64_t)kStage * blockDim.x) {
+      int32_t v[kStage];
+#pragma unroll
+      for (int q = 0; q < kStage; ++q) {
+        const int64_t s = s0 + (int64_t)q * blockDim.x;
+        v[q] = s <= n ? __ldg(woff_g + s) : 0;
+      }
+#pragma unroll
+      for (int q = 0; q < kStage; ++q) {
+        const int64_t s = s0 + (int64_t)q * blockDim.x;
+        if (s <= n) sm_plan[s] = v[q];
+      }
+    }
+  }
+  __syncthreads();
+  const int32_t* woff = staged ? sm_plan : woff_g;
+  if (stamp_err && __ldg(stamp_err) != 0) {
+    for (int c = tid; c < K; c += blockDim.x) out[c] = Chunk{0, 0, 0, 0};
+    return;
+  }
+  int32_t wm = 0;
+  for (int64_t s = tid; s < n; s += blockDim.x) wm = max(wm, woff[s + 1] - woff[s]);
+  wm = __reduce_max_sync(0xffffffffu, wm);
+  if ((tid & 31) == 0) atomicMax(&s_wmax, wm);
+  __syncthreads();
+  const int32_t wmax = s_wmax;
+  for (int64_t s = tid; s < n; s += blockDim.x)
+    if (2 * (woff[s + 1] - woff[s]) < wmax) {
+      atomicMin(&s_t, (unsigned long long)s);
+      break;   // a thread's slices ascend: its first hit is its smallest
+    }
+  __syncthreads();
+  const int64_t t = (int64_t)s_t;
+  for (int64_t s = t + tid; s < n; s += blockDim.x)
+    if (2 * (woff[s + 1] - woff[s]) >= wmax) s_bad = 1;
+  __syncthreads();
+  auto pw = [&](int64_t s) { return 4 * (int64_t)woff[s] + ov4 * s; };
+  const bool split = t > 0 && t < n && !s_bad && K >= 2;
+  const int64_t pn = pw(n);
+  int k1 = K;
+  if (split) {
+    const int64_t r = (2 * pw(t) * K + pn) / (2 * pn);   // K pw(t) / pw(n), rounded
+    k1 = (int)(r < 1 ? 1 : (r > K - 1 ? K - 1 : r));
+  }
+  for (int c = tid + 1; c < K; c += blockDim.x) {
+    int64_t a = 0, b = n, kr = K, cr = c;
+    if (split) {
+      if (c < k1) {
+        b = t;
+        kr = k1;
+      } else {
+        a = t;
+        kr = K - k1;
+        cr = c - k1;
+      }
+    }
+    int64_t cs;
+    if (cr == 0) {
+      cs = a;   // the region boundary
+    } else {
+      // smallest s in (a, b] with kr (pw(s) - pw(a)) >= cr (pw(b) - pw(a)), or s - 1 if nearer
+      // (pw < 2^39 and kr <= 2^13: the products fit in int64)
+      const int64_t base = pw(a), tgt = (pw(b) - base) * cr;
+      int64_t lo = a + 1, hi = b;
+      while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if ((pw(mid) - base) * kr >= tgt) hi = mid;
+        else lo = mid + 1;
+      }
+      if (lo - 1 > a && tgt - (pw(lo - 1) - base) * kr < (pw(lo) - base) * kr - tgt) --lo;
+      cs = lo;
+    }
+    cut[c] = (int32_t)cs;
+  }
+  if (tid == 0) {
+    cut[0] = 0;
+    cut[K] = (int32_t)n;
+  }
+  __syncthreads();
+  for (int c = tid; c < K; c += blockDim.x)
+    if (cut[c] >= cut[c + 1]) s_fix = 1;
+  __syncthreads();
+  if (s_fix && tid == 0) {   // only when a slice outweighs a chunk: one sequential pass
+    for (int c = 1; c < K; ++c) cut[c] = max(cut[c], cut[c - 1] + 1);
+    for (int c = K - 1; c >= 1; --c) cut[c] = min(cut[c], cut[c + 1] - 1);
+  }
+  __syncthreads();
+  for (int c = tid; c < K; c += blockDim.x) out[c] = Chunk{cut[c], cut[c + 1], 0, 0};
+}
+
+// Everything a single-instance solve writes before its kernel starts, in one
+// launch of one block: the barrier, counter and error words, the instance
+// state, one caller word (the half system's Hermitian flag), the instance
+// descriptor, and the chunk cuts when the plan is new (plan_cuts_block).
+struct Prologue {
+  unsigned* bar;
+  int* counters;
+  int* err;
+  InstState* state;
+  int32_t* extra;
+  SolveInst* inst_dst;
+  SolveInst inst;
+  int cuts;
+  const int32_t* woff;
+  int64_t n, ov4;
+  int K;
+  const int32_t* stamp_err;
+  Chunk* chunk;
+};
+
+__global__ void __launch_bounds__(kPlanThreads) k_solve_prologue(Prologue p) {
+  const int tid = threadIdx.x;
+  if (tid < 2) p.bar[tid] = 0u;
+  if (tid < 4) p.counters[tid] = 0;
+  if (tid == 0) {
+    *p.err = 0;
+    if (p.extra) *p.extra = 0;
+    *p.inst_dst = p.inst;
+  }
+  static_assert(sizeof(InstState) % sizeof(int32_t) == 0, "InstState is zeroed in 32-bit words");
+  for (int i = tid; i < (int)(sizeof(InstState) / sizeof(int32_t)); i += blockDim.x)
+    reinterpret_cast<int32_t*>(p.state)[i] = 0;
+  if (p.cuts) plan_cuts_block(p.woff, p.n, p.K, p.ov4, p.stamp_err, p.chunk);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- host side
+
+// The single-instance plan: K chunks (c_first 0, c_last K - 1, one partial
+// slot each) whose cuts the prologue computes on the device.
+static void plan_single(SolvePlan& plan, int64_t n_slices, int target, const int32_t* woff_dev, double overhead,
+                        const int32_t* stamp_err) {
+  const int K = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)target, n_slices, (int64_t)kPlanMaxK}));
+  plan.chunk.assign(K, Chunk{0, 0, 0, 0});
+  plan.n_parts = K;
+  SolveInst& in = plan.inst[0];
+  in.c_first = 0;
+  in.c_last = K - 1;
+  in.part_base = 0;
+  plan.dev_cuts = true;
+  plan.cuts_pending = true;
+  plan.cut_woff = woff_dev;
+  plan.cut_n = n_slices;
+  plan.cut_ov4 = std::llround(4.0 * overhead);
+  plan.cut_err = stamp_err;
+}
+
+// The prologue of a single-instance (dev_cuts) plan into the given words and
+// tables; the chunk cuts only when the plan's are not in `chunk` yet.
+static ss_status launch_prologue(SolvePlan& plan, unsigned* bar, int* counters, int* err, InstState* state,
+                                 int32_t* extra, SolveInst* inst_dst, Chunk* chunk, cudaStream_t st) {
+  Prologue p{};
+  p.bar = bar;
+  p.counters = counters;
+  p.err = err;
+  p.state = state;
+  p.extra = extra;
+  p.inst_dst = inst_dst;
+  p.inst = plan.inst[0];
+  p.cuts = plan.cuts_pending ? 1 : 0;
+  p.woff = plan.cut_woff;
+  p.n = plan.cut_n;
+  p.ov4 = plan.cut_ov4;
+  p.K = (int)plan.chunk.size();
+  p.stamp_err = plan.cut_err;
+  p.chunk = chunk;
+  const size_t smem =
+      p.cuts ? ((plan.cut_n + 1 <= kPlanSmemWoff ? (size_t)kPlanSmemWoff : 0) + (size_t)p.K + 1) * sizeof(int32_t) : 0;
+  static const cudaError_t attr = cudaFuncSetAttribute(k_solve_prologue, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)((kPlanSmemWoff + kPlanMaxK + 1) * sizeof(int32_t)));
+  SS_CUDA(attr);
+  k_solve_prologue<<<1, kPlanThreads, smem, st>>>(p);
+  SS_LAUNCH_CHECK();
+  plan.cuts_pending = false;
+  return SS_OK;
+}
 
 ss_status plan_chunks(SolvePlan& plan, const std::vector<int32_t>& woff, const std::vector<int32_t>& slice_inst,
                       int target_chunks, double slice_overhead) {
@@ -1062,61 +1275,9 @@ ss_status plan_chunks(SolvePlan& plan, const std::vector<int32_t>& woff, const s
   // (small when the row-wise phases split the rows on their own)
   auto weight = [&](int64_t s) { return (double)(woff[s + 1] - woff[s]) + slice_overhead; };
   auto inst_of = [&](int64_t s) { return slice_inst.empty() ? 0 : slice_inst[s]; };
-  if (slice_inst.empty()) {
-    // one instance: weights in quarter units (4 per entry row, 4 x overhead
-    // per slice, rounded), exact in int64; woff is the prefix sum of the
-    // widths, so the weight of slices [s0, s1) is a difference of two prefix
-    // weights (pw < 2^39 and K < 2^24: the products below fit in int64).
-    const int64_t ov4 = std::llround(4.0 * slice_overhead);
-    auto pw = [&](int64_t s) { return 4 * (int64_t)woff[s] + ov4 * s; };   // weight of slices [0, s)
-    // K chunks over slices [a, b): cut c sits at the slice boundary whose
-    // prefix weight is nearest c/K of the range's weight, so every block gets
-    // one chunk within half a slice of the mean and no remainder chunk is left
-    // over (a running cut that closes a chunk once it reaches the mean makes
-    // K - 1 chunks and leaves one SM idle).
-    auto cut_range = [&](int64_t a, int64_t b, int64_t K) {
-      K = std::max<int64_t>(1, std::min<int64_t>(K, b - a));
-      const int64_t base = pw(a), total = pw(b) - base;
-      int64_t s0 = a;
-      for (int64_t c = 1; c <= K && s0 < b; ++c) {
-        int64_t cut = b;
-        if (c < K) {
-          const int64_t tgt = total * c;   // smallest s in (s0, b] with K (pw(s) - base) >= tgt, or s - 1 if nearer
-          int64_t lo = s0 + 1, hi = b;
-          while (lo < hi) {
-            const int64_t mid = lo + (hi - lo) / 2;
-            if ((pw(mid) - base) * K >= tgt) hi = mid;
-            else lo = mid + 1;
-          }
-          if (lo - 1 > s0 && tgt - (pw(lo - 1) - base) * K < (pw(lo) - base) * K - tgt) --lo;
-          cut = lo;
-        }
-        plan.chunk.push_back(Chunk{s0, cut, 0, 0});
-        s0 = cut;
-      }
-    };
-    // Stamping operators order their rows by level: interior rows (every step
-    // of supp a_hat, width s_a) first, then the last level's rows with a few
-    // entries each.  A chunk that holds the transition gives its first warps
-    // an interior slice and boundary slices in the later rounds of the warp
-    // loop, so the transition gets a cut of its own: the first slice t whose
-    // width is below half the maximum, when no slice after it is wider than
-    // that, and the chunks are shared between [0, t) and [t, n) by weight.
-    int32_t wmax = 0;
-    for (int64_t s = 0; s < n_slices; ++s) wmax = std::max(wmax, woff[s + 1] - woff[s]);
-    int64_t t = 0;
-    while (t < n_slices && 2 * (woff[t + 1] - woff[t]) >= wmax) ++t;
-    bool split = t > 0 && t < n_slices;
-    for (int64_t s = t; split && s < n_slices; ++s) split = 2 * (woff[s + 1] - woff[s]) < wmax;
-    const int64_t K = std::max<int64_t>(1, std::min<int64_t>(target_chunks, n_slices));
-    if (split && K >= 2) {
-      const int64_t k1 = std::min<int64_t>(K - 1, std::max<int64_t>(1, (2 * pw(t) * K + pw(n_slices)) / (2 * pw(n_slices))));
-      cut_range(0, t, k1);
-      cut_range(t, n_slices, K - k1);
-    } else {
-      cut_range(0, n_slices, K);
-    }
-  } else {
+  // running cuts over the instances' slices (batches; a single instance is
+  // cut on the device by the solve prologue)
+  {
     double total = 0;
     for (int64_t s = 0; s < n_slices; ++s) total += weight(s);
     const double target = total / std::max(1, target_chunks);
@@ -1236,14 +1397,27 @@ ss_status work_alloc_df64(SolveWork& W, cudaStream_t st) {
   return SS_OK;
 }
 
-ss_status work_upload(SolveWork& W, const SolvePlan& plan, cudaStream_t st) {
+ss_status work_upload(SolveWork& W, SolvePlan& plan, cudaStream_t st) {
   const int n_inst = (int)plan.inst.size(), n_chunk = (int)plan.chunk.size();
   if (n_inst > W.cap_inst) { SS_TRY(W.inst.alloc(n_inst, st)); SS_TRY(W.state.alloc(n_inst, st)); W.cap_inst = n_inst; }
-  if (n_chunk > W.cap_chunk) { SS_TRY(W.chunk.alloc(n_chunk, st)); W.cap_chunk = n_chunk; }
+  if (n_chunk > W.cap_chunk) {
+    SS_TRY(W.chunk.alloc(n_chunk, st));
+    W.cap_chunk = n_chunk;
+    plan.cuts_pending = plan.dev_cuts;   // a new chunk table: its cuts are written again
+  }
   if (plan.n_parts > W.cap_parts) { SS_TRY(W.part.alloc(plan.n_parts * kNQ, st)); W.cap_parts = plan.n_parts; }
   W.inst.settle(); W.state.settle(); W.chunk.settle(); W.part.settle();   // reused across calls (see read_stats)
+  if (plan.dev_cuts) return SS_OK;   // descriptor, cuts and zeroed words: work_prologue
   return upload(st, {{W.inst.get(), plan.inst.data(), n_inst * sizeof(SolveInst)},
                      {W.chunk.get(), plan.chunk.data(), n_chunk * sizeof(Chunk)}});
+}
+
+// The prologue of a single-instance plan into its workspace (after
+// work_upload); `extra` is one more word to zero (or null).  The solve is then
+// launched with zeroed = true.
+static ss_status work_prologue(SolveWork& W, SolvePlan& plan, int32_t* extra, cudaStream_t st) {
+  return launch_prologue(plan, W.bar.get(), W.counters.get(), W.err.get(), W.state.get(), extra, W.inst.get(),
+                         W.chunk.get(), st);
 }
 
 ss_status max_grid(int mode, int block, int* grid) {
@@ -1278,7 +1452,7 @@ ss_status max_grid(int mode, int block, int* grid) {
 ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, const int32_t* slice_inst,
                        const int64_t* norm, const double2* ca64, const float2* ca32, const int32_t* pn,
                        double tol, int max_iter, int mode, cudaStream_t st, cudaEvent_t ev_begin,
-                       cudaEvent_t ev_end, const double2* cdiag) {
+                       cudaEvent_t ev_end, const double2* cdiag, bool zeroed) {
   if (mode == 2 && (!cdiag || !W.zrec.get() || !W.tv.get()))
     SS_FAIL(SS_ERR_INVALID, "solve: BiCGStab needs the operator diagonal and its workspace");
   if (mode == 3 && (!op.ecoefdf || !W.xdf.get() || !W.udf.get()))
@@ -1325,10 +1499,13 @@ ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, co
   P.max_inner = std::max(1, std::min(max_iter, 200));
   P.max_outer = std::max(1, max_iter);
   P.spin_limit = plan.spin_limit;   // 2 s unless solve_set_wait_limit changed it
-  P.rows_slices = plan.row_split && P.n_inst == 1 && !slice_inst ? plan.chunk.back().s1 : 0;
-  SS_TRY(fill_small(st, {{W.bar.get(), 2 * sizeof(unsigned), 0}, {W.counters.get(), 4 * sizeof(int), 0}}));
-  SS_CUDA(cudaMemsetAsync(W.err.get(), 0, sizeof(int), st));
-  SS_CUDA(cudaMemsetAsync(W.state.get(), 0, plan.inst.size() * sizeof(InstState), st));
+  const int64_t n_sl = plan.dev_cuts ? plan.cut_n : plan.chunk.back().s1;
+  P.rows_slices = plan.row_split && P.n_inst == 1 && !slice_inst ? n_sl : 0;
+  if (!zeroed) {
+    SS_TRY(fill_small(st, {{W.bar.get(), 2 * sizeof(unsigned), 0}, {W.counters.get(), 4 * sizeof(int), 0}}));
+    SS_CUDA(cudaMemsetAsync(W.err.get(), 0, sizeof(int), st));
+    SS_CUDA(cudaMemsetAsync(W.state.get(), 0, plan.inst.size() * sizeof(InstState), st));
+  }
   // cooperative launch: all blocks co-resident (required by the grid barrier);
   // expressed as a launch attribute so that it can be captured in a graph
   cudaLaunchConfig_t cfg = {};
@@ -1405,9 +1582,11 @@ struct ss_solve_ctx {
   ss::DevBuf<double2> fh, uh;
   ss::DevBuf<int32_t> hflag;
   int32_t* hflag_host = nullptr;
+  int32_t* chk_host = nullptr;   // pinned copy of a pending stamp's error words (stamp_build_pending)
   ~ss_solve_ctx() {
     if (f0_host) cudaFreeHost(f0_host);
     if (hflag_host) cudaFreeHost(hflag_host);
+    if (chk_host) cudaFreeHost(chk_host);
     delete half;
   }
 };
@@ -1434,8 +1613,7 @@ static double slice_overhead(int mode) {
 
 static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream_t st) {
   if (C.planned_mode == mode) return SS_OK;
-  if ((int64_t)s->woff_host.size() != s->n_slices + 1) SS_FAIL(SS_ERR_INVALID, "solve: stamp has no slice table");
-  const std::vector<int32_t>& woff = s->woff_host;
+  if (!s->slice_off.get() || s->n_slices < 1) SS_FAIL(SS_ERR_INVALID, "solve: stamp has no slice table");
   C.plan.inst.assign(1, SolveInst{});
   SolveInst& in = C.plan.inst[0];
   in.row0 = 0;
@@ -1454,7 +1632,7 @@ static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream
   // FP64 and DF64 CG: the vector updates run over an even split of the rows,
   // the apply phases over chunks balanced by entries
   C.plan.row_split = mode == 0 || mode == 3;
-  SS_TRY(plan_chunks(C.plan, woff, {}, target, slice_overhead(mode)));
+  plan_single(C.plan, s->n_slices, target, s->slice_off.get(), slice_overhead(mode), s->err_dev.get());
   C.plan.grid = std::min<int>(grid, (int)C.plan.chunk.size());
   SS_TRY(work_alloc(C.work, s->rows_pad + 1, s->norm.get(), nullptr, s->wide, st));
   if (mode == 2) SS_TRY(work_alloc_bicgstab(C.work, st));
@@ -1469,7 +1647,7 @@ static ss_status stamp_plan(ss_stamp_s* s, ss_solve_ctx& C, int mode, cudaStream
 // Plan and workspace of the Hermitian half system (FP64, FP32-refined and DF64 modes).
 static ss_status stamp_plan_half(ss_stamp_s* s, ss_solve_ctx& H, int mode, cudaStream_t st) {
   if (H.planned_mode == mode) return SS_OK;
-  if ((int64_t)s->woff_h_host.size() != s->n_slices_h + 1) SS_FAIL(SS_ERR_INVALID, "solve: no half-system table");
+  if (!s->woff_h.get() || s->n_slices_h < 1) SS_FAIL(SS_ERR_INVALID, "solve: no half-system table");
   H.plan.inst.assign(1, SolveInst{});
   SolveInst& in = H.plan.inst[0];
   in.row0 = 0;
@@ -1486,7 +1664,7 @@ static ss_status stamp_plan_half(ss_stamp_s* s, ss_solve_ctx& H, int mode, cudaS
   const int by_size = (int)std::max<int64_t>(1, s->n_slices_h / 8);
   const int target = std::min<int64_t>((int64_t)grid * H.chunks_per_block, by_size);
   H.plan.row_split = mode == 0 || mode == 3;
-  SS_TRY(plan_chunks(H.plan, s->woff_h_host, {}, target, slice_overhead(mode)));
+  plan_single(H.plan, s->n_slices_h, target, s->woff_h.get(), slice_overhead(mode), s->err_dev.get());
   H.plan.grid = std::min<int>(grid, (int)H.plan.chunk.size());
   SS_TRY(work_alloc(H.work, s->rows_pad_h + 1, s->norm_h.get(), nullptr, s->wide, st));
   if (mode == 3) {
@@ -1506,18 +1684,26 @@ __global__ void k_half_gather(const double2* __restrict__ f, const int32_t* __re
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_plus) return;
   const int64_t g = plus_rows[i];
-  const double2 a = f[g], b = f[mirror[g]];
-  if (!(a.x == b.x && a.y == -b.y)) atomicExch(flag, 1);
+  const int64_t m = mirror[g];   // -1: -k not found (the stamp's check fails): solved as the full system
+  const double2 a = f[g];
+  if (m < 0) {
+    atomicExch(flag, 1);
+  } else {
+    const double2 b = f[m];
+    if (!(a.x == b.x && a.y == -b.y)) atomicExch(flag, 1);
+  }
   f_h[i] = a;
 }
 
 // u on S from the compact solution: u_k (k > 0), conj(u_{-k}) (k < 0), 0 (k = 0).
 __global__ void k_half_scatter(const double2* __restrict__ u_h, const int32_t* __restrict__ hpos, int64_t size,
-                               double2* u) {
+                               int64_t n_plus, double2* u) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= size) return;
   const int32_t h = hpos[g];
-  if (h == -1) {
+  // positions outside the compact rows only come from a half system whose
+  // build failed (reported by the stamp's check); nothing is read there
+  if (h == -1 || h >= n_plus || (h < -1 && -2 - (int64_t)h >= n_plus)) {
     u[g] = make_double2(0.0, 0.0);
   } else if (h >= 0) {
     u[g] = u_h[h];
@@ -1620,16 +1806,33 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
   cudaStream_t st = as_stream(stream);
   if (s->adr && prec != SS_FP64) SS_FAIL(SS_ERR_INVALID, "solve: ADR stamps solve in SS_FP64 (BiCGStab)");
   ss_solve_ctx* C = solve_ctx(s);
+  // Host checks read back with the solve's statistics (one synchronisation
+  // for all), queued behind the solve kernel so that they do not delay it:
+  // f_hat_0 (must vanish) and the error words of a stamp whose build left
+  // them to this synchronisation (the one-call pipeline).
+  const bool pending = s->check_pending;
   const bool check_f0 = !s->adr && s->zero_idx >= 0;
-  if (check_f0) {
-    // read back with the solve's statistics (one synchronisation for both)
-    if (!C->f0_host) {
-      note_alloc();
-      SS_CUDA(cudaMallocHost(&C->f0_host, sizeof(double2)));
+  bool checks_queued = false;
+  auto queue_checks = [&]() -> ss_status {
+    if (checks_queued) return SS_OK;
+    checks_queued = true;
+    if (pending) {
+      if (!C->chk_host) {
+        note_alloc();
+        SS_CUDA(cudaMallocHost(&C->chk_host, 4 * sizeof(int32_t)));
+      }
+      SS_CUDA(cudaMemcpyAsync(C->chk_host, s->err_dev.get(), 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     }
-    SS_CUDA(cudaMemcpyAsync(C->f0_host, reinterpret_cast<const double2*>(f_on_S) + s->zero_idx, sizeof(double2),
-                            cudaMemcpyDeviceToHost, st));
-  }
+    if (check_f0) {
+      if (!C->f0_host) {
+        note_alloc();
+        SS_CUDA(cudaMallocHost(&C->f0_host, sizeof(double2)));
+      }
+      SS_CUDA(cudaMemcpyAsync(C->f0_host, reinterpret_cast<const double2*>(f_on_S) + s->zero_idx, sizeof(double2),
+                              cudaMemcpyDeviceToHost, st));
+    }
+    return SS_OK;
+  };
   const int mode = s->adr ? 2 : (prec == SS_FP64 ? 0 : (prec == SS_FP32 ? 1 : 3));
   if (mode != 2 && s->half_ok && C->use_half) {
     // Real data: solve the Hermitian half system (rows k >lex 0, neighbours
@@ -1651,14 +1854,14 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
       note_alloc();
       SS_CUDA(cudaMallocHost(&C->hflag_host, sizeof(int32_t)));
     }
-    SS_CUDA(cudaMemsetAsync(C->hflag.get(), 0, sizeof(int32_t), st));
+    H->plan.inst[0].f = C->fh.get();
+    H->plan.inst[0].u = C->uh.get();
+    SS_TRY(work_upload(H->work, H->plan, st));
+    SS_TRY(work_prologue(H->work, H->plan, C->hflag.get(), st));   // also clears the Hermitian flag
     const unsigned gb = (unsigned)((s->n_plus + 255) / 256), sb = (unsigned)((s->size + 255) / 256);
     k_half_gather<<<gb, 256, 0, st>>>(reinterpret_cast<const double2*>(f_on_S), s->plus_rows.get(), s->mirror.get(),
                                       s->n_plus, C->fh.get(), C->hflag.get());
     SS_LAUNCH_CHECK();
-    H->plan.inst[0].f = C->fh.get();
-    H->plan.inst[0].u = C->uh.get();
-    SS_TRY(work_upload(H->work, H->plan, st));
     OpView hop;
     hop.woff = s->woff_h.get();
     hop.ent = s->ent_h.get();
@@ -1675,17 +1878,20 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
     }
     H->plan.spin_limit = C->wait_ns;
     SS_TRY(launch_solve(H->work, H->plan, hop, nullptr, s->norm_h.get(), s->ca64.get(), s->ca32.get(), s->pn32.get(),
-                        tol, max_iter, mode, st, H->work.ev[0], H->work.ev[1], nullptr));
-    k_half_scatter<<<sb, 256, 0, st>>>(C->uh.get(), s->hpos.get(), s->size, reinterpret_cast<double2*>(u_on_S));
+                        tol, max_iter, mode, st, H->work.ev[0], H->work.ev[1], nullptr, true));
+    k_half_scatter<<<sb, 256, 0, st>>>(C->uh.get(), s->hpos.get(), s->size, s->n_plus,
+                                       reinterpret_cast<double2*>(u_on_S));
     SS_LAUNCH_CHECK();
     SS_CUDA(cudaMemcpyAsync(C->hflag_host, C->hflag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SS_TRY(queue_checks());
     ss_status worst;
     ss_solve_stats one{};
     SS_TRY(read_stats(H->work, 1, &one, &worst, st, H->work.ev[0], H->work.ev[1]));
     C->fh.settle();
     C->uh.settle();
     C->hflag.settle();
-    if (*C->hflag_host == 0) {
+    if (pending) SS_TRY(stamp_check_pending(s, C->chk_host));   // may withdraw the half system
+    if (*C->hflag_host == 0 && s->half_ok) {
       one.half_system = 1;
       one.real_coefficients = s->a_real;
       if (check_f0 && (C->f0_host->x != 0.0 || C->f0_host->y != 0.0)) {
@@ -1701,6 +1907,7 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
   C->plan.inst[0].f = reinterpret_cast<const double2*>(f_on_S);
   C->plan.inst[0].u = reinterpret_cast<double2*>(u_on_S);
   SS_TRY(work_upload(C->work, C->plan, st));
+  SS_TRY(work_prologue(C->work, C->plan, nullptr, st));
   OpView op;
   op.woff = s->slice_off.get();
   op.ent = s->ent.get();
@@ -1715,10 +1922,12 @@ extern "C" ss_status solve(ss_stamp s, const double* f_on_S, double* u_on_S, dou
   }
   C->plan.spin_limit = C->wait_ns;
   SS_TRY(launch_solve(C->work, C->plan, op, nullptr, s->norm.get(), s->ca64.get(), s->ca32.get(), s->pn32.get(), tol,
-                      max_iter, mode, st, C->work.ev[0], C->work.ev[1], s->adr ? s->diag64.get() : nullptr));
+                      max_iter, mode, st, C->work.ev[0], C->work.ev[1], s->adr ? s->diag64.get() : nullptr, true));
+  SS_TRY(queue_checks());
   ss_status worst;
   ss_solve_stats one{};
   SS_TRY(read_stats(C->work, 1, &one, &worst, st, C->work.ev[0], C->work.ev[1]));
+  if (pending) SS_TRY(stamp_check_pending(s, C->chk_host));
   one.real_coefficients = s->a_real;
   if (check_f0 && (C->f0_host->x != 0.0 || C->f0_host->y != 0.0)) {
     one.status = SS_ERR_INVALID;
@@ -1823,11 +2032,10 @@ extern "C" ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_o
   cudaStream_t st = as_stream(stream);
   unsigned char* base = nullptr;
   SS_TRY(noalloc_base(&base));
-  if ((int64_t)s->woff_host.size() != s->n_slices + 1) SS_FAIL(SS_ERR_INVALID, "solve_noalloc: stamp has no slice table");
-  // static work split, as solve() with its default tile shape, from the host
-  // copy of the slice table (host memory only)
+  if (!s->slice_off.get() || s->n_slices < 1) SS_FAIL(SS_ERR_INVALID, "solve_noalloc: stamp has no slice table");
+  // static work split, as solve() with its default tile shape: the cuts are
+  // computed on the device into the workspace's chunk table
   const int mode = prec == SS_FP64 ? 0 : 1;
-  const std::vector<int32_t>& woff = s->woff_host;
   SolvePlan plan;
   plan.inst.assign(1, SolveInst{});
   SolveInst& in = plan.inst[0];
@@ -1847,7 +2055,7 @@ extern "C" ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_o
   const int by_size = (int)std::max<int64_t>(1, s->n_slices / 8);
   // FP64 CG: the vector updates over an even split of the rows (as solve())
   plan.row_split = mode == 0;
-  SS_TRY(plan_chunks(plan, woff, {}, std::min(grid, by_size), slice_overhead(mode)));
+  plan_single(plan, s->n_slices, std::min(grid, by_size), s->slice_off.get(), slice_overhead(mode), s->err_dev.get());
   plan.grid = std::min<int>(grid, (int)plan.chunk.size());
   if ((int)plan.chunk.size() > kNoAllocChunks || plan.n_parts > kNoAllocParts)
     SS_FAIL(SS_ERR_INVALID, "solve_noalloc: work split exceeds the workspace tables");
@@ -1859,14 +2067,10 @@ extern "C" ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_o
   unsigned* d_bar = static_cast<unsigned*>(at(kOffBar));
   int* d_cnt = static_cast<int*>(at(kOffCnt));
   int* d_err = static_cast<int*>(at(kOffErr));
-  SS_CUDA(cudaMemcpyAsync(d_inst, plan.inst.data(), sizeof(SolveInst), cudaMemcpyHostToDevice, st));
-  SS_CUDA(cudaMemcpyAsync(d_chunk, plan.chunk.data(), plan.chunk.size() * sizeof(Chunk), cudaMemcpyHostToDevice, st));
-  // the array keeps the previous call's contents: reset what must start at zero
-  // (barrier, counters, error word, instance state) and the records' norm halves
-  SS_CUDA(cudaMemsetAsync(d_bar, 0, 2 * sizeof(unsigned), st));
-  SS_CUDA(cudaMemsetAsync(d_cnt, 0, 4 * sizeof(int), st));
-  SS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
-  SS_CUDA(cudaMemsetAsync(d_state, 0, sizeof(InstState), st));
+  // the array keeps the previous call's contents: the prologue writes the
+  // descriptor and the cuts and resets what must start at zero (barrier,
+  // counters, error word, instance state); the records are set up below
+  SS_TRY(launch_prologue(plan, d_bar, d_cnt, d_err, d_state, nullptr, d_inst, d_chunk, st));
   const int64_t recs = s->rows_pad + 1;
   k_init_solve_records<<<nblk(recs), 256, 0, st>>>(s->norm.get(), recs, nullptr, s->wide,
                                                   static_cast<double2*>(at(kOffXrec)),
@@ -1914,7 +2118,7 @@ extern "C" ss_status solve_noalloc(ss_stamp s, const double* f_on_S, double* u_o
   P.max_inner = std::max(1, std::min(max_iter, 200));
   P.max_outer = std::max(1, max_iter);
   P.spin_limit = 2000000000ll;
-  P.rows_slices = plan.row_split ? plan.chunk.back().s1 : 0;
+  P.rows_slices = plan.row_split ? plan.cut_n : 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(plan.grid);
   cfg.blockDim = dim3(plan.block);

@@ -83,6 +83,13 @@ struct SolvePlan {
   int grid = 0, block = 256;
   bool row_split = false;   // single instance: the row-wise CG phases split the slices evenly over the blocks
   long long spin_limit = 2000000000ll;   // bound on each grid-barrier wait (ns); below 0: give up at the first poll
+  // single instance: the chunk cuts are computed on the device from the
+  // device slice table (chunk holds K placeholders); cuts_pending until the
+  // cuts have been written into the workspace's chunk table
+  bool dev_cuts = false, cuts_pending = false;
+  const int32_t* cut_woff = nullptr;
+  int64_t cut_n = 0, cut_ov4 = 0;
+  const int32_t* cut_err = nullptr;   // the stamp's error words: an error empties every chunk
 };
 
 // Device workspace of one solve context (single stamp or batch).
@@ -124,7 +131,7 @@ struct SolveWork {
 // row) or, when null, `wide` for every row.
 ss_status work_alloc(SolveWork& W, int64_t rows_total, const int64_t* norm, const int8_t* wide_rows, bool wide,
                      cudaStream_t st);
-ss_status work_upload(SolveWork& W, const SolvePlan& plan, cudaStream_t st);
+ss_status work_upload(SolveWork& W, SolvePlan& plan, cudaStream_t st);
 ss_status max_grid(int mode, int block, int* grid);
 // mode: 0 FP64 CG, 1 FP32-refined CG, 2 FP64 BiCGStab (ADR operator; cdiag
 // = its complex diagonal, workspace from work_alloc_bicgstab), 3 double-float
@@ -132,7 +139,8 @@ ss_status max_grid(int mode, int block, int* grid);
 ss_status launch_solve(SolveWork& W, const SolvePlan& plan, const OpView& op, const int32_t* slice_inst,
                        const int64_t* norm, const double2* ca64, const float2* ca32, const int32_t* pn,
                        double tol, int max_iter, int mode, cudaStream_t st,
-                       cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr, const double2* cdiag = nullptr);
+                       cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr, const double2* cdiag = nullptr,
+                       bool zeroed = false);   // zeroed: a single-instance prologue reset the words
 ss_status work_alloc_bicgstab(SolveWork& W, cudaStream_t st);
 ss_status work_alloc_df64(SolveWork& W, cudaStream_t st);
 ss_status read_stats(SolveWork& W, int n_inst, ss_solve_stats* stats, ss_status* worst, cudaStream_t st,

@@ -238,7 +238,8 @@ struct ss_stamp_s {
   ss::DevBuf<float2> ca32;            // [s_a] same in FP32
   // neighbour table, sliced ELL with 32-row slices, column-major in a slice
   ss::DevBuf<int32_t> slice_off;      // [n_slices + 1], in units of 32 entries (one per row of a slice)
-  std::vector<int32_t> woff_host;     // host copy of slice_off (read back with the build's sizes; solve plans)
+  std::vector<int32_t> woff_host;     // host copy of slice_off, filled on demand (stamp_host_tables)
+  int32_t max_w = 0;                  // widest slice (entries per row)
   ss::DevBuf<uint32_t> ent;           // [n_ent] col | (j << colbits)
   ss::DevBuf<double2> ecoef64;        // [n_ent] 2 pi^2 (|k|^2 + |l|^2 - |p_j|^2) a_hat_j per entry (FP64 operator)
   ss::DevBuf<float4> ecoefdf;         // [n_ent + 1] the same as double-float, built on first DF64 solve
@@ -268,7 +269,10 @@ struct ss_stamp_s {
   ss::DevBuf<double2> ecoef_h;        // FP64 entry coefficients of the half table
   ss::DevBuf<int64_t> norm_h;         // [rows_pad_h + 1] |k|^2 of the compact rows (0 on padding)
   ss::DevBuf<float4> ecoefdf_h;       // the half table's coefficients as double-float (first DF64 solve)
-  std::vector<int32_t> woff_h_host;
+  std::vector<int32_t> woff_h_host;   // host copy of woff_h, filled on demand (stamp_host_tables)
+  // error words of the build not yet read (stamp_build_pending); the half
+  // system is tentative until they are (stamp_check_pending)
+  bool check_pending = false;
   // right-hand side and solution kept by sparse_spectral_solve (sol_size rows)
   ss::DevBuf<double2> rhs, sol;
   int64_t sol_size = 0;
@@ -316,6 +320,19 @@ ss_status sft_recover_both(const ss_lattice* lat, const ss_trig* a, const ss_tri
 
 // Releases the solver workspace cached for a stamp (solve.cu).
 void drop_solve_ctx(const ss_stamp_s* s);
+
+// stamp_build without its final synchronisation (stamp.cu): the build's error
+// words are left to the caller's next synchronisation.  The caller copies
+// err_dev (4 words) to the host in stream order and passes them to
+// stamp_check_pending after that synchronisation, before the stamp is used
+// from the host or handed out.
+ss_status stamp_build_pending(const ss_sparse* a_hat, const int32_t* f_freq, int64_t n_f, int32_t N, ss_stamp* out,
+                              cudaStream_t st);
+ss_status stamp_check_pending(ss_stamp_s* S, const int32_t* e);
+// Host copies of the slice offsets (woff_host, woff_h_host) for host-side
+// planning (batches); one synchronisation when they are missing, which also
+// settles a pending check.
+ss_status stamp_host_tables(ss_stamp_s* S, cudaStream_t st);
 
 }  // namespace ss
 

@@ -676,8 +676,9 @@ __global__ void __launch_bounds__(kNbrThreads) k_neighbors(KeyParams P, const ui
 
 // Per-slice widths (max over the slice's 32 rows) and nnz from the row counts.
 __global__ void k_slice_widths(const int32_t* __restrict__ cnt, int64_t size, int64_t rows_pad, int32_t* slice_w,
-                               unsigned long long* nnz) {
+                               unsigned long long* nnz, int32_t* wmax) {
   __shared__ unsigned s_tot[8];   // launched with 256 threads
+  __shared__ int32_t s_w[8];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int32_t c = i < size ? cnt[i] : 0;
   const int32_t w = __reduce_max_sync(0xffffffffu, c);
@@ -685,12 +686,18 @@ __global__ void k_slice_widths(const int32_t* __restrict__ cnt, int64_t size, in
   if ((threadIdx.x & 31) == 0) {
     if (i < rows_pad) slice_w[i / kSlice] = w;   // rows_pad is a multiple of the warp
     s_tot[threadIdx.x >> 5] = tot;
+    s_w[threadIdx.x >> 5] = w;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {   // one atomic per block
+  if (threadIdx.x == 0) {   // one atomic of each kind per block
     unsigned long long b = 0;
-    for (int q = 0; q < 8; ++q) b += s_tot[q];
+    int32_t m = 0;
+    for (int q = 0; q < 8; ++q) {
+      b += s_tot[q];
+      m = max(m, s_w[q]);
+    }
     atomicAdd(nnz, b);
+    atomicMax(wmax, m);
   }
 }
 
@@ -890,7 +897,7 @@ __global__ void k_scatter_vals(const int64_t* __restrict__ idx, const double2* _
   if (i >= n) return;
   const int64_t r = idx[i];
   if (r >= 0) out[r] = v[i];
-  else atomicAdd(outside, 1ull);
+  else if (outside) atomicAdd(outside, 1ull);   // counted only when asked for
 }
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -1162,11 +1169,14 @@ __global__ void k_half_fill(const int32_t* __restrict__ plus_rows, int64_t n_plu
                             const int32_t* __restrict__ woff, const uint32_t* __restrict__ ent,
                             const double2* __restrict__ ecoef, uint32_t colmask, int colbits, int64_t pad_col,
                             int colbits_h, int j0, const int32_t* __restrict__ hpos,
-                            const int32_t* __restrict__ woff_h, uint32_t* ent_h, double2* ecoef_h, bool real) {
+                            const int32_t* __restrict__ woff_h, uint32_t* ent_h, double2* ecoef_h, bool real,
+                            const int32_t* __restrict__ err) {
   const double* ecoef_re = reinterpret_cast<const double*>(ecoef);
   double* ecoef_h_re = reinterpret_cast<double*>(ecoef_h);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= rows_pad_h) return;
+  // a scan that gave up (err[0]) leaves woff_h and the compact positions
+  // incomplete: nothing is written from them
+  if (i >= rows_pad_h || __ldg(err) != 0) return;
   const int64_t sh = i / kSlice;
   const int64_t base_h = (int64_t)woff_h[sh] * kSlice + (i % kSlice);
   const int w_h = woff_h[sh + 1] - woff_h[sh];
@@ -1220,8 +1230,7 @@ static ss_status build_half(ss_stamp_s* S, cudaStream_t st) {
   S->n_slices_h = S->rows_pad_h / kSlice;
   S->colbits_h = 31 - S->jbits;
   if (S->colbits_h < 1 || S->rows_pad_h + 1 > ((int64_t)1 << S->colbits_h)) return SS_OK;   // no room for the conj bit
-  int32_t max_w = 0;
-  for (int64_t q = 0; q < S->n_slices; ++q) max_w = std::max(max_w, S->woff_host[q + 1] - S->woff_host[q]);
+  const int32_t max_w = S->max_w;
   const KeyParams P = make_key_params(S->key);
   DevBuf<int32_t> plus, ppos, slice_w;
   DevBuf<int64_t> total;
@@ -1273,17 +1282,33 @@ static ss_status build_half(ss_stamp_s* S, cudaStream_t st) {
     k_half_fill<<<nblk(S->rows_pad_h), 256, 0, st>>>(S->plus_rows.get(), n_plus, S->rows_pad_h, S->slice_off.get(),
                                                      S->ent.get(), S->ecoef64.get(), colmask, colbits_of(S->jbits),
                                                      S->rows_pad, S->colbits_h, S->j0, S->hpos.get(), S->woff_h.get(),
-                                                     S->ent_h.get(), S->ecoef_h.get(), S->a_real);
+                                                     S->ent_h.get(), S->ecoef_h.get(), S->a_real, S->err_dev.get());
   }
   SS_LAUNCH_CHECK();
-  S->woff_h_host.resize(S->n_slices_h + 1);
-  S->half_ok = true;   // confirmed by the caller's read-back of the mirror flag
+  S->woff_h_host.clear();   // host copy on demand (stamp_host_tables)
+  S->half_ok = true;        // confirmed by the caller's read-back of the mirror flag
+  return SS_OK;
+}
+
+// Error words of a stamp build (err_dev[0]: a device wait that gave up or
+// the table exhausted; [3]: some -k of the half system not found).
+static ss_status check_words(ss_stamp_s* S, const int32_t* e) {
+  S->check_pending = false;
+  if (e[0] == SS_ERR_TIMEOUT) SS_FAIL(SS_ERR_TIMEOUT, "stamp: a bounded device wait gave up");
+  if (e[0]) SS_FAIL((ss_status)e[0], "stamp: hash table exhausted");
+  if (S->half_ok && e[3]) S->half_ok = false;   // some -k not in S: no half system
   return SS_OK;
 }
 
 // Neighbour table (sliced ELL), FP64 entry coefficients and apply scratch
-// for the current set; synchronises and settles the stamp's buffers.
-static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
+// for the current set; settles the stamp's buffers.  The build synchronises
+// once for the table's size and once at its end for the error words; with
+// `defer` the second synchronisation is left to the caller's next one (the
+// one-call pipeline's solve, which copies the words in stream order and
+// checks them with its statistics, stamp_check_pending).  Until then the
+// half system is only tentative: its consumers are guarded against a failed
+// build (no read or write outside the stamp's buffers).
+static ss_status build_operator(ss_stamp_s* S, cudaStream_t st, bool defer) {
   const KeyParams P = make_key_params(S->key);
   const int s_a = S->s_a;
   if (S->size >= ((int64_t)1 << 31)) SS_FAIL(SS_ERR_KEY_RANGE, "stamp: |S| = %lld too large", (long long)S->size);
@@ -1298,7 +1323,7 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
     SS_TRY(compact_table(S, st));
   }
   if (S->cap > ((int64_t)1 << 32)) SS_FAIL(SS_ERR_KEY_RANGE, "stamp: hash table of %lld slots", (long long)S->cap);
-  DevBuf<int32_t> nbr_lo, nbr_hi, cnt, slice_w;
+  DevBuf<int32_t> nbr_lo, nbr_hi, cnt, slice_w, d_wmax;
   DevBuf<unsigned long long> d_nnz;
   DevBuf<int64_t> d_total;
   NbrView nb;
@@ -1313,9 +1338,11 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   SS_TRY(cnt.alloc_tmp(S->size, st));
   SS_TRY(slice_w.alloc_tmp(S->n_slices + 1, st));
   SS_TRY(d_nnz.alloc_tmp(1, st));
+  SS_TRY(d_wmax.alloc_tmp(1, st));
   SS_TRY(d_total.alloc_tmp(1, st));
   SS_TRY(fill_small(st, {{S->norm.get() + S->size, (S->rows_pad + 1 - S->size) * sizeof(int64_t), 0},
                          {d_nnz.get(), sizeof(unsigned long long), 0},
+                         {d_wmax.get(), sizeof(int32_t), 0},
                          {slice_w.get(), (S->n_slices + 1) * sizeof(int32_t), 0}}));
   {
     ProfScope prof_("k_neighbors", st, true);
@@ -1328,7 +1355,8 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
   }
   {
     ProfScope prof_("k_slice_widths", st);
-    k_slice_widths<<<nblk(S->rows_pad), 256, 0, st>>>(cnt.get(), S->size, S->rows_pad, slice_w.get(), d_nnz.get());
+    k_slice_widths<<<nblk(S->rows_pad), 256, 0, st>>>(cnt.get(), S->size, S->rows_pad, slice_w.get(), d_nnz.get(),
+                                                      d_wmax.get());
   }
   SS_LAUNCH_CHECK();
   SS_TRY(S->slice_off.alloc(S->n_slices + 1, st));
@@ -1336,11 +1364,16 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
                        S->err_dev.get(), st));
   int64_t total_w = 0;
   unsigned long long hnnz = 0;
-  S->woff_host.resize(S->n_slices + 1);
+  int32_t e0 = 0;
+  S->woff_host.clear();   // host copy on demand (stamp_host_tables)
   SS_TRY(read_back(st, {{&total_w, d_total.get(), sizeof(int64_t)},
                         {&hnnz, d_nnz.get(), sizeof(hnnz)},
                         {&S->zero_idx, S->zidx_dev.get(), sizeof(int64_t)},
-                        {S->woff_host.data(), S->slice_off.get(), (S->n_slices + 1) * sizeof(int32_t)}}));
+                        {&S->max_w, d_wmax.get(), sizeof(int32_t)},
+                        {&e0, S->err_dev.get(), sizeof(int32_t)}}));
+  // the slice offsets size and place every entry below: a scan that gave up
+  // is reported before they are used
+  if (e0 == SS_ERR_TIMEOUT) SS_FAIL(SS_ERR_TIMEOUT, "stamp: a bounded device wait gave up");
   S->nnz = (int64_t)hnnz;
   S->n_ent = total_w * kSlice;
   SS_TRY(S->ent.alloc(S->n_ent + 1, st));
@@ -1369,16 +1402,15 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st) {
                                                         S->rec64.get());
   SS_LAUNCH_CHECK();
   SS_TRY(build_half(S, st));
-  int32_t e[4] = {0, 0, 0, 0};
-  if (S->half_ok)
-    SS_TRY(read_back(st, {{e, S->err_dev.get(), sizeof(e)},
-                          {S->woff_h_host.data(), S->woff_h.get(), (S->n_slices_h + 1) * sizeof(int32_t)}}));
-  else
+  if (defer) {
+    S->check_pending = true;
+  } else {
+    int32_t e[4] = {0, 0, 0, 0};
     SS_TRY(read_back(st, {{e, S->err_dev.get(), sizeof(e)}}));
-  if (e[0] == SS_ERR_TIMEOUT) SS_FAIL(SS_ERR_TIMEOUT, "stamp: a bounded device wait gave up");
-  if (e[0]) SS_FAIL((ss_status)e[0], "stamp: hash table exhausted");
-  if (S->half_ok && e[3]) S->half_ok = false;   // some -k not in S: no half system
-  // the stamp's buffers outlive this call's stream (synchronised above)
+    SS_TRY(check_words(S, e));
+  }
+  // the stamp's buffers outlive this call's stream (synchronised above, or
+  // by the caller's next synchronisation before the stamp is handed out)
   S->keys.settle(); S->hl.settle(); S->level.settle(); S->norm.settle(); S->table.settle();
   S->afreq.settle(); S->stepkey.settle(); S->stepg.settle(); S->pnorm.settle(); S->pn32.settle(); S->aval.settle();
   S->ca64.settle(); S->ca32.settle(); S->slice_off.settle(); S->ent.settle(); S->ecoef64.settle();
@@ -1417,7 +1449,7 @@ static ss_status relayout(ss_stamp_s* S, const KeyLayout& L2, cudaStream_t st) {
 }
 
 static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t* f_freq, int64_t n_f, int N,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool defer = false) {
   const int d = a_hat->d;
   const int s_a = (int)a_hat->n;
   S->d = d;
@@ -1547,7 +1579,7 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   const int64_t rows = (int64_t)(S->keys.n / L.WT), keep = S->size + kSlice + 1;
   if (rows > 4 * keep && (double)rows * (8.0 * L.WT + 9.0) > 64e6) SS_TRY(resize_keys(S, keep, st));
   ProfScope prof_("stamp_operator", st);
-  return build_operator(S, st);
+  return build_operator(S, st, defer);
 }
 
 // Buffers replaced during an extension are freed on the extension's stream,
@@ -1599,14 +1631,11 @@ static ss_status extend_impl(ss_stamp_s* S, int levels, cudaStream_t st) {
   }
   SS_TRY(run_levels(S, S->N + 1, N2, st));
   S->N = N2;
-  return build_operator(S, st);
+  return build_operator(S, st, false);
 }
-}  // namespace ss
 
-using namespace ss;
-
-extern "C" ss_status stamp_build(const ss_sparse* a_hat, const int32_t* f_freq, int64_t n_f, int32_t N, ss_stamp* out,
-                                 void* stream) {
+static ss_status build_entry(const ss_sparse* a_hat, const int32_t* f_freq, int64_t n_f, int32_t N, ss_stamp* out,
+                             cudaStream_t st, bool defer) {
   if (!a_hat || !out || !f_freq || !a_hat->freq || !a_hat->val)
     SS_FAIL(SS_ERR_INVALID, "stamp_build: null argument");
   if (a_hat->d < 1 || a_hat->n < 1 || n_f < 1 || N < 0 || N > 120)
@@ -1616,16 +1645,50 @@ extern "C" ss_status stamp_build(const ss_sparse* a_hat, const int32_t* f_freq, 
   ss_stamp_s* S = new ss_stamp_s();
   ss_status s;
   {
-    ProfScope prof_("stamp_build", as_stream(stream));
-    s = build_impl(S, a_hat, f_freq, n_f, N, as_stream(stream));
+    ProfScope prof_("stamp_build", st);
+    s = build_impl(S, a_hat, f_freq, n_f, N, st, defer);
   }
   if (s != SS_OK) {
-    cudaStreamSynchronize(as_stream(stream));
+    cudaStreamSynchronize(st);
     delete S;
     return s;
   }
   *out = S;
   return SS_OK;
+}
+
+ss_status stamp_build_pending(const ss_sparse* a_hat, const int32_t* f_freq, int64_t n_f, int32_t N, ss_stamp* out,
+                              cudaStream_t st) {
+  return build_entry(a_hat, f_freq, n_f, N, out, st, true);
+}
+
+ss_status stamp_check_pending(ss_stamp_s* S, const int32_t* e) {
+  return S->check_pending ? check_words(S, e) : SS_OK;
+}
+
+ss_status stamp_host_tables(ss_stamp_s* S, cudaStream_t st) {
+  const bool need_full = (int64_t)S->woff_host.size() != S->n_slices + 1;
+  const bool need_half = S->half_ok && (int64_t)S->woff_h_host.size() != S->n_slices_h + 1;
+  if (!need_full && !need_half && !S->check_pending) return SS_OK;
+  int32_t e[4] = {0, 0, 0, 0};
+  if (need_full) S->woff_host.resize(S->n_slices + 1);
+  if (need_half) S->woff_h_host.resize(S->n_slices_h + 1);
+  SS_TRY(read_back(st, {{e, S->err_dev.get(), sizeof(e)},
+                        {need_full ? S->woff_host.data() : nullptr, S->slice_off.get(),
+                         need_full ? (S->n_slices + 1) * sizeof(int32_t) : 0},
+                        {need_half ? S->woff_h_host.data() : nullptr, S->woff_h.get(),
+                         need_half ? (S->n_slices_h + 1) * sizeof(int32_t) : 0}}));
+  SS_TRY(stamp_check_pending(S, e));
+  if (!S->half_ok) S->woff_h_host.clear();
+  return SS_OK;
+}
+}  // namespace ss
+
+using namespace ss;
+
+extern "C" ss_status stamp_build(const ss_sparse* a_hat, const int32_t* f_freq, int64_t n_f, int32_t N, ss_stamp* out,
+                                 void* stream) {
+  return build_entry(a_hat, f_freq, n_f, N, out, as_stream(stream), false);
 }
 
 namespace {
@@ -1827,8 +1890,10 @@ extern "C" ss_status stamp_scatter(ss_stamp s, const ss_sparse* g, double* out, 
   DevBuf<int64_t> idx;
   DevBuf<unsigned long long> outside;
   SS_TRY(idx.alloc_tmp(g->n, st));
-  SS_TRY(outside.alloc_tmp(1, st));
-  SS_CUDA(cudaMemsetAsync(outside.get(), 0, sizeof(unsigned long long), st));
+  if (n_outside) {
+    SS_TRY(outside.alloc_tmp(1, st));
+    SS_CUDA(cudaMemsetAsync(outside.get(), 0, sizeof(unsigned long long), st));
+  }
   SS_TRY(stamp_lookup(s, g->freq, g->n, idx.get(), stream));
   k_scatter_vals<<<nblk(g->n), 256, 0, st>>>(idx.get(), reinterpret_cast<const double2*>(g->val), g->n,
                                              reinterpret_cast<double2*>(out), outside.get());
