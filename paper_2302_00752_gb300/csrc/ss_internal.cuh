@@ -132,13 +132,13 @@ struct DevBuf {
   T* p = nullptr;
   size_t n = 0;
   cudaStream_t s = nullptr;
-  int tmp = 0;   // 1: scratch block, 2: pool fallback of alloc_tmp
+  int tmp = 0;   // 1: scratch block, 2: pool fallback of alloc_tmp, 3: view of another buffer (not owned)
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() { release(); }
   void release() {
-    if (p) {
+    if (p && tmp != 3) {
       if (tmp == 1) {
         scratch_give(p);
       } else {
@@ -169,6 +169,15 @@ struct DevBuf {
     return r;
   }
   ss_status ensure_tmp(size_t count, cudaStream_t stream) { return count <= n ? SS_OK : alloc_tmp(count, stream); }
+  // count elements at q inside a buffer that another DevBuf owns (an arena);
+  // released without a free, reallocated on its own by alloc()
+  void view(T* q, size_t count) {
+    release();
+    p = q;
+    n = count;
+    s = nullptr;
+    tmp = 3;
+  }
   void settle() { s = nullptr; }
   ss_status alloc(size_t count, cudaStream_t stream = nullptr) {
     release();
@@ -276,6 +285,7 @@ struct ss_stamp_s {
   // right-hand side and solution kept by sparse_spectral_solve (sol_size rows)
   ss::DevBuf<double2> rhs, sol;
   int64_t sol_size = 0;
+  ss::DevBuf<unsigned char> small_arena;   // one allocation for err_dev, zidx_dev and the step tables
   ss::DevBuf<int32_t> err_dev;        // [4] device-side error words
   ss::DevBuf<int64_t> zidx_dev;       // canonical index of k = 0, or -1
 };

@@ -1037,19 +1037,34 @@ static ss_status make_layout(int d, int64_t maxabs, KeyLayout* out) {
   return SS_OK;
 }
 
+// Candidate buffers of the levels (slot of each candidate, the winners in
+// candidate order): sized once by the caller when a bound is known, else
+// grown per level.
+struct LevelTmp {
+  DevBuf<int64_t> slot_of, cand;
+};
+constexpr int64_t kLevelTmpPresize = 512ll << 20;   // bytes of both, at most
+
 // Levels n_from..n_to of the breadth-first construction (see the file comment).
-static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st) {
+static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st, LevelTmp& lt) {
   const KeyParams P = make_key_params(S->key);
   const int s_a = S->s_a;
-  DevBuf<int64_t> slot_of, d_total, cand;
+  DevBuf<int64_t> d_total;
+  DevBuf<int64_t>& slot_of = lt.slot_of;
+  DevBuf<int64_t>& cand = lt.cand;
   SS_TRY(d_total.alloc_tmp(1, st));
   for (int n = n_from; n <= n_to; ++n) {
     const int64_t par0 = S->level_start[n - 1], n_par = S->level_start[n] - par0;
     const int64_t ncand = n_par * s_a;
     if (ncand >= ((int64_t)1 << 32) - 1) SS_FAIL(SS_ERR_KEY_RANGE, "stamp: too many candidates at level %d", n);
     if (ncand == 0) { S->level_start.push_back(S->size); continue; }
-    SS_TRY(grow_table(S, S->size + n_par * (s_a - 1), P, st, S->err_dev.get()));
-    SS_TRY(grow_keys(S, S->size + n_par * (s_a - 1), st));
+    // room for every candidate that may be new, but never more than the
+    // multiset bound |S^n| <= |F| C(s_a - 1 + n, n) (the build presized for it)
+    int64_t need = S->size + n_par * (s_a - 1);
+    const int64_t bnd = stamp_size_bound(S->level_start[1], s_a, n, kPresizeCap);
+    if (bnd < kPresizeCap) need = std::min(need, bnd);
+    SS_TRY(grow_table(S, need, P, st, S->err_dev.get()));
+    SS_TRY(grow_keys(S, need, st));
     SS_TRY(slot_of.ensure_tmp(ncand, st));
     SS_TRY(cand.ensure_tmp(ncand, st));
     {
@@ -1072,6 +1087,7 @@ static ss_status run_levels(ss_stamp_s* S, int n_from, int n_to, cudaStream_t st
     SS_TRY(read_back(st, {{&added, d_total.get(), sizeof(int64_t)}, {&e, S->err_dev.get(), sizeof(int32_t)}}));
     if (e == SS_ERR_TIMEOUT) SS_FAIL(SS_ERR_TIMEOUT, "stamp: a bounded device wait gave up at level %d", n);
     if (e) SS_FAIL((ss_status)e, "stamp: hash table exhausted at level %d", n);
+    SS_TRY(grow_keys(S, S->size + added, st));   // the exact count: the rows k_finalize writes always fit
     if (added > 0) {
       ProfScope prof_("k_finalize", st);
       SS_DISPATCH_WT(S->key.WT, (k_finalize<WT><<<nblk(added, kFinThreads), kFinThreads, 0, st>>>(
@@ -1414,7 +1430,7 @@ static ss_status build_operator(ss_stamp_s* S, cudaStream_t st, bool defer) {
   S->keys.settle(); S->hl.settle(); S->level.settle(); S->norm.settle(); S->table.settle();
   S->afreq.settle(); S->stepkey.settle(); S->stepg.settle(); S->pnorm.settle(); S->pn32.settle(); S->aval.settle();
   S->ca64.settle(); S->ca32.settle(); S->slice_off.settle(); S->ent.settle(); S->ecoef64.settle();
-  S->nw32.settle(); S->rec64.settle(); S->err_dev.settle(); S->zidx_dev.settle();
+  S->nw32.settle(); S->rec64.settle(); S->err_dev.settle(); S->zidx_dev.settle(); S->small_arena.settle();
   S->mirror.settle(); S->hpos.settle(); S->plus_rows.settle(); S->woff_h.settle(); S->ent_h.settle();
   S->ecoef_h.settle(); S->norm_h.settle();
   S->bval.settle(); S->cval.settle(); S->diag64.settle();
@@ -1456,17 +1472,40 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   S->N = N;
   S->s_a = s_a;
 
-  DevBuf<int32_t> Fs, As, rank, rank_a;
-  DevBuf<double2> avs;
+  // The error words, the zero index and the step tables (canonical step
+  // order) as views of one allocation; stepkey sized for the widest packed
+  // key, since the layout is known only after the preparation's read-back.
+  {
+    size_t off = 0;
+    auto at = [&](size_t bytes) {
+      const size_t o = off;
+      off += (bytes + 255) / 256 * 256;
+      return o;
+    };
+    const size_t o_err = at(4 * sizeof(int32_t)), o_z = at(sizeof(int64_t)),
+                 o_af = at((size_t)s_a * d * sizeof(int32_t)), o_av = at(s_a * sizeof(double2)),
+                 o_sk = at((size_t)s_a * kMaxWords * sizeof(uint64_t)), o_sg = at(s_a * sizeof(uint64_t)),
+                 o_pn = at(s_a * sizeof(int64_t)), o_p32 = at(s_a * sizeof(int32_t)),
+                 o_c64 = at(s_a * sizeof(double2)), o_c32 = at(s_a * sizeof(float2));
+    SS_TRY(S->small_arena.alloc(off, st));
+    unsigned char* b = S->small_arena.get();
+    S->err_dev.view(reinterpret_cast<int32_t*>(b + o_err), 4);
+    S->zidx_dev.view(reinterpret_cast<int64_t*>(b + o_z), 1);
+    S->afreq.view(reinterpret_cast<int32_t*>(b + o_af), (size_t)s_a * d);
+    S->aval.view(reinterpret_cast<double2*>(b + o_av), s_a);
+    S->stepkey.view(reinterpret_cast<uint64_t*>(b + o_sk), (size_t)s_a * kMaxWords);
+    S->stepg.view(reinterpret_cast<uint64_t*>(b + o_sg), s_a);
+    S->pnorm.view(reinterpret_cast<int64_t*>(b + o_pn), s_a);
+    S->pn32.view(reinterpret_cast<int32_t*>(b + o_p32), s_a);
+    S->ca64.view(reinterpret_cast<double2*>(b + o_c64), s_a);
+    S->ca32.view(reinterpret_cast<float2*>(b + o_c32), s_a);
+  }
+  DevBuf<int32_t> Fs, rank, rank_a;
   DevBuf<PrepOut> prep;
   SS_TRY(Fs.alloc_tmp(n_f * d, st));
-  SS_TRY(As.alloc_tmp((size_t)s_a * d, st));
-  SS_TRY(avs.alloc_tmp(s_a, st));
   SS_TRY(rank.alloc_tmp(n_f, st));
   SS_TRY(rank_a.alloc_tmp(s_a, st));
   SS_TRY(prep.alloc_tmp(1, st));
-  SS_TRY(S->err_dev.alloc(4, st));
-  SS_TRY(S->zidx_dev.alloc(1, st));
   int32_t* err = S->err_dev.get();
   SS_TRY(fill_small(st, {{err, 4 * sizeof(int32_t), 0}, {S->zidx_dev.get(), sizeof(int64_t), 0xff},
                          {rank.get(), n_f * sizeof(int32_t), 0}, {rank_a.get(), s_a * sizeof(int32_t), 0}}));
@@ -1490,12 +1529,33 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
     lex_rank(a_hat->freq, s_a, cha, nca, rank_a.get(), err + 2);
   }
   k_scatter_rows<<<nblk(s_a), 256, 0, st>>>(a_hat->freq, reinterpret_cast<const double2*>(a_hat->val), s_a, d,
-                                            rank_a.get(), As.get(), avs.get());
+                                            rank_a.get(), S->afreq.get(), S->aval.get());
   {
     ProfScope prof_("k_prep", st);
-    k_prep<<<1, kPrepThreads, 0, st>>>(Fs.get(), n_f, As.get(), avs.get(), s_a, d, prep.get());
+    k_prep<<<1, kPrepThreads, 0, st>>>(Fs.get(), n_f, S->afreq.get(), S->aval.get(), s_a, d, prep.get());
   }
   SS_LAUNCH_CHECK();
+  // While the GPU ranks and prepares: the buffers whose sizes follow from
+  // |F|, s_a and N alone.  The table, the rows' linear forms, levels and
+  // norms, and the candidate buffers of the levels are sized at once for the
+  // whole construction when the bound fits, so that the levels neither grow
+  // (copy, rehash) nor allocate; the keys wait for the packed layout.
+  S->level_start.assign(1, 0);
+  const int64_t pre = std::max<int64_t>(n_f, stamp_size_bound(n_f, s_a, N, kPresizeCap));
+  SS_TRY(grow_table(S, pre, KeyParams{}, st, err));
+  SS_TRY(S->hl.alloc(pre, st));
+  SS_TRY(S->level.alloc(pre, st));
+  SS_TRY(S->norm.alloc(pre + kSlice + 1, st));
+  LevelTmp lt;
+  if (N >= 1) {
+    // parents of the last level: |S^{N-1}| <= the same multiset bound
+    const int64_t par = N >= 2 ? stamp_size_bound(n_f, s_a, N - 1, kPresizeCap) : n_f;
+    const int64_t ncand = par * s_a;
+    if (par < kPresizeCap && ncand * 2 * (int64_t)sizeof(int64_t) <= kLevelTmpPresize) {
+      SS_TRY(lt.slot_of.alloc_tmp(ncand, st));
+      SS_TRY(lt.cand.alloc_tmp(ncand, st));
+    }
+  }
   PrepOut h{};
   int32_t herr[4];
   SS_TRY(read_back(st, {{&h, prep.get(), sizeof(h)}, {herr, err, sizeof(herr)}}));
@@ -1529,31 +1589,18 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   S->jbits = std::max(jb, 1);
 
   if (S->a_real) {
-    k_real_part<<<nblk(s_a), 256, 0, st>>>(avs.get(), s_a);
+    k_real_part<<<nblk(s_a), 256, 0, st>>>(S->aval.get(), s_a);
     SS_LAUNCH_CHECK();
   }
 
-  // steps and coefficients in canonical order
-  SS_TRY(S->afreq.alloc((size_t)s_a * d, st));
-  SS_CUDA(cudaMemcpyAsync(S->afreq.get(), As.get(), (size_t)s_a * d * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-  SS_TRY(S->aval.alloc(s_a, st));
-  SS_CUDA(cudaMemcpyAsync(S->aval.get(), avs.get(), s_a * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-  SS_TRY(S->stepkey.alloc((size_t)s_a * L.WT, st));
-  SS_TRY(S->stepg.alloc(s_a, st));
-  SS_TRY(S->pnorm.alloc(s_a, st));
-  SS_TRY(S->pn32.alloc(s_a, st));
-  SS_TRY(S->ca64.alloc(s_a, st));
-  SS_TRY(S->ca32.alloc(s_a, st));
-  SS_TRY(launch_steps(P, As.get(), avs.get(), s_a, S->stepkey.get(), S->stepg.get(), S->pnorm.get(), S->pn32.get(),
-                      S->wide, S->ca64.get(), S->ca32.get(), st));
+  // steps and coefficients in canonical order (afreq and aval were written
+  // in that order by the scatter above)
+  SS_TRY(launch_steps(P, S->afreq.get(), S->aval.get(), s_a, S->stepkey.get(), S->stepg.get(), S->pnorm.get(),
+                      S->pn32.get(), S->wide, S->ca64.get(), S->ca32.get(), st));
   SS_LAUNCH_CHECK();
 
-  // level 0; keys and table sized at once for the whole construction when
-  // the bound fits, so that the levels do not grow (copy, rehash) them
-  S->level_start.assign(1, 0);
-  const int64_t pre = std::max<int64_t>(n_f, stamp_size_bound(n_f, s_a, N, kPresizeCap));
-  SS_TRY(grow_keys(S, pre, st));
-  SS_TRY(grow_table(S, pre, P, st, err));
+  // level 0
+  SS_TRY(S->keys.alloc((size_t)pre * L.WT, st));
   {
     ProfScope prof_("k_level0", st);
     if (d > 16) {
@@ -1572,7 +1619,7 @@ static ss_status build_impl(ss_stamp_s* S, const ss_sparse* a_hat, const int32_t
   S->level_start.push_back(n_f);
   {
     ProfScope prof_("stamp_levels", st);
-    SS_TRY(run_levels(S, 1, N, st));
+    SS_TRY(run_levels(S, 1, N, st, lt));
   }
   // give back a large over-reservation of the size bound (the keys stay for
   // lookups, extension and export; the norms are read up to rows_pad + 1)
@@ -1629,7 +1676,8 @@ static ss_status extend_impl(ss_stamp_s* S, int levels, cudaStream_t st) {
                         S->pn32.get(), S->wide, S->ca64.get(), S->ca32.get(), st));
     SS_LAUNCH_CHECK();
   }
-  SS_TRY(run_levels(S, S->N + 1, N2, st));
+  LevelTmp lt;
+  SS_TRY(run_levels(S, S->N + 1, N2, st, lt));
   S->N = N2;
   return build_operator(S, st, false);
 }
