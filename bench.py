@@ -254,10 +254,10 @@ KERNEL_TRAFFIC = {
                  "note": "ncu capture at M = 2^23 (137.43 MB) scaled by the tiles to M = 2^26 (x8); "
                          "profiles/k_pr_eval_fwd_cfg5_M2e23.md"},
     "k_neighbors": {"sources": ["paper_2302_00752_gb300/csrc/stamp.cu", "paper_2302_00752_gb300/csrc/keys.cuh"],
-                    "source_sha16": "1a39ebc412376044", "dram_bytes_per_launch": 957.29e6,
+                    "source_sha16": "ff6ea75e5dd196e0", "dram_bytes_per_launch": 966.38e6,
                     "note": "ncu capture of the d = 100 stamp (full size); profiles/k_neighbors_insert_finalize_cfg5.md"},
     "k_solve<0>": {"sources": ["paper_2302_00752_gb300/csrc/solve.cu", "paper_2302_00752_gb300/csrc/apply.cuh"],
-                   "source_sha16": "3ac2e59f68b743eb", "dram_bytes_per_launch": 1230.15e6,
+                   "source_sha16": "9dcef38d48f2e20e", "dram_bytes_per_launch": 1022.51e6,
                    "note": "ncu capture of the d = 100 FP64 half-system solve (full size); "
                            "profiles/k_solve_fp64_half_cfg5.md"},
 }
