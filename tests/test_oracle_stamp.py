@@ -105,3 +105,38 @@ def test_symmetric_F_gives_symmetric_S():
 def test_duplicate_F_rejected():
     with pytest.raises(ValueError):
         stamp.stamp_bfs([[0], [1], [-1]], [[2], [2]], 1)
+
+
+def multiset_bound(n_f, s_a, n):
+    """|F| C(s_a - 1 + n, n): F plus a multiset of at most n of the s_a - 1
+    nonzero steps (the count the GPU build presizes its table and keys by)."""
+    from math import comb
+    return n_f * comb(s_a - 1 + n, n)
+
+
+@pytest.mark.parametrize("seed,symmetric", [(0, True), (1, True), (2, False), (3, False), (4, True)])
+def test_multiset_count_bounds_every_level(seed, symmetric):
+    # |S^n| <= |F| C(s_a - 1 + n, n) for every level n, whatever the steps
+    rng = np.random.default_rng(seed)
+    d = 3
+    P = rng.integers(-2, 3, size=(3, d))
+    P = P[np.any(P != 0, axis=1)]
+    A = np.vstack([np.zeros((1, d), int), P, -P]) if symmetric else np.vstack([np.zeros((1, d), int), P])
+    A = np.unique(A, axis=0)
+    F = np.unique(rng.integers(-3, 4, size=(5, d)), axis=0)
+    S, lvl = stamp.stamp_bfs(A, F, 4)
+    for n in range(5):
+        assert int(np.sum(lvl <= n)) <= multiset_bound(len(F), len(A), n)
+
+
+@pytest.mark.parametrize("seed,d,s_a,nf,N", [(0, 6, 5, 3, 3), (1, 4, 7, 2, 2), (2, 8, 4, 4, 4)])
+def test_multiset_count_attained_without_cancellation(seed, d, s_a, nf, N):
+    # generic steps without their negations: every multiset of at most N steps
+    # gives a distinct sum, so |S^N| equals the count (it is exact, not slack)
+    rng = np.random.default_rng(seed)
+    P = rng.integers(-10**4, 10**4, size=(s_a - 1, d))
+    A = np.vstack([np.zeros((1, d), int), P])
+    F = rng.integers(-10**4, 10**4, size=(nf, d))
+    S, lvl = stamp.stamp_bfs(A, F, N)
+    for n in range(N + 1):
+        assert int(np.sum(lvl <= n)) == multiset_bound(nf, s_a, n)
