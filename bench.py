@@ -257,7 +257,7 @@ KERNEL_TRAFFIC = {
                     "source_sha16": "ff6ea75e5dd196e0", "dram_bytes_per_launch": 966.38e6,
                     "note": "ncu capture of the d = 100 stamp (full size); profiles/k_neighbors_insert_finalize_cfg5.md"},
     "k_solve<0>": {"sources": ["paper_2302_00752_gb300/csrc/solve.cu", "paper_2302_00752_gb300/csrc/apply.cuh"],
-                   "source_sha16": "9dcef38d48f2e20e", "dram_bytes_per_launch": 1022.51e6,
+                   "source_sha16": "4239627e3c9dc49d", "dram_bytes_per_launch": 1022.51e6,
                    "note": "ncu capture of the d = 100 FP64 half-system solve (full size); "
                            "profiles/k_solve_fp64_half_cfg5.md"},
 }

@@ -1265,9 +1265,9 @@ static ss_status launch_prologue(SolvePlan& plan, unsigned* bar, int* counters, 
   p.chunk = chunk;
   const size_t smem =
       p.cuts ? ((plan.cut_n + 1 <= kPlanSmemWoff ? (size_t)kPlanSmemWoff : 0) + (size_t)p.K + 1) * sizeof(int32_t) : 0;
-  static const cudaError_t attr = cudaFuncSetAttribute(k_solve_prologue, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)((kPlanSmemWoff + kPlanMaxK + 1) * sizeof(int32_t)));
-  SS_CUDA(attr);
+  // the attribute belongs to the current device: set with every planning launch
+  if (smem > 48 * 1024)
+    SS_CUDA(cudaFuncSetAttribute(k_solve_prologue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_solve_prologue<<<1, kPlanThreads, smem, st>>>(p);
   SS_LAUNCH_CHECK();
   plan.cuts_pending = false;
